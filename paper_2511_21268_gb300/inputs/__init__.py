@@ -1,0 +1,264 @@
+"""Seeded synthetic inputs: IgA stiffness systems K u = F and random vectors.
+
+This module is the only code shared by the CPU oracle and the GPU path.  It
+builds the *inputs* of the AMG-PCG method (the matrix, the right-hand side,
+seeded random fields) and holds none of the method's arithmetic.  The
+numerical work happens in ``iga_gen.c`` (plain C, FP64, no FMA contraction).
+
+Workload recipes (arXiv 2511.21268, Sec. 2 and Sec. 5 for the problem class):
+
+* ``poisson_box(d, n, p)`` -- -Laplace u = f on the unit square/cube, B-splines
+  of degree p, C^{p-1}, n elements per direction, homogeneous Dirichlet data
+  eliminated, f from the manufactured solution u = prod sin(pi x_k).
+  N = (n+p-2)^d.
+* ``poisson_box_random_rhs`` -- same matrix, F = K u_true with u_true ~ N(0,1).
+* ``batch_instances`` -- the mixed batch of 2-D instances with p drawn from
+  {2,3,4} and n from {32..256} by a seeded SplitMix64 stream.
+* ``annulus_kappa`` -- NURBS quarter annulus extruded in z with a log-normal
+  coefficient kappa = exp(g), g a seeded Gaussian field.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .. import _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build_inputs()
+        L = ctypes.CDLL(path)
+        i32, i64, u64, dbl = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        P = ctypes.c_void_p
+        L.iga_rng_u01.argtypes = [u64, i64, P]
+        L.iga_rng_normal.argtypes = [u64, i64, P]
+        L.iga_gauss_legendre.argtypes = [i32, P, P]
+        L.iga_gauss_legendre.restype = i32
+        L.iga_bspline_local.argtypes = [i32, i32, i32, dbl, P, P]
+        L.iga_bspline_all.argtypes = [i32, i32, dbl, P, P]
+        L.iga_1d_matrices.argtypes = [i32, i32, i32, P, P]
+        L.iga_1d_matrices.restype = i32
+        L.iga_num_dofs.argtypes = [i32, i32, i32, i32]
+        L.iga_num_dofs.restype = i64
+        L.iga_nnz.argtypes = [i32, i32, i32, i32]
+        L.iga_nnz.restype = i64
+        L.iga_assemble_kron.argtypes = [i32, i32, i32, i32, P, P, P]
+        L.iga_assemble_kron.restype = i32
+        L.iga_load_sine.argtypes = [i32, i32, i32, i32, i32, P]
+        L.iga_load_sine.restype = i32
+        L.iga_assemble_elem.argtypes = [i32, i32, i32, i32, i32, i32, i32, dbl, dbl, u64, i32, P, P, P, P]
+        L.iga_assemble_elem.restype = i32
+        L.iga_l2_error_sine.argtypes = [i32, i32, i32, i32, P]
+        L.iga_l2_error_sine.restype = dbl
+        L.iga_csr_apply.argtypes = [i64, P, P, P, P, P]
+        L.iga_kappa_points.argtypes = [i32, dbl, dbl, u64, i64, P, P]
+        L.iga_geom_points.argtypes = [i32, i32, i64, P, P, P]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ----------------------------------------------------------------- RNG ----
+def rng_u01(seed: int, count: int) -> np.ndarray:
+    out = np.empty(count, np.float64)
+    lib().iga_rng_u01(seed & 0xFFFFFFFFFFFFFFFF, count, _p(out))
+    return out
+
+
+def rng_normal(seed: int, count: int) -> np.ndarray:
+    out = np.empty(count, np.float64)
+    lib().iga_rng_normal(seed & 0xFFFFFFFFFFFFFFFF, count, _p(out))
+    return out
+
+
+def splitmix64(seed: int, count: int) -> list[int]:
+    """Raw 64-bit SplitMix64 outputs (pure Python; used only to draw workload
+    parameters such as the batch's (p, n) pairs)."""
+    M = 0xFFFFFFFFFFFFFFFF
+    out = []
+    for k in range(count):
+        z = (seed + (k + 1) * 0x9E3779B97F4A7C15) & M
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+        out.append(z ^ (z >> 31))
+    return out
+
+
+# ----------------------------------------------------- basis / quadrature ----
+def gauss_legendre(q: int) -> tuple[np.ndarray, np.ndarray]:
+    x = np.empty(q)
+    w = np.empty(q)
+    if lib().iga_gauss_legendre(q, _p(x), _p(w)) != 0:
+        raise ValueError("bad quadrature order")
+    return x, w
+
+
+def bspline_all(n: int, p: int, xi: float) -> tuple[np.ndarray, np.ndarray]:
+    v = np.empty(n + p)
+    d = np.empty(n + p)
+    lib().iga_bspline_all(n, p, float(xi), _p(v), _p(d))
+    return v, d
+
+
+def one_d_matrices(n: int, p: int, nq: int | None = None) -> tuple[np.ndarray, np.ndarray]:
+    nb = n + p
+    K1 = np.empty((nb, nb))
+    M1 = np.empty((nb, nb))
+    if lib().iga_1d_matrices(n, p, nq or p + 1, _p(K1), _p(M1)) != 0:
+        raise ValueError("bad arguments")
+    return K1, M1
+
+
+def num_dofs(d: int, n: int, p: int, with_boundary: bool = False) -> int:
+    return int(lib().iga_num_dofs(d, n, p, int(with_boundary)))
+
+
+def nnz(d: int, n: int, p: int, with_boundary: bool = False) -> int:
+    return int(lib().iga_nnz(d, n, p, int(with_boundary)))
+
+
+# ------------------------------------------------------------ problems ----
+@dataclass
+class Problem:
+    """A CSR system K u = F (FP64, int64 row offsets, int32 sorted columns)."""
+
+    n: int
+    rowptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    F: np.ndarray
+    meta: dict = field(default_factory=dict)
+    u_true: np.ndarray | None = None
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+
+        return sp.csr_matrix((self.val, self.col, self.rowptr), shape=(self.n, self.n))
+
+
+def assemble_kron(d: int, n: int, p: int, with_boundary: bool = False):
+    N = num_dofs(d, n, p, with_boundary)
+    Z = nnz(d, n, p, with_boundary)
+    rowptr = np.empty(N + 1, np.int64)
+    col = np.empty(Z, np.int32)
+    val = np.empty(Z, np.float64)
+    if lib().iga_assemble_kron(d, n, p, int(with_boundary), _p(rowptr), _p(col), _p(val)) != 0:
+        raise ValueError("bad arguments")
+    return rowptr, col, val
+
+
+def load_sine(d: int, n: int, p: int, nq: int | None = None, with_boundary: bool = False) -> np.ndarray:
+    F = np.empty(num_dofs(d, n, p, with_boundary))
+    if lib().iga_load_sine(d, n, p, nq or p + 1, int(with_boundary), _p(F)) != 0:
+        raise ValueError("bad arguments")
+    return F
+
+
+def assemble_elem(d, n, p, nq=None, geom=0, with_boundary=False, kappa=None, fkind=0):
+    """Element-loop assembly. kappa = (M, ell, sigma, seed) or None (kappa=1).
+    fkind 0: f = 1; fkind 1: f = d pi^2 prod sin(pi x_k)."""
+    N = num_dofs(d, n, p, with_boundary)
+    Z = nnz(d, n, p, with_boundary)
+    rowptr = np.empty(N + 1, np.int64)
+    col = np.empty(Z, np.int32)
+    val = np.empty(Z, np.float64)
+    F = np.empty(N)
+    M, ell, sigma, seed = kappa if kappa is not None else (0, 1.0, 0.0, 0)
+    rc = lib().iga_assemble_elem(d, n, p, nq or p + 1, geom, int(with_boundary), M, ell, sigma, seed, fkind,
+                                 _p(rowptr), _p(col), _p(val), _p(F))
+    if rc != 0:
+        raise ValueError("bad arguments")
+    return rowptr, col, val, F
+
+
+def l2_error_sine(d: int, n: int, p: int, coef: np.ndarray, nq: int | None = None) -> float:
+    coef = np.ascontiguousarray(coef, np.float64)
+    return float(lib().iga_l2_error_sine(d, n, p, nq or p + 3, _p(coef)))
+
+
+def csr_apply(rowptr, col, val, x) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.empty(len(rowptr) - 1)
+    lib().iga_csr_apply(len(rowptr) - 1, _p(rowptr), _p(col), _p(val), _p(x), _p(y))
+    return y
+
+
+def kappa_points(M, ell, sigma, seed, pts: np.ndarray) -> np.ndarray:
+    pts = np.ascontiguousarray(pts, np.float64).reshape(-1, 3)
+    out = np.empty(len(pts))
+    lib().iga_kappa_points(M, ell, sigma, seed, len(pts), _p(pts), _p(out))
+    return out
+
+
+def geom_points(geom: int, d: int, xi: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    xi = np.ascontiguousarray(xi, np.float64).reshape(-1, d)
+    x = np.empty_like(xi)
+    det = np.empty(len(xi))
+    lib().iga_geom_points(geom, d, len(xi), _p(xi), _p(x), _p(det))
+    return x, det
+
+
+def poisson_box(d: int, n: int, p: int) -> Problem:
+    """-Laplace u = d pi^2 prod sin(pi x_k) on the unit box, Dirichlet u = 0."""
+    rowptr, col, val = assemble_kron(d, n, p)
+    F = load_sine(d, n, p)
+    return Problem(len(rowptr) - 1, rowptr, col, val, F,
+                   {"kind": "poisson_box", "d": d, "n": n, "p": p, "rhs": "sine"})
+
+
+def poisson_box_random_rhs(d: int, n: int, p: int, seed: int, nrhs: int = 1) -> Problem:
+    """Same matrix with F = K u_true, u_true ~ N(0,1) (column-major N x nrhs)."""
+    rowptr, col, val = assemble_kron(d, n, p)
+    N = len(rowptr) - 1
+    U = rng_normal(seed, N * nrhs).reshape(nrhs, N)
+    F = np.stack([csr_apply(rowptr, col, val, U[k]) for k in range(nrhs)])
+    prob = Problem(N, rowptr, col, val, F[0] if nrhs == 1 else F,
+                   {"kind": "poisson_box", "d": d, "n": n, "p": p, "rhs": "random", "seed": seed, "nrhs": nrhs})
+    prob.u_true = U[0] if nrhs == 1 else U
+    return prob
+
+
+def batch_params(seed: int, count: int, degrees=(2, 3, 4), n_lo: int = 32, n_hi: int = 256) -> list[tuple[int, int]]:
+    """(p, n) for each batch instance: p = degrees[z_{2k} mod 3],
+    n = n_lo + z_{2k+1} mod (n_hi - n_lo + 1), z the SplitMix64(seed) stream."""
+    z = splitmix64(seed, 2 * count)
+    return [(degrees[z[2 * k] % len(degrees)], n_lo + z[2 * k + 1] % (n_hi - n_lo + 1)) for k in range(count)]
+
+
+def batch_instances(seed: int = 20251126, count: int = 48, d: int = 2) -> list[Problem]:
+    out = []
+    for k, (p, n) in enumerate(batch_params(seed, count)):
+        out.append(poisson_box_random_rhs(d, n, p, seed=seed + 1 + k))
+        out[-1].meta["instance"] = k
+    return out
+
+
+ANNULUS_KAPPA = dict(M=256, ell=0.2, sigma=1.0)
+
+
+def annulus_kappa(n: int, p: int, kappa_seed: int = 7, nq: int | None = None) -> Problem:
+    """-div(kappa grad u) = 1 on the quarter annulus (radii 1, 2) x [0,1],
+    homogeneous Dirichlet, kappa = exp(g) with g of correlation length 0.2,
+    sigma = 1 (random Fourier features, M = 256)."""
+    k = ANNULUS_KAPPA
+    rowptr, col, val, F = assemble_elem(3, n, p, nq, geom=1, kappa=(k["M"], k["ell"], k["sigma"], kappa_seed), fkind=0)
+    return Problem(len(rowptr) - 1, rowptr, col, val, F,
+                   {"kind": "annulus_kappa", "d": 3, "n": n, "p": p, "kappa_seed": kappa_seed})
+
+
+def annulus_volume() -> float:
+    return 0.75 * math.pi

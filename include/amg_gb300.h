@@ -1,0 +1,173 @@
+/*
+ * amg_gb300.h -- C ABI of the GB300 (sm_103a) matching-based aggregation
+ * AMG preconditioned conjugate gradient solver for symmetric positive
+ * definite systems K u = F, such as the stiffness systems of isogeometric
+ * (B-spline / NURBS) discretisations of the Poisson problem.
+ *
+ * Method: arXiv 2511.21268 ("Parallel matching-based AMG preconditioners for
+ * elliptic equations discretized by IgA").
+ *   - Sec. 3: Galerkin hierarchy K^(l+1) = P^T K^(l) P (Eq. galerkin_matrix_
+ *     projection), two-level correction applied recursively as a V-cycle,
+ *     used as the preconditioner of CG.
+ *   - Sec. 3.1: aggregation by compatible weighted matching -- test vector w
+ *     from relaxation on K w = 0, edge weights c_ij (Eq. cij), maximum
+ *     product matching (Eq. maxprod) approximated greedily, pair/singleton
+ *     prolongator (Eq. prolongation), m-step aggregation P = P_1 ... P_m,
+ *     operator complexity (Eq. OPC).
+ *   - Sec. 3.2: l1-Jacobi smoother, d_i = k_ii + sum_{j!=i} |k_ij|.
+ *   - Sec. 4 ("Solver invocation"): u is the initial guess on input and the
+ *     solution on output; iteration count and final residual are returned.
+ *
+ * Conventions for every entry point:
+ *   - Return value 0 (AMG_OK) on success, a negative AMG_ERR_* code
+ *     otherwise; amg_strerror() names it.  No C++ exception crosses the ABI.
+ *   - Pointers are plain host or device addresses as stated per argument;
+ *     the caller keeps ownership of everything it passes in and the library
+ *     copies what it keeps.  The opaque amg_hierarchy is owned by the
+ *     library (device memory) until amg_free().
+ *   - All GPU work is enqueued on the CUDA stream given to amg_setup (NULL =
+ *     the legacy default stream); calls return after that work finished.
+ *   - Arithmetic: setup in FP64 with explicitly rounded operations in a
+ *     fixed order (results reproducible bit for bit); the solve in FP64
+ *     (AMG_FP64) or with an FP32/BF16 V-cycle (see amg_opts.precision).
+ */
+#ifndef AMG_GB300_H
+#define AMG_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define AMG_OK 0
+#define AMG_ERR_ARG (-1)            /* invalid argument or malformed CSR */
+#define AMG_ERR_NOT_SPD (-2)        /* nonpositive diagonal or failed coarse Cholesky */
+#define AMG_ERR_BREAKDOWN (-3)      /* p^T K p <= 0 in CG */
+#define AMG_ERR_NOT_CONVERGED (-4)  /* itmax reached before rtol */
+#define AMG_ERR_TIMEOUT (-5)        /* matching did not finish within max_match_rounds */
+#define AMG_ERR_CUDA (-6)           /* CUDA runtime error (see amg_last_cuda_error) */
+#define AMG_ERR_NAN (-7)            /* NaN/Inf met in the data or the iteration */
+#define AMG_ERR_COARSE_TOO_LARGE (-8) /* coarsest level above dense_max rows */
+#define AMG_ERR_NOMEM (-9)          /* device allocation failed */
+#define AMG_ERR_ROW_TOO_LONG (-10)  /* a Galerkin row exceeds the kernel's capacity */
+
+/* ---- precision of the V-cycle (amg_opts.precision) ---- */
+#define AMG_FP64 0          /* everything FP64 */
+#define AMG_FP32 1          /* FP32 level matrices and V-cycle vectors, FP64 outer CG */
+#define AMG_FP32_BF16FINE 2 /* as AMG_FP32 with BF16 values of the finest matrix in the V-cycle */
+
+/* ---- where a pointer lives ---- */
+#define AMG_MEM_HOST 0
+#define AMG_MEM_DEVICE 1
+
+/* Square sparse matrix in CSR: rowptr[n+1] (int64, rowptr[0] = 0,
+ * nondecreasing), col[nnz] (int32, strictly increasing within each row,
+ * diagonal stored), val[nnz] (FP64).  `mem` says whether the three arrays
+ * are host or device pointers.  Read only; the library copies it. */
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    const int64_t* rowptr;
+    const int32_t* col;
+    const double* val;
+    int32_t mem;
+} amg_csr;
+
+/* Options; fill with amg_opts_default() and override fields. */
+typedef struct {
+    int32_t nu_pre;              /* l1-Jacobi pre-smoothing sweeps (1) */
+    int32_t nu_post;             /* l1-Jacobi post-smoothing sweeps (1) */
+    int32_t match_passes;        /* m: matching passes per level, aggregates <= 2^m (2) */
+    int32_t coarse_max;          /* stop coarsening at <= this many rows (200) */
+    int32_t max_levels;          /* hierarchy depth limit (30) */
+    int32_t dense_max;           /* largest coarsest level solved densely (4096) */
+    int32_t testvec_sweeps;      /* relaxation sweeps for the test vector (4) */
+    int32_t testvec_kind;        /* 0 = SplitMix64 random start, 1 = all ones (0) */
+    uint64_t seed;               /* SplitMix64 seed of the random start (20251126) */
+    double stag;                 /* discard a level keeping > stag * rows (0.9) */
+    int32_t max_match_rounds;    /* bound on matching rounds per pass (1000) */
+    int32_t precision;           /* AMG_FP64 / AMG_FP32 / AMG_FP32_BF16FINE (AMG_FP64) */
+    int32_t flexible;            /* 0 = PCG, 1 = flexible CG with one direction (0) */
+    int32_t resid_replace_every; /* FP64 true-residual replacement period, 0 = off (0) */
+} amg_opts;
+
+#define AMG_MAX_LEVELS 32
+
+typedef struct {
+    int32_t levels;
+    int64_t n[AMG_MAX_LEVELS];
+    int64_t nnz[AMG_MAX_LEVELS];
+    double opc;          /* sum_l nnz_l / nnz_0, Eq. (OPC) */
+    double setup_ms;     /* device time of the last amg_setup */
+    double solve_ms;     /* device time of the last solve */
+    int32_t iters;       /* iterations of the last solve */
+    int32_t status;      /* status of the last solve */
+    double final_relres; /* ||F - K u|| / ||F|| of the last solve, recomputed in FP64 */
+    double vcycle_bytes; /* algorithmic bytes of one V-cycle */
+    double iter_bytes;   /* algorithmic bytes of one CG iteration (incl. V-cycle) */
+    int32_t match_rounds[AMG_MAX_LEVELS]; /* total matching rounds per level */
+} amg_info;
+
+typedef struct amg_hierarchy amg_hierarchy;
+
+/* Fill *o with the defaults listed above.  Returns AMG_OK or AMG_ERR_ARG (o NULL). */
+int amg_opts_default(amg_opts* o);
+
+/* Build the AMG hierarchy of K on the GPU (Sec. 3, 3.1, 3.2):
+ * l1 diagonal, test vector, edge weights, greedy-equivalent matching,
+ * aggregation, Galerkin products, coarsest dense factorisation.
+ * K: CSR as described at amg_csr (host or device).  opts: NULL = defaults.
+ * cuda_stream: a cudaStream_t (NULL = default stream) used for all later
+ * work on this hierarchy.  *out receives the library-owned hierarchy.
+ * Errors: AMG_ERR_ARG (malformed CSR/options), AMG_ERR_NOT_SPD,
+ * AMG_ERR_TIMEOUT, AMG_ERR_COARSE_TOO_LARGE, AMG_ERR_ROW_TOO_LONG,
+ * AMG_ERR_NOMEM, AMG_ERR_CUDA; *out is NULL on error. */
+int amg_setup(const amg_csr* K, const amg_opts* opts, void* cuda_stream, amg_hierarchy** out);
+
+/* Solve K u = F by preconditioned CG (flexible CG if opts.flexible) with one
+ * V-cycle as preconditioner, stopping when ||F - K u_k||_2 <= rtol ||F||_2
+ * on the recursive residual or after itmax iterations.
+ * F[n]: right-hand side; u[n]: initial guess in, solution out; both FP64,
+ * host pointers if mem == AMG_MEM_HOST, device pointers if AMG_MEM_DEVICE.
+ * iters, relres (may be NULL): iterations done, final ||F - K u|| / ||F||.
+ * Errors: AMG_ERR_ARG, AMG_ERR_NOT_CONVERGED (u holds the last iterate),
+ * AMG_ERR_BREAKDOWN, AMG_ERR_NAN, AMG_ERR_CUDA. */
+int amg_pcg_solve(amg_hierarchy* h, const double* F, double* u, int32_t mem, double rtol, int32_t itmax,
+                  int32_t* iters, double* relres);
+
+/* Apply one V-cycle z = B r (device pointers, n = rows of level 0).  Used by
+ * the parity tests and by callers with their own Krylov method. */
+int amg_vcycle_apply(amg_hierarchy* h, const double* r_dev, double* z_dev);
+
+/* y = K_l x on level l (device pointers). */
+int amg_level_spmv(amg_hierarchy* h, int32_t level, const double* x_dev, double* y_dev);
+
+/* Statistics of the hierarchy and of the last solve. */
+int amg_get_info(const amg_hierarchy* h, amg_info* info);
+
+/* Copy level data to host buffers (any pointer may be NULL):
+ * K_l as CSR (rowptr[n+1], col[nnz], val[nnz]); dl1[n], w[n] (test vector);
+ * agg[n], pval[n]: composite map to level l+1 (not for the coarsest). */
+int amg_export_level(const amg_hierarchy* h, int32_t level, int64_t* rowptr, int32_t* col, double* val,
+                     double* dl1, double* w, int32_t* agg, double* pval);
+
+/* Copy matching pass s of level l to host buffers: mate[n_s] (partner or
+ * -1 for a singleton), agg[n_s], pval[n_s]; *n_s = rows the pass matched. */
+int amg_export_pass(const amg_hierarchy* h, int32_t level, int32_t pass, int64_t* n_s, int32_t* mate, int32_t* agg,
+                    double* pval);
+
+/* Release the hierarchy and its device memory. */
+int amg_free(amg_hierarchy* h);
+
+/* Static description of a status code. */
+const char* amg_strerror(int code);
+
+/* Text of the last CUDA runtime error seen by this thread ("" if none). */
+const char* amg_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMG_GB300_H */

@@ -96,7 +96,7 @@ def build_cuda(force: bool = False, extra: list[str] | None = None, jobs: int | 
     with ThreadPoolExecutor(max_workers=jobs or min(8, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = AMG_LIB + ".tmp"
-    _run([NVCC, GENCODE, "-shared", "-o", tmp, *objs, "-lcudart"])
+    _run([NVCC, GENCODE, "-shared", "-cudart", "static", "-o", tmp, *objs])
     os.replace(tmp, AMG_LIB)
     return AMG_LIB
 

@@ -1,0 +1,298 @@
+"""Thin Python binding of the C ABI in ``include/amg_gb300.h``.
+
+Argument marshalling only: every step of setup and solve runs in the CUDA
+library ``libamg_gb300.so``.  PyTorch is used for device buffers and
+streams.  There is no fallback: if the library cannot be built or loaded,
+or no CUDA device is present, the calls raise.
+
+The module-level functions carry the C names (``amg_setup``,
+``amg_pcg_solve``, ...); ``Hierarchy`` wraps them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+AMG_OK = 0
+AMG_ERR_ARG = -1
+AMG_ERR_NOT_SPD = -2
+AMG_ERR_BREAKDOWN = -3
+AMG_ERR_NOT_CONVERGED = -4
+AMG_ERR_TIMEOUT = -5
+AMG_ERR_CUDA = -6
+AMG_ERR_NAN = -7
+AMG_ERR_COARSE_TOO_LARGE = -8
+AMG_ERR_NOMEM = -9
+AMG_ERR_ROW_TOO_LONG = -10
+
+AMG_FP64, AMG_FP32, AMG_FP32_BF16FINE = 0, 1, 2
+AMG_MEM_HOST, AMG_MEM_DEVICE = 0, 1
+AMG_MAX_LEVELS = 32
+
+
+class AmgCsr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p), ("mem", ctypes.c_int32)]
+
+
+class AmgOpts(ctypes.Structure):
+    _fields_ = [("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32), ("match_passes", ctypes.c_int32),
+                ("coarse_max", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("dense_max", ctypes.c_int32),
+                ("testvec_sweeps", ctypes.c_int32), ("testvec_kind", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("stag", ctypes.c_double), ("max_match_rounds", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("flexible", ctypes.c_int32), ("resid_replace_every", ctypes.c_int32)]
+
+
+class AmgInfo(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("n", ctypes.c_int64 * AMG_MAX_LEVELS),
+                ("nnz", ctypes.c_int64 * AMG_MAX_LEVELS), ("opc", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("iters", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("final_relres", ctypes.c_double), ("vcycle_bytes", ctypes.c_double),
+                ("iter_bytes", ctypes.c_double), ("match_rounds", ctypes.c_int32 * AMG_MAX_LEVELS)]
+
+
+class AmgError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = amg_strerror(code)
+        if code == AMG_ERR_CUDA:
+            msg += ": " + lib().amg_last_cuda_error().decode()
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+
+
+_lib = None
+
+# exported entry points and their signatures
+_SIGS = {
+    "amg_opts_default": (ctypes.c_int, [ctypes.c_void_p]),
+    "amg_setup": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_pcg_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                     ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_vcycle_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_level_spmv": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_export_level": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 7),
+    "amg_export_pass": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 4),
+    "amg_free": (ctypes.c_int, [ctypes.c_void_p]),
+    "amg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "amg_last_cuda_error": (ctypes.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _build.AMG_LIB
+
+
+def lib(build: bool = True):
+    """Load (building first if needed) the CUDA library."""
+    global _lib
+    if _lib is None:
+        path = _build.build_cuda() if build else _build.AMG_LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library missing: {path}")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != AMG_OK:
+        raise AmgError(rc, what)
+
+
+def amg_strerror(code: int) -> str:
+    return lib().amg_strerror(code).decode()
+
+
+def amg_last_cuda_error() -> str:
+    return lib().amg_last_cuda_error().decode()
+
+
+def amg_opts_default(**overrides) -> AmgOpts:
+    o = AmgOpts()
+    _check(lib().amg_opts_default(ctypes.byref(o)), "amg_opts_default")
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the AMG library runs on the GPU only")
+    return torch
+
+
+def _ptr(a):
+    """(pointer, mem kind, keepalive) of a numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a)
+        return a.ctypes.data, AMG_MEM_HOST, a
+    if a.is_cuda:
+        a = a.contiguous()
+        return a.data_ptr(), AMG_MEM_DEVICE, a
+    a = a.contiguous()
+    return a.data_ptr(), AMG_MEM_HOST, a
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def amg_setup(rowptr, col, val, opts: AmgOpts | None = None, stream=None):
+    """Build a hierarchy; arrays may be numpy (host) or torch (host/cuda)."""
+    _torch()
+    if isinstance(rowptr, np.ndarray):
+        rowptr = np.ascontiguousarray(rowptr, np.int64)
+        col = np.ascontiguousarray(col, np.int32)
+        val = np.ascontiguousarray(val, np.float64)
+    prp, m1, k1 = _ptr(rowptr)
+    pci, m2, k2 = _ptr(col)
+    pv, m3, k3 = _ptr(val)
+    if not (m1 == m2 == m3):
+        raise ValueError("rowptr, col and val must live in the same memory space")
+    csr = AmgCsr(len(rowptr) - 1, len(val), prp, pci, pv, m1)
+    h = ctypes.c_void_p()
+    rc = lib().amg_setup(ctypes.byref(csr), ctypes.byref(opts) if opts is not None else None,
+                         _stream_handle(stream), ctypes.byref(h))
+    _check(rc, "amg_setup")
+    del k1, k2, k3
+    return h
+
+
+def amg_pcg_solve(h, F, u, rtol: float, itmax: int):
+    """Solve in place: u (numpy or torch, FP64) holds x0 and receives the
+    solution.  Returns (status, iters, relres); status is AMG_OK or a
+    convergence status (errors other than those raise)."""
+    pF, mF, kF = _ptr(F)
+    pu, mu, ku = _ptr(u)
+    if mF != mu:
+        raise ValueError("F and u must live in the same memory space")
+    if ku is not u:
+        raise ValueError("u must be contiguous (it is written in place)")
+    it = ctypes.c_int32()
+    rr = ctypes.c_double()
+    rc = lib().amg_pcg_solve(h, pF, pu, mF, float(rtol), int(itmax), ctypes.byref(it), ctypes.byref(rr))
+    if rc not in (AMG_OK, AMG_ERR_NOT_CONVERGED, AMG_ERR_BREAKDOWN, AMG_ERR_NAN):
+        _check(rc, "amg_pcg_solve")
+    return rc, it.value, rr.value
+
+
+def amg_vcycle_apply(h, r, z):
+    _check(lib().amg_vcycle_apply(h, r.data_ptr(), z.data_ptr()), "amg_vcycle_apply")
+
+
+def amg_level_spmv(h, level: int, x, y):
+    _check(lib().amg_level_spmv(h, level, x.data_ptr(), y.data_ptr()), "amg_level_spmv")
+
+
+def amg_get_info(h) -> AmgInfo:
+    info = AmgInfo()
+    _check(lib().amg_get_info(h, ctypes.byref(info)), "amg_get_info")
+    return info
+
+
+def amg_export_level(h, level: int, n: int, nnz: int, with_map: bool, with_w: bool):
+    rp = np.empty(n + 1, np.int64)
+    ci = np.empty(nnz, np.int32)
+    v = np.empty(nnz)
+    d = np.empty(n)
+    w = np.empty(n) if with_w else None
+    agg = np.empty(n, np.int32) if with_map else None
+    pv = np.empty(n) if with_map else None
+    P = lambda a: a.ctypes.data if a is not None else None  # noqa: E731
+    _check(lib().amg_export_level(h, level, P(rp), P(ci), P(v), P(d), P(w), P(agg), P(pv)), "amg_export_level")
+    return dict(rowptr=rp, col=ci, val=v, dl1=d, w=w, agg=agg, pval=pv)
+
+
+def amg_export_pass(h, level: int, pass_: int):
+    ns = ctypes.c_int64()
+    _check(lib().amg_export_pass(h, level, pass_, ctypes.byref(ns), None, None, None), "amg_export_pass")
+    n = ns.value
+    mate = np.empty(n, np.int32)
+    agg = np.empty(n, np.int32)
+    pv = np.empty(n)
+    _check(lib().amg_export_pass(h, level, pass_, None, mate.ctypes.data, agg.ctypes.data, pv.ctypes.data),
+           "amg_export_pass")
+    return mate, agg, pv
+
+
+def amg_free(h):
+    _check(lib().amg_free(h), "amg_free")
+
+
+class Hierarchy:
+    """Owning wrapper of an ``amg_hierarchy*``."""
+
+    def __init__(self, rowptr, col, val, stream=None, **opts):
+        self.opts = amg_opts_default(**opts)
+        self._h = amg_setup(rowptr, col, val, self.opts, stream)
+        self.info = amg_get_info(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            amg_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def num_levels(self) -> int:
+        return self.info.levels
+
+    def level_n(self, l: int) -> int:
+        return int(self.info.n[l])
+
+    def level_nnz(self, l: int) -> int:
+        return int(self.info.nnz[l])
+
+    def solve(self, F, u=None, rtol: float = 1e-8, itmax: int = 10000):
+        """u is created as zeros (same memory space as F) when not given."""
+        if u is None:
+            if isinstance(F, np.ndarray):
+                u = np.zeros_like(F, dtype=np.float64)
+            else:
+                u = F.new_zeros(F.shape)
+        status, iters, relres = amg_pcg_solve(self._h, F, u, rtol, itmax)
+        self.info = amg_get_info(self._h)
+        return dict(u=u, iters=iters, relres=relres, status=status)
+
+    def vcycle(self, r):
+        z = r.new_empty(r.shape)
+        amg_vcycle_apply(self._h, r, z)
+        return z
+
+    def spmv(self, level: int, x):
+        y = x.new_empty((self.level_n(level),))
+        amg_level_spmv(self._h, level, x, y)
+        return y
+
+    def export_level(self, l: int):
+        last = l == self.num_levels - 1
+        return amg_export_level(self._h, l, self.level_n(l), self.level_nnz(l), not last, l == 0 and not last or l > 0)
+
+    def export_pass(self, l: int, s: int):
+        return amg_export_pass(self._h, l, s)

@@ -1,0 +1,636 @@
+// C ABI of the AMG-PCG library: hierarchy construction (setup driver),
+// solve loop and data export.  See include/amg_gb300.h for the contract.
+//
+// Setup (arXiv 2511.21268 Sec. 3.1, 3.2), per level l:
+//   l1 diagonal -> (level 0) test vector -> m matching passes, each:
+//   edge keys -> locally dominant matching rounds -> aggregates and
+//   prolongator values -> Galerkin product of the pass -> restricted test
+//   vector; then the composite map P = P_1 ... P_m and its member lists.
+// Coarsening stops at coarse_max rows, on stagnation or at max_levels; the
+// coarsest matrix is inverted densely.
+//
+// Solve: the CG start phase is launched directly, the iterations run as a
+// captured CUDA graph of kGraphIters iterations whose kernels turn into
+// no-ops once the device-side state says "done"; the host reads the state
+// once per graph launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "amg_internal.cuh"
+
+using namespace amg;
+
+namespace {
+
+constexpr int kGraphIters = 8;
+constexpr int kMaxGalerkinCap = 16384;  // candidate entries per Galerkin row (shared memory)
+constexpr int kHistCap = 1 << 16;
+
+thread_local char g_cuda_err[512] = "";
+
+int cuda_fail(cudaError_t e, const char* what) {
+    snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? AMG_ERR_NOMEM : AMG_ERR_CUDA;
+}
+
+#define CK(expr)                                          \
+    do {                                                  \
+        cudaError_t e__ = (expr);                         \
+        if (e__ != cudaSuccess) return cuda_fail(e__, #expr); \
+    } while (0)
+
+#define RC(expr)                     \
+    do {                             \
+        int r__ = (expr);            \
+        if (r__ != AMG_OK) return r__; \
+    } while (0)
+
+template <typename T>
+int dalloc(amg_hierarchy* h, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, sizeof(T) * count, h->s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    h->allocs.push_back(q);
+    *p = (T*)q;
+    return AMG_OK;
+}
+
+// temporary device buffer freed at scope exit (stream ordered)
+struct Tmp {
+    cudaStream_t s;
+    void* p = nullptr;
+    explicit Tmp(cudaStream_t st) : s(st) {}
+    ~Tmp() {
+        if (p) cudaFreeAsync(p, s);
+    }
+    template <typename T>
+    int get(T** out, size_t count) {
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMallocAsync(&p, sizeof(T) * count, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+        *out = (T*)p;
+        return AMG_OK;
+    }
+};
+
+void forget(amg_hierarchy* h, void* p) {
+    auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+    if (it != h->allocs.end()) {
+        cudaFreeAsync(p, h->s);
+        h->allocs.erase(it);
+    }
+}
+
+int read_flag(amg_hierarchy* h, int* value) {
+    CK(cudaMemcpyAsync(h->flag_host, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    *value = *h->flag_host;
+    return AMG_OK;
+}
+
+template <typename T>
+int read_scalar(amg_hierarchy* h, const T* dptr, T* value) {
+    CK(cudaMemcpyAsync(h->flag_host, dptr, sizeof(T), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    memcpy(value, h->flag_host, sizeof(T));
+    return AMG_OK;
+}
+
+int pow2ceil(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// One matching pass on A with test vector w: fills P and the coarse matrix C
+// (allocated in the hierarchy) and the coarse test vector *wc.
+int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevCSR& C, double** wc) {
+    const int n = A.n;
+    cudaStream_t s = h->s;
+    double* kii = nullptr;
+    Tmp tk(s), tkey(s), tstate(s), tcand(s), tlead(s), tcidx(s), tscan(s);
+    RC(tk.get(&kii, n));
+    CK(launch_diag(A, kii, s));
+    uint64_t* key;
+    int32_t *state, *cand, *leader, *cidx, *scr;
+    RC(tkey.get(&key, A.nnz));
+    RC(tstate.get(&state, n));
+    RC(tcand.get(&cand, n));
+    RC(tlead.get(&leader, n));
+    RC(tcidx.get(&cidx, n));
+    RC(tscan.get(&scr, scan_scratch_ints(n) + 1));
+    CK(launch_edge_keys(A, kii, w, key, s));
+    CK(launch_match_init(n, state, s));
+    int rounds = 0, active = n;
+    while (active > 0) {
+        if (rounds >= h->o.max_match_rounds) return AMG_ERR_TIMEOUT;
+        CK(launch_match_propose(A, key, state, cand, s));
+        CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+        CK(launch_match_commit(n, cand, state, h->flag, s));
+        rounds++;
+        RC(read_flag(h, &active));
+    }
+    P.rounds = rounds;
+    P.n = n;
+    RC(dalloc(h, &P.mate, n));
+    CK(launch_match_finish(n, state, P.mate, leader, s));
+    int32_t* total = scr + scan_scratch_ints(n);
+    CK(launch_exclusive_scan(leader, cidx, n, total, scr, s));
+    int nc = 0;
+    RC(read_scalar(h, total, &nc));
+    P.nc = nc;
+    RC(dalloc(h, &P.agg, n));
+    RC(dalloc(h, &P.pval, n));
+    int32_t *mem0, *mem1;
+    Tmp tm0(s), tm1(s);
+    RC(tm0.get(&mem0, nc));
+    RC(tm1.get(&mem1, nc));
+    RC(dalloc(h, wc, nc));
+    CK(launch_aggregate(n, P.mate, cidx, w, P.agg, P.pval, mem0, mem1, *wc, s));
+    // Galerkin product of this pass
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    CK(launch_row_stats(A, mem0, mem1, nc, h->flag, s));
+    int maxcand = 0;
+    RC(read_flag(h, &maxcand));
+    const int cap = pow2ceil(std::max(maxcand, 1));
+    if (cap > kMaxGalerkinCap) return AMG_ERR_ROW_TOO_LONG;
+    C.n = nc;
+    RC(dalloc(h, &C.rowptr, (size_t)nc + 1));
+    int64_t *rowcnt, *scr64;
+    Tmp trc(s), ts64(s);
+    RC(trc.get(&rowcnt, nc));
+    RC(ts64.get(&scr64, scan64_scratch(nc) + 1));
+    CK(launch_galerkin_count(A, P.agg, mem0, mem1, nc, cap, rowcnt, s));
+    CK(launch_scan64(rowcnt, C.rowptr, nc, scr64, s));
+    int64_t nnzc = 0;
+    RC(read_scalar(h, C.rowptr + nc, &nnzc));
+    C.nnz = nnzc;
+    RC(dalloc(h, &C.col, (size_t)nnzc));
+    RC(dalloc(h, &C.val, (size_t)nnzc));
+    CK(launch_galerkin_fill(A, P.agg, P.pval, mem0, mem1, cap, C, s));
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    CK(launch_galerkin_mirror(C, h->flag, s));
+    int bad = 0;
+    RC(read_flag(h, &bad));
+    if (bad) return AMG_ERR_ARG;  // structurally unsymmetric input
+    return AMG_OK;
+}
+
+void free_level_matrix(amg_hierarchy* h, DevCSR& A) {
+    forget(h, A.rowptr);
+    forget(h, A.col);
+    forget(h, A.val);
+    A = DevCSR{};
+}
+
+int build(amg_hierarchy* h, const amg_csr* K) {
+    cudaStream_t s = h->s;
+    const int n0 = K->n;
+    Level& L0 = h->lev[0];
+    L0.A.n = n0;
+    L0.A.nnz = K->nnz;
+    RC(dalloc(h, &L0.A.rowptr, (size_t)n0 + 1));
+    RC(dalloc(h, &L0.A.col, (size_t)K->nnz));
+    RC(dalloc(h, &L0.A.val, (size_t)K->nnz));
+    const cudaMemcpyKind kind = K->mem == AMG_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(L0.A.rowptr, K->rowptr, sizeof(int64_t) * (n0 + 1), kind, s));
+    CK(cudaMemcpyAsync(L0.A.col, K->col, sizeof(int32_t) * K->nnz, kind, s));
+    CK(cudaMemcpyAsync(L0.A.val, K->val, sizeof(double) * K->nnz, kind, s));
+    // structural checks
+    int64_t ends[2];
+    CK(cudaMemcpyAsync(h->flag_host, L0.A.rowptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ends[0] = *(int64_t*)h->flag_host;
+    CK(cudaMemcpyAsync(h->flag_host, L0.A.rowptr + n0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ends[1] = *(int64_t*)h->flag_host;
+    if (ends[0] != 0 || ends[1] != K->nnz) return AMG_ERR_ARG;
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    CK(launch_validate_csr(L0.A, h->flag, s));
+    int bad = 0;
+    RC(read_flag(h, &bad));
+    if (bad & 1) return AMG_ERR_ARG;
+    if (bad & 2) return AMG_ERR_NAN;
+    if (bad & 4) return AMG_ERR_NOT_SPD;
+
+    for (int l = 0;; l++) {
+        Level& F = h->lev[l];
+        const int n = F.A.n;
+        RC(dalloc(h, &F.kii, n));
+        RC(dalloc(h, &F.dl1, n));
+        RC(dalloc(h, &F.invd, n));
+        CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+        CK(launch_l1diag(F.A, F.kii, F.dl1, F.invd, h->flag, s));
+        RC(read_flag(h, &bad));
+        if (bad) return AMG_ERR_NOT_SPD;
+        h->nlev = l + 1;
+        if (n <= h->o.coarse_max || l + 1 >= h->o.max_levels) break;
+        if (l == 0) {
+            RC(dalloc(h, &F.w, n));
+            double* wt;
+            Tmp tw(s);
+            RC(tw.get(&wt, n));
+            CK(launch_testvec_init(n, h->o.testvec_kind, h->o.seed, F.w, s));
+            for (int sw = 0; sw < h->o.testvec_sweeps; sw++) {
+                CK(launch_testvec_sweep(F.A, F.dl1, F.w, wt, s));
+                CK(cudaMemcpyAsync(F.w, wt, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            }
+        }
+        // m matching passes
+        DevCSR cur = F.A;
+        double* cw = F.w;
+        DevCSR next;
+        double* nw = nullptr;
+        F.npass = h->o.match_passes;
+        for (int q = 0; q < F.npass; q++) {
+            next = DevCSR{};
+            RC(match_pass(h, cur, cw, F.pass[q], next, &nw));
+            if (q > 0) {  // intermediate pass matrix no longer needed
+                free_level_matrix(h, cur);
+                forget(h, cw);
+            }
+            cur = next;
+            cw = nw;
+        }
+        const int nc = cur.n;
+        if ((double)nc > h->o.stag * (double)n) {  // stagnation: discard and stop
+            free_level_matrix(h, cur);
+            forget(h, cw);
+            for (int q = 0; q < F.npass; q++) {
+                forget(h, F.pass[q].mate);
+                forget(h, F.pass[q].agg);
+                forget(h, F.pass[q].pval);
+                F.pass[q] = Pass{};
+            }
+            F.npass = 0;
+            break;
+        }
+        if (l + 1 >= AMG_MAX_LEVELS) return AMG_ERR_ARG;
+        // composite map and member lists
+        F.nc = nc;
+        RC(dalloc(h, &F.agg, n));
+        RC(dalloc(h, &F.pval, n));
+        CK(launch_compose(n, F.npass, F.pass, F.agg, F.pval, s));
+        int32_t* cnt;
+        Tmp tc(s), tsc(s), tcur(s);
+        RC(tc.get(&cnt, (size_t)nc + 1));
+        RC(dalloc(h, &F.mem_ptr, (size_t)nc + 1));
+        RC(dalloc(h, &F.mem_idx, n));
+        CK(launch_member_count(n, F.agg, nc, cnt, s));
+        int32_t* scr;
+        RC(tsc.get(&scr, scan_scratch_ints(nc + 1)));
+        CK(launch_exclusive_scan(cnt, F.mem_ptr, nc + 1, nullptr, scr, s));
+        int* cursor;
+        RC(tcur.get(&cursor, nc));
+        CK(launch_member_fill(n, F.agg, F.mem_ptr, nc, F.mem_idx, cursor, s));
+        Level& C = h->lev[l + 1];
+        C.A = cur;
+        C.w = cw;
+    }
+    // coarsest level: dense inverse
+    Level& Lc = h->lev[h->nlev - 1];
+    const int nd = Lc.A.n;
+    if (nd > h->o.dense_max) return AMG_ERR_COARSE_TOO_LARGE;
+    h->ndense = nd;
+    double* D;
+    Tmp td(s);
+    RC(td.get(&D, (size_t)nd * nd));
+    RC(dalloc(h, &h->Ainv, (size_t)2 * nd * nd));
+    CK(launch_dense_from_csr(Lc.A, D, s));
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    CK(launch_dense_spd_inverse(nd, D, h->Ainv, h->flag, s));
+    RC(read_flag(h, &bad));
+    if (bad) return AMG_ERR_NOT_SPD;
+    // solve workspace
+    for (int l = 0; l < h->nlev; l++) {
+        Level& F = h->lev[l];
+        const int n = F.A.n;
+        if (l > 0) RC(dalloc(h, &F.f, n));
+        RC(dalloc(h, &F.x, n));
+        RC(dalloc(h, &F.t, n));
+    }
+    RC(dalloc(h, &h->x, n0));
+    RC(dalloc(h, &h->r, n0));
+    RC(dalloc(h, &h->p, n0));
+    RC(dalloc(h, &h->q, n0));
+    RC(dalloc(h, &h->z, n0));
+    RC(dalloc(h, &h->F, n0));
+    h->npart = (int)partial_slot_size(n0, h->num_sms);
+    RC(dalloc(h, &h->partials, (size_t)7 * h->npart));
+    RC(dalloc(h, &h->st, 1));
+    h->hist_cap = kHistCap;
+    RC(dalloc(h, &h->hist, kHistCap));
+    CK(cudaMemsetAsync(h->st, 0, sizeof(SolveState), s));
+    return AMG_OK;
+}
+
+void fill_info(amg_hierarchy* h) {
+    amg_info& I = h->info;
+    I.levels = h->nlev;
+    double tot = 0.0, vbytes = 0.0;
+    for (int l = 0; l < h->nlev; l++) {
+        I.n[l] = h->lev[l].A.n;
+        I.nnz[l] = h->lev[l].A.nnz;
+        tot += (double)h->lev[l].A.nnz;
+        int rounds = 0;
+        for (int q = 0; q < h->lev[l].npass; q++) rounds += h->lev[l].pass[q].rounds;
+        I.match_rounds[l] = rounds;
+    }
+    I.opc = tot / (double)h->lev[0].A.nnz;
+    // algorithmic bytes: one matrix pass = nnz (8 + 4) + (n + 1) 8 + x read + y write
+    auto pass_bytes = [](const DevCSR& A) { return (double)A.nnz * 12.0 + (A.n + 1.0) * 8.0 + 2.0 * A.n * 8.0; };
+    if (h->nlev == 1) {
+        vbytes = (double)h->ndense * h->ndense * 8.0 + 2.0 * h->ndense * 8.0;
+    } else {
+        for (int l = 0; l < h->nlev - 1; l++) {
+            const DevCSR& A = h->lev[l].A;
+            vbytes += 2.0 * pass_bytes(A) + 6.0 * A.n * 8.0;
+        }
+        vbytes += (double)h->ndense * h->ndense * 8.0 + 2.0 * h->ndense * 8.0;
+    }
+    I.vcycle_bytes = vbytes;
+    I.iter_bytes = vbytes + pass_bytes(h->lev[0].A) + 10.0 * h->lev[0].A.n * 8.0;
+}
+
+void destroy(amg_hierarchy* h) {
+    if (!h) return;
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (void* p : h->allocs) cudaFreeAsync(p, h->s);
+    h->allocs.clear();
+    if (h->s) cudaStreamSynchronize(h->s);
+    if (h->flag_host) cudaFreeHost(h->flag_host);
+    if (h->st_host) cudaFreeHost(h->st_host);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->evs) cudaEventDestroy(h->evs);
+    if (h->s) cudaStreamDestroy(h->s);
+    delete h;
+}
+
+// order the internal stream after the caller's stream
+int join_caller(amg_hierarchy* h) {
+    CK(cudaEventRecord(h->evs, h->us));
+    CK(cudaStreamWaitEvent(h->s, h->evs, 0));
+    return AMG_OK;
+}
+
+int check_opts(const amg_opts& o) {
+    if (o.nu_pre < 1 || o.nu_post < 1 || o.nu_pre > 64 || o.nu_post > 64) return AMG_ERR_ARG;
+    if (o.match_passes < 1 || o.match_passes > kMaxPasses) return AMG_ERR_ARG;
+    if (o.coarse_max < 1 || o.max_levels < 1 || o.max_levels > AMG_MAX_LEVELS) return AMG_ERR_ARG;
+    if (o.dense_max < 1 || o.dense_max > 8192) return AMG_ERR_ARG;
+    if (o.testvec_sweeps < 0 || o.testvec_kind < 0 || o.testvec_kind > 1) return AMG_ERR_ARG;
+    if (!(o.stag > 0.0) || o.max_match_rounds < 1) return AMG_ERR_ARG;
+    if (o.precision != AMG_FP64) return AMG_ERR_ARG;  // mixed precision: see amg_opts.precision
+    if (o.flexible < 0 || o.flexible > 1) return AMG_ERR_ARG;
+    return AMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int amg_opts_default(amg_opts* o) {
+    if (!o) return AMG_ERR_ARG;
+    memset(o, 0, sizeof(*o));
+    o->nu_pre = 1;
+    o->nu_post = 1;
+    o->match_passes = 2;
+    o->coarse_max = 200;
+    o->max_levels = 30;
+    o->dense_max = 4096;
+    o->testvec_sweeps = 4;
+    o->testvec_kind = 0;
+    o->seed = 20251126ULL;
+    o->stag = 0.9;
+    o->max_match_rounds = 1000;
+    o->precision = AMG_FP64;
+    o->flexible = 0;
+    o->resid_replace_every = 0;
+    return AMG_OK;
+}
+
+int amg_setup(const amg_csr* K, const amg_opts* opts, void* cuda_stream, amg_hierarchy** out) {
+    if (!out) return AMG_ERR_ARG;
+    *out = nullptr;
+    if (!K || K->n < 1 || K->nnz < K->n || !K->rowptr || !K->col || !K->val) return AMG_ERR_ARG;
+    if (K->mem != AMG_MEM_HOST && K->mem != AMG_MEM_DEVICE) return AMG_ERR_ARG;
+    if (K->nnz > (int64_t)INT32_MAX * 4) return AMG_ERR_ARG;
+    amg_hierarchy* h = new (std::nothrow) amg_hierarchy();
+    if (!h) return AMG_ERR_NOMEM;
+    if (opts) h->o = *opts;
+    else amg_opts_default(&h->o);
+    int rc = check_opts(h->o);
+    if (rc != AMG_OK) {
+        delete h;
+        return rc;
+    }
+    memset(&h->info, 0, sizeof(h->info));
+    h->us = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->evs, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->flag_host, 64);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->st_host, sizeof(SolveState));
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "amg_setup init");
+        destroy(h);
+        return rc;
+    }
+    rc = join_caller(h);
+    if (rc == AMG_OK) rc = dalloc(h, &h->flag, 16);
+    if (rc == AMG_OK) {
+        cudaEventRecord(h->ev0, h->s);
+        rc = build(h, K);
+        cudaEventRecord(h->ev1, h->s);
+    }
+    if (rc == AMG_OK) {
+        e = cudaStreamSynchronize(h->s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "amg_setup");
+    }
+    if (rc != AMG_OK) {
+        cudaStreamSynchronize(h->s);
+        destroy(h);
+        return rc;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    h->info.setup_ms = ms;
+    fill_info(h);
+    *out = h;
+    return AMG_OK;
+}
+
+static int run_solve(amg_hierarchy* h, int32_t* iters) {
+    cudaStream_t s = h->s;
+    CK(cudaEventRecord(h->ev0, s));
+    CK(enqueue_pcg_start(h, s));
+    if (!h->graph) {
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < kGraphIters && e == cudaSuccess; k++) e = enqueue_pcg_iteration(h, s);
+        cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (e != cudaSuccess) return cuda_fail(e, "capture");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&h->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->graph = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        h->graph_iters = kGraphIters;
+    }
+    const int max_launches = h->itmax / kGraphIters + 2;
+    for (int k = 0; k <= max_launches; k++) {
+        CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (h->st_host->done) break;
+        CK(cudaGraphLaunch(h->graph, s));
+    }
+    CK(cudaEventRecord(h->ev1, s));
+    CK(launch_final_residual(h, s));
+    CK(cudaStreamSynchronize(s));
+    *iters = h->st_host->iters;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    h->info.solve_ms = ms;
+    return h->st_host->done ? h->st_host->status : AMG_ERR_NOT_CONVERGED;
+}
+
+int amg_pcg_solve(amg_hierarchy* h, const double* F, double* u, int32_t mem, double rtol, int32_t itmax,
+                  int32_t* iters, double* relres) {
+    if (!h || !F || !u || (mem != AMG_MEM_HOST && mem != AMG_MEM_DEVICE) || !(rtol >= 0.0) || itmax < 0)
+        return AMG_ERR_ARG;
+    const int n = h->lev[0].A.n;
+    cudaStream_t s = h->s;
+    RC(join_caller(h));
+    const cudaMemcpyKind in = mem == AMG_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind outk = mem == AMG_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(h->F, F, sizeof(double) * n, in, s));
+    CK(cudaMemcpyAsync(h->x, u, sizeof(double) * n, in, s));
+    h->rtol = rtol;
+    h->itmax = itmax;
+    int32_t it = 0;
+    int rc = run_solve(h, &it);
+    if (rc == AMG_ERR_CUDA || rc == AMG_ERR_NOMEM) return rc;
+    double res[2] = {0.0, 0.0};
+    CK(cudaMemcpyAsync(h->flag_host, final_residual_slot(h), 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    memcpy(res, h->flag_host, sizeof(res));
+    if (!(h->st_host->nF > 0.0) && rc == AMG_OK) {  // F = 0: u = 0
+        CK(cudaMemsetAsync(h->x, 0, sizeof(double) * n, s));
+        res[0] = 0.0;
+    }
+    const double rel = res[1] > 0.0 ? res[0] / res[1] : 0.0;
+    CK(cudaMemcpyAsync(u, h->x, sizeof(double) * n, outk, s));
+    CK(cudaStreamSynchronize(s));
+    h->info.iters = it;
+    h->info.status = rc;
+    h->info.final_relres = rel;
+    if (iters) *iters = it;
+    if (relres) *relres = rel;
+    return rc;
+}
+
+int amg_vcycle_apply(amg_hierarchy* h, const double* r_dev, double* z_dev) {
+    if (!h || !r_dev || !z_dev) return AMG_ERR_ARG;
+    const int n = h->lev[0].A.n;
+    cudaStream_t s = h->s;
+    RC(join_caller(h));
+    CK(cudaMemsetAsync(h->st, 0, sizeof(SolveState), s));
+    CK(cudaMemcpyAsync(h->r, r_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(enqueue_vcycle_standalone(h, s));
+    CK(cudaMemcpyAsync(z_dev, h->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+int amg_level_spmv(amg_hierarchy* h, int32_t level, const double* x_dev, double* y_dev) {
+    if (!h || level < 0 || level >= h->nlev || !x_dev || !y_dev) return AMG_ERR_ARG;
+    RC(join_caller(h));
+    CK(launch_spmv(h->lev[level].A, x_dev, y_dev, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return AMG_OK;
+}
+
+int amg_get_info(const amg_hierarchy* h, amg_info* info) {
+    if (!h || !info) return AMG_ERR_ARG;
+    *info = h->info;
+    return AMG_OK;
+}
+
+int amg_export_level(const amg_hierarchy* hc, int32_t level, int64_t* rowptr, int32_t* col, double* val, double* dl1,
+                     double* w, int32_t* agg, double* pval) {
+    amg_hierarchy* h = const_cast<amg_hierarchy*>(hc);
+    if (!h || level < 0 || level >= h->nlev) return AMG_ERR_ARG;
+    const Level& L = h->lev[level];
+    cudaStream_t s = h->s;
+    const int n = L.A.n;
+    if (rowptr) CK(cudaMemcpyAsync(rowptr, L.A.rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+    if (col) CK(cudaMemcpyAsync(col, L.A.col, sizeof(int32_t) * L.A.nnz, cudaMemcpyDeviceToHost, s));
+    if (val) CK(cudaMemcpyAsync(val, L.A.val, sizeof(double) * L.A.nnz, cudaMemcpyDeviceToHost, s));
+    if (dl1) CK(cudaMemcpyAsync(dl1, L.dl1, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    if (w) {
+        if (!L.w) return AMG_ERR_ARG;
+        CK(cudaMemcpyAsync(w, L.w, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    }
+    if (agg || pval) {
+        if (level == h->nlev - 1) return AMG_ERR_ARG;
+        if (agg) CK(cudaMemcpyAsync(agg, L.agg, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+        if (pval) CK(cudaMemcpyAsync(pval, L.pval, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+int amg_export_pass(const amg_hierarchy* hc, int32_t level, int32_t pass, int64_t* n_s, int32_t* mate, int32_t* agg,
+                    double* pval) {
+    amg_hierarchy* h = const_cast<amg_hierarchy*>(hc);
+    if (!h || level < 0 || level >= h->nlev || pass < 0 || pass >= h->lev[level].npass) return AMG_ERR_ARG;
+    const Pass& P = h->lev[level].pass[pass];
+    cudaStream_t s = h->s;
+    if (n_s) *n_s = P.n;
+    if (mate) CK(cudaMemcpyAsync(mate, P.mate, sizeof(int32_t) * P.n, cudaMemcpyDeviceToHost, s));
+    if (agg) CK(cudaMemcpyAsync(agg, P.agg, sizeof(int32_t) * P.n, cudaMemcpyDeviceToHost, s));
+    if (pval) CK(cudaMemcpyAsync(pval, P.pval, sizeof(double) * P.n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+int amg_free(amg_hierarchy* h) {
+    if (!h) return AMG_ERR_ARG;
+    destroy(h);
+    return AMG_OK;
+}
+
+const char* amg_strerror(int code) {
+    switch (code) {
+        case AMG_OK: return "ok";
+        case AMG_ERR_ARG: return "invalid argument or malformed matrix";
+        case AMG_ERR_NOT_SPD: return "matrix not symmetric positive definite (diagonal or coarse Cholesky)";
+        case AMG_ERR_BREAKDOWN: return "CG breakdown (p^T K p <= 0)";
+        case AMG_ERR_NOT_CONVERGED: return "not converged within itmax";
+        case AMG_ERR_TIMEOUT: return "matching did not finish within max_match_rounds";
+        case AMG_ERR_CUDA: return "CUDA runtime error";
+        case AMG_ERR_NAN: return "NaN or Inf encountered";
+        case AMG_ERR_COARSE_TOO_LARGE: return "coarsest level larger than dense_max";
+        case AMG_ERR_NOMEM: return "device memory allocation failed";
+        case AMG_ERR_ROW_TOO_LONG: return "Galerkin row exceeds kernel capacity";
+        default: return "unknown status";
+    }
+}
+
+const char* amg_last_cuda_error(void) { return g_cuda_err; }
+
+}  // extern "C"

@@ -1,0 +1,193 @@
+// Internal declarations shared by the CUDA translation units of the AMG
+// library: hierarchy layout, launch wrappers and small device helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "amg_gb300.h"
+
+namespace amg {
+
+constexpr int kWarp = 32;
+constexpr int kBlock = 256;  // threads per block of the row kernels
+constexpr int kWarpsPerBlock = kBlock / kWarp;
+constexpr int kMaxPasses = 4;
+constexpr int kMaxMembers = 1 << kMaxPasses;
+constexpr int kMaxPartials = 2048;  // block partial sums of one reduction
+
+// Device-side state words of a solve.
+struct SolveState {
+    int done;      // 1 once converged / failed / itmax
+    int iters;     // completed CG iterations
+    int status;    // AMG_OK or an error
+    int pad;
+    double nF;     // ||F||
+    double tol;    // rtol * ||F||
+    double rho;    // r^T z (PCG) of the current direction
+    double alpha;
+    double beta;
+    double pq;     // p^T K p
+    double nr;     // ||r|| of the last iteration
+    int itmax;
+    int pad2;
+};
+
+// One matching pass on a matrix with n rows -> nc coarse rows.
+struct Pass {
+    int n = 0, nc = 0;
+    int32_t* mate = nullptr;   // partner, -1 singleton (exported convention)
+    int32_t* agg = nullptr;    // fine -> coarse
+    double* pval = nullptr;    // prolongator value
+    int rounds = 0;
+};
+
+struct DevCSR {
+    int n = 0;
+    int64_t nnz = 0;
+    int64_t* rowptr = nullptr;
+    int32_t* col = nullptr;
+    double* val = nullptr;
+};
+
+struct Level {
+    DevCSR A;
+    double* kii = nullptr;   // diagonal
+    double* dl1 = nullptr;   // l1 diagonal
+    double* invd = nullptr;  // 1 / dl1
+    double* w = nullptr;     // test vector (setup only)
+    // map to the next level (absent on the coarsest)
+    int npass = 0;
+    Pass pass[kMaxPasses];
+    int nc = 0;
+    int32_t* agg = nullptr;      // composite fine -> coarse
+    double* pval = nullptr;      // composite prolongator value
+    int32_t* mem_ptr = nullptr;  // [nc+1] members of each next-level row
+    int32_t* mem_idx = nullptr;  // [n] fine rows, ascending within a row
+    // V-cycle vectors
+    double* f = nullptr;
+    double* x = nullptr;
+    double* t = nullptr;  // ping-pong buffer for extra smoothing sweeps
+    int maxrow = 0;
+};
+
+}  // namespace amg
+
+struct amg_hierarchy {
+    amg_opts o;
+    cudaStream_t s = nullptr;
+    int nlev = 0;
+    amg::Level lev[AMG_MAX_LEVELS];
+    int ndense = 0;
+    double* Ainv = nullptr;  // dense inverse of the coarsest matrix (row-major)
+    // CG workspace (level 0)
+    double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *F = nullptr;
+    double* partials = nullptr;  // 7 slots of npart doubles
+    int npart = 0;
+    double rtol = 0.0;
+    int itmax = 0;
+    cudaStream_t us = nullptr;   // caller's stream
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs = nullptr;
+    std::vector<void*> allocs;   // device allocations owned by the hierarchy
+    amg::SolveState* st = nullptr;
+    amg::SolveState* st_host = nullptr;  // pinned mirror
+    int* flag = nullptr;                 // device scratch flag / counter
+    int* flag_host = nullptr;            // pinned mirror
+    double* hist = nullptr;              // residual history (device)
+    int hist_cap = 0;
+    amg_info info;
+    int num_sms = 0;
+    // captured iteration graph
+    cudaGraphExec_t graph = nullptr;
+    int graph_iters = 0;
+};
+
+namespace amg {
+
+// ----------------------------------------------------------------- launch wrappers
+// setup_kernels.cu
+cudaError_t launch_validate_csr(const DevCSR& A, int* flag, cudaStream_t s);
+cudaError_t launch_l1diag(const DevCSR& A, double* kii, double* dl1, double* invd, int* flag, cudaStream_t s);
+cudaError_t launch_diag(const DevCSR& A, double* kii, cudaStream_t s);
+cudaError_t launch_testvec_init(int n, int kind, uint64_t seed, double* w, cudaStream_t s);
+cudaError_t launch_testvec_sweep(const DevCSR& A, const double* dl1, const double* w, double* wout, cudaStream_t s);
+cudaError_t launch_edge_keys(const DevCSR& A, const double* kii, const double* w, uint64_t* key, cudaStream_t s);
+cudaError_t launch_match_init(int n, int32_t* state, cudaStream_t s);
+cudaError_t launch_match_propose(const DevCSR& A, const uint64_t* key, const int32_t* state, int32_t* cand,
+                                 cudaStream_t s);
+cudaError_t launch_match_commit(int n, const int32_t* cand, int32_t* state, int* active, cudaStream_t s);
+cudaError_t launch_match_finish(int n, const int32_t* state, int32_t* mate, int32_t* leader, cudaStream_t s);
+cudaError_t launch_aggregate(int n, const int32_t* mate, const int32_t* cidx, const double* w, int32_t* agg,
+                             double* pval, int32_t* mem0, int32_t* mem1, double* wc, cudaStream_t s);
+cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int n, int32_t* total, int32_t* scratch,
+                                  cudaStream_t s);
+size_t scan_scratch_ints(int n);
+cudaError_t launch_galerkin_count(const DevCSR& A, const int32_t* agg, const int32_t* mem0, const int32_t* mem1,
+                                  int nc, int cap, int64_t* rowcnt, cudaStream_t s);
+cudaError_t launch_galerkin_fill(const DevCSR& A, const int32_t* agg, const double* pval, const int32_t* mem0,
+                                 const int32_t* mem1, int cap, DevCSR& C, cudaStream_t s);
+cudaError_t launch_galerkin_mirror(DevCSR& C, int* flag, cudaStream_t s);
+cudaError_t launch_scan64(const int64_t* in, int64_t* out, int n, int64_t* scratch, cudaStream_t s);
+size_t scan64_scratch(int n);
+cudaError_t launch_row_stats(const DevCSR& A, const int32_t* mem0, const int32_t* mem1, int nc, int* maxcand,
+                             cudaStream_t s);
+cudaError_t launch_compose(int n, int npass, const Pass* passes, int32_t* agg, double* pval, cudaStream_t s);
+cudaError_t launch_member_count(int n, const int32_t* agg, int nc, int32_t* cnt, cudaStream_t s);
+cudaError_t launch_member_fill(int n, const int32_t* agg, const int32_t* mem_ptr, int nc, int32_t* mem_idx,
+                               int* cursor, cudaStream_t s);
+cudaError_t launch_dense_from_csr(const DevCSR& A, double* D, cudaStream_t s);
+cudaError_t launch_dense_spd_inverse(int n, double* D, double* Ainv, int* flag, cudaStream_t s);
+
+// solve_kernels.cu
+cudaError_t launch_spmv(const DevCSR& A, const double* x, double* y, cudaStream_t s);
+cudaError_t enqueue_vcycle(amg_hierarchy* h, cudaStream_t s);
+cudaError_t enqueue_vcycle_standalone(amg_hierarchy* h, cudaStream_t s);
+cudaError_t enqueue_pcg_start(amg_hierarchy* h, cudaStream_t s);
+cudaError_t enqueue_pcg_iteration(amg_hierarchy* h, cudaStream_t s);
+cudaError_t launch_final_residual(amg_hierarchy* h, cudaStream_t s);
+double* final_residual_slot(amg_hierarchy* h);
+int rows_per_warp(int n, int num_sms);
+int row_blocks(int n, int rpw);
+int vec_blocks(int n, int num_sms);
+size_t partial_slot_size(int n0, int num_sms);
+
+// ----------------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+// Monotone map of a finite double to an unsigned key (larger value ->
+// larger key); -0 is folded onto +0.  Key 0 is reserved for "no edge".
+__device__ __forceinline__ uint64_t order_key(double c) {
+    if (c == 0.0) c = 0.0;
+    uint64_t b = (uint64_t)__double_as_longlong(c);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): draw k of the stream seeded `seed`.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + (k + 1) * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+#endif
+
+}  // namespace amg
+
+#define AMG_TRY(expr)                          \
+    do {                                       \
+        cudaError_t e__ = (expr);              \
+        if (e__ != cudaSuccess) return e__;    \
+    } while (0)

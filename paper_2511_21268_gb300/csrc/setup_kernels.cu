@@ -1,0 +1,844 @@
+// Setup kernels of the matching-based aggregation AMG (arXiv 2511.21268,
+// Sec. 3.1 and 3.2).  Every floating-point result that steers the matching
+// (l1 diagonal, test vector, edge weights, prolongator values, Galerkin
+// values) is computed with explicitly rounded operations (__dadd_rn,
+// __dmul_rn, __ddiv_rn, __dsqrt_rn) in a fixed order:
+//   - row sums run left to right over the row's entries in column order,
+//     starting from +0.0;
+//   - c_ij is evaluated in the canonical (lo = min(i,j), hi = max(i,j))
+//     order: c = 1 - ((2 k) w_lo) w_hi / (k_lolo (w_lo w_lo) + k_hihi (w_hi w_hi));
+//   - K_c(I,J), I <= J, sums (p_a k_ab) p_b over a in I ascending, then b in
+//     J ascending; K_c(J,I) copies K_c(I,J).
+// so the hierarchy is reproducible bit for bit.
+//
+// GB300 issues about two FP64 FMAs per SM per clock, so ordered row sums are
+// never computed redundantly across lanes: a warp folds 32 rows at once, each
+// lane owning one row, after staging 32x32 tiles through shared memory with
+// coalesced loads.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "amg_internal.cuh"
+
+namespace amg {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+int blocks_for(int64_t units, int per_block, int cap = 1 << 20) {
+    int64_t b = (units + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+// ------------------------------------------------------------------ CSR check
+// flag bits: 1 malformed (rowptr order, column range or order), 2 non-finite
+// value, 4 missing diagonal.
+__global__ void k_validate(int n, int64_t nnz, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const double* __restrict__ v, int* flag) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < n; i += nw) {
+        int64_t b = rp[i], e = rp[i + 1];
+        int bad = 0;
+        if (b > e || b < 0 || e > nnz) {
+            if (lane == 0) atomicOr(flag, 1);
+            continue;
+        }
+        bool has_diag = false;
+        for (int64_t k = b + lane; k < e; k += 32) {
+            int j = ci[k];
+            if (j < 0 || j >= n) bad |= 1;
+            if (k > b && ci[k - 1] >= j) bad |= 1;
+            if (!isfinite(v[k])) bad |= 2;
+            if (j == i) has_diag = true;
+        }
+        bad = __reduce_or_sync(FULL, bad);
+        if (!__any_sync(FULL, has_diag)) bad |= 4;
+        if (lane == 0 && bad) atomicOr(flag, bad);
+    }
+}
+
+// ------------------------------------------------------------- ordered folds
+// Warp-cooperative left-to-right row folds.  The warp owns rows
+// row0 .. row0+31; in each 32-column chunk lane r stages entry (chunk + lane)
+// of row r into tile[r][lane] (coalesced), then every lane adds the 32 staged
+// terms of its own row in order.  Padding terms are +0.0, which leaves a sum
+// that started at +0.0 unchanged.
+template <typename Term>
+__device__ __forceinline__ double fold_rows(int row0, int n, const int64_t* __restrict__ rp, Term term,
+                                            double (*tile)[33]) {
+    const int lane = threadIdx.x & 31;
+    const int my = row0 + lane;
+    const int64_t mb = my < n ? rp[my] : 0;
+    const int mlen = my < n ? (int)(rp[my + 1] - mb) : 0;
+    const int maxlen = __reduce_max_sync(FULL, mlen);
+    double acc = 0.0;
+    for (int c = 0; c < maxlen; c += 32) {
+#pragma unroll 4
+        for (int r = 0; r < 32; r++) {
+            const int64_t rb = __shfl_sync(FULL, mb, r);
+            const int rl = __shfl_sync(FULL, mlen, r);
+            const int t = c + lane;
+            tile[r][lane] = (t < rl) ? term(rb + t, row0 + r) : 0.0;
+        }
+        __syncwarp();
+#pragma unroll 8
+        for (int s = 0; s < 32; s++) acc = __dadd_rn(acc, tile[lane][s]);
+        __syncwarp();
+    }
+    return acc;
+}
+
+// l1 diagonal (Sec. 3.2): d_i = k_ii + sum_{j != i} |k_ij|.
+__global__ void __launch_bounds__(kBlock) k_l1diag(int n, const int64_t* __restrict__ rp,
+                                                    const int32_t* __restrict__ ci, const double* __restrict__ v,
+                                                    double* kii, double* dl1, double* invd, int* flag) {
+    __shared__ double tiles[kWarpsPerBlock][32][33];
+    double(*tile)[33] = tiles[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int row0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; row0 < n; row0 += nwarps * 32) {
+        auto term = [&](int64_t k, int row) -> double {
+            const int j = ci[k];
+            const double x = v[k];
+            if (j == row) {
+                kii[row] = x;
+                return 0.0;
+            }
+            return fabs(x);
+        };
+        const double s = fold_rows(row0, n, rp, term, tile);
+        __syncwarp();
+        const int i = row0 + lane;
+        if (i < n) {
+            const double d = kii[i];
+            if (!(d > 0.0)) atomicOr(flag, 1);
+            const double dl = __dadd_rn(d, s);
+            dl1[i] = dl;
+            if (invd) invd[i] = __ddiv_rn(1.0, dl);
+        }
+    }
+}
+
+__global__ void k_diag(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                       const double* __restrict__ v, double* kii) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < n; i += nw)
+        for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32)
+            if (ci[k] == i) kii[i] = v[k];
+}
+
+// Test vector start: U[0,1) from draw i of SplitMix64(seed), or all ones.
+__global__ void k_testvec_init(int n, int kind, uint64_t seed, double* w) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        w[i] = kind == 1 ? 1.0 : (double)(splitmix64_at(seed, (uint64_t)i) >> 11) * 0x1.0p-53;
+}
+
+// One relaxation sweep on K w = 0 (Sec. 3.1): w_i <- w_i - (K w)_i / d_i.
+__global__ void __launch_bounds__(kBlock) k_testvec_sweep(int n, const int64_t* __restrict__ rp,
+                                                           const int32_t* __restrict__ ci,
+                                                           const double* __restrict__ v,
+                                                           const double* __restrict__ dl1,
+                                                           const double* __restrict__ w, double* wout) {
+    __shared__ double tiles[kWarpsPerBlock][32][33];
+    double(*tile)[33] = tiles[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int row0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; row0 < n; row0 += nwarps * 32) {
+        auto term = [&](int64_t k, int) -> double { return __dmul_rn(v[k], w[ci[k]]); };
+        const double s = fold_rows(row0, n, rp, term, tile);
+        const int i = row0 + lane;
+        if (i < n) wout[i] = __dsub_rn(w[i], __ddiv_rn(s, dl1[i]));
+    }
+}
+
+// ------------------------------------------------------------------ matching
+// Edge key of every stored entry: order_key(c_ij) (Eq. cij) for eligible
+// edges, 0 otherwise.  Eligible: j != i, k_ij != 0, denominator > 0 and
+// w_lo^2 + w_hi^2 > 0.
+__global__ void k_edge_keys(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ v, const double* __restrict__ kii,
+                            const double* __restrict__ w, uint64_t* key) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < n; i += nw) {
+        const double wi = w[i], ki = kii[i];
+        for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
+            const int j = ci[k];
+            const double a = v[k];
+            uint64_t out = 0;
+            if (j != i && a != 0.0) {
+                const double wj = w[j], kj = kii[j];
+                const double wlo = i < j ? wi : wj, whi = i < j ? wj : wi;
+                const double klo = i < j ? ki : kj, khi = i < j ? kj : ki;
+                const double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a), wlo), whi);
+                const double den = __dadd_rn(__dmul_rn(klo, __dmul_rn(wlo, wlo)), __dmul_rn(khi, __dmul_rn(whi, whi)));
+                const double nrm2 = __dadd_rn(__dmul_rn(wlo, wlo), __dmul_rn(whi, whi));
+                if (den > 0.0 && nrm2 > 0.0) out = order_key(__dsub_rn(1.0, __ddiv_rn(num, den)));
+            }
+            key[k] = out;
+        }
+    }
+}
+
+// Matching state: -1 active (unmatched, may still match), -2 dead (no
+// active eligible neighbour left: singleton), >= 0 partner.
+__global__ void k_match_init(int n, int32_t* state) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) state[i] = -1;
+}
+
+// "a heavier than b" under the strict order (key desc, lo asc, hi asc).
+__device__ __forceinline__ bool heavier(uint64_t ka, int loa, int hia, uint64_t kb, int lob, int hib) {
+    if (ka != kb) return ka > kb;
+    if (loa != lob) return loa < lob;
+    return hia < hib;
+}
+
+// Every active vertex proposes to its heaviest eligible active neighbour.
+__global__ void k_match_propose(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                const uint64_t* __restrict__ key, const int32_t* __restrict__ state,
+                                int32_t* cand) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < n; i += nw) {
+        if (state[i] != -1) continue;
+        uint64_t bk = 0;
+        int blo = 0x7fffffff, bhi = 0x7fffffff, bj = -1;
+        for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
+            const uint64_t kk = key[k];
+            if (kk == 0) continue;
+            const int j = ci[k];
+            if (state[j] != -1) continue;
+            const int lo = min(i, j), hi = max(i, j);
+            if (bj < 0 || heavier(kk, lo, hi, bk, blo, bhi)) {
+                bk = kk;
+                blo = lo;
+                bhi = hi;
+                bj = j;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t ok = __shfl_xor_sync(FULL, bk, o);
+            const int olo = __shfl_xor_sync(FULL, blo, o);
+            const int ohi = __shfl_xor_sync(FULL, bhi, o);
+            const int oj = __shfl_xor_sync(FULL, bj, o);
+            if (oj >= 0 && (bj < 0 || heavier(ok, olo, ohi, bk, blo, bhi))) {
+                bk = ok;
+                blo = olo;
+                bhi = ohi;
+                bj = oj;
+            }
+        }
+        if (lane == 0) cand[i] = bj;
+    }
+}
+
+// Mutual proposals become pairs; vertices without a candidate die.
+__global__ void k_match_commit(int n, const int32_t* __restrict__ cand, int32_t* state, int* active) {
+    int left = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (state[i] != -1) continue;
+        const int c = cand[i];
+        if (c < 0) state[i] = -2;
+        else if (cand[c] == i) state[i] = c;
+        else left++;
+    }
+    left = __reduce_add_sync(FULL, left);
+    if ((threadIdx.x & 31) == 0 && left) atomicAdd(active, left);
+}
+
+__global__ void k_match_finish(int n, const int32_t* __restrict__ state, int32_t* mate, int32_t* leader) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int s = state[i];
+        const int m = s >= 0 ? s : -1;
+        mate[i] = m;
+        leader[i] = (m < 0 || m > i) ? 1 : 0;
+    }
+}
+
+// Aggregates (Eq. prolongation): coarse index = rank of the aggregate's
+// smallest fine index; pair (i<j): p = (w_i, w_j) / sqrt(w_i^2 + w_j^2);
+// singleton: p = sign(w_i) (+1 for 0).  Also w_c = P^T w.
+__global__ void k_aggregate(int n, const int32_t* __restrict__ mate, const int32_t* __restrict__ cidx,
+                            const double* __restrict__ w, int32_t* agg, double* pval, int32_t* mem0, int32_t* mem1,
+                            double* wc) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int j = mate[i];
+        if (j >= 0 && j < i) continue;  // handled by the pair's leader
+        const int I = cidx[i];
+        const double wi = w[i];
+        if (j < 0) {
+            agg[i] = I;
+            const double p = wi < 0.0 ? -1.0 : 1.0;
+            pval[i] = p;
+            mem0[I] = i;
+            mem1[I] = -1;
+            wc[I] = __dadd_rn(0.0, __dmul_rn(p, wi));
+        } else {
+            const double wj = w[j];
+            const double nrm = __dsqrt_rn(__dadd_rn(__dmul_rn(wi, wi), __dmul_rn(wj, wj)));
+            const double pi = __ddiv_rn(wi, nrm), pj = __ddiv_rn(wj, nrm);
+            agg[i] = I;
+            agg[j] = I;
+            pval[i] = pi;
+            pval[j] = pj;
+            mem0[I] = i;
+            mem1[I] = j;
+            wc[I] = __dadd_rn(__dadd_rn(0.0, __dmul_rn(pi, wi)), __dmul_rn(pj, wj));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ scans
+// Three-phase exclusive scan: per-block scan of 1024 items, sequential scan
+// of the block totals (one block looping in chunks), add-back.
+template <typename T>
+__device__ T block_exclusive_scan(T v, T* sh, T* total) {
+    // sh: 1024 / 32 entries
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        T s = lane < (int)(blockDim.x >> 5) ? sh[lane] : (T)0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(FULL, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < (int)(blockDim.x >> 5)) sh[lane] = s;
+    }
+    __syncthreads();
+    T pre = (wid > 0 ? sh[wid - 1] : (T)0) + x - v;
+    if (total) *total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return pre;
+}
+
+template <typename T>
+__global__ void k_scan_blocks(const T* __restrict__ in, T* out, int n, T* bsum) {
+    __shared__ T sh[32];
+    __shared__ T tot;
+    const int base = blockIdx.x * 1024;
+    T loc[4];
+    T s = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        int idx = base + threadIdx.x * 4 + q;
+        loc[q] = idx < n ? in[idx] : (T)0;
+        s += loc[q];
+    }
+    T pre = block_exclusive_scan<T>(s, sh, &tot);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        int idx = base + threadIdx.x * 4 + q;
+        if (idx < n) out[idx] = pre;
+        pre += loc[q];
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+template <typename T>
+__global__ void k_scan_sums(T* bsum, int nb, T* total) {
+    __shared__ T sh[32];
+    __shared__ T tot;
+    T carry = 0;
+    for (int base = 0; base < nb; base += blockDim.x) {
+        int idx = base + threadIdx.x;
+        T v = idx < nb ? bsum[idx] : (T)0;
+        T pre = block_exclusive_scan<T>(v, sh, &tot);
+        if (idx < nb) bsum[idx] = carry + pre;
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+template <typename T>
+__global__ void k_scan_add(T* out, int n, const T* __restrict__ bsum) {
+    const int base = blockIdx.x * 1024;
+    const T add = bsum[blockIdx.x];
+    for (int q = threadIdx.x; q < 1024; q += blockDim.x) {
+        int idx = base + q;
+        if (idx < n) out[idx] += add;
+    }
+}
+
+template <typename T>
+cudaError_t scan_impl(const T* in, T* out, int n, T* total, T* scratch, cudaStream_t s) {
+    const int nb = (n + 1023) / 1024;
+    if (n <= 0) {
+        if (total) AMG_TRY(cudaMemsetAsync(total, 0, sizeof(T), s));
+        return cudaSuccess;
+    }
+    k_scan_blocks<T><<<nb, 256, 0, s>>>(in, out, n, scratch);
+    k_scan_sums<T><<<1, 1024, 0, s>>>(scratch, nb, total);
+    k_scan_add<T><<<nb, 256, 0, s>>>(out, n, scratch);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Galerkin
+// One block per coarse row I with fine members a0 < a1 (a1 = -1 for a
+// singleton).  Candidate t enumerates the entries of row a0 then row a1 in
+// column order; key = (agg[col] << 32) | t.  After a bitonic sort by key,
+// equal coarse columns J form segments whose elements are in canonical
+// (a ascending, b ascending) order.
+__device__ __forceinline__ int pow2ceil(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+__device__ void block_bitonic_sort(uint64_t* a, int P) {
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < P; t += blockDim.x) {
+                const int u = t ^ j;
+                if (u > t) {
+                    const uint64_t x = a[t], y = a[u];
+                    const bool up = (t & k) == 0;
+                    if ((x > y) == up) {
+                        a[t] = y;
+                        a[u] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ int load_candidates(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                               const int32_t* __restrict__ agg, int a0, int a1, uint64_t* keys, int cap,
+                               int* len0_out) {
+    const int64_t b0 = rp[a0];
+    const int len0 = (int)(rp[a0 + 1] - b0);
+    const int64_t b1 = a1 >= 0 ? rp[a1] : 0;
+    const int len1 = a1 >= 0 ? (int)(rp[a1 + 1] - b1) : 0;
+    const int c = len0 + len1;
+    *len0_out = len0;
+    if (c > cap) return -1;
+    const int P = pow2ceil(c);
+    for (int t = threadIdx.x; t < P; t += blockDim.x) {
+        uint64_t kk = ~0ULL;
+        if (t < c) {
+            const int j = t < len0 ? ci[b0 + t] : ci[b1 + (t - len0)];
+            kk = ((uint64_t)(uint32_t)agg[j] << 32) | (uint32_t)t;
+        }
+        keys[t] = kk;
+    }
+    __syncthreads();
+    block_bitonic_sort(keys, P);
+    return c;
+}
+
+__global__ void k_galerkin_count(int nc, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                 const int32_t* __restrict__ agg, const int32_t* __restrict__ mem0,
+                                 const int32_t* __restrict__ mem1, int cap, int64_t* rowcnt) {
+    extern __shared__ uint64_t keys[];
+    __shared__ int cnt;
+    for (int I = blockIdx.x; I < nc; I += gridDim.x) {
+        if (threadIdx.x == 0) cnt = 0;
+        int len0;
+        const int c = load_candidates(rp, ci, agg, mem0[I], mem1[I], keys, cap, &len0);
+        if (c < 0) {
+            if (threadIdx.x == 0) rowcnt[I] = -1;
+            __syncthreads();
+            continue;
+        }
+        int local = 0;
+        for (int t = threadIdx.x; t < c; t += blockDim.x)
+            if (t == 0 || (keys[t] >> 32) != (keys[t - 1] >> 32)) local++;
+        local = __reduce_add_sync(FULL, local);
+        if ((threadIdx.x & 31) == 0 && local) atomicAdd(&cnt, local);
+        __syncthreads();
+        if (threadIdx.x == 0) rowcnt[I] = cnt;
+        __syncthreads();
+    }
+}
+
+__global__ void k_galerkin_fill(int nc, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                const double* __restrict__ v, const int32_t* __restrict__ agg,
+                                const double* __restrict__ pval, const int32_t* __restrict__ mem0,
+                                const int32_t* __restrict__ mem1, int cap, const int64_t* __restrict__ crp,
+                                int32_t* cci, double* cv) {
+    extern __shared__ uint64_t keys[];
+    __shared__ int wsum[32];
+    for (int I = blockIdx.x; I < nc; I += gridDim.x) {
+        const int a0 = mem0[I], a1 = mem1[I];
+        int len0;
+        const int c = load_candidates(rp, ci, agg, a0, a1, keys, cap, &len0);
+        if (c < 0) continue;  // reported by the count kernel
+        const int64_t b0 = rp[a0], b1 = a1 >= 0 ? rp[a1] : 0;
+        const double p0 = pval[a0], p1 = a1 >= 0 ? pval[a1] : 0.0;
+        // segment index of each segment start = exclusive count of starts before it;
+        // thread-contiguous chunks keep the scan simple
+        const int per = (c + blockDim.x - 1) / blockDim.x;
+        const int t0 = min(c, threadIdx.x * per), t1 = min(c, t0 + per);
+        int mine = 0;
+        for (int t = t0; t < t1; t++)
+            if (t == 0 || (keys[t] >> 32) != (keys[t - 1] >> 32)) mine++;
+        // block exclusive scan of `mine`
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        int x = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int sv = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(FULL, sv, o);
+                if (lane >= o) sv += y;
+            }
+            if (lane < (int)(blockDim.x >> 5)) wsum[lane] = sv;
+        }
+        __syncthreads();
+        int seg = (wid > 0 ? wsum[wid - 1] : 0) + x - mine;
+        const int64_t base = crp[I];
+        for (int t = t0; t < t1; t++) {
+            const uint32_t J = (uint32_t)(keys[t] >> 32);
+            if (!(t == 0 || (keys[t] >> 32) != (keys[t - 1] >> 32))) continue;
+            const int64_t o = base + seg;
+            seg++;
+            cci[o] = (int32_t)J;
+            double acc = 0.0;
+            if ((int)J >= I) {
+                for (int u = t; u < c && (uint32_t)(keys[u] >> 32) == J; u++) {
+                    const int q = (int)(uint32_t)keys[u];
+                    const bool first = q < len0;
+                    const int64_t k = first ? b0 + q : b1 + (q - len0);
+                    const double pa = first ? p0 : p1;
+                    const double term = __dmul_rn(__dmul_rn(pa, v[k]), pval[ci[k]]);
+                    acc = __dadd_rn(acc, term);
+                }
+            }
+            cv[o] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// K_c(I,J) for J < I := K_c(J,I) (binary search of I in row J).
+__global__ void k_galerkin_mirror(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, double* v,
+                                  int* flag) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int I = warp; I < n; I += nw) {
+        for (int64_t k = rp[I] + lane; k < rp[I + 1]; k += 32) {
+            const int J = ci[k];
+            if (J >= I) break;
+            int64_t lo = rp[J], hi = rp[J + 1] - 1;
+            int64_t pos = -1;
+            while (lo <= hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                const int cm = ci[mid];
+                if (cm == I) {
+                    pos = mid;
+                    break;
+                }
+                if (cm < I) lo = mid + 1;
+                else hi = mid - 1;
+            }
+            if (pos < 0) atomicOr(flag, 8);
+            else v[k] = v[pos];
+        }
+    }
+}
+
+// max over coarse rows of the candidate count len(a0) + len(a1)
+__global__ void k_row_stats(int nc, const int64_t* __restrict__ rp, const int32_t* __restrict__ mem0,
+                            const int32_t* __restrict__ mem1, int* maxcand) {
+    int m = 0;
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+        const int a0 = mem0[I], a1 = mem1[I];
+        int c = (int)(rp[a0 + 1] - rp[a0]);
+        if (a1 >= 0) c += (int)(rp[a1 + 1] - rp[a1]);
+        m = max(m, c);
+    }
+    m = __reduce_max_sync(FULL, m);
+    if ((threadIdx.x & 31) == 0) atomicMax(maxcand, m);
+}
+
+// Composite map P = P_1 ... P_m of one level.
+struct PassPtrs {
+    const int32_t* agg[kMaxPasses];
+    const double* pval[kMaxPasses];
+};
+
+__global__ void k_compose(int n, int npass, PassPtrs pp, int32_t* agg, double* pval) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int a = pp.agg[0][i];
+        double pv = pp.pval[0][i];
+        for (int s = 1; s < npass; s++) {
+            pv = __dmul_rn(pv, pp.pval[s][a]);
+            a = pp.agg[s][a];
+        }
+        agg[i] = a;
+        pval[i] = pv;
+    }
+}
+
+__global__ void k_member_count(int n, const int32_t* __restrict__ agg, int32_t* cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) atomicAdd(&cnt[agg[i]], 1);
+}
+
+// Members in ascending fine order: rank of i among the members of agg[i]
+// that precede it (members of one aggregate are at most 2^m apart in count,
+// scanned through the aggregate's own list after an unordered fill).
+__global__ void k_member_fill(int n, const int32_t* __restrict__ agg, const int32_t* __restrict__ mptr,
+                              int32_t* midx, int* cursor) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int I = agg[i];
+        const int slot = atomicAdd(&cursor[I], 1);
+        midx[mptr[I] + slot] = i;
+    }
+}
+
+__global__ void k_member_sort(int nc, const int32_t* __restrict__ mptr, int32_t* midx) {
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+        const int b = mptr[I], e = mptr[I + 1];
+        for (int u = b + 1; u < e; u++) {
+            const int x = midx[u];
+            int t = u - 1;
+            while (t >= b && midx[t] > x) {
+                midx[t + 1] = midx[t];
+                t--;
+            }
+            midx[t + 1] = x;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ coarsest
+__global__ void k_dense_from_csr(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                 const double* __restrict__ v, double* D) {
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        for (int j = threadIdx.x; j < n; j += blockDim.x) D[(int64_t)i * n + j] = 0.0;
+        __syncthreads();
+        for (int64_t k = rp[i] + threadIdx.x; k < rp[i + 1]; k += blockDim.x) D[(int64_t)i * n + ci[k]] = v[k];
+        __syncthreads();
+    }
+}
+
+// Right-looking Cholesky D = L L^T in place (lower triangle, one block).
+__global__ void k_cholesky(int n, double* D, int* flag) {
+    __shared__ double piv;
+    for (int j = 0; j < n; j++) {
+        if (threadIdx.x == 0) {
+            const double djj = D[(int64_t)j * n + j];
+            if (!(djj > 0.0)) {
+                atomicOr(flag, 16);
+                piv = 1.0;
+            } else {
+                piv = sqrt(djj);
+            }
+            D[(int64_t)j * n + j] = piv;
+        }
+        __syncthreads();
+        const double ljj = piv;
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) D[(int64_t)i * n + j] /= ljj;
+        __syncthreads();
+        const int m = n - j - 1;
+        for (int64_t t = threadIdx.x; t < (int64_t)m * m; t += blockDim.x) {
+            const int i = j + 1 + (int)(t / m), k = j + 1 + (int)(t % m);
+            if (k <= i) D[(int64_t)i * n + k] -= D[(int64_t)i * n + j] * D[(int64_t)k * n + j];
+        }
+        __syncthreads();
+    }
+}
+
+// Column c of A^-1 = L^-T L^-1 e_c, one block per column.
+__global__ void k_chol_inverse(int n, const double* __restrict__ L, double* Ainv, double* work) {
+    for (int c = blockIdx.x; c < n; c += gridDim.x) {
+        double* y = work + (int64_t)c * n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (i == c) ? 1.0 : 0.0;
+        __syncthreads();
+        for (int k = 0; k < n; k++) {  // forward: L y = e_c
+            __shared__ double yk;
+            if (threadIdx.x == 0) {
+                yk = y[k] / L[(int64_t)k * n + k];
+                y[k] = yk;
+            }
+            __syncthreads();
+            for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) y[i] -= L[(int64_t)i * n + k] * yk;
+            __syncthreads();
+        }
+        for (int k = n - 1; k >= 0; k--) {  // backward: L^T x = y
+            __shared__ double xk;
+            if (threadIdx.x == 0) {
+                xk = y[k] / L[(int64_t)k * n + k];
+                y[k] = xk;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] -= L[(int64_t)k * n + i] * xk;
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) Ainv[(int64_t)i * n + c] = y[i];
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// ============================================================== launch wrappers
+cudaError_t launch_validate_csr(const DevCSR& A, int* flag, cudaStream_t s) {
+    if (A.n == 0) return cudaSuccess;
+    k_validate<<<blocks_for(A.n, kWarpsPerBlock, 8192), kBlock, 0, s>>>(A.n, A.nnz, A.rowptr, A.col, A.val, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l1diag(const DevCSR& A, double* kii, double* dl1, double* invd, int* flag, cudaStream_t s) {
+    if (A.n == 0) return cudaSuccess;
+    AMG_TRY(cudaMemsetAsync(kii, 0, sizeof(double) * A.n, s));
+    k_l1diag<<<blocks_for(A.n, kBlock, 4096), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, kii, dl1, invd, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const DevCSR& A, double* kii, cudaStream_t s) {
+    AMG_TRY(cudaMemsetAsync(kii, 0, sizeof(double) * A.n, s));
+    k_diag<<<blocks_for(A.n, kWarpsPerBlock, 8192), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, kii);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_testvec_init(int n, int kind, uint64_t seed, double* w, cudaStream_t s) {
+    k_testvec_init<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, kind, seed, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_testvec_sweep(const DevCSR& A, const double* dl1, const double* w, double* wout, cudaStream_t s) {
+    k_testvec_sweep<<<blocks_for(A.n, kBlock, 4096), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, dl1, w, wout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_edge_keys(const DevCSR& A, const double* kii, const double* w, uint64_t* key, cudaStream_t s) {
+    k_edge_keys<<<blocks_for(A.n, kWarpsPerBlock, 8192), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, kii, w, key);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_match_init(int n, int32_t* state, cudaStream_t s) {
+    k_match_init<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, state);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_match_propose(const DevCSR& A, const uint64_t* key, const int32_t* state, int32_t* cand,
+                                 cudaStream_t s) {
+    k_match_propose<<<blocks_for(A.n, kWarpsPerBlock, 8192), kBlock, 0, s>>>(A.n, A.rowptr, A.col, key, state, cand);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_match_commit(int n, const int32_t* cand, int32_t* state, int* active, cudaStream_t s) {
+    k_match_commit<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, cand, state, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_match_finish(int n, const int32_t* state, int32_t* mate, int32_t* leader, cudaStream_t s) {
+    k_match_finish<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, state, mate, leader);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aggregate(int n, const int32_t* mate, const int32_t* cidx, const double* w, int32_t* agg,
+                             double* pval, int32_t* mem0, int32_t* mem1, double* wc, cudaStream_t s) {
+    k_aggregate<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, mate, cidx, w, agg, pval, mem0, mem1, wc);
+    return cudaGetLastError();
+}
+
+size_t scan_scratch_ints(int n) { return (size_t)(n + 1023) / 1024 + 1; }
+size_t scan64_scratch(int n) { return (size_t)(n + 1023) / 1024 + 1; }
+
+cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int n, int32_t* total, int32_t* scratch,
+                                  cudaStream_t s) {
+    return scan_impl<int32_t>(in, out, n, total, scratch, s);
+}
+
+cudaError_t launch_scan64(const int64_t* in, int64_t* out, int n, int64_t* scratch, cudaStream_t s) {
+    // out has n+1 entries: exclusive scan plus the total at out[n]
+    return scan_impl<int64_t>(in, out, n, out + n, scratch, s);
+}
+
+static size_t galerkin_smem(int cap) { return sizeof(uint64_t) * (size_t)cap; }
+
+cudaError_t launch_galerkin_count(const DevCSR& A, const int32_t* agg, const int32_t* mem0, const int32_t* mem1,
+                                  int nc, int cap, int64_t* rowcnt, cudaStream_t s) {
+    const size_t sm = galerkin_smem(cap);
+    if (sm > 48 * 1024) AMG_TRY(cudaFuncSetAttribute(k_galerkin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_galerkin_count<<<blocks_for(nc, 1, 65536), kBlock, sm, s>>>(nc, A.rowptr, A.col, agg, mem0, mem1, cap, rowcnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_galerkin_fill(const DevCSR& A, const int32_t* agg, const double* pval, const int32_t* mem0,
+                                 const int32_t* mem1, int cap, DevCSR& C, cudaStream_t s) {
+    const size_t sm = galerkin_smem(cap);
+    if (sm > 48 * 1024) AMG_TRY(cudaFuncSetAttribute(k_galerkin_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_galerkin_fill<<<blocks_for(C.n, 1, 65536), kBlock, sm, s>>>(C.n, A.rowptr, A.col, A.val, agg, pval, mem0, mem1,
+                                                                    cap, C.rowptr, C.col, C.val);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_galerkin_mirror(DevCSR& C, int* flag, cudaStream_t s) {
+    k_galerkin_mirror<<<blocks_for(C.n, kWarpsPerBlock, 8192), kBlock, 0, s>>>(C.n, C.rowptr, C.col, C.val, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_stats(const DevCSR& A, const int32_t* mem0, const int32_t* mem1, int nc, int* maxcand,
+                             cudaStream_t s) {
+    k_row_stats<<<blocks_for(nc, kBlock, 4096), kBlock, 0, s>>>(nc, A.rowptr, mem0, mem1, maxcand);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compose(int n, int npass, const Pass* passes, int32_t* agg, double* pval, cudaStream_t s) {
+    PassPtrs pp{};
+    for (int q = 0; q < npass; q++) {
+        pp.agg[q] = passes[q].agg;
+        pp.pval[q] = passes[q].pval;
+    }
+    k_compose<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, npass, pp, agg, pval);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_member_count(int n, const int32_t* agg, int nc, int32_t* cnt, cudaStream_t s) {
+    AMG_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nc + 1), s));
+    k_member_count<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, agg, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_member_fill(int n, const int32_t* agg, const int32_t* mem_ptr, int nc, int32_t* mem_idx,
+                               int* cursor, cudaStream_t s) {
+    AMG_TRY(cudaMemsetAsync(cursor, 0, sizeof(int) * nc, s));
+    k_member_fill<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, agg, mem_ptr, mem_idx, cursor);
+    k_member_sort<<<blocks_for(nc, kBlock, 4096), kBlock, 0, s>>>(nc, mem_ptr, mem_idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_from_csr(const DevCSR& A, double* D, cudaStream_t s) {
+    k_dense_from_csr<<<blocks_for(A.n, 1, 4096), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, D);
+    return cudaGetLastError();
+}
+
+// D (n x n, overwritten by its Cholesky factor); Ainv receives the inverse.
+// Ainv must have room for 2 n^2 doubles (second half is work space).
+cudaError_t launch_dense_spd_inverse(int n, double* D, double* Ainv, int* flag, cudaStream_t s) {
+    k_cholesky<<<1, 1024, 0, s>>>(n, D, flag);
+    k_chol_inverse<<<blocks_for(n, 1, 4096), kBlock, 0, s>>>(n, D, Ainv, Ainv + (int64_t)n * n);
+    return cudaGetLastError();
+}
+
+}  // namespace amg

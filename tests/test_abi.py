@@ -1,0 +1,41 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point that include/amg_gb300.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+from paper_2511_21268_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "amg_gb300.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(amg_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for required in ("amg_opts_default", "amg_setup", "amg_pcg_solve", "amg_get_info", "amg_export_level",
+                     "amg_free", "amg_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    path = _build.build_cuda()
+    L = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    L.amg_strerror.restype = ctypes.c_char_p
+    assert L.amg_strerror(-5).startswith(b"matching")
+    # argument checks run on the host, no device needed
+    assert L.amg_opts_default(None) == -1
+    assert L.amg_setup(None, None, None, None) == -1
+
+
+def test_binding_names_match_abi():
+    from paper_2511_21268_gb300 import amg
+
+    for name in declared_functions():
+        assert hasattr(amg, name), name

@@ -1,0 +1,392 @@
+"""Benchmark: time-to-solution of matching-based AMG-PCG on an IgA system.
+
+Workload (one GPU): 3-D Poisson on the unit cube, B-splines of degree p=3
+with C^2 continuity, n=64 elements per direction, homogeneous Dirichlet
+data eliminated (N = 65^3 = 274,625 unknowns, 86,938,307 nonzeros, FP64
+CSR 1.04 GB), f from the manufactured solution u = sin(pi x) sin(pi y)
+sin(pi z); PCG with the matching-based aggregation AMG V-cycle (two matching
+passes per level, one l1-Jacobi pre/post sweep, coarsest <= 200 rows solved
+densely), x0 = 0, rtol 1e-8, all in FP64.
+
+One step = amg_setup + amg_pcg_solve + amg_free on that system (the whole
+hot path), inputs resident in HBM.  The matrix (1.04 GB) is larger than L2
+(129 MB), so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own copy of the system (independent
+replicas, no collective on the data path): weak scaling.  Rank 0 prints one
+JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-solution at rtol 1e-8 and V-cycle HBM GB/s: mixed/learned vs FP64 AMG"
+WORKLOAD = "3-D Poisson unit cube, B-spline p=3 C^2, n=64 (N=274,625, nnz=86,938,307), FP64 AMG-PCG, rtol 1e-8"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fine_matrix_pass_fp64_3d_p3_n64.md")
+KERNEL_NAMES = ["k_spmv_pq<8> (q = K p)", "k_resid<8> (down-sweep residual)", "k_up0<8> (up-sweep smoothing)"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--p", type=int, default=3)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def committed_traffic():
+    """DRAM bytes per launch of the fine-level kernels from the committed ncu
+    summary, or None if the kernels changed since it was taken."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    txt = open(PROFILE_SUMMARY).read()
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    src = open(os.path.join(ROOT, "paper_2511_21268_gb300", "csrc", "solve_kernels.cu"), "rb").read()
+    if not m or m.group(1) != hashlib.sha256(src).hexdigest():
+        return None
+    out = {}
+    for k, v in re.findall(r"traffic_bytes_per_launch\[(\w+)\]:\s*([0-9.eE+]+)", txt):
+        out[k] = float(v)
+    return out or None
+
+
+class ClockSampler:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and parts[1] != self.uuid:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def init_dist(world):
+    import torch
+    import torch.distributed as dist
+
+    if world > 1 and not dist.is_initialized():
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------- oracle
+def cpu_baseline(prob, iters_gpu: int, rtol: float) -> dict:
+    """Time the CPU oracle on a bounded sample of the workload: the full setup
+    plus CG with itmax = 0 and 1 (their difference is one CG iteration), scaled
+    to the iteration count of the GPU solve (the two agree within +-1)."""
+    import oracle as O
+
+    t0 = time.perf_counter()
+    H = O.Hierarchy(prob.rowptr, prob.col, prob.val)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    H.pcg(prob.F, rtol=rtol, itmax=0)
+    t_start = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    H.pcg(prob.F, rtol=rtol, itmax=1)
+    t_iter = max(time.perf_counter() - t0 - t_start, 0.0)
+    value = t_setup + t_start + iters_gpu * t_iter
+    return {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"full oracle setup ({t_setup:.2f} s) + CG start ({t_start:.3f} s) + one CG iteration "
+                       f"({t_iter:.3f} s) on the full system, scaled to {iters_gpu} iterations; single-threaded "
+                       f"plain C oracle"),
+            "setup_s": t_setup, "iter_s": t_iter}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle as the reference arm, rank 0 only."""
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_2511_21268_gb300 import inputs as I
+
+    prob = I.poisson_box(3, args.n, args.p)
+    t0 = time.perf_counter()
+    H = O.Hierarchy(prob.rowptr, prob.col, prob.val)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    full = H.pcg(prob.F, rtol=args.rtol)
+    t_full = time.perf_counter() - t0
+    samples = []
+    for k in range(args.warmup + args.steps):  # each step: one CG iteration of the oracle
+        t0 = time.perf_counter()
+        H.pcg(prob.F, rtol=args.rtol, itmax=0)
+        a = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        H.pcg(prob.F, rtol=args.rtol, itmax=1)
+        b = time.perf_counter() - t0
+        if k >= args.warmup:
+            samples.append((a, b))
+    t_start = statistics.median(a for a, _ in samples)
+    t_iter = statistics.median(max(b - a, 0.0) for a, b in samples)
+    value = t_setup + t_start + full["iters"] * t_iter
+    sample = (f"oracle setup once ({t_setup:.2f} s), full oracle solve once ({full['iters']} iterations, "
+              f"{t_full:.1f} s); each step = one oracle CG iteration on the full system; value = setup + start + "
+              f"iterations x median step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": args.n, "p": args.p, "N": prob.n, "nnz": prob.nnz,
+                       "rtol": args.rtol},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "iters": full["iters"], "measured_full_solve_s": t_full, "setup_s": t_setup}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------- ours
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = env_rank()
+    dist = init_dist(world)
+    torch.cuda.set_device(local)
+    from paper_2511_21268_gb300 import amg as A
+    from paper_2511_21268_gb300 import inputs as I
+
+    A.lib()  # build/load the CUDA library before anything is timed
+    prob = I.poisson_box(3, args.n, args.p)
+    dev = torch.device("cuda", local)
+    rp = torch.from_numpy(prob.rowptr).to(dev)
+    ci = torch.from_numpy(prob.col).to(dev)
+    va = torch.from_numpy(prob.val).to(dev)
+    F = torch.from_numpy(prob.F).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    opts = A.amg_opts_default()
+
+    def step(profile=False):
+        h = A.amg_setup(rp, ci, va, opts, stream)
+        if profile:
+            A.amg_profile_kernels(h, True)
+        u = torch.zeros_like(F)
+        st, it, rr = A.amg_pcg_solve(h, F, u, args.rtol, 10000)
+        info = A.amg_get_info(h)
+        kt = A.amg_kernel_times(h) if profile else None
+        A.amg_free(h)
+        if st != A.AMG_OK:
+            raise RuntimeError(f"solve failed: {A.amg_strerror(st)}")
+        return it, rr, info, kt
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        uuid = None
+        try:
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+        except Exception:
+            pass
+        clocks = ClockSampler(uuid) if (rank == 0 and not args.no_clocks) else None
+        barrier(dist)
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        torch.cuda.nvtx.range_push("timed")
+        l0 = A.amg_kernel_launches()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ms_sum = np.zeros(3)
+        cnt_sum = np.zeros(3, np.int64)
+        kbytes = None
+        infos = []
+        for _ in range(args.steps):
+            it, rr, info, kt = step(profile=True)
+            ms_sum += kt[0]
+            cnt_sum += kt[1]
+            kbytes = kt[2]
+            infos.append((it, rr, info))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = A.amg_kernel_launches() - l0
+        torch.cuda.nvtx.range_pop()
+        clk = clocks.stop() if clocks else None
+        barrier(dist)
+        elapsed_ms = max_over_ranks(dist, e0.elapsed_time(e1))
+        ms_per_step = elapsed_ms / args.steps
+        it, rr, info = infos[-1]
+
+        # V-cycle alone (standalone applications, events on the same stream)
+        h = A.amg_setup(rp, ci, va, opts, stream)
+        vinfo = A.amg_get_info(h)
+        r = torch.randn(prob.n, dtype=torch.float64, device=dev)
+        z = torch.empty_like(r)
+        for _ in range(3):
+            A.amg_vcycle_apply(h, r, z)
+        v0 = torch.cuda.Event(enable_timing=True)
+        v1 = torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        nv = 20
+        for _ in range(nv):
+            A.amg_vcycle_apply(h, r, z)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        vcycle_ms = v0.elapsed_time(v1) / nv
+        A.amg_free(h)
+
+        # end to end through the public API with pinned host buffers
+        e2e = None
+        if not args.no_e2e:
+            hrp = torch.from_numpy(prob.rowptr).pin_memory()
+            hci = torch.from_numpy(prob.col).pin_memory()
+            hva = torch.from_numpy(prob.val).pin_memory()
+            hF = torch.from_numpy(prob.F).pin_memory()
+            hu = torch.zeros(prob.n, dtype=torch.float64).pin_memory()
+            e2e_steps = max(3, min(args.steps, 5))
+            ts = []
+            for k in range(e2e_steps + 1):
+                hu.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                h = A.amg_setup(hrp, hci, hva, opts, stream)
+                st, it2, rr2 = A.amg_pcg_solve(h, hF, hu, args.rtol, 10000)
+                A.amg_free(h)
+                torch.cuda.synchronize()
+                if k > 0:
+                    ts.append(time.perf_counter() - t0)
+                assert st == A.AMG_OK
+            e2e_s = max_over_ranks(dist, statistics.median(ts))
+            h2d = prob.rowptr.nbytes + prob.col.nbytes + prob.val.nbytes + prob.F.nbytes + prob.n * 8
+            e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(prob.n * 8),
+                   "steps": e2e_steps, "host_buffers": "pinned"}
+
+    peak, peak_kind = measured_peaks()
+    avg_ms = ms_sum / np.maximum(cnt_sum, 1)
+    per_kernel = {}
+    for q, name in enumerate(KERNEL_NAMES):
+        gbs = kbytes[q] / (avg_ms[q] * 1e-3) / 1e9 if avg_ms[q] > 0 else None
+        per_kernel[name] = {"bytes_per_launch": kbytes[q], "avg_ms": avg_ms[q], "launches": int(cnt_sum[q]),
+                            "achieved_gbs": gbs}
+    dom = int(np.argmax(ms_sum))
+    traffic = committed_traffic()
+    tkey = ["spmv_pq", "resid", "up0"][dom]
+    roof = {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": per_kernel[KERNEL_NAMES[dom]]["achieved_gbs"],
+            "peak": peak, "unit": "GB/s", "frac": (per_kernel[KERNEL_NAMES[dom]]["achieved_gbs"] or 0.0) / peak,
+            "traffic": (traffic or {}).get(tkey), "peak_kind": f"{peak_kind} (hbm_gbs, STREAM-style copy)",
+            "bytes_per_launch": kbytes[dom], "avg_launch_ms": avg_ms[dom], "all": per_kernel,
+            # the FP64 matrix pass issues one DFMA per nonzero; GB300's FP64 rate (nominal 1.25 TFLOP/s)
+            # makes that issue rate a second, nearly binding limit (ncu: FP64 pipe ~80 % busy)
+            "fp64_alu": {"achieved_tflops": 2.0 * prob.nnz / (avg_ms[dom] * 1e-3) / 1e12, "peak_tflops": 1.25,
+                         "frac": 2.0 * prob.nnz / (avg_ms[dom] * 1e-3) / 1.25e12, "peak_kind": "nominal"}}
+
+    line = {"metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": args.n, "p": args.p, "N": prob.n, "nnz": prob.nnz,
+                       "rtol": args.rtol, "precision": "fp64", "l2": "inputs larger than L2 (matrix 1.04 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "iters": it, "final_relres": rr, "setup_ms": info.setup_ms, "solve_ms": info.solve_ms,
+            "levels": [int(info.n[l]) for l in range(info.levels)], "opc": info.opc,
+            "iter_gbps": info.iter_bytes * it / (info.solve_ms * 1e-3) / 1e9 if info.solve_ms > 0 else None,
+            "vcycle_ms": vcycle_ms, "vcycle_gbps": vinfo.vcycle_bytes / (vcycle_ms * 1e-3) / 1e9,
+            "throughput_systems_per_s": world * args.steps / (elapsed_ms * 1e-3),
+            "roofline": roof, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prob, it, args.rtol)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

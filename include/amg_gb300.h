@@ -158,6 +158,23 @@ int amg_export_level(const amg_hierarchy* h, int32_t level, int64_t* rowptr, int
 int amg_export_pass(const amg_hierarchy* h, int32_t level, int32_t pass, int64_t* n_s, int32_t* mate, int32_t* agg,
                     double* pval);
 
+/* Number of CUDA kernels this library has launched in this process (graph
+ * launches count every kernel node).  Never fails. */
+int64_t amg_kernel_launches(void);
+
+/* Opt-in kernel timing (enable = 1 / 0).  While enabled, amg_pcg_solve
+ * records CUDA events, on the stream the kernels run on, around the three
+ * finest-level matrix passes of every CG iteration: [0] q = K p,
+ * [1] down-sweep residual r = f - K x, [2] up-sweep smoothing.  Resets the
+ * accumulated times. */
+int amg_profile_kernels(amg_hierarchy* h, int32_t enable);
+
+/* Accumulated timing of those kernels: ms[3] total milliseconds, count[3]
+ * launches that did full work, bytes[3] algorithmic bytes of one launch
+ * (values and column indices once, row pointers once, each vector read or
+ * written once).  Any pointer may be NULL. */
+int amg_kernel_times(const amg_hierarchy* h, double* ms, int64_t* count, double* bytes);
+
 /* Release the hierarchy and its device memory. */
 int amg_free(amg_hierarchy* h);
 

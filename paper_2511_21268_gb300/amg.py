@@ -78,6 +78,9 @@ _SIGS = {
     "amg_export_level": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 7),
     "amg_export_pass": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 4),
     "amg_free": (ctypes.c_int, [ctypes.c_void_p]),
+    "amg_kernel_launches": (ctypes.c_int64, []),
+    "amg_profile_kernels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "amg_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "amg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "amg_last_cuda_error": (ctypes.c_char_p, []),
 }
@@ -228,6 +231,23 @@ def amg_export_pass(h, level: int, pass_: int):
     _check(lib().amg_export_pass(h, level, pass_, None, mate.ctypes.data, agg.ctypes.data, pv.ctypes.data),
            "amg_export_pass")
     return mate, agg, pv
+
+
+def amg_kernel_launches() -> int:
+    return int(lib().amg_kernel_launches())
+
+
+def amg_profile_kernels(h, enable: bool):
+    _check(lib().amg_profile_kernels(h, int(enable)), "amg_profile_kernels")
+
+
+def amg_kernel_times(h):
+    """(ms[3], count[3], bytes[3]) of the three fine-level matrix passes."""
+    ms = np.zeros(3)
+    cnt = np.zeros(3, np.int64)
+    b = np.zeros(3)
+    _check(lib().amg_kernel_times(h, ms.ctypes.data, cnt.ctypes.data, b.ctypes.data), "amg_kernel_times")
+    return ms, cnt, b
 
 
 def amg_free(h):

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -23,6 +24,11 @@
 #include "amg_internal.cuh"
 
 using namespace amg;
+
+namespace amg {
+static std::atomic<long long> g_launches{0};
+long long note_launch() { return ++g_launches; }
+}  // namespace amg
 
 namespace {
 
@@ -369,12 +375,18 @@ void destroy(amg_hierarchy* h) {
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->evs) cudaEventDestroy(h->evs);
-    if (h->s) cudaStreamDestroy(h->s);
+    for (auto& a : h->prof_ev)
+        for (auto& b : a)
+            for (auto& e : b)
+                if (e) cudaEventDestroy(e);
+    if (h->s && h->own_stream) cudaStreamDestroy(h->s);
     delete h;
 }
 
-// order the internal stream after the caller's stream
+// order the internal stream after the caller's stream (no-op when the
+// library runs on the caller's stream itself)
 int join_caller(amg_hierarchy* h) {
+    if (!h->own_stream) return AMG_OK;
     CK(cudaEventRecord(h->evs, h->us));
     CK(cudaStreamWaitEvent(h->s, h->evs, 0));
     return AMG_OK;
@@ -433,7 +445,17 @@ int amg_setup(const amg_csr* K, const amg_opts* opts, void* cuda_stream, amg_hie
     }
     memset(&h->info, 0, sizeof(h->info));
     h->us = (cudaStream_t)cuda_stream;
-    cudaError_t e = cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking);
+    // A caller-provided stream is used directly (so caller events bracket the
+    // kernels); the legacy default stream cannot be captured into a graph,
+    // so a NULL stream gets a private stream ordered after it.
+    cudaError_t e = cudaSuccess;
+    if (h->us) {
+        h->s = h->us;
+        h->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking);
+        h->own_stream = true;
+    }
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->evs, cudaEventDisableTiming);
@@ -477,10 +499,17 @@ static int run_solve(amg_hierarchy* h, int32_t* iters) {
     CK(enqueue_pcg_start(h, s));
     if (!h->graph) {
         cudaGraph_t g;
+        const long long before = amg::g_launches.load();
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
-        for (int k = 0; k < kGraphIters && e == cudaSuccess; k++) e = enqueue_pcg_iteration(h, s);
+        for (int k = 0; k < kGraphIters && e == cudaSuccess; k++) {
+            h->prof_slot = h->prof ? k : -1;
+            e = enqueue_pcg_iteration(h, s);
+        }
+        h->prof_slot = -1;
         cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        h->graph_kernels = amg::g_launches.load() - before;
+        amg::g_launches -= h->graph_kernels;  // captured, not launched
         if (e != cudaSuccess) return cuda_fail(e, "capture");
         if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
         e = cudaGraphInstantiate(&h->graph, g, 0);
@@ -492,11 +521,27 @@ static int run_solve(amg_hierarchy* h, int32_t* iters) {
         h->graph_iters = kGraphIters;
     }
     const int max_launches = h->itmax / kGraphIters + 2;
-    for (int k = 0; k <= max_launches; k++) {
+    int it_before = 0;
+    for (int k = 0; k <= max_launches + 1; k++) {
         CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (h->st_host->done) break;
+        if (h->prof && k > 0) {  // accumulate the kernels of the launch that just finished
+            const int ndone = h->st_host->iters - it_before;
+            for (int j = 0; j < kGraphIters; j++)
+                for (int q = 0; q < 3; q++) {
+                    const int full = q == 0 ? ndone : ndone - (h->st_host->done ? 1 : 0);
+                    if (j >= full) continue;
+                    float ms = 0.f;
+                    if (cudaEventElapsedTime(&ms, h->prof_ev[j][q][0], h->prof_ev[j][q][1]) == cudaSuccess) {
+                        h->prof_ms[q] += ms;
+                        h->prof_cnt[q]++;
+                    }
+                }
+        }
+        it_before = h->st_host->iters;
+        if (h->st_host->done || k > max_launches) break;
         CK(cudaGraphLaunch(h->graph, s));
+        amg::g_launches += h->graph_kernels;
     }
     CK(cudaEventRecord(h->ev1, s));
     CK(launch_final_residual(h, s));
@@ -605,6 +650,42 @@ int amg_export_pass(const amg_hierarchy* hc, int32_t level, int32_t pass, int64_
     if (agg) CK(cudaMemcpyAsync(agg, P.agg, sizeof(int32_t) * P.n, cudaMemcpyDeviceToHost, s));
     if (pval) CK(cudaMemcpyAsync(pval, P.pval, sizeof(double) * P.n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+int64_t amg_kernel_launches(void) { return (int64_t)amg::g_launches.load(); }
+
+int amg_profile_kernels(amg_hierarchy* h, int32_t enable) {
+    if (!h || enable < 0 || enable > 1) return AMG_ERR_ARG;
+    if (enable && !h->prof_ev[0][0][0]) {
+        for (auto& a : h->prof_ev)
+            for (auto& b : a)
+                for (auto& e : b) CK(cudaEventCreate(&e));
+    }
+    if (h->prof != enable && h->graph) {  // the iteration graph changes shape
+        CK(cudaStreamSynchronize(h->s));
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->prof = enable;
+    for (int q = 0; q < 3; q++) {
+        h->prof_ms[q] = 0.0;
+        h->prof_cnt[q] = 0;
+    }
+    return AMG_OK;
+}
+
+int amg_kernel_times(const amg_hierarchy* h, double* ms, int64_t* count, double* bytes) {
+    if (!h) return AMG_ERR_ARG;
+    const double n = h->lev[0].A.n, nnz = (double)h->lev[0].A.nnz;
+    const double base = nnz * 12.0 + (n + 1.0) * 8.0;
+    const double flex = h->o.flexible ? 8.0 * n : 0.0;
+    const double b[3] = {base + 16.0 * n + flex, base + 24.0 * n, base + 32.0 * n + flex};
+    for (int q = 0; q < 3; q++) {
+        if (ms) ms[q] = h->prof_ms[q];
+        if (count) count[q] = h->prof_cnt[q];
+        if (bytes) bytes[q] = b[q];
+    }
     return AMG_OK;
 }
 

@@ -99,9 +99,19 @@ struct amg_hierarchy {
     int hist_cap = 0;
     amg_info info;
     int num_sms = 0;
+    bool own_stream = false;
     // captured iteration graph
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0;
+    long long graph_kernels = 0;  // kernels per graph launch
+    // opt-in timing of the three fine-level matrix-pass kernels of each CG
+    // iteration (q = K p, down-sweep residual, up-sweep) with event-record
+    // nodes in the iteration graph
+    int prof = 0;
+    cudaEvent_t prof_ev[16][3][2] = {};
+    double prof_ms[3] = {0, 0, 0};
+    long long prof_cnt[3] = {0, 0, 0};
+    int prof_slot = -1;  // iteration slot being captured, -1 = not capturing
 };
 
 namespace amg {
@@ -185,6 +195,13 @@ __device__ __forceinline__ float warp_sumf(float v) {
 #endif
 
 }  // namespace amg
+
+// Every kernel launch goes through AMG_GRID(grid) so the library can report
+// how many kernels it launched (amg_kernel_launches).
+namespace amg {
+long long note_launch();
+}
+#define AMG_GRID(g) (amg::note_launch(), (g))
 
 #define AMG_TRY(expr)                          \
     do {                                       \

@@ -384,9 +384,9 @@ cudaError_t scan_impl(const T* in, T* out, int n, T* total, T* scratch, cudaStre
         if (total) AMG_TRY(cudaMemsetAsync(total, 0, sizeof(T), s));
         return cudaSuccess;
     }
-    k_scan_blocks<T><<<nb, 256, 0, s>>>(in, out, n, scratch);
-    k_scan_sums<T><<<1, 1024, 0, s>>>(scratch, nb, total);
-    k_scan_add<T><<<nb, 256, 0, s>>>(out, n, scratch);
+    k_scan_blocks<T><<<AMG_GRID(nb), 256, 0, s>>>(in, out, n, scratch);
+    k_scan_sums<T><<<AMG_GRID(1), 1024, 0, s>>>(scratch, nb, total);
+    k_scan_add<T><<<AMG_GRID(nb), 256, 0, s>>>(out, n, scratch);
     return cudaGetLastError();
 }
 
@@ -702,62 +702,62 @@ __global__ void k_chol_inverse(int n, const double* __restrict__ L, double* Ainv
 // ============================================================== launch wrappers
 cudaError_t launch_validate_csr(const DevCSR& A, int* flag, cudaStream_t s) {
     if (A.n == 0) return cudaSuccess;
-    k_validate<<<blocks_for(A.n, kWarpsPerBlock, 8192), kBlock, 0, s>>>(A.n, A.nnz, A.rowptr, A.col, A.val, flag);
+    k_validate<<<AMG_GRID(blocks_for(A.n, kWarpsPerBlock, 8192)), kBlock, 0, s>>>(A.n, A.nnz, A.rowptr, A.col, A.val, flag);
     return cudaGetLastError();
 }
 
 cudaError_t launch_l1diag(const DevCSR& A, double* kii, double* dl1, double* invd, int* flag, cudaStream_t s) {
     if (A.n == 0) return cudaSuccess;
     AMG_TRY(cudaMemsetAsync(kii, 0, sizeof(double) * A.n, s));
-    k_l1diag<<<blocks_for(A.n, kBlock, 4096), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, kii, dl1, invd, flag);
+    k_l1diag<<<AMG_GRID(blocks_for(A.n, kBlock, 4096)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, kii, dl1, invd, flag);
     return cudaGetLastError();
 }
 
 cudaError_t launch_diag(const DevCSR& A, double* kii, cudaStream_t s) {
     AMG_TRY(cudaMemsetAsync(kii, 0, sizeof(double) * A.n, s));
-    k_diag<<<blocks_for(A.n, kWarpsPerBlock, 8192), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, kii);
+    k_diag<<<AMG_GRID(blocks_for(A.n, kWarpsPerBlock, 8192)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, kii);
     return cudaGetLastError();
 }
 
 cudaError_t launch_testvec_init(int n, int kind, uint64_t seed, double* w, cudaStream_t s) {
-    k_testvec_init<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, kind, seed, w);
+    k_testvec_init<<<AMG_GRID(blocks_for(n, kBlock, 4096)), kBlock, 0, s>>>(n, kind, seed, w);
     return cudaGetLastError();
 }
 
 cudaError_t launch_testvec_sweep(const DevCSR& A, const double* dl1, const double* w, double* wout, cudaStream_t s) {
-    k_testvec_sweep<<<blocks_for(A.n, kBlock, 4096), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, dl1, w, wout);
+    k_testvec_sweep<<<AMG_GRID(blocks_for(A.n, kBlock, 4096)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, dl1, w, wout);
     return cudaGetLastError();
 }
 
 cudaError_t launch_edge_keys(const DevCSR& A, const double* kii, const double* w, uint64_t* key, cudaStream_t s) {
-    k_edge_keys<<<blocks_for(A.n, kWarpsPerBlock, 8192), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, kii, w, key);
+    k_edge_keys<<<AMG_GRID(blocks_for(A.n, kWarpsPerBlock, 8192)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, kii, w, key);
     return cudaGetLastError();
 }
 
 cudaError_t launch_match_init(int n, int32_t* state, cudaStream_t s) {
-    k_match_init<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, state);
+    k_match_init<<<AMG_GRID(blocks_for(n, kBlock, 4096)), kBlock, 0, s>>>(n, state);
     return cudaGetLastError();
 }
 
 cudaError_t launch_match_propose(const DevCSR& A, const uint64_t* key, const int32_t* state, int32_t* cand,
                                  cudaStream_t s) {
-    k_match_propose<<<blocks_for(A.n, kWarpsPerBlock, 8192), kBlock, 0, s>>>(A.n, A.rowptr, A.col, key, state, cand);
+    k_match_propose<<<AMG_GRID(blocks_for(A.n, kWarpsPerBlock, 8192)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, key, state, cand);
     return cudaGetLastError();
 }
 
 cudaError_t launch_match_commit(int n, const int32_t* cand, int32_t* state, int* active, cudaStream_t s) {
-    k_match_commit<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, cand, state, active);
+    k_match_commit<<<AMG_GRID(blocks_for(n, kBlock, 4096)), kBlock, 0, s>>>(n, cand, state, active);
     return cudaGetLastError();
 }
 
 cudaError_t launch_match_finish(int n, const int32_t* state, int32_t* mate, int32_t* leader, cudaStream_t s) {
-    k_match_finish<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, state, mate, leader);
+    k_match_finish<<<AMG_GRID(blocks_for(n, kBlock, 4096)), kBlock, 0, s>>>(n, state, mate, leader);
     return cudaGetLastError();
 }
 
 cudaError_t launch_aggregate(int n, const int32_t* mate, const int32_t* cidx, const double* w, int32_t* agg,
                              double* pval, int32_t* mem0, int32_t* mem1, double* wc, cudaStream_t s) {
-    k_aggregate<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, mate, cidx, w, agg, pval, mem0, mem1, wc);
+    k_aggregate<<<AMG_GRID(blocks_for(n, kBlock, 4096)), kBlock, 0, s>>>(n, mate, cidx, w, agg, pval, mem0, mem1, wc);
     return cudaGetLastError();
 }
 
@@ -780,7 +780,7 @@ cudaError_t launch_galerkin_count(const DevCSR& A, const int32_t* agg, const int
                                   int nc, int cap, int64_t* rowcnt, cudaStream_t s) {
     const size_t sm = galerkin_smem(cap);
     if (sm > 48 * 1024) AMG_TRY(cudaFuncSetAttribute(k_galerkin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_galerkin_count<<<blocks_for(nc, 1, 65536), kBlock, sm, s>>>(nc, A.rowptr, A.col, agg, mem0, mem1, cap, rowcnt);
+    k_galerkin_count<<<AMG_GRID(blocks_for(nc, 1, 65536)), kBlock, sm, s>>>(nc, A.rowptr, A.col, agg, mem0, mem1, cap, rowcnt);
     return cudaGetLastError();
 }
 
@@ -788,19 +788,19 @@ cudaError_t launch_galerkin_fill(const DevCSR& A, const int32_t* agg, const doub
                                  const int32_t* mem1, int cap, DevCSR& C, cudaStream_t s) {
     const size_t sm = galerkin_smem(cap);
     if (sm > 48 * 1024) AMG_TRY(cudaFuncSetAttribute(k_galerkin_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_galerkin_fill<<<blocks_for(C.n, 1, 65536), kBlock, sm, s>>>(C.n, A.rowptr, A.col, A.val, agg, pval, mem0, mem1,
+    k_galerkin_fill<<<AMG_GRID(blocks_for(C.n, 1, 65536)), kBlock, sm, s>>>(C.n, A.rowptr, A.col, A.val, agg, pval, mem0, mem1,
                                                                     cap, C.rowptr, C.col, C.val);
     return cudaGetLastError();
 }
 
 cudaError_t launch_galerkin_mirror(DevCSR& C, int* flag, cudaStream_t s) {
-    k_galerkin_mirror<<<blocks_for(C.n, kWarpsPerBlock, 8192), kBlock, 0, s>>>(C.n, C.rowptr, C.col, C.val, flag);
+    k_galerkin_mirror<<<AMG_GRID(blocks_for(C.n, kWarpsPerBlock, 8192)), kBlock, 0, s>>>(C.n, C.rowptr, C.col, C.val, flag);
     return cudaGetLastError();
 }
 
 cudaError_t launch_row_stats(const DevCSR& A, const int32_t* mem0, const int32_t* mem1, int nc, int* maxcand,
                              cudaStream_t s) {
-    k_row_stats<<<blocks_for(nc, kBlock, 4096), kBlock, 0, s>>>(nc, A.rowptr, mem0, mem1, maxcand);
+    k_row_stats<<<AMG_GRID(blocks_for(nc, kBlock, 4096)), kBlock, 0, s>>>(nc, A.rowptr, mem0, mem1, maxcand);
     return cudaGetLastError();
 }
 
@@ -810,34 +810,34 @@ cudaError_t launch_compose(int n, int npass, const Pass* passes, int32_t* agg, d
         pp.agg[q] = passes[q].agg;
         pp.pval[q] = passes[q].pval;
     }
-    k_compose<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, npass, pp, agg, pval);
+    k_compose<<<AMG_GRID(blocks_for(n, kBlock, 4096)), kBlock, 0, s>>>(n, npass, pp, agg, pval);
     return cudaGetLastError();
 }
 
 cudaError_t launch_member_count(int n, const int32_t* agg, int nc, int32_t* cnt, cudaStream_t s) {
     AMG_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nc + 1), s));
-    k_member_count<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, agg, cnt);
+    k_member_count<<<AMG_GRID(blocks_for(n, kBlock, 4096)), kBlock, 0, s>>>(n, agg, cnt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_member_fill(int n, const int32_t* agg, const int32_t* mem_ptr, int nc, int32_t* mem_idx,
                                int* cursor, cudaStream_t s) {
     AMG_TRY(cudaMemsetAsync(cursor, 0, sizeof(int) * nc, s));
-    k_member_fill<<<blocks_for(n, kBlock, 4096), kBlock, 0, s>>>(n, agg, mem_ptr, mem_idx, cursor);
-    k_member_sort<<<blocks_for(nc, kBlock, 4096), kBlock, 0, s>>>(nc, mem_ptr, mem_idx);
+    k_member_fill<<<AMG_GRID(blocks_for(n, kBlock, 4096)), kBlock, 0, s>>>(n, agg, mem_ptr, mem_idx, cursor);
+    k_member_sort<<<AMG_GRID(blocks_for(nc, kBlock, 4096)), kBlock, 0, s>>>(nc, mem_ptr, mem_idx);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dense_from_csr(const DevCSR& A, double* D, cudaStream_t s) {
-    k_dense_from_csr<<<blocks_for(A.n, 1, 4096), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, D);
+    k_dense_from_csr<<<AMG_GRID(blocks_for(A.n, 1, 4096)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, D);
     return cudaGetLastError();
 }
 
 // D (n x n, overwritten by its Cholesky factor); Ainv receives the inverse.
 // Ainv must have room for 2 n^2 doubles (second half is work space).
 cudaError_t launch_dense_spd_inverse(int n, double* D, double* Ainv, int* flag, cudaStream_t s) {
-    k_cholesky<<<1, 1024, 0, s>>>(n, D, flag);
-    k_chol_inverse<<<blocks_for(n, 1, 4096), kBlock, 0, s>>>(n, D, Ainv, Ainv + (int64_t)n * n);
+    k_cholesky<<<AMG_GRID(1), 1024, 0, s>>>(n, D, flag);
+    k_chol_inverse<<<AMG_GRID(blocks_for(n, 1, 4096)), kBlock, 0, s>>>(n, D, Ainv, Ainv + (int64_t)n * n);
     return cudaGetLastError();
 }
 

@@ -460,9 +460,16 @@ cudaError_t launch_spmv(const DevCSR& A, const double* x, double* y, cudaStream_
     const int rpw = rows_per_warp(A.n, sms);
     const int nb = row_blocks(A.n, rpw);
     if (A.n == 0) return cudaSuccess;
-    pick(rpw, [&] { k_spmv<1><<<nb, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, y); },
-         [&] { k_spmv<8><<<nb, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, y); });
+    pick(rpw, [&] { k_spmv<1><<<AMG_GRID(nb), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, y); },
+         [&] { k_spmv<8><<<AMG_GRID(nb), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, y); });
     return cudaGetLastError();
+}
+
+// Event-record node around a timed fine-level kernel (only while the
+// iteration graph is being captured with profiling on).
+static void prof_mark(amg_hierarchy* h, int k, int side, cudaStream_t s) {
+    if (h->prof && h->prof_slot >= 0)
+        cudaEventRecordWithFlags(h->prof_ev[h->prof_slot][k][side], s, cudaEventRecordExternal);
 }
 
 // Partial-sum slots inside h->partials (h->npart doubles each).
@@ -477,7 +484,7 @@ cudaError_t enqueue_vcycle(amg_hierarchy* h, cudaStream_t s) {
     const int flex = h->o.flexible;
     const SolveState* st = h->st;
     if (L == 1) {
-        k_coarse<<<row_blocks(h->ndense, 1), kBlock, 0, s>>>(h->ndense, h->Ainv, h->r, nullptr, nullptr, nullptr,
+        k_coarse<<<AMG_GRID(row_blocks(h->ndense, 1)), kBlock, 0, s>>>(h->ndense, h->Ainv, h->r, nullptr, nullptr, nullptr,
                                                              nullptr, h->z, h->q, slot(h, S_RZ), slot(h, S_ZQ), flex,
                                                              st);
         return cudaGetLastError();
@@ -499,24 +506,26 @@ cudaError_t enqueue_vcycle(amg_hierarchy* h, cudaStream_t s) {
             double* xo = xcur[l];
             double* xn = xalt[l];
             pick(rpw,
-                 [&] { k_sweep<1><<<nb, kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xo, F.invd, xn, st); },
-                 [&] { k_sweep<8><<<nb, kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xo, F.invd, xn, st); });
+                 [&] { k_sweep<1><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xo, F.invd, xn, st); },
+                 [&] { k_sweep<8><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xo, F.invd, xn, st); });
             xcur[l] = xn;
             xalt[l] = xo;
         }
         double* rb = xalt[l];  // free buffer of this level holds the residual
         const double* xc = xcur[l];
-        pick(rpw, [&] { k_resid<1><<<nb, kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xc, rb, st); },
-             [&] { k_resid<8><<<nb, kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xc, rb, st); });
+        if (l == 0) prof_mark(h, 1, 0, s);
+        pick(rpw, [&] { k_resid<1><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xc, rb, st); },
+             [&] { k_resid<8><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xc, rb, st); });
+        if (l == 0) prof_mark(h, 1, 1, s);
         const bool coarsest = (l + 1 == L - 1);
-        k_restrict<<<vec_blocks(C.A.n, sms), kBlock, 0, s>>>(C.A.n, F.mem_ptr, F.mem_idx, F.pval, rb, C.f,
+        k_restrict<<<AMG_GRID(vec_blocks(C.A.n, sms)), kBlock, 0, s>>>(C.A.n, F.mem_ptr, F.mem_idx, F.pval, rb, C.f,
                                                              coarsest ? nullptr : xcur[l + 1], C.invd, st);
     }
     // coarsest
     {
         Level& F = h->lev[L - 2];
         Level& C = h->lev[L - 1];
-        k_coarse<<<row_blocks(C.A.n, 1), kBlock, 0, s>>>(C.A.n, h->Ainv, C.f, F.mem_ptr, F.mem_idx, F.pval,
+        k_coarse<<<AMG_GRID(row_blocks(C.A.n, 1)), kBlock, 0, s>>>(C.A.n, h->Ainv, C.f, F.mem_ptr, F.mem_idx, F.pval,
                                                          xcur[L - 2], nullptr, nullptr, nullptr, nullptr, 0, st);
     }
     // up
@@ -529,32 +538,34 @@ cudaError_t enqueue_vcycle(amg_hierarchy* h, cudaStream_t s) {
             double* xo = xcur[l];
             double* xn = xalt[l];
             pick(rpw,
-                 [&] { k_sweep<1><<<nb, kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xo, F.invd, xn, st); },
-                 [&] { k_sweep<8><<<nb, kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xo, F.invd, xn, st); });
+                 [&] { k_sweep<1><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xo, F.invd, xn, st); },
+                 [&] { k_sweep<8><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xo, F.invd, xn, st); });
             xcur[l] = xn;
             xalt[l] = xo;
         }
         const double* xc = xcur[l];
         if (l == 0) {
+            prof_mark(h, 2, 0, s);
             pick(rpw,
                  [&] {
-                     k_up0<1><<<nb, kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, h->r, xc, F.invd, h->z, h->q,
+                     k_up0<1><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, h->r, xc, F.invd, h->z, h->q,
                                                     slot(h, S_RZ), slot(h, S_ZQ), flex, st);
                  },
                  [&] {
-                     k_up0<8><<<nb, kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, h->r, xc, F.invd, h->z, h->q,
+                     k_up0<8><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, h->r, xc, F.invd, h->z, h->q,
                                                     slot(h, S_RZ), slot(h, S_ZQ), flex, st);
                  });
+            prof_mark(h, 2, 1, s);
         } else {
             Level& G = h->lev[l - 1];
             double* xf = xcur[l - 1];
             pick(rpw,
                  [&] {
-                     k_up<1><<<nb, kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, F.f, xc, F.invd, G.mem_ptr,
+                     k_up<1><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, F.f, xc, F.invd, G.mem_ptr,
                                                    G.mem_idx, G.pval, xf, st);
                  },
                  [&] {
-                     k_up<8><<<nb, kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, F.f, xc, F.invd, G.mem_ptr,
+                     k_up<8><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, F.f, xc, F.invd, G.mem_ptr,
                                                    G.mem_idx, G.pval, xf, st);
                  });
         }
@@ -580,11 +591,11 @@ static cudaError_t launch_residual(amg_hierarchy* h, double* r, double* x0, cuda
     const int rpw = rows_per_warp(n, h->num_sms), nb = row_blocks(n, rpw);
     pick(rpw,
          [&] {
-             k_residual0<1><<<nb, kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->x, h->F, L0.invd, r, x0,
+             k_residual0<1><<<AMG_GRID(nb), kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->x, h->F, L0.invd, r, x0,
                                                   slot(h, S_RR), slot(h, S_FF));
          },
          [&] {
-             k_residual0<8><<<nb, kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->x, h->F, L0.invd, r, x0,
+             k_residual0<8><<<AMG_GRID(nb), kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->x, h->F, L0.invd, r, x0,
                                                   slot(h, S_RR), slot(h, S_FF));
          });
     return cudaGetLastError();
@@ -594,11 +605,11 @@ static cudaError_t launch_residual(amg_hierarchy* h, double* r, double* x0, cuda
 cudaError_t enqueue_pcg_start(amg_hierarchy* h, cudaStream_t s) {
     const int n = h->lev[0].A.n;
     AMG_TRY(launch_residual(h, h->r, h->nlev > 1 ? h->lev[0].x : nullptr, s));
-    k_scal_init<<<1, 1024, 0, s>>>(slot(h, S_RR), slot(h, S_FF), nb0(h), h->rtol, h->itmax, h->hist, h->st);
+    k_scal_init<<<AMG_GRID(1), 1024, 0, s>>>(slot(h, S_RR), slot(h, S_FF), nb0(h), h->rtol, h->itmax, h->hist, h->st);
     AMG_TRY(cudaGetLastError());
     AMG_TRY(enqueue_vcycle(h, s));
-    k_scal_beta<<<1, 1024, 0, s>>>(slot(h, S_RZ), slot(h, S_ZQ), nbz(h), h->o.flexible, 1, h->st);
-    k_pupdate<<<nbv(h), kBlock, 0, s>>>(n, h->p, h->z, 1, h->st);
+    k_scal_beta<<<AMG_GRID(1), 1024, 0, s>>>(slot(h, S_RZ), slot(h, S_ZQ), nbz(h), h->o.flexible, 1, h->st);
+    k_pupdate<<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(n, h->p, h->z, 1, h->st);
     return cudaGetLastError();
 }
 
@@ -607,31 +618,33 @@ cudaError_t enqueue_pcg_iteration(amg_hierarchy* h, cudaStream_t s) {
     const int n = L0.A.n;
     const int flex = h->o.flexible;
     const int rpw = rows_per_warp(n, h->num_sms), nb = row_blocks(n, rpw);
+    prof_mark(h, 0, 0, s);
     pick(rpw,
          [&] {
-             k_spmv_pq<1><<<nb, kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->p, h->r, h->q, slot(h, S_PQ),
+             k_spmv_pq<1><<<AMG_GRID(nb), kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->p, h->r, h->q, slot(h, S_PQ),
                                                 slot(h, S_PR), flex, h->st);
          },
          [&] {
-             k_spmv_pq<8><<<nb, kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->p, h->r, h->q, slot(h, S_PQ),
+             k_spmv_pq<8><<<AMG_GRID(nb), kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->p, h->r, h->q, slot(h, S_PQ),
                                                 slot(h, S_PR), flex, h->st);
          });
-    k_scal_alpha<<<1, 1024, 0, s>>>(slot(h, S_PQ), slot(h, S_PR), nb, flex, h->st);
-    k_update<<<nbv(h), kBlock, 0, s>>>(n, h->x, h->r, h->p, h->q, L0.invd, h->nlev > 1 ? L0.x : nullptr,
+    prof_mark(h, 0, 1, s);
+    k_scal_alpha<<<AMG_GRID(1), 1024, 0, s>>>(slot(h, S_PQ), slot(h, S_PR), nb, flex, h->st);
+    k_update<<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(n, h->x, h->r, h->p, h->q, L0.invd, h->nlev > 1 ? L0.x : nullptr,
                                        slot(h, S_RR), h->st);
-    k_scal_conv<<<1, 1024, 0, s>>>(slot(h, S_RR), nbv(h), h->hist, h->hist_cap, h->st);
+    k_scal_conv<<<AMG_GRID(1), 1024, 0, s>>>(slot(h, S_RR), nbv(h), h->hist, h->hist_cap, h->st);
     AMG_TRY(cudaGetLastError());
     AMG_TRY(enqueue_vcycle(h, s));
-    k_scal_beta<<<1, 1024, 0, s>>>(slot(h, S_RZ), slot(h, S_ZQ), nbz(h), flex, 0, h->st);
-    k_pupdate<<<nbv(h), kBlock, 0, s>>>(n, h->p, h->z, 0, h->st);
+    k_scal_beta<<<AMG_GRID(1), 1024, 0, s>>>(slot(h, S_RZ), slot(h, S_ZQ), nbz(h), flex, 0, h->st);
+    k_pupdate<<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(n, h->p, h->z, 0, h->st);
     return cudaGetLastError();
 }
 
 // ||F - K x|| and ||F|| into slot(S_OUT)[0..1] (FP64, recomputed).
 cudaError_t launch_final_residual(amg_hierarchy* h, cudaStream_t s) {
     AMG_TRY(launch_residual(h, h->q, nullptr, s));
-    k_sqrt_sum<<<1, 1024, 0, s>>>(slot(h, S_RR), nb0(h), slot(h, S_OUT));
-    k_sqrt_sum<<<1, 1024, 0, s>>>(slot(h, S_FF), nb0(h), slot(h, S_OUT) + 1);
+    k_sqrt_sum<<<AMG_GRID(1), 1024, 0, s>>>(slot(h, S_RR), nb0(h), slot(h, S_OUT));
+    k_sqrt_sum<<<AMG_GRID(1), 1024, 0, s>>>(slot(h, S_FF), nb0(h), slot(h, S_OUT) + 1);
     return cudaGetLastError();
 }
 
@@ -640,7 +653,7 @@ double* final_residual_slot(amg_hierarchy* h) { return slot(h, S_OUT); }
 // z = B r for r already in h->r (state must not be "done").
 cudaError_t enqueue_vcycle_standalone(amg_hierarchy* h, cudaStream_t s) {
     if (h->nlev > 1)
-        k_scale<<<nbv(h), kBlock, 0, s>>>(h->lev[0].A.n, h->r, h->lev[0].invd, h->lev[0].x);
+        k_scale<<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(h->lev[0].A.n, h->r, h->lev[0].invd, h->lev[0].x);
     AMG_TRY(cudaGetLastError());
     return enqueue_vcycle(h, s);
 }

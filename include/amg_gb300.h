@@ -175,6 +175,28 @@ int amg_profile_kernels(amg_hierarchy* h, int32_t enable);
  * written once).  Any pointer may be NULL. */
 int amg_kernel_times(const amg_hierarchy* h, double* ms, int64_t* count, double* bytes);
 
+/* Largest system amg_relres_noalloc accepts (rows). */
+#define AMG_NOALLOC_MAX_ROWS (1 << 19)
+
+/* ||F - K u||_2 / ||F||_2 for a device-resident CSR matrix K (K->mem must be
+ * AMG_MEM_DEVICE) and device vectors F[n], u[n]; the result is written to
+ * the host double *relres (0 when F = 0).  The work is enqueued on
+ * cuda_stream (NULL = default stream) and the call returns after it.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- e.g. an application whose own pool
+ * allocator reserved the GPU's memory up front and forbids allocations
+ * outside it, or a time-critical loop where a cudaMalloc (and the device
+ * synchronisation it may cause) is not acceptable.  It allocates nothing:
+ * its reduction scratch is a fixed static device array of about 1 MB that
+ * every GPU which loads the library keeps until the process exits.
+ * The first call on a device looks up that array's device address (with the
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU
+ * (e.g. on different streams) race; serialise them.
+ * Errors: AMG_ERR_ARG for NULL pointers, host-resident K, n < 1 or
+ * n > AMG_NOALLOC_MAX_ROWS; AMG_ERR_CUDA on a CUDA failure. */
+int amg_relres_noalloc(const amg_csr* K, const double* F, const double* u, double* relres, void* cuda_stream);
+
 /* Release the hierarchy and its device memory. */
 int amg_free(amg_hierarchy* h);
 

@@ -79,6 +79,8 @@ _SIGS = {
     "amg_export_pass": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 4),
     "amg_free": (ctypes.c_int, [ctypes.c_void_p]),
     "amg_kernel_launches": (ctypes.c_int64, []),
+    "amg_relres_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
     "amg_profile_kernels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "amg_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "amg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -248,6 +250,16 @@ def amg_kernel_times(h):
     b = np.zeros(3)
     _check(lib().amg_kernel_times(h, ms.ctypes.data, cnt.ctypes.data, b.ctypes.data), "amg_kernel_times")
     return ms, cnt, b
+
+
+def amg_relres_noalloc(rowptr, col, val, F, u, stream=None) -> float:
+    """||F - K u|| / ||F|| for device tensors, through the entry point that
+    allocates no device memory (see include/amg_gb300.h)."""
+    csr = AmgCsr(len(rowptr) - 1, len(val), rowptr.data_ptr(), col.data_ptr(), val.data_ptr(), AMG_MEM_DEVICE)
+    out = ctypes.c_double()
+    _check(lib().amg_relres_noalloc(ctypes.byref(csr), F.data_ptr(), u.data_ptr(), ctypes.byref(out),
+                                    _stream_handle(stream)), "amg_relres_noalloc")
+    return out.value
 
 
 def amg_free(h):

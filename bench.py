@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
 
 
@@ -341,6 +342,60 @@ def run_ours(args):
             e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(prob.n * 8),
                    "steps": e2e_steps, "host_buffers": "pinned"}
 
+        # mixed precision on the same workload (FP32 V-cycle with BF16 finest values,
+        # FP32 outer SpMV, FP64 flexible-CG recurrences and true-residual replacement)
+        mixed = None
+        if not args.no_mixed:
+            mopts = A.amg_opts_default(precision=A.AMG_FP32_BF16FINE)
+            ref_u = torch.zeros_like(F)
+            h = A.amg_setup(rp, ci, va, opts, stream)
+            A.amg_pcg_solve(h, F, ref_u, args.rtol, 10000)
+            A.amg_free(h)
+
+            def mstep(profile=False):
+                h = A.amg_setup(rp, ci, va, mopts, stream)
+                if profile:
+                    A.amg_profile_kernels(h, True)
+                u = torch.zeros_like(F)
+                st, it, rr = A.amg_pcg_solve(h, F, u, args.rtol, 10000)
+                info = A.amg_get_info(h)
+                kt = A.amg_kernel_times(h) if profile else None
+                A.amg_free(h)
+                if st != A.AMG_OK:
+                    raise RuntimeError(f"mixed solve failed: {A.amg_strerror(st)}")
+                return u, it, rr, info, kt
+
+            for _ in range(args.warmup):
+                mstep()
+            torch.cuda.synchronize()
+            barrier(dist)
+            m0 = torch.cuda.Event(enable_timing=True)
+            m1 = torch.cuda.Event(enable_timing=True)
+            m0.record(stream)
+            mms = np.zeros(3)
+            mcnt = np.zeros(3, np.int64)
+            for _ in range(args.steps):
+                mu, mit, mrr, minfo, mkt = mstep(profile=True)
+                mms += mkt[0]
+                mcnt += mkt[1]
+            m1.record(stream)
+            torch.cuda.synchronize()
+            m_ms = max_over_ranks(dist, m0.elapsed_time(m1)) / args.steps
+            err = float(torch.linalg.norm(mu - ref_u) / torch.linalg.norm(ref_u))
+            mavg = mms / np.maximum(mcnt, 1)
+            mk = {name: {"bytes_per_launch": mkt[2][q], "avg_ms": mavg[q], "launches": int(mcnt[q]),
+                         "achieved_gbs": mkt[2][q] / (mavg[q] * 1e-3) / 1e9 if mavg[q] > 0 else None}
+                  for q, name in enumerate(["k_spmv_pq<8,f32> (q = K p)", "k_resid<8,bf16> (down-sweep residual)",
+                                            "k_up0<8,bf16> (up-sweep smoothing)"])}
+            mdom = max(mk, key=lambda k: mk[k]["avg_ms"] * mk[k]["launches"])
+            mixed = {"time_to_solution_s": m_ms / 1e3, "speedup_vs_fp64": ms_per_step / m_ms, "iters": mit,
+                     "final_relres_fp64": mrr, "rel_error_vs_fp64_solution": err, "setup_ms": minfo.setup_ms,
+                     "solve_ms": minfo.solve_ms, "precision": "fp32 V-cycle, bf16 finest values, fp32 outer SpMV, "
+                     "fp64 FCG(1) recurrences, fp64 true-residual replacement every 20 iterations",
+                     "iter_gbps": minfo.iter_bytes * mit / (minfo.solve_ms * 1e-3) / 1e9,
+                     "roofline": {"bound": "hbm", "kernel": mdom, "achieved": mk[mdom]["achieved_gbs"],
+                                  "unit": "GB/s", "all": mk}}
+
     peak, peak_kind = measured_peaks()
     avg_ms = ms_sum / np.maximum(cnt_sum, 1)
     per_kernel = {}
@@ -371,7 +426,10 @@ def run_ours(args):
             "iter_gbps": info.iter_bytes * it / (info.solve_ms * 1e-3) / 1e9 if info.solve_ms > 0 else None,
             "vcycle_ms": vcycle_ms, "vcycle_gbps": vinfo.vcycle_bytes / (vcycle_ms * 1e-3) / 1e9,
             "throughput_systems_per_s": world * args.steps / (elapsed_ms * 1e-3),
-            "roofline": roof, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches)}
+            "roofline": roof, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches), "mixed": mixed}
+    if mixed is not None:
+        mixed["roofline"]["peak"] = peak
+        mixed["roofline"]["frac"] = (mixed["roofline"]["achieved"] or 0.0) / peak
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, it, args.rtol)
     if rank == 0:

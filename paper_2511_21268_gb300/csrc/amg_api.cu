@@ -317,10 +317,25 @@ int build(amg_hierarchy* h, const amg_csr* K) {
     for (int l = 0; l < h->nlev; l++) {
         Level& F = h->lev[l];
         const int n = F.A.n;
-        if (l > 0) RC(dalloc(h, &F.f, n));
-        RC(dalloc(h, &F.x, n));
-        RC(dalloc(h, &F.t, n));
+        if (h->mixed) {  // FP32 copies of the level (BF16 finest values in the V-cycle if asked)
+            RC(dalloc(h, &F.val32, (size_t)F.A.nnz));
+            CK(launch_to_f32(F.A.val, F.val32, F.A.nnz, s));
+            if (l == 0 && h->o.precision == AMG_FP32_BF16FINE && h->nlev > 1) {
+                RC(dalloc(h, &F.val16, (size_t)F.A.nnz));
+                CK(launch_to_bf16(F.A.val, F.val16, F.A.nnz, s));
+            }
+            RC(dalloc(h, &F.invd32, n));
+            CK(launch_to_f32(F.invd, F.invd32, n, s));
+            if (l > 0) RC(dalloc(h, &F.f32, n));
+            RC(dalloc(h, &F.x32, n));
+            RC(dalloc(h, &F.t32, n));
+        } else {
+            if (l > 0) RC(dalloc(h, &F.f, n));
+            RC(dalloc(h, &F.x, n));
+            RC(dalloc(h, &F.t, n));
+        }
     }
+    if (h->mixed) RC(dalloc(h, &h->p32, n0));
     RC(dalloc(h, &h->x, n0));
     RC(dalloc(h, &h->r, n0));
     RC(dalloc(h, &h->p, n0));
@@ -328,7 +343,7 @@ int build(amg_hierarchy* h, const amg_csr* K) {
     RC(dalloc(h, &h->z, n0));
     RC(dalloc(h, &h->F, n0));
     h->npart = (int)partial_slot_size(n0, h->num_sms);
-    RC(dalloc(h, &h->partials, (size_t)7 * h->npart));
+    RC(dalloc(h, &h->partials, partial_slot_count() * h->npart));
     RC(dalloc(h, &h->st, 1));
     h->hist_cap = kHistCap;
     RC(dalloc(h, &h->hist, kHistCap));
@@ -349,19 +364,31 @@ void fill_info(amg_hierarchy* h) {
         I.match_rounds[l] = rounds;
     }
     I.opc = tot / (double)h->lev[0].A.nnz;
-    // algorithmic bytes: one matrix pass = nnz (8 + 4) + (n + 1) 8 + x read + y write
-    auto pass_bytes = [](const DevCSR& A) { return (double)A.nnz * 12.0 + (A.n + 1.0) * 8.0 + 2.0 * A.n * 8.0; };
+    // algorithmic bytes: one matrix pass = nnz (value + 4) + (n + 1) 8 + x read + y write
+    // (value and vector sizes of the V-cycle precision: 8 / 8 in FP64, 4 / 4 in
+    // mixed precision with 2-byte values on the finest level when BF16)
+    const double vb = h->mixed ? 4.0 : 8.0;
+    auto pass_bytes = [&](const DevCSR& A, double valb) {
+        return (double)A.nnz * (valb + 4.0) + (A.n + 1.0) * 8.0 + 2.0 * A.n * vb;
+    };
     if (h->nlev == 1) {
         vbytes = (double)h->ndense * h->ndense * 8.0 + 2.0 * h->ndense * 8.0;
     } else {
         for (int l = 0; l < h->nlev - 1; l++) {
             const DevCSR& A = h->lev[l].A;
-            vbytes += 2.0 * pass_bytes(A) + 6.0 * A.n * 8.0;
+            const double valb = (l == 0 && h->lev[0].val16) ? 2.0 : vb;
+            vbytes += 2.0 * pass_bytes(A, valb) + 6.0 * A.n * vb;
         }
         vbytes += (double)h->ndense * h->ndense * 8.0 + 2.0 * h->ndense * 8.0;
     }
     I.vcycle_bytes = vbytes;
-    I.iter_bytes = vbytes + pass_bytes(h->lev[0].A) + 10.0 * h->lev[0].A.n * 8.0;
+    const DevCSR& A0 = h->lev[0].A;
+    // outer q = K p (FP32 values in mixed mode) + CG vectors; mixed mode adds an
+    // FP64 residual replacement every resid_replace_every iterations
+    double outer = (double)A0.nnz * (vb + 4.0) + (A0.n + 1.0) * 8.0 + 2.0 * A0.n * 8.0;
+    if (h->mixed && h->o.resid_replace_every > 0)
+        outer += ((double)A0.nnz * 12.0 + (A0.n + 1.0) * 8.0 + 3.0 * A0.n * 8.0) / h->o.resid_replace_every;
+    I.iter_bytes = vbytes + outer + 10.0 * A0.n * 8.0;
 }
 
 void destroy(amg_hierarchy* h) {
@@ -399,8 +426,8 @@ int check_opts(const amg_opts& o) {
     if (o.dense_max < 1 || o.dense_max > 8192) return AMG_ERR_ARG;
     if (o.testvec_sweeps < 0 || o.testvec_kind < 0 || o.testvec_kind > 1) return AMG_ERR_ARG;
     if (!(o.stag > 0.0) || o.max_match_rounds < 1) return AMG_ERR_ARG;
-    if (o.precision != AMG_FP64) return AMG_ERR_ARG;  // mixed precision: see amg_opts.precision
-    if (o.flexible < 0 || o.flexible > 1) return AMG_ERR_ARG;
+    if (o.precision < AMG_FP64 || o.precision > AMG_FP32_BF16FINE) return AMG_ERR_ARG;
+    if (o.flexible < 0 || o.flexible > 1 || o.resid_replace_every < 0) return AMG_ERR_ARG;
     return AMG_OK;
 }
 
@@ -424,7 +451,7 @@ int amg_opts_default(amg_opts* o) {
     o->max_match_rounds = 1000;
     o->precision = AMG_FP64;
     o->flexible = 0;
-    o->resid_replace_every = 0;
+    o->resid_replace_every = 20;
     return AMG_OK;
 }
 
@@ -444,6 +471,10 @@ int amg_setup(const amg_csr* K, const amg_opts* opts, void* cuda_stream, amg_hie
         return rc;
     }
     memset(&h->info, 0, sizeof(h->info));
+    // the FP32/BF16 V-cycle is symmetric only up to rounding: mixed precision
+    // always runs the flexible CG variant
+    h->mixed = h->o.precision != AMG_FP64;
+    if (h->mixed) h->o.flexible = 1;
     h->us = (cudaStream_t)cuda_stream;
     // A caller-provided stream is used directly (so caller events bracket the
     // kernels); the legacy default stream cannot be captured into a graph,
@@ -678,9 +709,20 @@ int amg_profile_kernels(amg_hierarchy* h, int32_t enable) {
 int amg_kernel_times(const amg_hierarchy* h, double* ms, int64_t* count, double* bytes) {
     if (!h) return AMG_ERR_ARG;
     const double n = h->lev[0].A.n, nnz = (double)h->lev[0].A.nnz;
-    const double base = nnz * 12.0 + (n + 1.0) * 8.0;
     const double flex = h->o.flexible ? 8.0 * n : 0.0;
-    const double b[3] = {base + 16.0 * n + flex, base + 24.0 * n, base + 32.0 * n + flex};
+    double b[3];
+    if (h->mixed) {  // FP32 outer values, FP32 (or BF16) V-cycle values, FP32 V-cycle vectors
+        const double vcv = h->lev[0].val16 ? 2.0 : 4.0;
+        const double rows = (n + 1.0) * 8.0;
+        b[0] = nnz * 8.0 + rows + 4.0 * n + 8.0 * n + 8.0 * n + flex;  // p32 gather, q, p
+        b[1] = nnz * (vcv + 4.0) + rows + 8.0 * n + 4.0 * n + 4.0 * n;  // r, x, rbuf
+        b[2] = nnz * (vcv + 4.0) + rows + 8.0 * n + 4.0 * n + 4.0 * n + 8.0 * n + flex;  // r, x, invd, z
+    } else {
+        const double base = nnz * 12.0 + (n + 1.0) * 8.0;
+        b[0] = base + 16.0 * n + flex;
+        b[1] = base + 24.0 * n;
+        b[2] = base + 32.0 * n + flex;
+    }
     for (int q = 0; q < 3; q++) {
         if (ms) ms[q] = h->prof_ms[q];
         if (count) count[q] = h->prof_cnt[q];

@@ -2,6 +2,7 @@
 // library: hierarchy layout, launch wrappers and small device helpers.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,7 +33,9 @@ struct SolveState {
     double pq;     // p^T K p
     double nr;     // ||r|| of the last iteration
     int itmax;
-    int pad2;
+    int replace_now;  // mixed precision: recompute r = F - K x in FP64 this iteration
+    int repl_every;   // mixed precision: replacement period (0 = only at convergence)
+    int pad3;
 };
 
 // One matching pass on a matrix with n rows -> nc coarse rows.
@@ -66,10 +69,18 @@ struct Level {
     double* pval = nullptr;      // composite prolongator value
     int32_t* mem_ptr = nullptr;  // [nc+1] members of each next-level row
     int32_t* mem_idx = nullptr;  // [n] fine rows, ascending within a row
-    // V-cycle vectors
+    // V-cycle vectors (FP64 mode)
     double* f = nullptr;
     double* x = nullptr;
-    double* t = nullptr;  // ping-pong buffer for extra smoothing sweeps
+    double* t = nullptr;  // residual / ping-pong buffer
+    // mixed precision: FP32 values (BF16 values of the finest level in the
+    // V-cycle when requested), FP32 1/dl1 and FP32 V-cycle vectors
+    float* val32 = nullptr;
+    __nv_bfloat16* val16 = nullptr;
+    float* invd32 = nullptr;
+    float* f32 = nullptr;
+    float* x32 = nullptr;
+    float* t32 = nullptr;
     int maxrow = 0;
 };
 
@@ -84,6 +95,8 @@ struct amg_hierarchy {
     double* Ainv = nullptr;  // dense inverse of the coarsest matrix (row-major)
     // CG workspace (level 0)
     double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *F = nullptr;
+    float* p32 = nullptr;  // FP32 copy of p for the mixed-precision outer SpMV
+    int mixed = 0;         // precision != AMG_FP64
     double* partials = nullptr;  // 7 slots of npart doubles
     int npart = 0;
     double rtol = 0.0;
@@ -149,6 +162,8 @@ cudaError_t launch_member_fill(int n, const int32_t* agg, const int32_t* mem_ptr
                                int* cursor, cudaStream_t s);
 cudaError_t launch_dense_from_csr(const DevCSR& A, double* D, cudaStream_t s);
 cudaError_t launch_dense_spd_inverse(int n, double* D, double* Ainv, int* flag, cudaStream_t s);
+cudaError_t launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
+cudaError_t launch_to_bf16(const double* in, __nv_bfloat16* out, int64_t n, cudaStream_t s);
 
 // solve_kernels.cu
 cudaError_t launch_spmv(const DevCSR& A, const double* x, double* y, cudaStream_t s);
@@ -162,6 +177,7 @@ int rows_per_warp(int n, int num_sms);
 int row_blocks(int n, int rpw);
 int vec_blocks(int n, int num_sms);
 size_t partial_slot_size(int n0, int num_sms);
+size_t partial_slot_count();
 
 // ----------------------------------------------------------------- device helpers
 #ifdef __CUDACC__

@@ -697,9 +697,31 @@ __global__ void k_chol_inverse(int n, const double* __restrict__ L, double* Ainv
     }
 }
 
+// Precision copies for the mixed-precision solve (round to nearest even;
+// BF16 through FP32).
+__global__ void k_to_f32(const double* __restrict__ in, float* out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __double2float_rn(in[i]);
+}
+
+__global__ void k_to_bf16(const double* __restrict__ in, __nv_bfloat16* out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16_rn(__double2float_rn(in[i]));
+}
+
 }  // namespace
 
 // ============================================================== launch wrappers
+cudaError_t launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t s) {
+    k_to_f32<<<AMG_GRID(blocks_for(n, kBlock, 8192)), kBlock, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16(const double* in, __nv_bfloat16* out, int64_t n, cudaStream_t s) {
+    k_to_bf16<<<AMG_GRID(blocks_for(n, kBlock, 8192)), kBlock, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_validate_csr(const DevCSR& A, int* flag, cudaStream_t s) {
     if (A.n == 0) return cudaSuccess;
     k_validate<<<AMG_GRID(blocks_for(A.n, kWarpsPerBlock, 8192)), kBlock, 0, s>>>(A.n, A.nnz, A.rowptr, A.col, A.val, flag);

@@ -12,6 +12,15 @@
 // per clock, this keeps the FP64 work per row close to nnz/32 warp
 // instructions and runs each row's epilogue on RPW rows per instruction.
 //
+// Precision: every kernel is templated on the accumulation type A, the
+// stored value type V and the vector types.  FP64 mode instantiates them
+// with double everywhere.  Mixed mode runs the V-cycle in FP32 (values FP32,
+// or BF16 on the finest level; FP32 vectors and 1/dl1), the outer SpMV with
+// FP32 values and FP32 accumulation, and keeps FP64 for the CG vectors and
+// recurrences, the dot products, the coarsest solve and a true-residual
+// replacement r = F - K x with the FP64 matrix (periodic, and before any
+// convergence is declared).
+//
 // Fusions:
 //   * pre-smoothing from x = 0 is x = D^-1 f, written by whoever produces f
 //     (the CG update for level 0, the restriction for level l+1);
@@ -20,13 +29,16 @@
 //   * up sweep of level l: y = x + (f - K x) / d, prolongated at once into
 //     the finer level, x_{l-1}[c] += p_c y_a for the members c of a; on
 //     level 0 it writes z and the partial sums of r.z (and z.q);
-//   * coarsest solve: dense GEMV with the precomputed inverse, followed by
-//     the same prolongation.
+//   * coarsest solve: dense FP64 GEMV with the precomputed inverse, followed
+//     by the same prolongation.
 // Reductions are deterministic: fixed grids, fixed lane/warp/block order and
 // a single-block final sum.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "amg_internal.cuh"
 
@@ -36,34 +48,38 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-// Lane partial of row i: sum over k = b + lane + 32 t of v_k x_{c_k}.
-__device__ __forceinline__ double lane_partial(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                               const double* __restrict__ v, const double* __restrict__ x, int i,
-                                               int lane) {
+__device__ __forceinline__ double ldv(const double* v, int64_t k) { return __ldg(v + k); }
+__device__ __forceinline__ float ldv(const float* v, int64_t k) { return __ldg(v + k); }
+__device__ __forceinline__ float ldv(const __nv_bfloat16* v, int64_t k) { return __bfloat162float(v[k]); }
+
+// Lane partial of row i: sum over k = b + lane + 32 t of v_k x_{c_k}, in A.
+template <typename A, typename V, typename X>
+__device__ __forceinline__ A lane_partial(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                          const V* __restrict__ v, const X* __restrict__ x, int i, int lane) {
     const int64_t b = rp[i], e = rp[i + 1];
-    double acc = 0.0;
+    A acc = A(0);
     int64_t k = b + lane;
     for (; k + 96 < e; k += 128) {
-        const double v0 = __ldg(v + k), v1 = __ldg(v + k + 32), v2 = __ldg(v + k + 64), v3 = __ldg(v + k + 96);
+        const A v0 = (A)ldv(v, k), v1 = (A)ldv(v, k + 32), v2 = (A)ldv(v, k + 64), v3 = (A)ldv(v, k + 96);
         const int c0 = __ldg(ci + k), c1 = __ldg(ci + k + 32), c2 = __ldg(ci + k + 64), c3 = __ldg(ci + k + 96);
-        const double x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+        const A x0 = (A)x[c0], x1 = (A)x[c1], x2 = (A)x[c2], x3 = (A)x[c3];
         acc = fma(v0, x0, acc);
         acc = fma(v1, x1, acc);
         acc = fma(v2, x2, acc);
         acc = fma(v3, x3, acc);
     }
-    for (; k < e; k += 32) acc = fma(__ldg(v + k), x[__ldg(ci + k)], acc);
+    for (; k < e; k += 32) acc = fma((A)ldv(v, k), (A)x[__ldg(ci + k)], acc);
     return acc;
 }
 
 // Row totals for the RPW rows row0 .. row0+RPW-1 (rows >= n give 0).
 // Returns the total of row `row0 + lane / (32/RPW)` on every lane.
-template <int RPW>
-__device__ __forceinline__ double group_rows(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                             const double* __restrict__ v, const double* __restrict__ x, int row0,
-                                             int n, int lane, double (*tile)[33]) {
+template <int RPW, typename A, typename V, typename X>
+__device__ __forceinline__ A group_rows(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                        const V* __restrict__ v, const X* __restrict__ x, int row0, int n, int lane,
+                                        A (*tile)[33]) {
     if constexpr (RPW == 1) {
-        double s = row0 < n ? lane_partial(rp, ci, v, x, row0, lane) : 0.0;
+        A s = row0 < n ? lane_partial<A>(rp, ci, v, x, row0, lane) : A(0);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
         return s;
@@ -72,11 +88,11 @@ __device__ __forceinline__ double group_rows(const int64_t* __restrict__ rp, con
 #pragma unroll 1
         for (int r = 0; r < RPW; r++) {
             const int i = row0 + r;
-            tile[r][lane] = i < n ? lane_partial(rp, ci, v, x, i, lane) : 0.0;
+            tile[r][lane] = i < n ? lane_partial<A>(rp, ci, v, x, i, lane) : A(0);
         }
         __syncwarp();
         const int r = lane / LPR, q = lane % LPR;
-        double s = 0.0;
+        A s = A(0);
 #pragma unroll
         for (int t = 0; t < RPW; t++) s += tile[r][q * RPW + t];
 #pragma unroll
@@ -86,7 +102,7 @@ __device__ __forceinline__ double group_rows(const int64_t* __restrict__ rp, con
     }
 }
 
-// Deterministic sum of one value per owner lane over the block -> out.
+// Deterministic sum of one value per lane over the block -> *out (thread 0).
 __device__ __forceinline__ void block_partial(double tv, double* sh, double* out) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tv += __shfl_xor_sync(FULL, tv, o);
@@ -101,7 +117,9 @@ __device__ __forceinline__ void block_partial(double tv, double* sh, double* out
     }
 }
 
-// Deterministic single-block sum of nb partials (all threads get it).
+// Deterministic single-block sum of nb partials (result on every thread).
+// The warp totals are combined by thread 0 only: GB300's FP64 rate makes
+// redundant per-thread FP64 adds costly.
 __device__ double sum_partials(const double* __restrict__ part, int nb, double* sh) {
     double s = 0.0;
     for (int t = threadIdx.x; t < nb; t += blockDim.x) s += part[t];
@@ -111,8 +129,13 @@ __device__ double sum_partials(const double* __restrict__ part, int nb, double* 
     __syncthreads();
     if (lane == 0) sh[wid] = s;
     __syncthreads();
-    double tot = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += sh[w];
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += sh[w];
+        sh[32] = tot;
+    }
+    __syncthreads();
+    const double tot = sh[32];
     __syncthreads();
     return tot;
 }
@@ -123,8 +146,8 @@ __device__ double sum_partials(const double* __restrict__ part, int nb, double* 
     } while (0)
 
 // Common prologue of the row-group kernels.
-#define ROWGROUP_PROLOGUE                                              \
-    __shared__ double tiles[kWarpsPerBlock][RPW][33];                  \
+#define ROWGROUP_PROLOGUE(A)                                           \
+    __shared__ A tiles[kWarpsPerBlock][RPW][33];                       \
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;         \
     const int row0 = (blockIdx.x * kWarpsPerBlock + wid) * RPW;        \
     constexpr int LPR = 32 / RPW;                                      \
@@ -137,113 +160,119 @@ template <int RPW>
 __global__ void __launch_bounds__(kBlock) k_spmv(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                                   const double* __restrict__ v, const double* __restrict__ x,
                                                   double* y) {
-    ROWGROUP_PROLOGUE
+    ROWGROUP_PROLOGUE(double)
     const double s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
     if (owner) y[myrow] = s;
 }
 
-// r = F - K x, x0 = r / d (optional), partials ||r||^2 and ||F||^2.
-template <int RPW>
+// FP64: r = F - K x, x0 = r / d (optional, in X0), partials ||r||^2, ||F||^2.
+// `gate` (optional): run only while the solve is not done and a
+// residual replacement is due.
+template <int RPW, typename X0>
 __global__ void __launch_bounds__(kBlock) k_residual0(int n, const int64_t* __restrict__ rp,
                                                        const int32_t* __restrict__ ci, const double* __restrict__ v,
                                                        const double* __restrict__ x, const double* __restrict__ F,
-                                                       const double* __restrict__ invd, double* r, double* x0,
-                                                       double* part_rr, double* part_ff) {
-    ROWGROUP_PROLOGUE
+                                                       const X0* __restrict__ invd, double* r, X0* x0,
+                                                       double* part_rr, double* part_ff, const SolveState* gate) {
+    if (gate && (gate->done || !gate->replace_now)) return;
+    ROWGROUP_PROLOGUE(double)
     __shared__ double sh[kWarpsPerBlock];
     const double s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
     double rr = 0.0, ff = 0.0;
     if (owner) {
         const double fi = F[myrow], ri = fi - s;
         r[myrow] = ri;
-        if (x0) x0[myrow] = ri * invd[myrow];
+        if (x0) x0[myrow] = (X0)ri * invd[myrow];
         rr = ri * ri;
         ff = fi * fi;
     }
     block_partial(rr, sh, part_rr + blockIdx.x);
-    block_partial(ff, sh, part_ff + blockIdx.x);
+    if (part_ff) block_partial(ff, sh, part_ff + blockIdx.x);
 }
 
-// q = K p, partials p.q and (flexible) p.r.
-template <int RPW>
+// Outer SpMV q = K p (values V, gathered vector PX, accumulation A; q FP64),
+// partials p.q and (flexible) p.r with the FP64 p.
+template <int RPW, typename A, typename V, typename PX>
 __global__ void __launch_bounds__(kBlock) k_spmv_pq(int n, const int64_t* __restrict__ rp,
-                                                     const int32_t* __restrict__ ci, const double* __restrict__ v,
-                                                     const double* __restrict__ p, const double* __restrict__ r,
-                                                     double* q, double* part_pq, double* part_pr, int flexible,
-                                                     const SolveState* st) {
+                                                     const int32_t* __restrict__ ci, const V* __restrict__ v,
+                                                     const PX* __restrict__ pg, const double* __restrict__ p,
+                                                     const double* __restrict__ r, double* q, double* part_pq,
+                                                     double* part_pr, int flexible, const SolveState* st) {
     DONE_GUARD(st);
-    ROWGROUP_PROLOGUE
+    ROWGROUP_PROLOGUE(A)
     __shared__ double sh[kWarpsPerBlock];
-    const double s = group_rows<RPW>(rp, ci, v, p, row0, n, lane, tiles[wid]);
+    const A s = group_rows<RPW>(rp, ci, v, pg, row0, n, lane, tiles[wid]);
     double pq = 0.0, pr = 0.0;
     if (owner) {
-        q[myrow] = s;
+        const double qs = (double)s;
+        q[myrow] = qs;
         const double pi = p[myrow];
-        pq = pi * s;
+        pq = pi * qs;
         if (flexible) pr = pi * r[myrow];
     }
     block_partial(pq, sh, part_pq + blockIdx.x);
     if (flexible) block_partial(pr, sh, part_pr + blockIdx.x);
 }
 
-// rbuf = f - K x (down sweep residual of one level).
-template <int RPW>
+// rbuf = f - K x (down-sweep residual of one level).
+template <int RPW, typename A, typename V, typename FT, typename XT>
 __global__ void __launch_bounds__(kBlock) k_resid(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                   const double* __restrict__ v, const double* __restrict__ f,
-                                                   const double* __restrict__ x, double* rbuf, const SolveState* st) {
+                                                   const V* __restrict__ v, const FT* __restrict__ f,
+                                                   const XT* __restrict__ x, A* rbuf, const SolveState* st) {
     DONE_GUARD(st);
-    ROWGROUP_PROLOGUE
-    const double s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
-    if (owner) rbuf[myrow] = f[myrow] - s;
+    ROWGROUP_PROLOGUE(A)
+    const A s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
+    if (owner) rbuf[myrow] = (A)f[myrow] - s;
 }
 
 // t = x + (f - K x) / d (extra smoothing sweep).
-template <int RPW>
+template <int RPW, typename A, typename V, typename FT>
 __global__ void __launch_bounds__(kBlock) k_sweep(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                   const double* __restrict__ v, const double* __restrict__ f,
-                                                   const double* __restrict__ x, const double* __restrict__ invd,
-                                                   double* t, const SolveState* st) {
+                                                   const V* __restrict__ v, const FT* __restrict__ f,
+                                                   const A* __restrict__ x, const A* __restrict__ invd, A* t,
+                                                   const SolveState* st) {
     DONE_GUARD(st);
-    ROWGROUP_PROLOGUE
-    const double s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
-    if (owner) t[myrow] = fma(invd[myrow], f[myrow] - s, x[myrow]);
+    ROWGROUP_PROLOGUE(A)
+    const A s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
+    if (owner) t[myrow] = fma(invd[myrow], (A)f[myrow] - s, x[myrow]);
 }
 
 // Up sweep of level l >= 1: y_a = x_a + (f_a - (K x)_a) / d_a, then
 // x_{l-1}[c] += p_c y_a for the members c of a.
-template <int RPW>
+template <int RPW, typename A, typename V>
 __global__ void __launch_bounds__(kBlock) k_up(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                const double* __restrict__ v, const double* __restrict__ f,
-                                                const double* __restrict__ x, const double* __restrict__ invd,
+                                                const V* __restrict__ v, const A* __restrict__ f,
+                                                const A* __restrict__ x, const A* __restrict__ invd,
                                                 const int32_t* __restrict__ mptr, const int32_t* __restrict__ midx,
-                                                const double* __restrict__ pvalf, double* xf, const SolveState* st) {
+                                                const double* __restrict__ pvalf, A* xf, const SolveState* st) {
     DONE_GUARD(st);
-    ROWGROUP_PROLOGUE
-    const double s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
+    ROWGROUP_PROLOGUE(A)
+    const A s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
     if (owner) {
-        const double y = fma(invd[myrow], f[myrow] - s, x[myrow]);
+        const A y = fma(invd[myrow], f[myrow] - s, x[myrow]);
         for (int m = mptr[myrow]; m < mptr[myrow + 1]; m++) {
             const int c = midx[m];
-            xf[c] = fma(pvalf[c], y, xf[c]);
+            xf[c] = fma((A)pvalf[c], y, xf[c]);
         }
     }
 }
 
-// Up sweep of level 0: z = x + (r - K x) / d; partials r.z and (flexible) z.q.
-template <int RPW>
+// Up sweep of level 0: z = x + (r - K x) / d (z FP64); partials r.z and
+// (flexible) z.q.
+template <int RPW, typename A, typename V>
 __global__ void __launch_bounds__(kBlock) k_up0(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                 const double* __restrict__ v, const double* __restrict__ r,
-                                                 const double* __restrict__ x, const double* __restrict__ invd,
-                                                 double* z, const double* __restrict__ q, double* part_rz,
-                                                 double* part_zq, int flexible, const SolveState* st) {
+                                                 const V* __restrict__ v, const double* __restrict__ r,
+                                                 const A* __restrict__ x, const A* __restrict__ invd, double* z,
+                                                 const double* __restrict__ q, double* part_rz, double* part_zq,
+                                                 int flexible, const SolveState* st) {
     DONE_GUARD(st);
-    ROWGROUP_PROLOGUE
+    ROWGROUP_PROLOGUE(A)
     __shared__ double sh[kWarpsPerBlock];
-    const double s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
+    const A s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
     double rz = 0.0, zq = 0.0;
     if (owner) {
         const double ra = r[myrow];
-        const double za = fma(invd[myrow], ra - s, x[myrow]);
+        const double za = (double)fma(invd[myrow], (A)ra - s, x[myrow]);
         z[myrow] = za;
         rz = ra * za;
         if (flexible) zq = za * q[myrow];
@@ -253,27 +282,29 @@ __global__ void __launch_bounds__(kBlock) k_up0(int n, const int64_t* __restrict
 }
 
 // Restriction f_c[I] = sum_{a in I, ascending} p_a r_a, x_c = f_c / d_c.
+template <typename A>
 __global__ void k_restrict(int nc, const int32_t* __restrict__ mptr, const int32_t* __restrict__ midx,
-                           const double* __restrict__ pval, const double* __restrict__ rbuf, double* fc, double* xc,
-                           const double* __restrict__ invdc, const SolveState* st) {
+                           const double* __restrict__ pval, const A* __restrict__ rbuf, A* fc, A* xc,
+                           const A* __restrict__ invdc, const SolveState* st) {
     DONE_GUARD(st);
     for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
-        double acc = 0.0;
+        A acc = A(0);
         for (int m = mptr[I]; m < mptr[I + 1]; m++) {
             const int a = midx[m];
-            acc = fma(pval[a], rbuf[a], acc);
+            acc = fma((A)pval[a], rbuf[a], acc);
         }
         fc[I] = acc;
         if (xc) xc[I] = acc * invdc[I];
     }
 }
 
-// Coarsest level: e = A^-1 f with the dense symmetric inverse (row-major),
-// then prolongation into the finer level, or (single-level hierarchy) z = e
-// with the partial r.z (and z.q).
-__global__ void __launch_bounds__(kBlock) k_coarse(int n, const double* __restrict__ Ainv, const double* __restrict__ f,
+// Coarsest level: e = A^-1 f with the dense FP64 symmetric inverse
+// (row-major), then prolongation into the finer level, or (single-level
+// hierarchy) z = e with the partial r.z (and z.q).
+template <typename FT, typename XT>
+__global__ void __launch_bounds__(kBlock) k_coarse(int n, const double* __restrict__ Ainv, const FT* __restrict__ f,
                                                     const int32_t* __restrict__ mptr, const int32_t* __restrict__ midx,
-                                                    const double* __restrict__ pvalf, double* xf, double* z,
+                                                    const double* __restrict__ pvalf, XT* xf, double* z,
                                                     const double* __restrict__ q, double* part_rz, double* part_zq,
                                                     int flexible, const SolveState* st) {
     DONE_GUARD(st);
@@ -284,19 +315,19 @@ __global__ void __launch_bounds__(kBlock) k_coarse(int n, const double* __restri
     if (I < n) {
         const double* row = Ainv + (int64_t)I * n;
         double s = 0.0;
-        for (int j = lane; j < n; j += 32) s = fma(row[j], f[j], s);
+        for (int j = lane; j < n; j += 32) s = fma(row[j], (double)f[j], s);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
         if (z) {
             if (lane == 0) {
                 z[I] = s;
-                rz = f[I] * s;
+                rz = (double)f[I] * s;
                 if (flexible) zq = s * q[I];
             }
         } else if (lane == 0) {
             for (int m = mptr[I]; m < mptr[I + 1]; m++) {
                 const int c = midx[m];
-                xf[c] = fma(pvalf[c], s, xf[c]);
+                xf[c] = (XT)fma(pvalf[c], s, (double)xf[c]);
             }
         }
     }
@@ -308,9 +339,9 @@ __global__ void __launch_bounds__(kBlock) k_coarse(int n, const double* __restri
 
 // ------------------------------------------------------------ CG scalars
 __global__ void k_scal_init(const double* part_rr, const double* part_ff, int nb, double rtol, int itmax,
-                            double* hist, SolveState* st) {
+                            int repl_every, double* hist, SolveState* st) {
     // every field a later kernel reads is (re)set here
-    __shared__ double sh[32];
+    __shared__ double sh[33];
     const double rr = sum_partials(part_rr, nb, sh);
     const double ff = sum_partials(part_ff, nb, sh);
     if (threadIdx.x == 0) {
@@ -320,6 +351,8 @@ __global__ void k_scal_init(const double* part_rr, const double* part_ff, int nb
         st->nr = nr;
         st->iters = 0;
         st->itmax = itmax;
+        st->replace_now = 0;
+        st->repl_every = repl_every;
         st->status = AMG_OK;
         st->done = 0;
         if (hist) hist[0] = nF > 0.0 ? nr / nF : 0.0;
@@ -337,7 +370,7 @@ __global__ void k_scal_init(const double* part_rr, const double* part_ff, int nb
 
 __global__ void k_scal_alpha(const double* part_pq, const double* part_pr, int nb, int flexible, SolveState* st) {
     DONE_GUARD(st);
-    __shared__ double sh[32];
+    __shared__ double sh[33];
     const double pq = sum_partials(part_pq, nb, sh);
     const double num = flexible ? sum_partials(part_pr, nb, sh) : st->rho;
     if (threadIdx.x == 0) {
@@ -351,15 +384,43 @@ __global__ void k_scal_alpha(const double* part_pq, const double* part_pr, int n
     }
 }
 
-__global__ void k_scal_conv(const double* part_rr, int nb, double* hist, int hist_cap, SolveState* st) {
+// Convergence test on the recursive residual.  mixed = 1: convergence is
+// only declared on an FP64 true residual, so a replacement is requested
+// instead (also every repl_every iterations).
+__global__ void k_scal_conv(const double* part_rr, int nb, double* hist, int hist_cap, int mixed, SolveState* st) {
     DONE_GUARD(st);
-    __shared__ double sh[32];
+    __shared__ double sh[33];
     const double rr = sum_partials(part_rr, nb, sh);
     if (threadIdx.x == 0) {
         const double nr = sqrt(rr);
         const int it = st->iters + 1;
         st->iters = it;
         st->nr = nr;
+        if (hist && it < hist_cap) hist[it] = nr / st->nF;
+        if (isnan(nr) || isinf(nr)) {
+            st->status = AMG_ERR_NAN;
+            st->done = 1;
+        } else if (mixed && (nr <= st->tol || it >= st->itmax || (st->repl_every > 0 && it % st->repl_every == 0))) {
+            st->replace_now = 1;
+        } else if (nr <= st->tol) {
+            st->done = 1;
+        } else if (it >= st->itmax) {
+            st->status = AMG_ERR_NOT_CONVERGED;
+            st->done = 1;
+        }
+    }
+}
+
+// After a residual replacement: test the FP64 true residual.
+__global__ void k_scal_replaced(const double* part_rr, int nb, double* hist, int hist_cap, SolveState* st) {
+    if (st->done || !st->replace_now) return;
+    __shared__ double sh[33];
+    const double rr = sum_partials(part_rr, nb, sh);
+    if (threadIdx.x == 0) {
+        const double nr = sqrt(rr);
+        const int it = st->iters;
+        st->nr = nr;
+        st->replace_now = 0;
         if (hist && it < hist_cap) hist[it] = nr / st->nF;
         if (isnan(nr) || isinf(nr)) {
             st->status = AMG_ERR_NAN;
@@ -377,7 +438,7 @@ __global__ void k_scal_conv(const double* part_rr, int nb, double* hist, int his
 __global__ void k_scal_beta(const double* part_rz, const double* part_zq, int nb, int flexible, int first,
                             SolveState* st) {
     DONE_GUARD(st);
-    __shared__ double sh[32];
+    __shared__ double sh[33];
     const double rz = sum_partials(part_rz, nb, sh);
     const double zq = (flexible && !first) ? sum_partials(part_zq, nb, sh) : 0.0;
     if (threadIdx.x == 0) {
@@ -392,9 +453,10 @@ __global__ void k_scal_beta(const double* part_rz, const double* part_zq, int nb
     }
 }
 
-// x += alpha p, r -= alpha q, x0 = r / d, partial ||r||^2.
+// x += alpha p, r -= alpha q, x0 = r / d (in X0), partial ||r||^2.
+template <typename X0>
 __global__ void k_update(int n, double* x, double* r, const double* __restrict__ p, const double* __restrict__ q,
-                         const double* __restrict__ invd, double* x0, double* part_rr, const SolveState* st) {
+                         const X0* __restrict__ invd, X0* x0, double* part_rr, const SolveState* st) {
     DONE_GUARD(st);
     __shared__ double sh[kWarpsPerBlock];
     const double alpha = st->alpha;
@@ -403,35 +465,39 @@ __global__ void k_update(int n, double* x, double* r, const double* __restrict__
         x[i] = fma(alpha, p[i], x[i]);
         const double ri = fma(-alpha, q[i], r[i]);
         r[i] = ri;
-        if (x0) x0[i] = ri * invd[i];
+        if (x0) x0[i] = (X0)ri * invd[i];
         rr = fma(ri, ri, rr);
     }
     block_partial(rr, sh, part_rr + blockIdx.x);
 }
 
-// p = z + beta p (first direction: p = z).
-__global__ void k_pupdate(int n, double* p, const double* __restrict__ z, int first, const SolveState* st) {
+// p = z + beta p (first direction: p = z); p32 = FP32 copy (mixed).
+__global__ void k_pupdate(int n, double* p, const double* __restrict__ z, float* p32, int first, const SolveState* st) {
     DONE_GUARD(st);
     const double beta = st->beta;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        p[i] = first ? z[i] : fma(beta, p[i], z[i]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double pi = first ? z[i] : fma(beta, p[i], z[i]);
+        p[i] = pi;
+        if (p32) p32[i] = __double2float_rn(pi);
+    }
 }
 
-__global__ void k_scale(int n, const double* __restrict__ a, const double* __restrict__ b, double* out) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = a[i] * b[i];
+template <typename X0>
+__global__ void k_scale(int n, const double* __restrict__ a, const X0* __restrict__ b, X0* out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = (X0)a[i] * b[i];
 }
 
 __global__ void k_sqrt_sum(const double* part, int nb, double* out) {
-    __shared__ double sh[32];
+    __shared__ double sh[33];
     const double s = sum_partials(part, nb, sh);
     if (threadIdx.x == 0) *out = sqrt(s);
 }
 
 // ----------------------------------------------------------------- dispatch
-template <typename K1, typename K8>
-inline void pick(int rpw, K1 k1, K8 k8) {
-    if (rpw == 8) k8();
-    else k1();
+template <typename F>
+inline void with_rpw(int rpw, F&& f) {
+    if (rpw == 8) f(std::integral_constant<int, 8>{});
+    else f(std::integral_constant<int, 1>{});
 }
 
 }  // namespace
@@ -441,7 +507,9 @@ int rows_per_warp(int n, int num_sms) {
     return ((int64_t)n >= (int64_t)num_sms * kWarpsPerBlock * 8 * 4) ? 8 : 1;
 }
 
-int row_blocks(int n, int rpw) { return (int)(((int64_t)n + (int64_t)rpw * kWarpsPerBlock - 1) / ((int64_t)rpw * kWarpsPerBlock)); }
+int row_blocks(int n, int rpw) {
+    return (int)(((int64_t)n + (int64_t)rpw * kWarpsPerBlock - 1) / ((int64_t)rpw * kWarpsPerBlock));
+}
 
 int vec_blocks(int n, int num_sms) {
     int64_t b = ((int64_t)n + kBlock - 1) / kBlock;
@@ -451,8 +519,6 @@ int vec_blocks(int n, int num_sms) {
     return (int)b;
 }
 
-int grid_for_rows(int, int n, int num_sms) { return row_blocks(n, rows_per_warp(n, num_sms)); }
-
 cudaError_t launch_spmv(const DevCSR& A, const double* x, double* y, cudaStream_t s) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -460,8 +526,9 @@ cudaError_t launch_spmv(const DevCSR& A, const double* x, double* y, cudaStream_
     const int rpw = rows_per_warp(A.n, sms);
     const int nb = row_blocks(A.n, rpw);
     if (A.n == 0) return cudaSuccess;
-    pick(rpw, [&] { k_spmv<1><<<AMG_GRID(nb), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, y); },
-         [&] { k_spmv<8><<<AMG_GRID(nb), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, y); });
+    with_rpw(rpw, [&](auto R) {
+        k_spmv<decltype(R)::value><<<AMG_GRID(nb), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, y);
+    });
     return cudaGetLastError();
 }
 
@@ -474,26 +541,59 @@ static void prof_mark(amg_hierarchy* h, int k, int side, cudaStream_t s) {
 
 // Partial-sum slots inside h->partials (h->npart doubles each).
 static double* slot(amg_hierarchy* h, int k) { return h->partials + (int64_t)k * h->npart; }
-enum { S_RR = 0, S_FF, S_PQ, S_PR, S_RZ, S_ZQ, S_OUT };
+enum { S_RR = 0, S_FF, S_PQ, S_PR, S_RZ, S_ZQ, S_OUT, S_RR2, S_COUNT };
 
-// V-cycle on r (= f_0); the pre-smoothed level-0 iterate is already in lev[0].x.
-// Writes z and the partial sums of r.z (and z.q).
-cudaError_t enqueue_vcycle(amg_hierarchy* h, cudaStream_t s) {
+// ---------------------------------------------------------- per-mode views
+// Vectors and values of a level in the V-cycle precision A.
+template <typename A>
+struct View;
+
+template <>
+struct View<double> {
+    static double* f(Level& L) { return L.f; }
+    static double* x(Level& L) { return L.x; }
+    static double* t(Level& L) { return L.t; }
+    static const double* invd(Level& L) { return L.invd; }
+    template <typename Fn>
+    static void vals(Level& L, int, Fn&& fn) { fn(static_cast<const double*>(L.A.val)); }
+};
+
+template <>
+struct View<float> {
+    static float* f(Level& L) { return L.f32; }
+    static float* x(Level& L) { return L.x32; }
+    static float* t(Level& L) { return L.t32; }
+    static const float* invd(Level& L) { return L.invd32; }
+    template <typename Fn>
+    static void vals(Level& L, int l, Fn&& fn) {
+        if (l == 0 && L.val16) fn(static_cast<const __nv_bfloat16*>(L.val16));
+        else fn(static_cast<const float*>(L.val32));
+    }
+};
+
+template <typename T>
+using vtype = std::remove_cv_t<std::remove_pointer_t<T>>;
+
+// V-cycle on r (= f_0); the pre-smoothed level-0 iterate is already in x_0.
+// Writes z (FP64) and the partial sums of r.z (and z.q).
+template <typename A>
+static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
+    using Vw = View<A>;
     const int L = h->nlev;
     const int sms = h->num_sms;
     const int flex = h->o.flexible;
     const SolveState* st = h->st;
     if (L == 1) {
-        k_coarse<<<AMG_GRID(row_blocks(h->ndense, 1)), kBlock, 0, s>>>(h->ndense, h->Ainv, h->r, nullptr, nullptr, nullptr,
-                                                             nullptr, h->z, h->q, slot(h, S_RZ), slot(h, S_ZQ), flex,
-                                                             st);
+        k_coarse<double, A><<<AMG_GRID(row_blocks(h->ndense, 1)), kBlock, 0, s>>>(
+            h->ndense, h->Ainv, h->r, nullptr, nullptr, nullptr, nullptr, h->z, h->q, slot(h, S_RZ), slot(h, S_ZQ),
+            flex, st);
         return cudaGetLastError();
     }
-    double* xcur[AMG_MAX_LEVELS];
-    double* xalt[AMG_MAX_LEVELS];
+    A* xcur[AMG_MAX_LEVELS];
+    A* xalt[AMG_MAX_LEVELS];
     for (int l = 0; l < L; l++) {
-        xcur[l] = h->lev[l].x;
-        xalt[l] = h->lev[l].t;
+        xcur[l] = Vw::x(h->lev[l]);
+        xalt[l] = Vw::t(h->lev[l]);
     }
     // down
     for (int l = 0; l < L - 1; l++) {
@@ -501,76 +601,90 @@ cudaError_t enqueue_vcycle(amg_hierarchy* h, cudaStream_t s) {
         Level& C = h->lev[l + 1];
         const int n = F.A.n;
         const int rpw = rows_per_warp(n, sms), nb = row_blocks(n, rpw);
-        const double* f = (l == 0) ? h->r : F.f;
-        for (int sw = 1; sw < h->o.nu_pre; sw++) {
-            double* xo = xcur[l];
-            double* xn = xalt[l];
-            pick(rpw,
-                 [&] { k_sweep<1><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xo, F.invd, xn, st); },
-                 [&] { k_sweep<8><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xo, F.invd, xn, st); });
-            xcur[l] = xn;
-            xalt[l] = xo;
-        }
-        double* rb = xalt[l];  // free buffer of this level holds the residual
-        const double* xc = xcur[l];
-        if (l == 0) prof_mark(h, 1, 0, s);
-        pick(rpw, [&] { k_resid<1><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xc, rb, st); },
-             [&] { k_resid<8><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xc, rb, st); });
-        if (l == 0) prof_mark(h, 1, 1, s);
+        Vw::vals(F, l, [&](auto vp) {
+            using V = vtype<decltype(vp)>;
+            auto sweep_and_resid = [&](auto fp) {
+                using FT = vtype<decltype(fp)>;
+                for (int sw = 1; sw < h->o.nu_pre; sw++) {
+                    A* xo = xcur[l];
+                    A* xn = xalt[l];
+                    with_rpw(rpw, [&](auto R) {
+                        k_sweep<decltype(R)::value, A, V, FT><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                            n, F.A.rowptr, F.A.col, vp, fp, xo, Vw::invd(F), xn, st);
+                    });
+                    xcur[l] = xn;
+                    xalt[l] = xo;
+                }
+                A* rb = xalt[l];  // free buffer of this level holds the residual
+                const A* xc = xcur[l];
+                if (l == 0) prof_mark(h, 1, 0, s);
+                with_rpw(rpw, [&](auto R) {
+                    k_resid<decltype(R)::value, A, V, FT, A><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                        n, F.A.rowptr, F.A.col, vp, fp, xc, rb, st);
+                });
+                if (l == 0) prof_mark(h, 1, 1, s);
+            };
+            if (l == 0) sweep_and_resid(static_cast<const double*>(h->r));
+            else sweep_and_resid(static_cast<const A*>(Vw::f(F)));
+        });
         const bool coarsest = (l + 1 == L - 1);
-        k_restrict<<<AMG_GRID(vec_blocks(C.A.n, sms)), kBlock, 0, s>>>(C.A.n, F.mem_ptr, F.mem_idx, F.pval, rb, C.f,
-                                                             coarsest ? nullptr : xcur[l + 1], C.invd, st);
+        k_restrict<A><<<AMG_GRID(vec_blocks(C.A.n, sms)), kBlock, 0, s>>>(
+            C.A.n, F.mem_ptr, F.mem_idx, F.pval, xalt[l], Vw::f(C), coarsest ? nullptr : xcur[l + 1], Vw::invd(C), st);
     }
     // coarsest
     {
         Level& F = h->lev[L - 2];
         Level& C = h->lev[L - 1];
-        k_coarse<<<AMG_GRID(row_blocks(C.A.n, 1)), kBlock, 0, s>>>(C.A.n, h->Ainv, C.f, F.mem_ptr, F.mem_idx, F.pval,
-                                                         xcur[L - 2], nullptr, nullptr, nullptr, nullptr, 0, st);
+        k_coarse<A, A><<<AMG_GRID(row_blocks(C.A.n, 1)), kBlock, 0, s>>>(
+            C.A.n, h->Ainv, Vw::f(C), F.mem_ptr, F.mem_idx, F.pval, xcur[L - 2], nullptr, nullptr, nullptr, nullptr, 0,
+            st);
     }
     // up
     for (int l = L - 2; l >= 0; l--) {
         Level& F = h->lev[l];
         const int n = F.A.n;
         const int rpw = rows_per_warp(n, sms), nb = row_blocks(n, rpw);
-        const double* f = (l == 0) ? h->r : F.f;
-        for (int sw = 1; sw < h->o.nu_post; sw++) {
-            double* xo = xcur[l];
-            double* xn = xalt[l];
-            pick(rpw,
-                 [&] { k_sweep<1><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xo, F.invd, xn, st); },
-                 [&] { k_sweep<8><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, f, xo, F.invd, xn, st); });
-            xcur[l] = xn;
-            xalt[l] = xo;
-        }
-        const double* xc = xcur[l];
-        if (l == 0) {
-            prof_mark(h, 2, 0, s);
-            pick(rpw,
-                 [&] {
-                     k_up0<1><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, h->r, xc, F.invd, h->z, h->q,
-                                                    slot(h, S_RZ), slot(h, S_ZQ), flex, st);
-                 },
-                 [&] {
-                     k_up0<8><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, h->r, xc, F.invd, h->z, h->q,
-                                                    slot(h, S_RZ), slot(h, S_ZQ), flex, st);
-                 });
-            prof_mark(h, 2, 1, s);
-        } else {
-            Level& G = h->lev[l - 1];
-            double* xf = xcur[l - 1];
-            pick(rpw,
-                 [&] {
-                     k_up<1><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, F.f, xc, F.invd, G.mem_ptr,
-                                                   G.mem_idx, G.pval, xf, st);
-                 },
-                 [&] {
-                     k_up<8><<<AMG_GRID(nb), kBlock, 0, s>>>(n, F.A.rowptr, F.A.col, F.A.val, F.f, xc, F.invd, G.mem_ptr,
-                                                   G.mem_idx, G.pval, xf, st);
-                 });
-        }
+        Vw::vals(F, l, [&](auto vp) {
+            using V = vtype<decltype(vp)>;
+            auto sweeps = [&](auto fp) {
+                using FT = vtype<decltype(fp)>;
+                for (int sw = 1; sw < h->o.nu_post; sw++) {
+                    A* xo = xcur[l];
+                    A* xn = xalt[l];
+                    with_rpw(rpw, [&](auto R) {
+                        k_sweep<decltype(R)::value, A, V, FT><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                            n, F.A.rowptr, F.A.col, vp, fp, xo, Vw::invd(F), xn, st);
+                    });
+                    xcur[l] = xn;
+                    xalt[l] = xo;
+                }
+            };
+            if (l == 0) sweeps(static_cast<const double*>(h->r));
+            else sweeps(static_cast<const A*>(Vw::f(F)));
+            const A* xc = xcur[l];
+            if (l == 0) {
+                prof_mark(h, 2, 0, s);
+                with_rpw(rpw, [&](auto R) {
+                    k_up0<decltype(R)::value, A, V><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                        n, F.A.rowptr, F.A.col, vp, h->r, xc, Vw::invd(F), h->z, h->q, slot(h, S_RZ), slot(h, S_ZQ),
+                        flex, st);
+                });
+                prof_mark(h, 2, 1, s);
+            } else {
+                Level& G = h->lev[l - 1];
+                A* xf = xcur[l - 1];
+                with_rpw(rpw, [&](auto R) {
+                    k_up<decltype(R)::value, A, V><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                        n, F.A.rowptr, F.A.col, vp, Vw::f(F), xc, Vw::invd(F), G.mem_ptr, G.mem_idx, G.pval, xf, st);
+                });
+            }
+        });
     }
     return cudaGetLastError();
+}
+
+cudaError_t enqueue_vcycle(amg_hierarchy* h, cudaStream_t s) {
+    return h->mixed ? vcycle_impl<float>(h, s) : vcycle_impl<double>(h, s);
 }
 
 // blocks of the level-0 row kernels, of the vector kernels, and of the
@@ -585,31 +699,45 @@ size_t partial_slot_size(int n0, int num_sms) {
     return (size_t)((a > b ? a : b) + 2);
 }
 
-static cudaError_t launch_residual(amg_hierarchy* h, double* r, double* x0, cudaStream_t s) {
+size_t partial_slot_count() { return S_COUNT; }
+
+// FP64 residual r = F - K x (K the FP64 finest matrix) with x0 = r / d for
+// the V-cycle in its precision; partials into rr_slot (and ||F||^2 if ff).
+static cudaError_t launch_residual(amg_hierarchy* h, double* r, bool want_x0, int rr_slot, bool ff,
+                                   const SolveState* gate, cudaStream_t s) {
     Level& L0 = h->lev[0];
     const int n = L0.A.n;
     const int rpw = rows_per_warp(n, h->num_sms), nb = row_blocks(n, rpw);
-    pick(rpw,
-         [&] {
-             k_residual0<1><<<AMG_GRID(nb), kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->x, h->F, L0.invd, r, x0,
-                                                  slot(h, S_RR), slot(h, S_FF));
-         },
-         [&] {
-             k_residual0<8><<<AMG_GRID(nb), kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->x, h->F, L0.invd, r, x0,
-                                                  slot(h, S_RR), slot(h, S_FF));
-         });
+    const bool x0 = want_x0 && h->nlev > 1;
+    double* pff = ff ? slot(h, S_FF) : nullptr;
+    with_rpw(rpw, [&](auto R) {
+        constexpr int RPW = decltype(R)::value;
+        if (h->mixed)
+            k_residual0<RPW, float><<<AMG_GRID(nb), kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->x, h->F,
+                                                                    L0.invd32, r, x0 ? L0.x32 : nullptr,
+                                                                    slot(h, rr_slot), pff, gate);
+        else
+            k_residual0<RPW, double><<<AMG_GRID(nb), kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->x, h->F,
+                                                                     L0.invd, r, x0 ? L0.x : nullptr,
+                                                                     slot(h, rr_slot), pff, gate);
+    });
     return cudaGetLastError();
+}
+
+static void launch_pupdate(amg_hierarchy* h, int first, cudaStream_t s) {
+    k_pupdate<<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(h->lev[0].A.n, h->p, h->z, h->mixed ? h->p32 : nullptr, first,
+                                                  h->st);
 }
 
 // r = F - K x, ||F||, ||r||, first V-cycle, p = z, rho = r.z.
 cudaError_t enqueue_pcg_start(amg_hierarchy* h, cudaStream_t s) {
-    const int n = h->lev[0].A.n;
-    AMG_TRY(launch_residual(h, h->r, h->nlev > 1 ? h->lev[0].x : nullptr, s));
-    k_scal_init<<<AMG_GRID(1), 1024, 0, s>>>(slot(h, S_RR), slot(h, S_FF), nb0(h), h->rtol, h->itmax, h->hist, h->st);
+    AMG_TRY(launch_residual(h, h->r, true, S_RR, true, nullptr, s));
+    k_scal_init<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RR), slot(h, S_FF), nb0(h), h->rtol, h->itmax,
+                                            h->mixed ? h->o.resid_replace_every : 0, h->hist, h->st);
     AMG_TRY(cudaGetLastError());
     AMG_TRY(enqueue_vcycle(h, s));
-    k_scal_beta<<<AMG_GRID(1), 1024, 0, s>>>(slot(h, S_RZ), slot(h, S_ZQ), nbz(h), h->o.flexible, 1, h->st);
-    k_pupdate<<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(n, h->p, h->z, 1, h->st);
+    k_scal_beta<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RZ), slot(h, S_ZQ), nbz(h), h->o.flexible, 1, h->st);
+    launch_pupdate(h, 1, s);
     return cudaGetLastError();
 }
 
@@ -619,32 +747,41 @@ cudaError_t enqueue_pcg_iteration(amg_hierarchy* h, cudaStream_t s) {
     const int flex = h->o.flexible;
     const int rpw = rows_per_warp(n, h->num_sms), nb = row_blocks(n, rpw);
     prof_mark(h, 0, 0, s);
-    pick(rpw,
-         [&] {
-             k_spmv_pq<1><<<AMG_GRID(nb), kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->p, h->r, h->q, slot(h, S_PQ),
-                                                slot(h, S_PR), flex, h->st);
-         },
-         [&] {
-             k_spmv_pq<8><<<AMG_GRID(nb), kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->p, h->r, h->q, slot(h, S_PQ),
-                                                slot(h, S_PR), flex, h->st);
-         });
+    with_rpw(rpw, [&](auto R) {
+        constexpr int RPW = decltype(R)::value;
+        if (h->mixed)
+            k_spmv_pq<RPW, float, float, float><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                n, L0.A.rowptr, L0.A.col, L0.val32, h->p32, h->p, h->r, h->q, slot(h, S_PQ), slot(h, S_PR), flex, h->st);
+        else
+            k_spmv_pq<RPW, double, double, double><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                n, L0.A.rowptr, L0.A.col, L0.A.val, h->p, h->p, h->r, h->q, slot(h, S_PQ), slot(h, S_PR), flex, h->st);
+    });
     prof_mark(h, 0, 1, s);
-    k_scal_alpha<<<AMG_GRID(1), 1024, 0, s>>>(slot(h, S_PQ), slot(h, S_PR), nb, flex, h->st);
-    k_update<<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(n, h->x, h->r, h->p, h->q, L0.invd, h->nlev > 1 ? L0.x : nullptr,
-                                       slot(h, S_RR), h->st);
-    k_scal_conv<<<AMG_GRID(1), 1024, 0, s>>>(slot(h, S_RR), nbv(h), h->hist, h->hist_cap, h->st);
+    k_scal_alpha<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_PQ), slot(h, S_PR), nb, flex, h->st);
+    const bool x0 = h->nlev > 1;
+    if (h->mixed)
+        k_update<float><<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(n, h->x, h->r, h->p, h->q, L0.invd32, x0 ? L0.x32 : nullptr,
+                                                            slot(h, S_RR), h->st);
+    else
+        k_update<double><<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(n, h->x, h->r, h->p, h->q, L0.invd, x0 ? L0.x : nullptr,
+                                                             slot(h, S_RR), h->st);
+    k_scal_conv<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RR), nbv(h), h->hist, h->hist_cap, h->mixed, h->st);
+    if (h->mixed) {  // FP64 true-residual replacement, when due
+        AMG_TRY(launch_residual(h, h->r, true, S_RR2, false, h->st, s));
+        k_scal_replaced<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RR2), nb0(h), h->hist, h->hist_cap, h->st);
+    }
     AMG_TRY(cudaGetLastError());
     AMG_TRY(enqueue_vcycle(h, s));
-    k_scal_beta<<<AMG_GRID(1), 1024, 0, s>>>(slot(h, S_RZ), slot(h, S_ZQ), nbz(h), flex, 0, h->st);
-    k_pupdate<<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(n, h->p, h->z, 0, h->st);
+    k_scal_beta<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RZ), slot(h, S_ZQ), nbz(h), flex, 0, h->st);
+    launch_pupdate(h, 0, s);
     return cudaGetLastError();
 }
 
 // ||F - K x|| and ||F|| into slot(S_OUT)[0..1] (FP64, recomputed).
 cudaError_t launch_final_residual(amg_hierarchy* h, cudaStream_t s) {
-    AMG_TRY(launch_residual(h, h->q, nullptr, s));
-    k_sqrt_sum<<<AMG_GRID(1), 1024, 0, s>>>(slot(h, S_RR), nb0(h), slot(h, S_OUT));
-    k_sqrt_sum<<<AMG_GRID(1), 1024, 0, s>>>(slot(h, S_FF), nb0(h), slot(h, S_OUT) + 1);
+    AMG_TRY(launch_residual(h, h->q, false, S_RR, true, nullptr, s));
+    k_sqrt_sum<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RR), nb0(h), slot(h, S_OUT));
+    k_sqrt_sum<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_FF), nb0(h), slot(h, S_OUT) + 1);
     return cudaGetLastError();
 }
 
@@ -652,8 +789,13 @@ double* final_residual_slot(amg_hierarchy* h) { return slot(h, S_OUT); }
 
 // z = B r for r already in h->r (state must not be "done").
 cudaError_t enqueue_vcycle_standalone(amg_hierarchy* h, cudaStream_t s) {
-    if (h->nlev > 1)
-        k_scale<<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(h->lev[0].A.n, h->r, h->lev[0].invd, h->lev[0].x);
+    if (h->nlev > 1) {
+        Level& L0 = h->lev[0];
+        if (h->mixed)
+            k_scale<float><<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(L0.A.n, h->r, L0.invd32, L0.x32);
+        else
+            k_scale<double><<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(L0.A.n, h->r, L0.invd, L0.x);
+    }
     AMG_TRY(cudaGetLastError());
     return enqueue_vcycle(h, s);
 }

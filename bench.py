@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp64",
+                    help="precision of the main timed leg (profiling runs)")
     return ap.parse_args()
 
 
@@ -243,7 +245,8 @@ def run_ours(args):
     va = torch.from_numpy(prob.val).to(dev)
     F = torch.from_numpy(prob.F).to(dev)
     stream = torch.cuda.Stream(device=dev)
-    opts = A.amg_opts_default()
+    prec = {"fp64": A.AMG_FP64, "fp32": A.AMG_FP32, "bf16": A.AMG_FP32_BF16FINE}[args.precision]
+    opts = A.amg_opts_default(precision=prec)
 
     def step(profile=False):
         h = A.amg_setup(rp, ci, va, opts, stream)
@@ -422,6 +425,9 @@ def run_ours(args):
                        "rtol": args.rtol, "precision": "fp64", "l2": "inputs larger than L2 (matrix 1.04 GB)",
                        "parallelism": f"replicas x{world}"},
             "iters": it, "final_relres": rr, "setup_ms": info.setup_ms, "solve_ms": info.solve_ms,
+            "setup_phase_ms": dict(zip(["copy+checks", "l1+testvec+diag", "edge_weights", "matching",
+                                        "aggregation", "galerkin", "composite+members", "coarse_inverse",
+                                        "workspace"], [round(info.setup_phase_ms[k], 3) for k in range(9)])),
             "levels": [int(info.n[l]) for l in range(info.levels)], "opc": info.opc,
             "iter_gbps": info.iter_bytes * it / (info.solve_ms * 1e-3) / 1e9 if info.solve_ms > 0 else None,
             "vcycle_ms": vcycle_ms, "vcycle_gbps": vinfo.vcycle_bytes / (vcycle_ms * 1e-3) / 1e9,

@@ -108,6 +108,12 @@ typedef struct {
     double vcycle_bytes; /* algorithmic bytes of one V-cycle */
     double iter_bytes;   /* algorithmic bytes of one CG iteration (incl. V-cycle) */
     int32_t match_rounds[AMG_MAX_LEVELS]; /* total matching rounds per level */
+    /* setup time by phase (ms, stream-ordered events): [0] input copy and
+     * checks, [1] l1 diagonals and test vector, [2] edge weights,
+     * [3] matching rounds, [4] aggregation, [5] Galerkin products,
+     * [6] composite maps and member lists, [7] coarsest inverse,
+     * [8] precision copies and solve workspace */
+    double setup_phase_ms[12];
 } amg_info;
 
 typedef struct amg_hierarchy amg_hierarchy;

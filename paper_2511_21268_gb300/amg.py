@@ -52,7 +52,8 @@ class AmgInfo(ctypes.Structure):
                 ("nnz", ctypes.c_int64 * AMG_MAX_LEVELS), ("opc", ctypes.c_double), ("setup_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("iters", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("final_relres", ctypes.c_double), ("vcycle_bytes", ctypes.c_double),
-                ("iter_bytes", ctypes.c_double), ("match_rounds", ctypes.c_int32 * AMG_MAX_LEVELS)]
+                ("iter_bytes", ctypes.c_double), ("match_rounds", ctypes.c_int32 * AMG_MAX_LEVELS),
+                ("setup_phase_ms", ctypes.c_double * 12)]
 
 
 class AmgError(RuntimeError):

@@ -34,7 +34,11 @@ namespace {
 
 constexpr int kGraphIters = 8;
 constexpr int kMaxGalerkinCap = 16384;  // candidate entries per Galerkin row (shared memory)
+constexpr double kBitmapSmem = 200.0 * 1024;  // shared memory budget of the bitmap Galerkin kernels
 constexpr int kHistCap = 1 << 16;
+// Matrix column/value arrays get kPad trailing entries: the FP32/BF16 matrix
+// passes load groups of four entries from 4-aligned positions.
+constexpr size_t kPad = 8;
 
 thread_local char g_cuda_err[512] = "";
 
@@ -54,6 +58,16 @@ int cuda_fail(cudaError_t e, const char* what) {
         int r__ = (expr);            \
         if (r__ != AMG_OK) return r__; \
     } while (0)
+
+constexpr int kRoundBatch = 4;
+
+// Mark the start of setup phase `id` (see amg_info.setup_phase_ms).
+void phase(amg_hierarchy* h, int id) {
+    if (h->ph_n >= 512) return;
+    if (!h->ph_ev[h->ph_n] && cudaEventCreate(&h->ph_ev[h->ph_n]) != cudaSuccess) return;
+    cudaEventRecord(h->ph_ev[h->ph_n], h->s);
+    h->ph_id[h->ph_n++] = id;
+}
 
 template <typename T>
 int dalloc(amg_hierarchy* h, T** p, size_t count) {
@@ -131,18 +145,33 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
     RC(tlead.get(&leader, n));
     RC(tcidx.get(&cidx, n));
     RC(tscan.get(&scr, scan_scratch_ints(n) + 1));
+    phase(h, 2);
     CK(launch_edge_keys(A, kii, w, key, s));
+    phase(h, 3);
     CK(launch_match_init(n, state, s));
-    int rounds = 0, active = n;
-    while (active > 0) {
-        if (rounds >= h->o.max_match_rounds) return AMG_ERR_TIMEOUT;
-        CK(launch_match_propose(A, key, state, cand, s));
-        CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
-        CK(launch_match_commit(n, cand, state, h->flag, s));
-        rounds++;
-        RC(read_flag(h, &active));
+    // rounds in batches of kRoundBatch between host checks; rounds after
+    // the last active vertex are no-ops.  round_active[r] = active count
+    // after round r gives the exact round count.
+    const int maxr = h->o.max_match_rounds;
+    CK(cudaMemsetAsync(h->round_active, 0, sizeof(int) * (maxr + kRoundBatch), s));
+    int rounds = 0, done = 0;
+    while (!done) {
+        if (rounds >= maxr) return AMG_ERR_TIMEOUT;
+        const int cnt = std::min(kRoundBatch, maxr - rounds);
+        CK(launch_match_rounds(A, key, state, cand, h->round_active, rounds, cnt, s));
+        CK(cudaMemcpyAsync(h->flag_host, h->round_active + rounds, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int r = 0; r < cnt; r++) {
+            if (h->flag_host[r] == 0) {
+                rounds += r + 1;
+                done = 1;
+                break;
+            }
+        }
+        if (!done) rounds += cnt;
     }
     P.rounds = rounds;
+    phase(h, 4);
     P.n = n;
     RC(dalloc(h, &P.mate, n));
     CK(launch_match_finish(n, state, P.mate, leader, s));
@@ -160,31 +189,43 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
     RC(dalloc(h, wc, nc));
     CK(launch_aggregate(n, P.mate, cidx, w, P.agg, P.pval, mem0, mem1, *wc, s));
     // Galerkin product of this pass
+    phase(h, 5);
     CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
     CK(launch_row_stats(A, mem0, mem1, nc, h->flag, s));
     int maxcand = 0;
     RC(read_flag(h, &maxcand));
     const int cap = pow2ceil(std::max(maxcand, 1));
-    if (cap > kMaxGalerkinCap) return AMG_ERR_ROW_TOO_LONG;
+    // bitmap kernels when the widest coarse-column span fits shared memory,
+    // else the candidate-sorting kernels
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    CK(launch_row_span(A, P.agg, mem0, mem1, nc, h->flag, s));
+    int maxspan = 0;
+    RC(read_flag(h, &maxspan));
+    const int words = (maxspan + 31) / 32 + 1;
+    const bool bitmap = 8.0 * words + 16.0 * maxcand <= kBitmapSmem;
+    if (!bitmap && cap > kMaxGalerkinCap) return AMG_ERR_ROW_TOO_LONG;
     C.n = nc;
     RC(dalloc(h, &C.rowptr, (size_t)nc + 1));
     int64_t *rowcnt, *scr64;
     Tmp trc(s), ts64(s);
     RC(trc.get(&rowcnt, nc));
     RC(ts64.get(&scr64, scan64_scratch(nc) + 1));
-    CK(launch_galerkin_count(A, P.agg, mem0, mem1, nc, cap, rowcnt, s));
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    if (bitmap) CK(launch_galerkin_count_bitmap(A, P.agg, mem0, mem1, nc, maxcand, words, rowcnt, h->flag, s));
+    else CK(launch_galerkin_count(A, P.agg, mem0, mem1, nc, cap, rowcnt, s));
     CK(launch_scan64(rowcnt, C.rowptr, nc, scr64, s));
     int64_t nnzc = 0;
     RC(read_scalar(h, C.rowptr + nc, &nnzc));
     C.nnz = nnzc;
-    RC(dalloc(h, &C.col, (size_t)nnzc));
-    RC(dalloc(h, &C.val, (size_t)nnzc));
-    CK(launch_galerkin_fill(A, P.agg, P.pval, mem0, mem1, cap, C, s));
-    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    RC(dalloc(h, &C.col, (size_t)nnzc + kPad));
+    RC(dalloc(h, &C.val, (size_t)nnzc + kPad));
+    if (bitmap) CK(launch_galerkin_fill_bitmap(A, P.agg, P.pval, mem0, mem1, maxcand, words, C, h->flag, s));
+    else CK(launch_galerkin_fill(A, P.agg, P.pval, mem0, mem1, cap, C, s));
     CK(launch_galerkin_mirror(C, h->flag, s));
     int bad = 0;
     RC(read_flag(h, &bad));
     if (bad) return AMG_ERR_ARG;  // structurally unsymmetric input
+    phase(h, 1);
     return AMG_OK;
 }
 
@@ -198,12 +239,13 @@ void free_level_matrix(amg_hierarchy* h, DevCSR& A) {
 int build(amg_hierarchy* h, const amg_csr* K) {
     cudaStream_t s = h->s;
     const int n0 = K->n;
+    phase(h, 0);
     Level& L0 = h->lev[0];
     L0.A.n = n0;
     L0.A.nnz = K->nnz;
     RC(dalloc(h, &L0.A.rowptr, (size_t)n0 + 1));
-    RC(dalloc(h, &L0.A.col, (size_t)K->nnz));
-    RC(dalloc(h, &L0.A.val, (size_t)K->nnz));
+    RC(dalloc(h, &L0.A.col, (size_t)K->nnz + kPad));
+    RC(dalloc(h, &L0.A.val, (size_t)K->nnz + kPad));
     const cudaMemcpyKind kind = K->mem == AMG_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(cudaMemcpyAsync(L0.A.rowptr, K->rowptr, sizeof(int64_t) * (n0 + 1), kind, s));
     CK(cudaMemcpyAsync(L0.A.col, K->col, sizeof(int32_t) * K->nnz, kind, s));
@@ -225,7 +267,9 @@ int build(amg_hierarchy* h, const amg_csr* K) {
     if (bad & 2) return AMG_ERR_NAN;
     if (bad & 4) return AMG_ERR_NOT_SPD;
 
+    RC(dalloc(h, &h->round_active, (size_t)h->o.max_match_rounds + kRoundBatch));
     for (int l = 0;; l++) {
+        phase(h, 1);
         Level& F = h->lev[l];
         const int n = F.A.n;
         RC(dalloc(h, &F.kii, n));
@@ -279,6 +323,7 @@ int build(amg_hierarchy* h, const amg_csr* K) {
         }
         if (l + 1 >= AMG_MAX_LEVELS) return AMG_ERR_ARG;
         // composite map and member lists
+        phase(h, 6);
         F.nc = nc;
         RC(dalloc(h, &F.agg, n));
         RC(dalloc(h, &F.pval, n));
@@ -300,6 +345,7 @@ int build(amg_hierarchy* h, const amg_csr* K) {
         C.w = cw;
     }
     // coarsest level: dense inverse
+    phase(h, 7);
     Level& Lc = h->lev[h->nlev - 1];
     const int nd = Lc.A.n;
     if (nd > h->o.dense_max) return AMG_ERR_COARSE_TOO_LARGE;
@@ -314,14 +360,15 @@ int build(amg_hierarchy* h, const amg_csr* K) {
     RC(read_flag(h, &bad));
     if (bad) return AMG_ERR_NOT_SPD;
     // solve workspace
+    phase(h, 8);
     for (int l = 0; l < h->nlev; l++) {
         Level& F = h->lev[l];
         const int n = F.A.n;
         if (h->mixed) {  // FP32 copies of the level (BF16 finest values in the V-cycle if asked)
-            RC(dalloc(h, &F.val32, (size_t)F.A.nnz));
+            RC(dalloc(h, &F.val32, (size_t)F.A.nnz + kPad));
             CK(launch_to_f32(F.A.val, F.val32, F.A.nnz, s));
             if (l == 0 && h->o.precision == AMG_FP32_BF16FINE && h->nlev > 1) {
-                RC(dalloc(h, &F.val16, (size_t)F.A.nnz));
+                RC(dalloc(h, &F.val16, (size_t)F.A.nnz + kPad));
                 CK(launch_to_bf16(F.A.val, F.val16, F.A.nnz, s));
             }
             RC(dalloc(h, &F.invd32, n));
@@ -336,6 +383,13 @@ int build(amg_hierarchy* h, const amg_csr* K) {
         }
     }
     if (h->mixed) RC(dalloc(h, &h->p32, n0));
+    // the vectorised loads need 16-byte aligned column and value arrays
+    for (int l = 0; l < h->nlev; l++) {
+        const Level& F = h->lev[l];
+        const void* ptrs[4] = {F.A.col, F.A.val, F.val32, F.val16};
+        for (const void* p : ptrs)
+            if (p && (reinterpret_cast<uintptr_t>(p) & 15)) return AMG_ERR_CUDA;
+    }
     RC(dalloc(h, &h->x, n0));
     RC(dalloc(h, &h->r, n0));
     RC(dalloc(h, &h->p, n0));
@@ -406,6 +460,8 @@ void destroy(amg_hierarchy* h) {
         for (auto& b : a)
             for (auto& e : b)
                 if (e) cudaEventDestroy(e);
+    for (auto& e : h->ph_ev)
+        if (e) cudaEventDestroy(e);
     if (h->s && h->own_stream) cudaStreamDestroy(h->s);
     delete h;
 }
@@ -519,6 +575,12 @@ int amg_setup(const amg_csr* K, const amg_opts* opts, void* cuda_stream, amg_hie
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     h->info.setup_ms = ms;
+    for (int k = 0; k < h->ph_n; k++) {
+        float dt = 0.f;
+        cudaEvent_t end = (k + 1 < h->ph_n) ? h->ph_ev[k + 1] : h->ev1;
+        if (cudaEventElapsedTime(&dt, h->ph_ev[k], end) == cudaSuccess && h->ph_id[k] < 12)
+            h->info.setup_phase_ms[h->ph_id[k]] += dt;
+    }
     fill_info(h);
     *out = h;
     return AMG_OK;

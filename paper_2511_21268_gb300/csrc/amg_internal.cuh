@@ -125,6 +125,11 @@ struct amg_hierarchy {
     double prof_ms[3] = {0, 0, 0};
     long long prof_cnt[3] = {0, 0, 0};
     int prof_slot = -1;  // iteration slot being captured, -1 = not capturing
+    // setup phase timing: an event at every phase change
+    cudaEvent_t ph_ev[512] = {};
+    int ph_id[512] = {};
+    int ph_n = 0;
+    int* round_active = nullptr;  // active count after each matching round (device)
 };
 
 namespace amg {
@@ -141,6 +146,8 @@ cudaError_t launch_match_init(int n, int32_t* state, cudaStream_t s);
 cudaError_t launch_match_propose(const DevCSR& A, const uint64_t* key, const int32_t* state, int32_t* cand,
                                  cudaStream_t s);
 cudaError_t launch_match_commit(int n, const int32_t* cand, int32_t* state, int* active, cudaStream_t s);
+cudaError_t launch_match_rounds(const DevCSR& A, const uint64_t* key, int32_t* state, int32_t* cand, int* active,
+                                int first_round, int count, cudaStream_t s);
 cudaError_t launch_match_finish(int n, const int32_t* state, int32_t* mate, int32_t* leader, cudaStream_t s);
 cudaError_t launch_aggregate(int n, const int32_t* mate, const int32_t* cidx, const double* w, int32_t* agg,
                              double* pval, int32_t* mem0, int32_t* mem1, double* wc, cudaStream_t s);
@@ -152,6 +159,12 @@ cudaError_t launch_galerkin_count(const DevCSR& A, const int32_t* agg, const int
 cudaError_t launch_galerkin_fill(const DevCSR& A, const int32_t* agg, const double* pval, const int32_t* mem0,
                                  const int32_t* mem1, int cap, DevCSR& C, cudaStream_t s);
 cudaError_t launch_galerkin_mirror(DevCSR& C, int* flag, cudaStream_t s);
+cudaError_t launch_galerkin_count_bitmap(const DevCSR& A, const int32_t* agg, const int32_t* mem0, const int32_t* mem1,
+                                         int nc, int cap, int words, int64_t* rowcnt, int* flag, cudaStream_t s);
+cudaError_t launch_galerkin_fill_bitmap(const DevCSR& A, const int32_t* agg, const double* pval, const int32_t* mem0,
+                                        const int32_t* mem1, int cap, int words, DevCSR& C, int* flag, cudaStream_t s);
+cudaError_t launch_row_span(const DevCSR& A, const int32_t* agg, const int32_t* mem0, const int32_t* mem1, int nc,
+                            int* maxspan, cudaStream_t s);
 cudaError_t launch_scan64(const int64_t* in, int64_t* out, int n, int64_t* scratch, cudaStream_t s);
 size_t scan64_scratch(int n);
 cudaError_t launch_row_stats(const DevCSR& A, const int32_t* mem0, const int32_t* mem1, int nc, int* maxcand,

@@ -564,6 +564,172 @@ __global__ void k_galerkin_mirror(int n, const int64_t* __restrict__ rp, const i
     }
 }
 
+// Galerkin without sorting candidates.  One block per coarse row I: the
+// coarse columns J = agg[b] of the member rows' entries set bits of a
+// shared-memory bitmap over [Jmin, Jmax]; prefix popcounts of the bitmap
+// words give every J its position in the sorted row.  A coarse entry
+// K_c(I,J) has at most four terms; term (a, b) goes to slot
+// 2 * rank(a in I) + rank(b in J), so summing the slots in order is the
+// canonical (a ascending, b ascending) order -- no sort, bit-exact.
+__device__ __forceinline__ void block_minmax(int v_min, int v_max, int* smin, int* smax) {
+    v_min = __reduce_min_sync(FULL, v_min);
+    v_max = __reduce_max_sync(FULL, v_max);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(smin, v_min);
+        atomicMax(smax, v_max);
+    }
+}
+
+template <bool FILL>
+__global__ void k_galerkin_bitmap(int nc, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                  const double* __restrict__ v, const int32_t* __restrict__ agg,
+                                  const double* __restrict__ pval, const int32_t* __restrict__ mem0,
+                                  const int32_t* __restrict__ mem1, int cap, int words, int64_t* rowcnt,
+                                  const int64_t* __restrict__ crp, int32_t* cci, double* cv, int* flag) {
+    extern __shared__ __align__(16) unsigned char gsm[];
+    uint32_t* bits = reinterpret_cast<uint32_t*>(gsm);
+    int32_t* pre = reinterpret_cast<int32_t*>(gsm + 4 * (size_t)words);
+    int32_t* slot = reinterpret_cast<int32_t*>(gsm + 8 * (size_t)words);  // FILL: [cap][4]
+    __shared__ int jmin, jmax, wsum[33];
+    for (int I = blockIdx.x; I < nc; I += gridDim.x) {
+        const int a0 = mem0[I], a1 = mem1[I];
+        const int64_t b0 = rp[a0];
+        const int len0 = (int)(rp[a0 + 1] - b0);
+        const int64_t b1 = a1 >= 0 ? rp[a1] : 0;
+        const int len1 = a1 >= 0 ? (int)(rp[a1 + 1] - b1) : 0;
+        const int c = len0 + len1;
+        if (threadIdx.x == 0) {
+            jmin = 0x7fffffff;
+            jmax = -1;
+        }
+        __syncthreads();
+        int lmin = 0x7fffffff, lmax = -1;
+        for (int t = threadIdx.x; t < c; t += blockDim.x) {
+            const int J = agg[t < len0 ? ci[b0 + t] : ci[b1 + (t - len0)]];
+            lmin = min(lmin, J);
+            lmax = max(lmax, J);
+        }
+        block_minmax(lmin, lmax, &jmin, &jmax);
+        __syncthreads();
+        const int J0 = jmin;
+        const int W = ((jmax - J0) >> 5) + 1;
+        if (W > words || (FILL && c > cap)) {  // sized from the row statistics; cannot happen
+            if (threadIdx.x == 0) atomicOr(flag, 32);
+            __syncthreads();
+            continue;
+        }
+        for (int w = threadIdx.x; w < W; w += blockDim.x) bits[w] = 0u;
+        __syncthreads();
+        for (int t = threadIdx.x; t < c; t += blockDim.x) {
+            const int J = agg[t < len0 ? ci[b0 + t] : ci[b1 + (t - len0)]] - J0;
+            atomicOr(&bits[J >> 5], 1u << (J & 31));
+        }
+        __syncthreads();
+        // exclusive prefix of popcounts over the W words (thread-contiguous chunks)
+        const int per = (W + blockDim.x - 1) / blockDim.x;
+        const int w0 = min(W, (int)threadIdx.x * per), w1 = min(W, w0 + per);
+        int mine = 0;
+        for (int w = w0; w < w1; w++) mine += __popc(bits[w]);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        int xs = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, xs, o);
+            if (lane >= o) xs += y;
+        }
+        if (lane == 31) wsum[wid] = xs;
+        __syncthreads();
+        if (wid == 0) {
+            int sv = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, sv, o);
+                if (lane >= o) sv += y;
+            }
+            if (lane < (int)(blockDim.x >> 5)) wsum[lane] = sv;
+            if (lane == 31) wsum[32] = sv;
+        }
+        __syncthreads();
+        int run = (wid > 0 ? wsum[wid - 1] : 0) + xs - mine;
+        for (int w = w0; w < w1; w++) {
+            pre[w] = run;
+            run += __popc(bits[w]);
+        }
+        const int u = wsum[32];
+        if (!FILL) {
+            if (threadIdx.x == 0) rowcnt[I] = u;
+            __syncthreads();
+            continue;
+        }
+        __syncthreads();
+        const int64_t base = crp[I];
+        // sorted coarse columns
+        for (int w = threadIdx.x; w < W; w += blockDim.x) {
+            uint32_t m = bits[w];
+            int pos = pre[w];
+            while (m) {
+                const int bit = __ffs(m) - 1;
+                m &= m - 1;
+                cci[base + pos++] = J0 + (w << 5) + bit;
+            }
+        }
+        for (int t = threadIdx.x; t < 4 * u; t += blockDim.x) slot[t] = -1;
+        __syncthreads();
+        for (int t = threadIdx.x; t < c; t += blockDim.x) {
+            const int b = t < len0 ? ci[b0 + t] : ci[b1 + (t - len0)];
+            const int J = agg[b];
+            const int jj = J - J0;
+            const int pos = pre[jj >> 5] + __popc(bits[jj >> 5] & ((1u << (jj & 31)) - 1u));
+            const int q = 2 * (t < len0 ? 0 : 1) + (b == mem0[J] ? 0 : 1);
+            slot[4 * pos + q] = t;
+        }
+        __syncthreads();
+        const double p0 = pval[a0], p1 = a1 >= 0 ? pval[a1] : 0.0;
+        for (int pos = threadIdx.x; pos < u; pos += blockDim.x) {
+            const int J = cci[base + pos];
+            double acc = 0.0;
+            if (J >= I) {
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int t = slot[4 * pos + q];
+                    if (t < 0) continue;
+                    const bool first = t < len0;
+                    const int64_t k = first ? b0 + t : b1 + (t - len0);
+                    acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(first ? p0 : p1, v[k]), pval[ci[k]]));
+                }
+            }
+            cv[base + pos] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// max over coarse rows of the coarse-column span Jmax - Jmin + 1
+__global__ void k_row_span(int nc, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const int32_t* __restrict__ agg, const int32_t* __restrict__ mem0,
+                           const int32_t* __restrict__ mem1, int* maxspan) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    int best = 0;
+    for (int I = warp; I < nc; I += nw) {
+        int lo = 0x7fffffff, hi = -1;
+        for (int m = 0; m < 2; m++) {
+            const int a = m == 0 ? mem0[I] : mem1[I];
+            if (a < 0) continue;
+            for (int64_t k = rp[a] + lane; k < rp[a + 1]; k += 32) {
+                const int J = agg[ci[k]];
+                lo = min(lo, J);
+                hi = max(hi, J);
+            }
+        }
+        lo = __reduce_min_sync(FULL, lo);
+        hi = __reduce_max_sync(FULL, hi);
+        best = max(best, hi - lo + 1);
+    }
+    if (lane == 0) atomicMax(maxspan, best);
+}
+
 // max over coarse rows of the candidate count len(a0) + len(a1)
 __global__ void k_row_stats(int nc, const int64_t* __restrict__ rp, const int32_t* __restrict__ mem0,
                             const int32_t* __restrict__ mem1, int* maxcand) {
@@ -772,6 +938,17 @@ cudaError_t launch_match_commit(int n, const int32_t* cand, int32_t* state, int*
     return cudaGetLastError();
 }
 
+// `count` rounds back to back; active[r] receives the number of vertices
+// still active after round first_round + r (the caller zeroes active[]).
+cudaError_t launch_match_rounds(const DevCSR& A, const uint64_t* key, int32_t* state, int32_t* cand, int* active,
+                                int first_round, int count, cudaStream_t s) {
+    for (int r = 0; r < count; r++) {
+        AMG_TRY(launch_match_propose(A, key, state, cand, s));
+        AMG_TRY(launch_match_commit(A.n, cand, state, active + first_round + r, s));
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_match_finish(int n, const int32_t* state, int32_t* mate, int32_t* leader, cudaStream_t s) {
     k_match_finish<<<AMG_GRID(blocks_for(n, kBlock, 4096)), kBlock, 0, s>>>(n, state, mate, leader);
     return cudaGetLastError();
@@ -817,6 +994,37 @@ cudaError_t launch_galerkin_fill(const DevCSR& A, const int32_t* agg, const doub
 
 cudaError_t launch_galerkin_mirror(DevCSR& C, int* flag, cudaStream_t s) {
     k_galerkin_mirror<<<AMG_GRID(blocks_for(C.n, kWarpsPerBlock, 8192)), kBlock, 0, s>>>(C.n, C.rowptr, C.col, C.val, flag);
+    return cudaGetLastError();
+}
+
+static size_t bitmap_smem(int cap, int words, bool fill) {
+    return 8 * (size_t)words + (fill ? 16 * (size_t)cap : 0);
+}
+
+cudaError_t launch_galerkin_count_bitmap(const DevCSR& A, const int32_t* agg, const int32_t* mem0, const int32_t* mem1,
+                                         int nc, int cap, int words, int64_t* rowcnt, int* flag, cudaStream_t s) {
+    const size_t sm = bitmap_smem(cap, words, false);
+    if (sm > 48 * 1024)
+        AMG_TRY(cudaFuncSetAttribute(k_galerkin_bitmap<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_galerkin_bitmap<false><<<AMG_GRID(blocks_for(nc, 1, 65536)), kBlock, sm, s>>>(
+        nc, A.rowptr, A.col, A.val, agg, nullptr, mem0, mem1, cap, words, rowcnt, nullptr, nullptr, nullptr, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_galerkin_fill_bitmap(const DevCSR& A, const int32_t* agg, const double* pval, const int32_t* mem0,
+                                        const int32_t* mem1, int cap, int words, DevCSR& C, int* flag, cudaStream_t s) {
+    const size_t sm = bitmap_smem(cap, words, true);
+    if (sm > 48 * 1024)
+        AMG_TRY(cudaFuncSetAttribute(k_galerkin_bitmap<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_galerkin_bitmap<true><<<AMG_GRID(blocks_for(C.n, 1, 65536)), kBlock, sm, s>>>(
+        C.n, A.rowptr, A.col, A.val, agg, pval, mem0, mem1, cap, words, nullptr, C.rowptr, C.col, C.val, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_span(const DevCSR& A, const int32_t* agg, const int32_t* mem0, const int32_t* mem1, int nc,
+                            int* maxspan, cudaStream_t s) {
+    k_row_span<<<AMG_GRID(blocks_for(nc, kWarpsPerBlock, 8192)), kBlock, 0, s>>>(nc, A.rowptr, A.col, agg, mem0, mem1,
+                                                                               maxspan);
     return cudaGetLastError();
 }
 

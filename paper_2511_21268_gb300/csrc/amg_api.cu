@@ -146,7 +146,8 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
     RC(tcidx.get(&cidx, n));
     RC(tscan.get(&scr, scan_scratch_ints(n) + 1));
     phase(h, 2);
-    CK(launch_edge_keys(A, kii, w, key, s));
+    CK(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), s));
+    CK(launch_edge_keys(A, kii, w, key, h->flag + 1, s));
     phase(h, 3);
     CK(launch_match_init(n, state, s));
     // rounds in batches of kRoundBatch between host checks; rounds after
@@ -171,6 +172,9 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
         if (!done) rounds += cnt;
     }
     P.rounds = rounds;
+    int unsym = 0;
+    RC(read_scalar(h, h->flag + 1, &unsym));
+    if (unsym) return AMG_ERR_ARG;  // structurally unsymmetric matrix
     phase(h, 4);
     P.n = n;
     RC(dalloc(h, &P.mate, n));

@@ -141,7 +141,8 @@ cudaError_t launch_l1diag(const DevCSR& A, double* kii, double* dl1, double* inv
 cudaError_t launch_diag(const DevCSR& A, double* kii, cudaStream_t s);
 cudaError_t launch_testvec_init(int n, int kind, uint64_t seed, double* w, cudaStream_t s);
 cudaError_t launch_testvec_sweep(const DevCSR& A, const double* dl1, const double* w, double* wout, cudaStream_t s);
-cudaError_t launch_edge_keys(const DevCSR& A, const double* kii, const double* w, uint64_t* key, cudaStream_t s);
+cudaError_t launch_edge_keys(const DevCSR& A, const double* kii, const double* w, uint64_t* key, int* flag,
+                             cudaStream_t s);
 cudaError_t launch_match_init(int n, int32_t* state, cudaStream_t s);
 cudaError_t launch_match_propose(const DevCSR& A, const uint64_t* key, const int32_t* state, int32_t* cand,
                                  cudaStream_t s);

@@ -161,10 +161,13 @@ __global__ void __launch_bounds__(kBlock) k_testvec_sweep(int n, const int64_t* 
 // ------------------------------------------------------------------ matching
 // Edge key of every stored entry: order_key(c_ij) (Eq. cij) for eligible
 // edges, 0 otherwise.  Eligible: j != i, k_ij != 0, denominator > 0 and
-// w_lo^2 + w_hi^2 > 0.
+// w_lo^2 + w_hi^2 > 0.  Each edge is evaluated once, from its upper entry
+// (row i, column j > i), and the key is written to that entry and to its
+// mirror (row j, column i; found by binary search).  flag bit 64: a mirror
+// entry is missing (structurally unsymmetric matrix).
 __global__ void k_edge_keys(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                             const double* __restrict__ v, const double* __restrict__ kii,
-                            const double* __restrict__ w, uint64_t* key) {
+                            const double* __restrict__ w, uint64_t* key, int* flag) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -172,18 +175,34 @@ __global__ void k_edge_keys(int n, const int64_t* __restrict__ rp, const int32_t
         const double wi = w[i], ki = kii[i];
         for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
             const int j = ci[k];
+            if (j < i) continue;  // written by the owner of the upper entry
+            if (j == i) {
+                key[k] = 0;
+                continue;
+            }
             const double a = v[k];
             uint64_t out = 0;
-            if (j != i && a != 0.0) {
+            if (a != 0.0) {
                 const double wj = w[j], kj = kii[j];
-                const double wlo = i < j ? wi : wj, whi = i < j ? wj : wi;
-                const double klo = i < j ? ki : kj, khi = i < j ? kj : ki;
-                const double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a), wlo), whi);
-                const double den = __dadd_rn(__dmul_rn(klo, __dmul_rn(wlo, wlo)), __dmul_rn(khi, __dmul_rn(whi, whi)));
-                const double nrm2 = __dadd_rn(__dmul_rn(wlo, wlo), __dmul_rn(whi, whi));
+                const double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a), wi), wj);
+                const double den = __dadd_rn(__dmul_rn(ki, __dmul_rn(wi, wi)), __dmul_rn(kj, __dmul_rn(wj, wj)));
+                const double nrm2 = __dadd_rn(__dmul_rn(wi, wi), __dmul_rn(wj, wj));
                 if (den > 0.0 && nrm2 > 0.0) out = order_key(__dsub_rn(1.0, __ddiv_rn(num, den)));
             }
             key[k] = out;
+            int64_t lo = rp[j], hi = rp[j + 1] - 1, pos = -1;
+            while (lo <= hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                const int cm = ci[mid];
+                if (cm == i) {
+                    pos = mid;
+                    break;
+                }
+                if (cm < i) lo = mid + 1;
+                else hi = mid - 1;
+            }
+            if (pos < 0) atomicOr(flag, 64);
+            else key[pos] = out;
         }
     }
 }
@@ -917,8 +936,10 @@ cudaError_t launch_testvec_sweep(const DevCSR& A, const double* dl1, const doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_edge_keys(const DevCSR& A, const double* kii, const double* w, uint64_t* key, cudaStream_t s) {
-    k_edge_keys<<<AMG_GRID(blocks_for(A.n, kWarpsPerBlock, 8192)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, kii, w, key);
+cudaError_t launch_edge_keys(const DevCSR& A, const double* kii, const double* w, uint64_t* key, int* flag,
+                             cudaStream_t s) {
+    k_edge_keys<<<AMG_GRID(blocks_for(A.n, kWarpsPerBlock, 8192)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, kii, w,
+                                                                                key, flag);
     return cudaGetLastError();
 }
 

@@ -220,6 +220,15 @@ def test_errors_are_reported_not_trapped():
     with pytest.raises(A.AmgError) as e:
         A.Hierarchy(rp, ci, vv)
     assert e.value.code == A.AMG_ERR_NOT_SPD
+    # structurally unsymmetric: drop entry (5, j) for its first off-diagonal j, keep (j, 5)
+    k_drop = next(k for k in range(rp[5], rp[6]) if ci[k] != 5)
+    rp2 = rp.copy()
+    rp2[6:] -= 1
+    ci2 = np.delete(ci, k_drop)
+    v2 = np.delete(v, k_drop)
+    with pytest.raises(A.AmgError) as e:
+        A.Hierarchy(rp2, ci2, v2, coarse_max=10)
+    assert e.value.code == A.AMG_ERR_ARG
     # matching round budget
     with pytest.raises(A.AmgError) as e:
         A.Hierarchy(rp, ci, v, max_match_rounds=1, coarse_max=10)

@@ -143,6 +143,36 @@ int amg_setup(const amg_csr* K, const amg_opts* opts, void* cuda_stream, amg_hie
 int amg_pcg_solve(amg_hierarchy* h, const double* F, double* u, int32_t mem, double rtol, int32_t itmax,
                   int32_t* iters, double* relres);
 
+/* Several right-hand sides of one matrix: nrhs (1..32) independent
+ * (flexible) CG solves sharing the hierarchy, each with its own scalars and
+ * convergence test; every matrix pass of an iteration reads the matrix once
+ * for all right-hand sides (SpMM).  F and U are column-major n x nrhs with
+ * leading dimension ld >= n (U: initial guesses in, solutions out), host or
+ * device per `mem`.  iters[nrhs], relres[nrhs] (may be NULL) receive each
+ * system's iteration count and final ||F - K u|| / ||F||.  Requires
+ * nu_pre = nu_post = 1 and a hierarchy from amg_setup.  Returns AMG_OK when
+ * every system converged, otherwise the first failure status (NaN first).
+ * Errors as amg_pcg_solve. */
+int amg_pcg_solve_multi(amg_hierarchy* h, int32_t nrhs, const double* F, double* U, int64_t ld, int32_t mem,
+                        double rtol, int32_t itmax, int32_t* iters, double* relres);
+
+/* A batch of independent systems K_k u_k = F_k (count <= 1024): the
+ * matrices are assembled block-diagonally into one hierarchy (no entry
+ * couples two systems, so every aggregate and coarse operator stays inside
+ * one block and the V-cycle acts on each system separately).  Ks[count] as
+ * in amg_setup (each CSR in its own 0-based numbering, host or device).
+ * Errors as amg_setup. */
+int amg_setup_batch(int32_t count, const amg_csr* Ks, const amg_opts* opts, void* cuda_stream,
+                    amg_hierarchy** out);
+
+/* Solve every system of a batch hierarchy with its own CG iteration in one
+ * graph-captured loop; converged systems are frozen while others continue.
+ * F[count], U[count]: per-system pointers (host or device per `mem`; U holds
+ * initial guesses in, solutions out).  iters[count], relres[count] as in
+ * amg_pcg_solve_multi.  Requires nu_pre = nu_post = 1. */
+int amg_pcg_solve_batch(amg_hierarchy* h, const double* const* F, double* const* U, int32_t mem, double rtol,
+                        int32_t itmax, int32_t* iters, double* relres);
+
 /* Apply one V-cycle z = B r (device pointers, n = rows of level 0).  Used by
  * the parity tests and by callers with their own Krylov method. */
 int amg_vcycle_apply(amg_hierarchy* h, const double* r_dev, double* z_dev);

@@ -74,6 +74,13 @@ _SIGS = {
     "amg_pcg_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                      ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "amg_vcycle_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_pcg_solve_multi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_setup_batch": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "amg_pcg_solve_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                           ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "amg_level_spmv": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "amg_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "amg_export_level": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 7),
@@ -197,6 +204,65 @@ def amg_pcg_solve(h, F, u, rtol: float, itmax: int):
     return rc, it.value, rr.value
 
 
+def amg_pcg_solve_multi(h, F, U, rtol: float, itmax: int):
+    """F, U: (nrhs, n) C-contiguous arrays/tensors = column-major n x nrhs
+    (ld = n); U holds the initial guesses and receives the solutions.
+    Returns (status, iters[nrhs], relres[nrhs])."""
+    pF, mF, kF = _ptr(F)
+    pU, mU, kU = _ptr(U)
+    if mF != mU or kU is not U:
+        raise ValueError("F and U must share a memory space; U must be contiguous")
+    nrhs, n = F.shape
+    it = np.zeros(nrhs, np.int32)
+    rr = np.zeros(nrhs)
+    rc = lib().amg_pcg_solve_multi(h, nrhs, pF, pU, n, mF, float(rtol), int(itmax), it.ctypes.data, rr.ctypes.data)
+    if rc not in (AMG_OK, AMG_ERR_NOT_CONVERGED, AMG_ERR_BREAKDOWN, AMG_ERR_NAN):
+        _check(rc, "amg_pcg_solve_multi")
+    return rc, it, rr
+
+
+def amg_setup_batch(systems, opts: AmgOpts | None = None, stream=None):
+    """systems: list of (rowptr, col, val) (numpy or torch, one memory space)."""
+    _torch()
+    keep = []
+    arr = (AmgCsr * len(systems))()
+    for k, (rp, ci, va) in enumerate(systems):
+        if isinstance(rp, np.ndarray):
+            rp = np.ascontiguousarray(rp, np.int64)
+            ci = np.ascontiguousarray(ci, np.int32)
+            va = np.ascontiguousarray(va, np.float64)
+        prp, m1, k1 = _ptr(rp)
+        pci, m2, k2 = _ptr(ci)
+        pv, m3, k3 = _ptr(va)
+        keep += [k1, k2, k3]
+        arr[k] = AmgCsr(len(rp) - 1, len(va), prp, pci, pv, m1)
+    h = ctypes.c_void_p()
+    rc = lib().amg_setup_batch(len(systems), arr, ctypes.byref(opts) if opts is not None else None,
+                               _stream_handle(stream), ctypes.byref(h))
+    _check(rc, "amg_setup_batch")
+    del keep
+    return h
+
+
+def amg_pcg_solve_batch(h, Fs, Us, rtol: float, itmax: int):
+    """Fs, Us: per-system vectors (one memory space); Us solved in place.
+    Returns (status, iters[count], relres[count])."""
+    ptrF = [_ptr(F) for F in Fs]
+    ptrU = [_ptr(U) for U in Us]
+    mem = ptrF[0][1]
+    if any(p[1] != mem for p in ptrF + ptrU) or any(p[2] is not U for p, U in zip(ptrU, Us)):
+        raise ValueError("all vectors must share a memory space; U must be contiguous")
+    cnt = len(Fs)
+    aF = (ctypes.c_void_p * cnt)(*[p[0] for p in ptrF])
+    aU = (ctypes.c_void_p * cnt)(*[p[0] for p in ptrU])
+    it = np.zeros(cnt, np.int32)
+    rr = np.zeros(cnt)
+    rc = lib().amg_pcg_solve_batch(h, aF, aU, mem, float(rtol), int(itmax), it.ctypes.data, rr.ctypes.data)
+    if rc not in (AMG_OK, AMG_ERR_NOT_CONVERGED, AMG_ERR_BREAKDOWN, AMG_ERR_NAN):
+        _check(rc, "amg_pcg_solve_batch")
+    return rc, it, rr
+
+
 def amg_vcycle_apply(h, r, z):
     _check(lib().amg_vcycle_apply(h, r.data_ptr(), z.data_ptr()), "amg_vcycle_apply")
 
@@ -313,6 +379,14 @@ class Hierarchy:
         self.info = amg_get_info(self._h)
         return dict(u=u, iters=iters, relres=relres, status=status)
 
+    def solve_multi(self, F, U=None, rtol: float = 1e-8, itmax: int = 10000):
+        """F: (nrhs, n) array/tensor; returns dict(u, iters[], relres[], status)."""
+        if U is None:
+            U = np.zeros_like(F, dtype=np.float64) if isinstance(F, np.ndarray) else F.new_zeros(F.shape)
+        status, iters, relres = amg_pcg_solve_multi(self._h, F, U, rtol, itmax)
+        self.info = amg_get_info(self._h)
+        return dict(u=U, iters=iters, relres=relres, status=status)
+
     def vcycle(self, r):
         z = r.new_empty(r.shape)
         amg_vcycle_apply(self._h, r, z)
@@ -329,3 +403,21 @@ class Hierarchy:
 
     def export_pass(self, l: int, s: int):
         return amg_export_pass(self._h, l, s)
+
+
+class BatchHierarchy(Hierarchy):
+    """Owning wrapper of a batch hierarchy (amg_setup_batch)."""
+
+    def __init__(self, systems, stream=None, **opts):
+        self.opts = amg_opts_default(**opts)
+        self._h = amg_setup_batch(systems, self.opts, stream)
+        self.info = amg_get_info(self._h)
+        self.sizes = [len(rp) - 1 for rp, _, _ in systems]
+
+    def solve_batch(self, Fs, Us=None, rtol: float = 1e-8, itmax: int = 10000):
+        if Us is None:
+            Us = [np.zeros_like(F, dtype=np.float64) if isinstance(F, np.ndarray) else F.new_zeros(F.shape)
+                  for F in Fs]
+        status, iters, relres = amg_pcg_solve_batch(self._h, Fs, Us, rtol, itmax)
+        self.info = amg_get_info(self._h)
+        return dict(u=Us, iters=iters, relres=relres, status=status)

@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -60,6 +61,7 @@ int cuda_fail(cudaError_t e, const char* what) {
     } while (0)
 
 constexpr int kRoundBatch = 4;
+constexpr int kMaxSystems = 1024;  // systems of one batch (one scalar thread each)
 
 // Mark the start of setup phase `id` (see amg_info.setup_phase_ms).
 void phase(amg_hierarchy* h, int id) {
@@ -449,8 +451,30 @@ void fill_info(amg_hierarchy* h) {
     I.iter_bytes = vbytes + outer + 10.0 * A0.n * 8.0;
 }
 
+void free_multi(amg_hierarchy* h) {
+    MultiWork* w = h->mw;
+    if (!w) return;
+    if (w->graph) cudaGraphExecDestroy(w->graph);
+    for (void* p : w->allocs) cudaFreeAsync(p, h->s);
+    if (w->st_host) cudaFreeHost(w->st_host);
+    if (w->active_host) cudaFreeHost(w->active_host);
+    delete w;
+    h->mw = nullptr;
+}
+
+template <typename T>
+int walloc(amg_hierarchy* h, MultiWork& w, T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, sizeof(T) * (count ? count : 1), h->s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    w.allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return AMG_OK;
+}
+
 void destroy(amg_hierarchy* h) {
     if (!h) return;
+    free_multi(h);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     for (void* p : h->allocs) cudaFreeAsync(p, h->s);
     h->allocs.clear();
@@ -515,12 +539,14 @@ int amg_opts_default(amg_opts* o) {
     return AMG_OK;
 }
 
-int amg_setup(const amg_csr* K, const amg_opts* opts, void* cuda_stream, amg_hierarchy** out) {
-    if (!out) return AMG_ERR_ARG;
-    *out = nullptr;
-    if (!K || K->n < 1 || K->nnz < K->n || !K->rowptr || !K->col || !K->val) return AMG_ERR_ARG;
-    if (K->mem != AMG_MEM_HOST && K->mem != AMG_MEM_DEVICE) return AMG_ERR_ARG;
-    if (K->nnz > (int64_t)INT32_MAX * 4) return AMG_ERR_ARG;
+static bool csr_args_ok(const amg_csr* K) {
+    if (!K || K->n < 1 || K->nnz < K->n || !K->rowptr || !K->col || !K->val) return false;
+    if (K->mem != AMG_MEM_HOST && K->mem != AMG_MEM_DEVICE) return false;
+    return K->nnz <= (int64_t)INT32_MAX * 4;
+}
+
+// Hierarchy shell: options, stream, events, pinned mirrors.
+static int create_hierarchy(const amg_opts* opts, void* cuda_stream, amg_hierarchy** out) {
     amg_hierarchy* h = new (std::nothrow) amg_hierarchy();
     if (!h) return AMG_ERR_NOMEM;
     if (opts) h->o = *opts;
@@ -562,18 +588,25 @@ int amg_setup(const amg_csr* K, const amg_opts* opts, void* cuda_stream, amg_hie
     }
     rc = join_caller(h);
     if (rc == AMG_OK) rc = dalloc(h, &h->flag, 16);
-    if (rc == AMG_OK) {
-        cudaEventRecord(h->ev0, h->s);
-        rc = build(h, K);
-        cudaEventRecord(h->ev1, h->s);
+    if (rc != AMG_OK) {
+        destroy(h);
+        return rc;
     }
+    *out = h;
+    return AMG_OK;
+}
+
+// Build the hierarchy of K (device or host CSR), time it, fill the info.
+static int finish_setup(amg_hierarchy* h, const amg_csr* K) {
+    cudaEventRecord(h->ev0, h->s);
+    int rc = build(h, K);
+    cudaEventRecord(h->ev1, h->s);
     if (rc == AMG_OK) {
-        e = cudaStreamSynchronize(h->s);
+        cudaError_t e = cudaStreamSynchronize(h->s);
         if (e != cudaSuccess) rc = cuda_fail(e, "amg_setup");
     }
     if (rc != AMG_OK) {
         cudaStreamSynchronize(h->s);
-        destroy(h);
         return rc;
     }
     float ms = 0.f;
@@ -586,6 +619,88 @@ int amg_setup(const amg_csr* K, const amg_opts* opts, void* cuda_stream, amg_hie
             h->info.setup_phase_ms[h->ph_id[k]] += dt;
     }
     fill_info(h);
+    return AMG_OK;
+}
+
+int amg_setup(const amg_csr* K, const amg_opts* opts, void* cuda_stream, amg_hierarchy** out) {
+    if (!out) return AMG_ERR_ARG;
+    *out = nullptr;
+    if (!csr_args_ok(K)) return AMG_ERR_ARG;
+    amg_hierarchy* h = nullptr;
+    int rc = create_hierarchy(opts, cuda_stream, &h);
+    if (rc != AMG_OK) return rc;
+    rc = finish_setup(h, K);
+    if (rc != AMG_OK) {
+        destroy(h);
+        return rc;
+    }
+    *out = h;
+    return AMG_OK;
+}
+
+// Block-diagonal assembly of `count` systems into one device CSR, then the
+// usual setup.  Row offsets of the systems are kept for the solves.
+static int batch_build(amg_hierarchy* h, int count, const amg_csr* Ks, const std::vector<int64_t>& roff,
+                       const std::vector<int64_t>& zoff) {
+    cudaStream_t s = h->s;
+    const int64_t N = roff[count], Z = zoff[count];
+    int64_t maxn = 0;
+    for (int k = 0; k < count; k++) maxn = std::max<int64_t>(maxn, Ks[k].n);
+    int64_t *rp_all, *rp_tmp;
+    int32_t* col_all;
+    double* val_all;
+    Tmp t1(s), t2(s), t3(s), t4(s);
+    RC(t1.get(&rp_all, (size_t)N + 1));
+    RC(t2.get(&col_all, (size_t)Z));
+    RC(t3.get(&val_all, (size_t)Z));
+    RC(t4.get(&rp_tmp, (size_t)maxn + 1));
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    for (int k = 0; k < count; k++) {
+        const amg_csr& K = Ks[k];
+        const cudaMemcpyKind kind = K.mem == AMG_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        CK(cudaMemcpyAsync(col_all + zoff[k], K.col, sizeof(int32_t) * K.nnz, kind, s));
+        CK(cudaMemcpyAsync(val_all + zoff[k], K.val, sizeof(double) * K.nnz, kind, s));
+        CK(cudaMemcpyAsync(rp_tmp, K.rowptr, sizeof(int64_t) * (K.n + 1), kind, s));
+        int64_t first = 0, last = 0;
+        RC(read_scalar(h, rp_tmp, &first));
+        RC(read_scalar(h, rp_tmp + K.n, &last));
+        if (first != 0 || last != K.nnz) return AMG_ERR_ARG;
+        CK(launch_shift_block(K.n, K.nnz, rp_tmp, roff[k], zoff[k], rp_all + roff[k], col_all, h->flag, s));
+        CK(cudaStreamSynchronize(s));  // rp_tmp is reused by the next system
+    }
+    int bad = 0;
+    RC(read_flag(h, &bad));
+    if (bad) return AMG_ERR_ARG;
+    h->nsys = count;
+    h->sys_off = roff;
+    RC(dalloc(h, &h->sys_off_dev, (size_t)count + 1));
+    RC(dalloc(h, &h->sys_id, (size_t)N));
+    CK(cudaMemcpyAsync(h->sys_off_dev, roff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+    CK(launch_fill_sys_id(count, h->sys_off_dev, h->sys_id, s));
+    const amg_csr all = {(int32_t)N, Z, rp_all, col_all, val_all, AMG_MEM_DEVICE};
+    return finish_setup(h, &all);
+}
+
+int amg_setup_batch(int32_t count, const amg_csr* Ks, const amg_opts* opts, void* cuda_stream, amg_hierarchy** out) {
+    if (!out) return AMG_ERR_ARG;
+    *out = nullptr;
+    if (count < 1 || count > kMaxSystems || !Ks) return AMG_ERR_ARG;
+    std::vector<int64_t> roff(count + 1, 0), zoff(count + 1, 0);
+    for (int k = 0; k < count; k++) {
+        if (!csr_args_ok(&Ks[k])) return AMG_ERR_ARG;
+        roff[k + 1] = roff[k] + Ks[k].n;
+        zoff[k + 1] = zoff[k] + Ks[k].nnz;
+    }
+    if (roff[count] > INT32_MAX || zoff[count] > (int64_t)INT32_MAX * 4) return AMG_ERR_ARG;
+    amg_hierarchy* h = nullptr;
+    int rc = create_hierarchy(opts, cuda_stream, &h);
+    if (rc != AMG_OK) return rc;
+    rc = batch_build(h, count, Ks, roff, zoff);
+    if (rc != AMG_OK) {
+        cudaStreamSynchronize(h->s);
+        destroy(h);
+        return rc;
+    }
     *out = h;
     return AMG_OK;
 }
@@ -682,6 +797,197 @@ int amg_pcg_solve(amg_hierarchy* h, const double* F, double* u, int32_t mem, dou
     h->info.final_relres = rel;
     if (iters) *iters = it;
     if (relres) *relres = rel;
+    return rc;
+}
+
+// ------------------------------------------------------ multi-system solves
+// Workspace for S systems over R interleaved vectors (reused when unchanged).
+static int ensure_multi(amg_hierarchy* h, int R, int S, const int32_t* seg, const int64_t* segoff) {
+    if (h->mw && h->mw->R == R && h->mw->S == S && h->mw->seg == seg) return AMG_OK;
+    CK(cudaStreamSynchronize(h->s));
+    free_multi(h);
+    MultiWork* w = new (std::nothrow) MultiWork();
+    if (!w) return AMG_ERR_NOMEM;
+    h->mw = w;
+    w->R = R;
+    w->Rp = pow2ceil(R);
+    w->S = S;
+    w->seg = seg;
+    w->segoff = segoff;
+    const size_t E = (size_t)h->lev[0].A.n * R;
+    RC(walloc(h, *w, &w->x, E));
+    RC(walloc(h, *w, &w->r, E));
+    RC(walloc(h, *w, &w->p, E));
+    RC(walloc(h, *w, &w->q, E));
+    RC(walloc(h, *w, &w->z, E));
+    RC(walloc(h, *w, &w->F, E));
+    RC(walloc(h, *w, &w->pa, E));
+    RC(walloc(h, *w, &w->pb, E));
+    RC(walloc(h, *w, &w->stage, E));
+    if (h->mixed) RC(walloc(h, *w, &w->p32, E));
+    RC(walloc(h, *w, &w->dots, (size_t)S * multi_dot_stride()));
+    RC(walloc(h, *w, &w->st, (size_t)S));
+    RC(walloc(h, *w, &w->active, 1));
+    RC(walloc(h, *w, &w->params, 2));
+    CK(cudaMemsetAsync(w->pb, 0, sizeof(double) * E, h->s));
+    for (int l = 0; l < h->nlev; l++) {
+        const size_t El = (size_t)h->lev[l].A.n * R;
+        const size_t b = h->mixed ? 4 : 8;
+        char *f = nullptr, *x = nullptr, *t = nullptr;
+        if (l > 0) RC(walloc(h, *w, &f, El * b));
+        RC(walloc(h, *w, &x, El * b));
+        RC(walloc(h, *w, &t, El * b));
+        w->lf[l] = f;
+        w->lx[l] = x;
+        w->lt[l] = t;
+    }
+    CK(cudaMallocHost(&w->st_host, sizeof(MultiState) * S));
+    CK(cudaMallocHost(&w->active_host, sizeof(int)));
+    return AMG_OK;
+}
+
+// Runs the multi-system CG on the workspace (F and x already filled).
+// iters/relres/status per system (host arrays, may be NULL).
+static int run_multi(amg_hierarchy* h, int32_t* iters, double* relres, int32_t* zero_rhs) {
+    MultiWork& w = *h->mw;
+    cudaStream_t s = h->s;
+    CK(cudaEventRecord(h->ev0, s));
+    CK(enqueue_multi_start(h, s));
+    if (!w.graph) {
+        cudaGraph_t g;
+        const long long before = amg::g_launches.load();
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < kGraphIters && e == cudaSuccess; k++) e = enqueue_multi_iteration(h, s);
+        cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        w.graph_kernels = amg::g_launches.load() - before;
+        amg::g_launches -= w.graph_kernels;
+        if (e != cudaSuccess) return cuda_fail(e, "capture");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&w.graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            w.graph = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+    }
+    const int max_launches = h->itmax / kGraphIters + 2;
+    for (int k = 0; k <= max_launches + 1; k++) {
+        CK(cudaMemcpyAsync(w.active_host, w.active, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (*w.active_host == 0 || k > max_launches) break;
+        CK(cudaGraphLaunch(w.graph, s));
+        amg::g_launches += w.graph_kernels;
+    }
+    CK(cudaEventRecord(h->ev1, s));
+    CK(enqueue_multi_final(h, s));
+    std::vector<double> dots((size_t)w.S * multi_dot_stride());
+    CK(cudaMemcpyAsync(dots.data(), w.dots, sizeof(double) * dots.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(w.st_host, w.st, sizeof(MultiState) * w.S, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    h->info.solve_ms = ms;
+    int worst = AMG_OK, maxit = 0;
+    for (int k = 0; k < w.S; k++) {
+        const MultiState& m = w.st_host[k];
+        const double rr = std::sqrt(dots[(size_t)k * multi_dot_stride() + 0]);
+        const double ff = std::sqrt(dots[(size_t)k * multi_dot_stride() + 1]);
+        int st = m.done ? m.status : AMG_ERR_NOT_CONVERGED;
+        if (iters) iters[k] = m.iters;
+        if (relres) relres[k] = (ff > 0.0 && m.nF > 0.0) ? rr / ff : 0.0;
+        if (zero_rhs) zero_rhs[k] = !(m.nF > 0.0) && st == AMG_OK;
+        if (st != AMG_OK && (worst == AMG_OK || st == AMG_ERR_NAN)) worst = st;
+        maxit = std::max(maxit, m.iters);
+    }
+    h->info.iters = maxit;
+    h->info.status = worst;
+    return worst;
+}
+
+static int check_multi_opts(const amg_hierarchy* h) {
+    return (h->o.nu_pre == 1 && h->o.nu_post == 1) ? AMG_OK : AMG_ERR_ARG;
+}
+
+int amg_pcg_solve_multi(amg_hierarchy* h, int32_t nrhs, const double* F, double* U, int64_t ld, int32_t mem,
+                        double rtol, int32_t itmax, int32_t* iters, double* relres) {
+    if (!h || !F || !U || nrhs < 1 || nrhs > 32 || (mem != AMG_MEM_HOST && mem != AMG_MEM_DEVICE) ||
+        !(rtol >= 0.0) || itmax < 0 || h->nsys > 0)
+        return AMG_ERR_ARG;
+    const int n = h->lev[0].A.n;
+    if (ld < n) return AMG_ERR_ARG;
+    RC(check_multi_opts(h));
+    RC(join_caller(h));
+    RC(ensure_multi(h, nrhs, nrhs, nullptr, nullptr));
+    MultiWork& w = *h->mw;
+    cudaStream_t s = h->s;
+    const size_t colb = sizeof(double) * n, ldb = sizeof(double) * ld;
+    if (mem == AMG_MEM_HOST) {
+        CK(cudaMemcpy2DAsync(w.stage, colb, F, ldb, colb, nrhs, cudaMemcpyHostToDevice, s));
+        CK(launch_interleave(n, nrhs, n, w.stage, w.F, s));
+        CK(cudaMemcpy2DAsync(w.stage, colb, U, ldb, colb, nrhs, cudaMemcpyHostToDevice, s));
+        CK(launch_interleave(n, nrhs, n, w.stage, w.x, s));
+    } else {
+        CK(launch_interleave(n, nrhs, ld, F, w.F, s));
+        CK(launch_interleave(n, nrhs, ld, U, w.x, s));
+    }
+    h->rtol = rtol;
+    h->itmax = itmax;
+    std::vector<int32_t> zero(nrhs, 0);
+    const int rc = run_multi(h, iters, relres, zero.data());
+    if (rc == AMG_ERR_CUDA || rc == AMG_ERR_NOMEM) return rc;
+    if (mem == AMG_MEM_HOST) {
+        CK(launch_deinterleave(n, nrhs, n, w.x, w.stage, s));
+        CK(cudaMemcpy2DAsync(U, ldb, w.stage, colb, colb, nrhs, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int k = 0; k < nrhs; k++)
+            if (zero[k]) memset(U + (size_t)k * ld, 0, colb);
+    } else {
+        CK(launch_deinterleave(n, nrhs, ld, w.x, U, s));
+        for (int k = 0; k < nrhs; k++)
+            if (zero[k]) CK(cudaMemsetAsync(U + (size_t)k * ld, 0, colb, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return rc;
+}
+
+int amg_pcg_solve_batch(amg_hierarchy* h, const double* const* F, double* const* U, int32_t mem, double rtol,
+                        int32_t itmax, int32_t* iters, double* relres) {
+    if (!h || !F || !U || h->nsys < 1 || (mem != AMG_MEM_HOST && mem != AMG_MEM_DEVICE) || !(rtol >= 0.0) ||
+        itmax < 0)
+        return AMG_ERR_ARG;
+    for (int k = 0; k < h->nsys; k++)
+        if (!F[k] || !U[k]) return AMG_ERR_ARG;
+    RC(check_multi_opts(h));
+    RC(join_caller(h));
+    RC(ensure_multi(h, 1, h->nsys, h->sys_id, h->sys_off_dev));
+    MultiWork& w = *h->mw;
+    cudaStream_t s = h->s;
+    const cudaMemcpyKind in = mem == AMG_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind outk = mem == AMG_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int k = 0; k < h->nsys; k++) {
+        const int64_t o = h->sys_off[k], nk = h->sys_off[k + 1] - o;
+        CK(cudaMemcpyAsync(w.F + o, F[k], sizeof(double) * nk, in, s));
+        CK(cudaMemcpyAsync(w.x + o, U[k], sizeof(double) * nk, in, s));
+    }
+    h->rtol = rtol;
+    h->itmax = itmax;
+    std::vector<int32_t> zero(h->nsys, 0);
+    const int rc = run_multi(h, iters, relres, zero.data());
+    if (rc == AMG_ERR_CUDA || rc == AMG_ERR_NOMEM) return rc;
+    for (int k = 0; k < h->nsys; k++) {
+        const int64_t o = h->sys_off[k], nk = h->sys_off[k + 1] - o;
+        if (zero[k]) {
+            if (mem == AMG_MEM_DEVICE) CK(cudaMemsetAsync(U[k], 0, sizeof(double) * nk, s));
+            else {
+                CK(cudaStreamSynchronize(s));
+                memset(U[k], 0, sizeof(double) * nk);
+            }
+        } else {
+            CK(cudaMemcpyAsync(U[k], w.x + o, sizeof(double) * nk, outk, s));
+        }
+    }
+    CK(cudaStreamSynchronize(s));
     return rc;
 }
 

@@ -38,6 +38,36 @@ struct SolveState {
     int pad3;
 };
 
+// Per-system CG state of a multi-system solve (several right-hand sides or
+// a batch of block-diagonal systems).
+struct MultiState {
+    int done, iters, status, replace_now;
+    double nF, tol, rho, alpha, beta, pq, nr;
+};
+
+// Workspace of a multi-system solve.  Vectors are interleaved [N][R].
+struct MultiWork {
+    int R = 0, Rp = 0, S = 0;
+    const int32_t* seg = nullptr;     // batch: system of each row (R = 1)
+    const int64_t* segoff = nullptr;  // batch: [S + 1] row offsets of the systems
+    double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *F = nullptr;
+    float* p32 = nullptr;
+    double *pa = nullptr, *pb = nullptr;  // per-element products for the dots
+    double* dots = nullptr;               // [S][7]
+    double* stage = nullptr;              // column-major staging for copies
+    MultiState* st = nullptr;
+    MultiState* st_host = nullptr;
+    int* active = nullptr;     // systems still iterating
+    int* active_host = nullptr;
+    int* params = nullptr;     // itmax, replacement period
+    void* lf[AMG_MAX_LEVELS] = {};
+    void* lx[AMG_MAX_LEVELS] = {};
+    void* lt[AMG_MAX_LEVELS] = {};
+    cudaGraphExec_t graph = nullptr;
+    long long graph_kernels = 0;
+    std::vector<void*> allocs;
+};
+
 // One matching pass on a matrix with n rows -> nc coarse rows.
 struct Pass {
     int n = 0, nc = 0;
@@ -130,6 +160,13 @@ struct amg_hierarchy {
     int ph_id[512] = {};
     int ph_n = 0;
     int* round_active = nullptr;  // active count after each matching round (device)
+    // multi-system solves
+    amg::MultiWork* mw = nullptr;
+    // block-diagonal batch (amg_setup_batch): systems and their row offsets
+    int nsys = 0;
+    std::vector<int64_t> sys_off;    // host copy [nsys + 1]
+    int32_t* sys_id = nullptr;       // device [N]
+    int64_t* sys_off_dev = nullptr;  // device [nsys + 1]
 };
 
 namespace amg {
@@ -187,6 +224,17 @@ cudaError_t enqueue_pcg_start(amg_hierarchy* h, cudaStream_t s);
 cudaError_t enqueue_pcg_iteration(amg_hierarchy* h, cudaStream_t s);
 cudaError_t launch_final_residual(amg_hierarchy* h, cudaStream_t s);
 double* final_residual_slot(amg_hierarchy* h);
+// multi_solve.cu
+cudaError_t enqueue_multi_start(amg_hierarchy* h, cudaStream_t s);
+cudaError_t enqueue_multi_iteration(amg_hierarchy* h, cudaStream_t s);
+cudaError_t enqueue_multi_final(amg_hierarchy* h, cudaStream_t s);
+int multi_dot_stride();
+cudaError_t launch_interleave(int n, int R, int64_t ld, const double* src, double* dst, cudaStream_t s);
+cudaError_t launch_deinterleave(int n, int R, int64_t ld, const double* src, double* dst, cudaStream_t s);
+// batch assembly (setup_kernels.cu)
+cudaError_t launch_shift_block(int n, int64_t nnz, const int64_t* rp_in, int64_t row_off, int64_t nnz_off,
+                               int64_t* rp_out, int32_t* col, int* flag, cudaStream_t s);
+cudaError_t launch_fill_sys_id(int nsys, const int64_t* off, int32_t* id, cudaStream_t s);
 int rows_per_warp(int n, int num_sms);
 int row_blocks(int n, int rpw);
 int vec_blocks(int n, int num_sms);

@@ -894,9 +894,39 @@ __global__ void k_to_bf16(const double* __restrict__ in, __nv_bfloat16* out, int
         out[i] = __float2bfloat16_rn(__double2float_rn(in[i]));
 }
 
+// Block-diagonal assembly of a batch: instance rows are moved by row_off,
+// its entries by nnz_off (flag bit 1: a column outside the instance).
+__global__ void k_shift_block(int n, int64_t nnz, const int64_t* __restrict__ rp_in, int64_t row_off, int64_t nnz_off,
+                              int64_t* rp_out, int32_t* col, int* flag) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g <= n) rp_out[g] = rp_in[g] + nnz_off;
+    if (g < nnz) {
+        const int c = col[nnz_off + g];
+        if (c < 0 || c >= n) atomicOr(flag, 1);
+        col[nnz_off + g] = c + (int32_t)row_off;
+    }
+}
+
+__global__ void k_fill_sys_id(int nsys, const int64_t* __restrict__ off, int32_t* id) {
+    const int s = blockIdx.x;
+    if (s >= nsys) return;
+    for (int64_t i = off[s] + threadIdx.x; i < off[s + 1]; i += blockDim.x) id[i] = s;
+}
+
 }  // namespace
 
 // ============================================================== launch wrappers
+cudaError_t launch_shift_block(int n, int64_t nnz, const int64_t* rp_in, int64_t row_off, int64_t nnz_off,
+                               int64_t* rp_out, int32_t* col, int* flag, cudaStream_t s) {
+    const int64_t m = (nnz > (int64_t)n + 1 ? nnz : (int64_t)n + 1);
+    k_shift_block<<<AMG_GRID((int)((m + 255) / 256)), 256, 0, s>>>(n, nnz, rp_in, row_off, nnz_off, rp_out, col, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_sys_id(int nsys, const int64_t* off, int32_t* id, cudaStream_t s) {
+    k_fill_sys_id<<<AMG_GRID(nsys), 256, 0, s>>>(nsys, off, id);
+    return cudaGetLastError();
+}
 cudaError_t launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t s) {
     k_to_f32<<<AMG_GRID(blocks_for(n, kBlock, 8192)), kBlock, 0, s>>>(in, out, n);
     return cudaGetLastError();

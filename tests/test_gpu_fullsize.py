@@ -1,0 +1,126 @@
+"""Full-size checks on the workloads' own sizes, in the configuration bench.py
+times (device-resident inputs, default options).
+
+* 3-D Poisson p=3 n=64 (N=274,625, 86.9 M nonzeros), FP64: the whole
+  hierarchy bit-exact against the oracle, the V-cycle within 1e-12, and the
+  complete PCG solve at rtol 1e-8 against the oracle's (iterations +-1,
+  solution 1e-10).
+* Precision sweep p = 2/3/4 at n = 96/64/48: mixed-precision solves reach
+  the FP64 true residual 1e-8 (recomputed here with scipy) and stay within
+  1e-7 of the FP64 solution (itself oracle-checked above and in the parity
+  tests); the errors are printed.
+* The 48-system batch of 2-D problems (p in {2,3,4}, n in 32..256, seeded)
+  and 16 right-hand sides on 3-D p=3 n=48: every system's true residual
+  (scipy) meets rtol 1e-8; one right-hand side is compared with the oracle.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle as O  # noqa: E402
+from paper_2511_21268_gb300 import amg as A  # noqa: E402
+from paper_2511_21268_gb300 import inputs as I  # noqa: E402
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def true_relres(prob_or_csr, F, u):
+    rp, ci, v = prob_or_csr
+    K = sp.csr_matrix((v, ci, rp), shape=(len(rp) - 1,) * 2)
+    return np.linalg.norm(F - K @ u) / np.linalg.norm(F)
+
+
+@pytest.fixture(scope="module")
+def cube64():
+    prob = I.poisson_box(3, 64, 3)
+    Ho = O.Hierarchy(prob.rowptr, prob.col, prob.val)
+    return prob, Ho
+
+
+def test_fullsize_fp64_hierarchy_bit_exact(cube64):
+    prob, Ho = cube64
+    H = A.Hierarchy(dev(prob.rowptr), dev(prob.col), dev(prob.val))
+    assert H.num_levels == Ho.num_levels
+    for l in range(H.num_levels):
+        g = H.export_level(l)
+        rp, ci, v = Ho.level_csr(l)
+        assert np.array_equal(g["rowptr"], rp) and np.array_equal(g["col"], ci)
+        assert np.array_equal(g["val"].view(np.uint64), v.view(np.uint64))
+        if l < H.num_levels - 1:
+            agg, pv = Ho.level_map(l)
+            assert np.array_equal(g["agg"], agg) and np.array_equal(g["pval"].view(np.uint64), pv.view(np.uint64))
+    r = np.random.default_rng(5).standard_normal(prob.n)
+    z = H.vcycle(dev(r)).cpu().numpy()
+    zo = Ho.vcycle(r)
+    assert np.linalg.norm(z - zo) <= 1e-12 * np.linalg.norm(zo)
+
+
+def test_fullsize_fp64_solve_matches_oracle(cube64):
+    prob, Ho = cube64
+    H = A.Hierarchy(dev(prob.rowptr), dev(prob.col), dev(prob.val))
+    g = H.solve(dev(prob.F), rtol=1e-8)
+    ref = Ho.pcg(prob.F, rtol=1e-8)
+    assert g["status"] == 0 and ref["status"] == 0
+    assert abs(g["iters"] - ref["iters"]) <= 1
+    u = g["u"].cpu().numpy()
+    if g["iters"] != ref["iters"]:
+        u = H.solve(dev(prob.F), rtol=0.0, itmax=ref["iters"])["u"].cpu().numpy()
+    assert np.linalg.norm(u - ref["u"]) <= 1e-10 * np.linalg.norm(ref["u"])
+    assert true_relres((prob.rowptr, prob.col, prob.val), prob.F, g["u"].cpu().numpy()) <= 1e-8 * 1.0001
+
+
+@pytest.mark.parametrize("p,n", [(2, 96), (3, 64), (4, 48)])
+def test_fullsize_precision_sweep(p, n):
+    prob = I.poisson_box(3, n, p)
+    args = (dev(prob.rowptr), dev(prob.col), dev(prob.val))
+    F = dev(prob.F)
+    ref = A.Hierarchy(*args).solve(F, rtol=1e-8)
+    assert ref["status"] == 0
+    u64 = ref["u"].cpu().numpy()
+    for prec, name in [(A.AMG_FP32, "fp32"), (A.AMG_FP32_BF16FINE, "bf16-fine")]:
+        g = A.Hierarchy(*args, precision=prec).solve(F, rtol=1e-8)
+        assert g["status"] == 0
+        u = g["u"].cpu().numpy()
+        rr = true_relres((prob.rowptr, prob.col, prob.val), prob.F, u)
+        err = np.linalg.norm(u - u64) / np.linalg.norm(u64)
+        print(f"p={p} n={n} N={prob.n} {name}: iters {g['iters']} (fp64 {ref['iters']}), true relres {rr:.2e}, "
+              f"error vs FP64 {err:.2e}")
+        assert rr <= 1e-8 * 1.0001
+        assert err <= 1e-7
+
+
+def test_fullsize_batch_of_48():
+    probs = I.batch_instances(seed=20251126, count=48)
+    systems = [(dev(q.rowptr), dev(q.col), dev(q.val)) for q in probs]
+    B = A.BatchHierarchy(systems, precision=A.AMG_FP32)
+    out = B.solve_batch([dev(q.F) for q in probs], rtol=1e-8)
+    assert out["status"] == 0
+    worst = 0.0
+    for k, q in enumerate(probs):
+        u = out["u"][k].cpu().numpy()
+        rr = true_relres((q.rowptr, q.col, q.val), q.F, u)
+        worst = max(worst, rr)
+        assert rr <= 1e-8 * 1.0001, (k, rr)
+    print(f"48-system batch: N={sum(q.n for q in probs)}, iterations {int(out['iters'].min())}.."
+          f"{int(out['iters'].max())}, worst true relres {worst:.2e}")
+
+
+def test_fullsize_sixteen_rhs():
+    prob = I.poisson_box_random_rhs(3, 48, 3, seed=16, nrhs=16)
+    F = np.ascontiguousarray(prob.F.reshape(16, prob.n))
+    H = A.Hierarchy(dev(prob.rowptr), dev(prob.col), dev(prob.val), precision=A.AMG_FP32)
+    out = H.solve_multi(dev(F), rtol=1e-8)
+    assert out["status"] == 0
+    U = out["u"].cpu().numpy()
+    for c in range(16):
+        assert true_relres((prob.rowptr, prob.col, prob.val), F[c], U[c]) <= 1e-8 * 1.0001
+    Ho = O.Hierarchy(prob.rowptr, prob.col, prob.val)
+    ref = Ho.pcg(F[0], rtol=1e-8, flexible=True)
+    err = np.linalg.norm(U[0] - ref["u"]) / np.linalg.norm(ref["u"])
+    print(f"16 RHS, 3-D p=3 n=48: iterations {out['iters'].tolist()}, column 0 error vs FP64 oracle {err:.2e}")
+    assert err <= 1e-7

@@ -1,0 +1,241 @@
+"""CPU ORACLE (test infrastructure) for the learned smoother damping.
+
+The paper's l1-Jacobi smoother (Sec. 3.2) uses x <- x + D^-1 (f - K x)
+with the l1 diagonal D.  The learned variant scales it per row,
+x <- x + diag(omega_i / d_i) (f - K x), omega_i in (0, 2): since
+D - K is positive semidefinite, every such omega keeps the smoother
+convergent in the K-norm.  omega is produced by a small message-passing
+network over the matrix graph and trained to minimise the error
+reduction of the V-cycle (Sec. 3, two-level correction applied
+recursively) used as CG preconditioner.  The paper has no learned
+component; this file is the plain FP64 statement of what the GPU kernels
+compute, written out step by step.
+
+Network (hidden width 32, two message-passing layers):
+  node features  x_i = [rho_i, sig_i, log2(nnz_i) / 8, 1] with
+                 rho_i = sum_{j != i} |k_ij| / k_ii,
+                 sig_i = sum_{j != i} k_ij / k_ii
+  edge weights   a_ij = k_ij / sqrt(k_ii k_jj), j != i   (a_ii = 0)
+  h0  = relu(W0 x + b0)
+  m_l = sum_j a_ij h_{l-1, j}
+  h_l = relu(U_l m_l + V_l h_{l-1} + b_l),      l = 1, 2
+  omega = 2 sigmoid(q . h2 + c)
+applied to every level's matrix with the same weights.
+
+Loss for probe vectors x_k (SplitMix64 uniform in (-1, 1)):
+  L = (1/m) sum_k log( y_k^T K y_k / x_k^T K x_k ),  y_k = x_k - B_omega K x_k
+with B_omega the V-cycle (one pre- and one post-sweep, exact coarsest
+solve).  The gradient is obtained by reverse-mode differentiation of the
+V-cycle steps and of the network, written out by hand below.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sl
+import scipy.sparse as sp
+
+HIDDEN = 32
+NFEAT = 4
+# flat parameter layout (name, shape)
+LAYOUT = [("W0", (HIDDEN, NFEAT)), ("b0", (HIDDEN,)), ("U1", (HIDDEN, HIDDEN)), ("V1", (HIDDEN, HIDDEN)),
+          ("b1", (HIDDEN,)), ("U2", (HIDDEN, HIDDEN)), ("V2", (HIDDEN, HIDDEN)), ("b2", (HIDDEN,)),
+          ("q", (HIDDEN,)), ("c", (1,))]
+NPARAM = sum(int(np.prod(s)) for _, s in LAYOUT)
+
+
+def unpack(w):
+    out, o = {}, 0
+    for name, shape in LAYOUT:
+        k = int(np.prod(shape))
+        out[name] = np.asarray(w[o:o + k], np.float64).reshape(shape)
+        o += k
+    return out
+
+
+def pack(d):
+    return np.concatenate([np.asarray(d[name], np.float64).reshape(-1) for name, _ in LAYOUT])
+
+
+def init_weights(seed=1):
+    """Reference initialisation (scaled uniform from SplitMix64), c such that
+    omega = 1 when the network output q . h2 is zero."""
+    from paper_2511_21268_gb300 import inputs as I
+
+    u = I.rng_u01(seed, NPARAM) * 2.0 - 1.0
+    d, o = {}, 0
+    for name, shape in LAYOUT:
+        k = int(np.prod(shape))
+        fan = shape[1] if len(shape) == 2 else HIDDEN
+        d[name] = (u[o:o + k] * np.sqrt(3.0 / fan)).reshape(shape)
+        o += k
+    for b in ("b0", "b1", "b2"):
+        d[b] = np.zeros(HIDDEN)
+    d["q"] = d["q"] * 0.1
+    d["c"] = np.zeros(1)
+    return pack(d)
+
+
+# ---------------------------------------------------------------- features
+def features(rowptr, col, val):
+    """Node features x (N, 4) and the normalised off-diagonal matrix A'."""
+    n = len(rowptr) - 1
+    K = sp.csr_matrix((val, col, rowptr), shape=(n, n))
+    kii = K.diagonal()
+    off = K - sp.diags(kii)
+    off.eliminate_zeros()
+    rho = np.asarray(abs(off).sum(axis=1)).ravel() / kii
+    sig = np.asarray(off.sum(axis=1)).ravel() / kii
+    nnz = np.diff(rowptr).astype(np.float64)
+    x = np.stack([rho, sig, np.log2(nnz) / 8.0, np.ones(n)], axis=1)
+    s = 1.0 / np.sqrt(kii)
+    Ap = sp.diags(s) @ off @ sp.diags(s)
+    return x, sp.csr_matrix(Ap)
+
+
+# ----------------------------------------------------------------- network
+def forward(w, x, Ap):
+    p = unpack(w)
+    u0 = x @ p["W0"].T + p["b0"]
+    h0 = np.maximum(u0, 0.0)
+    m1 = Ap @ h0
+    u1 = m1 @ p["U1"].T + h0 @ p["V1"].T + p["b1"]
+    h1 = np.maximum(u1, 0.0)
+    m2 = Ap @ h1
+    u2 = m2 @ p["U2"].T + h1 @ p["V2"].T + p["b2"]
+    h2 = np.maximum(u2, 0.0)
+    z = h2 @ p["q"] + p["c"][0]
+    sg = 1.0 / (1.0 + np.exp(-z))
+    return 2.0 * sg, dict(x=x, u0=u0, h0=h0, m1=m1, u1=u1, h1=h1, m2=m2, u2=u2, h2=h2, z=z, sg=sg)
+
+
+def backward(w, tape, Ap, domega):
+    """Gradient of the loss w.r.t. the flat weights given d loss / d omega."""
+    p = unpack(w)
+    dz = domega * 2.0 * tape["sg"] * (1.0 - tape["sg"])
+    g = {"q": tape["h2"].T @ dz, "c": np.array([dz.sum()])}
+    dh2 = np.outer(dz, p["q"])
+    du2 = dh2 * (tape["u2"] > 0)
+    g["U2"] = du2.T @ tape["m2"]
+    g["V2"] = du2.T @ tape["h1"]
+    g["b2"] = du2.sum(axis=0)
+    dh1 = du2 @ p["V2"] + Ap.T @ (du2 @ p["U2"])
+    du1 = dh1 * (tape["u1"] > 0)
+    g["U1"] = du1.T @ tape["m1"]
+    g["V1"] = du1.T @ tape["h0"]
+    g["b1"] = du1.sum(axis=0)
+    dh0 = du1 @ p["V1"] + Ap.T @ (du1 @ p["U1"])
+    du0 = dh0 * (tape["u0"] > 0)
+    g["W0"] = du0.T @ tape["x"]
+    g["b0"] = du0.sum(axis=0)
+    return pack(g)
+
+
+# ------------------------------------------------------------ V-cycle with omega
+class Levels:
+    """Hierarchy data of an oracle Hierarchy as scipy operators."""
+
+    def __init__(self, H):
+        self.L = H.num_levels
+        self.K, self.d, self.P = [], [], []
+        for l in range(self.L):
+            rp, ci, v = H.level_csr(l)
+            n = len(rp) - 1
+            self.K.append(sp.csr_matrix((v, ci, rp), shape=(n, n)))
+            self.d.append(H.level_vectors(l)[0])
+            if l < self.L - 1:
+                agg, pv = H.level_map(l)
+                self.P.append(sp.csr_matrix((pv, (np.arange(n), agg)), shape=(n, H.level_n(l + 1))))
+        self.chol = H.coarse_chol()
+        self.csr = [(H.level_csr(l)) for l in range(self.L)]
+
+    def coarse_solve(self, f):
+        y = sl.solve_triangular(self.chol, f, lower=True)
+        return sl.solve_triangular(self.chol.T, y, lower=False)
+
+
+def vcycle_omega(lv: Levels, omegas, f, l=0, tape=None):
+    """B_omega f from level l: x1 = Dw f, r1 = f - K x1, e = V_{l+1}(P^T r1),
+    x2 = x1 + P e, r2 = f - K x2, x3 = x2 + Dw r2 (Dw = diag(omega / d))."""
+    if l == lv.L - 1:
+        return lv.coarse_solve(f)
+    K, P, Dw = lv.K[l], lv.P[l], omegas[l] / lv.d[l]
+    x1 = Dw * f
+    r1 = f - K @ x1
+    e = vcycle_omega(lv, omegas, P.T @ r1, l + 1, tape)
+    x2 = x1 + P @ e
+    r2 = f - K @ x2
+    if tape is not None:
+        tape[l] = (f, r2)
+    return x2 + Dw * r2
+
+
+def vcycle_omega_backward(lv: Levels, omegas, gbar, tape, domegas, l=0):
+    """Reverse of vcycle_omega: given d loss / d x3 at level l, accumulate
+    d loss / d omega_l into domegas[l] and return d loss / d f."""
+    if l == lv.L - 1:
+        return lv.coarse_solve(gbar)
+    K, P, d = lv.K[l], lv.P[l], lv.d[l]
+    Dw = omegas[l] / d
+    f, r2 = tape[l]
+    # x3 = x2 + Dw r2
+    dx2 = gbar.copy()
+    dr2 = Dw * gbar
+    domegas[l] += gbar * r2 / d
+    # r2 = f - K x2
+    df = dr2.copy()
+    dx2 -= K @ dr2
+    # x2 = x1 + P e
+    dx1 = dx2.copy()
+    de = P.T @ dx2
+    # e = V_{l+1}(fc), fc = P^T r1
+    dfc = vcycle_omega_backward(lv, omegas, de, tape, domegas, l + 1)
+    dr1 = P @ dfc
+    # r1 = f - K x1
+    df += dr1
+    dx1 -= K @ dr1
+    # x1 = Dw f
+    df += Dw * dx1
+    domegas[l] += dx1 * f / d
+    return df
+
+
+def probes(seed, m, n):
+    """Probe k, entry i: 2 U - 1 with U draw (k n + i) of SplitMix64(seed)."""
+    from paper_2511_21268_gb300 import inputs as I
+
+    return (I.rng_u01(seed, m * n) * 2.0 - 1.0).reshape(m, n)
+
+
+def loss_and_domega(lv: Levels, omegas, X):
+    """Mean over probes of log(y^T K y / x^T K x), y = x - B K x, and its
+    gradient with respect to every level's omega."""
+    K = lv.K[0]
+    total = 0.0
+    domegas = [np.zeros(lv.K[l].shape[0]) for l in range(lv.L)]
+    for x in X:
+        Kx = K @ x
+        tape = {}
+        z = vcycle_omega(lv, omegas, Kx, 0, tape)
+        y = x - z
+        Ky = K @ y
+        yKy, xKx = y @ Ky, x @ Kx
+        total += np.log(yKy) - np.log(xKx)
+        gbar = -2.0 * Ky / yKy  # d/dz of log(y^T K y), y = x - z
+        vcycle_omega_backward(lv, omegas, gbar, tape, domegas, 0)
+    m = len(X)
+    return total / m, [g / m for g in domegas]
+
+
+def loss_and_grad(H, w, nprobe=4, seed=99):
+    """Loss of the network's damping on hierarchy H and its gradient with
+    respect to the flat weights (network applied to every level)."""
+    lv = Levels(H)
+    feats = [features(*lv.csr[l]) for l in range(lv.L)]
+    outs = [forward(w, x, Ap) for x, Ap in feats]
+    omegas = [o[0] for o in outs]
+    X = probes(seed, nprobe, lv.K[0].shape[0])
+    loss, domegas = loss_and_domega(lv, omegas, X)
+    grad = np.zeros(NPARAM)
+    for l in range(lv.L):
+        grad += backward(w, outs[l][1], feats[l][1], domegas[l])
+    return loss, grad, omegas

@@ -1,0 +1,116 @@
+"""Pins for the learned-damping oracle (oracle/mpnn.py).
+
+Independent checks: central finite differences of the loss (w.r.t. the
+per-row damping and w.r.t. the network weights), reduction to the C
+oracle's plain V-cycle when omega = 1, symmetry of the damped V-cycle,
+scale invariance and permutation equivariance of the network.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mpnn as M
+from paper_2511_21268_gb300 import inputs as I
+
+
+@pytest.fixture(scope="module")
+def small():
+    prob = I.poisson_box(2, 10, 3)
+    H = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=20)
+    return prob, H, M.Levels(H)
+
+
+def unit_omega_weights():
+    d = M.unpack(M.init_weights(3))
+    d["q"] = np.zeros(M.HIDDEN)
+    d["c"] = np.zeros(1)  # 2 sigmoid(0) = 1
+    return M.pack(d)
+
+
+def test_nparam_and_layout():
+    assert M.NPARAM == 4353
+    w = M.init_weights(2)
+    assert np.array_equal(M.pack(M.unpack(w)), w)
+
+
+def test_unit_omega_reduces_to_plain_vcycle(small):
+    prob, H, lv = small
+    w = unit_omega_weights()
+    omegas = [M.forward(w, *M.features(*lv.csr[l]))[0] for l in range(lv.L)]
+    assert all(np.allclose(o, 1.0, rtol=0, atol=1e-15) for o in omegas)
+    r = np.random.default_rng(0).standard_normal(prob.n)
+    z = M.vcycle_omega(lv, omegas, r)
+    assert np.linalg.norm(z - H.vcycle(r)) <= 1e-13 * np.linalg.norm(z)
+
+
+def test_damped_vcycle_symmetric(small):
+    prob, H, lv = small
+    rng = np.random.default_rng(1)
+    omegas = [rng.uniform(0.2, 1.9, lv.K[l].shape[0]) for l in range(lv.L)]
+    x, y = rng.standard_normal(prob.n), rng.standard_normal(prob.n)
+    bx, by = M.vcycle_omega(lv, omegas, x), M.vcycle_omega(lv, omegas, y)
+    assert abs(x @ by - y @ bx) <= 1e-12 * np.linalg.norm(x) * np.linalg.norm(bx)
+    assert x @ bx > 0
+
+
+def test_loss_gradient_wrt_omega_finite_differences(small):
+    prob, H, lv = small
+    rng = np.random.default_rng(2)
+    omegas = [rng.uniform(0.5, 1.8, lv.K[l].shape[0]) for l in range(lv.L)]
+    X = M.probes(7, 3, prob.n)
+    L0, g = M.loss_and_domega(lv, omegas, X)
+    dirs = [rng.standard_normal(len(o)) for o in omegas]
+    h = 1e-6
+    Lp, _ = M.loss_and_domega(lv, [o + h * d for o, d in zip(omegas, dirs)], X)
+    Lm, _ = M.loss_and_domega(lv, [o - h * d for o, d in zip(omegas, dirs)], X)
+    fd = (Lp - Lm) / (2 * h)
+    an = sum(gl @ dl for gl, dl in zip(g, dirs))
+    assert abs(fd - an) <= 1e-6 * abs(an)
+    assert L0 < 0  # the V-cycle reduces the error
+
+
+def test_loss_gradient_wrt_weights_finite_differences(small):
+    prob, H, lv = small
+    w = M.init_weights(5)
+    d = M.unpack(w)
+    d["c"] = np.array([0.3])
+    d["b1"] = np.full(M.HIDDEN, 0.05)
+    w = M.pack(d)
+    L0, g, _ = M.loss_and_grad(H, w, nprobe=2, seed=11)
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        v = rng.standard_normal(M.NPARAM)
+        h = 1e-6
+        Lp, _, _ = M.loss_and_grad(H, w + h * v, nprobe=2, seed=11)
+        Lm, _, _ = M.loss_and_grad(H, w - h * v, nprobe=2, seed=11)
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - g @ v) <= 1e-5 * max(abs(fd), 1e-8), (fd, g @ v)
+
+
+def test_network_scale_invariance_and_permutation_equivariance(small):
+    prob, H, lv = small
+    w = M.init_weights(9)
+    d = M.unpack(w)
+    d["q"] = d["q"] * 20
+    w = M.pack(d)
+    om, _ = M.forward(w, *M.features(prob.rowptr, prob.col, prob.val))
+    om2, _ = M.forward(w, *M.features(prob.rowptr, prob.col, prob.val * 37.5))
+    assert np.allclose(om, om2, rtol=1e-12, atol=0)
+    assert om.std() > 1e-3  # the network output varies over the nodes
+    # relabel the unknowns: outputs are relabelled the same way
+    K = prob.to_scipy()
+    perm = np.random.default_rng(4).permutation(prob.n)
+    Kp = K[perm][:, perm].tocsr()
+    Kp.sort_indices()
+    omp, _ = M.forward(w, *M.features(Kp.indptr.astype(np.int64), Kp.indices.astype(np.int32), Kp.data))
+    assert np.allclose(omp, om[perm], rtol=1e-12, atol=1e-14)
+
+
+def test_damping_range_keeps_smoother_convergent(small):
+    prob, H, lv = small
+    K = lv.K[0].toarray()
+    rng = np.random.default_rng(5)
+    om = rng.uniform(0.01, 1.99, prob.n)
+    E = np.eye(prob.n) - (om / lv.d[0])[:, None] * K
+    Lk = np.linalg.cholesky(K)
+    assert np.linalg.norm(Lk.T @ E @ np.linalg.inv(Lk.T), 2) < 1

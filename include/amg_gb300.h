@@ -233,6 +233,78 @@ int amg_kernel_times(const amg_hierarchy* h, double* ms, int64_t* count, double*
  * n > AMG_NOALLOC_MAX_ROWS; AMG_ERR_CUDA on a CUDA failure. */
 int amg_relres_noalloc(const amg_csr* K, const double* F, const double* u, double* relres, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Learned per-row smoother damping.  The paper has no learned component;
+ * this extends its l1-Jacobi smoother (Sec. 3.2, x <- x + D^-1 (f - K x))
+ * to x <- x + diag(omega_i / d_i) (f - K x) with omega_i in (0, 2), which
+ * keeps the smoother convergent in the K-norm (D_l1 - K is positive
+ * semidefinite).  omega comes from a two-layer message-passing network
+ * (hidden width AMG_MPNN_HIDDEN) evaluated on every level's matrix graph:
+ *   x_i  = [sum_{j!=i}|k_ij|/k_ii, sum_{j!=i} k_ij/k_ii, log2(nnz_i)/8, 1]
+ *   a_ij = k_ij / sqrt(k_ii k_jj) (j != i)
+ *   h0 = relu(W0 x + b0); h_l = relu(U_l (A' h_{l-1}) + V_l h_{l-1} + b_l),
+ *   l = 1, 2; omega = 2 sigmoid(q . h2 + c).
+ * Weights: AMG_MPNN_NPARAM floats, row-major blocks in the order
+ * W0[32][4], b0[32], U1[32][32], V1[32][32], b1[32], U2, V2, b2, q[32], c[1].
+ * All weight, gradient and moment pointers are DEVICE pointers owned by the
+ * caller.  The network buffers (about 10 floats x 32 per row of every level
+ * plus one float per stored entry) are allocated on first use and kept
+ * with the hierarchy.  The calls order themselves after the caller's
+ * stream and return when their work is done.
+ * ------------------------------------------------------------------------ */
+#define AMG_MPNN_HIDDEN 32
+#define AMG_MPNN_NPARAM 4353
+
+/* Evaluate the network with weights w (weights rounded to BF16 when
+ * bf16_weights = 1, FP32 when 0; FP32 arithmetic) on every level that has a
+ * smoother and install omega / d as its smoother diagonal (FP64 and, in
+ * the mixed-precision modes, FP32).  w = NULL restores the plain 1 / d
+ * bit for bit.  Later solves, V-cycles and multi-system solves use the
+ * installed diagonal.  Errors: AMG_ERR_ARG (h NULL, bf16_weights not 0/1),
+ * AMG_ERR_NOMEM, AMG_ERR_CUDA. */
+int amg_mpnn_apply(amg_hierarchy* h, const float* w, int32_t bf16_weights);
+
+/* Copy the omega of the last network evaluation (amg_mpnn_apply or
+ * amg_mpnn_loss_grad) on `level` to the device array omega[n_level].
+ * AMG_ERR_ARG if there was none or the level has no smoother. */
+int amg_mpnn_omega(amg_hierarchy* h, int32_t level, float* omega);
+
+/* Training objective and its gradient for weights w (FP32 network):
+ *   loss = (1/m) sum_k log(y_k^T K y_k / x_k^T K x_k), y_k = x_k - B K x_k,
+ * B the V-cycle with the network's damping (one pre- and one post-sweep,
+ * exact coarsest solve), probe k entry i = 2 U - 1 with U the (k n + i)-th
+ * SplitMix64(seed) draw scaled to [0, 1) on 53 bits, m = nprobe.
+ * *loss (host) receives the loss, grad[AMG_MPNN_NPARAM] (device, FP64) the
+ * gradient (reverse mode through the V-cycle in FP64 and through the
+ * network in FP32; deterministic).  Does not change the installed damping.
+ * Errors: AMG_ERR_ARG (NULL pointers, nprobe < 1, a single-level
+ * hierarchy), AMG_ERR_BREAKDOWN (a non-positive energy, e.g. from a
+ * diverging network), AMG_ERR_NAN, AMG_ERR_NOMEM, AMG_ERR_CUDA. */
+int amg_mpnn_loss_grad(amg_hierarchy* h, const float* w, int32_t nprobe, uint64_t seed, double* loss,
+                       double* grad);
+
+/* One Adam step (Kingma and Ba 2015) on w with gradient grad (FP64) and
+ * moments m, v (FP32, zero before the first step); t counts steps from 1.
+ * AMG_ERR_ARG on NULL pointers or parameters out of range. */
+int amg_mpnn_adam(amg_hierarchy* h, float* w, const double* grad, float* m, float* v, int32_t t, float lr,
+                  float beta1, float beta2, float eps);
+
+/* `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on the
+ * loss of amg_mpnn_loss_grad with probe seed seed + step; w (device) is
+ * updated in place; loss_hist (host, optional) receives each step's loss
+ * before its update.  Errors as amg_mpnn_loss_grad. */
+int amg_mpnn_train(amg_hierarchy* h, float* w, int32_t steps, int32_t nprobe, uint64_t seed, float lr,
+                   double* loss_hist);
+
+/* Fallback rule: solve K u = F (F device, u0 = 0) with the plain smoother
+ * and with the network's damping (BF16 weights); keep the learned damping
+ * installed only if it converged in no more iterations than the plain one,
+ * else restore the plain smoother.  *used = 1 if the learned damping stays;
+ * the two iteration counts are returned.  Not for batch hierarchies
+ * (AMG_ERR_ARG). */
+int amg_mpnn_select(amg_hierarchy* h, const float* w, const double* F, double rtol, int32_t itmax, int32_t* used,
+                    int32_t* iters_plain, int32_t* iters_learned);
+
 /* Release the hierarchy and its device memory. */
 int amg_free(amg_hierarchy* h);
 

@@ -57,22 +57,14 @@ def pack(d):
 
 
 def init_weights(seed=1):
-    """Reference initialisation (scaled uniform from SplitMix64), c such that
-    omega = 1 when the network output q . h2 is zero."""
+    """Seeded initial weights: the shared input generator's recipe (scaled
+    uniform SplitMix64 draws, zero biases, q scaled by 0.1, so that omega
+    starts near 1)."""
     from paper_2511_21268_gb300 import inputs as I
 
-    u = I.rng_u01(seed, NPARAM) * 2.0 - 1.0
-    d, o = {}, 0
-    for name, shape in LAYOUT:
-        k = int(np.prod(shape))
-        fan = shape[1] if len(shape) == 2 else HIDDEN
-        d[name] = (u[o:o + k] * np.sqrt(3.0 / fan)).reshape(shape)
-        o += k
-    for b in ("b0", "b1", "b2"):
-        d[b] = np.zeros(HIDDEN)
-    d["q"] = d["q"] * 0.1
-    d["c"] = np.zeros(1)
-    return pack(d)
+    w = I.mpnn_init_weights(seed)
+    assert len(w) == NPARAM
+    return w
 
 
 # ---------------------------------------------------------------- features

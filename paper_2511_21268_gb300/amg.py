@@ -91,6 +91,15 @@ _SIGS = {
                                           ctypes.c_void_p]),
     "amg_profile_kernels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "amg_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_mpnn_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "amg_mpnn_omega": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "amg_mpnn_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_mpnn_adam": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int32] + [ctypes.c_float] * 4),
+    "amg_mpnn_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_uint64, ctypes.c_float, ctypes.c_void_p]),
+    "amg_mpnn_select": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                       ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "amg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "amg_last_cuda_error": (ctypes.c_char_p, []),
 }
@@ -333,6 +342,72 @@ def amg_free(h):
     _check(lib().amg_free(h), "amg_free")
 
 
+# ------------------------------------------------------ learned damping
+AMG_MPNN_HIDDEN = 32
+AMG_MPNN_NPARAM = 4353
+
+
+def _dev_weights(w):
+    """FP32 device tensor of the flat weights (copy of a numpy/host array)."""
+    torch = _torch()
+    if isinstance(w, np.ndarray):
+        w = torch.from_numpy(np.ascontiguousarray(w, dtype=np.float32))
+    if w.dtype != torch.float32 or not w.is_cuda:
+        w = w.to(device="cuda", dtype=torch.float32)
+    w = w.contiguous()
+    if w.numel() != AMG_MPNN_NPARAM:
+        raise ValueError(f"expected {AMG_MPNN_NPARAM} weights, got {w.numel()}")
+    return w
+
+
+def amg_mpnn_apply(h, w, bf16_weights: bool = True):
+    """Install the network's damping (w: weights) or, with w None, the plain
+    smoother diagonal."""
+    wd = None if w is None else _dev_weights(w)
+    _check(lib().amg_mpnn_apply(h, None if wd is None else wd.data_ptr(), int(bf16_weights)), "amg_mpnn_apply")
+
+
+def amg_mpnn_omega(h, level: int, n: int):
+    torch = _torch()
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    _check(lib().amg_mpnn_omega(h, level, out.data_ptr()), "amg_mpnn_omega")
+    return out
+
+
+def amg_mpnn_loss_grad(h, w, nprobe: int, seed: int):
+    """(loss, gradient as an FP64 device tensor)."""
+    torch = _torch()
+    wd = _dev_weights(w)
+    g = torch.empty(AMG_MPNN_NPARAM, dtype=torch.float64, device="cuda")
+    loss = ctypes.c_double()
+    _check(lib().amg_mpnn_loss_grad(h, wd.data_ptr(), nprobe, seed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(loss),
+                                    g.data_ptr()), "amg_mpnn_loss_grad")
+    return loss.value, g
+
+
+def amg_mpnn_adam(h, w, grad, m, v, t: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In-place Adam step on device tensors w, m, v (FP32) with FP64 grad."""
+    _check(lib().amg_mpnn_adam(h, w.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), t, lr, beta1, beta2,
+                               eps), "amg_mpnn_adam")
+
+
+def amg_mpnn_train(h, w, steps: int, nprobe: int, seed: int, lr: float):
+    """Train the FP32 device tensor w in place; returns the loss history."""
+    hist = np.zeros(max(steps, 1))
+    _check(lib().amg_mpnn_train(h, w.data_ptr(), steps, nprobe, seed & 0xFFFFFFFFFFFFFFFF, lr, hist.ctypes.data),
+           "amg_mpnn_train")
+    return hist[:steps]
+
+
+def amg_mpnn_select(h, w, F, rtol: float, itmax: int):
+    """(used, iters_plain, iters_learned) of the fallback rule."""
+    wd = _dev_weights(w)
+    used, ip, il = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().amg_mpnn_select(h, wd.data_ptr(), F.data_ptr(), rtol, itmax, ctypes.byref(used), ctypes.byref(ip),
+                                 ctypes.byref(il)), "amg_mpnn_select")
+    return bool(used.value), ip.value, il.value
+
+
 class Hierarchy:
     """Owning wrapper of an ``amg_hierarchy*``."""
 
@@ -403,6 +478,22 @@ class Hierarchy:
 
     def export_pass(self, l: int, s: int):
         return amg_export_pass(self._h, l, s)
+
+    # learned smoother damping
+    def mpnn_apply(self, w=None, bf16_weights: bool = True):
+        amg_mpnn_apply(self._h, w, bf16_weights)
+
+    def mpnn_omega(self, level: int):
+        return amg_mpnn_omega(self._h, level, self.level_n(level))
+
+    def mpnn_loss_grad(self, w, nprobe: int = 4, seed: int = 99):
+        return amg_mpnn_loss_grad(self._h, w, nprobe, seed)
+
+    def mpnn_train(self, w, steps: int, nprobe: int = 4, seed: int = 1000, lr: float = 1e-2):
+        return amg_mpnn_train(self._h, w, steps, nprobe, seed, lr)
+
+    def mpnn_select(self, w, F, rtol: float = 1e-8, itmax: int = 10000):
+        return amg_mpnn_select(self._h, w, F, rtol, itmax)
 
 
 class BatchHierarchy(Hierarchy):

@@ -475,6 +475,7 @@ int walloc(amg_hierarchy* h, MultiWork& w, T** p, size_t count) {
 void destroy(amg_hierarchy* h) {
     if (!h) return;
     free_multi(h);
+    mpnn_free(h);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     for (void* p : h->allocs) cudaFreeAsync(p, h->s);
     h->allocs.clear();
@@ -502,6 +503,14 @@ int join_caller(amg_hierarchy* h) {
     CK(cudaStreamWaitEvent(h->s, h->evs, 0));
     return AMG_OK;
 }
+
+}  // namespace
+
+namespace amg {
+int join_caller_stream(amg_hierarchy* h) { return join_caller(h); }
+}  // namespace amg
+
+namespace {
 
 int check_opts(const amg_opts& o) {
     if (o.nu_pre < 1 || o.nu_post < 1 || o.nu_pre > 64 || o.nu_post > 64) return AMG_ERR_ARG;

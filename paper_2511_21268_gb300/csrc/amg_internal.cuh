@@ -77,6 +77,8 @@ struct Pass {
     int rounds = 0;
 };
 
+struct MpnnWork;  // learned-damping buffers (mpnn.cu)
+
 struct DevCSR {
     int n = 0;
     int64_t nnz = 0;
@@ -162,6 +164,10 @@ struct amg_hierarchy {
     int* round_active = nullptr;  // active count after each matching round (device)
     // multi-system solves
     amg::MultiWork* mw = nullptr;
+    // learned smoother damping: network buffers, and whether the smoother
+    // diagonals currently hold omega / d instead of 1 / d
+    amg::MpnnWork* mp = nullptr;
+    int damping_learned = 0;
     // block-diagonal batch (amg_setup_batch): systems and their row offsets
     int nsys = 0;
     std::vector<int64_t> sys_off;    // host copy [nsys + 1]
@@ -229,6 +235,10 @@ cudaError_t enqueue_multi_start(amg_hierarchy* h, cudaStream_t s);
 cudaError_t enqueue_multi_iteration(amg_hierarchy* h, cudaStream_t s);
 cudaError_t enqueue_multi_final(amg_hierarchy* h, cudaStream_t s);
 int multi_dot_stride();
+// mpnn.cu
+void mpnn_free(amg_hierarchy* h);
+// amg_api.cu: order the library stream after the caller's stream
+int join_caller_stream(amg_hierarchy* h);
 cudaError_t launch_interleave(int n, int R, int64_t ld, const double* src, double* dst, cudaStream_t s);
 cudaError_t launch_deinterleave(int n, int R, int64_t ld, const double* src, double* dst, cudaStream_t s);
 // batch assembly (setup_kernels.cu)

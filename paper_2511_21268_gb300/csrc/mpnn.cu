@@ -1,0 +1,907 @@
+// Learned per-row smoother damping (the paper has no learned component).
+//
+// The l1-Jacobi smoother of Sec. 3.2 is scaled per row,
+//   x <- x + diag(omega_i / d_i) (f - K x),   omega_i in (0, 2),
+// which stays convergent in the K-norm for every such omega because D_l1 - K
+// is positive semidefinite.  omega comes from a two-layer message-passing
+// network over each level's matrix graph (the same weights on every level);
+// applying it only rescales each level's 1/d_i, so the FP64 and
+// mixed-precision V-cycle kernels run the learned smoother unchanged.
+//
+// Network (hidden width 32):
+//   node features  x_i = [rho_i, sig_i, log2(nnz_i) / 8, 1],
+//                  rho_i = sum_{j!=i} |k_ij| / k_ii, sig_i = sum_{j!=i} k_ij / k_ii
+//   edge weights   a_ij = k_ij / sqrt(k_ii k_jj)  (j != i; a_ii = 0)
+//   h0 = relu(W0 x + b0); m_l = sum_j a_ij h_{l-1,j};
+//   h_l = relu(U_l m_l + V_l h_{l-1} + b_l) (l = 1, 2); omega = 2 sigmoid(q.h2 + c)
+// Training loss over probe vectors x_k (SplitMix64 uniform in (-1, 1)):
+//   L = (1/m) sum_k log(y_k^T K y_k / x_k^T K x_k),  y_k = x_k - B_omega K x_k,
+// B_omega the V-cycle (one pre- and one post-sweep, exact coarsest solve).
+// The gradient runs the V-cycle steps backwards (FP64; the coarsest solve's
+// adjoint is a second solve with the same symmetric inverse), then the
+// network backwards (FP32 per node, per-block FP32 partial sums of the
+// weight gradients added over blocks in FP64 in block order: deterministic).
+//
+// Layout: node-major [n][32] FP32 activations, a warp per node with
+// lane = hidden unit; the aggregation is a 32-column SpMM over the level's
+// CSR (one coalesced 128-byte row of h per stored entry); layer weights
+// staged in shared memory, transposed so that a warp reads 32 consecutive
+// words.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "amg_internal.cuh"
+
+namespace amg {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int H = AMG_MPNN_HIDDEN;
+static_assert(H == kWarp, "a warp per node, lane = hidden unit");
+// flat parameter layout: W0[32][4], b0, U1[32][32], V1, b1, U2, V2, b2, q, c
+constexpr int O_W0 = 0, O_B0 = O_W0 + H * 4, O_U1 = O_B0 + H, O_V1 = O_U1 + H * H, O_B1 = O_V1 + H * H,
+              O_U2 = O_B1 + H, O_V2 = O_U2 + H * H, O_B2 = O_V2 + H * H, O_Q = O_B2 + H, O_C = O_Q + H,
+              O_END = O_C + 1;
+static_assert(O_END == AMG_MPNN_NPARAM, "parameter layout");
+constexpr int kGradBlocks = 256;           // blocks of the weight-gradient kernels
+constexpr int kGradSlots = 2 * H * H + H;  // partial sums one block writes (largest kernel)
+
+__device__ __forceinline__ float round_bf16(float w) { return __bfloat162float(__float2bfloat16_rn(w)); }
+
+// ---------------------------------------------------------------- features
+__global__ void k_nn_features(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                              const double* __restrict__ v, const double* __restrict__ kii, float* __restrict__ x,
+                              float* __restrict__ ap) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        const double ki = kii[i];
+        const double si = 1.0 / sqrt(ki);
+        double ab = 0.0, sg = 0.0;
+        for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
+            const int j = ci[k];
+            const double a = v[k];
+            float out = 0.f;
+            if (j != i) {
+                ab += fabs(a);
+                sg += a;
+                out = (float)(si * a * (1.0 / sqrt(kii[j])));
+            }
+            ap[k] = out;
+        }
+        ab = warp_sum(ab);
+        sg = warp_sum(sg);
+        if (lane == 0) {
+            x[4 * (int64_t)i + 0] = (float)(ab / ki);
+            x[4 * (int64_t)i + 1] = (float)(sg / ki);
+            x[4 * (int64_t)i + 2] = (float)(log2((double)(rp[i + 1] - rp[i])) / 8.0);
+            x[4 * (int64_t)i + 3] = 1.f;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ forward
+// One layer's weights in shared memory; Ut[k][j] = U[j][k] so that lane j
+// reads consecutive words.
+struct NetSmem {
+    float W0t[4 * H], b0[H], Ut[H * H], Vt[H * H], b[H], q[H], c;
+};
+
+__device__ void load_net(const float* __restrict__ w, NetSmem& s, int layer, int bf16) {
+    auto rd = [&](int o) { return bf16 ? round_bf16(w[o]) : w[o]; };
+    const int oU = layer == 1 ? O_U1 : O_U2, oV = layer == 1 ? O_V1 : O_V2, oB = layer == 1 ? O_B1 : O_B2;
+    for (int t = threadIdx.x; t < H * 4; t += blockDim.x) s.W0t[(t & 3) * H + (t >> 2)] = rd(O_W0 + t);
+    for (int t = threadIdx.x; t < H; t += blockDim.x) {
+        s.b0[t] = rd(O_B0 + t);
+        s.b[t] = rd(oB + t);
+        s.q[t] = rd(O_Q + t);
+    }
+    for (int t = threadIdx.x; t < H * H; t += blockDim.x) {
+        const int j = t / H, k = t % H;  // source U[j][k]
+        s.Ut[k * H + j] = rd(oU + t);
+        s.Vt[k * H + j] = rd(oV + t);
+    }
+    if (threadIdx.x == 0) s.c = rd(O_C);
+    __syncthreads();
+}
+
+// h0 = relu(u0), u0 = W0 x + b0
+__global__ void __launch_bounds__(kBlock) k_nn_in(int n, const float* __restrict__ w, int bf16,
+                                                   const float* __restrict__ x, float* __restrict__ u0,
+                                                   float* __restrict__ h0) {
+    __shared__ NetSmem s;
+    load_net(w, s, 1, bf16);
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        const float4 xi = *reinterpret_cast<const float4*>(x + 4 * (int64_t)i);
+        float u = s.b0[lane];
+        u = fmaf(s.W0t[0 * H + lane], xi.x, u);
+        u = fmaf(s.W0t[1 * H + lane], xi.y, u);
+        u = fmaf(s.W0t[2 * H + lane], xi.z, u);
+        u = fmaf(s.W0t[3 * H + lane], xi.w, u);
+        u0[(int64_t)i * H + lane] = u;
+        h0[(int64_t)i * H + lane] = fmaxf(u, 0.f);
+    }
+}
+
+// out = base + A' h: a warp per row, lane = hidden unit; 32 entries' (a, j)
+// are loaded at once (coalesced) and broadcast by shuffles.  A' is
+// symmetric, so this also applies A'^T in the backward pass.
+__global__ void __launch_bounds__(kBlock) k_nn_spmm(int n, const int64_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ ci, const float* __restrict__ ap,
+                                                     const float* __restrict__ h, const float* __restrict__ base,
+                                                     float* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        float acc0 = base ? base[(int64_t)i * H + lane] : 0.f, acc1 = 0.f;
+        const int64_t k0 = rp[i], k1 = rp[i + 1];
+        for (int64_t kb = k0; kb < k1; kb += 32) {
+            const int cnt = k1 - kb < 32 ? (int)(k1 - kb) : 32;
+            float a = 0.f;
+            int j = 0;
+            if (lane < cnt) {
+                a = ap[kb + lane];
+                j = ci[kb + lane];
+            }
+            int t = 0;
+            for (; t + 1 < cnt; t += 2) {
+                const float a0 = __shfl_sync(FULL, a, t), a1 = __shfl_sync(FULL, a, t + 1);
+                const int j0 = __shfl_sync(FULL, j, t), j1 = __shfl_sync(FULL, j, t + 1);
+                acc0 = fmaf(a0, h[(int64_t)j0 * H + lane], acc0);
+                acc1 = fmaf(a1, h[(int64_t)j1 * H + lane], acc1);
+            }
+            if (t < cnt) {
+                const float a0 = __shfl_sync(FULL, a, t);
+                const int j0 = __shfl_sync(FULL, j, t);
+                acc0 = fmaf(a0, h[(int64_t)j0 * H + lane], acc0);
+            }
+        }
+        out[(int64_t)i * H + lane] = acc0 + acc1;
+    }
+}
+
+// u = U m + V hp + b, h = relu(u); layer 2 also forms sigmoid(z) and omega.
+__global__ void __launch_bounds__(kBlock) k_nn_dense(int n, const float* __restrict__ w, int bf16, int layer,
+                                                      const float* __restrict__ m, const float* __restrict__ hp,
+                                                      float* __restrict__ u, float* __restrict__ h,
+                                                      float* __restrict__ sg, float* __restrict__ omega) {
+    __shared__ NetSmem s;
+    load_net(w, s, layer, bf16);
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        const float mi = m[(int64_t)i * H + lane], hi = hp[(int64_t)i * H + lane];
+        float a0 = s.b[lane], a1 = 0.f;
+#pragma unroll
+        for (int k = 0; k < H; k++) {
+            a0 = fmaf(s.Ut[k * H + lane], __shfl_sync(FULL, mi, k), a0);
+            a1 = fmaf(s.Vt[k * H + lane], __shfl_sync(FULL, hi, k), a1);
+        }
+        const float acc = a0 + a1;
+        u[(int64_t)i * H + lane] = acc;
+        const float hh = fmaxf(acc, 0.f);
+        h[(int64_t)i * H + lane] = hh;
+        if (layer == 2) {
+            const float t = warp_sumf(s.q[lane] * hh);
+            if (lane == 0) {
+                const float sgm = 1.f / (1.f + expf(-(t + s.c)));
+                sg[i] = sgm;
+                omega[i] = 2.f * sgm;
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------- backward
+// Fixed-order sum of one value per lane over the block's warps; warp 0
+// writes the 32 sums to dst.
+__device__ __forceinline__ void block_lane_sum(float (&red)[kWarpsPerBlock][H], float v, float* dst) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    red[wid][lane] = v;
+    __syncthreads();
+    if (wid == 0) {
+        float t = 0.f;
+        for (int k = 0; k < kWarpsPerBlock; k++) t += red[k][lane];
+        dst[lane] = t;
+    }
+    __syncthreads();
+}
+
+// dz = domega 2 sg (1 - sg); partials dq[j] = sum dz h2[j] (slots [0, H)),
+// dc = sum dz (slot H); du2 = dz q [u2 > 0]
+__global__ void __launch_bounds__(kBlock) k_nn_out_bwd(int n, const float* __restrict__ w,
+                                                        const double* __restrict__ domega,
+                                                        const float* __restrict__ sg, const float* __restrict__ h2,
+                                                        const float* __restrict__ u2, float* __restrict__ du2,
+                                                        float* __restrict__ part) {
+    __shared__ float red[kWarpsPerBlock][H];
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const float q = w[O_Q + lane];
+    float aq = 0.f, ac = 0.f;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        const float s = sg[i];
+        const float dz = (float)domega[i] * 2.f * s * (1.f - s);
+        aq = fmaf(dz, h2[(int64_t)i * H + lane], aq);
+        ac += dz;
+        du2[(int64_t)i * H + lane] = u2[(int64_t)i * H + lane] > 0.f ? dz * q : 0.f;
+    }
+    float* out = part + (int64_t)blockIdx.x * kGradSlots;
+    block_lane_sum(red, aq, out);
+    block_lane_sum(red, lane == 0 ? ac : 0.f, out + H);  // slot H holds dc; H+1.. get zeros
+}
+
+// Dense layer backward: dm = U^T du, dhp = V^T du; partials dU = du m^T
+// (slot k H + j for U[j][k]), dV = du hp^T (slot H H + k H + j), db = du
+// (slot 2 H H + j).
+__global__ void __launch_bounds__(kBlock) k_nn_dense_bwd(int n, const float* __restrict__ w, int layer,
+                                                          const float* __restrict__ du, const float* __restrict__ m,
+                                                          const float* __restrict__ hp, float* __restrict__ dm,
+                                                          float* __restrict__ dhp, float* __restrict__ part) {
+    __shared__ float Us[H * H], Vs[H * H];
+    __shared__ float red[kWarpsPerBlock][H];
+    const int oU = layer == 1 ? O_U1 : O_U2, oV = layer == 1 ? O_V1 : O_V2;
+    for (int t = threadIdx.x; t < H * H; t += blockDim.x) {
+        Us[t] = w[oU + t];
+        Vs[t] = w[oV + t];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    float gU[H], gV[H], gb = 0.f;
+#pragma unroll
+    for (int k = 0; k < H; k++) gU[k] = gV[k] = 0.f;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        const float dj = du[(int64_t)i * H + lane];  // lane as output unit j
+        const float mk = m[(int64_t)i * H + lane];   // lane as input unit k
+        const float hk = hp[(int64_t)i * H + lane];
+        float am = 0.f, ah = 0.f;
+#pragma unroll
+        for (int j = 0; j < H; j++) {
+            const float dd = __shfl_sync(FULL, dj, j);
+            am = fmaf(Us[j * H + lane], dd, am);
+            ah = fmaf(Vs[j * H + lane], dd, ah);
+        }
+        dm[(int64_t)i * H + lane] = am;
+        dhp[(int64_t)i * H + lane] = ah;
+#pragma unroll
+        for (int k = 0; k < H; k++) {
+            gU[k] = fmaf(dj, __shfl_sync(FULL, mk, k), gU[k]);
+            gV[k] = fmaf(dj, __shfl_sync(FULL, hk, k), gV[k]);
+        }
+        gb += dj;
+    }
+    float* out = part + (int64_t)blockIdx.x * kGradSlots;
+#pragma unroll
+    for (int k = 0; k < H; k++) {
+        block_lane_sum(red, gU[k], out + k * H);
+        block_lane_sum(red, gV[k], out + H * H + k * H);
+    }
+    block_lane_sum(red, gb, out + 2 * H * H);
+}
+
+// dh *= [u > 0] (in place), over cnt entries
+__global__ void k_nn_relu_mask(int64_t cnt, const float* __restrict__ u, float* __restrict__ dh) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g < cnt && !(u[g] > 0.f)) dh[g] = 0.f;
+}
+
+// partials dW0[j][f] = sum du0[j] x[f] (slot f H + j), db0 (slot 4 H + j)
+__global__ void __launch_bounds__(kBlock) k_nn_in_bwd(int n, const float* __restrict__ du0,
+                                                       const float* __restrict__ x, float* __restrict__ part) {
+    __shared__ float red[kWarpsPerBlock][H];
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    float g[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        const float dj = du0[(int64_t)i * H + lane];
+        const float4 xi = *reinterpret_cast<const float4*>(x + 4 * (int64_t)i);
+        g[0] = fmaf(dj, xi.x, g[0]);
+        g[1] = fmaf(dj, xi.y, g[1]);
+        g[2] = fmaf(dj, xi.z, g[2]);
+        g[3] = fmaf(dj, xi.w, g[3]);
+        g[4] += dj;
+    }
+    float* out = part + (int64_t)blockIdx.x * kGradSlots;
+#pragma unroll
+    for (int f = 0; f < 5; f++) block_lane_sum(red, g[f], out + f * H);
+}
+
+// gacc[dst[t]] += sum over blocks (in block order, FP64) of slot t
+__global__ void k_nn_grad_sum(int nblocks, const float* __restrict__ part, int count, const int* __restrict__ dst,
+                              double* __restrict__ gacc) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; b++) s += (double)part[(int64_t)b * kGradSlots + t];
+    gacc[dst[t]] += s;
+}
+
+// ------------------------------------------------ damped V-cycle (FP64)
+// out = y + s K x  (y may be NULL), a warp per row
+__global__ void __launch_bounds__(kBlock) k_v_spmv(int n, const int64_t* __restrict__ rp,
+                                                    const int32_t* __restrict__ ci, const double* __restrict__ v,
+                                                    const double* __restrict__ x, const double* __restrict__ y,
+                                                    double s, double* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        double acc = 0.0;
+        for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) acc = fma(v[k], x[ci[k]], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) out[i] = (y ? y[i] : 0.0) + s * acc;
+    }
+}
+
+// out = a + (omega / d) b   (a may be NULL)
+__global__ void k_v_damp(int n, const double* __restrict__ a, const float* __restrict__ om,
+                         const double* __restrict__ d, const double* __restrict__ b, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (a ? a[i] : 0.0) + ((double)om[i] / d[i]) * b[i];
+}
+
+// dom += g r / d
+__global__ void k_v_domega(int n, const double* __restrict__ g, const double* __restrict__ r,
+                           const double* __restrict__ d, double* __restrict__ dom) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dom[i] += g[i] * r[i] / d[i];
+}
+
+// fc = P^T r over each coarse row's members (ascending)
+__global__ void k_v_restrict(int nc, const int32_t* __restrict__ mptr, const int32_t* __restrict__ midx,
+                             const double* __restrict__ pval, const double* __restrict__ r, double* __restrict__ fc) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    double acc = 0.0;
+    for (int m = mptr[I]; m < mptr[I + 1]; m++) acc = fma(pval[midx[m]], r[midx[m]], acc);
+    fc[I] = acc;
+}
+
+// out = a + P e  (a may be NULL)
+__global__ void k_v_prolong(int n, const int32_t* __restrict__ agg, const double* __restrict__ pval,
+                            const double* __restrict__ e, const double* __restrict__ a, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (a ? a[i] : 0.0) + pval[i] * e[agg[i]];
+}
+
+// out = A^-1 f with the dense symmetric inverse of the coarsest matrix
+__global__ void k_v_dense(int nd, const double* __restrict__ Ainv, const double* __restrict__ f,
+                          double* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (I >= nd) return;
+    double s = 0.0;
+    for (int j = lane; j < nd; j += 32) s = fma(Ainv[(int64_t)I * nd + j], f[j], s);
+    s = warp_sum(s);
+    if (lane == 0) out[I] = s;
+}
+
+// out = dr2 + dr1 + (omega / d) dx1  (the three contributions to d loss / d f)
+__global__ void k_v_df(int n, const double* __restrict__ dr2, const double* __restrict__ dr1,
+                       const float* __restrict__ om, const double* __restrict__ d, const double* __restrict__ dx1,
+                       double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (dr2[i] + dr1[i]) + ((double)om[i] / d[i]) * dx1[i];
+}
+
+// probe x_i = 2 U - 1, U = top 53 bits of draw (k n + i) of SplitMix64(seed) / 2^53
+__global__ void k_v_probe(int n, uint64_t seed, int k, double* __restrict__ x) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const uint64_t z = splitmix64_at(seed, (uint64_t)k * (uint64_t)n + (uint64_t)i);
+        x[i] = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+    }
+}
+
+__global__ void k_v_sub(int n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] - b[i];
+}
+
+// dots[0] = a.b, dots[1] = c.d (one block, fixed order)
+__global__ void __launch_bounds__(1024) k_v_dot2(int n, const double* __restrict__ a, const double* __restrict__ b,
+                                                 const double* __restrict__ c, const double* __restrict__ d,
+                                                 double* __restrict__ dots) {
+    __shared__ double s1[32], s2[32];
+    double t1 = 0.0, t2 = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        t1 = fma(a[i], b[i], t1);
+        t2 = fma(c[i], d[i], t2);
+    }
+    t1 = warp_sum(t1);
+    t2 = warp_sum(t2);
+    if ((threadIdx.x & 31) == 0) {
+        s1[threadIdx.x >> 5] = t1;
+        s2[threadIdx.x >> 5] = t2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u1 = 0.0, u2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            u1 += s1[w];
+            u2 += s2[w];
+        }
+        dots[0] = u1;
+        dots[1] = u2;
+    }
+}
+
+// loss += (log(y.Ky) - log(x.Kx)) / m; gbar = -2 Ky / (y.Ky) / m
+// (d/dz of log(y^T K y) with y = x - z); flags a non-positive quotient
+__global__ void k_v_lossgrad(int n, const double* __restrict__ Ky, const double* __restrict__ dots, double inv_m,
+                             double* __restrict__ gbar, double* __restrict__ loss, int* __restrict__ bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double yKy = dots[0], xKx = dots[1];
+    const bool ok = yKy > 0.0 && xKx > 0.0;
+    if (i < n) gbar[i] = ok ? -2.0 * Ky[i] / yKy * inv_m : 0.0;
+    if (i == 0) {
+        if (ok)
+            *loss += (log(yKy) - log(xKx)) * inv_m;
+        else
+            *bad = 1;
+    }
+}
+
+// Adam (Kingma and Ba, 2015) on the flat weights; t counts from 1
+__global__ void k_adam(int n, float* __restrict__ w, const double* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int t, float lr, float b1, float b2, float eps) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = (float)g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / (1.f - powf(b1, (float)t)), vh = vi / (1.f - powf(b2, (float)t));
+    w[i] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+// smoother diagonal: invd = omega / dl1 (omega NULL: the plain 1 / dl1,
+// rounded as in setup) and its FP32 copy
+__global__ void k_set_damping(int n, const float* __restrict__ om, const double* __restrict__ dl1,
+                              double* __restrict__ invd, float* __restrict__ invd32) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = om ? (double)om[i] / dl1[i] : __ddiv_rn(1.0, dl1[i]);
+    invd[i] = v;
+    if (invd32) invd32[i] = __double2float_rn(v);
+}
+
+inline int eblk(int64_t n) { return (int)std::max<int64_t>(1, (n + kBlock - 1) / kBlock); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+// Per-level buffers of the network and of the differentiated V-cycle.
+struct MpnnLevel {
+    static constexpr int kTape = 8;  // u0 h0 m1 u1 h1 m2 u2 h2, [n][32] each
+    static constexpr int kVec = 7;   // FP64 V-cycle vectors
+    float* x = nullptr;              // features [n][4]
+    float* ap = nullptr;             // normalised off-diagonal values [nnz]
+    float* t[kTape] = {};
+    float* sg = nullptr;  // sigmoid(z)
+    float* omega = nullptr;
+    double* domega = nullptr;
+    double* v[kVec] = {};
+};
+
+struct MpnnWork {
+    MpnnLevel lev[AMG_MAX_LEVELS];
+    float* bw[3] = {};       // backward scratch, [n0][32] each
+    float* part = nullptr;   // per-block gradient partials
+    double* gacc = nullptr;  // FP64 gradient accumulator
+    double *px = nullptr, *py = nullptr, *pky = nullptr;  // probe, y, K y
+    double* dots = nullptr;
+    double* loss = nullptr;
+    int* bad = nullptr;
+    int* dst = nullptr;  // [4][kGradSlots] slot -> weight index maps
+    float *adam_m = nullptr, *adam_v = nullptr;
+    int have_omega = 0;  // omega of a network evaluation present
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+int grid_rows(const amg_hierarchy* h, int64_t n) {
+    const int64_t cap = (int64_t)std::max(1, h->num_sms) * 8;
+    return (int)std::min<int64_t>(std::max<int64_t>(1, (n + kWarpsPerBlock - 1) / kWarpsPerBlock), cap);
+}
+int grid_grad(int64_t n) {
+    return (int)std::min<int64_t>(std::max<int64_t>(1, (n + kWarpsPerBlock - 1) / kWarpsPerBlock), kGradBlocks);
+}
+
+int status_of(cudaError_t e) {
+    if (e == cudaSuccess) return AMG_OK;
+    return e == cudaErrorMemoryAllocation ? AMG_ERR_NOMEM : AMG_ERR_CUDA;
+}
+
+int mp_alloc(amg_hierarchy* h, void** p, size_t bytes) {
+    cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, h->s);
+    if (e != cudaSuccess) return status_of(e);
+    h->mp->allocs.push_back(*p);
+    return AMG_OK;
+}
+
+#define MP_ALLOC(ptr, bytes)                                               \
+    do {                                                                   \
+        int r__ = mp_alloc(h, reinterpret_cast<void**>(&(ptr)), (bytes));  \
+        if (r__ != AMG_OK) return r__;                                     \
+    } while (0)
+
+#define MP_CK(expr)                           \
+    do {                                      \
+        int r__ = status_of(expr);            \
+        if (r__ != AMG_OK) return r__;        \
+    } while (0)
+
+// Allocate the network and training buffers and compute every level's
+// features (once per hierarchy).
+int prepare(amg_hierarchy* h) {
+    if (h->mp) return AMG_OK;
+    h->mp = new (std::nothrow) MpnnWork();
+    if (!h->mp) return AMG_ERR_NOMEM;
+    MpnnWork& w = *h->mp;
+    cudaStream_t s = h->s;
+    const int64_t n0 = h->lev[0].A.n;
+    for (int l = 0; l < h->nlev; l++) {
+        Level& L = h->lev[l];
+        MpnnLevel& m = w.lev[l];
+        const int64_t n = L.A.n;
+        MP_ALLOC(m.x, sizeof(float) * 4 * n);
+        MP_ALLOC(m.ap, sizeof(float) * L.A.nnz);
+        for (int t = 0; t < MpnnLevel::kTape; t++) MP_ALLOC(m.t[t], sizeof(float) * H * n);
+        MP_ALLOC(m.sg, sizeof(float) * n);
+        MP_ALLOC(m.omega, sizeof(float) * n);
+        MP_ALLOC(m.domega, sizeof(double) * n);
+        for (int t = 0; t < MpnnLevel::kVec; t++) MP_ALLOC(m.v[t], sizeof(double) * n);
+        k_nn_features<<<AMG_GRID(grid_rows(h, n)), kBlock, 0, s>>>((int)n, L.A.rowptr, L.A.col, L.A.val, L.kii, m.x,
+                                                                     m.ap);
+    }
+    for (int t = 0; t < 3; t++) MP_ALLOC(w.bw[t], sizeof(float) * H * n0);
+    MP_ALLOC(w.part, sizeof(float) * kGradBlocks * kGradSlots);
+    MP_ALLOC(w.gacc, sizeof(double) * AMG_MPNN_NPARAM);
+    MP_ALLOC(w.px, sizeof(double) * n0);
+    MP_ALLOC(w.py, sizeof(double) * n0);
+    MP_ALLOC(w.pky, sizeof(double) * n0);
+    MP_ALLOC(w.dots, sizeof(double) * 2);
+    MP_ALLOC(w.loss, sizeof(double));
+    MP_ALLOC(w.bad, sizeof(int));
+    MP_ALLOC(w.dst, sizeof(int) * 4 * kGradSlots);
+    MP_ALLOC(w.adam_m, sizeof(float) * AMG_MPNN_NPARAM);
+    MP_ALLOC(w.adam_v, sizeof(float) * AMG_MPNN_NPARAM);
+    // slot -> flat weight index for the four backward kernels
+    std::vector<int> dst(4 * kGradSlots, 0);
+    int* d_out = dst.data();
+    int* d_l2 = d_out + kGradSlots;
+    int* d_l1 = d_l2 + kGradSlots;
+    int* d_in = d_l1 + kGradSlots;
+    for (int j = 0; j < H; j++) d_out[j] = O_Q + j;
+    d_out[H] = O_C;
+    for (int k = 0; k < H; k++)
+        for (int j = 0; j < H; j++) {
+            d_l2[k * H + j] = O_U2 + j * H + k;
+            d_l2[H * H + k * H + j] = O_V2 + j * H + k;
+            d_l1[k * H + j] = O_U1 + j * H + k;
+            d_l1[H * H + k * H + j] = O_V1 + j * H + k;
+        }
+    for (int j = 0; j < H; j++) {
+        d_l2[2 * H * H + j] = O_B2 + j;
+        d_l1[2 * H * H + j] = O_B1 + j;
+    }
+    for (int f = 0; f < 4; f++)
+        for (int j = 0; j < H; j++) d_in[f * H + j] = O_W0 + j * 4 + f;
+    for (int j = 0; j < H; j++) d_in[4 * H + j] = O_B0 + j;
+    MP_CK(cudaMemcpyAsync(w.dst, dst.data(), sizeof(int) * dst.size(), cudaMemcpyHostToDevice, s));
+    MP_CK(cudaStreamSynchronize(s));  // dst is a host stack vector
+    MP_CK(cudaGetLastError());
+    return AMG_OK;
+}
+
+// omega of levels [0, nlev - 1) from the network (FP32 arithmetic; weights
+// rounded to BF16 first when bf16 != 0).  The coarsest level has no smoother.
+cudaError_t net_forward(amg_hierarchy* h, const float* wd, int bf16) {
+    MpnnWork& w = *h->mp;
+    cudaStream_t s = h->s;
+    for (int l = 0; l + 1 < h->nlev; l++) {
+        Level& L = h->lev[l];
+        MpnnLevel& m = w.lev[l];
+        const int n = L.A.n;
+        const int g = grid_rows(h, n);
+        float *u0 = m.t[0], *h0 = m.t[1], *m1 = m.t[2], *u1 = m.t[3], *h1 = m.t[4], *m2 = m.t[5], *u2 = m.t[6],
+              *h2 = m.t[7];
+        k_nn_in<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, m.x, u0, h0);
+        k_nn_spmm<<<AMG_GRID(g), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, m.ap, h0, nullptr, m1);
+        k_nn_dense<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, 1, m1, h0, u1, h1, nullptr, nullptr);
+        k_nn_spmm<<<AMG_GRID(g), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, m.ap, h1, nullptr, m2);
+        k_nn_dense<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, 2, m2, h1, u2, h2, m.sg, m.omega);
+    }
+    w.have_omega = 1;
+    return cudaGetLastError();
+}
+
+// Network backward of level l given its domega; gradients added to gacc.
+cudaError_t net_backward(amg_hierarchy* h, const float* wd, int l) {
+    MpnnWork& w = *h->mp;
+    cudaStream_t s = h->s;
+    Level& L = h->lev[l];
+    MpnnLevel& m = w.lev[l];
+    const int n = L.A.n;
+    const int g = grid_rows(h, n), gg = grid_grad(n);
+    const int64_t cnt = (int64_t)n * H;
+    float *u0 = m.t[0], *h0 = m.t[1], *m1 = m.t[2], *u1 = m.t[3], *h1 = m.t[4], *m2 = m.t[5], *u2 = m.t[6],
+          *h2 = m.t[7];
+    float *b0 = w.bw[0], *b1 = w.bw[1], *b2 = w.bw[2];
+    const int gs = eblk(kGradSlots);
+    k_nn_out_bwd<<<AMG_GRID(gg), kBlock, 0, s>>>(n, wd, m.domega, m.sg, h2, u2, b0, w.part);
+    k_nn_grad_sum<<<AMG_GRID(gs), kBlock, 0, s>>>(gg, w.part, H + 1, w.dst, w.gacc);
+    // layer 2: du2 (b0) -> dm2 (b1), V2^T du2 (b2); dh1 = A' dm2 + V2^T du2 (b0)
+    k_nn_dense_bwd<<<AMG_GRID(gg), kBlock, 0, s>>>(n, wd, 2, b0, m2, h1, b1, b2, w.part);
+    k_nn_grad_sum<<<AMG_GRID(gs), kBlock, 0, s>>>(gg, w.part, 2 * H * H + H, w.dst + kGradSlots, w.gacc);
+    k_nn_spmm<<<AMG_GRID(g), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, m.ap, b1, b2, b0);
+    k_nn_relu_mask<<<AMG_GRID(eblk(cnt)), kBlock, 0, s>>>(cnt, u1, b0);
+    // layer 1
+    k_nn_dense_bwd<<<AMG_GRID(gg), kBlock, 0, s>>>(n, wd, 1, b0, m1, h0, b1, b2, w.part);
+    k_nn_grad_sum<<<AMG_GRID(gs), kBlock, 0, s>>>(gg, w.part, 2 * H * H + H, w.dst + 2 * kGradSlots, w.gacc);
+    k_nn_spmm<<<AMG_GRID(g), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, m.ap, b1, b2, b0);
+    k_nn_relu_mask<<<AMG_GRID(eblk(cnt)), kBlock, 0, s>>>(cnt, u0, b0);
+    // input layer
+    k_nn_in_bwd<<<AMG_GRID(gg), kBlock, 0, s>>>(n, b0, m.x, w.part);
+    k_nn_grad_sum<<<AMG_GRID(gs), kBlock, 0, s>>>(gg, w.part, 5 * H, w.dst + 3 * kGradSlots, w.gacc);
+    return cudaGetLastError();
+}
+
+// Vector slots of a level in the differentiated V-cycle.
+enum { V_F = 0, V_X1, V_R, V_X2, V_OUT, V_G, V_T };
+
+// Damped V-cycle from level l on f = v[V_F] into v[V_OUT], keeping the tape
+// (f in V_F, r2 in V_R):
+//   x1 = Dw f; r1 = f - K x1; e = V_{l+1}(P^T r1); x2 = x1 + P e;
+//   r2 = f - K x2; out = x2 + Dw r2,   Dw = diag(omega / d)
+void vcycle_fwd(amg_hierarchy* h, int l) {
+    MpnnWork& w = *h->mp;
+    cudaStream_t s = h->s;
+    Level& L = h->lev[l];
+    MpnnLevel& m = w.lev[l];
+    const int n = L.A.n;
+    if (l == h->nlev - 1) {
+        k_v_dense<<<AMG_GRID(eblk((int64_t)n * 32)), kBlock, 0, s>>>(n, h->Ainv, m.v[V_F], m.v[V_OUT]);
+        return;
+    }
+    Level& C = h->lev[l + 1];
+    MpnnLevel& mc = w.lev[l + 1];
+    const int gr = grid_rows(h, n), ge = eblk(n);
+    k_v_damp<<<AMG_GRID(ge), kBlock, 0, s>>>(n, nullptr, m.omega, L.dl1, m.v[V_F], m.v[V_X1]);
+    k_v_spmv<<<AMG_GRID(gr), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, m.v[V_X1], m.v[V_F], -1.0, m.v[V_R]);
+    k_v_restrict<<<AMG_GRID(eblk(C.A.n)), kBlock, 0, s>>>(C.A.n, L.mem_ptr, L.mem_idx, L.pval, m.v[V_R],
+                                                           mc.v[V_F]);
+    vcycle_fwd(h, l + 1);
+    k_v_prolong<<<AMG_GRID(ge), kBlock, 0, s>>>(n, L.agg, L.pval, mc.v[V_OUT], m.v[V_X1], m.v[V_X2]);
+    k_v_spmv<<<AMG_GRID(gr), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, m.v[V_X2], m.v[V_F], -1.0, m.v[V_R]);
+    k_v_damp<<<AMG_GRID(ge), kBlock, 0, s>>>(n, m.v[V_X2], m.omega, L.dl1, m.v[V_R], m.v[V_OUT]);
+}
+
+// Reverse of vcycle_fwd: g = d loss / d out in v[V_G]; d loss / d f into
+// v[V_OUT]; d loss / d omega added to domega.
+void vcycle_bwd(amg_hierarchy* h, int l) {
+    MpnnWork& w = *h->mp;
+    cudaStream_t s = h->s;
+    Level& L = h->lev[l];
+    MpnnLevel& m = w.lev[l];
+    const int n = L.A.n;
+    if (l == h->nlev - 1) {  // A^-1 is symmetric: the adjoint is the same solve
+        k_v_dense<<<AMG_GRID(eblk((int64_t)n * 32)), kBlock, 0, s>>>(n, h->Ainv, m.v[V_G], m.v[V_OUT]);
+        return;
+    }
+    Level& C = h->lev[l + 1];
+    MpnnLevel& mc = w.lev[l + 1];
+    const int gr = grid_rows(h, n), ge = eblk(n);
+    double* g = m.v[V_G];
+    double* dr2 = m.v[V_T];
+    double* dx2 = m.v[V_X2];
+    double* dr1 = m.v[V_X1];
+    // out = x2 + Dw r2: d omega += g r2 / d; dr2 = Dw g; dx2 = g
+    k_v_domega<<<AMG_GRID(ge), kBlock, 0, s>>>(n, g, m.v[V_R], L.dl1, m.domega);
+    k_v_damp<<<AMG_GRID(ge), kBlock, 0, s>>>(n, nullptr, m.omega, L.dl1, g, dr2);
+    // r2 = f - K x2: df = dr2; dx2 = g - K dr2
+    k_v_spmv<<<AMG_GRID(gr), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, dr2, g, -1.0, dx2);
+    // x2 = x1 + P e: dx1 = dx2 (so far); de = P^T dx2
+    k_v_restrict<<<AMG_GRID(eblk(C.A.n)), kBlock, 0, s>>>(C.A.n, L.mem_ptr, L.mem_idx, L.pval, dx2, mc.v[V_G]);
+    vcycle_bwd(h, l + 1);  // d loss / d fc in mc.v[V_OUT]
+    // fc = P^T r1: dr1 = P dfc; r1 = f - K x1: df += dr1, dx1 = dx2 - K dr1
+    k_v_prolong<<<AMG_GRID(ge), kBlock, 0, s>>>(n, L.agg, L.pval, mc.v[V_OUT], nullptr, dr1);
+    double* dx1 = g;  // g is no longer needed
+    k_v_spmv<<<AMG_GRID(gr), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, dr1, dx2, -1.0, dx1);
+    // x1 = Dw f: df += Dw dx1; d omega += dx1 f / d
+    k_v_domega<<<AMG_GRID(ge), kBlock, 0, s>>>(n, dx1, m.v[V_F], L.dl1, m.domega);
+    k_v_df<<<AMG_GRID(ge), kBlock, 0, s>>>(n, dr2, dr1, m.omega, L.dl1, dx1, m.v[V_OUT]);
+}
+
+// Loss and gradient for the weights wd: gradient left in gacc, loss in
+// loss (device).
+int loss_grad_enqueue(amg_hierarchy* h, const float* wd, int nprobe, uint64_t seed) {
+    MpnnWork& w = *h->mp;
+    cudaStream_t s = h->s;
+    Level& L0 = h->lev[0];
+    MpnnLevel& m0 = w.lev[0];
+    const int n = L0.A.n;
+    const int gr = grid_rows(h, n), ge = eblk(n);
+    MP_CK(cudaMemsetAsync(w.loss, 0, sizeof(double), s));
+    MP_CK(cudaMemsetAsync(w.bad, 0, sizeof(int), s));
+    MP_CK(cudaMemsetAsync(w.gacc, 0, sizeof(double) * AMG_MPNN_NPARAM, s));
+    for (int l = 0; l < h->nlev; l++)
+        MP_CK(cudaMemsetAsync(w.lev[l].domega, 0, sizeof(double) * h->lev[l].A.n, s));
+    MP_CK(net_forward(h, wd, 0));
+    const double inv_m = 1.0 / nprobe;
+    for (int k = 0; k < nprobe; k++) {
+        k_v_probe<<<AMG_GRID(ge), kBlock, 0, s>>>(n, seed, k, w.px);
+        // f = K x; z = B f; y = x - z
+        k_v_spmv<<<AMG_GRID(gr), kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, w.px, nullptr, 1.0,
+                                                 m0.v[V_F]);
+        vcycle_fwd(h, 0);
+        k_v_sub<<<AMG_GRID(ge), kBlock, 0, s>>>(n, w.px, m0.v[V_OUT], w.py);
+        k_v_spmv<<<AMG_GRID(gr), kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, w.py, nullptr, 1.0, w.pky);
+        k_v_dot2<<<AMG_GRID(1), 1024, 0, s>>>(n, w.py, w.pky, w.px, m0.v[V_F], w.dots);
+        k_v_lossgrad<<<AMG_GRID(ge), kBlock, 0, s>>>(n, w.pky, w.dots, inv_m, m0.v[V_G], w.loss, w.bad);
+        vcycle_bwd(h, 0);
+    }
+    for (int l = 0; l + 1 < h->nlev; l++) MP_CK(net_backward(h, wd, l));
+    MP_CK(cudaGetLastError());
+    return AMG_OK;
+}
+
+// Install the damping of the last network evaluation (learned) or the plain
+// l1-Jacobi diagonal on every level that has a smoother.
+cudaError_t set_damping(amg_hierarchy* h, bool learned) {
+    cudaStream_t s = h->s;
+    for (int l = 0; l + 1 < h->nlev; l++) {
+        Level& L = h->lev[l];
+        k_set_damping<<<AMG_GRID(eblk(L.A.n)), kBlock, 0, s>>>(L.A.n, learned ? h->mp->lev[l].omega : nullptr, L.dl1,
+                                                                L.invd, L.invd32);
+    }
+    return cudaGetLastError();
+}
+
+int sync_status(amg_hierarchy* h) { return status_of(cudaStreamSynchronize(h->s)); }
+
+template <typename T>
+int read_host(amg_hierarchy* h, const T* dptr, T* out) {
+    MP_CK(cudaMemcpyAsync(h->flag_host, dptr, sizeof(T), cudaMemcpyDeviceToHost, h->s));
+    MP_CK(cudaStreamSynchronize(h->s));
+    memcpy(out, h->flag_host, sizeof(T));
+    return AMG_OK;
+}
+
+}  // namespace
+
+void mpnn_free(amg_hierarchy* h) {
+    if (!h->mp) return;
+    for (void* p : h->mp->allocs) cudaFreeAsync(p, h->s);
+    delete h->mp;
+    h->mp = nullptr;
+}
+
+}  // namespace amg
+
+using namespace amg;
+
+#define MP_RC(expr)                    \
+    do {                               \
+        int r__ = (expr);              \
+        if (r__ != AMG_OK) return r__; \
+    } while (0)
+
+extern "C" {
+
+int amg_mpnn_apply(amg_hierarchy* h, const float* w, int32_t bf16_weights) {
+    if (!h || bf16_weights < 0 || bf16_weights > 1) return AMG_ERR_ARG;
+    MP_RC(join_caller_stream(h));
+    if (w) {
+        MP_RC(prepare(h));
+        MP_RC(status_of(net_forward(h, w, bf16_weights)));
+    }
+    MP_RC(status_of(set_damping(h, w != nullptr)));
+    MP_RC(sync_status(h));
+    h->damping_learned = w != nullptr;
+    return AMG_OK;
+}
+
+int amg_mpnn_omega(amg_hierarchy* h, int32_t level, float* omega) {
+    if (!h || !omega || level < 0 || level + 1 >= h->nlev) return AMG_ERR_ARG;
+    if (!h->mp || !h->mp->have_omega) return AMG_ERR_ARG;
+    MP_RC(join_caller_stream(h));
+    MP_RC(status_of(cudaMemcpyAsync(omega, h->mp->lev[level].omega, sizeof(float) * h->lev[level].A.n,
+                                    cudaMemcpyDeviceToDevice, h->s)));
+    return sync_status(h);
+}
+
+int amg_mpnn_loss_grad(amg_hierarchy* h, const float* w, int32_t nprobe, uint64_t seed, double* loss,
+                       double* grad) {
+    if (!h || !w || !loss || !grad || nprobe < 1 || h->nlev < 2) return AMG_ERR_ARG;
+    MP_RC(join_caller_stream(h));
+    MP_RC(prepare(h));
+    MP_RC(loss_grad_enqueue(h, w, nprobe, seed));
+    MpnnWork& mw = *h->mp;
+    MP_RC(status_of(
+        cudaMemcpyAsync(grad, mw.gacc, sizeof(double) * AMG_MPNN_NPARAM, cudaMemcpyDeviceToDevice, h->s)));
+    double lh = 0.0;
+    int bad = 0;
+    MP_RC(read_host(h, mw.loss, &lh));
+    MP_RC(read_host(h, mw.bad, &bad));
+    *loss = lh;
+    if (bad) return AMG_ERR_BREAKDOWN;
+    return isfinite(lh) ? AMG_OK : AMG_ERR_NAN;
+}
+
+int amg_mpnn_adam(amg_hierarchy* h, float* w, const double* grad, float* m, float* v, int32_t t, float lr,
+                  float beta1, float beta2, float eps) {
+    if (!h || !w || !grad || !m || !v || t < 1 || !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) ||
+        !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+        return AMG_ERR_ARG;
+    MP_RC(join_caller_stream(h));
+    k_adam<<<AMG_GRID(eblk(AMG_MPNN_NPARAM)), kBlock, 0, h->s>>>(AMG_MPNN_NPARAM, w, grad, m, v, t, lr, beta1, beta2,
+                                                                  eps);
+    MP_RC(status_of(cudaGetLastError()));
+    return sync_status(h);
+}
+
+int amg_mpnn_train(amg_hierarchy* h, float* w, int32_t steps, int32_t nprobe, uint64_t seed, float lr,
+                   double* loss_hist) {
+    if (!h || !w || steps < 0 || nprobe < 1 || !(lr > 0.f) || h->nlev < 2) return AMG_ERR_ARG;
+    MP_RC(join_caller_stream(h));
+    MP_RC(prepare(h));
+    MpnnWork& mw = *h->mp;
+    MP_RC(status_of(cudaMemsetAsync(mw.adam_m, 0, sizeof(float) * AMG_MPNN_NPARAM, h->s)));
+    MP_RC(status_of(cudaMemsetAsync(mw.adam_v, 0, sizeof(float) * AMG_MPNN_NPARAM, h->s)));
+    for (int t = 0; t < steps; t++) {
+        MP_RC(loss_grad_enqueue(h, w, nprobe, seed + (uint64_t)t));
+        k_adam<<<AMG_GRID(eblk(AMG_MPNN_NPARAM)), kBlock, 0, h->s>>>(AMG_MPNN_NPARAM, w, mw.gacc, mw.adam_m,
+                                                                      mw.adam_v, t + 1, lr, 0.9f, 0.999f, 1e-8f);
+        MP_RC(status_of(cudaGetLastError()));
+        int bad = 0;
+        MP_RC(read_host(h, mw.bad, &bad));
+        if (bad) return AMG_ERR_BREAKDOWN;
+        if (loss_hist) MP_RC(read_host(h, mw.loss, &loss_hist[t]));
+    }
+    return sync_status(h);
+}
+
+int amg_mpnn_select(amg_hierarchy* h, const float* w, const double* F, double rtol, int32_t itmax, int32_t* used,
+                    int32_t* iters_plain, int32_t* iters_learned) {
+    if (!h || !w || !F || !(rtol > 0.0) || itmax < 1 || h->nsys > 0) return AMG_ERR_ARG;
+    const int n = h->lev[0].A.n;
+    double* u = nullptr;
+    MP_RC(status_of(cudaMallocAsync(&u, sizeof(double) * n, h->s)));
+    struct Release {
+        double* p;
+        cudaStream_t s;
+        ~Release() { cudaFreeAsync(p, s); }
+    } release{u, h->s};
+    int32_t ip = 0, il = 0;
+    MP_RC(amg_mpnn_apply(h, nullptr, 0));
+    MP_RC(status_of(cudaMemsetAsync(u, 0, sizeof(double) * n, h->s)));
+    const int rp = amg_pcg_solve(h, F, u, AMG_MEM_DEVICE, rtol, itmax, &ip, nullptr);
+    if (rp == AMG_ERR_CUDA || rp == AMG_ERR_NOMEM) return rp;
+    MP_RC(amg_mpnn_apply(h, w, 1));
+    MP_RC(status_of(cudaMemsetAsync(u, 0, sizeof(double) * n, h->s)));
+    const int rl = amg_pcg_solve(h, F, u, AMG_MEM_DEVICE, rtol, itmax, &il, nullptr);
+    if (rl == AMG_ERR_CUDA || rl == AMG_ERR_NOMEM) return rl;
+    // keep the learned damping only if it converged in no more iterations
+    const bool keep = rl == AMG_OK && (rp != AMG_OK || il <= ip);
+    if (!keep) MP_RC(amg_mpnn_apply(h, nullptr, 0));
+    if (used) *used = keep ? 1 : 0;
+    if (iters_plain) *iters_plain = ip;
+    if (iters_learned) *iters_learned = il;
+    return AMG_OK;
+}
+
+}  // extern "C"

@@ -262,3 +262,31 @@ def annulus_kappa(n: int, p: int, kappa_seed: int = 7, nq: int | None = None) ->
 
 def annulus_volume() -> float:
     return 0.75 * math.pi
+
+
+# ------------------------------------------------------------ network weights
+# Block layout of the learned-damping network's flat weight vector (hidden
+# width 32, 4 node features): (name, shape) in storage order.
+MPNN_LAYOUT = [("W0", (32, 4)), ("b0", (32,)), ("U1", (32, 32)), ("V1", (32, 32)), ("b1", (32,)),
+               ("U2", (32, 32)), ("V2", (32, 32)), ("b2", (32,)), ("q", (32,)), ("c", (1,))]
+MPNN_NPARAM = sum(int(np.prod(s)) for _, s in MPNN_LAYOUT)
+
+
+def mpnn_init_weights(seed: int = 1) -> np.ndarray:
+    """Seeded initial weights (FP64): entry k of the flat vector is
+    (2 U_k - 1) sqrt(3 / fan_in) with U_k draw k of SplitMix64(seed), fan_in
+    the block's column count (32 for vectors); biases and c are zero and
+    the output weights q are scaled by 0.1, so omega starts near 1."""
+    u = rng_u01(seed, MPNN_NPARAM) * 2.0 - 1.0
+    out, o = [], 0
+    for name, shape in MPNN_LAYOUT:
+        k = int(np.prod(shape))
+        fan = shape[1] if len(shape) == 2 else 32
+        blk = u[o:o + k] * np.sqrt(3.0 / fan)
+        if name in ("b0", "b1", "b2", "c"):
+            blk = np.zeros(k)
+        elif name == "q":
+            blk = blk * 0.1
+        out.append(blk)
+        o += k
+    return np.concatenate(out)

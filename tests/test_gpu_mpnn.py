@@ -1,0 +1,187 @@
+"""Learned smoother damping on the GPU against the oracle (oracle/mpnn.py).
+
+* omega of the network on every level: FP32 weights and BF16-rounded
+  weights, against the oracle's FP64 forward with the same weights
+  (|diff| <= 2e-5; omega is in (0, 2) and the GPU computes in FP32).
+* The installed damping is what the V-cycle runs: GPU V-cycle vs the
+  oracle's damped V-cycle with the GPU's omega (1e-12), and restoring the
+  plain smoother is bitwise.
+* Loss and gradient: the loss with the GPU's omega equals the oracle's
+  FP64 loss for that omega (1e-10); against the oracle's end-to-end
+  loss/gradient for the same weights, loss 1e-5 and gradient 2e-3 relative
+  (FP32 network).  Two runs are bitwise identical.
+* Adam step against the textbook update; training lowers the loss and the
+  PCG iteration count; the fallback rule keeps the plain smoother when the
+  learned one is worse.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle as O  # noqa: E402
+from oracle import mpnn as M  # noqa: E402
+from paper_2511_21268_gb300 import amg as A  # noqa: E402
+from paper_2511_21268_gb300 import inputs as I  # noqa: E402
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def bf16_round(a):
+    """Round FP32 values to the nearest BF16 (ties to even), as FP32."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def varied_weights(seed):
+    """Initial weights with a larger output layer, so omega varies over
+    the rows and spans much of (0, 2)."""
+    d = M.unpack(I.mpnn_init_weights(seed))
+    d["q"] = d["q"] * 20
+    d["c"] = np.array([0.3])
+    d["b1"] = np.full(M.HIDDEN, 0.05)
+    return M.pack(d).astype(np.float32)
+
+
+CASES = [(2, 32, 3), (3, 10, 3)]  # 3-D rows hold up to 343 entries (several 32-entry chunks)
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: "d%d_n%d_p%d" % c)
+def case(request):
+    d, n, p = request.param
+    prob = I.poisson_box(d, n, p)
+    Ho = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=50)
+    H = A.Hierarchy(dev(prob.rowptr), dev(prob.col), dev(prob.val), coarse_max=50)
+    assert H.num_levels == Ho.num_levels >= 3
+    return prob, Ho, H, M.Levels(Ho)
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_omega_matches_oracle(case, bf16):
+    prob, Ho, H, lv = case
+    w32 = varied_weights(5)
+    H.mpnn_apply(dev(w32), bf16_weights=bf16)
+    wref = (bf16_round(w32) if bf16 else w32).astype(np.float64)
+    spread = 0.0
+    for l in range(H.num_levels - 1):
+        om = H.mpnn_omega(l).cpu().numpy().astype(np.float64)
+        ref, _ = M.forward(wref, *M.features(*lv.csr[l]))
+        assert np.max(np.abs(om - ref)) <= 2e-5, (l, np.max(np.abs(om - ref)))
+        spread = max(spread, ref.max() - ref.min())
+    assert spread > 0.1
+    H.mpnn_apply(None)
+
+
+def test_damped_vcycle_matches_oracle_and_restore_is_bitwise(case):
+    prob, Ho, H, lv = case
+    r = np.random.default_rng(3).standard_normal(prob.n)
+    z_plain = H.vcycle(dev(r)).cpu().numpy()
+    H.mpnn_apply(dev(varied_weights(7)), bf16_weights=True)
+    omegas = [H.mpnn_omega(l).cpu().numpy().astype(np.float64) for l in range(H.num_levels - 1)]
+    omegas.append(np.ones(H.level_n(H.num_levels - 1)))
+    z = H.vcycle(dev(r)).cpu().numpy()
+    zo = M.vcycle_omega(lv, omegas, r)
+    assert np.linalg.norm(z - zo) <= 1e-12 * np.linalg.norm(zo)
+    assert np.linalg.norm(z - z_plain) > 1e-3 * np.linalg.norm(z_plain)
+    H.mpnn_apply(None)
+    z_back = H.vcycle(dev(r)).cpu().numpy()
+    assert np.array_equal(z_back.view(np.uint64), z_plain.view(np.uint64))
+
+
+def test_loss_and_gradient_match_oracle(case):
+    prob, Ho, H, lv = case
+    w32 = varied_weights(11)
+    loss, g = H.mpnn_loss_grad(dev(w32), nprobe=3, seed=11)
+    g = g.cpu().numpy()
+    # the V-cycle part in FP64: the oracle's loss for the GPU's omega
+    omegas = [H.mpnn_omega(l).cpu().numpy().astype(np.float64) for l in range(H.num_levels - 1)]
+    omegas.append(np.ones(H.level_n(H.num_levels - 1)))
+    lo, _ = M.loss_and_domega(lv, omegas, M.probes(11, 3, prob.n))
+    assert abs(loss - lo) <= 1e-10 * abs(lo)
+    # end to end, FP64 oracle with the same weights
+    L_ref, g_ref, _ = M.loss_and_grad(Ho, w32.astype(np.float64), nprobe=3, seed=11)
+    assert abs(loss - L_ref) <= 1e-5 * abs(L_ref)
+    err = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    print(f"N={prob.n}: loss {loss:.6f} (oracle {L_ref:.6f}), gradient relative error {err:.2e}")
+    assert err <= 2e-3
+    # every parameter block receives its gradient
+    for name, blk in M.unpack(g_ref).items():
+        gb = M.unpack(g)[name]
+        assert np.linalg.norm(gb - blk) <= 5e-3 * np.linalg.norm(blk) + 1e-4 * np.linalg.norm(g_ref), name
+    loss2, g2 = H.mpnn_loss_grad(dev(w32), nprobe=3, seed=11)
+    assert loss2 == loss and np.array_equal(g2.cpu().numpy(), g)
+
+
+def test_adam_step_matches_textbook():
+    prob = I.poisson_box(2, 16, 2)
+    H = A.Hierarchy(dev(prob.rowptr), dev(prob.col), dev(prob.val), coarse_max=20)
+    rng = np.random.default_rng(0)
+    w = rng.standard_normal(A.AMG_MPNN_NPARAM).astype(np.float32)
+    m = (rng.standard_normal(A.AMG_MPNN_NPARAM) * 0.1).astype(np.float32)
+    v = (rng.random(A.AMG_MPNN_NPARAM) * 0.01).astype(np.float32)
+    g = rng.standard_normal(A.AMG_MPNN_NPARAM)
+    wd, md, vd, gd = dev(w), dev(m), dev(v), dev(g)
+    A.amg_mpnn_adam(H._h, wd, gd, md, vd, 3, 1e-2)
+    # the kernel's constants are FP32: 1 - beta2 = 1 - fl32(0.999) differs
+    # from 0.001 by 1.3e-5 relative, so the reference uses the same values
+    f = np.float32
+    b1, b2 = float(f(0.9)), float(f(0.999))
+    c1, c2 = float(f(1) - f(b1)), float(f(1) - f(b2))
+    m1 = b1 * m + c1 * g
+    v1 = b2 * v + c2 * g * g
+    w1 = w - 1e-2 * (m1 / (1 - b1 ** 3)) / (np.sqrt(v1 / (1 - b2 ** 3)) + 1e-8)
+    assert np.allclose(md.cpu().numpy(), m1, rtol=1e-5, atol=1e-7)
+    assert np.allclose(vd.cpu().numpy(), v1, rtol=1e-5, atol=1e-9)
+    assert np.allclose(wd.cpu().numpy(), w1, rtol=1e-5, atol=1e-6)
+
+
+def test_training_reduces_loss_and_iterations():
+    prob = I.poisson_box(2, 32, 3)
+    H = A.Hierarchy(dev(prob.rowptr), dev(prob.col), dev(prob.val), coarse_max=50)
+    w = dev(I.mpnn_init_weights(1).astype(np.float32))
+    hist = H.mpnn_train(w, steps=40, nprobe=4, seed=1000, lr=1e-2)
+    assert np.all(np.isfinite(hist))
+    assert hist[-10:].mean() < hist[0] - 0.5
+    used, ip, il = H.mpnn_select(w, dev(prob.F), rtol=1e-8)
+    print(f"2-D p=3 n=32: loss {hist[0]:.3f} -> {hist[-1]:.3f}; PCG iterations plain {ip}, learned {il}")
+    assert used and il <= 0.9 * ip
+    g = H.solve(dev(prob.F), rtol=1e-8)
+    assert g["status"] == 0 and g["iters"] == il
+    K = sp.csr_matrix((prob.val, prob.col, prob.rowptr))
+    u = g["u"].cpu().numpy()
+    assert np.linalg.norm(prob.F - K @ u) <= 1e-8 * 1.0001 * np.linalg.norm(prob.F)
+
+
+def test_fallback_keeps_plain_smoother_when_learned_is_worse():
+    prob = I.poisson_box(2, 32, 3)
+    H = A.Hierarchy(dev(prob.rowptr), dev(prob.col), dev(prob.val), coarse_max=50)
+    r = np.random.default_rng(1).standard_normal(prob.n)
+    z_plain = H.vcycle(dev(r)).cpu().numpy()
+    d = M.unpack(I.mpnn_init_weights(2))
+    d["c"] = np.array([-6.0])  # omega about 0.005: a very weak smoother
+    used, ip, il = H.mpnn_select(dev(M.pack(d).astype(np.float32)), dev(prob.F), rtol=1e-8, itmax=2000)
+    assert not used and il > ip
+    z = H.vcycle(dev(r)).cpu().numpy()
+    assert np.array_equal(z.view(np.uint64), z_plain.view(np.uint64))
+
+
+@pytest.mark.parametrize("prec", [A.AMG_FP32, A.AMG_FP32_BF16FINE])
+def test_learned_damping_in_mixed_precision(prec):
+    prob = I.poisson_box(3, 16, 3)
+    args = (dev(prob.rowptr), dev(prob.col), dev(prob.val))
+    w = dev(I.mpnn_init_weights(1).astype(np.float32))
+    A.Hierarchy(*args).mpnn_train(w, steps=30, nprobe=4, seed=500, lr=1e-2)
+    H = A.Hierarchy(*args, precision=prec)
+    plain = H.solve(dev(prob.F), rtol=1e-8)
+    H.mpnn_apply(w, bf16_weights=True)
+    g = H.solve(dev(prob.F), rtol=1e-8)
+    K = sp.csr_matrix((prob.val, prob.col, prob.rowptr))
+    u = g["u"].cpu().numpy()
+    print(f"3-D p=3 n=16 precision {prec}: iterations plain {plain['iters']}, learned {g['iters']}")
+    assert g["status"] == 0 and g["iters"] < plain["iters"]
+    assert np.linalg.norm(prob.F - K @ u) <= 1e-8 * 1.0001 * np.linalg.norm(prob.F)

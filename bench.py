@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=60)
     ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp64",
                     help="precision of the main timed leg (profiling runs)")
     return ap.parse_args()
@@ -227,6 +229,81 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------- ours
+def learned_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, ref_u, fp64_ms, mixed_ms):
+    """Mixed precision + learned smoother damping on the bench workload."""
+    dev = F.device
+    # training set: 3-D cube hierarchies, p in {2, 3, 4}, n = 16 (FP64)
+    train = []
+    for pp in (2, 3, 4):
+        q = I.poisson_box(3, 16, pp)
+        train.append(A.amg_setup(torch.from_numpy(q.rowptr).to(dev), torch.from_numpy(q.col).to(dev),
+                                 torch.from_numpy(q.val).to(dev), A.amg_opts_default(), stream))
+    w = torch.from_numpy(I.mpnn_init_weights(1).astype(np.float32)).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = A.amg_mpnn_train(train, w, args.train_steps, 4, 1000, 1e-2)
+    train_s = time.perf_counter() - t0
+    for h in train:
+        A.amg_free(h)
+    mopts = A.amg_opts_default(precision=A.AMG_FP32_BF16FINE)
+
+    # fallback rule on the workload itself (untimed): learned only if no worse
+    h = A.amg_setup(rp, ci, va, mopts, stream)
+    used, it_plain, it_learned = A.amg_mpnn_select(h, w, F, args.rtol, 10000)
+    # inference time alone (features are computed on the first call)
+    A.amg_mpnn_apply(h, w, True)
+    i0 = torch.cuda.Event(enable_timing=True)
+    i1 = torch.cuda.Event(enable_timing=True)
+    i0.record(stream)
+    for _ in range(5):
+        A.amg_mpnn_apply(h, w, True)
+    i1.record(stream)
+    torch.cuda.synchronize()
+    infer_ms = i0.elapsed_time(i1) / 5
+    A.amg_free(h)
+    h = A.amg_setup(rp, ci, va, A.amg_opts_default(), stream)
+    A.amg_mpnn_apply(h, w, True)
+    u64 = torch.zeros_like(F)
+    _, it64, _ = A.amg_pcg_solve(h, F, u64, args.rtol, 10000)
+    A.amg_free(h)
+
+    def lstep():
+        h = A.amg_setup(rp, ci, va, mopts, stream)
+        if used:
+            A.amg_mpnn_apply(h, w, True)
+        u = torch.zeros_like(F)
+        st, it, rr = A.amg_pcg_solve(h, F, u, args.rtol, 10000)
+        info = A.amg_get_info(h)
+        A.amg_free(h)
+        if st != A.AMG_OK:
+            raise RuntimeError(f"learned solve failed: {A.amg_strerror(st)}")
+        return u, it, rr, info
+
+    for _ in range(args.warmup):
+        lstep()
+    torch.cuda.synchronize()
+    barrier(dist)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        lu, lit, lrr, linfo = lstep()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    l_ms = max_over_ranks(dist, e0.elapsed_time(e1)) / args.steps
+    err = float(torch.linalg.norm(lu - ref_u) / torch.linalg.norm(ref_u))
+    return {"time_to_solution_s": l_ms / 1e3, "speedup_vs_fp64": fp64_ms / l_ms, "speedup_vs_mixed": mixed_ms / l_ms,
+            "iters": lit, "iters_mixed_plain": it_plain, "iters_fp64_learned": it64, "learned_kept": bool(used),
+            "final_relres_fp64": lrr, "rel_error_vs_fp64_solution": err, "inference_ms": infer_ms,
+            "setup_ms": linfo.setup_ms, "solve_ms": linfo.solve_ms,
+            "training": {"set": "3-D cube p in {2,3,4}, n=16, FP64 hierarchies", "steps": args.train_steps,
+                         "probes": 4, "lr": 1e-2, "seconds": train_s,
+                         "loss_first": float(hist[0]) if len(hist) else None,
+                         "loss_last": float(hist[-1]) if len(hist) else None},
+            "precision": "network BF16 weights / FP32 arithmetic; mixed-precision solve as in 'mixed'",
+            "timed_step": "setup + network inference + solve + free"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -399,6 +476,13 @@ def run_ours(args):
                      "roofline": {"bound": "hbm", "kernel": mdom, "achieved": mk[mdom]["achieved_gbs"],
                                   "unit": "GB/s", "all": mk}}
 
+        # learned damping on top of mixed precision: the network is trained
+        # (untimed) on small hierarchies of the same family, then each timed
+        # step is setup + network inference (BF16 weights) + solve + free
+        learned = None
+        if not args.no_learned and not args.no_mixed:
+            learned = learned_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, ref_u, ms_per_step, m_ms)
+
     peak, peak_kind = measured_peaks()
     avg_ms = ms_sum / np.maximum(cnt_sum, 1)
     per_kernel = {}
@@ -432,7 +516,8 @@ def run_ours(args):
             "iter_gbps": info.iter_bytes * it / (info.solve_ms * 1e-3) / 1e9 if info.solve_ms > 0 else None,
             "vcycle_ms": vcycle_ms, "vcycle_gbps": vinfo.vcycle_bytes / (vcycle_ms * 1e-3) / 1e9,
             "throughput_systems_per_s": world * args.steps / (elapsed_ms * 1e-3),
-            "roofline": roof, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches), "mixed": mixed}
+            "roofline": roof, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches), "mixed": mixed,
+            "learned": learned}
     if mixed is not None:
         mixed["roofline"]["peak"] = peak
         mixed["roofline"]["frac"] = (mixed["roofline"]["achieved"] or 0.0) / peak

@@ -290,11 +290,13 @@ int amg_mpnn_adam(amg_hierarchy* h, float* w, const double* grad, float* m, floa
                   float beta1, float beta2, float eps);
 
 /* `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on the
- * loss of amg_mpnn_loss_grad with probe seed seed + step; w (device) is
- * updated in place; loss_hist (host, optional) receives each step's loss
- * before its update.  Errors as amg_mpnn_loss_grad. */
-int amg_mpnn_train(amg_hierarchy* h, float* w, int32_t steps, int32_t nprobe, uint64_t seed, float lr,
-                   double* loss_hist);
+ * mean over the `count` hierarchies hs[0..count) (1 <= count <= 64, all on
+ * the current device) of the loss of amg_mpnn_loss_grad, with probe seed
+ * seed + step; w (device) is updated in place; loss_hist (host, optional)
+ * receives each step's mean loss before its update.  The Adam moments live
+ * with hs[0].  Errors as amg_mpnn_loss_grad. */
+int amg_mpnn_train(amg_hierarchy* const* hs, int32_t count, float* w, int32_t steps, int32_t nprobe, uint64_t seed,
+                   float lr, double* loss_hist);
 
 /* Fallback rule: solve K u = F (F device, u0 = 0) with the plain smoother
  * and with the network's damping (BF16 weights); keep the learned damping

@@ -96,8 +96,8 @@ _SIGS = {
     "amg_mpnn_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64,
                                           ctypes.c_void_p, ctypes.c_void_p]),
     "amg_mpnn_adam": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int32] + [ctypes.c_float] * 4),
-    "amg_mpnn_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
-                                      ctypes.c_uint64, ctypes.c_float, ctypes.c_void_p]),
+    "amg_mpnn_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_uint64, ctypes.c_float, ctypes.c_void_p]),
     "amg_mpnn_select": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "amg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -391,11 +391,14 @@ def amg_mpnn_adam(h, w, grad, m, v, t: int, lr: float, beta1=0.9, beta2=0.999, e
                                eps), "amg_mpnn_adam")
 
 
-def amg_mpnn_train(h, w, steps: int, nprobe: int, seed: int, lr: float):
-    """Train the FP32 device tensor w in place; returns the loss history."""
+def amg_mpnn_train(hs, w, steps: int, nprobe: int, seed: int, lr: float):
+    """Train the FP32 device tensor w in place on one hierarchy handle or a
+    list of them (mean loss); returns the loss history."""
+    hs = list(hs) if isinstance(hs, (list, tuple)) else [hs]
+    arr = (ctypes.c_void_p * len(hs))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in hs])
     hist = np.zeros(max(steps, 1))
-    _check(lib().amg_mpnn_train(h, w.data_ptr(), steps, nprobe, seed & 0xFFFFFFFFFFFFFFFF, lr, hist.ctypes.data),
-           "amg_mpnn_train")
+    _check(lib().amg_mpnn_train(arr, len(hs), w.data_ptr(), steps, nprobe, seed & 0xFFFFFFFFFFFFFFFF, lr,
+                                hist.ctypes.data), "amg_mpnn_train")
     return hist[:steps]
 
 
@@ -489,8 +492,9 @@ class Hierarchy:
     def mpnn_loss_grad(self, w, nprobe: int = 4, seed: int = 99):
         return amg_mpnn_loss_grad(self._h, w, nprobe, seed)
 
-    def mpnn_train(self, w, steps: int, nprobe: int = 4, seed: int = 1000, lr: float = 1e-2):
-        return amg_mpnn_train(self._h, w, steps, nprobe, seed, lr)
+    def mpnn_train(self, w, steps: int, nprobe: int = 4, seed: int = 1000, lr: float = 1e-2, others=()):
+        """Train w on this hierarchy (and the hierarchies in `others`)."""
+        return amg_mpnn_train([self._h] + [o._h for o in others], w, steps, nprobe, seed, lr)
 
     def mpnn_select(self, w, F, rtol: float = 1e-8, itmax: int = 10000):
         return amg_mpnn_select(self._h, w, F, rtol, itmax)

@@ -452,6 +452,12 @@ __global__ void k_v_lossgrad(int n, const double* __restrict__ Ky, const double*
     }
 }
 
+// out = (first ? 0 : out) + s a
+__global__ void k_scale_add(int n, const double* __restrict__ a, double s, int first, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (first ? 0.0 : out[i]) + s * a[i];
+}
+
 // Adam (Kingma and Ba, 2015) on the flat weights; t counts from 1
 __global__ void k_adam(int n, float* __restrict__ w, const double* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, int t, float lr, float b1, float b2, float eps) {
@@ -500,6 +506,7 @@ struct MpnnWork {
     float* bw[3] = {};       // backward scratch, [n0][32] each
     float* part = nullptr;   // per-block gradient partials
     double* gacc = nullptr;  // FP64 gradient accumulator
+    double* gsum = nullptr;  // mean gradient over the hierarchies of a training step
     double *px = nullptr, *py = nullptr, *pky = nullptr;  // probe, y, K y
     double* dots = nullptr;
     double* loss = nullptr;
@@ -570,6 +577,7 @@ int prepare(amg_hierarchy* h) {
     for (int t = 0; t < 3; t++) MP_ALLOC(w.bw[t], sizeof(float) * H * n0);
     MP_ALLOC(w.part, sizeof(float) * kGradBlocks * kGradSlots);
     MP_ALLOC(w.gacc, sizeof(double) * AMG_MPNN_NPARAM);
+    MP_ALLOC(w.gsum, sizeof(double) * AMG_MPNN_NPARAM);
     MP_ALLOC(w.px, sizeof(double) * n0);
     MP_ALLOC(w.py, sizeof(double) * n0);
     MP_ALLOC(w.pky, sizeof(double) * n0);
@@ -854,25 +862,46 @@ int amg_mpnn_adam(amg_hierarchy* h, float* w, const double* grad, float* m, floa
     return sync_status(h);
 }
 
-int amg_mpnn_train(amg_hierarchy* h, float* w, int32_t steps, int32_t nprobe, uint64_t seed, float lr,
-                   double* loss_hist) {
-    if (!h || !w || steps < 0 || nprobe < 1 || !(lr > 0.f) || h->nlev < 2) return AMG_ERR_ARG;
-    MP_RC(join_caller_stream(h));
-    MP_RC(prepare(h));
-    MpnnWork& mw = *h->mp;
-    MP_RC(status_of(cudaMemsetAsync(mw.adam_m, 0, sizeof(float) * AMG_MPNN_NPARAM, h->s)));
-    MP_RC(status_of(cudaMemsetAsync(mw.adam_v, 0, sizeof(float) * AMG_MPNN_NPARAM, h->s)));
-    for (int t = 0; t < steps; t++) {
-        MP_RC(loss_grad_enqueue(h, w, nprobe, seed + (uint64_t)t));
-        k_adam<<<AMG_GRID(eblk(AMG_MPNN_NPARAM)), kBlock, 0, h->s>>>(AMG_MPNN_NPARAM, w, mw.gacc, mw.adam_m,
-                                                                      mw.adam_v, t + 1, lr, 0.9f, 0.999f, 1e-8f);
-        MP_RC(status_of(cudaGetLastError()));
-        int bad = 0;
-        MP_RC(read_host(h, mw.bad, &bad));
-        if (bad) return AMG_ERR_BREAKDOWN;
-        if (loss_hist) MP_RC(read_host(h, mw.loss, &loss_hist[t]));
+int amg_mpnn_train(amg_hierarchy* const* hs, int32_t count, float* w, int32_t steps, int32_t nprobe, uint64_t seed,
+                   float lr, double* loss_hist) {
+    if (!hs || count < 1 || count > 64 || !w || steps < 0 || nprobe < 1 || !(lr > 0.f)) return AMG_ERR_ARG;
+    for (int k = 0; k < count; k++)
+        if (!hs[k] || hs[k]->nlev < 2) return AMG_ERR_ARG;
+    for (int k = 0; k < count; k++) {
+        MP_RC(join_caller_stream(hs[k]));
+        MP_RC(prepare(hs[k]));
+        MP_RC(sync_status(hs[k]));
     }
-    return sync_status(h);
+    amg_hierarchy* h0 = hs[0];
+    MpnnWork& w0 = *h0->mp;
+    MP_RC(status_of(cudaMemsetAsync(w0.adam_m, 0, sizeof(float) * AMG_MPNN_NPARAM, h0->s)));
+    MP_RC(status_of(cudaMemsetAsync(w0.adam_v, 0, sizeof(float) * AMG_MPNN_NPARAM, h0->s)));
+    MP_RC(sync_status(h0));
+    for (int t = 0; t < steps; t++) {
+        double lsum = 0.0;
+        // every hierarchy's loss and gradient with the same weights (its own
+        // stream, waited for on the host before the weights change)
+        for (int k = 0; k < count; k++) {
+            MP_RC(loss_grad_enqueue(hs[k], w, nprobe, seed + (uint64_t)t));
+            int bad = 0;
+            double lk = 0.0;
+            MP_RC(read_host(hs[k], hs[k]->mp->bad, &bad));
+            if (bad) return AMG_ERR_BREAKDOWN;
+            MP_RC(read_host(hs[k], hs[k]->mp->loss, &lk));
+            if (!isfinite(lk)) return AMG_ERR_NAN;
+            lsum += lk;
+        }
+        // mean gradient (fixed hierarchy order), then one Adam step
+        for (int k = 0; k < count; k++)
+            k_scale_add<<<AMG_GRID(eblk(AMG_MPNN_NPARAM)), kBlock, 0, h0->s>>>(
+                AMG_MPNN_NPARAM, hs[k]->mp->gacc, 1.0 / count, k == 0, w0.gsum);
+        k_adam<<<AMG_GRID(eblk(AMG_MPNN_NPARAM)), kBlock, 0, h0->s>>>(AMG_MPNN_NPARAM, w, w0.gsum, w0.adam_m,
+                                                                       w0.adam_v, t + 1, lr, 0.9f, 0.999f, 1e-8f);
+        MP_RC(status_of(cudaGetLastError()));
+        MP_RC(sync_status(h0));
+        if (loss_hist) loss_hist[t] = lsum / count;
+    }
+    return AMG_OK;
 }
 
 int amg_mpnn_select(amg_hierarchy* h, const float* w, const double* F, double rtol, int32_t itmax, int32_t* used,

@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
     assert L.amg_setup(None, None, None, None) == -1
     assert L.amg_mpnn_apply(None, None, 0) == -1
     assert L.amg_mpnn_loss_grad(None, None, 1, ctypes.c_uint64(0), None, None) == -1
-    assert L.amg_mpnn_train(None, None, 1, 1, ctypes.c_uint64(0), ctypes.c_float(0.01), None) == -1
+    assert L.amg_mpnn_train(None, 1, None, 1, 1, ctypes.c_uint64(0), ctypes.c_float(0.01), None) == -1
 
 
 def test_binding_names_match_abi():

@@ -124,3 +124,62 @@ def test_fullsize_sixteen_rhs():
     err = np.linalg.norm(U[0] - ref["u"]) / np.linalg.norm(ref["u"])
     print(f"16 RHS, 3-D p=3 n=48: iterations {out['iters'].tolist()}, column 0 error vs FP64 oracle {err:.2e}")
     assert err <= 1e-7
+
+
+def _oracle_omega_at(prob, rows, w64):
+    """Oracle omega of level 0 at a few rows, from the sub-matrix on their
+    3-hop neighbourhood (the network reads 2 hops; the third keeps every
+    needed row complete)."""
+    from oracle import mpnn as M
+
+    K = sp.csr_matrix((prob.val, prob.col, prob.rowptr), shape=(prob.n, prob.n))
+    S = np.asarray(rows)
+    ring = S
+    for _ in range(3):
+        ring = np.unique(np.concatenate([ring, K[ring].indices]))
+    sub = K[ring][:, ring].tocsr()
+    sub.sort_indices()
+    om, _ = M.forward(w64, *M.features(sub.indptr.astype(np.int64), sub.indices.astype(np.int32), sub.data))
+    return om[np.searchsorted(ring, S)]
+
+
+def test_fullsize_learned_damping_mixed_precision(cube64):
+    """Network trained on 3-D p in {2,3,4} n=16 cubes, applied to the 3-D p=3
+    n=64 workload: omega at sampled rows against the oracle (BF16 weights),
+    then the mixed-precision learned solve meets rtol 1e-8 (true FP64
+    residual), stays within 1e-7 of the FP64 solution and needs fewer
+    iterations than the plain mixed-precision solve."""
+    prob, Ho = cube64
+    train = []
+    for pp in (2, 3, 4):
+        q = I.poisson_box(3, 16, pp)
+        train.append(A.Hierarchy(dev(q.rowptr), dev(q.col), dev(q.val)))
+    w = dev(I.mpnn_init_weights(1).astype(np.float32))
+    hist = train[0].mpnn_train(w, steps=60, nprobe=4, seed=1000, lr=1e-2, others=train[1:])
+    assert hist[-10:].mean() < hist[0]
+    args = (dev(prob.rowptr), dev(prob.col), dev(prob.val))
+    F = dev(prob.F)
+    u64 = A.Hierarchy(*args).solve(F, rtol=1e-8)["u"].cpu().numpy()
+    H = A.Hierarchy(*args, precision=A.AMG_FP32_BF16FINE)
+    plain = H.solve(F, rtol=1e-8)
+    H.mpnn_apply(w, bf16_weights=True)
+    om = H.mpnn_omega(0).cpu().numpy().astype(np.float64)
+    rows = np.random.default_rng(9).choice(prob.n, 5, replace=False)
+    rows = np.sort(np.concatenate([rows, [0, prob.n // 2]]))
+
+    def bf16(a):
+        b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+        return ((((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16).astype(np.uint32)).view(np.float32)
+
+    ref = _oracle_omega_at(prob, rows, bf16(w.cpu().numpy()).astype(np.float64))
+    assert np.max(np.abs(om[rows] - ref)) <= 2e-5
+    g = H.solve(F, rtol=1e-8)
+    assert g["status"] == 0
+    u = g["u"].cpu().numpy()
+    rr = true_relres((prob.rowptr, prob.col, prob.val), prob.F, u)
+    err = np.linalg.norm(u - u64) / np.linalg.norm(u64)
+    print(f"learned + mixed, 3-D p=3 n=64: iterations {g['iters']} (plain mixed {plain['iters']}), "
+          f"true relres {rr:.2e}, error vs FP64 {err:.2e}, omega mean {om.mean():.3f} "
+          f"[{om.min():.3f}, {om.max():.3f}]")
+    assert rr <= 1e-8 * 1.0001 and err <= 1e-7
+    assert g["iters"] < plain["iters"]

@@ -185,3 +185,21 @@ def test_learned_damping_in_mixed_precision(prec):
     print(f"3-D p=3 n=16 precision {prec}: iterations plain {plain['iters']}, learned {g['iters']}")
     assert g["status"] == 0 and g["iters"] < plain["iters"]
     assert np.linalg.norm(prob.F - K @ u) <= 1e-8 * 1.0001 * np.linalg.norm(prob.F)
+
+
+def test_training_over_several_hierarchies_uses_the_mean_loss():
+    probs = [I.poisson_box(2, 16, 3), I.poisson_box(2, 24, 2)]
+    Hs = [A.Hierarchy(dev(q.rowptr), dev(q.col), dev(q.val), coarse_max=20) for q in probs]
+    w0 = I.mpnn_init_weights(4).astype(np.float32)
+    losses, grads = zip(*[H.mpnn_loss_grad(dev(w0), nprobe=2, seed=77) for H in Hs])
+    w = dev(w0)
+    hist = Hs[0].mpnn_train(w, steps=1, nprobe=2, seed=77, lr=1e-3, others=Hs[1:])
+    assert abs(hist[0] - 0.5 * (losses[0] + losses[1])) <= 1e-14 * abs(hist[0])
+    # first Adam step: w - lr g / (|g| + eps) elementwise (bias-corrected moments)
+    g = 0.5 * (grads[0].cpu().numpy() + grads[1].cpu().numpy())
+    f = np.float32
+    c1, c2 = float(f(1) - f(0.9)), float(f(1) - f(0.999))
+    mh = c1 * g / (1 - float(f(0.9)))
+    vh = c2 * g * g / (1 - float(f(0.999)))
+    expect = w0 - 1e-3 * mh / (np.sqrt(vh) + 1e-8)
+    assert np.allclose(w.cpu().numpy(), expect, rtol=1e-5, atol=1e-6)

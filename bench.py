@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--train-steps", type=int, default=60)
     ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp64",
                     help="precision of the main timed leg (profiling runs)")
@@ -304,6 +305,83 @@ def learned_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, ref_u, fp64_
             "timed_step": "setup + network inference + solve + free"}
 
 
+def batched_leg(args, A, I, torch, np, stream):
+    """Batched solves (FP32 V-cycle, FP64 outer FCG(1), rtol as the bench):
+    48 uneven 2-D instances as one block-diagonal hierarchy, and one 3-D
+    p=3 n=48 system with 16 right-hand sides (SpMM passes), each against the
+    same systems solved one by one through amg_setup + amg_pcg_solve."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    fp32 = A.amg_opts_default(precision=A.AMG_FP32)
+    reps = 3
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    probs = I.batch_instances(seed=20251126, count=48)
+    systems = [tuple(torch.from_numpy(a).to(dev) for a in (q.rowptr, q.col, q.val)) for q in probs]
+    Fs = [torch.from_numpy(q.F).to(dev) for q in probs]
+
+    def batch_once():
+        h = A.amg_setup_batch(systems, fp32, stream)
+        Us = [torch.zeros_like(F) for F in Fs]
+        st, it, rr = A.amg_pcg_solve_batch(h, Fs, Us, args.rtol, 10000)
+        A.amg_free(h)
+        assert st == A.AMG_OK
+        return it
+
+    def batch_seq():
+        its = []
+        for (rp, ci, va), F in zip(systems, Fs):
+            h = A.amg_setup(rp, ci, va, fp32, stream)
+            st, it, _ = A.amg_pcg_solve(h, F, torch.zeros_like(F), args.rtol, 10000)
+            A.amg_free(h)
+            assert st == A.AMG_OK
+            its.append(it)
+        return its
+
+    tb, itb = timed(batch_once)
+    ts, its = timed(batch_seq)
+    q = I.poisson_box_random_rhs(3, 48, 3, seed=16, nrhs=16)
+    rp, ci, va = (torch.from_numpy(a).to(dev) for a in (q.rowptr, q.col, q.val))
+    Fm = torch.from_numpy(np.ascontiguousarray(q.F.reshape(16, q.n))).to(dev)
+
+    def multi_once():
+        h = A.amg_setup(rp, ci, va, fp32, stream)
+        st, it, rr = A.amg_pcg_solve_multi(h, Fm, torch.zeros_like(Fm), args.rtol, 10000)
+        A.amg_free(h)
+        assert st == A.AMG_OK
+        return it
+
+    def multi_seq():
+        h = A.amg_setup(rp, ci, va, fp32, stream)
+        its = []
+        for c in range(16):
+            st, it, _ = A.amg_pcg_solve(h, Fm[c].contiguous(), torch.zeros(q.n, dtype=torch.float64, device=dev),
+                                        args.rtol, 10000)
+            assert st == A.AMG_OK
+            its.append(it)
+        A.amg_free(h)
+        return its
+
+    tm, itm = timed(multi_once)
+    tq, itq = timed(multi_seq)
+    return {"batch48": {"instances": "48 x 2-D, p in {2,3,4}, n in 32..256 (seeded), F = K u, u ~ N(0,1)",
+                        "N_total": int(sum(p.n for p in probs)), "ms": tb, "ms_one_by_one": ts,
+                        "speedup": ts / tb, "iters_min_max": [int(min(itb)), int(max(itb))]},
+            "rhs16": {"system": "3-D p=3 n=48 (N=117,649), 16 right-hand sides ~ N(0,1)", "ms": tm,
+                      "ms_one_by_one": tq, "speedup": tq / tm, "iters_min_max": [int(min(itm)), int(max(itm))]},
+            "timed": "setup + solve + free per batch (one-by-one: per system; the 16-RHS baseline shares one setup)"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -483,6 +561,10 @@ def run_ours(args):
         if not args.no_learned and not args.no_mixed:
             learned = learned_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, ref_u, ms_per_step, m_ms)
 
+        batched = None
+        if not args.no_batched:
+            batched = batched_leg(args, A, I, torch, np, stream)
+
     peak, peak_kind = measured_peaks()
     avg_ms = ms_sum / np.maximum(cnt_sum, 1)
     per_kernel = {}
@@ -517,7 +599,7 @@ def run_ours(args):
             "vcycle_ms": vcycle_ms, "vcycle_gbps": vinfo.vcycle_bytes / (vcycle_ms * 1e-3) / 1e9,
             "throughput_systems_per_s": world * args.steps / (elapsed_ms * 1e-3),
             "roofline": roof, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches), "mixed": mixed,
-            "learned": learned}
+            "learned": learned, "batched": batched}
     if mixed is not None:
         mixed["roofline"]["peak"] = peak
         mixed["roofline"]["frac"] = (mixed["roofline"]["achieved"] or 0.0) / peak

@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--train-steps", type=int, default=60)
+    ap.add_argument("--matrix-format", type=int, choices=[0, 1, 2], default=2,
+                    help="2 = run-encoded finest level + bulk-copy streamed mixed passes (default), 1 = run-encoded, 0 = CSR")
     ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp64",
                     help="precision of the main timed leg (profiling runs)")
     return ap.parse_args()
@@ -246,7 +248,7 @@ def learned_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, ref_u, fp64_
     train_s = time.perf_counter() - t0
     for h in train:
         A.amg_free(h)
-    mopts = A.amg_opts_default(precision=A.AMG_FP32_BF16FINE)
+    mopts = A.amg_opts_default(precision=A.AMG_FP32_BF16FINE, matrix_format=args.matrix_format)
 
     # fallback rule on the workload itself (untimed): learned only if no worse
     h = A.amg_setup(rp, ci, va, mopts, stream)
@@ -262,7 +264,7 @@ def learned_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, ref_u, fp64_
     torch.cuda.synchronize()
     infer_ms = i0.elapsed_time(i1) / 5
     A.amg_free(h)
-    h = A.amg_setup(rp, ci, va, A.amg_opts_default(), stream)
+    h = A.amg_setup(rp, ci, va, A.amg_opts_default(matrix_format=args.matrix_format), stream)
     A.amg_mpnn_apply(h, w, True)
     u64 = torch.zeros_like(F)
     _, it64, _ = A.amg_pcg_solve(h, F, u64, args.rtol, 10000)
@@ -286,11 +288,13 @@ def learned_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, ref_u, fp64_
     barrier(dist)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("learned")
     e0.record(stream)
     for _ in range(args.steps):
         lu, lit, lrr, linfo = lstep()
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     l_ms = max_over_ranks(dist, e0.elapsed_time(e1)) / args.steps
     err = float(torch.linalg.norm(lu - ref_u) / torch.linalg.norm(ref_u))
     return {"time_to_solution_s": l_ms / 1e3, "speedup_vs_fp64": fp64_ms / l_ms, "speedup_vs_mixed": mixed_ms / l_ms,
@@ -401,7 +405,7 @@ def run_ours(args):
     F = torch.from_numpy(prob.F).to(dev)
     stream = torch.cuda.Stream(device=dev)
     prec = {"fp64": A.AMG_FP64, "fp32": A.AMG_FP32, "bf16": A.AMG_FP32_BF16FINE}[args.precision]
-    opts = A.amg_opts_default(precision=prec)
+    opts = A.amg_opts_default(precision=prec, matrix_format=args.matrix_format)
 
     def step(profile=False):
         h = A.amg_setup(rp, ci, va, opts, stream)
@@ -504,7 +508,7 @@ def run_ours(args):
         # FP32 outer SpMV, FP64 flexible-CG recurrences and true-residual replacement)
         mixed = None
         if not args.no_mixed:
-            mopts = A.amg_opts_default(precision=A.AMG_FP32_BF16FINE)
+            mopts = A.amg_opts_default(precision=A.AMG_FP32_BF16FINE, matrix_format=args.matrix_format)
             ref_u = torch.zeros_like(F)
             h = A.amg_setup(rp, ci, va, opts, stream)
             A.amg_pcg_solve(h, F, ref_u, args.rtol, 10000)
@@ -529,6 +533,7 @@ def run_ours(args):
             barrier(dist)
             m0 = torch.cuda.Event(enable_timing=True)
             m1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push("mixed")
             m0.record(stream)
             mms = np.zeros(3)
             mcnt = np.zeros(3, np.int64)
@@ -538,6 +543,7 @@ def run_ours(args):
                 mcnt += mkt[1]
             m1.record(stream)
             torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
             m_ms = max_over_ranks(dist, m0.elapsed_time(m1)) / args.steps
             err = float(torch.linalg.norm(mu - ref_u) / torch.linalg.norm(ref_u))
             mavg = mms / np.maximum(mcnt, 1)
@@ -589,6 +595,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": args.n, "p": args.p, "N": prob.n, "nnz": prob.nnz,
                        "rtol": args.rtol, "precision": "fp64", "l2": "inputs larger than L2 (matrix 1.04 GB)",
+                       "matrix_format": ["csr", "run-encoded finest level", "run-encoded + streamed mixed passes"][args.matrix_format],
                        "parallelism": f"replicas x{world}"},
             "iters": it, "final_relres": rr, "setup_ms": info.setup_ms, "solve_ms": info.solve_ms,
             "setup_phase_ms": dict(zip(["copy+checks", "l1+testvec+diag", "edge_weights", "matching",

@@ -90,7 +90,12 @@ typedef struct {
     int32_t max_match_rounds;    /* bound on matching rounds per pass (1000) */
     int32_t precision;           /* AMG_FP64 / AMG_FP32 / AMG_FP32_BF16FINE (AMG_FP64) */
     int32_t flexible;            /* 0 = PCG, 1 = flexible CG with one direction (0) */
-    int32_t resid_replace_every; /* FP64 true-residual replacement period, 0 = off (0) */
+    int32_t resid_replace_every; /* FP64 true-residual replacement period, 0 = off (20) */
+    int32_t matrix_format;       /* finest-level matrix passes: 0 = plain CSR; 1 = run-encoded
+                                    columns when every row is a sequence of equal runs (2..9
+                                    entries, rows < 65536 entries) of consecutive columns, as in
+                                    tensor-product IgA matrices; 2 = as 1, and the mixed-precision
+                                    passes stream the matrix into shared memory by bulk copies (2) */
 } amg_opts;
 
 #define AMG_MAX_LEVELS 32
@@ -114,6 +119,7 @@ typedef struct {
      * [6] composite maps and member lists, [7] coarsest inverse,
      * [8] precision copies and solve workspace */
     double setup_phase_ms[12];
+    int32_t level_format[AMG_MAX_LEVELS]; /* 1 = run-encoded columns, 0 = plain CSR */
 } amg_info;
 
 typedef struct amg_hierarchy amg_hierarchy;

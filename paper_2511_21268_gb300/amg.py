@@ -44,7 +44,8 @@ class AmgOpts(ctypes.Structure):
                 ("coarse_max", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("dense_max", ctypes.c_int32),
                 ("testvec_sweeps", ctypes.c_int32), ("testvec_kind", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("stag", ctypes.c_double), ("max_match_rounds", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("flexible", ctypes.c_int32), ("resid_replace_every", ctypes.c_int32)]
+                ("flexible", ctypes.c_int32), ("resid_replace_every", ctypes.c_int32),
+                ("matrix_format", ctypes.c_int32)]
 
 
 class AmgInfo(ctypes.Structure):
@@ -53,7 +54,7 @@ class AmgInfo(ctypes.Structure):
                 ("solve_ms", ctypes.c_double), ("iters", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("final_relres", ctypes.c_double), ("vcycle_bytes", ctypes.c_double),
                 ("iter_bytes", ctypes.c_double), ("match_rounds", ctypes.c_int32 * AMG_MAX_LEVELS),
-                ("setup_phase_ms", ctypes.c_double * 12)]
+                ("setup_phase_ms", ctypes.c_double * 12), ("level_format", ctypes.c_int32 * AMG_MAX_LEVELS)]
 
 
 class AmgError(RuntimeError):

@@ -242,6 +242,40 @@ void free_level_matrix(amg_hierarchy* h, DevCSR& A) {
     A = DevCSR{};
 }
 
+// Run-encoded columns of level L (left as plain CSR when a row does not
+// split into equal runs of consecutive columns).
+int build_runs(amg_hierarchy* h, Level& L) {
+    cudaStream_t s = h->s;
+    const int n = L.A.n;
+    if (n < 1) return AMG_OK;
+    int32_t* cnt;
+    Tmp tc(s);
+    RC(tc.get(&cnt, (size_t)n + 1));
+    uint8_t* len;
+    RC(dalloc(h, &len, (size_t)n + 16));  // padded for 16-byte copies
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(cnt + n, 0, sizeof(int32_t), s));
+    CK(launch_run_rows(L.A, cnt, len, h->flag, s));
+    int bad = 0;
+    RC(read_flag(h, &bad));
+    if (bad) {
+        forget(h, len);
+        return AMG_OK;
+    }
+    RC(dalloc(h, &L.run_ptr, (size_t)n + 5));  // padded for 16-byte copies
+    int32_t* scr;
+    Tmp tsc(s);
+    RC(tsc.get(&scr, scan_scratch_ints(n + 1)));
+    CK(launch_exclusive_scan(cnt, L.run_ptr, n + 1, nullptr, scr, s));
+    int32_t total = 0;
+    RC(read_scalar(h, L.run_ptr + n, &total));
+    RC(dalloc(h, &L.run_start, (size_t)total + kPad));
+    CK(launch_run_fill(L.A, L.run_ptr, len, L.run_start, s));
+    L.run_len = len;
+    L.nruns = total;
+    return AMG_OK;
+}
+
 int build(amg_hierarchy* h, const amg_csr* K) {
     cudaStream_t s = h->s;
     const int n0 = K->n;
@@ -249,7 +283,8 @@ int build(amg_hierarchy* h, const amg_csr* K) {
     Level& L0 = h->lev[0];
     L0.A.n = n0;
     L0.A.nnz = K->nnz;
-    RC(dalloc(h, &L0.A.rowptr, (size_t)n0 + 1));
+    // + 2: the staged finest-level passes copy row offsets in 16-byte units
+    RC(dalloc(h, &L0.A.rowptr, (size_t)n0 + 3));
     RC(dalloc(h, &L0.A.col, (size_t)K->nnz + kPad));
     RC(dalloc(h, &L0.A.val, (size_t)K->nnz + kPad));
     const cudaMemcpyKind kind = K->mem == AMG_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -377,18 +412,22 @@ int build(amg_hierarchy* h, const amg_csr* K) {
                 RC(dalloc(h, &F.val16, (size_t)F.A.nnz + kPad));
                 CK(launch_to_bf16(F.A.val, F.val16, F.A.nnz, s));
             }
-            RC(dalloc(h, &F.invd32, n));
+            RC(dalloc(h, &F.invd32, (size_t)n + 4));
             CK(launch_to_f32(F.invd, F.invd32, n, s));
             if (l > 0) RC(dalloc(h, &F.f32, n));
-            RC(dalloc(h, &F.x32, n));
-            RC(dalloc(h, &F.t32, n));
+            // + 4: the staged finest-level passes copy vector windows widened
+            // to 16-byte boundaries
+            RC(dalloc(h, &F.x32, (size_t)n + 4));
+            RC(dalloc(h, &F.t32, (size_t)n + 4));
         } else {
             if (l > 0) RC(dalloc(h, &F.f, n));
             RC(dalloc(h, &F.x, n));
             RC(dalloc(h, &F.t, n));
         }
     }
-    if (h->mixed) RC(dalloc(h, &h->p32, n0));
+    if (h->mixed) RC(dalloc(h, &h->p32, (size_t)n0 + 4));
+    // run-encoded columns of the finest matrix when every row qualifies
+    if (h->o.matrix_format >= 1 && h->nlev > 0 && L0.A.nnz < INT32_MAX) RC(build_runs(h, L0));
     // the vectorised loads need 16-byte aligned column and value arrays
     for (int l = 0; l < h->nlev; l++) {
         const Level& F = h->lev[l];
@@ -396,19 +435,29 @@ int build(amg_hierarchy* h, const amg_csr* K) {
         for (const void* p : ptrs)
             if (p && (reinterpret_cast<uintptr_t>(p) & 15)) return AMG_ERR_CUDA;
     }
-    RC(dalloc(h, &h->x, n0));
-    RC(dalloc(h, &h->r, n0));
-    RC(dalloc(h, &h->p, n0));
-    RC(dalloc(h, &h->q, n0));
-    RC(dalloc(h, &h->z, n0));
-    RC(dalloc(h, &h->F, n0));
+    // CG vectors, padded by 4 entries for the 16-byte copies of the staged passes
+    RC(dalloc(h, &h->x, (size_t)n0 + 4));
+    RC(dalloc(h, &h->r, (size_t)n0 + 4));
+    RC(dalloc(h, &h->p, (size_t)n0 + 4));
+    RC(dalloc(h, &h->q, (size_t)n0 + 4));
+    RC(dalloc(h, &h->z, (size_t)n0 + 4));
+    RC(dalloc(h, &h->F, (size_t)n0 + 4));
     h->npart = (int)partial_slot_size(n0, h->num_sms);
     RC(dalloc(h, &h->partials, partial_slot_count() * h->npart));
     RC(dalloc(h, &h->st, 1));
     h->hist_cap = kHistCap;
     RC(dalloc(h, &h->hist, kHistCap));
     CK(cudaMemsetAsync(h->st, 0, sizeof(SolveState), s));
+    if (h->o.matrix_format == 2) RC(stream_prepare(h, h->flag));
     return AMG_OK;
+}
+
+// Bytes of a level's column information per matrix pass: 4 per entry in
+// CSR; with run-encoded columns 4 per run + 4 per row (run_ptr) + 1 per
+// row (run length).
+double index_bytes(const Level& L) {
+    if (L.run_ptr) return (double)L.nruns * 4.0 + (L.A.n + 1.0) * 4.0 + (double)L.A.n;
+    return (double)L.A.nnz * 4.0;
 }
 
 void fill_info(amg_hierarchy* h) {
@@ -422,14 +471,16 @@ void fill_info(amg_hierarchy* h) {
         int rounds = 0;
         for (int q = 0; q < h->lev[l].npass; q++) rounds += h->lev[l].pass[q].rounds;
         I.match_rounds[l] = rounds;
+        I.level_format[l] = h->lev[l].run_ptr ? 1 : 0;
     }
     I.opc = tot / (double)h->lev[0].A.nnz;
     // algorithmic bytes: one matrix pass = nnz (value + 4) + (n + 1) 8 + x read + y write
     // (value and vector sizes of the V-cycle precision: 8 / 8 in FP64, 4 / 4 in
     // mixed precision with 2-byte values on the finest level when BF16)
     const double vb = h->mixed ? 4.0 : 8.0;
-    auto pass_bytes = [&](const DevCSR& A, double valb) {
-        return (double)A.nnz * (valb + 4.0) + (A.n + 1.0) * 8.0 + 2.0 * A.n * vb;
+    auto pass_bytes = [&](const Level& L, double valb) {
+        const DevCSR& A = L.A;
+        return (double)A.nnz * valb + index_bytes(L) + (A.n + 1.0) * 8.0 + 2.0 * A.n * vb;
     };
     if (h->nlev == 1) {
         vbytes = (double)h->ndense * h->ndense * 8.0 + 2.0 * h->ndense * 8.0;
@@ -437,7 +488,7 @@ void fill_info(amg_hierarchy* h) {
         for (int l = 0; l < h->nlev - 1; l++) {
             const DevCSR& A = h->lev[l].A;
             const double valb = (l == 0 && h->lev[0].val16) ? 2.0 : vb;
-            vbytes += 2.0 * pass_bytes(A, valb) + 6.0 * A.n * vb;
+            vbytes += 2.0 * pass_bytes(h->lev[l], valb) + 6.0 * A.n * vb;
         }
         vbytes += (double)h->ndense * h->ndense * 8.0 + 2.0 * h->ndense * 8.0;
     }
@@ -445,9 +496,10 @@ void fill_info(amg_hierarchy* h) {
     const DevCSR& A0 = h->lev[0].A;
     // outer q = K p (FP32 values in mixed mode) + CG vectors; mixed mode adds an
     // FP64 residual replacement every resid_replace_every iterations
-    double outer = (double)A0.nnz * (vb + 4.0) + (A0.n + 1.0) * 8.0 + 2.0 * A0.n * 8.0;
+    const double ib0 = index_bytes(h->lev[0]);
+    double outer = (double)A0.nnz * vb + ib0 + (A0.n + 1.0) * 8.0 + 2.0 * A0.n * 8.0;
     if (h->mixed && h->o.resid_replace_every > 0)
-        outer += ((double)A0.nnz * 12.0 + (A0.n + 1.0) * 8.0 + 3.0 * A0.n * 8.0) / h->o.resid_replace_every;
+        outer += ((double)A0.nnz * 8.0 + ib0 + (A0.n + 1.0) * 8.0 + 3.0 * A0.n * 8.0) / h->o.resid_replace_every;
     I.iter_bytes = vbytes + outer + 10.0 * A0.n * 8.0;
 }
 
@@ -521,6 +573,7 @@ int check_opts(const amg_opts& o) {
     if (!(o.stag > 0.0) || o.max_match_rounds < 1) return AMG_ERR_ARG;
     if (o.precision < AMG_FP64 || o.precision > AMG_FP32_BF16FINE) return AMG_ERR_ARG;
     if (o.flexible < 0 || o.flexible > 1 || o.resid_replace_every < 0) return AMG_ERR_ARG;
+    if (o.matrix_format < 0 || o.matrix_format > 2) return AMG_ERR_ARG;
     return AMG_OK;
 }
 
@@ -545,6 +598,7 @@ int amg_opts_default(amg_opts* o) {
     o->precision = AMG_FP64;
     o->flexible = 0;
     o->resid_replace_every = 20;
+    o->matrix_format = 2;
     return AMG_OK;
 }
 
@@ -1091,15 +1145,16 @@ int amg_kernel_times(const amg_hierarchy* h, double* ms, int64_t* count, double*
     if (!h) return AMG_ERR_ARG;
     const double n = h->lev[0].A.n, nnz = (double)h->lev[0].A.nnz;
     const double flex = h->o.flexible ? 8.0 * n : 0.0;
+    const double ib = index_bytes(h->lev[0]);
     double b[3];
     if (h->mixed) {  // FP32 outer values, FP32 (or BF16) V-cycle values, FP32 V-cycle vectors
         const double vcv = h->lev[0].val16 ? 2.0 : 4.0;
-        const double rows = (n + 1.0) * 8.0;
-        b[0] = nnz * 8.0 + rows + 4.0 * n + 8.0 * n + 8.0 * n + flex;  // p32 gather, q, p
-        b[1] = nnz * (vcv + 4.0) + rows + 8.0 * n + 4.0 * n + 4.0 * n;  // r, x, rbuf
-        b[2] = nnz * (vcv + 4.0) + rows + 8.0 * n + 4.0 * n + 4.0 * n + 8.0 * n + flex;  // r, x, invd, z
+        const double rows = (n + 1.0) * 8.0 + ib;
+        b[0] = nnz * 4.0 + rows + 4.0 * n + 8.0 * n + 8.0 * n + flex;  // p32 gather, q, p
+        b[1] = nnz * vcv + rows + 8.0 * n + 4.0 * n + 4.0 * n;  // r, x, rbuf
+        b[2] = nnz * vcv + rows + 8.0 * n + 4.0 * n + 4.0 * n + 8.0 * n + flex;  // r, x, invd, z
     } else {
-        const double base = nnz * 12.0 + (n + 1.0) * 8.0;
+        const double base = nnz * 8.0 + ib + (n + 1.0) * 8.0;
         b[0] = base + 16.0 * n + flex;
         b[1] = base + 24.0 * n;
         b[2] = base + 32.0 * n + flex;

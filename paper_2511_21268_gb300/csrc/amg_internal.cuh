@@ -18,6 +18,7 @@ constexpr int kWarpsPerBlock = kBlock / kWarp;
 constexpr int kMaxPasses = 4;
 constexpr int kMaxMembers = 1 << kMaxPasses;
 constexpr int kMaxPartials = 2048;  // block partial sums of one reduction
+constexpr int kMaxRunLen = 9;       // longest run of the run-encoded column format (2p+1, p <= 4)
 
 // Device-side state words of a solve.
 struct SolveState {
@@ -113,7 +114,19 @@ struct Level {
     float* f32 = nullptr;
     float* x32 = nullptr;
     float* t32 = nullptr;
+    // finest level, staged mixed-precision passes: values with each row's
+    // runs interleaved (entry o of run r at rowptr[i] + o R + r)
+    __nv_bfloat16* val16t = nullptr;
+    float* val32t = nullptr;
     int maxrow = 0;
+    // run-encoded columns (level 0, when every row is a sequence of equal
+    // runs of consecutive columns): row i has run_ptr[i+1] - run_ptr[i] runs
+    // of run_len[i] entries; run r starts at column run_start[r] and at entry
+    // rowptr[i] + (r - run_ptr[i]) * run_len[i]
+    int32_t* run_ptr = nullptr;
+    uint8_t* run_len = nullptr;
+    int32_t* run_start = nullptr;
+    int64_t nruns = 0;
 };
 
 }  // namespace amg
@@ -162,6 +175,15 @@ struct amg_hierarchy {
     int ph_id[512] = {};
     int ph_n = 0;
     int* round_active = nullptr;  // active count after each matching round (device)
+    // bulk-copy streamed finest-level passes of the mixed-precision solve
+    int stream = 0;             // in use
+    int stream_blocks = 0;      // persistent grid (one block per SM)
+    int stream_rpw = 0;         // rows per warp of a slab (slab = 8 warps x rpw rows)
+    int stream_xbytes = 0;      // shared-memory bytes of the vector window
+    int stream_vbytes[2] = {};  // value buffer bytes: [0] BF16 values, [1] FP32 values
+    int stream_rbytes[2] = {};  // run-start buffer bytes
+    int stream_nbuf[2] = {};    // buffers in the copy ring
+    int* stream_win = nullptr;  // int2 per block: first and last column of its rows
     // multi-system solves
     amg::MultiWork* mw = nullptr;
     // learned smoother damping: network buffers, and whether the smoother
@@ -237,6 +259,13 @@ cudaError_t enqueue_multi_final(amg_hierarchy* h, cudaStream_t s);
 int multi_dot_stride();
 // mpnn.cu
 void mpnn_free(amg_hierarchy* h);
+// stream_kernels.cu
+int stream_prepare(amg_hierarchy* h, int* scratch2);
+cudaError_t launch_stream_resid(amg_hierarchy* h, const double* f, const float* x, float* rbuf, cudaStream_t s);
+cudaError_t launch_stream_up0(amg_hierarchy* h, const double* r, const float* x, const float* invd, double* z,
+                              const double* q, double* part_rz, double* part_zq, int flexible, cudaStream_t s);
+cudaError_t launch_stream_spmv_pq(amg_hierarchy* h, const float* p32, const double* p, const double* r, double* q,
+                                  double* part_pq, double* part_pr, int flexible, cudaStream_t s);
 // amg_api.cu: order the library stream after the caller's stream
 int join_caller_stream(amg_hierarchy* h);
 cudaError_t launch_interleave(int n, int R, int64_t ld, const double* src, double* dst, cudaStream_t s);
@@ -245,10 +274,13 @@ cudaError_t launch_deinterleave(int n, int R, int64_t ld, const double* src, dou
 cudaError_t launch_shift_block(int n, int64_t nnz, const int64_t* rp_in, int64_t row_off, int64_t nnz_off,
                                int64_t* rp_out, int32_t* col, int* flag, cudaStream_t s);
 cudaError_t launch_fill_sys_id(int nsys, const int64_t* off, int32_t* id, cudaStream_t s);
+cudaError_t launch_run_rows(const DevCSR& A, int32_t* runcnt, uint8_t* runlen, int* flag, cudaStream_t s);
+cudaError_t launch_run_fill(const DevCSR& A, const int32_t* run_ptr, const uint8_t* runlen, int32_t* run_start,
+                            cudaStream_t s);
 int rows_per_warp(int n, int num_sms);
 int row_blocks(int n, int rpw);
 int vec_blocks(int n, int num_sms);
-size_t partial_slot_size(int n0, int num_sms);
+size_t partial_slot_size(int n0, int num_sms);  // >= num_sms + 2
 size_t partial_slot_count();
 
 // ----------------------------------------------------------------- device helpers

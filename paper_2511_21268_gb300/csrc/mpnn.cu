@@ -57,31 +57,39 @@ constexpr int kGradSlots = 2 * H * H + H;  // partial sums one block writes (lar
 __device__ __forceinline__ float round_bf16(float w) { return __bfloat162float(__float2bfloat16_rn(w)); }
 
 // ---------------------------------------------------------------- features
+// s_i = 1 / sqrt(k_ii) (FP32 copy of the FP64 value)
+__global__ void k_nn_rsqrt_diag(int n, const double* __restrict__ kii, float* __restrict__ s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) s[i] = (float)(1.0 / sqrt(kii[i]));
+}
+
+// Node features and edge weights in FP32: a_ij = s_i k_ij s_j (j != i),
+// rho_i = sum |k_ij| / k_ii, sig_i = sum k_ij / k_ii over j != i.
 __global__ void k_nn_features(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                              const double* __restrict__ v, const double* __restrict__ kii, float* __restrict__ x,
-                              float* __restrict__ ap) {
+                              const double* __restrict__ v, const double* __restrict__ kii,
+                              const float* __restrict__ sd, float* __restrict__ x, float* __restrict__ ap) {
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
-        const double ki = kii[i];
-        const double si = 1.0 / sqrt(ki);
-        double ab = 0.0, sg = 0.0;
+        const float si = sd[i];
+        float ab = 0.f, sg = 0.f;
         for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
             const int j = ci[k];
-            const double a = v[k];
+            const float a = (float)v[k];
             float out = 0.f;
             if (j != i) {
-                ab += fabs(a);
+                ab += fabsf(a);
                 sg += a;
-                out = (float)(si * a * (1.0 / sqrt(kii[j])));
+                out = si * a * sd[j];
             }
             ap[k] = out;
         }
-        ab = warp_sum(ab);
-        sg = warp_sum(sg);
+        ab = warp_sumf(ab);
+        sg = warp_sumf(sg);
         if (lane == 0) {
-            x[4 * (int64_t)i + 0] = (float)(ab / ki);
-            x[4 * (int64_t)i + 1] = (float)(sg / ki);
+            const float ki = (float)kii[i];
+            x[4 * (int64_t)i + 0] = ab / ki;
+            x[4 * (int64_t)i + 1] = sg / ki;
             x[4 * (int64_t)i + 2] = (float)(log2((double)(rp[i + 1] - rp[i])) / 8.0);
             x[4 * (int64_t)i + 3] = 1.f;
         }
@@ -571,8 +579,10 @@ int prepare(amg_hierarchy* h) {
         MP_ALLOC(m.omega, sizeof(float) * n);
         MP_ALLOC(m.domega, sizeof(double) * n);
         for (int t = 0; t < MpnnLevel::kVec; t++) MP_ALLOC(m.v[t], sizeof(double) * n);
-        k_nn_features<<<AMG_GRID(grid_rows(h, n)), kBlock, 0, s>>>((int)n, L.A.rowptr, L.A.col, L.A.val, L.kii, m.x,
-                                                                     m.ap);
+        // m.sg holds 1 / sqrt(k_ii) until the first network evaluation
+        k_nn_rsqrt_diag<<<AMG_GRID(eblk(n)), kBlock, 0, s>>>((int)n, L.kii, m.sg);
+        k_nn_features<<<AMG_GRID(grid_rows(h, n)), kBlock, 0, s>>>((int)n, L.A.rowptr, L.A.col, L.A.val, L.kii, m.sg,
+                                                                     m.x, m.ap);
     }
     for (int t = 0; t < 3; t++) MP_ALLOC(w.bw[t], sizeof(float) * H * n0);
     MP_ALLOC(w.part, sizeof(float) * kGradBlocks * kGradSlots);

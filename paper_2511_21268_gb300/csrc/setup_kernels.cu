@@ -913,6 +913,63 @@ __global__ void k_fill_sys_id(int nsys, const int64_t* __restrict__ off, int32_t
     for (int64_t i = off[s] + threadIdx.x; i < off[s + 1]; i += blockDim.x) id[i] = s;
 }
 
+// ------------------------------------------------ run-encoded column index
+// A row qualifies when its columns split into runs of L consecutive
+// columns, all of the same length L (2 <= L <= kMaxRunLen, rows shorter than
+// 2^16 entries); the tensor-product
+// IgA matrices have this form (L = the row's band width in the fastest
+// direction).  k_run_rows (a warp per row) writes the run count and L of
+// every row, or sets *flag when a row does not qualify.
+__global__ void k_run_rows(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t* runcnt,
+                           uint8_t* runlen, int* flag) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        const int64_t b = rp[i], e = rp[i + 1];
+        // length of the first run: position of the first break after b
+        int64_t first_break = e;
+        for (int64_t k0 = b + 1; k0 < e && first_break == e; k0 += 32) {
+            const int64_t k = k0 + lane;
+            const bool brk = k < e && ci[k] != ci[k - 1] + 1;
+            const unsigned m = __ballot_sync(0xffffffffu, brk);
+            if (m) first_break = k0 + __ffs(m) - 1;
+        }
+        const int64_t L = first_break - b;
+        bool ok = L >= 2 && L <= kMaxRunLen && (e - b) % L == 0 && (e - b) < 65536;
+        if (ok) {
+            for (int64_t k = b + 1 + lane; k < e; k += 32) {
+                const bool brk = ci[k] != ci[k - 1] + 1;
+                if (brk != ((k - b) % L == 0)) ok = false;
+            }
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (lane == 0) {
+            if (ok) {
+                runcnt[i] = (int32_t)((e - b) / L);
+                runlen[i] = (uint8_t)L;
+            } else {
+                runcnt[i] = 0;
+                runlen[i] = 0;
+                atomicOr(flag, 1);
+            }
+        }
+    }
+}
+
+// run_start[run_ptr[i] + r] = first column of run r of row i
+__global__ void k_run_fill(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const int32_t* __restrict__ run_ptr, const uint8_t* __restrict__ runlen,
+                           int32_t* run_start) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        const int64_t b = rp[i];
+        const int L = runlen[i];
+        const int r0 = run_ptr[i], R = run_ptr[i + 1] - r0;
+        for (int r = lane; r < R; r += 32) run_start[r0 + r] = ci[b + (int64_t)r * L];
+    }
+}
+
 }  // namespace
 
 // ============================================================== launch wrappers
@@ -920,6 +977,21 @@ cudaError_t launch_shift_block(int n, int64_t nnz, const int64_t* rp_in, int64_t
                                int64_t* rp_out, int32_t* col, int* flag, cudaStream_t s) {
     const int64_t m = (nnz > (int64_t)n + 1 ? nnz : (int64_t)n + 1);
     k_shift_block<<<AMG_GRID((int)((m + 255) / 256)), 256, 0, s>>>(n, nnz, rp_in, row_off, nnz_off, rp_out, col, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_run_rows(const DevCSR& A, int32_t* runcnt, uint8_t* runlen, int* flag, cudaStream_t s) {
+    if (A.n == 0) return cudaSuccess;
+    k_run_rows<<<AMG_GRID(blocks_for(A.n, kWarpsPerBlock, 8192)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, runcnt, runlen,
+                                                                                    flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_run_fill(const DevCSR& A, const int32_t* run_ptr, const uint8_t* runlen, int32_t* run_start,
+                            cudaStream_t s) {
+    if (A.n == 0) return cudaSuccess;
+    k_run_fill<<<AMG_GRID(blocks_for(A.n, kWarpsPerBlock, 8192)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, run_ptr,
+                                                                                    runlen, run_start);
     return cudaGetLastError();
 }
 

@@ -72,14 +72,71 @@ __device__ __forceinline__ A lane_partial(const int64_t* __restrict__ rp, const 
     return acc;
 }
 
+// Matrix views of the row-group kernels.  CsrM: plain CSR.  RunM: CSR
+// values with run-encoded columns (every row a sequence of equal runs of L
+// consecutive columns): one 4-byte start column per run replaces the run's
+// column indices, so a pass reads s_v + 4/L bytes per entry from HBM
+// instead of s_v + 4.  The lanes keep the CSR order (lane t reads entries
+// b + t + 32 j, coalesced); entry b + u lies in run u / L at offset u % L,
+// the quotient taken as __umulhi(u, ceil(2^32 / L)) (exact for u < 2^16),
+// and the run's start column is an L1-resident load shared by the L lanes
+// of the run.
+__constant__ uint32_t kRunMagic[kMaxRunLen + 1] = {0u,          0u,          2147483648u, 1431655766u, 1073741824u,
+                                                   858993460u,  715827883u,  613566757u,  536870912u,  477218589u};
+
+template <typename V>
+struct CsrM {
+    const int64_t* __restrict__ rp;
+    const int32_t* __restrict__ ci;
+    const V* __restrict__ v;
+    template <typename A, typename X>
+    __device__ __forceinline__ A partial(const X* __restrict__ x, int i, int lane) const {
+        return lane_partial<A>(rp, ci, v, x, i, lane);
+    }
+};
+
+template <typename V>
+struct RunM {
+    const int64_t* __restrict__ rp;
+    const int32_t* __restrict__ rptr;
+    const uint8_t* __restrict__ rlen;
+    const int32_t* __restrict__ rst;
+    const V* __restrict__ v;
+    template <typename A, typename X>
+    __device__ __forceinline__ A partial(const X* __restrict__ x, int i, int lane) const {
+        const int64_t b = __ldg(rp + i), e = __ldg(rp + i + 1);
+        const uint32_t L = rlen[i];
+        const uint32_t mg = kRunMagic[L];
+        const int32_t* __restrict__ rs = rst + __ldg(rptr + i);
+        const uint32_t len = (uint32_t)(e - b);
+        const V* __restrict__ vr = v + b;
+        A acc = A(0);
+        uint32_t u = lane;
+        auto col = [&](uint32_t w) {
+            const uint32_t q = __umulhi(w, mg);
+            return __ldg(rs + q) + (int)(w - q * L);
+        };
+        for (; u + 96 < len; u += 128) {
+            const A v0 = (A)ldv(vr, u), v1 = (A)ldv(vr, u + 32), v2 = (A)ldv(vr, u + 64), v3 = (A)ldv(vr, u + 96);
+            const int c0 = col(u), c1 = col(u + 32), c2 = col(u + 64), c3 = col(u + 96);
+            const A x0 = (A)x[c0], x1 = (A)x[c1], x2 = (A)x[c2], x3 = (A)x[c3];
+            acc = fma(v0, x0, acc);
+            acc = fma(v1, x1, acc);
+            acc = fma(v2, x2, acc);
+            acc = fma(v3, x3, acc);
+        }
+        for (; u < len; u += 32) acc = fma((A)ldv(vr, u), (A)x[col(u)], acc);
+        return acc;
+    }
+};
+
 // Row totals for the RPW rows row0 .. row0+RPW-1 (rows >= n give 0).
 // Returns the total of row `row0 + lane / (32/RPW)` on every lane.
-template <int RPW, typename A, typename V, typename X>
-__device__ __forceinline__ A group_rows(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                        const V* __restrict__ v, const X* __restrict__ x, int row0, int n, int lane,
+template <int RPW, typename A, typename M, typename X>
+__device__ __forceinline__ A group_rows(const M& mat, const X* __restrict__ x, int row0, int n, int lane,
                                         A (*tile)[33]) {
     if constexpr (RPW == 1) {
-        A s = row0 < n ? lane_partial<A>(rp, ci, v, x, row0, lane) : A(0);
+        A s = row0 < n ? mat.template partial<A>(x, row0, lane) : A(0);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
         return s;
@@ -88,7 +145,7 @@ __device__ __forceinline__ A group_rows(const int64_t* __restrict__ rp, const in
 #pragma unroll 1
         for (int r = 0; r < RPW; r++) {
             const int i = row0 + r;
-            tile[r][lane] = i < n ? lane_partial<A>(rp, ci, v, x, i, lane) : A(0);
+            tile[r][lane] = i < n ? mat.template partial<A>(x, i, lane) : A(0);
         }
         __syncwarp();
         const int r = lane / LPR, q = lane % LPR;
@@ -156,35 +213,41 @@ __device__ double sum_partials(const double* __restrict__ part, int nb, double* 
     (void)owner;
 
 // ----------------------------------------------------------------- kernels
-template <int RPW>
-__global__ void __launch_bounds__(kBlock) k_spmv(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                  const double* __restrict__ v, const double* __restrict__ x,
-                                                  double* y) {
+template <int RPW, typename M>
+__global__ void __launch_bounds__(kBlock) k_spmv(int n, M mat, const double* __restrict__ x, double* y) {
     ROWGROUP_PROLOGUE(double)
-    const double s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
+    const double s = group_rows<RPW, double>(mat, x, row0, n, lane, tiles[wid]);
     if (owner) y[myrow] = s;
 }
 
 // FP64: r = F - K x, x0 = r / d (optional, in X0), partials ||r||^2, ||F||^2.
 // `gate` (optional): run only while the solve is not done and a
 // residual replacement is due.
-template <int RPW, typename X0>
-__global__ void __launch_bounds__(kBlock) k_residual0(int n, const int64_t* __restrict__ rp,
-                                                       const int32_t* __restrict__ ci, const double* __restrict__ v,
-                                                       const double* __restrict__ x, const double* __restrict__ F,
+template <int RPW, typename X0, typename M>
+__global__ void __launch_bounds__(kBlock) k_residual0(int n, M mat, const double* __restrict__ x,
+                                                       const double* __restrict__ F,
                                                        const X0* __restrict__ invd, double* r, X0* x0,
                                                        double* part_rr, double* part_ff, const SolveState* gate) {
+    // grid-stride over row groups (a small grid: the gated launch of every
+    // mixed-precision iteration returns at once unless a replacement is due)
     if (gate && (gate->done || !gate->replace_now)) return;
-    ROWGROUP_PROLOGUE(double)
+    __shared__ double tiles[kWarpsPerBlock][RPW][33];
     __shared__ double sh[kWarpsPerBlock];
-    const double s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int LPR = 32 / RPW;
     double rr = 0.0, ff = 0.0;
-    if (owner) {
-        const double fi = F[myrow], ri = fi - s;
-        r[myrow] = ri;
-        if (x0) x0[myrow] = (X0)ri * invd[myrow];
-        rr = ri * ri;
-        ff = fi * fi;
+    const int ngroups = (n + RPW - 1) / RPW;
+    for (int g = blockIdx.x * kWarpsPerBlock + wid; g - wid < ngroups; g += gridDim.x * kWarpsPerBlock) {
+        const int row0 = g * RPW;  // groups past the end give zero rows (uniform per block)
+        const double s = group_rows<RPW, double>(mat, x, row0, n, lane, tiles[wid]);
+        const int myrow = row0 + lane / LPR;
+        if ((lane % LPR) == 0 && myrow < n) {
+            const double fi = F[myrow], ri = fi - s;
+            r[myrow] = ri;
+            if (x0) x0[myrow] = (X0)ri * invd[myrow];
+            rr += ri * ri;
+            ff += fi * fi;
+        }
     }
     block_partial(rr, sh, part_rr + blockIdx.x);
     if (part_ff) block_partial(ff, sh, part_ff + blockIdx.x);
@@ -192,16 +255,15 @@ __global__ void __launch_bounds__(kBlock) k_residual0(int n, const int64_t* __re
 
 // Outer SpMV q = K p (values V, gathered vector PX, accumulation A; q FP64),
 // partials p.q and (flexible) p.r with the FP64 p.
-template <int RPW, typename A, typename V, typename PX>
-__global__ void __launch_bounds__(kBlock) k_spmv_pq(int n, const int64_t* __restrict__ rp,
-                                                     const int32_t* __restrict__ ci, const V* __restrict__ v,
-                                                     const PX* __restrict__ pg, const double* __restrict__ p,
+template <int RPW, typename A, typename M, typename PX>
+__global__ void __launch_bounds__(kBlock) k_spmv_pq(int n, M mat, const PX* __restrict__ pg,
+                                                     const double* __restrict__ p,
                                                      const double* __restrict__ r, double* q, double* part_pq,
                                                      double* part_pr, int flexible, const SolveState* st) {
     DONE_GUARD(st);
     ROWGROUP_PROLOGUE(A)
     __shared__ double sh[kWarpsPerBlock];
-    const A s = group_rows<RPW>(rp, ci, v, pg, row0, n, lane, tiles[wid]);
+    const A s = group_rows<RPW, A>(mat, pg, row0, n, lane, tiles[wid]);
     double pq = 0.0, pr = 0.0;
     if (owner) {
         const double qs = (double)s;
@@ -215,39 +277,35 @@ __global__ void __launch_bounds__(kBlock) k_spmv_pq(int n, const int64_t* __rest
 }
 
 // rbuf = f - K x (down-sweep residual of one level).
-template <int RPW, typename A, typename V, typename FT, typename XT>
-__global__ void __launch_bounds__(kBlock) k_resid(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                   const V* __restrict__ v, const FT* __restrict__ f,
-                                                   const XT* __restrict__ x, A* rbuf, const SolveState* st) {
+template <int RPW, typename A, typename M, typename FT, typename XT>
+__global__ void __launch_bounds__(kBlock) k_resid(int n, M mat, const FT* __restrict__ f, const XT* __restrict__ x,
+                                                   A* rbuf, const SolveState* st) {
     DONE_GUARD(st);
     ROWGROUP_PROLOGUE(A)
-    const A s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
+    const A s = group_rows<RPW, A>(mat, x, row0, n, lane, tiles[wid]);
     if (owner) rbuf[myrow] = (A)f[myrow] - s;
 }
 
 // t = x + (f - K x) / d (extra smoothing sweep).
-template <int RPW, typename A, typename V, typename FT>
-__global__ void __launch_bounds__(kBlock) k_sweep(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                   const V* __restrict__ v, const FT* __restrict__ f,
-                                                   const A* __restrict__ x, const A* __restrict__ invd, A* t,
-                                                   const SolveState* st) {
+template <int RPW, typename A, typename M, typename FT>
+__global__ void __launch_bounds__(kBlock) k_sweep(int n, M mat, const FT* __restrict__ f, const A* __restrict__ x,
+                                                   const A* __restrict__ invd, A* t, const SolveState* st) {
     DONE_GUARD(st);
     ROWGROUP_PROLOGUE(A)
-    const A s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
+    const A s = group_rows<RPW, A>(mat, x, row0, n, lane, tiles[wid]);
     if (owner) t[myrow] = fma(invd[myrow], (A)f[myrow] - s, x[myrow]);
 }
 
 // Up sweep of level l >= 1: y_a = x_a + (f_a - (K x)_a) / d_a, then
 // x_{l-1}[c] += p_c y_a for the members c of a.
-template <int RPW, typename A, typename V>
-__global__ void __launch_bounds__(kBlock) k_up(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                const V* __restrict__ v, const A* __restrict__ f,
-                                                const A* __restrict__ x, const A* __restrict__ invd,
+template <int RPW, typename A, typename M>
+__global__ void __launch_bounds__(kBlock) k_up(int n, M mat, const A* __restrict__ f, const A* __restrict__ x,
+                                                const A* __restrict__ invd,
                                                 const int32_t* __restrict__ mptr, const int32_t* __restrict__ midx,
                                                 const double* __restrict__ pvalf, A* xf, const SolveState* st) {
     DONE_GUARD(st);
     ROWGROUP_PROLOGUE(A)
-    const A s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
+    const A s = group_rows<RPW, A>(mat, x, row0, n, lane, tiles[wid]);
     if (owner) {
         const A y = fma(invd[myrow], f[myrow] - s, x[myrow]);
         for (int m = mptr[myrow]; m < mptr[myrow + 1]; m++) {
@@ -259,16 +317,15 @@ __global__ void __launch_bounds__(kBlock) k_up(int n, const int64_t* __restrict_
 
 // Up sweep of level 0: z = x + (r - K x) / d (z FP64); partials r.z and
 // (flexible) z.q.
-template <int RPW, typename A, typename V>
-__global__ void __launch_bounds__(kBlock) k_up0(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                 const V* __restrict__ v, const double* __restrict__ r,
+template <int RPW, typename A, typename M>
+__global__ void __launch_bounds__(kBlock) k_up0(int n, M mat, const double* __restrict__ r,
                                                  const A* __restrict__ x, const A* __restrict__ invd, double* z,
                                                  const double* __restrict__ q, double* part_rz, double* part_zq,
                                                  int flexible, const SolveState* st) {
     DONE_GUARD(st);
     ROWGROUP_PROLOGUE(A)
     __shared__ double sh[kWarpsPerBlock];
-    const A s = group_rows<RPW>(rp, ci, v, x, row0, n, lane, tiles[wid]);
+    const A s = group_rows<RPW, A>(mat, x, row0, n, lane, tiles[wid]);
     double rz = 0.0, zq = 0.0;
     if (owner) {
         const double ra = r[myrow];
@@ -527,7 +584,7 @@ cudaError_t launch_spmv(const DevCSR& A, const double* x, double* y, cudaStream_
     const int nb = row_blocks(A.n, rpw);
     if (A.n == 0) return cudaSuccess;
     with_rpw(rpw, [&](auto R) {
-        k_spmv<decltype(R)::value><<<AMG_GRID(nb), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, y);
+        k_spmv<decltype(R)::value><<<AMG_GRID(nb), kBlock, 0, s>>>(A.n, CsrM<double>{A.rowptr, A.col, A.val}, x, y);
     });
     return cudaGetLastError();
 }
@@ -544,6 +601,14 @@ static double* slot(amg_hierarchy* h, int k) { return h->partials + (int64_t)k *
 enum { S_RR = 0, S_FF, S_PQ, S_PR, S_RZ, S_ZQ, S_OUT, S_RR2, S_COUNT };
 
 // ---------------------------------------------------------- per-mode views
+// Matrix view of level L with values v: run-encoded columns when the level
+// has them, plain CSR otherwise.
+template <typename V, typename Fn>
+static void with_mat(const Level& L, const V* v, Fn&& fn) {
+    if (L.run_ptr) fn(RunM<V>{L.A.rowptr, L.run_ptr, L.run_len, L.run_start, v});
+    else fn(CsrM<V>{L.A.rowptr, L.A.col, v});
+}
+
 // Vectors and values of a level in the V-cycle precision A.
 template <typename A>
 struct View;
@@ -555,7 +620,7 @@ struct View<double> {
     static double* t(Level& L) { return L.t; }
     static const double* invd(Level& L) { return L.invd; }
     template <typename Fn>
-    static void vals(Level& L, int, Fn&& fn) { fn(static_cast<const double*>(L.A.val)); }
+    static void vals(Level& L, int, Fn&& fn) { with_mat(L, static_cast<const double*>(L.A.val), fn); }
 };
 
 template <>
@@ -566,8 +631,8 @@ struct View<float> {
     static const float* invd(Level& L) { return L.invd32; }
     template <typename Fn>
     static void vals(Level& L, int l, Fn&& fn) {
-        if (l == 0 && L.val16) fn(static_cast<const __nv_bfloat16*>(L.val16));
-        else fn(static_cast<const float*>(L.val32));
+        if (l == 0 && L.val16) with_mat(L, static_cast<const __nv_bfloat16*>(L.val16), fn);
+        else with_mat(L, static_cast<const float*>(L.val32), fn);
     }
 };
 
@@ -601,16 +666,16 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
         Level& C = h->lev[l + 1];
         const int n = F.A.n;
         const int rpw = rows_per_warp(n, sms), nb = row_blocks(n, rpw);
-        Vw::vals(F, l, [&](auto vp) {
-            using V = vtype<decltype(vp)>;
+        Vw::vals(F, l, [&](auto mat) {
+            using M = decltype(mat);
             auto sweep_and_resid = [&](auto fp) {
                 using FT = vtype<decltype(fp)>;
                 for (int sw = 1; sw < h->o.nu_pre; sw++) {
                     A* xo = xcur[l];
                     A* xn = xalt[l];
                     with_rpw(rpw, [&](auto R) {
-                        k_sweep<decltype(R)::value, A, V, FT><<<AMG_GRID(nb), kBlock, 0, s>>>(
-                            n, F.A.rowptr, F.A.col, vp, fp, xo, Vw::invd(F), xn, st);
+                        k_sweep<decltype(R)::value, A, M, FT><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                            n, mat, fp, xo, Vw::invd(F), xn, st);
                     });
                     xcur[l] = xn;
                     xalt[l] = xo;
@@ -618,9 +683,15 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
                 A* rb = xalt[l];  // free buffer of this level holds the residual
                 const A* xc = xcur[l];
                 if (l == 0) prof_mark(h, 1, 0, s);
+                if constexpr (std::is_same_v<A, float>) {
+                    if (l == 0 && h->stream) {
+                        launch_stream_resid(h, h->r, xc, rb, s);
+                        prof_mark(h, 1, 1, s);
+                        return;
+                    }
+                }
                 with_rpw(rpw, [&](auto R) {
-                    k_resid<decltype(R)::value, A, V, FT, A><<<AMG_GRID(nb), kBlock, 0, s>>>(
-                        n, F.A.rowptr, F.A.col, vp, fp, xc, rb, st);
+                    k_resid<decltype(R)::value, A, M, FT, A><<<AMG_GRID(nb), kBlock, 0, s>>>(n, mat, fp, xc, rb, st);
                 });
                 if (l == 0) prof_mark(h, 1, 1, s);
             };
@@ -644,16 +715,16 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
         Level& F = h->lev[l];
         const int n = F.A.n;
         const int rpw = rows_per_warp(n, sms), nb = row_blocks(n, rpw);
-        Vw::vals(F, l, [&](auto vp) {
-            using V = vtype<decltype(vp)>;
+        Vw::vals(F, l, [&](auto mat) {
+            using M = decltype(mat);
             auto sweeps = [&](auto fp) {
                 using FT = vtype<decltype(fp)>;
                 for (int sw = 1; sw < h->o.nu_post; sw++) {
                     A* xo = xcur[l];
                     A* xn = xalt[l];
                     with_rpw(rpw, [&](auto R) {
-                        k_sweep<decltype(R)::value, A, V, FT><<<AMG_GRID(nb), kBlock, 0, s>>>(
-                            n, F.A.rowptr, F.A.col, vp, fp, xo, Vw::invd(F), xn, st);
+                        k_sweep<decltype(R)::value, A, M, FT><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                            n, mat, fp, xo, Vw::invd(F), xn, st);
                     });
                     xcur[l] = xn;
                     xalt[l] = xo;
@@ -664,18 +735,25 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
             const A* xc = xcur[l];
             if (l == 0) {
                 prof_mark(h, 2, 0, s);
+                if constexpr (std::is_same_v<A, float>) {
+                    if (h->stream) {
+                        launch_stream_up0(h, h->r, xc, Vw::invd(F), h->z, h->q, slot(h, S_RZ), slot(h, S_ZQ), flex,
+                                          s);
+                        prof_mark(h, 2, 1, s);
+                        return;
+                    }
+                }
                 with_rpw(rpw, [&](auto R) {
-                    k_up0<decltype(R)::value, A, V><<<AMG_GRID(nb), kBlock, 0, s>>>(
-                        n, F.A.rowptr, F.A.col, vp, h->r, xc, Vw::invd(F), h->z, h->q, slot(h, S_RZ), slot(h, S_ZQ),
-                        flex, st);
+                    k_up0<decltype(R)::value, A, M><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                        n, mat, h->r, xc, Vw::invd(F), h->z, h->q, slot(h, S_RZ), slot(h, S_ZQ), flex, st);
                 });
                 prof_mark(h, 2, 1, s);
             } else {
                 Level& G = h->lev[l - 1];
                 A* xf = xcur[l - 1];
                 with_rpw(rpw, [&](auto R) {
-                    k_up<decltype(R)::value, A, V><<<AMG_GRID(nb), kBlock, 0, s>>>(
-                        n, F.A.rowptr, F.A.col, vp, Vw::f(F), xc, Vw::invd(F), G.mem_ptr, G.mem_idx, G.pval, xf, st);
+                    k_up<decltype(R)::value, A, M><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                        n, mat, Vw::f(F), xc, Vw::invd(F), G.mem_ptr, G.mem_idx, G.pval, xf, st);
                 });
             }
         });
@@ -691,12 +769,20 @@ cudaError_t enqueue_vcycle(amg_hierarchy* h, cudaStream_t s) {
 // kernel that produces z (level-0 up sweep or single-level coarse solve)
 static int nb0(amg_hierarchy* h) { return row_blocks(h->lev[0].A.n, rows_per_warp(h->lev[0].A.n, h->num_sms)); }
 static int nbv(amg_hierarchy* h) { return vec_blocks(h->lev[0].A.n, h->num_sms); }
-static int nbz(amg_hierarchy* h) { return h->nlev > 1 ? nb0(h) : row_blocks(h->ndense, 1); }
+// blocks (= partial sums) of the FP64 residual kernel
+static int nb_res(amg_hierarchy* h) {
+    const int b = nb0(h), cap = h->num_sms * 4;
+    return b < cap ? b : cap;
+}
+// partial sums written by the level-0 q = K p and up-sweep kernels
+static int nb_fine(amg_hierarchy* h) { return h->stream ? h->stream_blocks : nb0(h); }
+static int nbz(amg_hierarchy* h) { return h->nlev > 1 ? nb_fine(h) : row_blocks(h->ndense, 1); }
 
 size_t partial_slot_size(int n0, int num_sms) {
     const int a = row_blocks(n0, rows_per_warp(n0, num_sms));
     const int b = vec_blocks(n0, num_sms);
-    return (size_t)((a > b ? a : b) + 2);
+    const int m = a > b ? a : b;
+    return (size_t)((m > num_sms ? m : num_sms) + 2);
 }
 
 size_t partial_slot_count() { return S_COUNT; }
@@ -707,19 +793,22 @@ static cudaError_t launch_residual(amg_hierarchy* h, double* r, bool want_x0, in
                                    const SolveState* gate, cudaStream_t s) {
     Level& L0 = h->lev[0];
     const int n = L0.A.n;
-    const int rpw = rows_per_warp(n, h->num_sms), nb = row_blocks(n, rpw);
+    const int rpw = rows_per_warp(n, h->num_sms), nb = nb_res(h);
     const bool x0 = want_x0 && h->nlev > 1;
     double* pff = ff ? slot(h, S_FF) : nullptr;
     with_rpw(rpw, [&](auto R) {
         constexpr int RPW = decltype(R)::value;
-        if (h->mixed)
-            k_residual0<RPW, float><<<AMG_GRID(nb), kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->x, h->F,
-                                                                    L0.invd32, r, x0 ? L0.x32 : nullptr,
-                                                                    slot(h, rr_slot), pff, gate);
-        else
-            k_residual0<RPW, double><<<AMG_GRID(nb), kBlock, 0, s>>>(n, L0.A.rowptr, L0.A.col, L0.A.val, h->x, h->F,
-                                                                     L0.invd, r, x0 ? L0.x : nullptr,
-                                                                     slot(h, rr_slot), pff, gate);
+        with_mat(L0, static_cast<const double*>(L0.A.val), [&](auto mat) {
+            using M = decltype(mat);
+            if (h->mixed)
+                k_residual0<RPW, float, M><<<AMG_GRID(nb), kBlock, 0, s>>>(n, mat, h->x, h->F, L0.invd32, r,
+                                                                           x0 ? L0.x32 : nullptr, slot(h, rr_slot),
+                                                                           pff, gate);
+            else
+                k_residual0<RPW, double, M><<<AMG_GRID(nb), kBlock, 0, s>>>(n, mat, h->x, h->F, L0.invd, r,
+                                                                            x0 ? L0.x : nullptr, slot(h, rr_slot),
+                                                                            pff, gate);
+        });
     });
     return cudaGetLastError();
 }
@@ -732,7 +821,7 @@ static void launch_pupdate(amg_hierarchy* h, int first, cudaStream_t s) {
 // r = F - K x, ||F||, ||r||, first V-cycle, p = z, rho = r.z.
 cudaError_t enqueue_pcg_start(amg_hierarchy* h, cudaStream_t s) {
     AMG_TRY(launch_residual(h, h->r, true, S_RR, true, nullptr, s));
-    k_scal_init<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RR), slot(h, S_FF), nb0(h), h->rtol, h->itmax,
+    k_scal_init<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RR), slot(h, S_FF), nb_res(h), h->rtol, h->itmax,
                                             h->mixed ? h->o.resid_replace_every : 0, h->hist, h->st);
     AMG_TRY(cudaGetLastError());
     AMG_TRY(enqueue_vcycle(h, s));
@@ -749,15 +838,21 @@ cudaError_t enqueue_pcg_iteration(amg_hierarchy* h, cudaStream_t s) {
     prof_mark(h, 0, 0, s);
     with_rpw(rpw, [&](auto R) {
         constexpr int RPW = decltype(R)::value;
-        if (h->mixed)
-            k_spmv_pq<RPW, float, float, float><<<AMG_GRID(nb), kBlock, 0, s>>>(
-                n, L0.A.rowptr, L0.A.col, L0.val32, h->p32, h->p, h->r, h->q, slot(h, S_PQ), slot(h, S_PR), flex, h->st);
+        if (h->mixed && h->stream)
+            launch_stream_spmv_pq(h, h->p32, h->p, h->r, h->q, slot(h, S_PQ), slot(h, S_PR), flex, s);
+        else if (h->mixed)
+            with_mat(L0, static_cast<const float*>(L0.val32), [&](auto mat) {
+                k_spmv_pq<RPW, float, decltype(mat), float><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                    n, mat, h->p32, h->p, h->r, h->q, slot(h, S_PQ), slot(h, S_PR), flex, h->st);
+            });
         else
-            k_spmv_pq<RPW, double, double, double><<<AMG_GRID(nb), kBlock, 0, s>>>(
-                n, L0.A.rowptr, L0.A.col, L0.A.val, h->p, h->p, h->r, h->q, slot(h, S_PQ), slot(h, S_PR), flex, h->st);
+            with_mat(L0, static_cast<const double*>(L0.A.val), [&](auto mat) {
+                k_spmv_pq<RPW, double, decltype(mat), double><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                    n, mat, h->p, h->p, h->r, h->q, slot(h, S_PQ), slot(h, S_PR), flex, h->st);
+            });
     });
     prof_mark(h, 0, 1, s);
-    k_scal_alpha<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_PQ), slot(h, S_PR), nb, flex, h->st);
+    k_scal_alpha<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_PQ), slot(h, S_PR), nb_fine(h), flex, h->st);
     const bool x0 = h->nlev > 1;
     if (h->mixed)
         k_update<float><<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(n, h->x, h->r, h->p, h->q, L0.invd32, x0 ? L0.x32 : nullptr,
@@ -768,7 +863,7 @@ cudaError_t enqueue_pcg_iteration(amg_hierarchy* h, cudaStream_t s) {
     k_scal_conv<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RR), nbv(h), h->hist, h->hist_cap, h->mixed, h->st);
     if (h->mixed) {  // FP64 true-residual replacement, when due
         AMG_TRY(launch_residual(h, h->r, true, S_RR2, false, h->st, s));
-        k_scal_replaced<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RR2), nb0(h), h->hist, h->hist_cap, h->st);
+        k_scal_replaced<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RR2), nb_res(h), h->hist, h->hist_cap, h->st);
     }
     AMG_TRY(cudaGetLastError());
     AMG_TRY(enqueue_vcycle(h, s));
@@ -780,8 +875,8 @@ cudaError_t enqueue_pcg_iteration(amg_hierarchy* h, cudaStream_t s) {
 // ||F - K x|| and ||F|| into slot(S_OUT)[0..1] (FP64, recomputed).
 cudaError_t launch_final_residual(amg_hierarchy* h, cudaStream_t s) {
     AMG_TRY(launch_residual(h, h->q, false, S_RR, true, nullptr, s));
-    k_sqrt_sum<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RR), nb0(h), slot(h, S_OUT));
-    k_sqrt_sum<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_FF), nb0(h), slot(h, S_OUT) + 1);
+    k_sqrt_sum<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RR), nb_res(h), slot(h, S_OUT));
+    k_sqrt_sum<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_FF), nb_res(h), slot(h, S_OUT) + 1);
     return cudaGetLastError();
 }
 

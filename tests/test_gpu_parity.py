@@ -102,9 +102,11 @@ def test_level_spmv_matches_oracle(d, n, p):
 
 @pytest.mark.parametrize("d,n,p", CASES)
 @pytest.mark.parametrize("nu", [(1, 1), (2, 3)])
-def test_vcycle_matches_oracle(d, n, p, nu):
+@pytest.mark.parametrize("fmt", [0, 1], ids=["csr", "runs"])
+def test_vcycle_matches_oracle(d, n, p, nu, fmt):
     prob = I.poisson_box(d, n, p)
-    H, Ho = setup_both(prob, coarse_max=20, nu_pre=nu[0], nu_post=nu[1])
+    H, Ho = setup_both(prob, coarse_max=20, nu_pre=nu[0], nu_post=nu[1], matrix_format=fmt)
+    assert H.info.level_format[0] == fmt  # tensor-product rows: equal runs of consecutive columns
     rng = np.random.default_rng(1)
     for _ in range(3):
         r = rng.standard_normal(prob.n)
@@ -129,8 +131,9 @@ def compare_solves(prob, rtol, flexible=False, **opts):
 
 
 @pytest.mark.parametrize("d,n,p", CASES)
-def test_pcg_matches_oracle(d, n, p):
-    compare_solves(I.poisson_box(d, n, p), 1e-8, coarse_max=20)
+@pytest.mark.parametrize("fmt", [0, 1], ids=["csr", "runs"])
+def test_pcg_matches_oracle(d, n, p, fmt):
+    compare_solves(I.poisson_box(d, n, p), 1e-8, coarse_max=20, matrix_format=fmt)
 
 
 def test_pcg_small_plain_method_config():

@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-annulus", action="store_true")
     ap.add_argument("--train-steps", type=int, default=60)
     ap.add_argument("--matrix-format", type=int, choices=[0, 1, 2], default=2,
                     help="2 = run-encoded finest level + bulk-copy streamed mixed passes (default), 1 = run-encoded, 0 = CSR")
@@ -386,6 +387,78 @@ def batched_leg(args, A, I, torch, np, stream):
             "timed": "setup + solve + free per batch (one-by-one: per system; the 16-RHS baseline shares one setup)"}
 
 
+def annulus_leg(args, A, I, torch, np, stream, dist):
+    """Learned-damping workload: quarter annulus (NURBS arc, radii 1 and 2)
+    extruded over z in [0, 1], B-splines p=3, n=64, kappa = exp(g), g a
+    seeded Gaussian random field (correlation length 0.2, sigma 1).  The
+    network is trained (untimed) on annulus hierarchies with p in {2,3,4},
+    n in {16,32}; timed: plain FP64 AMG-PCG vs mixed precision + learned
+    damping, each step = setup (+ inference) + solve + free."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.perf_counter()
+    prob = I.annulus_kappa(64, 3)
+    asm_s = time.perf_counter() - t0
+    rp, ci, va, F = (torch.from_numpy(a).to(dev) for a in (prob.rowptr, prob.col, prob.val, prob.F))
+    train = []
+    for n in (16, 32):
+        for pp in (2, 3, 4):
+            q = I.annulus_kappa(n, pp)
+            train.append(A.amg_setup(torch.from_numpy(q.rowptr).to(dev), torch.from_numpy(q.col).to(dev),
+                                     torch.from_numpy(q.val).to(dev), A.amg_opts_default(), stream))
+    w = torch.from_numpy(I.mpnn_init_weights(1).astype(np.float32)).to(dev)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    hist = A.amg_mpnn_train(train, w, args.train_steps, 4, 2000, 1e-2)
+    train_s = time.perf_counter() - t1
+    for h in train:
+        A.amg_free(h)
+    o64 = A.amg_opts_default(matrix_format=args.matrix_format)
+    omx = A.amg_opts_default(precision=A.AMG_FP32_BF16FINE, matrix_format=args.matrix_format)
+
+    def step(opts, learned):
+        h = A.amg_setup(rp, ci, va, opts, stream)
+        if learned:
+            A.amg_mpnn_apply(h, w, True)
+        u = torch.zeros_like(F)
+        st, it, rr = A.amg_pcg_solve(h, F, u, args.rtol, 20000)
+        A.amg_free(h)
+        if st != A.AMG_OK:
+            raise RuntimeError(f"annulus solve failed: {A.amg_strerror(st)}")
+        return u, it, rr
+
+    def timed(opts, learned, k):
+        for _ in range(2):
+            step(opts, learned)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            u, it, rr = step(opts, learned)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(dist, e0.elapsed_time(e1)) / k, u, it, rr
+
+    k = max(2, min(args.steps, 3))
+    t64, u64, it64, rr64 = timed(o64, False, k)
+    tml, uml, itml, rrml = timed(omx, True, k)
+    h = A.amg_setup(rp, ci, va, omx, stream)
+    used, ip, il = A.amg_mpnn_select(h, w, F, args.rtol, 20000)
+    A.amg_free(h)
+    err = float(torch.linalg.norm(uml - u64) / torch.linalg.norm(u64))
+    return {"workload": "quarter annulus x [0,1], NURBS geometry, B-spline p=3 C^2, n=64 (N=274,625, nnz=86,938,307), "
+                        "kappa = exp(g), random Fourier features M=256, l=0.2, sigma=1",
+            "assembly_s": asm_s, "fp64_time_to_solution_s": t64 / 1e3, "fp64_iters": it64,
+            "mixed_learned_time_to_solution_s": tml / 1e3, "mixed_learned_iters": itml,
+            "speedup_vs_fp64": t64 / tml, "rel_error_vs_fp64_solution": err, "final_relres_fp64": rrml,
+            "fallback_rule": {"learned_kept": bool(used), "iters_mixed_plain": ip, "iters_mixed_learned": il},
+            "training": {"set": "annulus hierarchies p in {2,3,4}, n in {16,32} (FP64)", "steps": args.train_steps,
+                         "probes": 4, "lr": 1e-2, "seconds": train_s,
+                         "loss_first": float(hist[0]) if len(hist) else None,
+                         "loss_last": float(hist[-1]) if len(hist) else None},
+            "steps": k}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -570,6 +643,9 @@ def run_ours(args):
         batched = None
         if not args.no_batched:
             batched = batched_leg(args, A, I, torch, np, stream)
+        annulus = None
+        if not args.no_annulus:
+            annulus = annulus_leg(args, A, I, torch, np, stream, dist)
 
     peak, peak_kind = measured_peaks()
     avg_ms = ms_sum / np.maximum(cnt_sum, 1)
@@ -606,7 +682,7 @@ def run_ours(args):
             "vcycle_ms": vcycle_ms, "vcycle_gbps": vinfo.vcycle_bytes / (vcycle_ms * 1e-3) / 1e9,
             "throughput_systems_per_s": world * args.steps / (elapsed_ms * 1e-3),
             "roofline": roof, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches), "mixed": mixed,
-            "learned": learned, "batched": batched}
+            "learned": learned, "batched": batched, "annulus_learned": annulus}
     if mixed is not None:
         mixed["roofline"]["peak"] = peak
         mixed["roofline"]["frac"] = (mixed["roofline"]["achieved"] or 0.0) / peak

@@ -46,7 +46,7 @@ def _run(cmd: list[str]) -> None:
 def build_inputs(force: bool = False) -> str:
     if force or _stale(IGA_LIB, [IGA_SRC]):
         tmp = IGA_LIB + ".tmp"
-        _run(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, IGA_SRC, "-lm"])
+        _run(["gcc", "-O3", "-ffp-contract=off", "-fPIC", "-shared", "-pthread", "-o", tmp, IGA_SRC, "-lm"])
         os.replace(tmp, IGA_LIB)
     return IGA_LIB
 

@@ -428,151 +428,372 @@ void iga_geom_points(int geom, int d, int64_t npts, const double* xi, double* x,
 }
 
 /* ---------------------------------------------------- element loop ---- */
-/* k_ij = sum_e sum_q (grad_xi N_j)^T G (grad_xi N_i) kappa(x_q) w_q with
- * G = |det J| J^-1 J^-T, accumulated element by element (lexicographic, x
- * fastest) into the upper triangle (I <= J) and mirrored.  F_i = sum_e sum_q
- * f(x_q) N_i |det J| w_q, with f = 1 (fkind 0) or the manufactured source
- * d pi^2 prod sin(pi x_k) (fkind 1, identity geometry).  nq points per
- * direction. */
+/* k_ij = sum_e sum_q kappa(x_q) w_q |det J| (J^-T grad_xi N_i) . (J^-T grad_xi N_j),
+ * F_i = sum_e sum_q f(x_q) N_i |det J| w_q, with f = 1 (fkind 0) or the
+ * manufactured source d pi^2 prod sin(pi x_k) (fkind 1, identity geometry);
+ * nq Gauss points per direction.
+ *
+ * Element matrices: with B_q = sqrt(kappa w |det J|) J^-T grad_xi N (d x nloc),
+ * k^e = sum_q B_q^T B_q (upper triangle, in that order).  Elements are
+ * processed plane by plane (fixed e3): the element matrices of a plane are
+ * computed in parallel, then scattered into the upper triangle of K in
+ * parallel by ranges of the second row index, each entry receiving the
+ * element contributions in lexicographic element order (x fastest) -- the
+ * order of a sequential element loop, so the result does not depend on the
+ * thread count.  The lower triangle is mirrored at the end.
+ *
+ * kappa = exp(g), g = sigma sqrt(2/M) sum_m cos(w_m . x + phi_m): with
+ * x = (x(xi1, xi2), y(xi1, xi2), z(xi3)) (both geometries are extruded in
+ * z), cos(a + b) = cos a cos b - sin a sin b separates the (xi1, xi2) and
+ * xi3 parts, so kappa at all quadrature points costs M sines and cosines
+ * per point of each factor plus an M-term product sum per point. */
+#include <pthread.h>
+#include <unistd.h>
+
+typedef struct {
+    int d, n, p, nq, geom, off, m, P1, nloc, nqe, fkind, e3;
+    double h;
+    const double *V, *D, *gx, *gw;
+    const double* kap;  /* [z point][2-D point] or NULL (kappa = 1) */
+    double* ke;         /* [n^(d-1) elements of the plane][nloc (nloc+1) / 2] */
+    double* fe;         /* [elements][nloc] */
+    const int64_t* rowptr;
+    const int32_t* col;
+    double* val;
+    double* F;
+    int nthreads;
+} elem_ctx;
+
+typedef struct {
+    elem_ctx* c;
+    int t;
+} elem_job;
+
+static int num_threads(void) {
+    long t = sysconf(_SC_NPROCESSORS_ONLN);
+    if (t < 1) t = 1;
+    if (t > 32) t = 32;
+    return (int)t;
+}
+
+/* Run fn(job) on nthreads threads (thread t gets job t; a job whose thread
+ * cannot be created runs on the calling thread). */
+static void run_parallel(void* (*fn)(void*), elem_ctx* c) {
+    pthread_t th[32];
+    elem_job jobs[32];
+    int joined[32];
+    for (int t = 0; t < c->nthreads; t++) {
+        jobs[t].c = c;
+        jobs[t].t = t;
+        joined[t] = 0;
+        if (t > 0) {
+            if (pthread_create(&th[t], NULL, fn, &jobs[t]) == 0) joined[t] = 1;
+            else fn(&jobs[t]);
+        }
+    }
+    fn(&jobs[0]);
+    for (int t = 1; t < c->nthreads; t++)
+        if (joined[t]) pthread_join(th[t], NULL);
+}
+
+/* element matrix and load vector of element (e1, e2, c->e3) */
+static void element(const elem_ctx* c, int e1, int e2, double* ke, double* fe) {
+    const double pi = 3.14159265358979323846264338328;
+    const int d = c->d, nq = c->nq, P1 = c->P1, nloc = c->nloc, n = c->n, e3 = c->e3;
+    const double h = c->h;
+    double B[3][729]; /* nloc <= (IGA_MAXP + 1)^3 = 729 */
+    double N[729];
+    memset(ke, 0, sizeof(double) * nloc * (nloc + 1) / 2);
+    memset(fe, 0, sizeof(double) * nloc);
+    for (int qq = 0; qq < c->nqe; qq++) {
+        const int q1 = qq % nq, q2 = (qq / nq) % nq, q3 = (d == 3) ? qq / (nq * nq) : 0;
+        const double xi[3] = {(e1 + 0.5 * (c->gx[q1] + 1.0)) * h, (e2 + 0.5 * (c->gx[q2] + 1.0)) * h,
+                              (d == 3) ? (e3 + 0.5 * (c->gx[q3] + 1.0)) * h : 0.0};
+        double wq = (0.5 * h * c->gw[q1]) * (0.5 * h * c->gw[q2]);
+        if (d == 3) wq *= 0.5 * h * c->gw[q3];
+        double x[3] = {0, 0, 0}, J[3][3];
+        geom_eval(c->geom, d, xi, x, J);
+        double inv[3][3], detJ;
+        if (d == 2) {
+            detJ = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+            inv[0][0] = J[1][1] / detJ;
+            inv[0][1] = -J[0][1] / detJ;
+            inv[1][0] = -J[1][0] / detJ;
+            inv[1][1] = J[0][0] / detJ;
+        } else {
+            const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+            const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+            const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+            detJ = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+            inv[0][0] = c00 / detJ;
+            inv[1][0] = c01 / detJ;
+            inv[2][0] = c02 / detJ;
+            inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / detJ;
+            inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / detJ;
+            inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / detJ;
+            inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / detJ;
+            inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / detJ;
+            inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / detJ;
+        }
+        double kap = 1.0;
+        if (c->kap) {
+            const int nqn = n * nq;
+            const int64_t ip2 = (int64_t)(e2 * nq + q2) * nqn + (e1 * nq + q1);
+            const int64_t iz = (d == 3) ? (int64_t)(e3 * nq + q3) : 0;
+            kap = c->kap[iz * (int64_t)nqn * nqn + ip2];
+        }
+        double fval = 1.0;
+        if (c->fkind == 1) {
+            fval = d * pi * pi;
+            for (int k = 0; k < d; k++) fval *= sin(pi * x[k]);
+        }
+        const double sc = sqrt(kap * wq * fabs(detJ));
+        const double* v1 = c->V + (e1 * nq + q1) * P1;
+        const double* d1 = c->D + (e1 * nq + q1) * P1;
+        const double* v2 = c->V + (e2 * nq + q2) * P1;
+        const double* d2 = c->D + (e2 * nq + q2) * P1;
+        const double* v3 = c->V + (e3 * nq + q3) * P1;
+        const double* d3 = c->D + (e3 * nq + q3) * P1;
+        for (int l = 0; l < nloc; l++) {
+            const int a1 = l % P1, a2 = (l / P1) % P1, a3 = (d == 3) ? l / (P1 * P1) : 0;
+            double g[3];
+            if (d == 2) {
+                g[0] = d1[a1] * v2[a2];
+                g[1] = v1[a1] * d2[a2];
+                g[2] = 0.0;
+                N[l] = v1[a1] * v2[a2];
+            } else {
+                g[0] = d1[a1] * v2[a2] * v3[a3];
+                g[1] = v1[a1] * d2[a2] * v3[a3];
+                g[2] = v1[a1] * v2[a2] * d3[a3];
+                N[l] = v1[a1] * v2[a2] * v3[a3];
+            }
+            /* physical gradient J^-T g, scaled */
+            for (int r = 0; r < d; r++) {
+                double t = 0.0;
+                for (int k = 0; k < d; k++) t += inv[k][r] * g[k];
+                B[r][l] = sc * t;
+            }
+        }
+        const double fw = fval * fabs(detJ) * wq;
+        int64_t pos = 0;
+        for (int a = 0; a < nloc; a++) {
+            double* row = ke + pos - a; /* row[b] for b >= a */
+            const double b0 = B[0][a], b1 = B[1][a], b2 = d == 3 ? B[2][a] : 0.0;
+            if (d == 3) {
+                for (int b = a; b < nloc; b++) row[b] += (b0 * B[0][b] + b1 * B[1][b]) + b2 * B[2][b];
+            } else {
+                for (int b = a; b < nloc; b++) row[b] += b0 * B[0][b] + b1 * B[1][b];
+            }
+            pos += nloc - a;
+            fe[a] += fw * N[a];
+        }
+    }
+}
+
+static void* compute_job(void* arg) {
+    elem_job* j = (elem_job*)arg;
+    elem_ctx* c = j->c;
+    const int n = c->n, nel = n * n;
+    const int64_t kes = (int64_t)c->nloc * (c->nloc + 1) / 2;
+    for (int el = j->t; el < nel; el += c->nthreads) {
+        const int e1 = el % n, e2 = el / n;
+        element(c, e1, e2, c->ke + el * kes, c->fe + (int64_t)el * c->nloc);
+    }
+    return NULL;
+}
+
+/* scatter the plane's element matrices into rows whose second index lies in
+ * this thread's range [lo, hi) of i2 (element order e2, e1 ascending) */
+static void* scatter_job(void* arg) {
+    elem_job* j = (elem_job*)arg;
+    elem_ctx* c = j->c;
+    const int n = c->n, m = c->m, p = c->p, P1 = c->P1, nloc = c->nloc, d = c->d, off = c->off, e3 = c->e3;
+    const int lo = (int)((int64_t)m * j->t / c->nthreads), hi = (int)((int64_t)m * (j->t + 1) / c->nthreads);
+    const int64_t kes = (int64_t)nloc * (nloc + 1) / 2;
+    int e2a = lo + off - p, e2b = hi - 1 + off;
+    if (e2a < 0) e2a = 0;
+    if (e2b > n - 1) e2b = n - 1;
+    for (int e2 = e2a; e2 <= e2b; e2++)
+        for (int e1 = 0; e1 < n; e1++) {
+            const int el = e2 * n + e1;
+            const double* ke = c->ke + el * kes;
+            const double* fe = c->fe + (int64_t)el * nloc;
+            for (int a = 0; a < nloc; a++) {
+                const int a1 = a % P1, a2 = (a / P1) % P1, a3 = (d == 3) ? a / (P1 * P1) : 0;
+                const int i1 = e1 + a1 - off, i2 = e2 + a2 - off, i3 = (d == 3) ? e3 + a3 - off : 0;
+                if (i2 < lo || i2 >= hi) continue;
+                if (i1 < 0 || i1 >= m || i2 < 0 || i3 < 0 || i3 >= m) continue;
+                const int64_t I = i1 + (int64_t)m * (i2 + (int64_t)m * i3);
+                if (c->F) c->F[I] += fe[a];
+                for (int b = 0; b < nloc; b++) {
+                    const int b1 = b % P1, b2 = (b / P1) % P1, b3 = (d == 3) ? b / (P1 * P1) : 0;
+                    const int j1 = e1 + b1 - off, j2 = e2 + b2 - off, j3 = (d == 3) ? e3 + b3 - off : 0;
+                    if (j1 < 0 || j1 >= m || j2 < 0 || j2 >= m || j3 < 0 || j3 >= m) continue;
+                    const int64_t Jg = j1 + (int64_t)m * (j2 + (int64_t)m * j3);
+                    if (Jg < I) continue;
+                    const int lo_ab = a <= b ? a : b, hi_ab = a <= b ? b : a;
+                    const double kab = ke[(int64_t)lo_ab * nloc - (int64_t)lo_ab * (lo_ab - 1) / 2 + (hi_ab - lo_ab)];
+                    c->val[c->rowptr[I] + pat_pos(d, m, p, i1, i2, i3, j1, j2, j3)] += kab;
+                }
+            }
+        }
+    return NULL;
+}
+
+/* lower triangle := mirror of the upper one, rows [N t / T, N (t+1) / T) */
+static void* mirror_job(void* arg) {
+    elem_job* j = (elem_job*)arg;
+    elem_ctx* c = j->c;
+    const int d = c->d, m = c->m, p = c->p;
+    const int64_t N = (d == 2) ? (int64_t)m * m : (int64_t)m * m * m;
+    const int64_t I0 = N * j->t / c->nthreads, I1 = N * (j->t + 1) / c->nthreads;
+    for (int64_t I = I0; I < I1; I++) {
+        int i1 = (int)(I % m), i2 = (int)((I / m) % m), i3 = (d == 3) ? (int)(I / ((int64_t)m * m)) : 0;
+        for (int64_t k = c->rowptr[I]; k < c->rowptr[I + 1]; k++) {
+            int64_t Jg = c->col[k];
+            if (Jg >= I) continue;
+            int j1 = (int)(Jg % m), j2 = (int)((Jg / m) % m), j3 = (d == 3) ? (int)(Jg / ((int64_t)m * m)) : 0;
+            c->val[k] = c->val[c->rowptr[Jg] + pat_pos(d, m, p, j1, j2, j3, i1, i2, i3)];
+        }
+    }
+    return NULL;
+}
+
+/* kappa at every quadrature point: [iz][ip2], iz = e3 nq + q3 (one z point
+ * in 2-D), ip2 = (e2 nq + q2) (n nq) + e1 nq + q1. */
+typedef struct {
+    const kappa_field* kf;
+    int d, n, nq, geom, nthreads, t;
+    const double *gx, *zc, *zs;  /* cos / sin of w_m3 z for every z point: [iz][M] */
+    double* out;
+} kappa_job;
+
+static void* kappa_worker(void* arg) {
+    kappa_job* j = (kappa_job*)arg;
+    const kappa_field* kf = j->kf;
+    const int M = kf->M, n = j->n, nq = j->nq, nqn = n * nq, nz = (j->d == 3) ? nqn : 1;
+    const double h = 1.0 / n, amp = kf->sigma * sqrt(2.0 / M);
+    double* ac = (double*)malloc(sizeof(double) * M);
+    double* as = (double*)malloc(sizeof(double) * M);
+    for (int64_t ip2 = j->t; ip2 < (int64_t)nqn * nqn; ip2 += j->nthreads) {
+        const int i1 = (int)(ip2 % nqn), i2 = (int)(ip2 / nqn);
+        const double xi[3] = {((i1 / nq) + 0.5 * (j->gx[i1 % nq] + 1.0)) * h,
+                              ((i2 / nq) + 0.5 * (j->gx[i2 % nq] + 1.0)) * h, 0.0};
+        double x[3] = {0, 0, 0}, J[3][3];
+        geom_eval(j->geom, j->d, xi, x, J);
+        for (int m = 0; m < M; m++) {
+            const double a = kf->phi[m] + kf->omega[3 * m] * x[0] + kf->omega[3 * m + 1] * x[1];
+            ac[m] = cos(a);
+            as[m] = sin(a);
+        }
+        for (int iz = 0; iz < nz; iz++) {
+            const double* zc = j->zc + (int64_t)iz * M;
+            const double* zs = j->zs + (int64_t)iz * M;
+            double g = 0.0;
+            for (int m = 0; m < M; m++) g += ac[m] * zc[m] - as[m] * zs[m];
+            j->out[(int64_t)iz * nqn * nqn + ip2] = exp(amp * g);
+        }
+    }
+    free(ac);
+    free(as);
+    return NULL;
+}
+
+static double* kappa_table(const kappa_field* kf, int d, int n, int nq, int geom, const double* gx, int nthreads) {
+    const int M = kf->M, nqn = n * nq, nz = (d == 3) ? nqn : 1;
+    double* out = (double*)malloc(sizeof(double) * (size_t)nz * nqn * nqn);
+    double* zc = (double*)malloc(sizeof(double) * (size_t)nz * M);
+    double* zs = (double*)malloc(sizeof(double) * (size_t)nz * M);
+    if (!out || !zc || !zs) {
+        free(out); free(zc); free(zs);
+        return NULL;
+    }
+    for (int iz = 0; iz < nz; iz++) {
+        const double z = (d == 3) ? ((iz / nq) + 0.5 * (gx[iz % nq] + 1.0)) / n : 0.0;
+        for (int m = 0; m < M; m++) {
+            const double b = kf->omega[3 * m + 2] * z;
+            zc[(int64_t)iz * M + m] = cos(b);
+            zs[(int64_t)iz * M + m] = sin(b);
+        }
+    }
+    pthread_t th[32];
+    kappa_job jobs[32];
+    for (int t = 0; t < nthreads; t++) {
+        jobs[t] = (kappa_job){kf, d, n, nq, geom, nthreads, t, gx, zc, zs, out};
+        if (t > 0 && pthread_create(&th[t], NULL, kappa_worker, &jobs[t]) != 0) {
+            kappa_worker(&jobs[t]);
+            jobs[t].t = -1;
+        }
+    }
+    kappa_worker(&jobs[0]);
+    for (int t = 1; t < nthreads; t++)
+        if (jobs[t].t >= 0) pthread_join(th[t], NULL);
+    free(zc);
+    free(zs);
+    return out;
+}
+
 int iga_assemble_elem(int d, int n, int p, int nq, int geom, int with_boundary, int kappa_M, double kappa_ell,
                       double kappa_sigma, uint64_t kappa_seed, int fkind, int64_t* rowptr, int32_t* col, double* val,
                       double* F) {
-    const double pi = 3.14159265358979323846264338328;
     if ((d != 2 && d != 3) || p < 1 || p > IGA_MAXP || nq < 1 || nq > IGA_MAXQ) return -1;
     if (geom == 1 && d != 3) return -1;
     const int nb = n + p, off = with_boundary ? 0 : 1, m = with_boundary ? nb : nb - 2;
+    const int P1 = p + 1;
+    const int nloc = (d == 2) ? P1 * P1 : P1 * P1 * P1;
+    if (nloc > 729) return -1;
     build_pattern(d, m, p, rowptr, col);
     const int64_t N = (d == 2) ? (int64_t)m * m : (int64_t)m * m * m;
     memset(val, 0, sizeof(double) * rowptr[N]);
     if (F) memset(F, 0, sizeof(double) * N);
-    kappa_field kf;
-    kappa_init(&kf, kappa_M, kappa_ell, kappa_sigma, kappa_seed);
+
+    elem_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.d = d; c.n = n; c.p = p; c.nq = nq; c.geom = geom; c.off = off; c.m = m; c.P1 = P1; c.nloc = nloc;
+    c.nqe = (d == 2) ? nq * nq : nq * nq * nq;
+    c.fkind = fkind;
+    c.h = 1.0 / n;
+    c.rowptr = rowptr; c.val = val; c.F = F;
+    c.nthreads = num_threads();
 
     double gx[IGA_MAXQ], gw[IGA_MAXQ];
     iga_gauss_legendre(nq, gx, gw);
-    const double h = 1.0 / n;
-    /* 1-D tables: V[e][q][a], D[e][q][a] */
-    const int P1 = p + 1;
+    c.gx = gx; c.gw = gw;
     double* V = (double*)malloc(sizeof(double) * n * nq * P1);
     double* D = (double*)malloc(sizeof(double) * n * nq * P1);
     for (int e = 0; e < n; e++)
         for (int q = 0; q < nq; q++)
-            iga_bspline_local(n, p, e, (e + 0.5 * (gx[q] + 1.0)) * h, V + (e * nq + q) * P1, D + (e * nq + q) * P1);
+            iga_bspline_local(n, p, e, (e + 0.5 * (gx[q] + 1.0)) * c.h, V + (e * nq + q) * P1, D + (e * nq + q) * P1);
+    c.V = V; c.D = D;
 
-    const int nloc = (d == 2) ? P1 * P1 : P1 * P1 * P1;
-    const int nqe = (d == 2) ? nq * nq : nq * nq * nq;
-    double* ke = (double*)malloc(sizeof(double) * nloc * nloc);
-    double* fe = (double*)malloc(sizeof(double) * nloc);
-    double* gradl = (double*)malloc(sizeof(double) * nloc * 3);
-    double* vall = (double*)malloc(sizeof(double) * nloc);
-    const int ne3 = (d == 3) ? n : 1;
-    for (int e3 = 0; e3 < ne3; e3++)
-        for (int e2 = 0; e2 < n; e2++)
-            for (int e1 = 0; e1 < n; e1++) {
-                memset(ke, 0, sizeof(double) * nloc * nloc);
-                memset(fe, 0, sizeof(double) * nloc);
-                for (int qq = 0; qq < nqe; qq++) {
-                    int q1 = qq % nq, q2 = (qq / nq) % nq, q3 = (d == 3) ? qq / (nq * nq) : 0;
-                    double xi[3] = {(e1 + 0.5 * (gx[q1] + 1.0)) * h, (e2 + 0.5 * (gx[q2] + 1.0)) * h,
-                                    (d == 3) ? (e3 + 0.5 * (gx[q3] + 1.0)) * h : 0.0};
-                    double wq = (0.5 * h * gw[q1]) * (0.5 * h * gw[q2]);
-                    if (d == 3) wq *= 0.5 * h * gw[q3];
-                    double x[3] = {0, 0, 0}, J[3][3];
-                    geom_eval(geom, d, xi, x, J);
-                    /* G = |det J| J^-1 J^-T via the adjugate */
-                    double G[3][3], detJ;
-                    if (d == 2) {
-                        detJ = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-                        double inv[2][2] = {{J[1][1] / detJ, -J[0][1] / detJ}, {-J[1][0] / detJ, J[0][0] / detJ}};
-                        for (int a = 0; a < 2; a++)
-                            for (int b = 0; b < 2; b++) G[a][b] = fabs(detJ) * (inv[a][0] * inv[b][0] + inv[a][1] * inv[b][1]);
-                    } else {
-                        double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-                        double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-                        double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-                        detJ = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-                        double inv[3][3];
-                        inv[0][0] = c00 / detJ;
-                        inv[1][0] = c01 / detJ;
-                        inv[2][0] = c02 / detJ;
-                        inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / detJ;
-                        inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / detJ;
-                        inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / detJ;
-                        inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / detJ;
-                        inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / detJ;
-                        inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / detJ;
-                        for (int a = 0; a < 3; a++)
-                            for (int b = 0; b < 3; b++)
-                                G[a][b] = fabs(detJ) * (inv[a][0] * inv[b][0] + inv[a][1] * inv[b][1] + inv[a][2] * inv[b][2]);
-                    }
-                    double kap = kappa_eval(&kf, d, x);
-                    double fval = 1.0;
-                    if (fkind == 1) {
-                        fval = d * pi * pi;
-                        for (int c = 0; c < d; c++) fval *= sin(pi * x[c]);
-                    }
-                    const double* v1 = V + (e1 * nq + q1) * P1;
-                    const double* d1 = D + (e1 * nq + q1) * P1;
-                    const double* v2 = V + (e2 * nq + q2) * P1;
-                    const double* d2 = D + (e2 * nq + q2) * P1;
-                    const double* v3 = V + (e3 * nq + q3) * P1;
-                    const double* d3 = D + (e3 * nq + q3) * P1;
-                    for (int l = 0; l < nloc; l++) {
-                        int a1 = l % P1, a2 = (l / P1) % P1, a3 = (d == 3) ? l / (P1 * P1) : 0;
-                        if (d == 2) {
-                            gradl[3 * l + 0] = d1[a1] * v2[a2];
-                            gradl[3 * l + 1] = v1[a1] * d2[a2];
-                            gradl[3 * l + 2] = 0.0;
-                            vall[l] = v1[a1] * v2[a2];
-                        } else {
-                            gradl[3 * l + 0] = d1[a1] * v2[a2] * v3[a3];
-                            gradl[3 * l + 1] = v1[a1] * d2[a2] * v3[a3];
-                            gradl[3 * l + 2] = v1[a1] * v2[a2] * d3[a3];
-                            vall[l] = v1[a1] * v2[a2] * v3[a3];
-                        }
-                    }
-                    const double s = kap * wq;
-                    for (int a = 0; a < nloc; a++) {
-                        double Ga[3] = {0, 0, 0};
-                        for (int r = 0; r < d; r++)
-                            for (int c = 0; c < d; c++) Ga[r] += G[r][c] * gradl[3 * a + c];
-                        for (int b = a; b < nloc; b++) {
-                            double t = 0.0;
-                            for (int r = 0; r < d; r++) t += gradl[3 * b + r] * Ga[r];
-                            ke[a * nloc + b] += t * s;
-                        }
-                        fe[a] += fval * vall[a] * fabs(detJ) * wq;
-                    }
-                }
-                /* scatter: upper triangle in global numbering */
-                for (int a = 0; a < nloc; a++) {
-                    int a1 = a % P1, a2 = (a / P1) % P1, a3 = (d == 3) ? a / (P1 * P1) : 0;
-                    int i1 = e1 + a1 - off, i2 = e2 + a2 - off, i3 = (d == 3) ? e3 + a3 - off : 0;
-                    if (i1 < 0 || i1 >= m || i2 < 0 || i2 >= m || i3 < 0 || i3 >= m) continue;
-                    int64_t I = i1 + (int64_t)m * (i2 + (int64_t)m * i3);
-                    if (F) F[I] += fe[a];
-                    for (int b = 0; b < nloc; b++) {
-                        int b1 = b % P1, b2 = (b / P1) % P1, b3 = (d == 3) ? b / (P1 * P1) : 0;
-                        int j1 = e1 + b1 - off, j2 = e2 + b2 - off, j3 = (d == 3) ? e3 + b3 - off : 0;
-                        if (j1 < 0 || j1 >= m || j2 < 0 || j2 >= m || j3 < 0 || j3 >= m) continue;
-                        int64_t Jg = j1 + (int64_t)m * (j2 + (int64_t)m * j3);
-                        if (Jg < I) continue;
-                        double kab = (a <= b) ? ke[a * nloc + b] : ke[b * nloc + a];
-                        val[rowptr[I] + pat_pos(d, m, p, i1, i2, i3, j1, j2, j3)] += kab;
-                    }
-                }
-            }
-    /* mirror the upper triangle */
-    for (int64_t I = 0; I < N; I++) {
-        int i1 = (int)(I % m), i2 = (int)((I / m) % m), i3 = (d == 3) ? (int)(I / ((int64_t)m * m)) : 0;
-        for (int64_t k = rowptr[I]; k < rowptr[I + 1]; k++) {
-            int64_t Jg = col[k];
-            if (Jg >= I) continue;
-            int j1 = (int)(Jg % m), j2 = (int)((Jg / m) % m), j3 = (d == 3) ? (int)(Jg / ((int64_t)m * m)) : 0;
-            val[k] = val[rowptr[Jg] + pat_pos(d, m, p, j1, j2, j3, i1, i2, i3)];
-        }
+    kappa_field kf;
+    kappa_init(&kf, kappa_M, kappa_ell, kappa_sigma, kappa_seed);
+    double* kap = NULL;
+    if (kf.M > 0) {
+        kap = kappa_table(&kf, d, n, nq, geom, gx, c.nthreads);
+        if (!kap) { free(V); free(D); kappa_free(&kf); return -2; }
     }
-    free(V); free(D); free(ke); free(fe); free(gradl); free(vall);
+    c.kap = kap;
+
+    const int nel = n * n; /* elements of a plane (of the whole square in 2-D) */
+    const int64_t kes = (int64_t)nloc * (nloc + 1) / 2;
+    c.ke = (double*)malloc(sizeof(double) * (size_t)nel * kes);
+    c.fe = (double*)malloc(sizeof(double) * (size_t)nel * nloc);
+    if (!c.ke || !c.fe) {
+        free(c.ke); free(c.fe); free(V); free(D); free(kap); kappa_free(&kf);
+        return -2;
+    }
+    const int ne3 = (d == 3) ? n : 1;
+    for (int e3 = 0; e3 < ne3; e3++) {
+        c.e3 = e3;
+        run_parallel(compute_job, &c);
+        run_parallel(scatter_job, &c);
+    }
+    /* mirror the upper triangle (rows in parallel; reads only upper entries) */
+    c.col = col;
+    run_parallel(mirror_job, &c);
+    free(c.ke); free(c.fe); free(V); free(D); free(kap);
     kappa_free(&kf);
     return 0;
 }

@@ -183,3 +183,37 @@ def test_fullsize_learned_damping_mixed_precision(cube64):
           f"[{om.min():.3f}, {om.max():.3f}]")
     assert rr <= 1e-8 * 1.0001 and err <= 1e-7
     assert g["iters"] < plain["iters"]
+
+
+def test_fullsize_annulus_learned_mixed_precision():
+    """The learned-damping workload: quarter annulus (NURBS geometry) p=3
+    n=64 with a random log-normal coefficient.  Network trained on annulus
+    hierarchies p in {2,3,4}, n in {16,32}; the mixed-precision learned
+    solve meets rtol 1e-8 on the FP64 true residual, stays within 1e-7 of
+    the FP64 solution and needs fewer iterations than plain FP64 AMG."""
+    prob = I.annulus_kappa(64, 3)
+    args = (dev(prob.rowptr), dev(prob.col), dev(prob.val))
+    F = dev(prob.F)
+    train = []
+    for n in (16, 32):
+        for pp in (2, 3, 4):
+            q = I.annulus_kappa(n, pp)
+            train.append(A.Hierarchy(dev(q.rowptr), dev(q.col), dev(q.val)))
+    w = dev(I.mpnn_init_weights(1).astype(np.float32))
+    hist = train[0].mpnn_train(w, steps=60, nprobe=4, seed=2000, lr=1e-2, others=train[1:])
+    ref = A.Hierarchy(*args).solve(F, rtol=1e-8)
+    assert ref["status"] == 0
+    u64 = ref["u"].cpu().numpy()
+    H = A.Hierarchy(*args, precision=A.AMG_FP32_BF16FINE)
+    H.mpnn_apply(w, bf16_weights=True)
+    g = H.solve(F, rtol=1e-8)
+    assert g["status"] == 0
+    u = g["u"].cpu().numpy()
+    rr = true_relres((prob.rowptr, prob.col, prob.val), prob.F, u)
+    err = np.linalg.norm(u - u64) / np.linalg.norm(u64)
+    om = H.mpnn_omega(0).cpu().numpy()
+    print(f"annulus p=3 n=64: FP64 plain {ref['iters']} iterations, mixed + learned {g['iters']}; true relres "
+          f"{rr:.2e}, error vs FP64 {err:.2e}; loss {hist[0]:.3f} -> {hist[-1]:.3f}; omega [{om.min():.3f}, "
+          f"{om.max():.3f}]")
+    assert rr <= 1e-8 * 1.0001 and err <= 1e-7
+    assert g["iters"] < ref["iters"]

@@ -38,7 +38,11 @@ if ROOT not in sys.path:
 METRIC = "time-to-solution at rtol 1e-8 and V-cycle HBM GB/s: mixed/learned vs FP64 AMG"
 WORKLOAD = "3-D Poisson unit cube, B-spline p=3 C^2, n=64 (N=274,625, nnz=86,938,307), FP64 AMG-PCG, rtol 1e-8"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fine_matrix_pass_fp64_3d_p3_n64.md")
+STREAM_SUMMARY = os.path.join(ROOT, "profiles", "staged_mixed_passes_3d_p3_n64.md")
 KERNEL_NAMES = ["k_spmv_pq<8> (q = K p)", "k_resid<8> (down-sweep residual)", "k_up0<8> (up-sweep smoothing)"]
+# staged mixed-precision passes (k_stream, run-encoded finest matrix; default matrix_format 2)
+MIXED_KERNEL_NAMES = ["k_stream<EpiPQ, f32> (q = K p)", "k_stream<EpiResid, bf16> (down-sweep residual)",
+                      "k_stream<EpiUp0, bf16> (up-sweep smoothing)"]
 
 
 def parse():
@@ -635,10 +639,12 @@ def run_ours(args):
             m_ms = max_over_ranks(dist, m0.elapsed_time(m1)) / args.steps
             err = float(torch.linalg.norm(mu - ref_u) / torch.linalg.norm(ref_u))
             mavg = mms / np.maximum(mcnt, 1)
+            mnames = MIXED_KERNEL_NAMES if args.matrix_format == 2 else [
+                "k_spmv_pq<8,f32> (q = K p)", "k_resid<8,bf16> (down-sweep residual)",
+                "k_up0<8,bf16> (up-sweep smoothing)"]
             mk = {name: {"bytes_per_launch": mkt[2][q], "avg_ms": mavg[q], "launches": int(mcnt[q]),
                          "achieved_gbs": mkt[2][q] / (mavg[q] * 1e-3) / 1e9 if mavg[q] > 0 else None}
-                  for q, name in enumerate(["k_spmv_pq<8,f32> (q = K p)", "k_resid<8,bf16> (down-sweep residual)",
-                                            "k_up0<8,bf16> (up-sweep smoothing)"])}
+                  for q, name in enumerate(mnames)}
             mdom = max(mk, key=lambda k: mk[k]["avg_ms"] * mk[k]["launches"])
             mixed = {"time_to_solution_s": m_ms / 1e3, "speedup_vs_fp64": ms_per_step / m_ms, "iters": mit,
                      "final_relres_fp64": mrr, "rel_error_vs_fp64_solution": err, "setup_ms": minfo.setup_ms,
@@ -646,7 +652,10 @@ def run_ours(args):
                      "fp64 FCG(1) recurrences, fp64 true-residual replacement every 20 iterations",
                      "iter_gbps": minfo.iter_bytes * mit / (minfo.solve_ms * 1e-3) / 1e9,
                      "roofline": {"bound": "hbm", "kernel": mdom, "achieved": mk[mdom]["achieved_gbs"],
-                                  "unit": "GB/s", "all": mk}}
+                                  "unit": "GB/s", "traffic": None,
+                                  "tkey": ["pq", "resid", "up0"][mnames.index(mdom)],
+                                  "bytes_per_launch": mk[mdom]["bytes_per_launch"],
+                                  "avg_launch_ms": mk[mdom]["avg_ms"], "all": mk}}
 
         # learned damping on top of mixed precision: the network is trained
         # (untimed) on small hierarchies of the same family, then each timed
@@ -705,6 +714,9 @@ def run_ours(args):
     if mixed is not None:
         mixed["roofline"]["peak"] = peak
         mixed["roofline"]["frac"] = (mixed["roofline"]["achieved"] or 0.0) / peak
+        st = committed_traffic(STREAM_SUMMARY, ("stream_kernels.cu",))
+        if st and "k_stream" in mixed["roofline"]["kernel"]:
+            mixed["roofline"]["traffic"] = st.get(mixed["roofline"]["tkey"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, it, args.rtol)
     if rank == 0:

@@ -79,10 +79,13 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  : "memory");
 }
 
-// Bounded wait for phase `parity` of the mbarrier (one thread).
+// Bounded wait for phase `parity` of the mbarrier (one thread); backs off
+// between polls so that waiting warps leave the issue slots to the others.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (int it = 0; it < kWaitIters; it++) {
+        __nanosleep(32);
         if (mbar_try_wait(bar, parity)) return true;
         if (clock64() - t0 > kWaitCycles) break;
     }

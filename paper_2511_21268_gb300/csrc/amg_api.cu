@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "amg_internal.cuh"
@@ -43,6 +44,65 @@ constexpr size_t kPad = 8;
 
 thread_local char g_cuda_err[512] = "";
 
+// Process-wide pool of the small per-hierarchy resources whose creation is
+// slow (page-locked host blocks, CUDA events), so that building and freeing
+// hierarchies in a loop does not pay for them every time.  Keyed by device.
+struct ResourcePool {
+    std::mutex mu;
+    std::vector<std::pair<int, void*>> pinned;              // (device, 512-byte block)
+    std::vector<std::pair<int, cudaEvent_t>> timed, plain;  // (device, event)
+};
+ResourcePool& pool() {
+    static ResourcePool* p = new ResourcePool();  // never destroyed: outlives static destructors
+    return *p;
+}
+constexpr size_t kPinnedBlock = 512;
+
+cudaError_t pinned_get(void** out) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> g(pool().mu);
+        auto& v = pool().pinned;
+        for (size_t i = 0; i < v.size(); i++)
+            if (v[i].first == dev) {
+                *out = v[i].second;
+                v.erase(v.begin() + i);
+                return cudaSuccess;
+            }
+    }
+    return cudaMallocHost(out, kPinnedBlock);
+}
+void pinned_put(void* p) {
+    if (!p) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(pool().mu);
+    pool().pinned.emplace_back(dev, p);
+}
+cudaError_t event_get(cudaEvent_t* e, bool timing) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> g(pool().mu);
+        auto& v = timing ? pool().timed : pool().plain;
+        for (size_t i = v.size(); i-- > 0;)
+            if (v[i].first == dev) {
+                *e = v[i].second;
+                v.erase(v.begin() + i);
+                return cudaSuccess;
+            }
+    }
+    return timing ? cudaEventCreate(e) : cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+}
+void event_put(cudaEvent_t e, bool timing) {
+    if (!e) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(pool().mu);
+    (timing ? pool().timed : pool().plain).emplace_back(dev, e);
+}
+
 int cuda_fail(cudaError_t e, const char* what) {
     snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? AMG_ERR_NOMEM : AMG_ERR_CUDA;
@@ -60,13 +120,13 @@ int cuda_fail(cudaError_t e, const char* what) {
         if (r__ != AMG_OK) return r__; \
     } while (0)
 
-constexpr int kRoundBatch = 4;
+constexpr int kRoundBatch = 16;  // matching rounds between host reads (later rounds are no-ops)
 constexpr int kMaxSystems = 1024;  // systems of one batch (one scalar thread each)
 
 // Mark the start of setup phase `id` (see amg_info.setup_phase_ms).
 void phase(amg_hierarchy* h, int id) {
     if (h->ph_n >= 512) return;
-    if (!h->ph_ev[h->ph_n] && cudaEventCreate(&h->ph_ev[h->ph_n]) != cudaSuccess) return;
+    if (!h->ph_ev[h->ph_n] && event_get(&h->ph_ev[h->ph_n], true) != cudaSuccess) return;
     cudaEventRecord(h->ph_ev[h->ph_n], h->s);
     h->ph_id[h->ph_n++] = id;
 }
@@ -163,6 +223,8 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
         const int cnt = std::min(kRoundBatch, maxr - rounds);
         CK(launch_match_rounds(A, key, state, cand, h->round_active, rounds, cnt, s));
         CK(cudaMemcpyAsync(h->flag_host, h->round_active + rounds, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
+        // the edge-key kernel's unsymmetric-pattern flag rides on the same read
+        CK(cudaMemcpyAsync(h->flag_host + 32, h->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         for (int r = 0; r < cnt; r++) {
             if (h->flag_host[r] == 0) {
@@ -174,9 +236,7 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
         if (!done) rounds += cnt;
     }
     P.rounds = rounds;
-    int unsym = 0;
-    RC(read_scalar(h, h->flag + 1, &unsym));
-    if (unsym) return AMG_ERR_ARG;  // structurally unsymmetric matrix
+    if (h->flag_host[32]) return AMG_ERR_ARG;  // structurally unsymmetric matrix
     phase(h, 4);
     P.n = n;
     RC(dalloc(h, &P.mate, n));
@@ -196,17 +256,16 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
     CK(launch_aggregate(n, P.mate, cidx, w, P.agg, P.pval, mem0, mem1, *wc, s));
     // Galerkin product of this pass
     phase(h, 5);
-    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    // widest candidate list and coarse-column span of the coarse rows (one read)
+    CK(cudaMemsetAsync(h->flag, 0, 3 * sizeof(int), s));
     CK(launch_row_stats(A, mem0, mem1, nc, h->flag, s));
-    int maxcand = 0;
-    RC(read_flag(h, &maxcand));
+    CK(launch_row_span(A, P.agg, mem0, mem1, nc, h->flag + 2, s));
+    CK(cudaMemcpyAsync(h->flag_host, h->flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int maxcand = h->flag_host[0], maxspan = h->flag_host[2];
     const int cap = pow2ceil(std::max(maxcand, 1));
     // bitmap kernels when the widest coarse-column span fits shared memory,
     // else the candidate-sorting kernels
-    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
-    CK(launch_row_span(A, P.agg, mem0, mem1, nc, h->flag, s));
-    int maxspan = 0;
-    RC(read_flag(h, &maxspan));
     const int words = (maxspan + 31) / 32 + 1;
     const bool bitmap = 8.0 * words + 16.0 * maxcand <= kBitmapSmem;
     if (!bitmap && cap > kMaxGalerkinCap) return AMG_ERR_ROW_TOO_LONG;
@@ -216,8 +275,8 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
     Tmp trc(s), ts64(s);
     RC(trc.get(&rowcnt, nc));
     RC(ts64.get(&scr64, scan64_scratch(nc) + 1));
-    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
-    if (bitmap) CK(launch_galerkin_count_bitmap(A, P.agg, mem0, mem1, nc, maxcand, words, rowcnt, h->flag, s));
+    // Galerkin errors accumulate in flag[3], read once after the last level
+    if (bitmap) CK(launch_galerkin_count_bitmap(A, P.agg, mem0, mem1, nc, maxcand, words, rowcnt, h->flag + 3, s));
     else CK(launch_galerkin_count(A, P.agg, mem0, mem1, nc, cap, rowcnt, s));
     CK(launch_scan64(rowcnt, C.rowptr, nc, scr64, s));
     int64_t nnzc = 0;
@@ -225,12 +284,9 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
     C.nnz = nnzc;
     RC(dalloc(h, &C.col, (size_t)nnzc + kPad));
     RC(dalloc(h, &C.val, (size_t)nnzc + kPad));
-    if (bitmap) CK(launch_galerkin_fill_bitmap(A, P.agg, P.pval, mem0, mem1, maxcand, words, C, h->flag, s));
+    if (bitmap) CK(launch_galerkin_fill_bitmap(A, P.agg, P.pval, mem0, mem1, maxcand, words, C, h->flag + 3, s));
     else CK(launch_galerkin_fill(A, P.agg, P.pval, mem0, mem1, cap, C, s));
-    CK(launch_galerkin_mirror(C, h->flag, s));
-    int bad = 0;
-    RC(read_flag(h, &bad));
-    if (bad) return AMG_ERR_ARG;  // structurally unsymmetric input
+    CK(launch_galerkin_mirror(C, h->flag + 3, s));
     phase(h, 1);
     return AMG_OK;
 }
@@ -316,10 +372,14 @@ int build(amg_hierarchy* h, const amg_csr* K) {
         RC(dalloc(h, &F.kii, n));
         RC(dalloc(h, &F.dl1, n));
         RC(dalloc(h, &F.invd, n));
-        CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
-        CK(launch_l1diag(F.A, F.kii, F.dl1, F.invd, h->flag, s));
-        RC(read_flag(h, &bad));
-        if (bad) return AMG_ERR_NOT_SPD;
+        if (l == 0) {
+            CK(cudaMemsetAsync(h->flag, 0, 16 * sizeof(int), s));  // also clears the deferred error words
+            CK(launch_l1diag(F.A, F.kii, F.dl1, F.invd, h->flag, s));
+            RC(read_flag(h, &bad));
+            if (bad) return AMG_ERR_NOT_SPD;
+        } else {  // coarse levels: checked once after the loop (flag[4])
+            CK(launch_l1diag(F.A, F.kii, F.dl1, F.invd, h->flag + 4, s));
+        }
         h->nlev = l + 1;
         if (n <= h->o.coarse_max || l + 1 >= h->o.max_levels) break;
         if (l == 0) {
@@ -385,6 +445,11 @@ int build(amg_hierarchy* h, const amg_csr* K) {
         C.A = cur;
         C.w = cw;
     }
+    // deferred checks of the coarse levels: Galerkin structure, positive diagonals
+    CK(cudaMemcpyAsync(h->flag_host, h->flag, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h->flag_host[3]) return AMG_ERR_ARG;  // structurally unsymmetric input
+    if (h->flag_host[4]) return AMG_ERR_NOT_SPD;
     // coarsest level: dense inverse
     phase(h, 7);
     Level& Lc = h->lev[h->nlev - 1];
@@ -532,17 +597,14 @@ void destroy(amg_hierarchy* h) {
     for (void* p : h->allocs) cudaFreeAsync(p, h->s);
     h->allocs.clear();
     if (h->s) cudaStreamSynchronize(h->s);
-    if (h->flag_host) cudaFreeHost(h->flag_host);
-    if (h->st_host) cudaFreeHost(h->st_host);
-    if (h->ev0) cudaEventDestroy(h->ev0);
-    if (h->ev1) cudaEventDestroy(h->ev1);
-    if (h->evs) cudaEventDestroy(h->evs);
+    pinned_put(h->flag_host);  // st_host lives in the same block
+    event_put(h->ev0, true);
+    event_put(h->ev1, true);
+    event_put(h->evs, false);
     for (auto& a : h->prof_ev)
         for (auto& b : a)
-            for (auto& e : b)
-                if (e) cudaEventDestroy(e);
-    for (auto& e : h->ph_ev)
-        if (e) cudaEventDestroy(e);
+            for (auto& e : b) event_put(e, true);
+    for (auto& e : h->ph_ev) event_put(e, true);
     if (h->s && h->own_stream) cudaStreamDestroy(h->s);
     delete h;
 }
@@ -636,11 +698,16 @@ static int create_hierarchy(const amg_opts* opts, void* cuda_stream, amg_hierarc
         e = cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking);
         h->own_stream = true;
     }
-    if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
-    if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->evs, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMallocHost(&h->flag_host, 64);
-    if (e == cudaSuccess) e = cudaMallocHost(&h->st_host, sizeof(SolveState));
+    if (e == cudaSuccess) e = event_get(&h->ev0, true);
+    if (e == cudaSuccess) e = event_get(&h->ev1, true);
+    if (e == cudaSuccess) e = event_get(&h->evs, false);
+    void* pin = nullptr;  // flag words (256 B) and the solve-state mirror in one pooled block
+    if (e == cudaSuccess) e = pinned_get(&pin);
+    if (e == cudaSuccess) {
+        static_assert(256 + sizeof(SolveState) <= kPinnedBlock, "pinned block layout");
+        h->flag_host = static_cast<int*>(pin);
+        h->st_host = reinterpret_cast<SolveState*>(static_cast<char*>(pin) + 256);
+    }
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1126,7 +1193,8 @@ int amg_profile_kernels(amg_hierarchy* h, int32_t enable) {
     if (enable && !h->prof_ev[0][0][0]) {
         for (auto& a : h->prof_ev)
             for (auto& b : a)
-                for (auto& e : b) CK(cudaEventCreate(&e));
+                for (auto& e : b)
+                    if (!e) CK(event_get(&e, true));
     }
     if (h->prof != enable && h->graph) {  // the iteration graph changes shape
         CK(cudaStreamSynchronize(h->s));

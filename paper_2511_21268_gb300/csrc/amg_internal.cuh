@@ -210,8 +210,9 @@ cudaError_t launch_edge_keys(const DevCSR& A, const double* kii, const double* w
                              cudaStream_t s);
 cudaError_t launch_match_init(int n, int32_t* state, cudaStream_t s);
 cudaError_t launch_match_propose(const DevCSR& A, const uint64_t* key, const int32_t* state, int32_t* cand,
-                                 cudaStream_t s);
-cudaError_t launch_match_commit(int n, const int32_t* cand, int32_t* state, int* active, cudaStream_t s);
+                                 const int* prev_active, cudaStream_t s);
+cudaError_t launch_match_commit(int n, const int32_t* cand, int32_t* state, int* active, const int* prev_active,
+                                cudaStream_t s);
 cudaError_t launch_match_rounds(const DevCSR& A, const uint64_t* key, int32_t* state, int32_t* cand, int* active,
                                 int first_round, int count, cudaStream_t s);
 cudaError_t launch_match_finish(int n, const int32_t* state, int32_t* mate, int32_t* leader, cudaStream_t s);

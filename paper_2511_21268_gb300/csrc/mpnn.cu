@@ -161,14 +161,22 @@ __global__ void __launch_bounds__(kBlock) k_nn_spmm(int n, const int64_t* __rest
                 a = ap[kb + lane];
                 j = ci[kb + lane];
             }
+            // 8 rows of h in flight per lane
             int t = 0;
-            for (; t + 1 < cnt; t += 2) {
-                const float a0 = __shfl_sync(FULL, a, t), a1 = __shfl_sync(FULL, a, t + 1);
-                const int j0 = __shfl_sync(FULL, j, t), j1 = __shfl_sync(FULL, j, t + 1);
-                acc0 = fmaf(a0, h[(int64_t)j0 * H + lane], acc0);
-                acc1 = fmaf(a1, h[(int64_t)j1 * H + lane], acc1);
+            for (; t + 7 < cnt; t += 8) {
+                float hv[8], av[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    av[u] = __shfl_sync(FULL, a, t + u);
+                    hv[u] = h[(int64_t)__shfl_sync(FULL, j, t + u) * H + lane];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; u += 2) {
+                    acc0 = fmaf(av[u], hv[u], acc0);
+                    acc1 = fmaf(av[u + 1], hv[u + 1], acc1);
+                }
             }
-            if (t < cnt) {
+            for (; t < cnt; t++) {
                 const float a0 = __shfl_sync(FULL, a, t);
                 const int j0 = __shfl_sync(FULL, j, t);
                 acc0 = fmaf(a0, h[(int64_t)j0 * H + lane], acc0);

@@ -223,7 +223,8 @@ __device__ __forceinline__ bool heavier(uint64_t ka, int loa, int hia, uint64_t 
 // Every active vertex proposes to its heaviest eligible active neighbour.
 __global__ void k_match_propose(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                 const uint64_t* __restrict__ key, const int32_t* __restrict__ state,
-                                int32_t* cand) {
+                                int32_t* cand, const int* prev_active) {
+    if (prev_active && *prev_active == 0) return;  // the matching already ended: a no-op round
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -262,7 +263,9 @@ __global__ void k_match_propose(int n, const int64_t* __restrict__ rp, const int
 }
 
 // Mutual proposals become pairs; vertices without a candidate die.
-__global__ void k_match_commit(int n, const int32_t* __restrict__ cand, int32_t* state, int* active) {
+__global__ void k_match_commit(int n, const int32_t* __restrict__ cand, int32_t* state, int* active,
+                               const int* prev_active) {
+    if (prev_active && *prev_active == 0) return;
     int left = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (state[i] != -1) continue;
@@ -1051,13 +1054,15 @@ cudaError_t launch_match_init(int n, int32_t* state, cudaStream_t s) {
 }
 
 cudaError_t launch_match_propose(const DevCSR& A, const uint64_t* key, const int32_t* state, int32_t* cand,
-                                 cudaStream_t s) {
-    k_match_propose<<<AMG_GRID(blocks_for(A.n, kWarpsPerBlock, 8192)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, key, state, cand);
+                                 const int* prev_active, cudaStream_t s) {
+    k_match_propose<<<AMG_GRID(blocks_for(A.n, kWarpsPerBlock, 8192)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, key, state, cand,
+                                                                                        prev_active);
     return cudaGetLastError();
 }
 
-cudaError_t launch_match_commit(int n, const int32_t* cand, int32_t* state, int* active, cudaStream_t s) {
-    k_match_commit<<<AMG_GRID(blocks_for(n, kBlock, 4096)), kBlock, 0, s>>>(n, cand, state, active);
+cudaError_t launch_match_commit(int n, const int32_t* cand, int32_t* state, int* active, const int* prev_active,
+                                cudaStream_t s) {
+    k_match_commit<<<AMG_GRID(blocks_for(n, kBlock, 4096)), kBlock, 0, s>>>(n, cand, state, active, prev_active);
     return cudaGetLastError();
 }
 
@@ -1066,8 +1071,10 @@ cudaError_t launch_match_commit(int n, const int32_t* cand, int32_t* state, int*
 cudaError_t launch_match_rounds(const DevCSR& A, const uint64_t* key, int32_t* state, int32_t* cand, int* active,
                                 int first_round, int count, cudaStream_t s) {
     for (int r = 0; r < count; r++) {
-        AMG_TRY(launch_match_propose(A, key, state, cand, s));
-        AMG_TRY(launch_match_commit(A.n, cand, state, active + first_round + r, s));
+        const int round = first_round + r;
+        const int* prev = round > 0 ? active + round - 1 : nullptr;
+        AMG_TRY(launch_match_propose(A, key, state, cand, prev, s));
+        AMG_TRY(launch_match_commit(A.n, cand, state, active + round, prev, s));
     }
     return cudaSuccess;
 }

@@ -205,19 +205,60 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // Lane partial of one row whose R runs have LL entries each, values
 // run-interleaved (entry o of run r at rv[o R + r]); lane t takes the runs
 // t, t + 32, ...  Two accumulators halve the FMA dependency chain.
+// Shared-memory loads with 32-bit shared addresses (the window entry at a
+// compile-time offset from the run's first column).
+__device__ __forceinline__ float lds_val(uint32_t a, const float*) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float lds_val(uint32_t a, const __nv_bfloat16*) {
+    unsigned short u;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(u) : "r"(a));
+    return __uint_as_float((uint32_t)u << 16);
+}
+__device__ __forceinline__ int lds_s32(uint32_t a) {
+    int v;
+    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ float lds_x(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF));
+    return v;
+}
+
+// Entries O .. LL-1 of one run: value at va + o vstride, vector entry at
+// xa + 4 o; two accumulators halve the FMA dependency chain.
+template <int O, int LL, typename V>
+struct RunDot {
+    static __device__ __forceinline__ void run(uint32_t va, uint32_t vstride, uint32_t xa, float& a0, float& a1) {
+        const float v = lds_val(va, static_cast<const V*>(nullptr));
+        const float x = lds_x<4 * O>(xa);
+        if (O & 1) a1 = fmaf(v, x, a1);
+        else a0 = fmaf(v, x, a0);
+        RunDot<O + 1, LL, V>::run(va + vstride, vstride, xa, a0, a1);
+    }
+};
 template <int LL, typename V>
-__device__ __forceinline__ float row_runs(const V* rv, const int32_t* rr, const float* xs, int R, int lane) {
+struct RunDot<LL, LL, V> {
+    static __device__ __forceinline__ void run(uint32_t, uint32_t, uint32_t, float&, float&) {}
+};
+
+// Lane partial of one row whose R runs have LL entries each, values
+// run-interleaved (entry o of run r at value index o R + r from the row's
+// first value, shared address va0); run starts at shared address ra; the
+// window entry of column c at xbase + 4 c (32-bit wrap-around arithmetic).
+// Lane t takes the runs t, t + 32, ...
+template <int LL, typename V>
+__device__ __forceinline__ float row_runs(uint32_t va0, uint32_t ra, uint32_t xbase, int R, int lane) {
+    constexpr uint32_t es = sizeof(V);
     float a0 = 0.f, a1 = 0.f;
+    const uint32_t vstride = (uint32_t)R * es;
     for (int r = lane; r < R; r += 32) {
-        const float* xr = xs + rr[r];
-        const V* vr = rv + r;
-#pragma unroll
-        for (int o = 0; o < LL; o++) {
-            const float v = ldsv(vr, 0);
-            if (o & 1) a1 = fmaf(v, xr[o], a1);
-            else a0 = fmaf(v, xr[o], a0);
-            vr += R;
-        }
+        const uint32_t xa = xbase + 4u * (uint32_t)lds_s32(ra + 4u * (uint32_t)r);
+        RunDot<0, LL, V>::run(va0 + es * (uint32_t)r, vstride, xa, a0, a1);
     }
     return a0 + a1;
 }
@@ -352,6 +393,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
             ok = __shfl_sync(FULL, ok, 0);
         }
         const float* xs = xw - *xlo;  // xs[c] = vector entry c (inside the window)
+        // shared address of vector entry 0 (32-bit wrap-around: entry c at xbase + 4 c)
+        const uint32_t xbase = smem_addr(xw) - 4u * (uint32_t)(*xlo);
         for (int k = s0; k < s1 && ok; k++) {
             const int u = (k - s0) / nbuf, j = (k - s0) % nbuf;
             if (lane == 0) ok = !*ctrl && mbar_wait_bounded(bar_full(j), (uint32_t)u & 1u);
@@ -376,18 +419,19 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                     // (entry o of run r at o R + r), so lane r reads run r
                     const int64_t b = srp[tl];
                     const int L = srlen[tl];
-                    const int R = srptr[tl + 1] - srptr[tl];
-                    const V* rv = sv + (b - vb);
-                    const int32_t* rr = sr + (srptr[tl] - rbs);
+                    const int r0 = srptr[tl];
+                    const int R = srptr[tl + 1] - r0;
+                    const uint32_t va0 = smem_addr(sv) + (uint32_t)(b - vb) * (uint32_t)sizeof(V);
+                    const uint32_t ra = smem_addr(sr) + 4u * (uint32_t)(r0 - rbs);
                     switch (L) {  // warp-uniform: the run length of the row
-                        case 2: acc = row_runs<2>(rv, rr, xs, R, lane); break;
-                        case 3: acc = row_runs<3>(rv, rr, xs, R, lane); break;
-                        case 4: acc = row_runs<4>(rv, rr, xs, R, lane); break;
-                        case 5: acc = row_runs<5>(rv, rr, xs, R, lane); break;
-                        case 6: acc = row_runs<6>(rv, rr, xs, R, lane); break;
-                        case 7: acc = row_runs<7>(rv, rr, xs, R, lane); break;
-                        case 8: acc = row_runs<8>(rv, rr, xs, R, lane); break;
-                        default: acc = row_runs<9>(rv, rr, xs, R, lane); break;
+                        case 2: acc = row_runs<2, V>(va0, ra, xbase, R, lane); break;
+                        case 3: acc = row_runs<3, V>(va0, ra, xbase, R, lane); break;
+                        case 4: acc = row_runs<4, V>(va0, ra, xbase, R, lane); break;
+                        case 5: acc = row_runs<5, V>(va0, ra, xbase, R, lane); break;
+                        case 6: acc = row_runs<6, V>(va0, ra, xbase, R, lane); break;
+                        case 7: acc = row_runs<7, V>(va0, ra, xbase, R, lane); break;
+                        case 8: acc = row_runs<8, V>(va0, ra, xbase, R, lane); break;
+                        default: acc = row_runs<9, V>(va0, ra, xbase, R, lane); break;
                     }
                 }
                 tiles[wid][t][lane] = acc;

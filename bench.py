@@ -418,12 +418,13 @@ def annulus_leg(args, A, I, torch, np, stream, dist):
     prob = I.annulus_kappa(64, 3)
     asm_s = time.perf_counter() - t0
     rp, ci, va, F = (torch.from_numpy(a).to(dev) for a in (prob.rowptr, prob.col, prob.val, prob.F))
-    train = []
+    train = []  # p in {2,3,4} x n in {16,32} x 4 coefficient fields (seeds 101-104; the workload uses 7)
     for n in (16, 32):
         for pp in (2, 3, 4):
-            q = I.annulus_kappa(n, pp)
-            train.append(A.amg_setup(torch.from_numpy(q.rowptr).to(dev), torch.from_numpy(q.col).to(dev),
-                                     torch.from_numpy(q.val).to(dev), A.amg_opts_default(), stream))
+            for ks in (101, 102, 103, 104):
+                q = I.annulus_kappa(n, pp, kappa_seed=ks)
+                train.append(A.amg_setup(torch.from_numpy(q.rowptr).to(dev), torch.from_numpy(q.col).to(dev),
+                                         torch.from_numpy(q.val).to(dev), A.amg_opts_default(), stream))
     w = torch.from_numpy(I.mpnn_init_weights(1).astype(np.float32)).to(dev)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -471,7 +472,8 @@ def annulus_leg(args, A, I, torch, np, stream, dist):
             "mixed_learned_time_to_solution_s": tml / 1e3, "mixed_learned_iters": itml,
             "speedup_vs_fp64": t64 / tml, "rel_error_vs_fp64_solution": err, "final_relres_fp64": rrml,
             "fallback_rule": {"learned_kept": bool(used), "iters_mixed_plain": ip, "iters_mixed_learned": il},
-            "training": {"set": "annulus hierarchies p in {2,3,4}, n in {16,32} (FP64)", "steps": args.train_steps,
+            "training": {"set": "annulus hierarchies p in {2,3,4}, n in {16,32}, 4 coefficient seeds each (FP64)",
+                         "steps": args.train_steps,
                          "probes": 4, "lr": 1e-2, "seconds": train_s,
                          "loss_first": float(hist[0]) if len(hist) else None,
                          "loss_last": float(hist[-1]) if len(hist) else None},

@@ -188,17 +188,19 @@ def test_fullsize_learned_damping_mixed_precision(cube64):
 def test_fullsize_annulus_learned_mixed_precision():
     """The learned-damping workload: quarter annulus (NURBS geometry) p=3
     n=64 with a random log-normal coefficient.  Network trained on annulus
-    hierarchies p in {2,3,4}, n in {16,32}; the mixed-precision learned
+    hierarchies p in {2,3,4}, n in {16,32} with four other coefficient
+    fields each; the mixed-precision learned
     solve meets rtol 1e-8 on the FP64 true residual, stays within 1e-7 of
     the FP64 solution and needs fewer iterations than plain FP64 AMG."""
     prob = I.annulus_kappa(64, 3)
     args = (dev(prob.rowptr), dev(prob.col), dev(prob.val))
     F = dev(prob.F)
-    train = []
+    train = []  # p in {2,3,4} x n in {16,32} x 4 coefficient fields (not the evaluated one, seed 7)
     for n in (16, 32):
         for pp in (2, 3, 4):
-            q = I.annulus_kappa(n, pp)
-            train.append(A.Hierarchy(dev(q.rowptr), dev(q.col), dev(q.val)))
+            for ks in (101, 102, 103, 104):
+                q = I.annulus_kappa(n, pp, kappa_seed=ks)
+                train.append(A.Hierarchy(dev(q.rowptr), dev(q.col), dev(q.val)))
     w = dev(I.mpnn_init_weights(1).astype(np.float32))
     hist = train[0].mpnn_train(w, steps=60, nprobe=4, seed=2000, lr=1e-2, others=train[1:])
     ref = A.Hierarchy(*args).solve(F, rtol=1e-8)

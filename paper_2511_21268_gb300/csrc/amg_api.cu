@@ -44,6 +44,45 @@ constexpr size_t kPad = 8;
 
 thread_local char g_cuda_err[512] = "";
 
+}  // namespace
+
+namespace amg {
+// Device memory of the library comes from its own stream-ordered memory pool
+// (one per device) that keeps freed memory reserved, so that building and
+// freeing hierarchies in a loop reuses it instead of returning it to the
+// driver at every synchronisation.  The caller's default pool is untouched.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            e = cudaMemPoolCreate(&pools[dev], &props);
+            if (e != cudaSuccess) {
+                pools[dev] = nullptr;
+                return e;
+            }
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        pool = pools[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+}  // namespace amg
+
+namespace {
+
 // Process-wide pool of the small per-hierarchy resources whose creation is
 // slow (page-locked host blocks, CUDA events), so that building and freeing
 // hierarchies in a loop does not pay for them every time.  Keyed by device.
@@ -136,8 +175,8 @@ int dalloc(amg_hierarchy* h, T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
     void* q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, sizeof(T) * count, h->s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    cudaError_t e = dev_alloc(&q, sizeof(T) * count, h->s);
+    if (e != cudaSuccess) return cuda_fail(e, "device allocation");
     h->allocs.push_back(q);
     *p = (T*)q;
     return AMG_OK;
@@ -154,8 +193,8 @@ struct Tmp {
     template <typename T>
     int get(T** out, size_t count) {
         if (count == 0) count = 1;
-        cudaError_t e = cudaMallocAsync(&p, sizeof(T) * count, s);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+        cudaError_t e = dev_alloc(&p, sizeof(T) * count, s);
+        if (e != cudaSuccess) return cuda_fail(e, "device allocation");
         *out = (T*)p;
         return AMG_OK;
     }
@@ -582,8 +621,8 @@ void free_multi(amg_hierarchy* h) {
 template <typename T>
 int walloc(amg_hierarchy* h, MultiWork& w, T** p, size_t count) {
     void* q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, sizeof(T) * (count ? count : 1), h->s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    cudaError_t e = dev_alloc(&q, sizeof(T) * (count ? count : 1), h->s);
+    if (e != cudaSuccess) return cuda_fail(e, "device allocation");
     w.allocs.push_back(q);
     *p = static_cast<T*>(q);
     return AMG_OK;

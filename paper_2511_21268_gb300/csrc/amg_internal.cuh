@@ -269,6 +269,8 @@ cudaError_t launch_stream_spmv_pq(amg_hierarchy* h, const float* p32, const doub
                                   double* part_pq, double* part_pr, int flexible, cudaStream_t s);
 // amg_api.cu: order the library stream after the caller's stream
 int join_caller_stream(amg_hierarchy* h);
+// amg_api.cu: stream-ordered device allocation from the library's memory pool
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
 cudaError_t launch_interleave(int n, int R, int64_t ld, const double* src, double* dst, cudaStream_t s);
 cudaError_t launch_deinterleave(int n, int R, int64_t ld, const double* src, double* dst, cudaStream_t s);
 // batch assembly (setup_kernels.cu)

@@ -549,7 +549,7 @@ int status_of(cudaError_t e) {
 }
 
 int mp_alloc(amg_hierarchy* h, void** p, size_t bytes) {
-    cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, h->s);
+    cudaError_t e = dev_alloc(p, bytes ? bytes : 16, h->s);
     if (e != cudaSuccess) return status_of(e);
     h->mp->allocs.push_back(*p);
     return AMG_OK;
@@ -927,7 +927,7 @@ int amg_mpnn_select(amg_hierarchy* h, const float* w, const double* F, double rt
     if (!h || !w || !F || !(rtol > 0.0) || itmax < 1 || h->nsys > 0) return AMG_ERR_ARG;
     const int n = h->lev[0].A.n;
     double* u = nullptr;
-    MP_RC(status_of(cudaMallocAsync(&u, sizeof(double) * n, h->s)));
+    MP_RC(status_of(dev_alloc(reinterpret_cast<void**>(&u), sizeof(double) * n, h->s)));
     struct Release {
         double* p;
         cudaStream_t s;

@@ -230,6 +230,12 @@ __global__ void k_match_propose(int n, const int64_t* __restrict__ rp, const int
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = warp; i < n; i += nw) {
         if (state[i] != -1) continue;
+        // Active neighbours only leave between rounds, so the heaviest one of
+        // the previous round is still the heaviest while it stays active.
+        if (prev_active) {
+            const int c = cand[i];
+            if (c >= 0 && state[c] == -1) continue;
+        }
         uint64_t bk = 0;
         int blo = 0x7fffffff, bhi = 0x7fffffff, bj = -1;
         for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {

@@ -579,7 +579,7 @@ int stream_prepare(amg_hierarchy* h, int* scratch2) {
     for (const void* a : arrays)
         if (a && (reinterpret_cast<uintptr_t>(a) & 15)) return AMG_OK;
     int2* win = nullptr;
-    if (cudaMallocAsync(&win, sizeof(int2) * G, h->s) != cudaSuccess) return AMG_ERR_NOMEM;
+    if (dev_alloc(reinterpret_cast<void**>(&win), sizeof(int2) * G, h->s) != cudaSuccess) return AMG_ERR_NOMEM;
     h->allocs.push_back(win);
     for (int v = 0; v < 2; v++) {  // v = 0: RPW 2 (32-row slabs), v = 1: RPW 1 (16-row slabs)
         const int rpw = v == 0 ? 2 : 1;
@@ -634,13 +634,13 @@ int stream_prepare(amg_hierarchy* h, int* scratch2) {
         const int64_t nnz = F0.A.nnz;
         const int gw = (int)std::min<int64_t>((n + 7) / 8, 8192);
         if (F0.val16) {
-            if (cudaMallocAsync(&F0.val16t, sizeof(__nv_bfloat16) * (nnz + 16), h->s) != cudaSuccess)
+            if (dev_alloc(reinterpret_cast<void**>(&F0.val16t), sizeof(__nv_bfloat16) * (nnz + 16), h->s) != cudaSuccess)
                 return AMG_ERR_NOMEM;
             h->allocs.push_back(F0.val16t);
             k_interleave_runs<<<AMG_GRID(gw), 256, 0, h->s>>>(n, F0.A.rowptr, F0.run_ptr, F0.run_len, F0.val16,
                                                                F0.val16t);
         }
-        if (cudaMallocAsync(&F0.val32t, sizeof(float) * (nnz + 16), h->s) != cudaSuccess) return AMG_ERR_NOMEM;
+        if (dev_alloc(reinterpret_cast<void**>(&F0.val32t), sizeof(float) * (nnz + 16), h->s) != cudaSuccess) return AMG_ERR_NOMEM;
         h->allocs.push_back(F0.val32t);
         k_interleave_runs<<<AMG_GRID(gw), 256, 0, h->s>>>(n, F0.A.rowptr, F0.run_ptr, F0.run_len, F0.val32,
                                                            F0.val32t);

@@ -73,7 +73,28 @@ __global__ void k_nn_features(int n, const int64_t* __restrict__ rp, const int32
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
         const float si = sd[i];
         float ab = 0.f, sg = 0.f;
-        for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
+        const int64_t e = rp[i + 1];
+        int64_t k = rp[i] + lane;
+        // four entries per lane in flight
+        for (; k + 96 < e; k += 128) {
+            int j[4];
+            float a[4], s[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                j[u] = ci[k + 32 * u];
+                a[u] = (float)v[k + 32 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) s[u] = sd[j[u]];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const bool off = j[u] != i;
+                ab += off ? fabsf(a[u]) : 0.f;
+                sg += off ? a[u] : 0.f;
+                ap[k + 32 * u] = off ? si * a[u] * s[u] : 0.f;
+            }
+        }
+        for (; k < e; k += 32) {
             const int j = ci[k];
             const float a = (float)v[k];
             float out = 0.f;

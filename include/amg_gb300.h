@@ -120,6 +120,10 @@ typedef struct {
      * [8] precision copies and solve workspace */
     double setup_phase_ms[12];
     int32_t level_format[AMG_MAX_LEVELS]; /* 1 = run-encoded columns, 0 = plain CSR */
+    int32_t staged_passes; /* finest-level passes of a mixed-precision solve: 0 = row-group
+                              kernels, 1 = staged slabs with a lane per run, 2 = staged sliced
+                              slabs with a lane per row (matrix_format 2) */
+    int64_t staged_slots;  /* value slots of the sliced slabs (padding included), 0 if unused */
 } amg_info;
 
 typedef struct amg_hierarchy amg_hierarchy;

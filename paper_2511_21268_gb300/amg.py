@@ -54,7 +54,8 @@ class AmgInfo(ctypes.Structure):
                 ("solve_ms", ctypes.c_double), ("iters", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("final_relres", ctypes.c_double), ("vcycle_bytes", ctypes.c_double),
                 ("iter_bytes", ctypes.c_double), ("match_rounds", ctypes.c_int32 * AMG_MAX_LEVELS),
-                ("setup_phase_ms", ctypes.c_double * 12), ("level_format", ctypes.c_int32 * AMG_MAX_LEVELS)]
+                ("setup_phase_ms", ctypes.c_double * 12), ("level_format", ctypes.c_int32 * AMG_MAX_LEVELS),
+                ("staged_passes", ctypes.c_int32), ("staged_slots", ctypes.c_int64)]
 
 
 class AmgError(RuntimeError):

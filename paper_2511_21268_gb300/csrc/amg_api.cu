@@ -577,6 +577,8 @@ void fill_info(amg_hierarchy* h) {
         I.match_rounds[l] = rounds;
         I.level_format[l] = h->lev[l].run_ptr ? 1 : 0;
     }
+    I.staged_passes = h->stream;
+    I.staged_slots = h->stream == 2 ? h->sell_slots * h->sell_lm * 32 : 0;
     I.opc = tot / (double)h->lev[0].A.nnz;
     // algorithmic bytes: one matrix pass = nnz (value + 4) + (n + 1) 8 + x read + y write
     // (value and vector sizes of the V-cycle precision: 8 / 8 in FP64, 4 / 4 in

@@ -176,7 +176,7 @@ struct amg_hierarchy {
     int ph_n = 0;
     int* round_active = nullptr;  // active count after each matching round (device)
     // bulk-copy streamed finest-level passes of the mixed-precision solve
-    int stream = 0;             // in use
+    int stream = 0;             // in use: 1 = lane-per-run slabs, 2 = sliced (lane-per-row) slabs
     int stream_blocks = 0;      // persistent grid (one block per SM)
     int stream_rpw = 0;         // rows per warp of a slab (slab = 8 warps x rpw rows)
     int stream_xbytes = 0;      // shared-memory bytes of the vector window
@@ -184,6 +184,17 @@ struct amg_hierarchy {
     int stream_rbytes[2] = {};  // run-start buffer bytes
     int stream_nbuf[2] = {};    // buffers in the copy ring
     int* stream_win = nullptr;  // int2 per block: first and last column of its rows
+    // sliced copy of the run-encoded finest level (32-row slabs, lane per
+    // row) used by the staged passes when stream == 2
+    int sell_lm = 0;                     // value slots per run slot (odd, 3..9)
+    int sell_nsl = 0;                    // slabs
+    int64_t sell_slots = 0;              // run slots in all
+    int32_t* sell_soff = nullptr;        // nsl + 1: first run slot of each slab
+    int32_t* sell_rs = nullptr;          // start column of each (slot, lane)
+    float* sell_v32 = nullptr;           // FP32 values, slot-major, lane-minor
+    __nv_bfloat16* sell_v16 = nullptr;   // BF16 values (BF16 finest values only)
+    int sell_vbytes[2] = {};             // value area per buffer: [0] BF16, [1] FP32
+    int sell_rbytes = 0;                 // start-column area per buffer
     // multi-system solves
     amg::MultiWork* mw = nullptr;
     // learned smoother damping: network buffers, and whether the smoother
@@ -267,6 +278,13 @@ cudaError_t launch_stream_up0(amg_hierarchy* h, const double* r, const float* x,
                               const double* q, double* part_rz, double* part_zq, int flexible, cudaStream_t s);
 cudaError_t launch_stream_spmv_pq(amg_hierarchy* h, const float* p32, const double* p, const double* r, double* q,
                                   double* part_pq, double* part_pr, int flexible, cudaStream_t s);
+// sell_kernels.cu
+int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used);
+cudaError_t sell_resid(amg_hierarchy* h, const double* f, const float* x, float* rbuf, cudaStream_t s);
+cudaError_t sell_up0(amg_hierarchy* h, const double* r, const float* x, const float* invd, double* z,
+                     const double* q, double* part_rz, double* part_zq, int flexible, cudaStream_t s);
+cudaError_t sell_spmv_pq(amg_hierarchy* h, const float* p32, const double* p, const double* r, double* q,
+                         double* part_pq, double* part_pr, int flexible, cudaStream_t s);
 // amg_api.cu: order the library stream after the caller's stream
 int join_caller_stream(amg_hierarchy* h);
 // amg_api.cu: stream-ordered device allocation from the library's memory pool

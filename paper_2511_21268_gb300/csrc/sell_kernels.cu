@@ -1,0 +1,552 @@
+// Finest-level passes of the mixed-precision solve on a sliced copy of the
+// run-encoded matrix: 32-row slabs, one lane per row.
+//
+// The lane-per-run slab kernels (stream_kernels.cu) spend most of their
+// issue slots on per-row work: row metadata, the run-length dispatch, the
+// lane-partial tile and its shuffle reduction, and lanes left idle when a
+// row's run count is not a multiple of 32 (49 runs of a 3-D cubic row fill
+// 64 lane slots).  Here the finest matrix is re-laid out once, at setup, in
+// slabs of 32 consecutive rows:
+//   * slab k has Rs[k] = the largest run count of its rows run slots; slot r
+//     of lane t (row 32 k + t) holds the start column of that row's run r
+//     and LM value slots (LM = the largest run length, rounded up to odd),
+//     stored slot-major and lane-minor: value o of slot r of lane t at
+//     ((soff[k] + r) LM + o) 32 + t, start column at (soff[k] + r) 32 + t;
+//   * rows with fewer runs, shorter runs, or no row at all (the last slab)
+//     are padded with zero values whose columns stay inside the matrix; a run
+//     that would reach past the last column is shifted left, its values
+//     placed at the shifted offsets.
+// Each block (one per SM) owns a contiguous range of slabs and first copies
+// the window of the gathered vector its slabs reference into shared memory.
+// A producer warp streams the slabs (values, start columns, epilogue vector
+// segments) with cp.async.bulk into a ring of buffers completing on
+// mbarriers.  The 16 compute warps split a slab's run slots (warp w takes
+// slots w', w' + 16, ...; the assignment rotates from slab to slab), each
+// lane accumulating its own row, so a slot costs one start-column load, and
+// per value one value load, one vector load and one FMA, every load from
+// shared memory at a compile-time offset.  Every warp writes its 32 partial
+// row sums to the buffer; the slab's epilogue warp (rotating) waits for all
+// 16, adds them in warp order (deterministic), and runs the epilogue
+// (residual, smoothing with z and r.z, q = K p with p.q) with one lane per
+// row.  Dot products accumulate in the epilogue lanes in slab order and are
+// written as one deterministic partial per block.
+//
+// Every wait on an mbarrier is bounded; on expiry the kernel records
+// AMG_ERR_TIMEOUT in the solve state, waits (again bounded) for its copies
+// in flight and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "amg_internal.cuh"
+#include "stream_common.cuh"
+
+namespace amg {
+
+namespace {
+
+constexpr int kSlab = 32;                                   // rows per slab (one per lane)
+constexpr uint32_t kSegBytes = kSlab * 8;                   // one staged epilogue segment
+constexpr uint32_t kPartBytes = kStreamWarps * kSlab * 4;   // partial row sums of the 16 warps
+constexpr uint32_t kSellCtl = 128;                          // barriers and control words
+
+struct SellShape {
+    uint32_t xbytes;  // vector window bytes
+    uint32_t vbytes;  // value area bytes per buffer (largest slab)
+    uint32_t rbytes;  // start-column area bytes per buffer
+    int nbuf;         // buffers in the ring (2..kMaxBuf)
+};
+
+__host__ __device__ inline uint32_t sell_buffer_bytes(SellShape sh) {
+    return sh.vbytes + sh.rbytes + kMaxVec * kSegBytes + kPartBytes;
+}
+
+__host__ __device__ inline uint32_t sell_smem_bytes(SellShape sh) {
+    return sh.xbytes + (uint32_t)sh.nbuf * sell_buffer_bytes(sh) + kSellCtl;
+}
+
+template <int OFF>
+__device__ __forceinline__ float lds_val_at(uint32_t a, const float*) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF));
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ float lds_val_at(uint32_t a, const __nv_bfloat16*) {
+    unsigned short u;
+    asm volatile("ld.shared.u16 %0, [%1+%2];" : "=h"(u) : "r"(a), "n"(OFF));
+    return __uint_as_float((uint32_t)u << 16);
+}
+
+// Value slots O .. LM-1 of one run slot: value o at va + o 32 sizeof(V),
+// vector entry at xa + 4 o; two accumulators halve the FMA chain.
+template <int O, int LM, typename V>
+struct SlotDot {
+    static __device__ __forceinline__ void run(uint32_t va, uint32_t xa, float& a0, float& a1) {
+        const float v = lds_val_at<O * kSlab * (int)sizeof(V)>(va, static_cast<const V*>(nullptr));
+        const float x = lds_x<4 * O>(xa);
+        if (O & 1) a1 = fmaf(v, x, a1);
+        else a0 = fmaf(v, x, a0);
+        SlotDot<O + 1, LM, V>::run(va, xa, a0, a1);
+    }
+};
+template <int LM, typename V>
+struct SlotDot<LM, LM, V> {
+    static __device__ __forceinline__ void run(uint32_t, uint32_t, float&, float&) {}
+};
+
+// Block b owns slabs [b nsl / G, (b + 1) nsl / G) and the vector window
+// win[b] = (lo, hi), the smallest and largest column its slabs read.  The
+// epilogue vectors are read in 16-byte-widened segments of the slab's rows
+// (the vectors are padded for the last slab).
+template <int LM, typename V, typename Epi>
+__global__ void __launch_bounds__(kStreamThreads, 1)
+    k_sell(int n, int nsl, const int32_t* __restrict__ soff, const V* __restrict__ val, const int32_t* __restrict__ rs,
+           const float* __restrict__ xg, const int2* __restrict__ win, SellShape shape, Epi epi, double* part1,
+           double* part2, SolveState* st) {
+    if (st && st->done) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int nbuf = shape.nbuf;
+    const float* xw = reinterpret_cast<const float*>(smem);
+    unsigned char* ring = smem + shape.xbytes;
+    const uint32_t bufstride = sell_buffer_bytes(shape);
+    const uint32_t o_rs = shape.vbytes, o_seg = o_rs + shape.rbytes, o_part = o_seg + kMaxVec * kSegBytes;
+    unsigned char* ctl = ring + nbuf * bufstride;
+    // [0] window, [1 + j] full[j], [1 + kMaxBuf + j] empty[j], [1 + 2 kMaxBuf + j] partials[j]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ctl);
+    constexpr int kBarBytes = 8 * (1 + 3 * kMaxBuf);
+    int* rsl = reinterpret_cast<int*>(ctl + kBarBytes);                                 // run slots of buffer j
+    volatile int* ctrl = reinterpret_cast<int*>(ctl + kBarBytes + 4 * kMaxBuf);        // 0 = go on, 1 = give up
+    int* xlo = reinterpret_cast<int*>(ctl + kBarBytes + 4 * kMaxBuf + 4);             // first window entry
+    __shared__ double red[kStreamWarps + 1];
+
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int s0 = (int)((int64_t)blockIdx.x * nsl / gridDim.x);
+    const int s1 = (int)((int64_t)(blockIdx.x + 1) * nsl / gridDim.x);
+    const uint32_t bar_win = smem_addr(&bars[0]);
+    auto bar_full = [&](int j) { return smem_addr(&bars[1 + j]); };
+    auto bar_empty = [&](int j) { return smem_addr(&bars[1 + kMaxBuf + j]); };
+    auto bar_part = [&](int j) { return smem_addr(&bars[1 + 2 * kMaxBuf + j]); };
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar_win, 1);
+        for (int j = 0; j < kMaxBuf; j++) {
+            mbar_init(bar_full(j), 1);
+            mbar_init(bar_empty(j), kStreamWarps);
+            mbar_init(bar_part(j), kStreamWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        *ctrl = 0;
+        *xlo = 0;
+        if (s0 < s1) *xlo = win[blockIdx.x].x & ~3;
+    }
+    __syncthreads();
+
+    double acc1 = 0.0, acc2 = 0.0;
+    if (wid == kStreamWarps) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0 && s0 < s1) {
+            const int2 w = win[blockIdx.x];
+            const int lo = w.x & ~3;
+            const uint32_t bytes = align16((uint32_t)(w.y + 1 - lo) * 4u);
+            mbar_expect_tx(bar_win, bytes);
+            bulk_g2s(smem_addr(smem), xg + lo, bytes, bar_win);
+            int last_use[kMaxBuf] = {-1, -1, -1};
+            for (int k = s0; k < s1; k++) {
+                if (*ctrl) break;
+                const int u = (k - s0) / nbuf, j = (k - s0) % nbuf;
+                if (u > 0 && !mbar_wait_bounded(bar_empty(j), (uint32_t)(u - 1) & 1u)) {
+                    *ctrl = 1;
+                    break;
+                }
+                const int o0 = soff[k];
+                const int R = soff[k + 1] - o0;
+                rsl[j] = R;
+                const int a = k * kSlab;
+                const uint32_t cnt = (uint32_t)min(kSlab, n - a);
+                const uint32_t vb = (uint32_t)R * (uint32_t)(LM * kSlab * sizeof(V));
+                const uint32_t rb = (uint32_t)R * (uint32_t)(kSlab * 4);
+                uint32_t tx = vb + rb;
+#pragma unroll
+                for (int v = 0; v < kMaxVec; v++)
+                    if (v < epi.nvec) tx += align16(cnt * (uint32_t)epi.es[v]);
+                unsigned char* bv = ring + j * bufstride;
+                const uint32_t bar = bar_full(j);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(bar, tx);
+                if (R > 0) {
+                    bulk_g2s(smem_addr(bv), val + (int64_t)o0 * (LM * kSlab), vb, bar);
+                    bulk_g2s(smem_addr(bv + o_rs), rs + (int64_t)o0 * kSlab, rb, bar);
+                }
+#pragma unroll
+                for (int v = 0; v < kMaxVec; v++)
+                    if (v < epi.nvec)
+                        bulk_g2s(smem_addr(bv + o_seg + v * kSegBytes),
+                                 reinterpret_cast<const unsigned char*>(epi.vec[v]) + (int64_t)a * epi.es[v],
+                                 align16(cnt * (uint32_t)epi.es[v]), bar);
+                if (j == 0) last_use[0] = u;
+                else if (j == 1) last_use[1] = u;
+                else last_use[2] = u;
+            }
+            if (*ctrl) {  // drain copies that may still be in flight (bounded), keeping smem alive
+                mbar_wait_bounded(bar_win, 0u);
+                if (last_use[0] >= 0) mbar_wait_bounded(bar_full(0), (uint32_t)last_use[0] & 1u);
+                if (last_use[1] >= 0) mbar_wait_bounded(bar_full(1), (uint32_t)last_use[1] & 1u);
+                if (last_use[2] >= 0) mbar_wait_bounded(bar_full(2), (uint32_t)last_use[2] & 1u);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ consumers
+        bool ok = true;
+        if (s0 < s1) {
+            if (lane == 0) ok = mbar_wait_bounded(bar_win, 0u);
+            ok = __shfl_sync(FULL, ok, 0);
+            __syncwarp();
+        }
+        const float* xs = xw - *xlo;  // xs[c] = vector entry c (inside the window)
+        // shared address of vector entry 0 (32-bit wrap-around: entry c at xbase + 4 c)
+        const uint32_t xbase = smem_addr(xw) - 4u * (uint32_t)(*xlo);
+        for (int k = s0; k < s1 && ok; k++) {
+            const int u = (k - s0) / nbuf, j = (k - s0) % nbuf;
+            if (lane == 0) ok = !*ctrl && mbar_wait_bounded(bar_full(j), (uint32_t)u & 1u);
+            ok = __shfl_sync(FULL, ok, 0);
+            if (!ok) break;
+            __syncwarp();
+            unsigned char* bv = ring + j * bufstride;
+            const int R = rsl[j];
+            const int e = (k - s0) % kStreamWarps;              // the slab's epilogue warp ...
+            const int r0 = (wid - e - 1) & (kStreamWarps - 1);  // ... takes the last slot offset
+            const uint32_t va0 = smem_addr(bv) + (uint32_t)sizeof(V) * (uint32_t)lane;
+            const uint32_t ra0 = smem_addr(bv + o_rs) + 4u * (uint32_t)lane;
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll 1
+            for (int r = r0; r < R; r += kStreamWarps) {
+                const uint32_t xa = xbase + 4u * (uint32_t)lds_s32(ra0 + (uint32_t)r * (uint32_t)(kSlab * 4));
+                SlotDot<0, LM, V>::run(va0 + (uint32_t)r * (uint32_t)(LM * kSlab * sizeof(V)), xa, a0, a1);
+            }
+            float* part = reinterpret_cast<float*>(bv + o_part);
+            part[wid * kSlab + lane] = a0 + a1;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_part(j));
+            if (wid != e) {
+                if (lane == 0) mbar_arrive(bar_empty(j));  // done with buffer j
+                continue;
+            }
+            if (lane == 0) ok = mbar_wait_bounded(bar_part(j), (uint32_t)u & 1u);
+            ok = __shfl_sync(FULL, ok, 0);
+            if (!ok) break;
+            __syncwarp();
+            float s = 0.f;
+#pragma unroll
+            for (int w = 0; w < kStreamWarps; w++) s += part[w * kSlab + lane];  // warp order
+            const int i = k * kSlab + lane;
+            if (i < n) epi(i, lane, s, bv + o_seg, kSegBytes, xs, acc1, acc2);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_empty(j));
+        }
+        if (!ok && lane == 0) *ctrl = 1;
+    }
+    __syncthreads();
+    if (*ctrl) {
+        if (threadIdx.x == 0 && st) {
+            st->status = AMG_ERR_TIMEOUT;
+            st->done = 1;
+        }
+        return;
+    }
+    if (part1) block_sum_to(acc1, red, part1 + blockIdx.x);
+    if (part2) block_sum_to(acc2, red, part2 + blockIdx.x);
+}
+
+// Run slots of each slab (the largest run count of its rows) and the
+// largest run length of the matrix (atomic max); a warp per slab.
+__global__ void k_sell_slots(int n, int nsl, const int32_t* __restrict__ rptr, const uint8_t* __restrict__ rlen,
+                             int32_t* slots, int* lmax) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nsl; k += nw) {
+        const int i = k * kSlab + lane;
+        int R = 0, L = 0;
+        if (i < n) {
+            R = rptr[i + 1] - rptr[i];
+            L = rlen[i];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            R = max(R, __shfl_xor_sync(FULL, R, o));
+            L = max(L, __shfl_xor_sync(FULL, L, o));
+        }
+        if (lane == 0) {
+            slots[k] = R;
+            atomicMax(lmax, L);
+        }
+    }
+}
+
+// Fill the sliced copy (a warp per slab, a lane per row): start columns,
+// FP32 values and (if o16) BF16 values; swin[k] = the smallest and largest
+// column slab k reads.  A run of row i (start c, L entries) goes to slot r
+// at start c' = min(c, n - LM), its value q at offset q + c - c'; empty
+// slots (r >= the row's runs, or no row) read LM zeros from the slab's
+// first start column.
+__global__ void k_sell_fill(int n, int nsl, int LM, const int64_t* __restrict__ rp, const int32_t* __restrict__ rptr,
+                            const uint8_t* __restrict__ rlen, const int32_t* __restrict__ rst,
+                            const int32_t* __restrict__ soff, const float* __restrict__ v32,
+                            const __nv_bfloat16* __restrict__ v16, float* o32, __nv_bfloat16* o16, int32_t* ors,
+                            int2* swin) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nsl; k += nw) {
+        const int i = k * kSlab + lane;
+        const int o0 = soff[k], Rs = soff[k + 1] - o0;
+        int r0 = 0, Ri = 0, Li = 0;
+        int64_t b = 0;
+        if (i < n) {
+            r0 = rptr[i];
+            Ri = rptr[i + 1] - r0;
+            Li = rlen[i];
+            b = rp[i];
+        }
+        const int f0 = rptr[k * kSlab];
+        const int cpad = rptr[k * kSlab + 1] > f0 ? max(0, min(rst[f0], n - LM)) : 0;
+        int lo = INT32_MAX, hi = -1;
+        for (int r = 0; r < Rs; r++) {
+            int c = cpad, sh = 0;
+            const bool has = r < Ri;
+            if (has) {
+                const int c0 = rst[r0 + r];
+                c = min(c0, n - LM);
+                sh = c0 - c;
+            }
+            const int64_t slot = (int64_t)o0 + r;
+            ors[slot * kSlab + lane] = c;
+            lo = min(lo, c);
+            hi = max(hi, c + LM - 1);
+            for (int o = 0; o < LM; o++) {
+                const int q = o - sh;
+                const bool hv = has && q >= 0 && q < Li;
+                const int64_t dst = (slot * LM + o) * kSlab + lane;
+                const int64_t src = b + (int64_t)r * Li + q;
+                o32[dst] = hv ? v32[src] : 0.f;
+                if (o16) o16[dst] = hv ? v16[src] : __float2bfloat16_rn(0.f);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(FULL, lo, o));
+            hi = max(hi, __shfl_xor_sync(FULL, hi, o));
+        }
+        if (lane == 0) swin[k] = make_int2(lo, hi);
+    }
+}
+
+// Window of each grid block: smallest and largest column over its slabs.
+__global__ void k_sell_window(int nsl, int G, const int2* __restrict__ swin, int2* win) {
+    __shared__ int slo[256], shi[256];
+    const int b = blockIdx.x;
+    const int k0 = (int)((int64_t)b * nsl / G), k1 = (int)((int64_t)(b + 1) * nsl / G);
+    int lo = INT32_MAX, hi = -1;
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        lo = min(lo, swin[k].x);
+        hi = max(hi, swin[k].y);
+    }
+    slo[threadIdx.x] = lo;
+    shi[threadIdx.x] = hi;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            slo[threadIdx.x] = min(slo[threadIdx.x], slo[threadIdx.x + o]);
+            shi[threadIdx.x] = max(shi[threadIdx.x], shi[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) win[b] = k1 > k0 ? make_int2(slo[0], shi[0]) : make_int2(0, 0);
+}
+
+SellShape sell_shape(const amg_hierarchy* h, int q) {
+    return SellShape{(uint32_t)h->stream_xbytes, (uint32_t)h->sell_vbytes[q], (uint32_t)h->sell_rbytes,
+                     h->stream_nbuf[q]};
+}
+
+template <int LM, typename V, typename Epi>
+bool sell_attr(uint32_t smem) {
+    return cudaFuncSetAttribute(k_sell<LM, V, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+           cudaSuccess;
+}
+
+template <int LM>
+bool sell_attrs_lm(uint32_t m16, uint32_t m32) {
+    return sell_attr<LM, __nv_bfloat16, EpiResid>(m16) && sell_attr<LM, __nv_bfloat16, EpiUp0>(m16) &&
+           sell_attr<LM, float, EpiResid>(m32) && sell_attr<LM, float, EpiUp0>(m32) &&
+           sell_attr<LM, float, EpiPQ>(m32);
+}
+
+template <int LM, typename V, typename Epi>
+cudaError_t sell_launch_lm(amg_hierarchy* h, int q, const V* val, const float* x, const Epi& epi, double* p1,
+                           double* p2, cudaStream_t s) {
+    const SellShape sh = sell_shape(h, q);
+    k_sell<LM, V, Epi><<<AMG_GRID(h->stream_blocks), kStreamThreads, sell_smem_bytes(sh), s>>>(
+        h->lev[0].A.n, h->sell_nsl, h->sell_soff, val, h->sell_rs, x, reinterpret_cast<const int2*>(h->stream_win),
+        sh, epi, p1, p2, h->st);
+    return cudaGetLastError();
+}
+
+template <typename V, typename Epi>
+cudaError_t sell_launch(amg_hierarchy* h, int q, const V* val, const float* x, const Epi& epi, double* p1,
+                        double* p2, cudaStream_t s) {
+    switch (h->sell_lm) {
+        case 3: return sell_launch_lm<3>(h, q, val, x, epi, p1, p2, s);
+        case 5: return sell_launch_lm<5>(h, q, val, x, epi, p1, p2, s);
+        case 7: return sell_launch_lm<7>(h, q, val, x, epi, p1, p2, s);
+        default: return sell_launch_lm<9>(h, q, val, x, epi, p1, p2, s);
+    }
+}
+
+}  // namespace
+
+// Build the sliced copy and size the ring; sets h->stream = 2 and returns
+// AMG_OK with *used = 1 when the slabs average at least kMinSlots run slots
+// (enough to occupy the 16 compute warps) and everything fits the
+// shared-memory budget, else leaves the hierarchy unchanged (*used = 0).
+int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
+    constexpr int kMinSlots = 16;
+    *used = 0;
+    Level& F0 = h->lev[0];
+    const int n = F0.A.n;
+    const int G = h->num_sms;
+    if (n < 16) return AMG_OK;
+    const int nsl = (n + kSlab - 1) / kSlab;
+    int32_t* slots = nullptr;
+    if (dev_alloc(reinterpret_cast<void**>(&slots), sizeof(int32_t) * (nsl + 1), h->s) != cudaSuccess)
+        return AMG_ERR_NOMEM;
+    h->allocs.push_back(slots);
+    const int gw = std::min((nsl + 7) / 8, 8192);
+    if (cudaMemsetAsync(scratch, 0, sizeof(int), h->s) != cudaSuccess) return AMG_ERR_CUDA;
+    k_sell_slots<<<AMG_GRID(gw), 256, 0, h->s>>>(n, nsl, F0.run_ptr, F0.run_len, slots, scratch);
+    std::vector<int32_t> hs(nsl + 1);
+    int lmax = 0;
+    if (cudaMemcpyAsync(hs.data(), slots, sizeof(int32_t) * nsl, cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
+        cudaMemcpyAsync(&lmax, scratch, sizeof(int), cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
+        cudaStreamSynchronize(h->s) != cudaSuccess)
+        return AMG_ERR_CUDA;
+    if (lmax < 2 || lmax > kMaxRunLen) return AMG_OK;
+    const int LM = lmax | 1;
+    if (n < LM) return AMG_OK;
+    int64_t total = 0;
+    int rmax = 0;
+    for (int k = 0; k < nsl; k++) {
+        const int32_t r = hs[k];
+        hs[k] = (int32_t)total;
+        total += r;
+        rmax = std::max(rmax, r);
+    }
+    hs[nsl] = (int32_t)total;
+    if (total < (int64_t)kMinSlots * nsl || total * LM * kSlab >= ((int64_t)1 << 40) || total >= INT32_MAX)
+        return AMG_OK;
+    // shared-memory shape
+    const int64_t vb16 = (int64_t)rmax * LM * kSlab * 2, vb32 = (int64_t)rmax * LM * kSlab * 4;
+    const int64_t rb = (int64_t)rmax * kSlab * 4;
+    if (vb32 + rb > (1 << 20)) return AMG_OK;
+    if (cudaMemcpyAsync(slots, hs.data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice, h->s) != cudaSuccess)
+        return AMG_ERR_CUDA;
+    // the sliced copy
+    const bool with16 = F0.val16 != nullptr;
+    float* o32 = nullptr;
+    __nv_bfloat16* o16 = nullptr;
+    int32_t* ors = nullptr;
+    int2* swin = nullptr;
+    int2* win = nullptr;
+    const size_t nv = (size_t)total * LM * kSlab;
+    if (dev_alloc(reinterpret_cast<void**>(&o32), sizeof(float) * nv, h->s) != cudaSuccess) return AMG_ERR_NOMEM;
+    h->allocs.push_back(o32);
+    if (with16) {
+        if (dev_alloc(reinterpret_cast<void**>(&o16), sizeof(__nv_bfloat16) * nv, h->s) != cudaSuccess)
+            return AMG_ERR_NOMEM;
+        h->allocs.push_back(o16);
+    }
+    if (dev_alloc(reinterpret_cast<void**>(&ors), sizeof(int32_t) * (size_t)total * kSlab, h->s) != cudaSuccess)
+        return AMG_ERR_NOMEM;
+    h->allocs.push_back(ors);
+    if (dev_alloc(reinterpret_cast<void**>(&swin), sizeof(int2) * nsl, h->s) != cudaSuccess) return AMG_ERR_NOMEM;
+    h->allocs.push_back(swin);
+    if (dev_alloc(reinterpret_cast<void**>(&win), sizeof(int2) * G, h->s) != cudaSuccess) return AMG_ERR_NOMEM;
+    h->allocs.push_back(win);
+    const void* arrays[] = {o32, o16, ors};
+    for (const void* a : arrays)
+        if (a && (reinterpret_cast<uintptr_t>(a) & 15)) return AMG_OK;
+    k_sell_fill<<<AMG_GRID(gw), 256, 0, h->s>>>(n, nsl, LM, F0.A.rowptr, F0.run_ptr, F0.run_len, F0.run_start, slots,
+                                                F0.val32, F0.val16, o32, o16, ors, swin);
+    k_sell_window<<<AMG_GRID(G), 256, 0, h->s>>>(nsl, G, swin, win);
+    std::vector<int2> hw(G);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(hw.data(), win, sizeof(int2) * G, cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
+        cudaStreamSynchronize(h->s) != cudaSuccess)
+        return AMG_ERR_CUDA;
+    int64_t xw = 16;
+    for (int b = 0; b < G; b++)
+        xw = std::max<int64_t>(xw, ((int64_t)(hw[b].y + 1 - (hw[b].x & ~3)) * 4 + 15) & ~(int64_t)15);
+    if (xw >= (1 << 20)) return AMG_OK;
+    int nb[2] = {0, 0};
+    for (int q = 0; q < 2; q++) {
+        const uint32_t vb = (uint32_t)(q == 0 ? vb16 : vb32);
+        for (int k = kMaxBuf; k >= 2 && !nb[q]; k--) {
+            const SellShape sh{(uint32_t)xw, vb, (uint32_t)rb, k};
+            if (sell_smem_bytes(sh) + 256u <= (uint32_t)optin) nb[q] = k;  // 256: static shared memory
+        }
+    }
+    if (!nb[1] || (with16 && !nb[0])) return AMG_OK;
+    h->sell_lm = LM;
+    h->sell_nsl = nsl;
+    h->sell_soff = slots;
+    h->sell_v32 = o32;
+    h->sell_v16 = o16;
+    h->sell_rs = ors;
+    h->sell_vbytes[0] = (int)vb16;
+    h->sell_vbytes[1] = (int)vb32;
+    h->sell_rbytes = (int)rb;
+    h->sell_slots = total;
+    h->stream_xbytes = (int)xw;
+    h->stream_nbuf[0] = nb[0];
+    h->stream_nbuf[1] = nb[1];
+    h->stream_win = reinterpret_cast<int*>(win);
+    const uint32_t m16 = nb[0] ? sell_smem_bytes(sell_shape(h, 0)) : 0u;
+    const uint32_t m32 = sell_smem_bytes(sell_shape(h, 1));
+    bool attrs;
+    switch (LM) {
+        case 3: attrs = sell_attrs_lm<3>(m16 ? m16 : m32, m32); break;
+        case 5: attrs = sell_attrs_lm<5>(m16 ? m16 : m32, m32); break;
+        case 7: attrs = sell_attrs_lm<7>(m16 ? m16 : m32, m32); break;
+        default: attrs = sell_attrs_lm<9>(m16 ? m16 : m32, m32); break;
+    }
+    if (!attrs) return AMG_ERR_CUDA;
+    h->stream_blocks = G;
+    h->stream = 2;
+    *used = 1;
+    return AMG_OK;
+}
+
+cudaError_t sell_resid(amg_hierarchy* h, const double* f, const float* x, float* rbuf, cudaStream_t s) {
+    const EpiResid epi{{f, nullptr, nullptr}, {8, 0, 0}, 1, rbuf};
+    if (h->sell_v16) return sell_launch(h, 0, h->sell_v16, x, epi, nullptr, nullptr, s);
+    return sell_launch(h, 1, h->sell_v32, x, epi, nullptr, nullptr, s);
+}
+
+cudaError_t sell_up0(amg_hierarchy* h, const double* r, const float* x, const float* invd, double* z,
+                     const double* q, double* part_rz, double* part_zq, int flexible, cudaStream_t s) {
+    const EpiUp0 epi{{r, invd, q}, {8, 4, 8}, flexible ? 3 : 2, z, flexible};
+    double* p2 = flexible ? part_zq : nullptr;
+    if (h->sell_v16) return sell_launch(h, 0, h->sell_v16, x, epi, part_rz, p2, s);
+    return sell_launch(h, 1, h->sell_v32, x, epi, part_rz, p2, s);
+}
+
+cudaError_t sell_spmv_pq(amg_hierarchy* h, const float* p32, const double* p, const double* r, double* q,
+                         double* part_pq, double* part_pr, int flexible, cudaStream_t s) {
+    const EpiPQ epi{{p, r, nullptr}, {8, 8, 0}, flexible ? 2 : 1, q, flexible};
+    return sell_launch(h, 1, h->sell_v32, p32, epi, part_pq, flexible ? part_pr : nullptr, s);
+}
+
+}  // namespace amg

@@ -33,74 +33,17 @@
 #include <vector>
 
 #include "amg_internal.cuh"
+#include "stream_common.cuh"
 
 namespace amg {
 
 namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
-constexpr int kStreamWarps = 16;                    // compute warps
-constexpr int kStreamThreads = (kStreamWarps + 1) * 32;  // + one producer warp
-constexpr int kMaxBuf = 3;
-constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
-constexpr int kWaitIters = 1 << 28;
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n"
-        ".reg .pred p;\n"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n"
-        "}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// global -> shared bulk copy completing on the mbarrier (16-byte aligned
-// addresses, size a multiple of 16)
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-// Bounded wait for phase `parity` of the mbarrier (one thread); backs off
-// between polls so that waiting warps leave the issue slots to the others.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    for (int it = 0; it < kWaitIters; it++) {
-        __nanosleep(32);
-        if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > kWaitCycles) break;
-    }
-    return false;
-}
-
-__device__ __forceinline__ float ldsv(const float* p, uint32_t k) { return p[k]; }
-__device__ __forceinline__ float ldsv(const __nv_bfloat16* p, uint32_t k) { return __bfloat162float(p[k]); }
 
 // Shared-memory layout: [vector window][NBUF x slab buffer][mbarriers
 // (window + NBUF), copy bases, control words][row tiles].  A slab buffer
 // holds the slab's values, run starts, row metadata (row offsets, run
 // offsets, run lengths) and up to kMaxVec vector segments its epilogue reads,
 // so the compute loop reads only shared memory.
-constexpr int kMaxVec = 3;
 
 struct StreamShape {
     uint32_t xbytes;  // vector window bytes
@@ -110,8 +53,6 @@ struct StreamShape {
 };
 
 constexpr uint32_t kCtrlBytes = 128;  // barriers, bases and the control words
-
-__host__ __device__ constexpr uint32_t align16(uint32_t b) { return (b + 15u) & ~15u; }
 
 // per-buffer bytes of the row metadata and of the vector segments of a slab of S rows
 template <int S>
@@ -132,101 +73,6 @@ __host__ __device__ constexpr uint32_t tile_bytes() {
 template <int RPW>
 __host__ __device__ inline uint32_t stream_smem_bytes(StreamShape sh) {
     return sh.xbytes + (uint32_t)sh.nbuf * buffer_bytes<RPW>(sh) + kCtrlBytes + tile_bytes<RPW>();
-}
-
-// Epilogues: the owner lane of row i (t = i - first row of the slab) gets
-// its total s; seg + v ss holds the slab's staged segment of the epilogue's
-// input vector vec[v] (element t = entry i), xs the vector window (entry c
-// at xs[c]); a1/a2 are the thread's running dot-product terms.
-struct EpiResid {  // rbuf = f - K x
-    const void* vec[kMaxVec];
-    int es[kMaxVec];
-    int nvec;
-    float* rbuf;
-    __device__ __forceinline__ void operator()(int i, int t, float s, const unsigned char* seg, uint32_t,
-                                               const float*, double&, double&) const {
-        const double fi = reinterpret_cast<const double*>(seg)[t];
-        rbuf[i] = (float)fi - s;
-    }
-};
-
-struct EpiUp0 {  // z = x + (r - K x) / d, r.z, z.q
-    const void* vec[kMaxVec];  // r (FP64), 1/d (FP32), q (FP64, flexible)
-    int es[kMaxVec];
-    int nvec;
-    double* z;
-    int flexible;
-    __device__ __forceinline__ void operator()(int i, int t, float s, const unsigned char* seg, uint32_t ss,
-                                               const float* xs, double& rz, double& zq) const {
-        const double ra = reinterpret_cast<const double*>(seg)[t];
-        const float di = reinterpret_cast<const float*>(seg + ss)[t];
-        const double za = (double)fmaf(di, (float)ra - s, xs[i]);
-        z[i] = za;
-        rz += ra * za;
-        if (flexible) zq += za * reinterpret_cast<const double*>(seg + 2 * ss)[t];
-    }
-};
-
-struct EpiPQ {  // q = K p, p.q, p.r
-    const void* vec[kMaxVec];  // p (FP64), r (FP64, flexible)
-    int es[kMaxVec];
-    int nvec;
-    double* q;
-    int flexible;
-    __device__ __forceinline__ void operator()(int i, int t, float s, const unsigned char* seg, uint32_t ss,
-                                               const float*, double& pq, double& pr) const {
-        const double qs = (double)s;
-        q[i] = qs;
-        const double pi = reinterpret_cast<const double*>(seg)[t];
-        pq += pi * qs;
-        if (flexible) pr += pi * reinterpret_cast<const double*>(seg + ss)[t];
-    }
-};
-
-// Deterministic per-block sum of one double per thread -> out (thread 0).
-__device__ __forceinline__ void block_sum_to(double v, double* sh, double* out) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w <= kStreamWarps; w++) t += sh[w];
-        *out = t;
-    }
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// Lane partial of one row whose R runs have LL entries each, values
-// run-interleaved (entry o of run r at rv[o R + r]); lane t takes the runs
-// t, t + 32, ...  Two accumulators halve the FMA dependency chain.
-// Shared-memory loads with 32-bit shared addresses (the window entry at a
-// compile-time offset from the run's first column).
-__device__ __forceinline__ float lds_val(uint32_t a, const float*) {
-    float v;
-    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
-    return v;
-}
-__device__ __forceinline__ float lds_val(uint32_t a, const __nv_bfloat16*) {
-    unsigned short u;
-    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(u) : "r"(a));
-    return __uint_as_float((uint32_t)u << 16);
-}
-__device__ __forceinline__ int lds_s32(uint32_t a) {
-    int v;
-    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
-    return v;
-}
-template <int OFF>
-__device__ __forceinline__ float lds_x(uint32_t a) {
-    float v;
-    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF));
-    return v;
 }
 
 // Entries O .. LL-1 of one run: value at va + o vstride, vector entry at
@@ -578,6 +424,11 @@ int stream_prepare(amg_hierarchy* h, int* scratch2) {
                             L0.t32,      L0.invd32,  h->p32,     h->r,         h->p,     h->q};
     for (const void* a : arrays)
         if (a && (reinterpret_cast<uintptr_t>(a) & 15)) return AMG_OK;
+    {  // rows of many runs: the sliced lane-per-row slabs
+        int used = 0;
+        const int rc = sell_prepare(h, scratch2, optin, &used);
+        if (rc != AMG_OK || used) return rc;
+    }
     int2* win = nullptr;
     if (dev_alloc(reinterpret_cast<void**>(&win), sizeof(int2) * G, h->s) != cudaSuccess) return AMG_ERR_NOMEM;
     h->allocs.push_back(win);
@@ -655,6 +506,7 @@ int stream_prepare(amg_hierarchy* h, int* scratch2) {
 }
 
 cudaError_t launch_stream_resid(amg_hierarchy* h, const double* f, const float* x, float* rbuf, cudaStream_t s) {
+    if (h->stream == 2) return sell_resid(h, f, x, rbuf, s);
     const Level& L0 = h->lev[0];
     const EpiResid epi{{f, nullptr, nullptr}, {8, 0, 0}, 1, rbuf};
     if (L0.val16) return dispatch(h, 0, L0.val16t, x, epi, nullptr, nullptr, s);
@@ -663,6 +515,7 @@ cudaError_t launch_stream_resid(amg_hierarchy* h, const double* f, const float* 
 
 cudaError_t launch_stream_up0(amg_hierarchy* h, const double* r, const float* x, const float* invd, double* z,
                               const double* q, double* part_rz, double* part_zq, int flexible, cudaStream_t s) {
+    if (h->stream == 2) return sell_up0(h, r, x, invd, z, q, part_rz, part_zq, flexible, s);
     const Level& L0 = h->lev[0];
     const EpiUp0 epi{{r, invd, q}, {8, 4, 8}, flexible ? 3 : 2, z, flexible};
     double* p2 = flexible ? part_zq : nullptr;
@@ -672,6 +525,7 @@ cudaError_t launch_stream_up0(amg_hierarchy* h, const double* r, const float* x,
 
 cudaError_t launch_stream_spmv_pq(amg_hierarchy* h, const float* p32, const double* p, const double* r, double* q,
                                   double* part_pq, double* part_pr, int flexible, cudaStream_t s) {
+    if (h->stream == 2) return sell_spmv_pq(h, p32, p, r, q, part_pq, part_pr, flexible, s);
     const Level& L0 = h->lev[0];
     const EpiPQ epi{{p, r, nullptr}, {8, 8, 0}, flexible ? 2 : 1, q, flexible};
     return dispatch(h, 1, L0.val32t, p32, epi, part_pq, flexible ? part_pr : nullptr, s);

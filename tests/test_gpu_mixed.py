@@ -71,3 +71,39 @@ def test_mixed_replacement_only_at_convergence_and_itmax():
     assert c["status"] == A.AMG_ERR_NOT_CONVERGED and c["iters"] == 7
     z = H.solve(torch.zeros(prob.n, dtype=torch.float64, device="cuda"), rtol=1e-8)
     assert z["iters"] == 0 and z["status"] == 0
+
+
+def _expected_staged_kind(prob):
+    """Sliced lane-per-row slabs (2) when the 32-row slabs average at least
+    16 run slots (the largest run count of their rows), else lane-per-run
+    slabs (1); runs are maximal sequences of consecutive columns."""
+    rp, ci = prob.rowptr, prob.col
+    runs = np.array([1 + np.count_nonzero(np.diff(ci[rp[i]:rp[i + 1]]) != 1) for i in range(prob.n)])
+    nsl = (prob.n + 31) // 32
+    pad = np.zeros(nsl * 32, dtype=runs.dtype)
+    pad[:prob.n] = runs
+    return 2 if pad.reshape(nsl, 32).max(axis=1).mean() >= 16 else 1
+
+
+@pytest.mark.parametrize("prec", [A.AMG_FP32, A.AMG_FP32_BF16FINE])
+@pytest.mark.parametrize("d,n,p", [(3, 14, 3), (3, 16, 2), (3, 10, 4), (2, 40, 2)])
+def test_staged_finest_passes_kind_and_vcycle(prec, d, n, p):
+    """Both staged finest-level layouts (sliced slabs with LM = 5, 7, 9 and
+    lane-per-run slabs) give the FP64 oracle's V-cycle within the precision's
+    bound, and the layout follows the slab run-count rule."""
+    prob = I.poisson_box(d, n, p)
+    Ho = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=20)
+    H = A.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=20, precision=prec)
+    kind = _expected_staged_kind(prob)
+    assert H.info.level_format[0] == 1
+    assert H.info.staged_passes == kind
+    if kind == 2:
+        assert H.info.staged_slots >= prob.nnz
+    r = np.random.default_rng(5).standard_normal(prob.n)
+    z = H.vcycle(gpu(r)).cpu().numpy()
+    zo = Ho.vcycle(r)
+    err = np.linalg.norm(z - zo) / np.linalg.norm(zo)
+    print(f"precision={prec} d={d} n={n} p={p}: staged kind {kind}, V-cycle error vs FP64 oracle {err:.2e}")
+    assert err <= VCYCLE_ERR[prec]
+    g = H.solve(gpu(prob.F), rtol=1e-8)
+    assert g["status"] == 0 and g["relres"] <= 1e-8

@@ -40,9 +40,17 @@ WORKLOAD = "3-D Poisson unit cube, B-spline p=3 C^2, n=64 (N=274,625, nnz=86,938
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fine_matrix_pass_fp64_3d_p3_n64.md")
 STREAM_SUMMARY = os.path.join(ROOT, "profiles", "staged_mixed_passes_3d_p3_n64.md")
 KERNEL_NAMES = ["k_spmv_pq<8> (q = K p)", "k_resid<8> (down-sweep residual)", "k_up0<8> (up-sweep smoothing)"]
-# staged mixed-precision passes (k_stream, run-encoded finest matrix; default matrix_format 2)
-MIXED_KERNEL_NAMES = ["k_stream<EpiPQ, f32> (q = K p)", "k_stream<EpiResid, bf16> (down-sweep residual)",
-                      "k_stream<EpiUp0, bf16> (up-sweep smoothing)"]
+# staged mixed-precision passes of the run-encoded finest matrix (matrix_format 2), by the
+# layout the library chose (amg_info.staged_passes): 2 = sliced slabs with a lane per row
+# (k_sell), 1 = slabs with a lane per run (k_stream)
+MIXED_KERNEL_NAMES = {
+    2: ["k_sell<7, f32, EpiPQ> (q = K p)", "k_sell<7, bf16, EpiResid> (down-sweep residual)",
+        "k_sell<7, bf16, EpiUp0> (up-sweep smoothing)"],
+    1: ["k_stream<EpiPQ, f32> (q = K p)", "k_stream<EpiResid, bf16> (down-sweep residual)",
+        "k_stream<EpiUp0, bf16> (up-sweep smoothing)"],
+    0: ["k_spmv_pq<8,f32> (q = K p)", "k_resid<8,bf16> (down-sweep residual)", "k_up0<8,bf16> (up-sweep smoothing)"],
+}
+STAGED_SOURCES = {2: ("sell_kernels.cu", "stream_common.cuh"), 1: ("stream_kernels.cu", "stream_common.cuh")}
 
 
 def parse():
@@ -641,9 +649,8 @@ def run_ours(args):
             m_ms = max_over_ranks(dist, m0.elapsed_time(m1)) / args.steps
             err = float(torch.linalg.norm(mu - ref_u) / torch.linalg.norm(ref_u))
             mavg = mms / np.maximum(mcnt, 1)
-            mnames = MIXED_KERNEL_NAMES if args.matrix_format == 2 else [
-                "k_spmv_pq<8,f32> (q = K p)", "k_resid<8,bf16> (down-sweep residual)",
-                "k_up0<8,bf16> (up-sweep smoothing)"]
+            mkind = int(minfo.staged_passes)
+            mnames = MIXED_KERNEL_NAMES[mkind]
             mk = {name: {"bytes_per_launch": mkt[2][q], "avg_ms": mavg[q], "launches": int(mcnt[q]),
                          "achieved_gbs": mkt[2][q] / (mavg[q] * 1e-3) / 1e9 if mavg[q] > 0 else None}
                   for q, name in enumerate(mnames)}
@@ -657,7 +664,12 @@ def run_ours(args):
                                   "unit": "GB/s", "traffic": None,
                                   "tkey": ["pq", "resid", "up0"][mnames.index(mdom)],
                                   "bytes_per_launch": mk[mdom]["bytes_per_launch"],
-                                  "avg_launch_ms": mk[mdom]["avg_ms"], "all": mk}}
+                                  "avg_launch_ms": mk[mdom]["avg_ms"], "all": mk},
+                     "staged_passes": {"kind": ["row-group kernels", "slabs, lane per run",
+                                                "sliced slabs, lane per row"][mkind],
+                                       "value_slots": int(minfo.staged_slots),
+                                       "ring_buffers_bf16_fp32": [int(x) for x in minfo.staged_buffers],
+                                       "window_bytes": int(minfo.staged_window_bytes)}}
 
         # learned damping on top of mixed precision: the network is trained
         # (untimed) on small hierarchies of the same family, then each timed
@@ -716,8 +728,9 @@ def run_ours(args):
     if mixed is not None:
         mixed["roofline"]["peak"] = peak
         mixed["roofline"]["frac"] = (mixed["roofline"]["achieved"] or 0.0) / peak
-        st = committed_traffic(STREAM_SUMMARY, ("stream_kernels.cu",))
-        if st and "k_stream" in mixed["roofline"]["kernel"]:
+        kind = next((k for k, v in MIXED_KERNEL_NAMES.items() if mixed["roofline"]["kernel"] in v), 0)
+        st = committed_traffic(STREAM_SUMMARY, STAGED_SOURCES[kind]) if kind in STAGED_SOURCES else None
+        if st:
             mixed["roofline"]["traffic"] = st.get(mixed["roofline"]["tkey"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, it, args.rtol)

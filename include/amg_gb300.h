@@ -124,6 +124,8 @@ typedef struct {
                               kernels, 1 = staged slabs with a lane per run, 2 = staged sliced
                               slabs with a lane per row (matrix_format 2) */
     int64_t staged_slots;  /* value slots of the sliced slabs (padding included), 0 if unused */
+    int32_t staged_buffers[2]; /* copy-ring buffers of the staged passes: [0] BF16 values, [1] FP32 */
+    int32_t staged_window_bytes; /* largest per-block vector window of the staged passes */
 } amg_info;
 
 typedef struct amg_hierarchy amg_hierarchy;

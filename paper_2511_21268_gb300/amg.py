@@ -55,7 +55,8 @@ class AmgInfo(ctypes.Structure):
                 ("final_relres", ctypes.c_double), ("vcycle_bytes", ctypes.c_double),
                 ("iter_bytes", ctypes.c_double), ("match_rounds", ctypes.c_int32 * AMG_MAX_LEVELS),
                 ("setup_phase_ms", ctypes.c_double * 12), ("level_format", ctypes.c_int32 * AMG_MAX_LEVELS),
-                ("staged_passes", ctypes.c_int32), ("staged_slots", ctypes.c_int64)]
+                ("staged_passes", ctypes.c_int32), ("staged_slots", ctypes.c_int64),
+                ("staged_buffers", ctypes.c_int32 * 2), ("staged_window_bytes", ctypes.c_int32)]
 
 
 class AmgError(RuntimeError):

@@ -579,6 +579,9 @@ void fill_info(amg_hierarchy* h) {
     }
     I.staged_passes = h->stream;
     I.staged_slots = h->stream == 2 ? h->sell_slots * h->sell_lm * 32 : 0;
+    I.staged_buffers[0] = h->stream ? h->stream_nbuf[0] : 0;
+    I.staged_buffers[1] = h->stream ? h->stream_nbuf[1] : 0;
+    I.staged_window_bytes = h->stream ? h->stream_xbytes : 0;
     I.opc = tot / (double)h->lev[0].A.nnz;
     // algorithmic bytes: one matrix pass = nnz (value + 4) + (n + 1) 8 + x read + y write
     // (value and vector sizes of the V-cycle precision: 8 / 8 in FP64, 4 / 4 in

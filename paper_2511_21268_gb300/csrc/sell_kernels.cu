@@ -51,13 +51,14 @@ namespace {
 constexpr int kSlab = 32;                                   // rows per slab (one per lane)
 constexpr uint32_t kSegBytes = kSlab * 8;                   // one staged epilogue segment
 constexpr uint32_t kPartBytes = kStreamWarps * kSlab * 4;   // partial row sums of the 16 warps
-constexpr uint32_t kSellCtl = 128;                          // barriers and control words
+constexpr int kSellBuf = 6;                                 // largest ring
+constexpr uint32_t kSellCtl = 256;                          // barriers and control words
 
 struct SellShape {
     uint32_t xbytes;  // vector window bytes
     uint32_t vbytes;  // value area bytes per buffer (largest slab)
     uint32_t rbytes;  // start-column area bytes per buffer
-    int nbuf;         // buffers in the ring (2..kMaxBuf)
+    int nbuf;         // buffers in the ring (2..kSellBuf)
 };
 
 __host__ __device__ inline uint32_t sell_buffer_bytes(SellShape sh) {
@@ -115,12 +116,13 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     const uint32_t bufstride = sell_buffer_bytes(shape);
     const uint32_t o_rs = shape.vbytes, o_seg = o_rs + shape.rbytes, o_part = o_seg + kMaxVec * kSegBytes;
     unsigned char* ctl = ring + nbuf * bufstride;
-    // [0] window, [1 + j] full[j], [1 + kMaxBuf + j] empty[j], [1 + 2 kMaxBuf + j] partials[j]
+    // [0] window, [1 + j] full[j], [1 + kSellBuf + j] empty[j], [1 + 2 kSellBuf + j] partials[j]
     uint64_t* bars = reinterpret_cast<uint64_t*>(ctl);
-    constexpr int kBarBytes = 8 * (1 + 3 * kMaxBuf);
+    constexpr int kBarBytes = 8 * (1 + 3 * kSellBuf);
+    static_assert(kBarBytes + 4 * kSellBuf + 8 <= (int)kSellCtl, "control area");
     int* rsl = reinterpret_cast<int*>(ctl + kBarBytes);                                 // run slots of buffer j
-    volatile int* ctrl = reinterpret_cast<int*>(ctl + kBarBytes + 4 * kMaxBuf);        // 0 = go on, 1 = give up
-    int* xlo = reinterpret_cast<int*>(ctl + kBarBytes + 4 * kMaxBuf + 4);             // first window entry
+    volatile int* ctrl = reinterpret_cast<int*>(ctl + kBarBytes + 4 * kSellBuf);       // 0 = go on, 1 = give up
+    int* xlo = reinterpret_cast<int*>(ctl + kBarBytes + 4 * kSellBuf + 4);            // first window entry
     __shared__ double red[kStreamWarps + 1];
 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -128,12 +130,12 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     const int s1 = (int)((int64_t)(blockIdx.x + 1) * nsl / gridDim.x);
     const uint32_t bar_win = smem_addr(&bars[0]);
     auto bar_full = [&](int j) { return smem_addr(&bars[1 + j]); };
-    auto bar_empty = [&](int j) { return smem_addr(&bars[1 + kMaxBuf + j]); };
-    auto bar_part = [&](int j) { return smem_addr(&bars[1 + 2 * kMaxBuf + j]); };
+    auto bar_empty = [&](int j) { return smem_addr(&bars[1 + kSellBuf + j]); };
+    auto bar_part = [&](int j) { return smem_addr(&bars[1 + 2 * kSellBuf + j]); };
 
     if (threadIdx.x == 0) {
         mbar_init(bar_win, 1);
-        for (int j = 0; j < kMaxBuf; j++) {
+        for (int j = 0; j < kSellBuf; j++) {
             mbar_init(bar_full(j), 1);
             mbar_init(bar_empty(j), kStreamWarps);
             mbar_init(bar_part(j), kStreamWarps);
@@ -149,73 +151,83 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     double acc1 = 0.0, acc2 = 0.0;
     if (wid == kStreamWarps) {
         // ------------------------------------------------------------ producer
-        if (lane == 0 && s0 < s1) {
-            const int2 w = win[blockIdx.x];
-            const int lo = w.x & ~3;
-            const uint32_t bytes = align16((uint32_t)(w.y + 1 - lo) * 4u);
-            mbar_expect_tx(bar_win, bytes);
-            bulk_g2s(smem_addr(smem), xg + lo, bytes, bar_win);
-            int last_use[kMaxBuf] = {-1, -1, -1};
-            for (int k = s0; k < s1; k++) {
-                if (*ctrl) break;
-                const int u = (k - s0) / nbuf, j = (k - s0) % nbuf;
-                if (u > 0 && !mbar_wait_bounded(bar_empty(j), (uint32_t)(u - 1) & 1u)) {
-                    *ctrl = 1;
-                    break;
-                }
-                const int o0 = soff[k];
-                const int R = soff[k + 1] - o0;
-                rsl[j] = R;
-                const int a = k * kSlab;
-                const uint32_t cnt = (uint32_t)min(kSlab, n - a);
-                const uint32_t vb = (uint32_t)R * (uint32_t)(LM * kSlab * sizeof(V));
-                const uint32_t rb = (uint32_t)R * (uint32_t)(kSlab * 4);
-                uint32_t tx = vb + rb;
-#pragma unroll
-                for (int v = 0; v < kMaxVec; v++)
-                    if (v < epi.nvec) tx += align16(cnt * (uint32_t)epi.es[v]);
-                unsigned char* bv = ring + j * bufstride;
-                const uint32_t bar = bar_full(j);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(bar, tx);
-                if (R > 0) {
-                    bulk_g2s(smem_addr(bv), val + (int64_t)o0 * (LM * kSlab), vb, bar);
-                    bulk_g2s(smem_addr(bv + o_rs), rs + (int64_t)o0 * kSlab, rb, bar);
-                }
-#pragma unroll
-                for (int v = 0; v < kMaxVec; v++)
-                    if (v < epi.nvec)
-                        bulk_g2s(smem_addr(bv + o_seg + v * kSegBytes),
-                                 reinterpret_cast<const unsigned char*>(epi.vec[v]) + (int64_t)a * epi.es[v],
-                                 align16(cnt * (uint32_t)epi.es[v]), bar);
-                if (j == 0) last_use[0] = u;
-                else if (j == 1) last_use[1] = u;
-                else last_use[2] = u;
+        // The whole warp loads the slot offsets of the next 32 slabs at once
+        // (one coalesced load instead of a dependent load per slab); lane 0
+        // waits for buffers and issues the copies.
+        if (s0 < s1) {
+            int last_use = -1;  // last slab issued (lane 0)
+            if (lane == 0) {
+                const int2 w = win[blockIdx.x];
+                const int lo = w.x & ~3;
+                const uint32_t bytes = align16((uint32_t)(w.y + 1 - lo) * 4u);
+                mbar_expect_tx(bar_win, bytes);
+                bulk_g2s(smem_addr(smem), xg + lo, bytes, bar_win);
             }
-            if (*ctrl) {  // drain copies that may still be in flight (bounded), keeping smem alive
+            bool go = true;
+            for (int kb = s0; kb < s1 && go; kb += 32) {
+                const int ofs = soff[min(kb + lane, s1)];
+                const int ofs_end = soff[min(kb + 32, s1)];
+                const int cnt_k = min(32, s1 - kb);
+                for (int t = 0; t < cnt_k; t++) {
+                    const int o0 = __shfl_sync(FULL, ofs, t);
+                    const int o1n = __shfl_sync(FULL, ofs, (t + 1) & 31);
+                    const int o1 = t == 31 ? ofs_end : o1n;
+                    if (lane == 0) {
+                        const int k = kb + t;
+                        const int u = (k - s0) / nbuf, j = (k - s0) % nbuf;
+                        if (*ctrl || (u > 0 && !mbar_wait_bounded(bar_empty(j), (uint32_t)(u - 1) & 1u))) {
+                            *ctrl = 1;
+                            go = false;
+                        } else {
+                            const int R = o1 - o0;
+                            rsl[j] = R;
+                            const int a = k * kSlab;
+                            const uint32_t cnt = (uint32_t)min(kSlab, n - a);
+                            const uint32_t vb = (uint32_t)R * (uint32_t)(LM * kSlab * sizeof(V));
+                            const uint32_t rb = (uint32_t)R * (uint32_t)(kSlab * 4);
+                            uint32_t tx = vb + rb;
+#pragma unroll
+                            for (int v = 0; v < kMaxVec; v++)
+                                if (v < epi.nvec) tx += align16(cnt * (uint32_t)epi.es[v]);
+                            unsigned char* bv = ring + j * bufstride;
+                            const uint32_t bar = bar_full(j);
+                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                            mbar_expect_tx(bar, tx);
+                            if (R > 0) {
+                                bulk_g2s(smem_addr(bv), val + (int64_t)o0 * (LM * kSlab), vb, bar);
+                                bulk_g2s(smem_addr(bv + o_rs), rs + (int64_t)o0 * kSlab, rb, bar);
+                            }
+#pragma unroll
+                            for (int v = 0; v < kMaxVec; v++)
+                                if (v < epi.nvec)
+                                    bulk_g2s(smem_addr(bv + o_seg + v * kSegBytes),
+                                             reinterpret_cast<const unsigned char*>(epi.vec[v]) +
+                                                 (int64_t)a * epi.es[v],
+                                             align16(cnt * (uint32_t)epi.es[v]), bar);
+                            last_use = k;
+                        }
+                    }
+                    go = __shfl_sync(FULL, go, 0);
+                    if (!go) break;
+                }
+            }
+            if (lane == 0 && *ctrl) {  // drain copies that may still be in flight (bounded), keeping smem alive
                 mbar_wait_bounded(bar_win, 0u);
-                if (last_use[0] >= 0) mbar_wait_bounded(bar_full(0), (uint32_t)last_use[0] & 1u);
-                if (last_use[1] >= 0) mbar_wait_bounded(bar_full(1), (uint32_t)last_use[1] & 1u);
-                if (last_use[2] >= 0) mbar_wait_bounded(bar_full(2), (uint32_t)last_use[2] & 1u);
+                for (int k = max(s0, last_use - nbuf + 1); k <= last_use; k++)
+                    mbar_wait_bounded(bar_full((k - s0) % nbuf), (uint32_t)((k - s0) / nbuf) & 1u);
             }
         }
     } else {
         // ------------------------------------------------------------ consumers
         bool ok = true;
-        if (s0 < s1) {
-            if (lane == 0) ok = mbar_wait_bounded(bar_win, 0u);
-            ok = __shfl_sync(FULL, ok, 0);
-            __syncwarp();
-        }
+        if (s0 < s1) ok = __all_sync(FULL, mbar_wait_bounded(bar_win, 0u));
         const float* xs = xw - *xlo;  // xs[c] = vector entry c (inside the window)
         // shared address of vector entry 0 (32-bit wrap-around: entry c at xbase + 4 c)
         const uint32_t xbase = smem_addr(xw) - 4u * (uint32_t)(*xlo);
         for (int k = s0; k < s1 && ok; k++) {
             const int u = (k - s0) / nbuf, j = (k - s0) % nbuf;
-            if (lane == 0) ok = !*ctrl && mbar_wait_bounded(bar_full(j), (uint32_t)u & 1u);
-            ok = __shfl_sync(FULL, ok, 0);
+            ok = __all_sync(FULL, !*ctrl && mbar_wait_bounded(bar_full(j), (uint32_t)u & 1u));
             if (!ok) break;
-            __syncwarp();
             unsigned char* bv = ring + j * bufstride;
             const int R = rsl[j];
             const int e = (k - s0) % kStreamWarps;              // the slab's epilogue warp ...
@@ -236,10 +248,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                 if (lane == 0) mbar_arrive(bar_empty(j));  // done with buffer j
                 continue;
             }
-            if (lane == 0) ok = mbar_wait_bounded(bar_part(j), (uint32_t)u & 1u);
-            ok = __shfl_sync(FULL, ok, 0);
+            ok = __all_sync(FULL, mbar_wait_bounded(bar_part(j), (uint32_t)u & 1u));
             if (!ok) break;
-            __syncwarp();
             float s = 0.f;
 #pragma unroll
             for (int w = 0; w < kStreamWarps; w++) s += part[w * kSlab + lane];  // warp order
@@ -493,7 +503,7 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
     int nb[2] = {0, 0};
     for (int q = 0; q < 2; q++) {
         const uint32_t vb = (uint32_t)(q == 0 ? vb16 : vb32);
-        for (int k = kMaxBuf; k >= 2 && !nb[q]; k--) {
+        for (int k = kSellBuf; k >= 2 && !nb[q]; k--) {
             const SellShape sh{(uint32_t)xw, vb, (uint32_t)rb, k};
             if (sell_smem_bytes(sh) + 256u <= (uint32_t)optin) nb[q] = k;  // 256: static shared memory
         }

@@ -53,14 +53,31 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  : "memory");
 }
 
-// Bounded wait for phase `parity` of the mbarrier (one thread); backs off
-// between polls so that waiting warps leave the issue slots to the others.
+// try_wait that may suspend the thread for up to `ns` nanoseconds; the
+// hardware resumes it when the phase completes.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint32_t bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of the mbarrier, suspending in the
+// barrier between polls (the hardware resumes the waiter as soon as the
+// phase completes; a sleep between polls instead cost microseconds per
+// wait); every lane of a warp may call it together.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (int it = 0; it < kWaitIters; it++) {
-        __nanosleep(32);
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_suspend(bar, parity, 20000u)) return true;
         if (clock64() - t0 > kWaitCycles) break;
     }
     return false;

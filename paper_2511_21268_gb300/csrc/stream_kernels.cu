@@ -234,17 +234,13 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     } else {
         // ------------------------------------------------------------ consumers
         bool ok = true;
-        if (s0 < s1) {
-            if (lane == 0) ok = mbar_wait_bounded(bar_win, 0u);
-            ok = __shfl_sync(FULL, ok, 0);
-        }
+        if (s0 < s1) ok = __all_sync(FULL, mbar_wait_bounded(bar_win, 0u));
         const float* xs = xw - *xlo;  // xs[c] = vector entry c (inside the window)
         // shared address of vector entry 0 (32-bit wrap-around: entry c at xbase + 4 c)
         const uint32_t xbase = smem_addr(xw) - 4u * (uint32_t)(*xlo);
         for (int k = s0; k < s1 && ok; k++) {
             const int u = (k - s0) / nbuf, j = (k - s0) % nbuf;
-            if (lane == 0) ok = !*ctrl && mbar_wait_bounded(bar_full(j), (uint32_t)u & 1u);
-            ok = __shfl_sync(FULL, ok, 0);
+            ok = __all_sync(FULL, !*ctrl && mbar_wait_bounded(bar_full(j), (uint32_t)u & 1u));
             if (!ok) break;
             const unsigned char* bv = ring + j * bufstride;
             const V* sv = reinterpret_cast<const V*>(bv);

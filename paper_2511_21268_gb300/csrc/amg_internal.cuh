@@ -4,6 +4,8 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <utility>
 #include <stdint.h>
 
 #include <vector>
@@ -190,7 +192,7 @@ struct amg_hierarchy {
     int sell_nsl = 0;                    // slabs
     int64_t sell_slots = 0;              // run slots in all
     int32_t* sell_soff = nullptr;        // nsl + 1: first run slot of each slab
-    int32_t* sell_rs = nullptr;          // start column of each (slot, lane)
+    uint16_t* sell_rs = nullptr;         // window offset of the start of each (slot, lane)
     float* sell_v32 = nullptr;           // FP32 values, slot-major, lane-minor
     __nv_bfloat16* sell_v16 = nullptr;   // BF16 values (BF16 finest values only)
     int sell_vbytes[2] = {};             // value area per buffer: [0] BF16, [1] FP32
@@ -343,6 +345,37 @@ namespace amg {
 long long note_launch();
 }
 #define AMG_GRID(g) (amg::note_launch(), (g))
+
+namespace amg {
+// Programmatic dependent launch.  A kernel launched with launch_pdl starts
+// with pdl_entry(), which waits until the previous kernel of the stream has
+// completed and its memory is visible, before any other instruction touches
+// memory; the launch itself (block scheduling) overlaps the predecessor's
+// completion.  Kernels do not trigger their dependents early: blocks of
+// later kernels parked on the SMs slowed the solve (the staged passes need
+// a whole SM's shared memory).  Launched without the attribute the wait
+// does nothing.
+__device__ __forceinline__ void pdl_entry() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch `kernel` (whose first statement is pdl_entry()) allowing
+// programmatic stream serialization with the previous kernel.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+    note_launch();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+}  // namespace amg
 
 #define AMG_TRY(expr)                          \
     do {                                       \

@@ -163,6 +163,7 @@ __device__ __forceinline__ void block_partial(double tv, double* sh, double* out
 // ----------------------------------------------------------------- kernels
 template <int RPW, typename M>
 __global__ void __launch_bounds__(kBlock) k_spmv(int n, M mat, const double* __restrict__ x, double* y) {
+    pdl_entry();
     ROWGROUP_PROLOGUE(double)
     const double s = group_rows<RPW, double>(mat, x, row0, n, lane, tiles[wid]);
     if (owner) y[myrow] = s;
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(kBlock) k_residual0(int n, M mat, const double
                                                        const double* __restrict__ F,
                                                        const X0* __restrict__ invd, double* r, X0* x0,
                                                        double* part_rr, double* part_ff, const SolveState* gate) {
+    pdl_entry();
     // grid-stride over row groups (a small grid: the gated launch of every
     // mixed-precision iteration returns at once unless a replacement is due)
     if (gate && (gate->done || !gate->replace_now)) return;
@@ -208,6 +210,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_pq(int n, M mat, const PX* __re
                                                      const double* __restrict__ p,
                                                      const double* __restrict__ r, double* q, double* part_pq,
                                                      double* part_pr, int flexible, const SolveState* st) {
+    pdl_entry();
     DONE_GUARD(st);
     ROWGROUP_PROLOGUE(A)
     __shared__ double sh[kWarpsPerBlock];
@@ -228,6 +231,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_pq(int n, M mat, const PX* __re
 template <int RPW, typename A, typename M, typename FT, typename XT>
 __global__ void __launch_bounds__(kBlock) k_resid(int n, M mat, const FT* __restrict__ f, const XT* __restrict__ x,
                                                    A* rbuf, const SolveState* st) {
+    pdl_entry();
     DONE_GUARD(st);
     ROWGROUP_PROLOGUE(A)
     const A s = group_rows<RPW, A>(mat, x, row0, n, lane, tiles[wid]);
@@ -238,6 +242,7 @@ __global__ void __launch_bounds__(kBlock) k_resid(int n, M mat, const FT* __rest
 template <int RPW, typename A, typename M, typename FT>
 __global__ void __launch_bounds__(kBlock) k_sweep(int n, M mat, const FT* __restrict__ f, const A* __restrict__ x,
                                                    const A* __restrict__ invd, A* t, const SolveState* st) {
+    pdl_entry();
     DONE_GUARD(st);
     ROWGROUP_PROLOGUE(A)
     const A s = group_rows<RPW, A>(mat, x, row0, n, lane, tiles[wid]);
@@ -251,6 +256,7 @@ __global__ void __launch_bounds__(kBlock) k_up(int n, M mat, const A* __restrict
                                                 const A* __restrict__ invd,
                                                 const int32_t* __restrict__ mptr, const int32_t* __restrict__ midx,
                                                 const double* __restrict__ pvalf, A* xf, const SolveState* st) {
+    pdl_entry();
     DONE_GUARD(st);
     ROWGROUP_PROLOGUE(A)
     const A s = group_rows<RPW, A>(mat, x, row0, n, lane, tiles[wid]);
@@ -270,6 +276,7 @@ __global__ void __launch_bounds__(kBlock) k_up0(int n, M mat, const double* __re
                                                  const A* __restrict__ x, const A* __restrict__ invd, double* z,
                                                  const double* __restrict__ q, double* part_rz, double* part_zq,
                                                  int flexible, const SolveState* st) {
+    pdl_entry();
     DONE_GUARD(st);
     ROWGROUP_PROLOGUE(A)
     __shared__ double sh[kWarpsPerBlock];

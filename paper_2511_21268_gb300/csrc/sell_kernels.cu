@@ -8,10 +8,12 @@
 // 64 lane slots).  Here the finest matrix is re-laid out once, at setup, in
 // slabs of 32 consecutive rows:
 //   * slab k has Rs[k] = the largest run count of its rows run slots; slot r
-//     of lane t (row 32 k + t) holds the start column of that row's run r
-//     and LM value slots (LM = the largest run length, rounded up to odd),
-//     stored slot-major and lane-minor: value o of slot r of lane t at
-//     ((soff[k] + r) LM + o) 32 + t, start column at (soff[k] + r) 32 + t;
+//     of lane t (row 32 k + t) holds the start of that row's run r and LM
+//     value slots (LM = the largest run length, rounded up to odd), stored
+//     slot-major and lane-minor: value o of slot r of lane t at
+//     ((soff[k] + r) LM + o) 32 + t, start at (soff[k] + r) 32 + t; the start
+//     is kept as a 16-bit offset into the vector window of the grid block
+//     that owns the slab (the window always fits in 64 K entries);
 //   * rows with fewer runs, shorter runs, or no row at all (the last slab)
 //     are padded with zero values whose columns stay inside the matrix; a run
 //     that would reach past the last column is shifted left, its values
@@ -82,6 +84,12 @@ __device__ __forceinline__ float lds_val_at(uint32_t a, const __nv_bfloat16*) {
     return __uint_as_float((uint32_t)u << 16);
 }
 
+__device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
+    unsigned short u;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(u) : "r"(a));
+    return (uint32_t)u;
+}
+
 // Value slots O .. LM-1 of one run slot: value o at va + o 32 sizeof(V),
 // vector entry at xa + 4 o; two accumulators halve the FMA chain.
 template <int O, int LM, typename V>
@@ -105,9 +113,10 @@ struct SlotDot<LM, LM, V> {
 // (the vectors are padded for the last slab).
 template <int LM, typename V, typename Epi>
 __global__ void __launch_bounds__(kStreamThreads, 1)
-    k_sell(int n, int nsl, const int32_t* __restrict__ soff, const V* __restrict__ val, const int32_t* __restrict__ rs,
+    k_sell(int n, int nsl, const int32_t* __restrict__ soff, const V* __restrict__ val, const uint16_t* __restrict__ rs,
            const float* __restrict__ xg, const int2* __restrict__ win, SellShape shape, Epi epi, double* part1,
            double* part2, SolveState* st) {
+    pdl_entry();
     if (st && st->done) return;
     extern __shared__ __align__(128) unsigned char smem[];
     const int nbuf = shape.nbuf;
@@ -184,7 +193,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                             const int a = k * kSlab;
                             const uint32_t cnt = (uint32_t)min(kSlab, n - a);
                             const uint32_t vb = (uint32_t)R * (uint32_t)(LM * kSlab * sizeof(V));
-                            const uint32_t rb = (uint32_t)R * (uint32_t)(kSlab * 4);
+                            const uint32_t rb = (uint32_t)R * (uint32_t)(kSlab * 2);
                             uint32_t tx = vb + rb;
 #pragma unroll
                             for (int v = 0; v < kMaxVec; v++)
@@ -221,9 +230,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         // ------------------------------------------------------------ consumers
         bool ok = true;
         if (s0 < s1) ok = __all_sync(FULL, mbar_wait_bounded(bar_win, 0u));
-        const float* xs = xw - *xlo;  // xs[c] = vector entry c (inside the window)
-        // shared address of vector entry 0 (32-bit wrap-around: entry c at xbase + 4 c)
-        const uint32_t xbase = smem_addr(xw) - 4u * (uint32_t)(*xlo);
+        const float* xs = xw - *xlo;        // xs[c] = vector entry c (inside the window)
+        const uint32_t xbase = smem_addr(xw);  // window offset q at xbase + 4 q
         for (int k = s0; k < s1 && ok; k++) {
             const int u = (k - s0) / nbuf, j = (k - s0) % nbuf;
             ok = __all_sync(FULL, !*ctrl && mbar_wait_bounded(bar_full(j), (uint32_t)u & 1u));
@@ -233,11 +241,11 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
             const int e = (k - s0) % kStreamWarps;              // the slab's epilogue warp ...
             const int r0 = (wid - e - 1) & (kStreamWarps - 1);  // ... takes the last slot offset
             const uint32_t va0 = smem_addr(bv) + (uint32_t)sizeof(V) * (uint32_t)lane;
-            const uint32_t ra0 = smem_addr(bv + o_rs) + 4u * (uint32_t)lane;
+            const uint32_t ra0 = smem_addr(bv + o_rs) + 2u * (uint32_t)lane;
             float a0 = 0.f, a1 = 0.f;
 #pragma unroll 1
             for (int r = r0; r < R; r += kStreamWarps) {
-                const uint32_t xa = xbase + 4u * (uint32_t)lds_s32(ra0 + (uint32_t)r * (uint32_t)(kSlab * 4));
+                const uint32_t xa = xbase + 4u * lds_u16(ra0 + (uint32_t)r * (uint32_t)(kSlab * 2));
                 SlotDot<0, LM, V>::run(va0 + (uint32_t)r * (uint32_t)(LM * kSlab * sizeof(V)), xa, a0, a1);
             }
             float* part = reinterpret_cast<float*>(bv + o_part);
@@ -276,6 +284,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
 // largest run length of the matrix (atomic max); a warp per slab.
 __global__ void k_sell_slots(int n, int nsl, const int32_t* __restrict__ rptr, const uint8_t* __restrict__ rlen,
                              int32_t* slots, int* lmax) {
+    pdl_entry();
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nsl; k += nw) {
@@ -297,52 +306,30 @@ __global__ void k_sell_slots(int n, int nsl, const int32_t* __restrict__ rptr, c
     }
 }
 
-// Fill the sliced copy (a warp per slab, a lane per row): start columns,
-// FP32 values and (if o16) BF16 values; swin[k] = the smallest and largest
-// column slab k reads.  A run of row i (start c, L entries) goes to slot r
-// at start c' = min(c, n - LM), its value q at offset q + c - c'; empty
-// slots (r >= the row's runs, or no row) read LM zeros from the slab's
-// first start column.
-__global__ void k_sell_fill(int n, int nsl, int LM, const int64_t* __restrict__ rp, const int32_t* __restrict__ rptr,
-                            const uint8_t* __restrict__ rlen, const int32_t* __restrict__ rst,
-                            const int32_t* __restrict__ soff, const float* __restrict__ v32,
-                            const __nv_bfloat16* __restrict__ v16, float* o32, __nv_bfloat16* o16, int32_t* ors,
-                            int2* swin) {
+// Start column of slot r of row i in the sliced layout: the run's start c
+// shifted left to min(c, n - LM) (its values move right by the shift), or
+// the slab's padding column for an empty slot.
+__device__ __forceinline__ int slot_start(int c0, int n, int LM) { return min(c0, n - LM); }
+
+// Smallest and largest column each slab reads (a warp per slab, a lane per
+// row): swin[k].
+__global__ void k_sell_span(int n, int nsl, int LM, const int32_t* __restrict__ rptr,
+                            const int32_t* __restrict__ rst, const int32_t* __restrict__ soff, int2* swin) {
+    pdl_entry();
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nsl; k += nw) {
         const int i = k * kSlab + lane;
-        const int o0 = soff[k], Rs = soff[k + 1] - o0;
-        int r0 = 0, Ri = 0, Li = 0;
-        int64_t b = 0;
-        if (i < n) {
-            r0 = rptr[i];
-            Ri = rptr[i + 1] - r0;
-            Li = rlen[i];
-            b = rp[i];
-        }
+        const int Rs = soff[k + 1] - soff[k];
         const int f0 = rptr[k * kSlab];
-        const int cpad = rptr[k * kSlab + 1] > f0 ? max(0, min(rst[f0], n - LM)) : 0;
-        int lo = INT32_MAX, hi = -1;
-        for (int r = 0; r < Rs; r++) {
-            int c = cpad, sh = 0;
-            const bool has = r < Ri;
-            if (has) {
-                const int c0 = rst[r0 + r];
-                c = min(c0, n - LM);
-                sh = c0 - c;
-            }
-            const int64_t slot = (int64_t)o0 + r;
-            ors[slot * kSlab + lane] = c;
-            lo = min(lo, c);
-            hi = max(hi, c + LM - 1);
-            for (int o = 0; o < LM; o++) {
-                const int q = o - sh;
-                const bool hv = has && q >= 0 && q < Li;
-                const int64_t dst = (slot * LM + o) * kSlab + lane;
-                const int64_t src = b + (int64_t)r * Li + q;
-                o32[dst] = hv ? v32[src] : 0.f;
-                if (o16) o16[dst] = hv ? v16[src] : __float2bfloat16_rn(0.f);
+        const int cpad = rptr[k * kSlab + 1] > f0 ? max(0, slot_start(rst[f0], n, LM)) : 0;
+        int lo = cpad, hi = cpad + LM - 1;
+        if (i < n) {
+            const int r0 = rptr[i], Ri = rptr[i + 1] - r0;
+            for (int r = 0; r < Ri; r++) {
+                const int c = slot_start(rst[r0 + r], n, LM);
+                lo = min(lo, c);
+                hi = max(hi, c + LM - 1);
             }
         }
 #pragma unroll
@@ -354,8 +341,61 @@ __global__ void k_sell_fill(int n, int nsl, int LM, const int64_t* __restrict__ 
     }
 }
 
+// Fill the sliced copy (a warp per slab, a lane per row): FP32 values,
+// BF16 values (if o16) and the window offsets of the slot starts (the
+// window of the block b = ((k + 1) G - 1) / nsl that owns slab k starts at
+// column win[b].x & ~3).  A run of row i (start c, L entries) goes to slot r
+// at start c' = min(c, n - LM), its value q at offset q + c - c'; empty
+// slots (r >= the row's runs, or no row) read LM zeros from the slab's
+// padding column (its first row's first start).
+__global__ void k_sell_fill(int n, int nsl, int G, int LM, const int64_t* __restrict__ rp,
+                            const int32_t* __restrict__ rptr, const uint8_t* __restrict__ rlen,
+                            const int32_t* __restrict__ rst, const int32_t* __restrict__ soff,
+                            const int2* __restrict__ win, const float* __restrict__ v32,
+                            const __nv_bfloat16* __restrict__ v16, float* o32, __nv_bfloat16* o16, uint16_t* ors) {
+    pdl_entry();
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nsl; k += nw) {
+        const int i = k * kSlab + lane;
+        const int o0 = soff[k], Rs = soff[k + 1] - o0;
+        const int b = (int)(((int64_t)(k + 1) * G - 1) / nsl);
+        const int lo4 = win[b].x & ~3;
+        int r0 = 0, Ri = 0, Li = 0;
+        int64_t e0 = 0;
+        if (i < n) {
+            r0 = rptr[i];
+            Ri = rptr[i + 1] - r0;
+            Li = rlen[i];
+            e0 = rp[i];
+        }
+        const int f0 = rptr[k * kSlab];
+        const int cpad = rptr[k * kSlab + 1] > f0 ? max(0, slot_start(rst[f0], n, LM)) : 0;
+        for (int r = 0; r < Rs; r++) {
+            int c = cpad, sh = 0;
+            const bool has = r < Ri;
+            if (has) {
+                const int c0 = rst[r0 + r];
+                c = slot_start(c0, n, LM);
+                sh = c0 - c;
+            }
+            const int64_t slot = (int64_t)o0 + r;
+            ors[slot * kSlab + lane] = (uint16_t)(c - lo4);
+            for (int o = 0; o < LM; o++) {
+                const int q = o - sh;
+                const bool hv = has && q >= 0 && q < Li;
+                const int64_t dst = (slot * LM + o) * kSlab + lane;
+                const int64_t src = e0 + (int64_t)r * Li + q;
+                o32[dst] = hv ? v32[src] : 0.f;
+                if (o16) o16[dst] = hv ? v16[src] : __float2bfloat16_rn(0.f);
+            }
+        }
+    }
+}
+
 // Window of each grid block: smallest and largest column over its slabs.
 __global__ void k_sell_window(int nsl, int G, const int2* __restrict__ swin, int2* win) {
+    pdl_entry();
     __shared__ int slo[256], shi[256];
     const int b = blockIdx.x;
     const int k0 = (int)((int64_t)b * nsl / G), k1 = (int)((int64_t)(b + 1) * nsl / G);
@@ -399,7 +439,7 @@ template <int LM, typename V, typename Epi>
 cudaError_t sell_launch_lm(amg_hierarchy* h, int q, const V* val, const float* x, const Epi& epi, double* p1,
                            double* p2, cudaStream_t s) {
     const SellShape sh = sell_shape(h, q);
-    k_sell<LM, V, Epi><<<AMG_GRID(h->stream_blocks), kStreamThreads, sell_smem_bytes(sh), s>>>(
+    launch_pdl(k_sell<LM, V, Epi>, h->stream_blocks, kStreamThreads, sell_smem_bytes(sh), s,
         h->lev[0].A.n, h->sell_nsl, h->sell_soff, val, h->sell_rs, x, reinterpret_cast<const int2*>(h->stream_win),
         sh, epi, p1, p2, h->st);
     return cudaGetLastError();
@@ -436,7 +476,7 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
     h->allocs.push_back(slots);
     const int gw = std::min((nsl + 7) / 8, 8192);
     if (cudaMemsetAsync(scratch, 0, sizeof(int), h->s) != cudaSuccess) return AMG_ERR_CUDA;
-    k_sell_slots<<<AMG_GRID(gw), 256, 0, h->s>>>(n, nsl, F0.run_ptr, F0.run_len, slots, scratch);
+    launch_pdl(k_sell_slots, gw, 256, 0, h->s, n, nsl, F0.run_ptr, F0.run_len, slots, scratch);
     std::vector<int32_t> hs(nsl + 1);
     int lmax = 0;
     if (cudaMemcpyAsync(hs.data(), slots, sizeof(int32_t) * nsl, cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
@@ -459,7 +499,7 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
         return AMG_OK;
     // shared-memory shape
     const int64_t vb16 = (int64_t)rmax * LM * kSlab * 2, vb32 = (int64_t)rmax * LM * kSlab * 4;
-    const int64_t rb = (int64_t)rmax * kSlab * 4;
+    const int64_t rb = (int64_t)rmax * kSlab * 2;
     if (vb32 + rb > (1 << 20)) return AMG_OK;
     if (cudaMemcpyAsync(slots, hs.data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice, h->s) != cudaSuccess)
         return AMG_ERR_CUDA;
@@ -467,7 +507,7 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
     const bool with16 = F0.val16 != nullptr;
     float* o32 = nullptr;
     __nv_bfloat16* o16 = nullptr;
-    int32_t* ors = nullptr;
+    uint16_t* ors = nullptr;
     int2* swin = nullptr;
     int2* win = nullptr;
     const size_t nv = (size_t)total * LM * kSlab;
@@ -478,7 +518,7 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
             return AMG_ERR_NOMEM;
         h->allocs.push_back(o16);
     }
-    if (dev_alloc(reinterpret_cast<void**>(&ors), sizeof(int32_t) * (size_t)total * kSlab, h->s) != cudaSuccess)
+    if (dev_alloc(reinterpret_cast<void**>(&ors), sizeof(uint16_t) * (size_t)total * kSlab, h->s) != cudaSuccess)
         return AMG_ERR_NOMEM;
     h->allocs.push_back(ors);
     if (dev_alloc(reinterpret_cast<void**>(&swin), sizeof(int2) * nsl, h->s) != cudaSuccess) return AMG_ERR_NOMEM;
@@ -488,9 +528,8 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
     const void* arrays[] = {o32, o16, ors};
     for (const void* a : arrays)
         if (a && (reinterpret_cast<uintptr_t>(a) & 15)) return AMG_OK;
-    k_sell_fill<<<AMG_GRID(gw), 256, 0, h->s>>>(n, nsl, LM, F0.A.rowptr, F0.run_ptr, F0.run_len, F0.run_start, slots,
-                                                F0.val32, F0.val16, o32, o16, ors, swin);
-    k_sell_window<<<AMG_GRID(G), 256, 0, h->s>>>(nsl, G, swin, win);
+    launch_pdl(k_sell_span, gw, 256, 0, h->s, n, nsl, LM, F0.run_ptr, F0.run_start, slots, swin);
+    launch_pdl(k_sell_window, G, 256, 0, h->s, nsl, G, swin, win);
     std::vector<int2> hw(G);
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(hw.data(), win, sizeof(int2) * G, cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
@@ -499,7 +538,7 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
     int64_t xw = 16;
     for (int b = 0; b < G; b++)
         xw = std::max<int64_t>(xw, ((int64_t)(hw[b].y + 1 - (hw[b].x & ~3)) * 4 + 15) & ~(int64_t)15);
-    if (xw >= (1 << 20)) return AMG_OK;
+    if (xw > 4 * 65536) return AMG_OK;  // window offsets are 16-bit
     int nb[2] = {0, 0};
     for (int q = 0; q < 2; q++) {
         const uint32_t vb = (uint32_t)(q == 0 ? vb16 : vb32);
@@ -509,6 +548,9 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
         }
     }
     if (!nb[1] || (with16 && !nb[0])) return AMG_OK;
+    launch_pdl(k_sell_fill, gw, 256, 0, h->s, n, nsl, G, LM, F0.A.rowptr, F0.run_ptr, F0.run_len, F0.run_start,
+                                                slots, win, F0.val32, F0.val16, o32, o16, ors);
+    if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
     h->sell_lm = LM;
     h->sell_nsl = nsl;
     h->sell_soff = slots;

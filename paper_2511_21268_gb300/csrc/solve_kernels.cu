@@ -75,6 +75,7 @@ template <typename A>
 __global__ void k_restrict(int nc, const int32_t* __restrict__ mptr, const int32_t* __restrict__ midx,
                            const double* __restrict__ pval, const A* __restrict__ rbuf, A* fc, A* xc,
                            const A* __restrict__ invdc, const SolveState* st) {
+    pdl_entry();
     DONE_GUARD(st);
     for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
         A acc = A(0);
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse(int n, const double* __restri
                                                     const double* __restrict__ pvalf, XT* xf, double* z,
                                                     const double* __restrict__ q, double* part_rz, double* part_zq,
                                                     int flexible, const SolveState* st) {
+    pdl_entry();
     DONE_GUARD(st);
     __shared__ double sh[kWarpsPerBlock];
     const int lane = threadIdx.x & 31;
@@ -129,6 +131,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse(int n, const double* __restri
 // ------------------------------------------------------------ CG scalars
 __global__ void k_scal_init(const double* part_rr, const double* part_ff, int nb, double rtol, int itmax,
                             int repl_every, double* hist, SolveState* st) {
+    pdl_entry();
     // every field a later kernel reads is (re)set here
     __shared__ double sh[33];
     const double rr = sum_partials(part_rr, nb, sh);
@@ -158,6 +161,7 @@ __global__ void k_scal_init(const double* part_rr, const double* part_ff, int nb
 }
 
 __global__ void k_scal_alpha(const double* part_pq, const double* part_pr, int nb, int flexible, SolveState* st) {
+    pdl_entry();
     DONE_GUARD(st);
     __shared__ double sh[33];
     const double pq = sum_partials(part_pq, nb, sh);
@@ -177,6 +181,7 @@ __global__ void k_scal_alpha(const double* part_pq, const double* part_pr, int n
 // only declared on an FP64 true residual, so a replacement is requested
 // instead (also every repl_every iterations).
 __global__ void k_scal_conv(const double* part_rr, int nb, double* hist, int hist_cap, int mixed, SolveState* st) {
+    pdl_entry();
     DONE_GUARD(st);
     __shared__ double sh[33];
     const double rr = sum_partials(part_rr, nb, sh);
@@ -202,6 +207,7 @@ __global__ void k_scal_conv(const double* part_rr, int nb, double* hist, int his
 
 // After a residual replacement: test the FP64 true residual.
 __global__ void k_scal_replaced(const double* part_rr, int nb, double* hist, int hist_cap, SolveState* st) {
+    pdl_entry();
     if (st->done || !st->replace_now) return;
     __shared__ double sh[33];
     const double rr = sum_partials(part_rr, nb, sh);
@@ -226,6 +232,7 @@ __global__ void k_scal_replaced(const double* part_rr, int nb, double* hist, int
 // rho = r.z; beta = rho_new / rho (PCG) or -z.q / p.q (flexible); first: beta = 0.
 __global__ void k_scal_beta(const double* part_rz, const double* part_zq, int nb, int flexible, int first,
                             SolveState* st) {
+    pdl_entry();
     DONE_GUARD(st);
     __shared__ double sh[33];
     const double rz = sum_partials(part_rz, nb, sh);
@@ -246,6 +253,7 @@ __global__ void k_scal_beta(const double* part_rz, const double* part_zq, int nb
 template <typename X0>
 __global__ void k_update(int n, double* x, double* r, const double* __restrict__ p, const double* __restrict__ q,
                          const X0* __restrict__ invd, X0* x0, double* part_rr, const SolveState* st) {
+    pdl_entry();
     DONE_GUARD(st);
     __shared__ double sh[kWarpsPerBlock];
     const double alpha = st->alpha;
@@ -262,6 +270,7 @@ __global__ void k_update(int n, double* x, double* r, const double* __restrict__
 
 // p = z + beta p (first direction: p = z); p32 = FP32 copy (mixed).
 __global__ void k_pupdate(int n, double* p, const double* __restrict__ z, float* p32, int first, const SolveState* st) {
+    pdl_entry();
     DONE_GUARD(st);
     const double beta = st->beta;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -273,10 +282,12 @@ __global__ void k_pupdate(int n, double* p, const double* __restrict__ z, float*
 
 template <typename X0>
 __global__ void k_scale(int n, const double* __restrict__ a, const X0* __restrict__ b, X0* out) {
+    pdl_entry();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = (X0)a[i] * b[i];
 }
 
 __global__ void k_sqrt_sum(const double* part, int nb, double* out) {
+    pdl_entry();
     __shared__ double sh[33];
     const double s = sum_partials(part, nb, sh);
     if (threadIdx.x == 0) *out = sqrt(s);
@@ -316,7 +327,7 @@ cudaError_t launch_spmv(const DevCSR& A, const double* x, double* y, cudaStream_
     const int nb = row_blocks(A.n, rpw);
     if (A.n == 0) return cudaSuccess;
     with_rpw(rpw, [&](auto R) {
-        k_spmv<decltype(R)::value><<<AMG_GRID(nb), kBlock, 0, s>>>(A.n, CsrM<double>{A.rowptr, A.col, A.val}, x, y);
+        launch_pdl(k_spmv<decltype(R)::value, CsrM<double>>, nb, kBlock, 0, s, A.n, CsrM<double>{A.rowptr, A.col, A.val}, x, y);
     });
     return cudaGetLastError();
 }
@@ -381,7 +392,7 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
     const int flex = h->o.flexible;
     const SolveState* st = h->st;
     if (L == 1) {
-        k_coarse<double, A><<<AMG_GRID(row_blocks(h->ndense, 1)), kBlock, 0, s>>>(
+        launch_pdl(k_coarse<double, A>, row_blocks(h->ndense, 1), kBlock, 0, s,
             h->ndense, h->Ainv, h->r, nullptr, nullptr, nullptr, nullptr, h->z, h->q, slot(h, S_RZ), slot(h, S_ZQ),
             flex, st);
         return cudaGetLastError();
@@ -406,7 +417,7 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
                     A* xo = xcur[l];
                     A* xn = xalt[l];
                     with_rpw(rpw, [&](auto R) {
-                        k_sweep<decltype(R)::value, A, M, FT><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                        launch_pdl(k_sweep<decltype(R)::value, A, M, FT>, nb, kBlock, 0, s,
                             n, mat, fp, xo, Vw::invd(F), xn, st);
                     });
                     xcur[l] = xn;
@@ -423,7 +434,7 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
                     }
                 }
                 with_rpw(rpw, [&](auto R) {
-                    k_resid<decltype(R)::value, A, M, FT, A><<<AMG_GRID(nb), kBlock, 0, s>>>(n, mat, fp, xc, rb, st);
+                    launch_pdl(k_resid<decltype(R)::value, A, M, FT, A>, nb, kBlock, 0, s, n, mat, fp, xc, rb, st);
                 });
                 if (l == 0) prof_mark(h, 1, 1, s);
             };
@@ -431,14 +442,14 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
             else sweep_and_resid(static_cast<const A*>(Vw::f(F)));
         });
         const bool coarsest = (l + 1 == L - 1);
-        k_restrict<A><<<AMG_GRID(vec_blocks(C.A.n, sms)), kBlock, 0, s>>>(
+        launch_pdl(k_restrict<A>, vec_blocks(C.A.n, sms), kBlock, 0, s,
             C.A.n, F.mem_ptr, F.mem_idx, F.pval, xalt[l], Vw::f(C), coarsest ? nullptr : xcur[l + 1], Vw::invd(C), st);
     }
     // coarsest
     {
         Level& F = h->lev[L - 2];
         Level& C = h->lev[L - 1];
-        k_coarse<A, A><<<AMG_GRID(row_blocks(C.A.n, 1)), kBlock, 0, s>>>(
+        launch_pdl(k_coarse<A, A>, row_blocks(C.A.n, 1), kBlock, 0, s,
             C.A.n, h->Ainv, Vw::f(C), F.mem_ptr, F.mem_idx, F.pval, xcur[L - 2], nullptr, nullptr, nullptr, nullptr, 0,
             st);
     }
@@ -455,7 +466,7 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
                     A* xo = xcur[l];
                     A* xn = xalt[l];
                     with_rpw(rpw, [&](auto R) {
-                        k_sweep<decltype(R)::value, A, M, FT><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                        launch_pdl(k_sweep<decltype(R)::value, A, M, FT>, nb, kBlock, 0, s,
                             n, mat, fp, xo, Vw::invd(F), xn, st);
                     });
                     xcur[l] = xn;
@@ -476,7 +487,7 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
                     }
                 }
                 with_rpw(rpw, [&](auto R) {
-                    k_up0<decltype(R)::value, A, M><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                    launch_pdl(k_up0<decltype(R)::value, A, M>, nb, kBlock, 0, s,
                         n, mat, h->r, xc, Vw::invd(F), h->z, h->q, slot(h, S_RZ), slot(h, S_ZQ), flex, st);
                 });
                 prof_mark(h, 2, 1, s);
@@ -484,7 +495,7 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
                 Level& G = h->lev[l - 1];
                 A* xf = xcur[l - 1];
                 with_rpw(rpw, [&](auto R) {
-                    k_up<decltype(R)::value, A, M><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                    launch_pdl(k_up<decltype(R)::value, A, M>, nb, kBlock, 0, s,
                         n, mat, Vw::f(F), xc, Vw::invd(F), G.mem_ptr, G.mem_idx, G.pval, xf, st);
                 });
             }
@@ -533,11 +544,11 @@ static cudaError_t launch_residual(amg_hierarchy* h, double* r, bool want_x0, in
         with_mat(L0, static_cast<const double*>(L0.A.val), [&](auto mat) {
             using M = decltype(mat);
             if (h->mixed)
-                k_residual0<RPW, float, M><<<AMG_GRID(nb), kBlock, 0, s>>>(n, mat, h->x, h->F, L0.invd32, r,
+                launch_pdl(k_residual0<RPW, float, M>, nb, kBlock, 0, s, n, mat, h->x, h->F, L0.invd32, r,
                                                                            x0 ? L0.x32 : nullptr, slot(h, rr_slot),
                                                                            pff, gate);
             else
-                k_residual0<RPW, double, M><<<AMG_GRID(nb), kBlock, 0, s>>>(n, mat, h->x, h->F, L0.invd, r,
+                launch_pdl(k_residual0<RPW, double, M>, nb, kBlock, 0, s, n, mat, h->x, h->F, L0.invd, r,
                                                                             x0 ? L0.x : nullptr, slot(h, rr_slot),
                                                                             pff, gate);
         });
@@ -546,18 +557,18 @@ static cudaError_t launch_residual(amg_hierarchy* h, double* r, bool want_x0, in
 }
 
 static void launch_pupdate(amg_hierarchy* h, int first, cudaStream_t s) {
-    k_pupdate<<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(h->lev[0].A.n, h->p, h->z, h->mixed ? h->p32 : nullptr, first,
+    launch_pdl(k_pupdate, nbv(h), kBlock, 0, s, h->lev[0].A.n, h->p, h->z, h->mixed ? h->p32 : nullptr, first,
                                                   h->st);
 }
 
 // r = F - K x, ||F||, ||r||, first V-cycle, p = z, rho = r.z.
 cudaError_t enqueue_pcg_start(amg_hierarchy* h, cudaStream_t s) {
     AMG_TRY(launch_residual(h, h->r, true, S_RR, true, nullptr, s));
-    k_scal_init<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RR), slot(h, S_FF), nb_res(h), h->rtol, h->itmax,
+    launch_pdl(k_scal_init, 1, 256, 0, s, slot(h, S_RR), slot(h, S_FF), nb_res(h), h->rtol, h->itmax,
                                             h->mixed ? h->o.resid_replace_every : 0, h->hist, h->st);
     AMG_TRY(cudaGetLastError());
     AMG_TRY(enqueue_vcycle(h, s));
-    k_scal_beta<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RZ), slot(h, S_ZQ), nbz(h), h->o.flexible, 1, h->st);
+    launch_pdl(k_scal_beta, 1, 256, 0, s, slot(h, S_RZ), slot(h, S_ZQ), nbz(h), h->o.flexible, 1, h->st);
     launch_pupdate(h, 1, s);
     return cudaGetLastError();
 }
@@ -574,32 +585,32 @@ cudaError_t enqueue_pcg_iteration(amg_hierarchy* h, cudaStream_t s) {
             launch_stream_spmv_pq(h, h->p32, h->p, h->r, h->q, slot(h, S_PQ), slot(h, S_PR), flex, s);
         else if (h->mixed)
             with_mat(L0, static_cast<const float*>(L0.val32), [&](auto mat) {
-                k_spmv_pq<RPW, float, decltype(mat), float><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                launch_pdl(k_spmv_pq<RPW, float, decltype(mat), float>, nb, kBlock, 0, s,
                     n, mat, h->p32, h->p, h->r, h->q, slot(h, S_PQ), slot(h, S_PR), flex, h->st);
             });
         else
             with_mat(L0, static_cast<const double*>(L0.A.val), [&](auto mat) {
-                k_spmv_pq<RPW, double, decltype(mat), double><<<AMG_GRID(nb), kBlock, 0, s>>>(
+                launch_pdl(k_spmv_pq<RPW, double, decltype(mat), double>, nb, kBlock, 0, s,
                     n, mat, h->p, h->p, h->r, h->q, slot(h, S_PQ), slot(h, S_PR), flex, h->st);
             });
     });
     prof_mark(h, 0, 1, s);
-    k_scal_alpha<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_PQ), slot(h, S_PR), nb_fine(h), flex, h->st);
+    launch_pdl(k_scal_alpha, 1, 256, 0, s, slot(h, S_PQ), slot(h, S_PR), nb_fine(h), flex, h->st);
     const bool x0 = h->nlev > 1;
     if (h->mixed)
-        k_update<float><<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(n, h->x, h->r, h->p, h->q, L0.invd32, x0 ? L0.x32 : nullptr,
+        launch_pdl(k_update<float>, nbv(h), kBlock, 0, s, n, h->x, h->r, h->p, h->q, L0.invd32, x0 ? L0.x32 : nullptr,
                                                             slot(h, S_RR), h->st);
     else
-        k_update<double><<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(n, h->x, h->r, h->p, h->q, L0.invd, x0 ? L0.x : nullptr,
+        launch_pdl(k_update<double>, nbv(h), kBlock, 0, s, n, h->x, h->r, h->p, h->q, L0.invd, x0 ? L0.x : nullptr,
                                                              slot(h, S_RR), h->st);
-    k_scal_conv<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RR), nbv(h), h->hist, h->hist_cap, h->mixed, h->st);
+    launch_pdl(k_scal_conv, 1, 256, 0, s, slot(h, S_RR), nbv(h), h->hist, h->hist_cap, h->mixed, h->st);
     if (h->mixed) {  // FP64 true-residual replacement, when due
         AMG_TRY(launch_residual(h, h->r, true, S_RR2, false, h->st, s));
-        k_scal_replaced<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RR2), nb_res(h), h->hist, h->hist_cap, h->st);
+        launch_pdl(k_scal_replaced, 1, 256, 0, s, slot(h, S_RR2), nb_res(h), h->hist, h->hist_cap, h->st);
     }
     AMG_TRY(cudaGetLastError());
     AMG_TRY(enqueue_vcycle(h, s));
-    k_scal_beta<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RZ), slot(h, S_ZQ), nbz(h), flex, 0, h->st);
+    launch_pdl(k_scal_beta, 1, 256, 0, s, slot(h, S_RZ), slot(h, S_ZQ), nbz(h), flex, 0, h->st);
     launch_pupdate(h, 0, s);
     return cudaGetLastError();
 }
@@ -607,8 +618,8 @@ cudaError_t enqueue_pcg_iteration(amg_hierarchy* h, cudaStream_t s) {
 // ||F - K x|| and ||F|| into slot(S_OUT)[0..1] (FP64, recomputed).
 cudaError_t launch_final_residual(amg_hierarchy* h, cudaStream_t s) {
     AMG_TRY(launch_residual(h, h->q, false, S_RR, true, nullptr, s));
-    k_sqrt_sum<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_RR), nb_res(h), slot(h, S_OUT));
-    k_sqrt_sum<<<AMG_GRID(1), 256, 0, s>>>(slot(h, S_FF), nb_res(h), slot(h, S_OUT) + 1);
+    launch_pdl(k_sqrt_sum, 1, 256, 0, s, slot(h, S_RR), nb_res(h), slot(h, S_OUT));
+    launch_pdl(k_sqrt_sum, 1, 256, 0, s, slot(h, S_FF), nb_res(h), slot(h, S_OUT) + 1);
     return cudaGetLastError();
 }
 
@@ -619,9 +630,9 @@ cudaError_t enqueue_vcycle_standalone(amg_hierarchy* h, cudaStream_t s) {
     if (h->nlev > 1) {
         Level& L0 = h->lev[0];
         if (h->mixed)
-            k_scale<float><<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(L0.A.n, h->r, L0.invd32, L0.x32);
+            launch_pdl(k_scale<float>, nbv(h), kBlock, 0, s, L0.A.n, h->r, L0.invd32, L0.x32);
         else
-            k_scale<double><<<AMG_GRID(nbv(h)), kBlock, 0, s>>>(L0.A.n, h->r, L0.invd, L0.x);
+            launch_pdl(k_scale<double>, nbv(h), kBlock, 0, s, L0.A.n, h->r, L0.invd, L0.x);
     }
     AMG_TRY(cudaGetLastError());
     return enqueue_vcycle(h, s);

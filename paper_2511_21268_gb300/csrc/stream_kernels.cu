@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
              const int32_t* __restrict__ rst, const V* __restrict__ val, const float* __restrict__ xg,
              const int2* __restrict__ win, StreamShape shape, Epi epi, double* part1, double* part2,
              SolveState* st) {
+    pdl_entry();
     if (st && st->done) return;
     constexpr int S = kStreamWarps * RPW;
     constexpr int LPR = 32 / RPW;
@@ -312,6 +313,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
 template <typename T>
 __global__ void k_interleave_runs(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ rptr,
                                   const uint8_t* __restrict__ rlen, const T* __restrict__ in, T* out) {
+    pdl_entry();
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
@@ -324,6 +326,7 @@ __global__ void k_interleave_runs(int n, const int64_t* __restrict__ rp, const i
 
 // Largest slab of S rows: entries and runs (atomic max over slabs).
 __global__ void k_slab_max(int n, int S, const int64_t* __restrict__ rp, const int32_t* __restrict__ rptr, int* out) {
+    pdl_entry();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int nsl = (n + S - 1) / S;
     if (k >= nsl) return;
@@ -336,6 +339,7 @@ __global__ void k_slab_max(int n, int S, const int64_t* __restrict__ rp, const i
 // last column over the rows of its slabs (a thread block per grid block).
 __global__ void k_block_window(int n, int S, int G, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                int2* win) {
+    pdl_entry();
     __shared__ int slo[256], shi[256];
     const int b = blockIdx.x;
     const int nsl = (n + S - 1) / S;
@@ -374,7 +378,7 @@ cudaError_t launch(amg_hierarchy* h, const V* val, const float* x, StreamShape s
                    double* p2, cudaStream_t s) {
     const Level& L0 = h->lev[0];
     const uint32_t smem = stream_smem_bytes<RPW>(sh);
-    k_stream<RPW, V, Epi><<<AMG_GRID(h->stream_blocks), kStreamThreads, smem, s>>>(
+    launch_pdl(k_stream<RPW, V, Epi>, h->stream_blocks, kStreamThreads, smem, s,
         L0.A.n, L0.A.rowptr, L0.run_ptr, L0.run_len, L0.run_start, val, x, reinterpret_cast<const int2*>(h->stream_win),
         sh, epi, p1, p2, h->st);
     return cudaGetLastError();
@@ -431,12 +435,12 @@ int stream_prepare(amg_hierarchy* h, int* scratch2) {
     for (int v = 0; v < 2; v++) {  // v = 0: RPW 2 (32-row slabs), v = 1: RPW 1 (16-row slabs)
         const int rpw = v == 0 ? 2 : 1;
         const int S = kStreamWarps * rpw;
-        k_block_window<<<AMG_GRID(G), 256, 0, h->s>>>(n, S, G, L0.A.rowptr, L0.A.col, win);
+        launch_pdl(k_block_window, G, 256, 0, h->s, n, S, G, L0.A.rowptr, L0.A.col, win);
         std::vector<int2> hw(G);
         int slab[2] = {0, 0};  // entries, runs of the largest slab
         if (cudaMemsetAsync(scratch2, 0, 2 * sizeof(int), h->s) != cudaSuccess) return AMG_ERR_CUDA;
         const int nsl = (n + S - 1) / S;
-        k_slab_max<<<AMG_GRID((nsl + 255) / 256), 256, 0, h->s>>>(n, S, L0.A.rowptr, L0.run_ptr, scratch2);
+        launch_pdl(k_slab_max, (nsl + 255) / 256, 256, 0, h->s, n, S, L0.A.rowptr, L0.run_ptr, scratch2);
         if (cudaMemcpyAsync(hw.data(), win, sizeof(int2) * G, cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
             cudaMemcpyAsync(slab, scratch2, sizeof(slab), cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
             cudaStreamSynchronize(h->s) != cudaSuccess)
@@ -484,13 +488,13 @@ int stream_prepare(amg_hierarchy* h, int* scratch2) {
             if (dev_alloc(reinterpret_cast<void**>(&F0.val16t), sizeof(__nv_bfloat16) * (nnz + 16), h->s) != cudaSuccess)
                 return AMG_ERR_NOMEM;
             h->allocs.push_back(F0.val16t);
-            k_interleave_runs<<<AMG_GRID(gw), 256, 0, h->s>>>(n, F0.A.rowptr, F0.run_ptr, F0.run_len, F0.val16,
-                                                               F0.val16t);
+            launch_pdl(k_interleave_runs<__nv_bfloat16>, gw, 256, 0, h->s, n, F0.A.rowptr, F0.run_ptr, F0.run_len,
+                       F0.val16, F0.val16t);
         }
         if (dev_alloc(reinterpret_cast<void**>(&F0.val32t), sizeof(float) * (nnz + 16), h->s) != cudaSuccess) return AMG_ERR_NOMEM;
         h->allocs.push_back(F0.val32t);
-        k_interleave_runs<<<AMG_GRID(gw), 256, 0, h->s>>>(n, F0.A.rowptr, F0.run_ptr, F0.run_len, F0.val32,
-                                                           F0.val32t);
+        launch_pdl(k_interleave_runs<float>, gw, 256, 0, h->s, n, F0.A.rowptr, F0.run_ptr, F0.run_len, F0.val32,
+                   F0.val32t);
         if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
         if ((reinterpret_cast<uintptr_t>(F0.val32t) & 15) || (reinterpret_cast<uintptr_t>(F0.val16t) & 15))
             return AMG_OK;

@@ -564,6 +564,16 @@ double index_bytes(const Level& L) {
     return (double)L.A.nnz * 4.0;
 }
 
+// Index and row-structure bytes of one finest-level pass of the precision
+// in use (padding excluded): the sliced slabs read a 16-bit window offset
+// per run and one slot offset per slab; the other formats read the row
+// offsets (8 B per row) and the column index (index_bytes).
+static double fine_structure_bytes(const amg_hierarchy* h) {
+    const Level& L0 = h->lev[0];
+    if (h->stream == 2) return (double)L0.nruns * 2.0 + (h->sell_nsl + 1.0) * 4.0;
+    return index_bytes(L0) + (L0.A.n + 1.0) * 8.0;
+}
+
 void fill_info(amg_hierarchy* h) {
     amg_info& I = h->info;
     I.levels = h->nlev;
@@ -589,7 +599,8 @@ void fill_info(amg_hierarchy* h) {
     const double vb = h->mixed ? 4.0 : 8.0;
     auto pass_bytes = [&](const Level& L, double valb) {
         const DevCSR& A = L.A;
-        return (double)A.nnz * valb + index_bytes(L) + (A.n + 1.0) * 8.0 + 2.0 * A.n * vb;
+        const double sb = (&L == &h->lev[0]) ? fine_structure_bytes(h) : index_bytes(L) + (A.n + 1.0) * 8.0;
+        return (double)A.nnz * valb + sb + 2.0 * A.n * vb;
     };
     if (h->nlev == 1) {
         vbytes = (double)h->ndense * h->ndense * 8.0 + 2.0 * h->ndense * 8.0;
@@ -606,7 +617,7 @@ void fill_info(amg_hierarchy* h) {
     // outer q = K p (FP32 values in mixed mode) + CG vectors; mixed mode adds an
     // FP64 residual replacement every resid_replace_every iterations
     const double ib0 = index_bytes(h->lev[0]);
-    double outer = (double)A0.nnz * vb + ib0 + (A0.n + 1.0) * 8.0 + 2.0 * A0.n * 8.0;
+    double outer = (double)A0.nnz * vb + fine_structure_bytes(h) + 2.0 * A0.n * 8.0;
     if (h->mixed && h->o.resid_replace_every > 0)
         outer += ((double)A0.nnz * 8.0 + ib0 + (A0.n + 1.0) * 8.0 + 3.0 * A0.n * 8.0) / h->o.resid_replace_every;
     I.iter_bytes = vbytes + outer + 10.0 * A0.n * 8.0;
@@ -1261,7 +1272,7 @@ int amg_kernel_times(const amg_hierarchy* h, double* ms, int64_t* count, double*
     double b[3];
     if (h->mixed) {  // FP32 outer values, FP32 (or BF16) V-cycle values, FP32 V-cycle vectors
         const double vcv = h->lev[0].val16 ? 2.0 : 4.0;
-        const double rows = (n + 1.0) * 8.0 + ib;
+        const double rows = fine_structure_bytes(h);
         b[0] = nnz * 4.0 + rows + 4.0 * n + 8.0 * n + 8.0 * n + flex;  // p32 gather, q, p
         b[1] = nnz * vcv + rows + 8.0 * n + 4.0 * n + 4.0 * n;  // r, x, rbuf
         b[2] = nnz * vcv + rows + 8.0 * n + 4.0 * n + 4.0 * n + 8.0 * n + flex;  // r, x, invd, z

@@ -28,7 +28,7 @@
 // per value one value load, one vector load and one FMA, every load from
 // shared memory at a compile-time offset.  Every warp writes its 32 partial
 // row sums to the buffer; the slab's epilogue warp (rotating) waits for all
-// 16, adds them in warp order (deterministic), and runs the epilogue
+// 16, adds them in a fixed pairwise tree (deterministic), and runs the epilogue
 // (residual, smoothing with z and r.z, q = K p with p.q) with one lane per
 // row.  Dot products accumulate in the epilogue lanes in slab order and are
 // written as one deterministic partial per block.
@@ -258,9 +258,15 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
             }
             ok = __all_sync(FULL, mbar_wait_bounded(bar_part(j), (uint32_t)u & 1u));
             if (!ok) break;
-            float s = 0.f;
+            // pairwise tree over the 16 warp partials (a fixed order)
+            float t[kStreamWarps];
 #pragma unroll
-            for (int w = 0; w < kStreamWarps; w++) s += part[w * kSlab + lane];  // warp order
+            for (int w = 0; w < kStreamWarps; w++) t[w] = part[w * kSlab + lane];
+#pragma unroll
+            for (int h = kStreamWarps / 2; h > 0; h >>= 1)
+#pragma unroll
+                for (int w = 0; w < h; w++) t[w] += t[w + h];
+            const float s = t[0];
             const int i = k * kSlab + lane;
             if (i < n) epi(i, lane, s, bv + o_seg, kSegBytes, xs, acc1, acc2);
             __syncwarp();

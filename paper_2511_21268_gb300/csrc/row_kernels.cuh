@@ -250,7 +250,8 @@ __global__ void __launch_bounds__(kBlock) k_sweep(int n, M mat, const FT* __rest
 }
 
 // Up sweep of level l >= 1: y_a = x_a + (f_a - (K x)_a) / d_a, then
-// x_{l-1}[c] += p_c y_a for the members c of a.
+// x_{l-1}[c] += p_c y_a for the members c of a (one member per lane of the
+// row's lane group).
 template <int RPW, typename A, typename M>
 __global__ void __launch_bounds__(kBlock) k_up(int n, M mat, const A* __restrict__ f, const A* __restrict__ x,
                                                 const A* __restrict__ invd,
@@ -260,9 +261,12 @@ __global__ void __launch_bounds__(kBlock) k_up(int n, M mat, const A* __restrict
     DONE_GUARD(st);
     ROWGROUP_PROLOGUE(A)
     const A s = group_rows<RPW, A>(mat, x, row0, n, lane, tiles[wid]);
-    if (owner) {
+    // every lane of the row's group has the total; the aggregate's members
+    // (independent fine rows) are spread over those LPR lanes
+    if (myrow < n) {
         const A y = fma(invd[myrow], f[myrow] - s, x[myrow]);
-        for (int m = mptr[myrow]; m < mptr[myrow + 1]; m++) {
+        const int m1 = mptr[myrow + 1];
+        for (int m = mptr[myrow] + lane % LPR; m < m1; m += LPR) {
             const int c = midx[m];
             xf[c] = fma((A)pvalf[c], y, xf[c]);
         }

@@ -71,20 +71,42 @@ __device__ double sum_partials(const double* __restrict__ part, int nb, double* 
 }
 
 // Restriction f_c[I] = sum_{a in I, ascending} p_a r_a, x_c = f_c / d_c.
-template <typename A>
+// GS lanes per coarse row load its members in parallel (members GS apart);
+// the group's first lane then folds the terms in member order, so the sum
+// is the same FMA chain as a sequential loop.
+template <typename A, int GS>
 __global__ void k_restrict(int nc, const int32_t* __restrict__ mptr, const int32_t* __restrict__ midx,
                            const double* __restrict__ pval, const A* __restrict__ rbuf, A* fc, A* xc,
                            const A* __restrict__ invdc, const SolveState* st) {
     pdl_entry();
     DONE_GUARD(st);
-    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+    constexpr int G = 32 / GS;  // coarse rows per warp
+    const int lane = threadIdx.x & 31, q = lane % GS, gbase = lane - q;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int I0 = warp * G; I0 < nc; I0 += nwarps * G) {  // warp-uniform
+        const int I = I0 + lane / GS;
+        const bool valid = I < nc;
+        const int m0 = valid ? mptr[I] : 0, cnt = valid ? mptr[I + 1] - m0 : 0;
+        const int cmax = __reduce_max_sync(FULL, cnt);
         A acc = A(0);
-        for (int m = mptr[I]; m < mptr[I + 1]; m++) {
-            const int a = midx[m];
-            acc = fma((A)pval[a], rbuf[a], acc);
+        for (int base = 0; base < cmax; base += GS) {
+            A pa = A(0), ra = A(0);
+            if (base + q < cnt) {
+                const int a = midx[m0 + base + q];
+                pa = (A)pval[a];
+                ra = rbuf[a];
+            }
+#pragma unroll
+            for (int j = 0; j < GS; j++) {
+                const A pj = __shfl_sync(FULL, pa, gbase + j), rj = __shfl_sync(FULL, ra, gbase + j);
+                if (base + j < cnt) acc = fma(pj, rj, acc);
+            }
         }
-        fc[I] = acc;
-        if (xc) xc[I] = acc * invdc[I];
+        if (valid && q == 0) {
+            fc[I] = acc;
+            if (xc) xc[I] = acc * invdc[I];
+        }
     }
 }
 
@@ -115,8 +137,9 @@ __global__ void __launch_bounds__(kBlock) k_coarse(int n, const double* __restri
                 rz = (double)f[I] * s;
                 if (flexible) zq = s * q[I];
             }
-        } else if (lane == 0) {
-            for (int m = mptr[I]; m < mptr[I + 1]; m++) {
+        } else {  // the aggregate's members, one per lane
+            const int m1 = mptr[I + 1];
+            for (int m = mptr[I] + lane; m < m1; m += 32) {
                 const int c = midx[m];
                 xf[c] = (XT)fma(pvalf[c], s, (double)xf[c]);
             }
@@ -319,6 +342,11 @@ int vec_blocks(int n, int num_sms) {
     return (int)b;
 }
 
+// blocks of the restriction: 4 lanes per coarse row
+static int restrict_blocks(int nc, int num_sms) {
+    return vec_blocks((int)std::min<int64_t>((int64_t)nc * 4, INT32_MAX), num_sms);
+}
+
 cudaError_t launch_spmv(const DevCSR& A, const double* x, double* y, cudaStream_t s) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -442,7 +470,7 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
             else sweep_and_resid(static_cast<const A*>(Vw::f(F)));
         });
         const bool coarsest = (l + 1 == L - 1);
-        launch_pdl(k_restrict<A>, vec_blocks(C.A.n, sms), kBlock, 0, s,
+        launch_pdl(k_restrict<A, 4>, restrict_blocks(C.A.n, sms), kBlock, 0, s,
             C.A.n, F.mem_ptr, F.mem_idx, F.pval, xalt[l], Vw::f(C), coarsest ? nullptr : xcur[l + 1], Vw::invd(C), st);
     }
     // coarsest

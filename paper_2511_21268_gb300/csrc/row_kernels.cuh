@@ -57,6 +57,7 @@ __constant__ uint32_t kRunMagic[kMaxRunLen + 1] = {0u,          0u,          214
 
 template <typename V>
 struct CsrM {
+    static constexpr bool kFlat = true;
     const int64_t* __restrict__ rp;
     const int32_t* __restrict__ ci;
     const V* __restrict__ v;
@@ -64,10 +65,64 @@ struct CsrM {
     __device__ __forceinline__ A partial(const X* __restrict__ x, int i, int lane) const {
         return lane_partial<A>(rp, ci, v, x, i, lane);
     }
+    // Lane partials of the RPW rows row0 .. row0+RPW-1 into tile[r][lane]:
+    // the warp streams the rows' contiguous entries, lane t taking entries
+    // e0 + t + 32 j in order with four loads in flight, so no row waits for
+    // the previous one.  A lane keeps one running sum and stores it to
+    // tile[r][t] when its next entry lies past row r (rows it never
+    // touches keep 0).
+    template <int RPW, typename A, typename X>
+    __device__ __forceinline__ void flat(const X* __restrict__ x, int row0, int n, int lane, A (*tile)[33]) const {
+        const int64_t myb = lane <= RPW ? rp[min(row0 + lane, n)] : 0;
+        const int64_t e0 = __shfl_sync(FULL, myb, 0);
+        const int rel = (int)(myb - e0);  // row bound j on lane j, relative to e0
+        int bnd[RPW + 1];
+#pragma unroll
+        for (int j = 0; j <= RPW; j++) bnd[j] = __shfl_sync(FULL, rel, j);
+#pragma unroll
+        for (int r = 0; r < RPW; r++) tile[r][lane] = A(0);
+        const int len = bnd[RPW];
+        const V* __restrict__ vr = v + e0;
+        const int32_t* __restrict__ cr = ci + e0;
+        int r = 0, nb = bnd[1];
+        A acc = A(0);
+        auto take = [&](int k, A val, A xv) {
+            while (k >= nb) {  // rows ending before entry k
+                tile[r][lane] = acc;
+                acc = A(0);
+                r++;
+#pragma unroll
+                for (int j = 1; j <= RPW; j++)
+                    if (j == r + 1) nb = bnd[j];
+            }
+            acc = fma(val, xv, acc);
+        };
+        for (int k0 = lane; k0 < len; k0 += 128) {
+            const int k1 = k0 + 32, k2 = k0 + 64, k3 = k0 + 96;
+            const A v0 = (A)ldv(vr, k0);
+            const A v1 = k1 < len ? (A)ldv(vr, k1) : A(0);
+            const A v2 = k2 < len ? (A)ldv(vr, k2) : A(0);
+            const A v3 = k3 < len ? (A)ldv(vr, k3) : A(0);
+            const int c0 = __ldg(cr + k0);
+            const int c1 = k1 < len ? __ldg(cr + k1) : 0;
+            const int c2 = k2 < len ? __ldg(cr + k2) : 0;
+            const int c3 = k3 < len ? __ldg(cr + k3) : 0;
+            const A x0 = (A)x[c0];
+            const A x1 = k1 < len ? (A)x[c1] : A(0);
+            const A x2 = k2 < len ? (A)x[c2] : A(0);
+            const A x3 = k3 < len ? (A)x[c3] : A(0);
+            take(k0, v0, x0);
+            if (k1 < len) take(k1, v1, x1);
+            if (k2 < len) take(k2, v2, x2);
+            if (k3 < len) take(k3, v3, x3);
+        }
+        if (r < RPW) tile[r][lane] = acc;
+    }
 };
 
 template <typename V>
 struct RunM {
+    static constexpr bool kFlat = false;
     const int64_t* __restrict__ rp;
     const int32_t* __restrict__ rptr;
     const uint8_t* __restrict__ rlen;
@@ -113,10 +168,14 @@ __device__ __forceinline__ A group_rows(const M& mat, const X* __restrict__ x, i
         return s;
     } else {
         constexpr int LPR = 32 / RPW;  // lanes per row in the finishing step
+        if constexpr (M::kFlat) {
+            mat.template flat<RPW, A>(x, row0, n, lane, tile);
+        } else {
 #pragma unroll 1
-        for (int r = 0; r < RPW; r++) {
-            const int i = row0 + r;
-            tile[r][lane] = i < n ? mat.template partial<A>(x, i, lane) : A(0);
+            for (int r = 0; r < RPW; r++) {
+                const int i = row0 + r;
+                tile[r][lane] = i < n ? mat.template partial<A>(x, i, lane) : A(0);
+            }
         }
         __syncwarp();
         const int r = lane / LPR, q = lane % LPR;

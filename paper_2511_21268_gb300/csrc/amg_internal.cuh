@@ -197,6 +197,9 @@ struct amg_hierarchy {
     __nv_bfloat16* sell_v16 = nullptr;   // BF16 values (BF16 finest values only)
     int sell_vbytes[2] = {};             // value area per buffer: [0] BF16, [1] FP32
     int sell_rbytes = 0;                 // start-column area per buffer
+    void* sell_wint = nullptr;           // int4 per window interval (kMaxWinIntervals per block)
+    int* sell_wcnt = nullptr;            // window intervals of each block
+    int* sell_wbytes = nullptr;          // compacted window bytes of each block
     // multi-system solves
     amg::MultiWork* mw = nullptr;
     // learned smoother damping: network buffers, and whether the smoother

@@ -52,6 +52,8 @@ namespace {
 
 constexpr int kSlab = 32;                                   // rows per slab (one per lane)
 constexpr uint32_t kSegBytes = kSlab * 8;                   // one staged epilogue segment
+constexpr int kSellVec = 4;                                 // staged epilogue vectors, at most
+constexpr int kMaxWinIntervals = 64;                        // window copies per block, at most
 constexpr uint32_t kPartBytes = kStreamWarps * kSlab * 4;   // partial row sums of the 16 warps
 constexpr int kSellBuf = 6;                                 // largest ring
 constexpr uint32_t kSellCtl = 256;                          // barriers and control words
@@ -64,11 +66,38 @@ struct SellShape {
 };
 
 __host__ __device__ inline uint32_t sell_buffer_bytes(SellShape sh) {
-    return sh.vbytes + sh.rbytes + kMaxVec * kSegBytes + kPartBytes;
+    return sh.vbytes + sh.rbytes + kSellVec * kSegBytes + kPartBytes;
 }
 
 __host__ __device__ inline uint32_t sell_smem_bytes(SellShape sh) {
     return sh.xbytes + (uint32_t)sh.nbuf * sell_buffer_bytes(sh) + kSellCtl;
+}
+
+// Up sweep of level 0 for the sliced slabs: z = x + (r - K x) / d, r.z and
+// z.q; x_i comes from a staged segment (the compacted window holds only
+// the columns the slabs read, in their own order).
+struct EpiUp0S {
+    const void* vec[kSellVec];  // r (FP64), 1/d (FP32), x (FP32), q (FP64, flexible)
+    int es[kSellVec];
+    int nvec;
+    double* z;
+    int flexible;
+    __device__ __forceinline__ void operator()(int i, int t, float s, const unsigned char* seg, uint32_t ss,
+                                               const float*, double& rz, double& zq) const {
+        const double ra = reinterpret_cast<const double*>(seg)[t];
+        const float di = reinterpret_cast<const float*>(seg + ss)[t];
+        const float xi = reinterpret_cast<const float*>(seg + 2 * ss)[t];
+        const double za = (double)fmaf(di, (float)ra - s, xi);
+        z[i] = za;
+        rz += ra * za;
+        if (flexible) zq += za * reinterpret_cast<const double*>(seg + 3 * ss)[t];
+    }
+};
+
+// number of staged vectors an epilogue type can name
+template <typename Epi>
+constexpr int epi_vecs() {
+    return (int)(sizeof(Epi::vec) / sizeof(Epi::vec[0]));
 }
 
 template <int OFF>
@@ -114,8 +143,8 @@ struct SlotDot<LM, LM, V> {
 template <int LM, typename V, typename Epi>
 __global__ void __launch_bounds__(kStreamThreads, 1)
     k_sell(int n, int nsl, const int32_t* __restrict__ soff, const V* __restrict__ val, const uint16_t* __restrict__ rs,
-           const float* __restrict__ xg, const int2* __restrict__ win, SellShape shape, Epi epi, double* part1,
-           double* part2, SolveState* st) {
+           const float* __restrict__ xg, const int4* __restrict__ wint, const int* __restrict__ wcnt,
+           const int* __restrict__ wbytes, SellShape shape, Epi epi, double* part1, double* part2, SolveState* st) {
     pdl_entry();
     if (st && st->done) return;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -123,7 +152,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     const float* xw = reinterpret_cast<const float*>(smem);
     unsigned char* ring = smem + shape.xbytes;
     const uint32_t bufstride = sell_buffer_bytes(shape);
-    const uint32_t o_rs = shape.vbytes, o_seg = o_rs + shape.rbytes, o_part = o_seg + kMaxVec * kSegBytes;
+    const uint32_t o_rs = shape.vbytes, o_seg = o_rs + shape.rbytes, o_part = o_seg + kSellVec * kSegBytes;
     unsigned char* ctl = ring + nbuf * bufstride;
     // [0] window, [1 + j] full[j], [1 + kSellBuf + j] empty[j], [1 + 2 kSellBuf + j] partials[j]
     uint64_t* bars = reinterpret_cast<uint64_t*>(ctl);
@@ -131,7 +160,6 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     static_assert(kBarBytes + 4 * kSellBuf + 8 <= (int)kSellCtl, "control area");
     int* rsl = reinterpret_cast<int*>(ctl + kBarBytes);                                 // run slots of buffer j
     volatile int* ctrl = reinterpret_cast<int*>(ctl + kBarBytes + 4 * kSellBuf);       // 0 = go on, 1 = give up
-    int* xlo = reinterpret_cast<int*>(ctl + kBarBytes + 4 * kSellBuf + 4);            // first window entry
     __shared__ double red[kStreamWarps + 1];
 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -152,8 +180,6 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         *ctrl = 0;
-        *xlo = 0;
-        if (s0 < s1) *xlo = win[blockIdx.x].x & ~3;
     }
     __syncthreads();
 
@@ -165,12 +191,13 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         // waits for buffers and issues the copies.
         if (s0 < s1) {
             int last_use = -1;  // last slab issued (lane 0)
-            if (lane == 0) {
-                const int2 w = win[blockIdx.x];
-                const int lo = w.x & ~3;
-                const uint32_t bytes = align16((uint32_t)(w.y + 1 - lo) * 4u);
-                mbar_expect_tx(bar_win, bytes);
-                bulk_g2s(smem_addr(smem), xg + lo, bytes, bar_win);
+            // the compacted window: interval q copies entries [x, x + y) of the
+            // vector to window offset z (all multiples of 4)
+            if (lane == 0) mbar_expect_tx(bar_win, (uint32_t)wbytes[blockIdx.x]);
+            __syncwarp();
+            for (int q = lane; q < wcnt[blockIdx.x]; q += 32) {
+                const int4 iv = wint[blockIdx.x * kMaxWinIntervals + q];
+                bulk_g2s(smem_addr(smem) + 4u * (uint32_t)iv.z, xg + iv.x, 4u * (uint32_t)iv.y, bar_win);
             }
             bool go = true;
             for (int kb = s0; kb < s1 && go; kb += 32) {
@@ -196,7 +223,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                             const uint32_t rb = (uint32_t)R * (uint32_t)(kSlab * 2);
                             uint32_t tx = vb + rb;
 #pragma unroll
-                            for (int v = 0; v < kMaxVec; v++)
+                            for (int v = 0; v < epi_vecs<Epi>(); v++)
                                 if (v < epi.nvec) tx += align16(cnt * (uint32_t)epi.es[v]);
                             unsigned char* bv = ring + j * bufstride;
                             const uint32_t bar = bar_full(j);
@@ -207,7 +234,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                                 bulk_g2s(smem_addr(bv + o_rs), rs + (int64_t)o0 * kSlab, rb, bar);
                             }
 #pragma unroll
-                            for (int v = 0; v < kMaxVec; v++)
+                            for (int v = 0; v < epi_vecs<Epi>(); v++)
                                 if (v < epi.nvec)
                                     bulk_g2s(smem_addr(bv + o_seg + v * kSegBytes),
                                              reinterpret_cast<const unsigned char*>(epi.vec[v]) +
@@ -230,7 +257,6 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         // ------------------------------------------------------------ consumers
         bool ok = true;
         if (s0 < s1) ok = __all_sync(FULL, mbar_wait_bounded(bar_win, 0u));
-        const float* xs = xw - *xlo;        // xs[c] = vector entry c (inside the window)
         const uint32_t xbase = smem_addr(xw);  // window offset q at xbase + 4 q
         for (int k = s0; k < s1 && ok; k++) {
             const int u = (k - s0) / nbuf, j = (k - s0) % nbuf;
@@ -268,7 +294,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                 for (int w = 0; w < h; w++) t[w] += t[w + h];
             const float s = t[0];
             const int i = k * kSlab + lane;
-            if (i < n) epi(i, lane, s, bv + o_seg, kSegBytes, xs, acc1, acc2);
+            if (i < n) epi(i, lane, s, bv + o_seg, kSegBytes, nullptr, acc1, acc2);
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_empty(j));
         }
@@ -347,17 +373,135 @@ __global__ void k_sell_span(int n, int nsl, int LM, const int32_t* __restrict__ 
     }
 }
 
+// The vector window of grid block b (owner of slab k when
+// b = ((k + 1) G - 1) / nsl) is compacted: column c lies in 4-entry group
+// g = (c - lo4) / 4, lo4 = win[b].x & ~3; only groups some slot reads are
+// copied, in order, and group g lands at window offset 4 rank[goff[b] + g].
+// k_sell_mark sets bit g of the block's group bitmap (from word
+// wordoff[b]) for every group a slot reads; the lanes of a warp (one slot
+// of 32 neighbouring rows) OR their masks over two words first.
+__device__ __forceinline__ int slot_pad(const int32_t* __restrict__ rptr, const int32_t* __restrict__ rst, int k,
+                                        int n, int LM) {
+    const int f0 = rptr[k * kSlab];
+    return rptr[k * kSlab + 1] > f0 ? max(0, slot_start(rst[f0], n, LM)) : 0;
+}
+
+__global__ void k_sell_mark(int n, int nsl, int G, int LM, const int32_t* __restrict__ rptr,
+                            const int32_t* __restrict__ rst, const int32_t* __restrict__ soff,
+                            const int2* __restrict__ win, const int* __restrict__ wordoff, uint32_t* bits) {
+    pdl_entry();
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nsl; k += nw) {
+        const int i = k * kSlab + lane;
+        const int Rs = soff[k + 1] - soff[k];
+        const int b = (int)(((int64_t)(k + 1) * G - 1) / nsl);
+        const int lo4 = win[b].x & ~3;
+        uint32_t* bb = bits + wordoff[b];
+        int r0 = 0, Ri = 0;
+        if (i < n) {
+            r0 = rptr[i];
+            Ri = rptr[i + 1] - r0;
+        }
+        const int cpad = slot_pad(rptr, rst, k, n, LM);
+        for (int r = 0; r < Rs; r++) {
+            const int c = r < Ri ? slot_start(rst[r0 + r], n, LM) : cpad;
+            const int g0 = (c - lo4) >> 2, g1 = (c + LM - 1 - lo4) >> 2;
+            const int w0 = __reduce_min_sync(FULL, g0) >> 5;  // the warp's first word
+            uint32_t m0 = 0, m1 = 0;
+            bool alone = false;
+            for (int g = g0; g <= g1; g++) {
+                const int d = g - w0 * 32;
+                if (d < 32) m0 |= 1u << d;
+                else if (d < 64) m1 |= 1u << (d - 32);
+                else alone = true;
+            }
+            if (alone)  // groups beyond the two shared words
+                for (int g = g0; g <= g1; g++)
+                    if (g - w0 * 32 >= 64) atomicOr(bb + (g >> 5), 1u << (g & 31));
+            m0 = __reduce_or_sync(FULL, m0);
+            m1 = __reduce_or_sync(FULL, m1);
+            if (lane == 0 && m0) atomicOr(bb + w0, m0);
+            if (lane == 1 && m1) atomicOr(bb + w0 + 1, m1);
+        }
+    }
+}
+
+// Intervals of the compacted window of grid block b (a thread block per
+// grid block; its first thread scans the group bitmap): maximal runs of
+// marked groups, at most kMaxWinIntervals of them (the smallest gaps are
+// filled: the threshold T is the least gap length that leaves few enough
+// runs when every gap <= T is copied too).  Writes the runs as (first
+// column, entries, window offset) to wint[b kMaxWinIntervals + q], their
+// count, the window bytes, and the group ranks.  More runs than the scan
+// buffer holds: one interval over the whole range (no compaction).
+__global__ void k_sell_intervals(int G, const int2* __restrict__ win, const int* __restrict__ wordoff,
+                                 const int* __restrict__ goff, const uint32_t* __restrict__ bits, int4* wint,
+                                 int* wcnt, int* wbytes, uint16_t* rank) {
+    pdl_entry();
+    constexpr int kRuns = 2048;
+    __shared__ int rs[kRuns], re[kRuns];
+    const int b = blockIdx.x;
+    if (b >= G || threadIdx.x != 0) return;
+    const int lo4 = win[b].x & ~3;
+    const int ng = goff[b + 1] - goff[b];
+    const uint32_t* bb = bits + wordoff[b];
+    int nr = 0;
+    bool over = false;
+    for (int g = 0; g < ng && !over; g++) {
+        if (!((bb[g >> 5] >> (g & 31)) & 1u)) continue;
+        if (nr > 0 && re[nr - 1] == g) {
+            re[nr - 1] = g + 1;
+        } else if (nr < kRuns) {
+            rs[nr] = g;
+            re[nr] = g + 1;
+            nr++;
+        } else {
+            over = true;
+        }
+    }
+    if (over || nr == 0) {
+        rs[0] = 0;
+        re[0] = ng;
+        nr = 1;
+    }
+    int T = -1;  // fill gaps <= T
+    if (nr > kMaxWinIntervals) {
+        int lo = 0, hi = ng;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            int cnt = 1;
+            for (int q = 0; q + 1 < nr; q++) cnt += (rs[q + 1] - re[q] > mid);
+            if (cnt <= kMaxWinIntervals) hi = mid;
+            else lo = mid + 1;
+        }
+        T = lo;
+    }
+    int m = 0, d = 0;
+    for (int q = 0; q < nr; q++) {
+        const int a = rs[q];
+        int e = re[q];
+        while (q + 1 < nr && rs[q + 1] - e <= T) e = re[++q];
+        wint[b * kMaxWinIntervals + m] = make_int4(lo4 + 4 * a, 4 * (e - a), 4 * d, 0);
+        for (int g = a; g < e; g++) rank[goff[b] + g] = (uint16_t)(d + g - a);
+        d += e - a;
+        m++;
+    }
+    wcnt[b] = m;
+    wbytes[b] = 16 * d;
+}
+
 // Fill the sliced copy (a warp per slab, a lane per row): FP32 values,
-// BF16 values (if o16) and the window offsets of the slot starts (the
-// window of the block b = ((k + 1) G - 1) / nsl that owns slab k starts at
-// column win[b].x & ~3).  A run of row i (start c, L entries) goes to slot r
-// at start c' = min(c, n - LM), its value q at offset q + c - c'; empty
-// slots (r >= the row's runs, or no row) read LM zeros from the slab's
-// padding column (its first row's first start).
+// BF16 values (if o16) and the compacted-window offsets of the slot starts.
+// A run of row i (start c, L entries) goes to slot r at start
+// c' = min(c, n - LM), its value q at offset q + c - c'; empty slots
+// (r >= the row's runs, or no row) read LM zeros from the slab's padding
+// column (its first row's first start).
 __global__ void k_sell_fill(int n, int nsl, int G, int LM, const int64_t* __restrict__ rp,
                             const int32_t* __restrict__ rptr, const uint8_t* __restrict__ rlen,
                             const int32_t* __restrict__ rst, const int32_t* __restrict__ soff,
-                            const int2* __restrict__ win, const float* __restrict__ v32,
+                            const int2* __restrict__ win, const int* __restrict__ goff,
+                            const uint16_t* __restrict__ rank, const float* __restrict__ v32,
                             const __nv_bfloat16* __restrict__ v16, float* o32, __nv_bfloat16* o16, uint16_t* ors) {
     pdl_entry();
     const int lane = threadIdx.x & 31;
@@ -367,6 +511,7 @@ __global__ void k_sell_fill(int n, int nsl, int G, int LM, const int64_t* __rest
         const int o0 = soff[k], Rs = soff[k + 1] - o0;
         const int b = (int)(((int64_t)(k + 1) * G - 1) / nsl);
         const int lo4 = win[b].x & ~3;
+        const uint16_t* rk = rank + goff[b];
         int r0 = 0, Ri = 0, Li = 0;
         int64_t e0 = 0;
         if (i < n) {
@@ -375,8 +520,7 @@ __global__ void k_sell_fill(int n, int nsl, int G, int LM, const int64_t* __rest
             Li = rlen[i];
             e0 = rp[i];
         }
-        const int f0 = rptr[k * kSlab];
-        const int cpad = rptr[k * kSlab + 1] > f0 ? max(0, slot_start(rst[f0], n, LM)) : 0;
+        const int cpad = slot_pad(rptr, rst, k, n, LM);
         for (int r = 0; r < Rs; r++) {
             int c = cpad, sh = 0;
             const bool has = r < Ri;
@@ -386,7 +530,7 @@ __global__ void k_sell_fill(int n, int nsl, int G, int LM, const int64_t* __rest
                 sh = c0 - c;
             }
             const int64_t slot = (int64_t)o0 + r;
-            ors[slot * kSlab + lane] = (uint16_t)(c - lo4);
+            ors[slot * kSlab + lane] = (uint16_t)(4 * rk[(c - lo4) >> 2] + ((c - lo4) & 3));
             for (int o = 0; o < LM; o++) {
                 const int q = o - sh;
                 const bool hv = has && q >= 0 && q < Li;
@@ -436,8 +580,8 @@ bool sell_attr(uint32_t smem) {
 
 template <int LM>
 bool sell_attrs_lm(uint32_t m16, uint32_t m32) {
-    return sell_attr<LM, __nv_bfloat16, EpiResid>(m16) && sell_attr<LM, __nv_bfloat16, EpiUp0>(m16) &&
-           sell_attr<LM, float, EpiResid>(m32) && sell_attr<LM, float, EpiUp0>(m32) &&
+    return sell_attr<LM, __nv_bfloat16, EpiResid>(m16) && sell_attr<LM, __nv_bfloat16, EpiUp0S>(m16) &&
+           sell_attr<LM, float, EpiResid>(m32) && sell_attr<LM, float, EpiUp0S>(m32) &&
            sell_attr<LM, float, EpiPQ>(m32);
 }
 
@@ -445,9 +589,9 @@ template <int LM, typename V, typename Epi>
 cudaError_t sell_launch_lm(amg_hierarchy* h, int q, const V* val, const float* x, const Epi& epi, double* p1,
                            double* p2, cudaStream_t s) {
     const SellShape sh = sell_shape(h, q);
-    launch_pdl(k_sell<LM, V, Epi>, h->stream_blocks, kStreamThreads, sell_smem_bytes(sh), s,
-        h->lev[0].A.n, h->sell_nsl, h->sell_soff, val, h->sell_rs, x, reinterpret_cast<const int2*>(h->stream_win),
-        sh, epi, p1, p2, h->st);
+    launch_pdl(k_sell<LM, V, Epi>, h->stream_blocks, kStreamThreads, sell_smem_bytes(sh), s, h->lev[0].A.n,
+               h->sell_nsl, h->sell_soff, val, h->sell_rs, x, static_cast<const int4*>(h->sell_wint), h->sell_wcnt,
+               h->sell_wbytes, sh, epi, p1, p2, h->st);
     return cudaGetLastError();
 }
 
@@ -541,10 +685,45 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
         cudaMemcpyAsync(hw.data(), win, sizeof(int2) * G, cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
         cudaStreamSynchronize(h->s) != cudaSuccess)
         return AMG_ERR_CUDA;
+    // compacted windows: group bitmaps, intervals and group ranks
+    std::vector<int> hword(G + 1, 0), hgoff(G + 1, 0);
+    for (int b = 0; b < G; b++) {
+        const int lo4 = hw[b].x & ~3;
+        const int ng = hw[b].y >= lo4 ? ((hw[b].y - lo4) >> 2) + 1 : 0;
+        if ((int64_t)ng * 16 > 4 * 65536) return AMG_OK;  // offsets into the window are 16-bit
+        hgoff[b + 1] = hgoff[b] + ng;
+        hword[b + 1] = hword[b] + (ng + 31) / 32;
+    }
+    int *wordoff = nullptr, *goff = nullptr, *wcnt = nullptr, *wbytes = nullptr;
+    uint32_t* bits = nullptr;
+    uint16_t* rank = nullptr;
+    int4* wint = nullptr;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (dev_alloc(p, bytes, h->s) != cudaSuccess) return false;
+        h->allocs.push_back(*p);
+        return true;
+    };
+    if (!alloc(reinterpret_cast<void**>(&wordoff), sizeof(int) * (G + 1)) ||
+        !alloc(reinterpret_cast<void**>(&goff), sizeof(int) * (G + 1)) ||
+        !alloc(reinterpret_cast<void**>(&wcnt), sizeof(int) * G) ||
+        !alloc(reinterpret_cast<void**>(&wbytes), sizeof(int) * G) ||
+        !alloc(reinterpret_cast<void**>(&bits), sizeof(uint32_t) * std::max(hword[G], 1)) ||
+        !alloc(reinterpret_cast<void**>(&rank), sizeof(uint16_t) * std::max(hgoff[G], 1)) ||
+        !alloc(reinterpret_cast<void**>(&wint), sizeof(int4) * (size_t)G * kMaxWinIntervals))
+        return AMG_ERR_NOMEM;
+    std::vector<int> hwb(G);
+    if (cudaMemcpyAsync(wordoff, hword.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, h->s) != cudaSuccess ||
+        cudaMemcpyAsync(goff, hgoff.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, h->s) != cudaSuccess ||
+        cudaMemsetAsync(bits, 0, sizeof(uint32_t) * std::max(hword[G], 1), h->s) != cudaSuccess)
+        return AMG_ERR_CUDA;
+    launch_pdl(k_sell_mark, gw, 256, 0, h->s, n, nsl, G, LM, F0.run_ptr, F0.run_start, slots, win, wordoff, bits);
+    launch_pdl(k_sell_intervals, G, 32, 0, h->s, G, win, wordoff, goff, bits, wint, wcnt, wbytes, rank);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(hwb.data(), wbytes, sizeof(int) * G, cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
+        cudaStreamSynchronize(h->s) != cudaSuccess)
+        return AMG_ERR_CUDA;
     int64_t xw = 16;
-    for (int b = 0; b < G; b++)
-        xw = std::max<int64_t>(xw, ((int64_t)(hw[b].y + 1 - (hw[b].x & ~3)) * 4 + 15) & ~(int64_t)15);
-    if (xw > 4 * 65536) return AMG_OK;  // window offsets are 16-bit
+    for (int b = 0; b < G; b++) xw = std::max<int64_t>(xw, hwb[b]);
     int nb[2] = {0, 0};
     for (int q = 0; q < 2; q++) {
         const uint32_t vb = (uint32_t)(q == 0 ? vb16 : vb32);
@@ -555,7 +734,7 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
     }
     if (!nb[1] || (with16 && !nb[0])) return AMG_OK;
     launch_pdl(k_sell_fill, gw, 256, 0, h->s, n, nsl, G, LM, F0.A.rowptr, F0.run_ptr, F0.run_len, F0.run_start,
-                                                slots, win, F0.val32, F0.val16, o32, o16, ors);
+               slots, win, goff, rank, F0.val32, F0.val16, o32, o16, ors);
     if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
     h->sell_lm = LM;
     h->sell_nsl = nsl;
@@ -571,6 +750,9 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
     h->stream_nbuf[0] = nb[0];
     h->stream_nbuf[1] = nb[1];
     h->stream_win = reinterpret_cast<int*>(win);
+    h->sell_wint = wint;
+    h->sell_wcnt = wcnt;
+    h->sell_wbytes = wbytes;
     const uint32_t m16 = nb[0] ? sell_smem_bytes(sell_shape(h, 0)) : 0u;
     const uint32_t m32 = sell_smem_bytes(sell_shape(h, 1));
     bool attrs;
@@ -595,7 +777,7 @@ cudaError_t sell_resid(amg_hierarchy* h, const double* f, const float* x, float*
 
 cudaError_t sell_up0(amg_hierarchy* h, const double* r, const float* x, const float* invd, double* z,
                      const double* q, double* part_rz, double* part_zq, int flexible, cudaStream_t s) {
-    const EpiUp0 epi{{r, invd, q}, {8, 4, 8}, flexible ? 3 : 2, z, flexible};
+    const EpiUp0S epi{{r, invd, x, q}, {8, 4, 4, 8}, flexible ? 4 : 3, z, flexible};
     double* p2 = flexible ? part_zq : nullptr;
     if (h->sell_v16) return sell_launch(h, 0, h->sell_v16, x, epi, part_rz, p2, s);
     return sell_launch(h, 1, h->sell_v32, x, epi, part_rz, p2, s);

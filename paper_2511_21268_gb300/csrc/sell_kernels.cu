@@ -26,12 +26,13 @@
 // slots w', w' + 16, ...; the assignment rotates from slab to slab), each
 // lane accumulating its own row, so a slot costs one start-column load, and
 // per value one value load, one vector load and one FMA, every load from
-// shared memory at a compile-time offset.  Every warp writes its 32 partial
-// row sums to the buffer; the slab's epilogue warp (rotating) waits for all
-// 16, adds them in a fixed pairwise tree (deterministic), and runs the epilogue
-// (residual, smoothing with z and r.z, q = K p with p.q) with one lane per
-// row.  Dot products accumulate in the epilogue lanes in slab order and are
-// written as one deterministic partial per block.
+// shared memory at a compile-time offset.  Every compute warp writes its 32
+// partial row sums to the buffer and moves on; a dedicated epilogue warp
+// waits for all 16, adds them in a fixed pairwise tree (deterministic), and
+// runs the epilogue (residual, smoothing with z and r.z, q = K p with p.q)
+// with one lane per row, so no compute warp waits for an epilogue.  Dot
+// products accumulate in the epilogue lanes in slab order and are written
+// as one deterministic partial per block.
 //
 // Every wait on an mbarrier is bounded; on expiry the kernel records
 // AMG_ERR_TIMEOUT in the solve state, waits (again bounded) for its copies
@@ -56,6 +57,9 @@ constexpr int kSellVec = 4;                                 // staged epilogue v
 constexpr int kMaxWinIntervals = 64;                        // window copies per block, at most
 constexpr uint32_t kPartBytes = kStreamWarps * kSlab * 4;   // partial row sums of the 16 warps
 constexpr int kSellBuf = 6;                                 // largest ring
+constexpr int kProdWarp = kStreamWarps;                     // warp 16: producer
+constexpr int kEpiWarp = kStreamWarps + 1;                  // warp 17: epilogues
+constexpr int kSellThreads = (kStreamWarps + 2) * 32;
 constexpr uint32_t kSellCtl = 256;                          // barriers and control words
 
 struct SellShape {
@@ -141,7 +145,7 @@ struct SlotDot<LM, LM, V> {
 // epilogue vectors are read in 16-byte-widened segments of the slab's rows
 // (the vectors are padded for the last slab).
 template <int LM, typename V, typename Epi>
-__global__ void __launch_bounds__(kStreamThreads, 1)
+__global__ void __launch_bounds__(kSellThreads, 1)
     k_sell(int n, int nsl, const int32_t* __restrict__ soff, const V* __restrict__ val, const uint16_t* __restrict__ rs,
            const float* __restrict__ xg, const int4* __restrict__ wint, const int* __restrict__ wcnt,
            const int* __restrict__ wbytes, SellShape shape, Epi epi, double* part1, double* part2, SolveState* st) {
@@ -160,8 +164,6 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     static_assert(kBarBytes + 4 * kSellBuf + 8 <= (int)kSellCtl, "control area");
     int* rsl = reinterpret_cast<int*>(ctl + kBarBytes);                                 // run slots of buffer j
     volatile int* ctrl = reinterpret_cast<int*>(ctl + kBarBytes + 4 * kSellBuf);       // 0 = go on, 1 = give up
-    __shared__ double red[kStreamWarps + 1];
-
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int s0 = (int)((int64_t)blockIdx.x * nsl / gridDim.x);
     const int s1 = (int)((int64_t)(blockIdx.x + 1) * nsl / gridDim.x);
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         mbar_init(bar_win, 1);
         for (int j = 0; j < kSellBuf; j++) {
             mbar_init(bar_full(j), 1);
-            mbar_init(bar_empty(j), kStreamWarps);
+            mbar_init(bar_empty(j), kStreamWarps + 1);  // compute warps + the epilogue warp
             mbar_init(bar_part(j), kStreamWarps);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     __syncthreads();
 
     double acc1 = 0.0, acc2 = 0.0;
-    if (wid == kStreamWarps) {
+    if (wid == kProdWarp) {
         // ------------------------------------------------------------ producer
         // The whole warp loads the slot offsets of the next 32 slabs at once
         // (one coalesced load instead of a dependent load per slab); lane 0
@@ -253,8 +255,32 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                     mbar_wait_bounded(bar_full((k - s0) % nbuf), (uint32_t)((k - s0) / nbuf) & 1u);
             }
         }
+    } else if (wid == kEpiWarp) {
+        // ------------------------------------------------------------ epilogues
+        // slab by slab: wait for the 16 partial row sums, add them in a fixed
+        // pairwise tree, run the epilogue (a lane per row), release the buffer
+        bool ok = true;
+        for (int k = s0; k < s1 && ok; k++) {
+            const int u = (k - s0) / nbuf, j = (k - s0) % nbuf;
+            ok = __all_sync(FULL, !*ctrl && mbar_wait_bounded(bar_part(j), (uint32_t)u & 1u));
+            if (!ok) break;
+            const unsigned char* bv = ring + j * bufstride;
+            const float* part = reinterpret_cast<const float*>(bv + o_part);
+            float t[kStreamWarps];
+#pragma unroll
+            for (int w = 0; w < kStreamWarps; w++) t[w] = part[w * kSlab + lane];
+#pragma unroll
+            for (int h = kStreamWarps / 2; h > 0; h >>= 1)
+#pragma unroll
+                for (int w = 0; w < h; w++) t[w] += t[w + h];
+            const int i = k * kSlab + lane;
+            if (i < n) epi(i, lane, t[0], bv + o_seg, kSegBytes, nullptr, acc1, acc2);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_empty(j));
+        }
+        if (!ok && lane == 0) *ctrl = 1;
     } else {
-        // ------------------------------------------------------------ consumers
+        // ------------------------------------------------------------ compute warps
         bool ok = true;
         if (s0 < s1) ok = __all_sync(FULL, mbar_wait_bounded(bar_win, 0u));
         const uint32_t xbase = smem_addr(xw);  // window offset q at xbase + 4 q
@@ -264,8 +290,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
             if (!ok) break;
             unsigned char* bv = ring + j * bufstride;
             const int R = rsl[j];
-            const int e = (k - s0) % kStreamWarps;              // the slab's epilogue warp ...
-            const int r0 = (wid - e - 1) & (kStreamWarps - 1);  // ... takes the last slot offset
+            const int r0 = (wid + k - s0) & (kStreamWarps - 1);  // rotating slot offset
             const uint32_t va0 = smem_addr(bv) + (uint32_t)sizeof(V) * (uint32_t)lane;
             const uint32_t ra0 = smem_addr(bv + o_rs) + 2u * (uint32_t)lane;
             float a0 = 0.f, a1 = 0.f;
@@ -277,26 +302,10 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
             float* part = reinterpret_cast<float*>(bv + o_part);
             part[wid * kSlab + lane] = a0 + a1;
             __syncwarp();
-            if (lane == 0) mbar_arrive(bar_part(j));
-            if (wid != e) {
-                if (lane == 0) mbar_arrive(bar_empty(j));  // done with buffer j
-                continue;
+            if (lane == 0) {
+                mbar_arrive(bar_part(j));
+                mbar_arrive(bar_empty(j));  // done with buffer j
             }
-            ok = __all_sync(FULL, mbar_wait_bounded(bar_part(j), (uint32_t)u & 1u));
-            if (!ok) break;
-            // pairwise tree over the 16 warp partials (a fixed order)
-            float t[kStreamWarps];
-#pragma unroll
-            for (int w = 0; w < kStreamWarps; w++) t[w] = part[w * kSlab + lane];
-#pragma unroll
-            for (int h = kStreamWarps / 2; h > 0; h >>= 1)
-#pragma unroll
-                for (int w = 0; w < h; w++) t[w] += t[w + h];
-            const float s = t[0];
-            const int i = k * kSlab + lane;
-            if (i < n) epi(i, lane, s, bv + o_seg, kSegBytes, nullptr, acc1, acc2);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar_empty(j));
         }
         if (!ok && lane == 0) *ctrl = 1;
     }
@@ -308,8 +317,17 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         }
         return;
     }
-    if (part1) block_sum_to(acc1, red, part1 + blockIdx.x);
-    if (part2) block_sum_to(acc2, red, part2 + blockIdx.x);
+    if (wid == kEpiWarp) {  // the block's dot-product partials (fixed order)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc1 += __shfl_xor_sync(FULL, acc1, o);
+            acc2 += __shfl_xor_sync(FULL, acc2, o);
+        }
+        if (lane == 0) {
+            if (part1) part1[blockIdx.x] = acc1;
+            if (part2) part2[blockIdx.x] = acc2;
+        }
+    }
 }
 
 // Run slots of each slab (the largest run count of its rows) and the
@@ -352,7 +370,6 @@ __global__ void k_sell_span(int n, int nsl, int LM, const int32_t* __restrict__ 
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nsl; k += nw) {
         const int i = k * kSlab + lane;
-        const int Rs = soff[k + 1] - soff[k];
         const int f0 = rptr[k * kSlab];
         const int cpad = rptr[k * kSlab + 1] > f0 ? max(0, slot_start(rst[f0], n, LM)) : 0;
         int lo = cpad, hi = cpad + LM - 1;
@@ -589,7 +606,7 @@ template <int LM, typename V, typename Epi>
 cudaError_t sell_launch_lm(amg_hierarchy* h, int q, const V* val, const float* x, const Epi& epi, double* p1,
                            double* p2, cudaStream_t s) {
     const SellShape sh = sell_shape(h, q);
-    launch_pdl(k_sell<LM, V, Epi>, h->stream_blocks, kStreamThreads, sell_smem_bytes(sh), s, h->lev[0].A.n,
+    launch_pdl(k_sell<LM, V, Epi>, h->stream_blocks, kSellThreads, sell_smem_bytes(sh), s, h->lev[0].A.n,
                h->sell_nsl, h->sell_soff, val, h->sell_rs, x, static_cast<const int4*>(h->sell_wint), h->sell_wcnt,
                h->sell_wbytes, sh, epi, p1, p2, h->st);
     return cudaGetLastError();

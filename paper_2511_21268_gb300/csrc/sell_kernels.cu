@@ -444,118 +444,192 @@ __global__ void k_sell_mark(int n, int nsl, int G, int LM, const int32_t* __rest
     }
 }
 
-// Intervals of the compacted window of grid block b (a thread block per
-// grid block; its first thread scans the group bitmap): maximal runs of
-// marked groups, at most kMaxWinIntervals of them (the smallest gaps are
-// filled: the threshold T is the least gap length that leaves few enough
-// runs when every gap <= T is copied too).  Writes the runs as (first
-// column, entries, window offset) to wint[b kMaxWinIntervals + q], their
-// count, the window bytes, and the group ranks.  More runs than the scan
-// buffer holds: one interval over the whole range (no compaction).
+// Intervals of the compacted window of grid block b (one warp per grid
+// block): maximal runs of marked groups, found 32 groups at a time (a lane
+// per group; run boundaries by ballot, written in order), at most
+// kMaxWinIntervals of them: the smallest gaps are filled, the threshold T
+// being the least gap length that leaves few enough runs when every gap
+// <= T is copied too.  Writes the runs as (first column, entries, window
+// offset) to wint[b kMaxWinIntervals + q], their count, the window bytes
+// and the group ranks.  More run boundaries than the scan buffer holds:
+// one interval over the whole range (no compaction).
 __global__ void k_sell_intervals(int G, const int2* __restrict__ win, const int* __restrict__ wordoff,
                                  const int* __restrict__ goff, const uint32_t* __restrict__ bits, int4* wint,
                                  int* wcnt, int* wbytes, uint16_t* rank) {
     pdl_entry();
-    constexpr int kRuns = 2048;
-    __shared__ int rs[kRuns], re[kRuns];
-    const int b = blockIdx.x;
-    if (b >= G || threadIdx.x != 0) return;
+    constexpr int kBounds = 4096;  // run boundaries (2 per run)
+    __shared__ int bpos[kBounds];
+    __shared__ int ia[kMaxWinIntervals], ie[kMaxWinIntervals], id[kMaxWinIntervals];
+    __shared__ int nint_s, d_s;
+    const int b = blockIdx.x, lane = threadIdx.x;
+    if (b >= G) return;
     const int lo4 = win[b].x & ~3;
     const int ng = goff[b + 1] - goff[b];
     const uint32_t* bb = bits + wordoff[b];
-    int nr = 0;
-    bool over = false;
-    for (int g = 0; g < ng && !over; g++) {
-        if (!((bb[g >> 5] >> (g & 31)) & 1u)) continue;
-        if (nr > 0 && re[nr - 1] == g) {
-            re[nr - 1] = g + 1;
-        } else if (nr < kRuns) {
-            rs[nr] = g;
-            re[nr] = g + 1;
-            nr++;
-        } else {
-            over = true;
-        }
+    // boundaries: g where marked(g) != marked(g - 1) (marked(-1) = marked(ng) = 0)
+    int nb = 0;
+    bool prev_last = false, over = false;
+    for (int base = 0; base <= ng; base += 32) {
+        const int g = base + lane;
+        const bool m = g < ng && ((bb[g >> 5] >> (g & 31)) & 1u);
+        const bool mp = __shfl_up_sync(FULL, m, 1);
+        const bool prev = lane == 0 ? prev_last : mp;
+        const unsigned bm = __ballot_sync(FULL, g <= ng && m != prev);
+        const int at = nb + __popc(bm & ((1u << lane) - 1u));
+        if (((bm >> lane) & 1u) && at < kBounds) bpos[at] = g;
+        nb += __popc(bm);
+        prev_last = __shfl_sync(FULL, m, 31);
     }
+    if (nb > kBounds) over = true;
+    __syncwarp();
+    int nr = nb / 2;  // runs [bpos[2q], bpos[2q + 1])
     if (over || nr == 0) {
-        rs[0] = 0;
-        re[0] = ng;
+        if (lane == 0) {
+            bpos[0] = 0;
+            bpos[1] = ng;
+        }
         nr = 1;
+        __syncwarp();
     }
     int T = -1;  // fill gaps <= T
     if (nr > kMaxWinIntervals) {
         int lo = 0, hi = ng;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            int cnt = 1;
-            for (int q = 0; q + 1 < nr; q++) cnt += (rs[q + 1] - re[q] > mid);
+            int cnt = 0;
+            for (int q = lane; q + 1 < nr; q += 32) cnt += (bpos[2 * q + 2] - bpos[2 * q + 1] > mid);
+            cnt = 1 + __reduce_add_sync(FULL, cnt);
             if (cnt <= kMaxWinIntervals) hi = mid;
             else lo = mid + 1;
         }
         T = lo;
     }
-    int m = 0, d = 0;
-    for (int q = 0; q < nr; q++) {
-        const int a = rs[q];
-        int e = re[q];
-        while (q + 1 < nr && rs[q + 1] - e <= T) e = re[++q];
-        wint[b * kMaxWinIntervals + m] = make_int4(lo4 + 4 * a, 4 * (e - a), 4 * d, 0);
-        for (int g = a; g < e; g++) rank[goff[b] + g] = (uint16_t)(d + g - a);
-        d += e - a;
-        m++;
+    if (lane == 0) {  // merge runs separated by gaps <= T, assign window offsets
+        int m = 0, d = 0;
+        for (int q = 0; q < nr; q++) {
+            const int a = bpos[2 * q];
+            int e = bpos[2 * q + 1];
+            while (q + 1 < nr && bpos[2 * q + 2] - e <= T) e = bpos[2 * (++q) + 1];
+            ia[m] = a;
+            ie[m] = e;
+            id[m] = d;
+            wint[b * kMaxWinIntervals + m] = make_int4(lo4 + 4 * a, 4 * (e - a), 4 * d, 0);
+            d += e - a;
+            m++;
+        }
+        nint_s = m;
+        d_s = d;
+        wcnt[b] = m;
+        wbytes[b] = 16 * d;
     }
-    wcnt[b] = m;
-    wbytes[b] = 16 * d;
+    __syncwarp();
+    const int m = nint_s;
+    for (int q = 0; q < m; q++)
+        for (int g = ia[q] + lane; g < ie[q]; g += 32) rank[goff[b] + g] = (uint16_t)(id[q] + g - ia[q]);
 }
 
-// Fill the sliced copy (a warp per slab, a lane per row): FP32 values,
-// BF16 values (if o16) and the compacted-window offsets of the slot starts.
-// A run of row i (start c, L entries) goes to slot r at start
-// c' = min(c, n - LM), its value q at offset q + c - c'; empty slots
-// (r >= the row's runs, or no row) read LM zeros from the slab's padding
-// column (its first row's first start).
-__global__ void k_sell_fill(int n, int nsl, int G, int LM, const int64_t* __restrict__ rp,
-                            const int32_t* __restrict__ rptr, const uint8_t* __restrict__ rlen,
-                            const int32_t* __restrict__ rst, const int32_t* __restrict__ soff,
-                            const int2* __restrict__ win, const int* __restrict__ goff,
-                            const uint16_t* __restrict__ rank, const float* __restrict__ v32,
-                            const __nv_bfloat16* __restrict__ v16, float* o32, __nv_bfloat16* o16, uint16_t* ors) {
+// Fill the sliced copy, a thread block per slab: FP32 values, BF16 values
+// (if o16: rounded from the FP32 value, as the BF16 copy of the level is)
+// and the compacted-window offsets of the slot starts.  The slab's rows are
+// consecutive, so their CSR values and run starts are two contiguous ranges:
+// the block stages them in shared memory with coalesced loads (slabs larger
+// than the stage read them from global memory) and writes the outputs in
+// their own order, coalesced.  A run of row i (start c, L entries) goes to
+// slot r at start c' = min(c, n - LM), its value q at offset q + c - c';
+// empty slots (r >= the row's runs, or no row) read LM zeros from the
+// slab's padding column (its first row's first start).
+constexpr int kFillVals = 10240;  // staged values per slab
+constexpr int kFillRuns = 2048;   // staged run starts per slab
+
+__global__ void __launch_bounds__(256) k_sell_fill(int n, int nsl, int G, int LM, const int64_t* __restrict__ rp,
+                                                   const int32_t* __restrict__ rptr, const uint8_t* __restrict__ rlen,
+                                                   const int32_t* __restrict__ rst, const int32_t* __restrict__ soff,
+                                                   const int2* __restrict__ win, const int* __restrict__ goff,
+                                                   const uint16_t* __restrict__ rank, const float* __restrict__ v32,
+                                                   float* o32, __nv_bfloat16* o16, uint16_t* ors) {
     pdl_entry();
-    const int lane = threadIdx.x & 31;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nsl; k += nw) {
-        const int i = k * kSlab + lane;
+    __shared__ float sv[kFillVals];
+    __shared__ int srs[kFillRuns];
+    __shared__ int mr0[kSlab], mri[kSlab], mli[kSlab];
+    __shared__ int64_t me0[kSlab];
+    for (int k = blockIdx.x; k < nsl; k += gridDim.x) {
+        const int a = k * kSlab, e = min(n, a + kSlab);
+        const int64_t ebase = rp[a], eend = rp[e];
+        const int rbase = rptr[a], rend = rptr[e];
+        const bool staged = eend - ebase <= kFillVals && rend - rbase <= kFillRuns;
+        __syncthreads();  // the previous slab's readers are done
+        if (staged) {  // eight loads in flight per thread before the stores
+            constexpr int U = 8;
+            for (int64_t q0 = ebase + threadIdx.x; q0 < eend; q0 += U * blockDim.x) {
+                float t[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int64_t q = q0 + (int64_t)u * blockDim.x;
+                    t[u] = q < eend ? v32[q] : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int64_t q = q0 + (int64_t)u * blockDim.x;
+                    if (q < eend) sv[q - ebase] = t[u];
+                }
+            }
+            for (int q0 = rbase + threadIdx.x; q0 < rend; q0 += U * blockDim.x) {
+                int t[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int q = q0 + u * blockDim.x;
+                    t[u] = q < rend ? rst[q] : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int q = q0 + u * blockDim.x;
+                    if (q < rend) srs[q - rbase] = t[u];
+                }
+            }
+        }
+        if (threadIdx.x < kSlab) {
+            const int i = a + threadIdx.x;
+            int r0 = 0, ri = 0, li = 0;
+            int64_t e0 = 0;
+            if (i < n) {
+                r0 = rptr[i];
+                ri = rptr[i + 1] - r0;
+                li = rlen[i];
+                e0 = rp[i];
+            }
+            mr0[threadIdx.x] = staged ? r0 - rbase : r0;
+            mri[threadIdx.x] = ri;
+            mli[threadIdx.x] = li;
+            me0[threadIdx.x] = staged ? e0 - ebase : e0;
+        }
+        __syncthreads();
         const int o0 = soff[k], Rs = soff[k + 1] - o0;
         const int b = (int)(((int64_t)(k + 1) * G - 1) / nsl);
         const int lo4 = win[b].x & ~3;
         const uint16_t* rk = rank + goff[b];
-        int r0 = 0, Ri = 0, Li = 0;
-        int64_t e0 = 0;
-        if (i < n) {
-            r0 = rptr[i];
-            Ri = rptr[i + 1] - r0;
-            Li = rlen[i];
-            e0 = rp[i];
-        }
         const int cpad = slot_pad(rptr, rst, k, n, LM);
-        for (int r = 0; r < Rs; r++) {
-            int c = cpad, sh = 0;
-            const bool has = r < Ri;
-            if (has) {
-                const int c0 = rst[r0 + r];
-                c = slot_start(c0, n, LM);
-                sh = c0 - c;
+        const int* runs = staged ? srs : rst;
+#pragma unroll 4
+        for (int q = threadIdx.x; q < Rs * kSlab; q += blockDim.x) {  // slot starts
+            const int t = q & (kSlab - 1), r = q / kSlab;
+            const int c = r < mri[t] ? slot_start(runs[mr0[t] + r], n, LM) : cpad;
+            ors[((int64_t)o0 + r) * kSlab + t] = (uint16_t)(4 * rk[(c - lo4) >> 2] + ((c - lo4) & 3));
+        }
+        for (int q = threadIdx.x; q < Rs * LM * kSlab; q += blockDim.x) {  // values
+            const int t = q & (kSlab - 1), ro = q / kSlab;
+            const int r = ro / LM, o = ro - r * LM;
+            float val = 0.f;
+            if (r < mri[t]) {
+                const int c0 = runs[mr0[t] + r];
+                const int qv = o - (c0 - slot_start(c0, n, LM));
+                if (qv >= 0 && qv < mli[t]) {
+                    const int64_t src = me0[t] + (int64_t)r * mli[t] + qv;
+                    val = staged ? sv[src] : v32[src];
+                }
             }
-            const int64_t slot = (int64_t)o0 + r;
-            ors[slot * kSlab + lane] = (uint16_t)(4 * rk[(c - lo4) >> 2] + ((c - lo4) & 3));
-            for (int o = 0; o < LM; o++) {
-                const int q = o - sh;
-                const bool hv = has && q >= 0 && q < Li;
-                const int64_t dst = (slot * LM + o) * kSlab + lane;
-                const int64_t src = e0 + (int64_t)r * Li + q;
-                o32[dst] = hv ? v32[src] : 0.f;
-                if (o16) o16[dst] = hv ? v16[src] : __float2bfloat16_rn(0.f);
-            }
+            const int64_t dst = (((int64_t)o0 + r) * LM + o) * kSlab + t;
+            o32[dst] = val;
+            if (o16) o16[dst] = __float2bfloat16_rn(val);
         }
     }
 }
@@ -750,8 +824,8 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
         }
     }
     if (!nb[1] || (with16 && !nb[0])) return AMG_OK;
-    launch_pdl(k_sell_fill, gw, 256, 0, h->s, n, nsl, G, LM, F0.A.rowptr, F0.run_ptr, F0.run_len, F0.run_start,
-               slots, win, goff, rank, F0.val32, F0.val16, o32, o16, ors);
+    launch_pdl(k_sell_fill, std::min(nsl, 65535), 256, 0, h->s, n, nsl, G, LM, F0.A.rowptr, F0.run_ptr, F0.run_len,
+               F0.run_start, slots, win, goff, rank, F0.val32, o32, o16, ors);
     if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
     h->sell_lm = LM;
     h->sell_nsl = nsl;

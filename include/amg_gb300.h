@@ -126,6 +126,7 @@ typedef struct {
     int64_t staged_slots;  /* value slots of the sliced slabs (padding included), 0 if unused */
     int32_t staged_buffers[2]; /* copy-ring buffers of the staged passes: [0] BF16 values, [1] FP32 */
     int32_t staged_window_bytes; /* largest per-block vector window of the staged passes */
+    int32_t staged_level1; /* 1: level 1 also runs sliced staged passes (plain CSR, FP32 values) */
 } amg_info;
 
 typedef struct amg_hierarchy amg_hierarchy;

@@ -56,7 +56,8 @@ class AmgInfo(ctypes.Structure):
                 ("iter_bytes", ctypes.c_double), ("match_rounds", ctypes.c_int32 * AMG_MAX_LEVELS),
                 ("setup_phase_ms", ctypes.c_double * 12), ("level_format", ctypes.c_int32 * AMG_MAX_LEVELS),
                 ("staged_passes", ctypes.c_int32), ("staged_slots", ctypes.c_int64),
-                ("staged_buffers", ctypes.c_int32 * 2), ("staged_window_bytes", ctypes.c_int32)]
+                ("staged_buffers", ctypes.c_int32 * 2), ("staged_window_bytes", ctypes.c_int32),
+                ("staged_level1", ctypes.c_int32)]
 
 
 class AmgError(RuntimeError):

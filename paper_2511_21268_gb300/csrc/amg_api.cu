@@ -518,7 +518,7 @@ int build(amg_hierarchy* h, const amg_csr* K) {
             }
             RC(dalloc(h, &F.invd32, (size_t)n + 4));
             CK(launch_to_f32(F.invd, F.invd32, n, s));
-            if (l > 0) RC(dalloc(h, &F.f32, n));
+            if (l > 0) RC(dalloc(h, &F.f32, (size_t)n + 4));  // padded: staged segment copies
             // + 4: the staged finest-level passes copy vector windows widened
             // to 16-byte boundaries
             RC(dalloc(h, &F.x32, (size_t)n + 4));
@@ -552,7 +552,10 @@ int build(amg_hierarchy* h, const amg_csr* K) {
     h->hist_cap = kHistCap;
     RC(dalloc(h, &h->hist, kHistCap));
     CK(cudaMemsetAsync(h->st, 0, sizeof(SolveState), s));
-    if (h->o.matrix_format == 2) RC(stream_prepare(h, h->flag));
+    if (h->o.matrix_format == 2) {
+        RC(stream_prepare(h, h->flag));
+        RC(sell_prepare_level1(h, h->flag));
+    }
     return AMG_OK;
 }
 
@@ -570,7 +573,7 @@ double index_bytes(const Level& L) {
 // offsets (8 B per row) and the column index (index_bytes).
 static double fine_structure_bytes(const amg_hierarchy* h) {
     const Level& L0 = h->lev[0];
-    if (h->stream == 2) return (double)L0.nruns * 2.0 + (h->sell_nsl + 1.0) * 4.0;
+    if (h->stream == 2) return (double)L0.nruns * 2.0 + (h->sell[0].nsl + 1.0) * 4.0;
     return index_bytes(L0) + (L0.A.n + 1.0) * 8.0;
 }
 
@@ -588,10 +591,12 @@ void fill_info(amg_hierarchy* h) {
         I.level_format[l] = h->lev[l].run_ptr ? 1 : 0;
     }
     I.staged_passes = h->stream;
-    I.staged_slots = h->stream == 2 ? h->sell_slots * h->sell_lm * 32 : 0;
-    I.staged_buffers[0] = h->stream ? h->stream_nbuf[0] : 0;
-    I.staged_buffers[1] = h->stream ? h->stream_nbuf[1] : 0;
-    I.staged_window_bytes = h->stream ? h->stream_xbytes : 0;
+    const bool sl = h->stream == 2;
+    I.staged_slots = sl ? h->sell[0].slots * h->sell[0].lm * 32 : 0;
+    I.staged_buffers[0] = sl ? h->sell[0].nbuf[0] : h->stream ? h->stream_nbuf[0] : 0;
+    I.staged_buffers[1] = sl ? h->sell[0].nbuf[1] : h->stream ? h->stream_nbuf[1] : 0;
+    I.staged_window_bytes = sl ? h->sell[0].xbytes : h->stream ? h->stream_xbytes : 0;
+    I.staged_level1 = h->sell[1].on;
     I.opc = tot / (double)h->lev[0].A.nnz;
     // algorithmic bytes: one matrix pass = nnz (value + 4) + (n + 1) 8 + x read + y write
     // (value and vector sizes of the V-cycle precision: 8 / 8 in FP64, 4 / 4 in

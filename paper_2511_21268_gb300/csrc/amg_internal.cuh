@@ -131,6 +131,28 @@ struct Level {
     int64_t nruns = 0;
 };
 
+// Sliced copy of one level for the staged passes: slab k (32 consecutive
+// rows, a lane per row) has soff[k + 1] - soff[k] run slots; slot r of lane
+// t holds lm value slots and the 16-bit offset of its first column in the
+// owning block's compacted vector window.
+struct SellLevel {
+    int on = 0;
+    int lm = 0;                    // value slots per run slot (1, 3, 5, 7, 9)
+    int nsl = 0;                   // slabs
+    int64_t slots = 0;             // run slots in all
+    int32_t* soff = nullptr;       // nsl + 1
+    uint16_t* rs = nullptr;        // window offset of each (slot, lane)
+    float* v32 = nullptr;          // FP32 values, slot-major, lane-minor
+    __nv_bfloat16* v16 = nullptr;  // BF16 values (BF16 finest values only)
+    int vbytes[2] = {};            // value area per buffer: [0] BF16, [1] FP32
+    int rbytes = 0;                // offset area per buffer
+    int xbytes = 0;                // largest compacted window
+    int nbuf[2] = {};              // ring buffers: [0] BF16, [1] FP32 values
+    void* wint = nullptr;          // int4 per window interval (kMaxWinIntervals per block)
+    int* wcnt = nullptr;           // window intervals of each block
+    int* wbytes = nullptr;         // compacted window bytes of each block
+};
+
 }  // namespace amg
 
 struct amg_hierarchy {
@@ -186,20 +208,10 @@ struct amg_hierarchy {
     int stream_rbytes[2] = {};  // run-start buffer bytes
     int stream_nbuf[2] = {};    // buffers in the copy ring
     int* stream_win = nullptr;  // int2 per block: first and last column of its rows
-    // sliced copy of the run-encoded finest level (32-row slabs, lane per
-    // row) used by the staged passes when stream == 2
-    int sell_lm = 0;                     // value slots per run slot (odd, 3..9)
-    int sell_nsl = 0;                    // slabs
-    int64_t sell_slots = 0;              // run slots in all
-    int32_t* sell_soff = nullptr;        // nsl + 1: first run slot of each slab
-    uint16_t* sell_rs = nullptr;         // window offset of the start of each (slot, lane)
-    float* sell_v32 = nullptr;           // FP32 values, slot-major, lane-minor
-    __nv_bfloat16* sell_v16 = nullptr;   // BF16 values (BF16 finest values only)
-    int sell_vbytes[2] = {};             // value area per buffer: [0] BF16, [1] FP32
-    int sell_rbytes = 0;                 // start-column area per buffer
-    void* sell_wint = nullptr;           // int4 per window interval (kMaxWinIntervals per block)
-    int* sell_wcnt = nullptr;            // window intervals of each block
-    int* sell_wbytes = nullptr;          // compacted window bytes of each block
+    // sliced copies (32-row slabs, lane per row) used by the staged passes:
+    // [0] the finest level (when stream == 2), [1] level 1 (plain CSR, each
+    // entry a run of length 1)
+    amg::SellLevel sell[2];
     // multi-system solves
     amg::MultiWork* mw = nullptr;
     // learned smoother damping: network buffers, and whether the smoother
@@ -285,6 +297,9 @@ cudaError_t launch_stream_spmv_pq(amg_hierarchy* h, const float* p32, const doub
                                   double* part_pq, double* part_pr, int flexible, cudaStream_t s);
 // sell_kernels.cu
 int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used);
+int sell_prepare_level1(amg_hierarchy* h, int* scratch);
+cudaError_t sell_resid1(amg_hierarchy* h, const float* f, const float* x, float* rbuf, cudaStream_t s);
+cudaError_t sell_upy1(amg_hierarchy* h, const float* f, const float* x, const float* invd, float* y, cudaStream_t s);
 cudaError_t sell_resid(amg_hierarchy* h, const double* f, const float* x, float* rbuf, cudaStream_t s);
 cudaError_t sell_up0(amg_hierarchy* h, const double* r, const float* x, const float* invd, double* z,
                      const double* q, double* part_rz, double* part_zq, int flexible, cudaStream_t s);

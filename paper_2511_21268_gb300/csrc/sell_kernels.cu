@@ -98,6 +98,34 @@ struct EpiUp0S {
     }
 };
 
+// Level 1 (FP32 vectors): down-sweep residual rbuf = f - K x, and the up
+// sweep's smoothed value y = x + (f - K x) / d (the prolongation into the
+// finer level follows as a separate gather).
+struct EpiResidF {
+    const void* vec[1];  // f (FP32)
+    int es[1];
+    int nvec;
+    float* rbuf;
+    __device__ __forceinline__ void operator()(int i, int t, float s, const unsigned char* seg, uint32_t,
+                                               const float*, double&, double&) const {
+        rbuf[i] = reinterpret_cast<const float*>(seg)[t] - s;
+    }
+};
+
+struct EpiUpY {
+    const void* vec[3];  // f, 1/d, x (FP32)
+    int es[3];
+    int nvec;
+    float* y;
+    __device__ __forceinline__ void operator()(int i, int t, float s, const unsigned char* seg, uint32_t ss,
+                                               const float*, double&, double&) const {
+        const float f = reinterpret_cast<const float*>(seg)[t];
+        const float di = reinterpret_cast<const float*>(seg + ss)[t];
+        const float xi = reinterpret_cast<const float*>(seg + 2 * ss)[t];
+        y[i] = fmaf(di, f - s, xi);
+    }
+};
+
 // number of staged vectors an epilogue type can name
 template <typename Epi>
 constexpr int epi_vecs() {
@@ -634,6 +662,13 @@ __global__ void __launch_bounds__(256) k_sell_fill(int n, int nsl, int G, int LM
     }
 }
 
+// int32 copy of row offsets (a plain CSR level's run pointers: every entry
+// a run of one column).
+__global__ void k_rowptr32(int n, const int64_t* __restrict__ rp, int32_t* out) {
+    pdl_entry();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) out[i] = (int32_t)rp[i];
+}
+
 // Window of each grid block: smallest and largest column over its slabs.
 __global__ void k_sell_window(int nsl, int G, const int2* __restrict__ swin, int2* win) {
     pdl_entry();
@@ -658,9 +693,8 @@ __global__ void k_sell_window(int nsl, int G, const int2* __restrict__ swin, int
     if (threadIdx.x == 0) win[b] = k1 > k0 ? make_int2(slo[0], shi[0]) : make_int2(0, 0);
 }
 
-SellShape sell_shape(const amg_hierarchy* h, int q) {
-    return SellShape{(uint32_t)h->stream_xbytes, (uint32_t)h->sell_vbytes[q], (uint32_t)h->sell_rbytes,
-                     h->stream_nbuf[q]};
+SellShape sell_shape(const SellLevel& S, int q) {
+    return SellShape{(uint32_t)S.xbytes, (uint32_t)S.vbytes[q], (uint32_t)S.rbytes, S.nbuf[q]};
 }
 
 template <int LM, typename V, typename Epi>
@@ -677,37 +711,36 @@ bool sell_attrs_lm(uint32_t m16, uint32_t m32) {
 }
 
 template <int LM, typename V, typename Epi>
-cudaError_t sell_launch_lm(amg_hierarchy* h, int q, const V* val, const float* x, const Epi& epi, double* p1,
-                           double* p2, cudaStream_t s) {
-    const SellShape sh = sell_shape(h, q);
-    launch_pdl(k_sell<LM, V, Epi>, h->stream_blocks, kSellThreads, sell_smem_bytes(sh), s, h->lev[0].A.n,
-               h->sell_nsl, h->sell_soff, val, h->sell_rs, x, static_cast<const int4*>(h->sell_wint), h->sell_wcnt,
-               h->sell_wbytes, sh, epi, p1, p2, h->st);
+cudaError_t sell_launch_lm(amg_hierarchy* h, const SellLevel& S, int n, int q, const V* val, const float* x,
+                           const Epi& epi, double* p1, double* p2, cudaStream_t s) {
+    const SellShape sh = sell_shape(S, q);
+    launch_pdl(k_sell<LM, V, Epi>, h->num_sms, kSellThreads, sell_smem_bytes(sh), s, n, S.nsl, S.soff, val, S.rs, x,
+               static_cast<const int4*>(S.wint), S.wcnt, S.wbytes, sh, epi, p1, p2, h->st);
     return cudaGetLastError();
 }
 
 template <typename V, typename Epi>
 cudaError_t sell_launch(amg_hierarchy* h, int q, const V* val, const float* x, const Epi& epi, double* p1,
                         double* p2, cudaStream_t s) {
-    switch (h->sell_lm) {
-        case 3: return sell_launch_lm<3>(h, q, val, x, epi, p1, p2, s);
-        case 5: return sell_launch_lm<5>(h, q, val, x, epi, p1, p2, s);
-        case 7: return sell_launch_lm<7>(h, q, val, x, epi, p1, p2, s);
-        default: return sell_launch_lm<9>(h, q, val, x, epi, p1, p2, s);
+    const SellLevel& S = h->sell[0];
+    const int n = h->lev[0].A.n;
+    switch (S.lm) {
+        case 3: return sell_launch_lm<3>(h, S, n, q, val, x, epi, p1, p2, s);
+        case 5: return sell_launch_lm<5>(h, S, n, q, val, x, epi, p1, p2, s);
+        case 7: return sell_launch_lm<7>(h, S, n, q, val, x, epi, p1, p2, s);
+        default: return sell_launch_lm<9>(h, S, n, q, val, x, epi, p1, p2, s);
     }
 }
 
-}  // namespace
-
-// Build the sliced copy and size the ring; sets h->stream = 2 and returns
-// AMG_OK with *used = 1 when the slabs average at least kMinSlots run slots
-// (enough to occupy the 16 compute warps) and everything fits the
-// shared-memory budget, else leaves the hierarchy unchanged (*used = 0).
-int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
+// Build the sliced copy of one level (rows with runs: rp row offsets, rptr
+// run pointers, rlen run lengths, rst run starts; a plain CSR level passes
+// int32 row offsets as rptr, ones as rlen and its columns as rst) and size
+// its ring.  Leaves S.on = 0 when the slabs average fewer than kMinSlots run
+// slots (too few to occupy the 16 compute warps) or the window and two
+// buffers do not fit the shared-memory budget.
+int prepare_level(amg_hierarchy* h, SellLevel& S, int n, const int64_t* rp, const int32_t* rptr, const uint8_t* rlen,
+                  const int32_t* rst, const float* v32, bool with16, int* scratch, int optin) {
     constexpr int kMinSlots = 16;
-    *used = 0;
-    Level& F0 = h->lev[0];
-    const int n = F0.A.n;
     const int G = h->num_sms;
     if (n < 16) return AMG_OK;
     const int nsl = (n + kSlab - 1) / kSlab;
@@ -717,14 +750,14 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
     h->allocs.push_back(slots);
     const int gw = std::min((nsl + 7) / 8, 8192);
     if (cudaMemsetAsync(scratch, 0, sizeof(int), h->s) != cudaSuccess) return AMG_ERR_CUDA;
-    launch_pdl(k_sell_slots, gw, 256, 0, h->s, n, nsl, F0.run_ptr, F0.run_len, slots, scratch);
+    launch_pdl(k_sell_slots, gw, 256, 0, h->s, n, nsl, rptr, rlen, slots, scratch);
     std::vector<int32_t> hs(nsl + 1);
     int lmax = 0;
     if (cudaMemcpyAsync(hs.data(), slots, sizeof(int32_t) * nsl, cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
         cudaMemcpyAsync(&lmax, scratch, sizeof(int), cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
         cudaStreamSynchronize(h->s) != cudaSuccess)
         return AMG_ERR_CUDA;
-    if (lmax < 2 || lmax > kMaxRunLen) return AMG_OK;
+    if (lmax < 1 || lmax > kMaxRunLen) return AMG_OK;
     const int LM = lmax | 1;
     if (n < LM) return AMG_OK;
     int64_t total = 0;
@@ -745,7 +778,6 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
     if (cudaMemcpyAsync(slots, hs.data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice, h->s) != cudaSuccess)
         return AMG_ERR_CUDA;
     // the sliced copy
-    const bool with16 = F0.val16 != nullptr;
     float* o32 = nullptr;
     __nv_bfloat16* o16 = nullptr;
     uint16_t* ors = nullptr;
@@ -769,7 +801,7 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
     const void* arrays[] = {o32, o16, ors};
     for (const void* a : arrays)
         if (a && (reinterpret_cast<uintptr_t>(a) & 15)) return AMG_OK;
-    launch_pdl(k_sell_span, gw, 256, 0, h->s, n, nsl, LM, F0.run_ptr, F0.run_start, slots, swin);
+    launch_pdl(k_sell_span, gw, 256, 0, h->s, n, nsl, LM, rptr, rst, slots, swin);
     launch_pdl(k_sell_window, G, 256, 0, h->s, nsl, G, swin, win);
     std::vector<int2> hw(G);
     if (cudaGetLastError() != cudaSuccess ||
@@ -807,7 +839,7 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
         cudaMemcpyAsync(goff, hgoff.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, h->s) != cudaSuccess ||
         cudaMemsetAsync(bits, 0, sizeof(uint32_t) * std::max(hword[G], 1), h->s) != cudaSuccess)
         return AMG_ERR_CUDA;
-    launch_pdl(k_sell_mark, gw, 256, 0, h->s, n, nsl, G, LM, F0.run_ptr, F0.run_start, slots, win, wordoff, bits);
+    launch_pdl(k_sell_mark, gw, 256, 0, h->s, n, nsl, G, LM, rptr, rst, slots, win, wordoff, bits);
     launch_pdl(k_sell_intervals, G, 32, 0, h->s, G, win, wordoff, goff, bits, wint, wcnt, wbytes, rank);
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(hwb.data(), wbytes, sizeof(int) * G, cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
@@ -824,37 +856,51 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
         }
     }
     if (!nb[1] || (with16 && !nb[0])) return AMG_OK;
-    launch_pdl(k_sell_fill, std::min(nsl, 65535), 256, 0, h->s, n, nsl, G, LM, F0.A.rowptr, F0.run_ptr, F0.run_len,
-               F0.run_start, slots, win, goff, rank, F0.val32, o32, o16, ors);
+    launch_pdl(k_sell_fill, std::min(nsl, 65535), 256, 0, h->s, n, nsl, G, LM, rp, rptr, rlen, rst, slots, win, goff,
+               rank, v32, o32, o16, ors);
     if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
-    h->sell_lm = LM;
-    h->sell_nsl = nsl;
-    h->sell_soff = slots;
-    h->sell_v32 = o32;
-    h->sell_v16 = o16;
-    h->sell_rs = ors;
-    h->sell_vbytes[0] = (int)vb16;
-    h->sell_vbytes[1] = (int)vb32;
-    h->sell_rbytes = (int)rb;
-    h->sell_slots = total;
-    h->stream_xbytes = (int)xw;
-    h->stream_nbuf[0] = nb[0];
-    h->stream_nbuf[1] = nb[1];
-    h->stream_win = reinterpret_cast<int*>(win);
-    h->sell_wint = wint;
-    h->sell_wcnt = wcnt;
-    h->sell_wbytes = wbytes;
-    const uint32_t m16 = nb[0] ? sell_smem_bytes(sell_shape(h, 0)) : 0u;
-    const uint32_t m32 = sell_smem_bytes(sell_shape(h, 1));
+    S.lm = LM;
+    S.nsl = nsl;
+    S.soff = slots;
+    S.v32 = o32;
+    S.v16 = o16;
+    S.rs = ors;
+    S.vbytes[0] = (int)vb16;
+    S.vbytes[1] = (int)vb32;
+    S.rbytes = (int)rb;
+    S.slots = total;
+    S.xbytes = (int)xw;
+    S.nbuf[0] = nb[0];
+    S.nbuf[1] = nb[1];
+    S.wint = wint;
+    S.wcnt = wcnt;
+    S.wbytes = wbytes;
+    S.on = 1;
+    return AMG_OK;
+}
+
+}  // namespace
+
+// Level 0: the sliced copy of the run-encoded finest level; sets h->stream =
+// 2 and *used = 1 when it applies, else leaves the hierarchy unchanged.
+int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
+    *used = 0;
+    Level& F0 = h->lev[0];
+    SellLevel& S = h->sell[0];
+    const int rc = prepare_level(h, S, F0.A.n, F0.A.rowptr, F0.run_ptr, F0.run_len, F0.run_start, F0.val32,
+                                 F0.val16 != nullptr, scratch, optin);
+    if (rc != AMG_OK || !S.on) return rc;
+    const uint32_t m16 = S.nbuf[0] ? sell_smem_bytes(sell_shape(S, 0)) : 0u;
+    const uint32_t m32 = sell_smem_bytes(sell_shape(S, 1));
     bool attrs;
-    switch (LM) {
+    switch (S.lm) {
         case 3: attrs = sell_attrs_lm<3>(m16 ? m16 : m32, m32); break;
         case 5: attrs = sell_attrs_lm<5>(m16 ? m16 : m32, m32); break;
         case 7: attrs = sell_attrs_lm<7>(m16 ? m16 : m32, m32); break;
         default: attrs = sell_attrs_lm<9>(m16 ? m16 : m32, m32); break;
     }
     if (!attrs) return AMG_ERR_CUDA;
-    h->stream_blocks = G;
+    h->stream_blocks = h->num_sms;
     h->stream = 2;
     *used = 1;
     return AMG_OK;
@@ -862,22 +908,66 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
 
 cudaError_t sell_resid(amg_hierarchy* h, const double* f, const float* x, float* rbuf, cudaStream_t s) {
     const EpiResid epi{{f, nullptr, nullptr}, {8, 0, 0}, 1, rbuf};
-    if (h->sell_v16) return sell_launch(h, 0, h->sell_v16, x, epi, nullptr, nullptr, s);
-    return sell_launch(h, 1, h->sell_v32, x, epi, nullptr, nullptr, s);
+    if (h->sell[0].v16) return sell_launch(h, 0, h->sell[0].v16, x, epi, nullptr, nullptr, s);
+    return sell_launch(h, 1, h->sell[0].v32, x, epi, nullptr, nullptr, s);
 }
 
 cudaError_t sell_up0(amg_hierarchy* h, const double* r, const float* x, const float* invd, double* z,
                      const double* q, double* part_rz, double* part_zq, int flexible, cudaStream_t s) {
     const EpiUp0S epi{{r, invd, x, q}, {8, 4, 4, 8}, flexible ? 4 : 3, z, flexible};
     double* p2 = flexible ? part_zq : nullptr;
-    if (h->sell_v16) return sell_launch(h, 0, h->sell_v16, x, epi, part_rz, p2, s);
-    return sell_launch(h, 1, h->sell_v32, x, epi, part_rz, p2, s);
+    if (h->sell[0].v16) return sell_launch(h, 0, h->sell[0].v16, x, epi, part_rz, p2, s);
+    return sell_launch(h, 1, h->sell[0].v32, x, epi, part_rz, p2, s);
 }
 
 cudaError_t sell_spmv_pq(amg_hierarchy* h, const float* p32, const double* p, const double* r, double* q,
                          double* part_pq, double* part_pr, int flexible, cudaStream_t s) {
     const EpiPQ epi{{p, r, nullptr}, {8, 8, 0}, flexible ? 2 : 1, q, flexible};
-    return sell_launch(h, 1, h->sell_v32, p32, epi, part_pq, flexible ? part_pr : nullptr, s);
+    return sell_launch(h, 1, h->sell[0].v32, p32, epi, part_pq, flexible ? part_pr : nullptr, s);
+}
+
+// Level 1 (plain CSR, FP32 values): the sliced copy with every entry a run
+// of one column, when the hierarchy is mixed precision, has a level below
+// level 1, fits int32 entry offsets, and the layout applies.
+int sell_prepare_level1(amg_hierarchy* h, int* scratch) {
+    SellLevel& S = h->sell[1];
+    S.on = 0;
+    if (!h->mixed || h->nlev < 3 || h->stream != 2) return AMG_OK;
+    Level& L1 = h->lev[1];
+    const int n = L1.A.n;
+    if (n < 16 * kSlab || L1.A.nnz >= INT32_MAX || !L1.val32) return AMG_OK;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return AMG_ERR_CUDA;
+    int32_t* rp32 = nullptr;
+    uint8_t* ones = nullptr;
+    if (dev_alloc(reinterpret_cast<void**>(&rp32), sizeof(int32_t) * (n + 1), h->s) != cudaSuccess)
+        return AMG_ERR_NOMEM;
+    h->allocs.push_back(rp32);
+    if (dev_alloc(reinterpret_cast<void**>(&ones), (size_t)n + 16, h->s) != cudaSuccess) return AMG_ERR_NOMEM;
+    h->allocs.push_back(ones);
+    if (cudaMemsetAsync(ones, 1, (size_t)n + 16, h->s) != cudaSuccess) return AMG_ERR_CUDA;
+    launch_pdl(k_rowptr32, std::min((n + 256) / 256, 4096), 256, 0, h->s, n, L1.A.rowptr, rp32);
+    const int rc = prepare_level(h, S, n, L1.A.rowptr, rp32, ones, L1.A.col, L1.val32, false, scratch, optin);
+    if (rc != AMG_OK || !S.on) return rc;
+    if (S.lm != 1) {  // every run has one entry here
+        S.on = 0;
+        return AMG_OK;
+    }
+    const uint32_t m32 = sell_smem_bytes(sell_shape(S, 1));
+    if (!sell_attr<1, float, EpiResidF>(m32) || !sell_attr<1, float, EpiUpY>(m32)) return AMG_ERR_CUDA;
+    return AMG_OK;
+}
+
+cudaError_t sell_resid1(amg_hierarchy* h, const float* f, const float* x, float* rbuf, cudaStream_t s) {
+    const EpiResidF epi{{f}, {4}, 1, rbuf};
+    return sell_launch_lm<1>(h, h->sell[1], h->lev[1].A.n, 1, h->sell[1].v32, x, epi, nullptr, nullptr, s);
+}
+
+cudaError_t sell_upy1(amg_hierarchy* h, const float* f, const float* x, const float* invd, float* y, cudaStream_t s) {
+    const EpiUpY epi{{f, invd, x}, {4, 4, 4}, 3, y};
+    return sell_launch_lm<1>(h, h->sell[1], h->lev[1].A.n, 1, h->sell[1].v32, x, epi, nullptr, nullptr, s);
 }
 
 }  // namespace amg

@@ -110,6 +110,18 @@ __global__ void k_restrict(int nc, const int32_t* __restrict__ mptr, const int32
     }
 }
 
+// Prolongation as a gather over the finer level's rows: x_f[c] +=
+// p_c y[agg[c]] (the same FMA per row as scattering y over the aggregates'
+// members).
+template <typename A>
+__global__ void k_prolong(int n, const int32_t* __restrict__ agg, const double* __restrict__ pval,
+                          const A* __restrict__ y, A* xf, const SolveState* st) {
+    pdl_entry();
+    DONE_GUARD(st);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        xf[c] = fma((A)pval[c], y[agg[c]], xf[c]);
+}
+
 // Coarsest level: e = A^-1 f with the dense FP64 symmetric inverse
 // (row-major), then prolongation into the finer level, or (single-level
 // hierarchy) z = e with the partial r.z (and z.q).
@@ -460,6 +472,10 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
                         prof_mark(h, 1, 1, s);
                         return;
                     }
+                    if (l == 1 && h->sell[1].on) {
+                        sell_resid1(h, static_cast<const float*>(Vw::f(F)), xc, rb, s);
+                        return;
+                    }
                 }
                 with_rpw(rpw, [&](auto R) {
                     launch_pdl(k_resid<decltype(R)::value, A, M, FT, A>, nb, kBlock, 0, s, n, mat, fp, xc, rb, st);
@@ -522,6 +538,15 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
             } else {
                 Level& G = h->lev[l - 1];
                 A* xf = xcur[l - 1];
+                if constexpr (std::is_same_v<A, float>) {
+                    if (l == 1 && h->sell[1].on) {  // y = smoothed level 1, then the gather into level 0
+                        A* y = xalt[1];
+                        sell_upy1(h, static_cast<const float*>(Vw::f(F)), xc, Vw::invd(F), y, s);
+                        launch_pdl(k_prolong<A>, vec_blocks(G.A.n, sms), kBlock, 0, s, G.A.n, G.agg, G.pval, y, xf,
+                                   st);
+                        return;
+                    }
+                }
                 with_rpw(rpw, [&](auto R) {
                     launch_pdl(k_up<decltype(R)::value, A, M>, nb, kBlock, 0, s,
                         n, mat, Vw::f(F), xc, Vw::invd(F), G.mem_ptr, G.mem_idx, G.pval, xf, st);

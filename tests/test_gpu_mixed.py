@@ -89,8 +89,9 @@ def _expected_staged_kind(prob):
 @pytest.mark.parametrize("d,n,p", [(3, 14, 3), (3, 16, 2), (3, 10, 4), (2, 40, 2)])
 def test_staged_finest_passes_kind_and_vcycle(prec, d, n, p):
     """Both staged finest-level layouts (sliced slabs with LM = 5, 7, 9 and
-    lane-per-run slabs) give the FP64 oracle's V-cycle within the precision's
-    bound, and the layout follows the slab run-count rule."""
+    lane-per-run slabs), with level 1 sliced too where it applies, give the
+    FP64 oracle's V-cycle within the precision's bound, and the layout follows
+    the slab run-count rule."""
     prob = I.poisson_box(d, n, p)
     Ho = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=20)
     H = A.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=20, precision=prec)
@@ -99,6 +100,10 @@ def test_staged_finest_passes_kind_and_vcycle(prec, d, n, p):
     assert H.info.staged_passes == kind
     if kind == 2:
         assert H.info.staged_slots >= prob.nnz
+    # level 1 (plain CSR) is sliced as well when the finest level is and it
+    # has at least 16 slabs of rows above a coarser level
+    expect1 = int(kind == 2 and H.num_levels >= 3 and H.info.n[1] >= 16 * 32)
+    assert H.info.staged_level1 == expect1
     r = np.random.default_rng(5).standard_normal(prob.n)
     z = H.vcycle(gpu(r)).cpu().numpy()
     zo = Ho.vcycle(r)

@@ -322,8 +322,29 @@ __global__ void __launch_bounds__(kSellThreads, 1)
             const uint32_t va0 = smem_addr(bv) + (uint32_t)sizeof(V) * (uint32_t)lane;
             const uint32_t ra0 = smem_addr(bv + o_rs) + 2u * (uint32_t)lane;
             float a0 = 0.f, a1 = 0.f;
+            int r = r0;
+            if constexpr (LM == 1) {  // one entry per slot: four slots in flight
+                float a2 = 0.f, a3 = 0.f;
 #pragma unroll 1
-            for (int r = r0; r < R; r += kStreamWarps) {
+                for (; r + 3 * kStreamWarps < R; r += 4 * kStreamWarps) {
+                    uint32_t xa[4];
+                    float v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const uint32_t ru = (uint32_t)(r + u * kStreamWarps);
+                        xa[u] = xbase + 4u * lds_u16(ra0 + ru * (uint32_t)(kSlab * 2));
+                        v[u] = lds_val_at<0>(va0 + ru * (uint32_t)(kSlab * sizeof(V)), static_cast<const V*>(nullptr));
+                    }
+                    a0 = fmaf(v[0], lds_x<0>(xa[0]), a0);
+                    a1 = fmaf(v[1], lds_x<0>(xa[1]), a1);
+                    a2 = fmaf(v[2], lds_x<0>(xa[2]), a2);
+                    a3 = fmaf(v[3], lds_x<0>(xa[3]), a3);
+                }
+                a0 += a2;
+                a1 += a3;
+            }
+#pragma unroll 1
+            for (; r < R; r += kStreamWarps) {
                 const uint32_t xa = xbase + 4u * lds_u16(ra0 + (uint32_t)r * (uint32_t)(kSlab * 2));
                 SlotDot<0, LM, V>::run(va0 + (uint32_t)r * (uint32_t)(LM * kSlab * sizeof(V)), xa, a0, a1);
             }
@@ -423,8 +444,8 @@ __global__ void k_sell_span(int n, int nsl, int LM, const int32_t* __restrict__ 
 // g = (c - lo4) / 4, lo4 = win[b].x & ~3; only groups some slot reads are
 // copied, in order, and group g lands at window offset 4 rank[goff[b] + g].
 // k_sell_mark sets bit g of the block's group bitmap (from word
-// wordoff[b]) for every group a slot reads; the lanes of a warp (one slot
-// of 32 neighbouring rows) OR their masks over two words first.
+// wordoff[b]) for every group a slot reads; lanes of a warp whose groups
+// fall in the same word OR their masks first (one atomic per word).
 __device__ __forceinline__ int slot_pad(const int32_t* __restrict__ rptr, const int32_t* __restrict__ rst, int k,
                                         int n, int LM) {
     const int f0 = rptr[k * kSlab];
@@ -451,23 +472,21 @@ __global__ void k_sell_mark(int n, int nsl, int G, int LM, const int32_t* __rest
         const int cpad = slot_pad(rptr, rst, k, n, LM);
         for (int r = 0; r < Rs; r++) {
             const int c = r < Ri ? slot_start(rst[r0 + r], n, LM) : cpad;
-            const int g0 = (c - lo4) >> 2, g1 = (c + LM - 1 - lo4) >> 2;
-            const int w0 = __reduce_min_sync(FULL, g0) >> 5;  // the warp's first word
-            uint32_t m0 = 0, m1 = 0;
-            bool alone = false;
+            const int g0 = (c - lo4) >> 2, g1 = (c + LM - 1 - lo4) >> 2;  // at most 3 groups, 2 words
+            const int wa = g0 >> 5, wb = g1 >> 5;
+            uint32_t ma = 0, mb = 0;
             for (int g = g0; g <= g1; g++) {
-                const int d = g - w0 * 32;
-                if (d < 32) m0 |= 1u << d;
-                else if (d < 64) m1 |= 1u << (d - 32);
-                else alone = true;
+                if ((g >> 5) == wa) ma |= 1u << (g & 31);
+                else mb |= 1u << (g & 31);
             }
-            if (alone)  // groups beyond the two shared words
-                for (int g = g0; g <= g1; g++)
-                    if (g - w0 * 32 >= 64) atomicOr(bb + (g >> 5), 1u << (g & 31));
-            m0 = __reduce_or_sync(FULL, m0);
-            m1 = __reduce_or_sync(FULL, m1);
-            if (lane == 0 && m0) atomicOr(bb + w0, m0);
-            if (lane == 1 && m1) atomicOr(bb + w0 + 1, m1);
+            // lanes sharing a word OR their masks; the lowest of them writes
+            const unsigned pa = __match_any_sync(FULL, wa);
+            ma = __reduce_or_sync(pa, ma);
+            if (lane == __ffs(pa) - 1) atomicOr(bb + wa, ma);
+            const bool two = wb != wa;
+            const unsigned pb = __match_any_sync(FULL, two ? wb : -1);
+            mb = __reduce_or_sync(pb, mb);
+            if (two && lane == __ffs(pb) - 1) atomicOr(bb + wb, mb);
         }
     }
 }
@@ -560,31 +579,30 @@ __global__ void k_sell_intervals(int G, const int2* __restrict__ win, const int*
 // (if o16: rounded from the FP32 value, as the BF16 copy of the level is)
 // and the compacted-window offsets of the slot starts.  The slab's rows are
 // consecutive, so their CSR values and run starts are two contiguous ranges:
-// the block stages them in shared memory with coalesced loads (slabs larger
-// than the stage read them from global memory) and writes the outputs in
-// their own order, coalesced.  A run of row i (start c, L entries) goes to
+// the block stages them in shared memory (sized for the largest slab: cap
+// values, then capr run starts) with coalesced loads and writes the outputs
+// in their own order, coalesced.  A run of row i (start c, L entries) goes to
 // slot r at start c' = min(c, n - LM), its value q at offset q + c - c';
 // empty slots (r >= the row's runs, or no row) read LM zeros from the
 // slab's padding column (its first row's first start).
-constexpr int kFillVals = 10240;  // staged values per slab
-constexpr int kFillRuns = 2048;   // staged run starts per slab
-
-__global__ void __launch_bounds__(256) k_sell_fill(int n, int nsl, int G, int LM, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(256) k_sell_fill(int n, int nsl, int G, int LM, int cap, int capr,
+                                                   const int64_t* __restrict__ rp,
                                                    const int32_t* __restrict__ rptr, const uint8_t* __restrict__ rlen,
                                                    const int32_t* __restrict__ rst, const int32_t* __restrict__ soff,
                                                    const int2* __restrict__ win, const int* __restrict__ goff,
                                                    const uint16_t* __restrict__ rank, const float* __restrict__ v32,
                                                    float* o32, __nv_bfloat16* o16, uint16_t* ors) {
     pdl_entry();
-    __shared__ float sv[kFillVals];
-    __shared__ int srs[kFillRuns];
+    extern __shared__ __align__(16) unsigned char fill_smem[];
+    float* sv = reinterpret_cast<float*>(fill_smem);
+    int* srs = reinterpret_cast<int*>(fill_smem + 4 * (size_t)cap);
     __shared__ int mr0[kSlab], mri[kSlab], mli[kSlab];
     __shared__ int64_t me0[kSlab];
     for (int k = blockIdx.x; k < nsl; k += gridDim.x) {
         const int a = k * kSlab, e = min(n, a + kSlab);
         const int64_t ebase = rp[a], eend = rp[e];
         const int rbase = rptr[a], rend = rptr[e];
-        const bool staged = eend - ebase <= kFillVals && rend - rbase <= kFillRuns;
+        const bool staged = eend - ebase <= cap && rend - rbase <= capr;
         __syncthreads();  // the previous slab's readers are done
         if (staged) {  // eight loads in flight per thread before the stores
             constexpr int U = 8;
@@ -856,8 +874,14 @@ int prepare_level(amg_hierarchy* h, SellLevel& S, int n, const int64_t* rp, cons
         }
     }
     if (!nb[1] || (with16 && !nb[0])) return AMG_OK;
-    launch_pdl(k_sell_fill, std::min(nsl, 65535), 256, 0, h->s, n, nsl, G, LM, rp, rptr, rlen, rst, slots, win, goff,
-               rank, v32, o32, o16, ors);
+    // stage: the largest slab's values and run starts (within the opt-in budget)
+    const int capr = (int)std::min<int64_t>((int64_t)rmax * kSlab, (optin - 1024) / 8);
+    const int cap = (int)std::min<int64_t>((int64_t)capr * LM, (optin - 1024 - 4 * (int64_t)capr) / 4);
+    const size_t fsm = 4 * (size_t)cap + 4 * (size_t)capr;
+    if (cudaFuncSetAttribute(k_sell_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm) != cudaSuccess)
+        return AMG_ERR_CUDA;
+    launch_pdl(k_sell_fill, std::min(nsl, 65535), 256, fsm, h->s, n, nsl, G, LM, cap, capr, rp, rptr, rlen, rst,
+               slots, win, goff, rank, v32, o32, o16, ors);
     if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
     S.lm = LM;
     S.nsl = nsl;

@@ -547,15 +547,21 @@ def run_ours(args):
         kbytes = None
         infos = []
         for _ in range(args.steps):
-            it, rr, info, kt = step(profile=True)
-            ms_sum += kt[0]
-            cnt_sum += kt[1]
-            kbytes = kt[2]
+            it, rr, info, _ = step()
             infos.append((it, rr, info))
         e1.record(stream)
         torch.cuda.synchronize()
         launches = A.amg_kernel_launches() - l0
         torch.cuda.nvtx.range_pop()
+        # per-kernel durations: event-record nodes around the finest-level
+        # passes inside the iteration graph, in as many profiled steps run
+        # right after the timed ones (their nodes stay out of the timed steps)
+        for _ in range(args.steps):
+            _, _, _, kt = step(profile=True)
+            ms_sum += kt[0]
+            cnt_sum += kt[1]
+            kbytes = kt[2]
+        torch.cuda.synchronize()
         clk = clocks.stop() if clocks else None
         barrier(dist)
         elapsed_ms = max_over_ranks(dist, e0.elapsed_time(e1))
@@ -640,12 +646,15 @@ def run_ours(args):
             mms = np.zeros(3)
             mcnt = np.zeros(3, np.int64)
             for _ in range(args.steps):
-                mu, mit, mrr, minfo, mkt = mstep(profile=True)
-                mms += mkt[0]
-                mcnt += mkt[1]
+                mu, mit, mrr, minfo, _ = mstep()
             m1.record(stream)
             torch.cuda.synchronize()
             torch.cuda.nvtx.range_pop()
+            for _ in range(args.steps):  # per-kernel durations, as for the FP64 leg
+                _, _, _, _, mkt = mstep(profile=True)
+                mms += mkt[0]
+                mcnt += mkt[1]
+            torch.cuda.synchronize()
             m_ms = max_over_ranks(dist, m0.elapsed_time(m1)) / args.steps
             err = float(torch.linalg.norm(mu - ref_u) / torch.linalg.norm(ref_u))
             mavg = mms / np.maximum(mcnt, 1)
@@ -724,6 +733,9 @@ def run_ours(args):
             "vcycle_ms": vcycle_ms, "vcycle_gbps": vinfo.vcycle_bytes / (vcycle_ms * 1e-3) / 1e9,
             "throughput_systems_per_s": world * args.steps / (elapsed_ms * 1e-3),
             "roofline": roof, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches), "mixed": mixed,
+            "kernel_timing": "CUDA event-record nodes on the library's stream around each finest-level pass "
+                             "inside the iteration graph, over as many profiled steps run right after the "
+                             "timed (unprofiled) steps",
             "learned": learned, "batched": batched, "annulus_learned": annulus}
     if mixed is not None:
         mixed["roofline"]["peak"] = peak

@@ -127,6 +127,8 @@ typedef struct {
     int32_t staged_buffers[2]; /* copy-ring buffers of the staged passes: [0] BF16 values, [1] FP32 */
     int32_t staged_window_bytes; /* largest per-block vector window of the staged passes */
     int32_t staged_level1; /* 1: level 1 also runs sliced staged passes (plain CSR, FP32 values) */
+    double graph_build_ms; /* host time capturing and instantiating the iteration graph in the last
+                              solve (0 when the hierarchy's graph was reused) */
 } amg_info;
 
 typedef struct amg_hierarchy amg_hierarchy;
@@ -325,6 +327,17 @@ int amg_free(amg_hierarchy* h);
 
 /* Static description of a status code. */
 const char* amg_strerror(int code);
+
+/* Self-test of the bounded waits of the staged passes (the mbarrier waits of
+ * the bulk-copy pipelines, which on expiry end the kernel with
+ * AMG_ERR_TIMEOUT instead of hanging).  Runs one thread on the current
+ * device that waits, with a limit of limit_ms (0 < limit_ms <= 1000), on an
+ * mbarrier that nothing completes and then on one whose phase it completed
+ * itself.  *timed_out = 1 when the first wait gave up; *completed = 1 when
+ * the second returned.  Synchronous; returns AMG_OK, AMG_ERR_ARG,
+ * AMG_ERR_NOMEM or AMG_ERR_CUDA.  No GPU fault or hang is involved: the
+ * waits are bounded. */
+int amg_staged_wait_selftest(double limit_ms, int32_t* timed_out, int32_t* completed);
 
 /* Text of the last CUDA runtime error seen by this thread ("" if none). */
 const char* amg_last_cuda_error(void);

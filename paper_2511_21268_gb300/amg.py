@@ -57,7 +57,7 @@ class AmgInfo(ctypes.Structure):
                 ("setup_phase_ms", ctypes.c_double * 12), ("level_format", ctypes.c_int32 * AMG_MAX_LEVELS),
                 ("staged_passes", ctypes.c_int32), ("staged_slots", ctypes.c_int64),
                 ("staged_buffers", ctypes.c_int32 * 2), ("staged_window_bytes", ctypes.c_int32),
-                ("staged_level1", ctypes.c_int32)]
+                ("staged_level1", ctypes.c_int32), ("graph_build_ms", ctypes.c_double)]
 
 
 class AmgError(RuntimeError):
@@ -104,6 +104,7 @@ _SIGS = {
                                       ctypes.c_int32, ctypes.c_uint64, ctypes.c_float, ctypes.c_void_p]),
     "amg_mpnn_select": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_staged_wait_selftest": (ctypes.c_int, [ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "amg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "amg_last_cuda_error": (ctypes.c_char_p, []),
 }
@@ -132,6 +133,15 @@ def lib(build: bool = True):
 def _check(rc: int, what: str):
     if rc != AMG_OK:
         raise AmgError(rc, what)
+
+
+def amg_staged_wait_selftest(limit_ms: float = 2.0):
+    """(timed_out, completed) of the bounded-wait self-test of the staged
+    passes: a wait that nothing completes must give up after limit_ms, a
+    completed one must return."""
+    to, done = ctypes.c_int32(-1), ctypes.c_int32(-1)
+    _check(lib().amg_staged_wait_selftest(limit_ms, ctypes.byref(to), ctypes.byref(done)), "amg_staged_wait_selftest")
+    return to.value, done.value
 
 
 def amg_strerror(code: int) -> str:

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -899,7 +900,9 @@ static int run_solve(amg_hierarchy* h, int32_t* iters) {
     cudaStream_t s = h->s;
     CK(cudaEventRecord(h->ev0, s));
     CK(enqueue_pcg_start(h, s));
+    h->info.graph_build_ms = 0.0;
     if (!h->graph) {
+        const auto tb0 = std::chrono::steady_clock::now();
         cudaGraph_t g;
         const long long before = amg::g_launches.load();
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -921,6 +924,8 @@ static int run_solve(amg_hierarchy* h, int32_t* iters) {
             return cuda_fail(e, "cudaGraphInstantiate");
         }
         h->graph_iters = kGraphIters;
+        h->info.graph_build_ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tb0).count();
     }
     const int max_launches = h->itmax / kGraphIters + 2;
     int it_before = 0;

@@ -72,13 +72,14 @@ __device__ __forceinline__ bool mbar_try_wait_suspend(uint32_t bar, uint32_t par
 // Bounded wait for phase `parity` of the mbarrier, suspending in the
 // barrier between polls (the hardware resumes the waiter as soon as the
 // phase completes; a sleep between polls instead cost microseconds per
-// wait); every lane of a warp may call it together.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// wait); every lane of a warp may call it together.  `limit`: clock cycles
+// before giving up (about 2 s by default).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long limit = kWaitCycles) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (int it = 0; it < kWaitIters; it++) {
         if (mbar_try_wait_suspend(bar, parity, 20000u)) return true;
-        if (clock64() - t0 > kWaitCycles) break;
+        if (clock64() - t0 > limit) break;
     }
     return false;
 }

@@ -531,4 +531,39 @@ cudaError_t launch_stream_spmv_pq(amg_hierarchy* h, const float* p32, const doub
     return dispatch(h, 1, L0.val32t, p32, epi, part_pq, flexible ? part_pr : nullptr, s);
 }
 
+// Self-test of the bounded mbarrier wait of the staged passes: one thread
+// waits, with a limit of `limit` cycles, on a barrier that nothing ever
+// completes (it must give up) and on one whose phase it completes itself
+// (it must return at once).
+__global__ void k_wait_probe(long long limit, int* out) {
+    __shared__ __align__(8) uint64_t bars[2];
+    if (threadIdx.x != 0) return;
+    const uint32_t b0 = smem_addr(&bars[0]), b1 = smem_addr(&bars[1]);
+    mbar_init(b0, 1);
+    mbar_init(b1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    out[0] = mbar_wait_bounded(b0, 0u, limit) ? 0 : 1;  // never completed: expires
+    mbar_arrive(b1);
+    out[1] = mbar_wait_bounded(b1, 0u, limit) ? 1 : 0;  // completed phase 0
+}
+
 }  // namespace amg
+
+int amg_staged_wait_selftest(double limit_ms, int32_t* timed_out, int32_t* completed) {
+    if (!timed_out || !completed || !(limit_ms > 0.0) || limit_ms > 1000.0) return AMG_ERR_ARG;
+    int dev = 0, khz = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess)
+        return AMG_ERR_CUDA;
+    int* d = nullptr;
+    if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) return AMG_ERR_NOMEM;
+    int hbuf[2] = {-1, -1};
+    const long long limit = (long long)(limit_ms * (double)khz);  // kHz x ms = cycles
+    amg::k_wait_probe<<<1, 32>>>(limit, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(hbuf, d, sizeof(hbuf), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return AMG_ERR_CUDA;
+    *timed_out = hbuf[0];
+    *completed = hbuf[1];
+    return AMG_OK;
+}

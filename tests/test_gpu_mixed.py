@@ -112,3 +112,18 @@ def test_staged_finest_passes_kind_and_vcycle(prec, d, n, p):
     assert err <= VCYCLE_ERR[prec]
     g = H.solve(gpu(prob.F), rtol=1e-8)
     assert g["status"] == 0 and g["relres"] <= 1e-8
+
+
+def test_staged_wait_expires_and_context_stays_usable():
+    """The bounded mbarrier wait of the staged passes gives up on a barrier
+    that nothing completes (status, no hang) and returns on a completed one;
+    the device is usable afterwards."""
+    import time
+    t0 = time.perf_counter()
+    timed_out, completed = A.amg_staged_wait_selftest(2.0)
+    assert timed_out == 1 and completed == 1
+    assert time.perf_counter() - t0 < 5.0
+    prob = I.poisson_box(3, 9, 3)
+    H = A.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=20, precision=A.AMG_FP32_BF16FINE)
+    g = H.solve(gpu(prob.F), rtol=1e-8)
+    assert g["status"] == 0 and g["relres"] <= 1e-8

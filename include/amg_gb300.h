@@ -96,6 +96,13 @@ typedef struct {
                                     entries, rows < 65536 entries) of consecutive columns, as in
                                     tensor-product IgA matrices; 2 = as 1, and the mixed-precision
                                     passes stream the matrix into shared memory by bulk copies (2) */
+    const float* mpnn_weights;   /* NULL, or the weights of the damping network (AMG_MPNN_NPARAM
+                                    floats in the layout of amg_mpnn_apply; DEVICE pointer, read
+                                    during amg_setup only).  Setup then installs the learned damping
+                                    exactly as amg_mpnn_apply(h, mpnn_weights, mpnn_bf16) right after
+                                    it would; the finest level's features and network run on a
+                                    second stream alongside the coarse-level setup (NULL) */
+    int32_t mpnn_bf16;           /* 1: weights rounded to BF16, 0: FP32, for mpnn_weights (1) */
 } amg_opts;
 
 #define AMG_MAX_LEVELS 32
@@ -117,7 +124,9 @@ typedef struct {
      * checks, [1] l1 diagonals and test vector, [2] edge weights,
      * [3] matching rounds, [4] aggregation, [5] Galerkin products,
      * [6] composite maps and member lists, [7] coarsest inverse,
-     * [8] precision copies and solve workspace */
+     * [8] precision copies and solve workspace, [9] learned damping at the
+     * end of a setup with mpnn_weights (network on the coarse levels, wait for
+     * the finest level's evaluation, install) */
     double setup_phase_ms[12];
     int32_t level_format[AMG_MAX_LEVELS]; /* 1 = run-encoded columns, 0 = plain CSR */
     int32_t staged_passes; /* finest-level passes of a mixed-precision solve: 0 = row-group

@@ -45,7 +45,7 @@ class AmgOpts(ctypes.Structure):
                 ("testvec_sweeps", ctypes.c_int32), ("testvec_kind", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("stag", ctypes.c_double), ("max_match_rounds", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("flexible", ctypes.c_int32), ("resid_replace_every", ctypes.c_int32),
-                ("matrix_format", ctypes.c_int32)]
+                ("matrix_format", ctypes.c_int32), ("mpnn_weights", ctypes.c_void_p), ("mpnn_bf16", ctypes.c_int32)]
 
 
 class AmgInfo(ctypes.Structure):
@@ -158,6 +158,9 @@ def amg_opts_default(**overrides) -> AmgOpts:
     for k, v in overrides.items():
         if not hasattr(o, k):
             raise AttributeError(k)
+        if k == "mpnn_weights" and v is not None and not isinstance(v, int):
+            o._weights = _dev_weights(v)  # kept alive with the options
+            v = o._weights.data_ptr()
         setattr(o, k, v)
     return o
 

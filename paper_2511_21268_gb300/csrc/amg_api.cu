@@ -417,6 +417,8 @@ int build(amg_hierarchy* h, const amg_csr* K) {
             CK(launch_l1diag(F.A, F.kii, F.dl1, F.invd, h->flag, s));
             RC(read_flag(h, &bad));
             if (bad) return AMG_ERR_NOT_SPD;
+            // the finest level will have a smoother: start its network now
+            if (h->o.mpnn_weights && n > h->o.coarse_max && h->o.max_levels > 1) RC(mpnn_setup_fork(h));
         } else {  // coarse levels: checked once after the loop (flag[4])
             CK(launch_l1diag(F.A, F.kii, F.dl1, F.invd, h->flag + 4, s));
         }
@@ -556,6 +558,10 @@ int build(amg_hierarchy* h, const amg_csr* K) {
     if (h->o.matrix_format == 2) {
         RC(stream_prepare(h, h->flag));
         RC(sell_prepare_level1(h, h->flag));
+    }
+    if (h->o.mpnn_weights) {
+        phase(h, 9);
+        RC(mpnn_setup_join(h));
     }
     return AMG_OK;
 }
@@ -697,6 +703,7 @@ int check_opts(const amg_opts& o) {
     if (o.precision < AMG_FP64 || o.precision > AMG_FP32_BF16FINE) return AMG_ERR_ARG;
     if (o.flexible < 0 || o.flexible > 1 || o.resid_replace_every < 0) return AMG_ERR_ARG;
     if (o.matrix_format < 0 || o.matrix_format > 2) return AMG_ERR_ARG;
+    if (o.mpnn_bf16 < 0 || o.mpnn_bf16 > 1) return AMG_ERR_ARG;
     return AMG_OK;
 }
 
@@ -722,6 +729,8 @@ int amg_opts_default(amg_opts* o) {
     o->flexible = 0;
     o->resid_replace_every = 20;
     o->matrix_format = 2;
+    o->mpnn_weights = nullptr;
+    o->mpnn_bf16 = 1;
     return AMG_OK;
 }
 

@@ -288,6 +288,8 @@ cudaError_t enqueue_multi_final(amg_hierarchy* h, cudaStream_t s);
 int multi_dot_stride();
 // mpnn.cu
 void mpnn_free(amg_hierarchy* h);
+int mpnn_setup_fork(amg_hierarchy* h);
+int mpnn_setup_join(amg_hierarchy* h);
 // stream_kernels.cu
 int stream_prepare(amg_hierarchy* h, int* scratch2);
 cudaError_t launch_stream_resid(amg_hierarchy* h, const double* f, const float* x, float* rbuf, cudaStream_t s);

@@ -536,6 +536,8 @@ struct MpnnLevel {
     float* omega = nullptr;
     double* domega = nullptr;
     double* v[kVec] = {};
+    int alloc = 0;     // buffers allocated
+    int features = 0;  // features enqueued
 };
 
 struct MpnnWork {
@@ -551,6 +553,12 @@ struct MpnnWork {
     int* dst = nullptr;  // [4][kGradSlots] slot -> weight index maps
     float *adam_m = nullptr, *adam_v = nullptr;
     int have_omega = 0;  // omega of a network evaluation present
+    int shared = 0;      // training buffers allocated
+    // setup with weights: the finest level's network runs on `side` from the
+    // moment its diagonal is known, concurrently with the rest of the setup
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_done = nullptr;
+    int forked = 0;
     std::vector<void*> allocs;
 };
 
@@ -588,31 +596,61 @@ int mp_alloc(amg_hierarchy* h, void** p, size_t bytes) {
         if (r__ != AMG_OK) return r__;        \
     } while (0)
 
-// Allocate the network and training buffers and compute every level's
-// features (once per hierarchy).
-int prepare(amg_hierarchy* h) {
+#define MP_TRY(expr)                   \
+    do {                               \
+        int r__ = (expr);              \
+        if (r__ != AMG_OK) return r__; \
+    } while (0)
+
+int ensure_work(amg_hierarchy* h) {
     if (h->mp) return AMG_OK;
     h->mp = new (std::nothrow) MpnnWork();
-    if (!h->mp) return AMG_ERR_NOMEM;
+    return h->mp ? AMG_OK : AMG_ERR_NOMEM;
+}
+
+// Network buffers of level l, allocated on the library stream (stream-ordered).
+int alloc_level(amg_hierarchy* h, int l) {
+    MpnnLevel& m = h->mp->lev[l];
+    if (m.alloc) return AMG_OK;
+    const Level& L = h->lev[l];
+    const int64_t n = L.A.n;
+    MP_ALLOC(m.x, sizeof(float) * 4 * n);
+    MP_ALLOC(m.ap, sizeof(float) * L.A.nnz);
+    for (int t = 0; t < MpnnLevel::kTape; t++) MP_ALLOC(m.t[t], sizeof(float) * H * n);
+    MP_ALLOC(m.sg, sizeof(float) * n);
+    MP_ALLOC(m.omega, sizeof(float) * n);
+    MP_ALLOC(m.domega, sizeof(double) * n);
+    for (int t = 0; t < MpnnLevel::kVec; t++) MP_ALLOC(m.v[t], sizeof(double) * n);
+    m.alloc = 1;
+    return AMG_OK;
+}
+
+// Node and edge features of level l (Sec. 4.2) on stream s; the buffers must
+// be allocated and ordered before s.
+void features_level(amg_hierarchy* h, int l, cudaStream_t s) {
+    MpnnLevel& m = h->mp->lev[l];
+    if (m.features) return;
+    const Level& L = h->lev[l];
+    const int64_t n = L.A.n;
+    // m.sg holds 1 / sqrt(k_ii) until the first network evaluation
+    k_nn_rsqrt_diag<<<AMG_GRID(eblk(n)), kBlock, 0, s>>>((int)n, L.kii, m.sg);
+    k_nn_features<<<AMG_GRID(grid_rows(h, n)), kBlock, 0, s>>>((int)n, L.A.rowptr, L.A.col, L.A.val, L.kii, m.sg,
+                                                                 m.x, m.ap);
+    m.features = 1;
+}
+
+// Allocate the network buffers and compute the features of every level (once
+// per hierarchy), and the training buffers.
+int prepare(amg_hierarchy* h) {
+    MP_TRY(ensure_work(h));
     MpnnWork& w = *h->mp;
+    for (int l = 0; l < h->nlev; l++) {
+        MP_TRY(alloc_level(h, l));
+        features_level(h, l, h->s);
+    }
+    if (w.shared) return AMG_OK;
     cudaStream_t s = h->s;
     const int64_t n0 = h->lev[0].A.n;
-    for (int l = 0; l < h->nlev; l++) {
-        Level& L = h->lev[l];
-        MpnnLevel& m = w.lev[l];
-        const int64_t n = L.A.n;
-        MP_ALLOC(m.x, sizeof(float) * 4 * n);
-        MP_ALLOC(m.ap, sizeof(float) * L.A.nnz);
-        for (int t = 0; t < MpnnLevel::kTape; t++) MP_ALLOC(m.t[t], sizeof(float) * H * n);
-        MP_ALLOC(m.sg, sizeof(float) * n);
-        MP_ALLOC(m.omega, sizeof(float) * n);
-        MP_ALLOC(m.domega, sizeof(double) * n);
-        for (int t = 0; t < MpnnLevel::kVec; t++) MP_ALLOC(m.v[t], sizeof(double) * n);
-        // m.sg holds 1 / sqrt(k_ii) until the first network evaluation
-        k_nn_rsqrt_diag<<<AMG_GRID(eblk(n)), kBlock, 0, s>>>((int)n, L.kii, m.sg);
-        k_nn_features<<<AMG_GRID(grid_rows(h, n)), kBlock, 0, s>>>((int)n, L.A.rowptr, L.A.col, L.A.val, L.kii, m.sg,
-                                                                     m.x, m.ap);
-    }
     for (int t = 0; t < 3; t++) MP_ALLOC(w.bw[t], sizeof(float) * H * n0);
     MP_ALLOC(w.part, sizeof(float) * kGradBlocks * kGradSlots);
     MP_ALLOC(w.gacc, sizeof(double) * AMG_MPNN_NPARAM);
@@ -651,28 +689,31 @@ int prepare(amg_hierarchy* h) {
     MP_CK(cudaMemcpyAsync(w.dst, dst.data(), sizeof(int) * dst.size(), cudaMemcpyHostToDevice, s));
     MP_CK(cudaStreamSynchronize(s));  // dst is a host stack vector
     MP_CK(cudaGetLastError());
+    w.shared = 1;
     return AMG_OK;
 }
 
-// omega of levels [0, nlev - 1) from the network (FP32 arithmetic; weights
-// rounded to BF16 first when bf16 != 0).  The coarsest level has no smoother.
+// omega of level l from the network (Sec. 4.2: encoder, two message-passing
+// layers, decoder; FP32 arithmetic, weights rounded to BF16 first when
+// bf16 != 0), on stream s.
+void forward_level(amg_hierarchy* h, int l, const float* wd, int bf16, cudaStream_t s) {
+    const Level& L = h->lev[l];
+    MpnnLevel& m = h->mp->lev[l];
+    const int n = L.A.n;
+    const int g = grid_rows(h, n);
+    float *u0 = m.t[0], *h0 = m.t[1], *m1 = m.t[2], *u1 = m.t[3], *h1 = m.t[4], *m2 = m.t[5], *u2 = m.t[6],
+          *h2 = m.t[7];
+    k_nn_in<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, m.x, u0, h0);
+    k_nn_spmm<<<AMG_GRID(g), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, m.ap, h0, nullptr, m1);
+    k_nn_dense<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, 1, m1, h0, u1, h1, nullptr, nullptr);
+    k_nn_spmm<<<AMG_GRID(g), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, m.ap, h1, nullptr, m2);
+    k_nn_dense<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, 2, m2, h1, u2, h2, m.sg, m.omega);
+}
+
+// omega of levels [0, nlev - 1); the coarsest level has no smoother.
 cudaError_t net_forward(amg_hierarchy* h, const float* wd, int bf16) {
-    MpnnWork& w = *h->mp;
-    cudaStream_t s = h->s;
-    for (int l = 0; l + 1 < h->nlev; l++) {
-        Level& L = h->lev[l];
-        MpnnLevel& m = w.lev[l];
-        const int n = L.A.n;
-        const int g = grid_rows(h, n);
-        float *u0 = m.t[0], *h0 = m.t[1], *m1 = m.t[2], *u1 = m.t[3], *h1 = m.t[4], *m2 = m.t[5], *u2 = m.t[6],
-              *h2 = m.t[7];
-        k_nn_in<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, m.x, u0, h0);
-        k_nn_spmm<<<AMG_GRID(g), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, m.ap, h0, nullptr, m1);
-        k_nn_dense<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, 1, m1, h0, u1, h1, nullptr, nullptr);
-        k_nn_spmm<<<AMG_GRID(g), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, m.ap, h1, nullptr, m2);
-        k_nn_dense<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, 2, m2, h1, u2, h2, m.sg, m.omega);
-    }
-    w.have_omega = 1;
+    for (int l = 0; l + 1 < h->nlev; l++) forward_level(h, l, wd, bf16, h->s);
+    h->mp->have_omega = 1;
     return cudaGetLastError();
 }
 
@@ -830,9 +871,54 @@ int read_host(amg_hierarchy* h, const T* dptr, T* out) {
 
 }  // namespace
 
+// Setup with network weights, first half: once the finest level's diagonal
+// is known, its features and network run on a second stream while the setup
+// goes on building the coarse levels on the library stream.
+int mpnn_setup_fork(amg_hierarchy* h) {
+    MP_TRY(ensure_work(h));
+    MpnnWork& w = *h->mp;
+    MP_TRY(alloc_level(h, 0));
+    MP_CK(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
+    MP_CK(cudaEventCreateWithFlags(&w.ev_fork, cudaEventDisableTiming));
+    MP_CK(cudaEventCreateWithFlags(&w.ev_done, cudaEventDisableTiming));
+    MP_CK(cudaEventRecord(w.ev_fork, h->s));
+    MP_CK(cudaStreamWaitEvent(w.side, w.ev_fork, 0));
+    features_level(h, 0, w.side);
+    forward_level(h, 0, h->o.mpnn_weights, h->o.mpnn_bf16, w.side);
+    MP_CK(cudaEventRecord(w.ev_done, w.side));
+    w.forked = 1;
+    MP_CK(cudaGetLastError());
+    return AMG_OK;
+}
+
+// Second half, at the end of the setup: the network on the other levels with
+// a smoother, the join with the finest level's evaluation, and the damping
+// omega / d installed on every smoothed level (as amg_mpnn_apply does).
+int mpnn_setup_join(amg_hierarchy* h) {
+    MP_TRY(ensure_work(h));
+    MpnnWork& w = *h->mp;
+    for (int l = w.forked ? 1 : 0; l + 1 < h->nlev; l++) {
+        MP_TRY(alloc_level(h, l));
+        features_level(h, l, h->s);
+        forward_level(h, l, h->o.mpnn_weights, h->o.mpnn_bf16, h->s);
+    }
+    if (w.forked) MP_CK(cudaStreamWaitEvent(h->s, w.ev_done, 0));
+    w.have_omega = 1;
+    MP_CK(set_damping(h, true));
+    h->damping_learned = 1;
+    return AMG_OK;
+}
+
 void mpnn_free(amg_hierarchy* h) {
     if (!h->mp) return;
-    for (void* p : h->mp->allocs) cudaFreeAsync(p, h->s);
+    MpnnWork& w = *h->mp;
+    // a setup that failed between fork and join leaves work on the second
+    // stream that reads buffers freed below
+    if (w.side) cudaStreamSynchronize(w.side);
+    for (void* p : w.allocs) cudaFreeAsync(p, h->s);
+    if (w.ev_fork) cudaEventDestroy(w.ev_fork);
+    if (w.ev_done) cudaEventDestroy(w.ev_done);
+    if (w.side) cudaStreamDestroy(w.side);
     delete h->mp;
     h->mp = nullptr;
 }

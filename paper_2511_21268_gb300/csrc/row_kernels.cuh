@@ -23,24 +23,54 @@ __device__ __forceinline__ double ldv(const double* v, int64_t k) { return __ldg
 __device__ __forceinline__ float ldv(const float* v, int64_t k) { return __ldg(v + k); }
 __device__ __forceinline__ float ldv(const __nv_bfloat16* v, int64_t k) { return __bfloat162float(v[k]); }
 
-// Lane partial of row i: sum over k = b + lane + 32 t of v_k x_{c_k}, in A.
-template <typename A, typename V, typename X>
-__device__ __forceinline__ A lane_partial(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                          const V* __restrict__ v, const X* __restrict__ x, int i, int lane) {
+// Lane partial of row i: sum over k = b + lane + 32 t of v_k x_{c_k}, in A,
+// with xload(c) giving x_c (the same FMA chain for every U).  The rows this runs on (levels with few rows,
+// a warp per row) are latency-bound: each chunk of U entries per lane loads
+// all its values and columns, then all its x entries, then runs the FMA
+// chain in entry order, and the last partial chunk does the same with
+// predicated loads, so a row of up to 32 U entries costs two dependent
+// round trips.
+template <int U, typename A, typename V, typename XL>
+__device__ __forceinline__ A lane_partial_with(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                               const V* __restrict__ v, XL xload, int i, int lane) {
     const int64_t b = rp[i], e = rp[i + 1];
     A acc = A(0);
     int64_t k = b + lane;
-    for (; k + 96 < e; k += 128) {
-        const A v0 = (A)ldv(v, k), v1 = (A)ldv(v, k + 32), v2 = (A)ldv(v, k + 64), v3 = (A)ldv(v, k + 96);
-        const int c0 = __ldg(ci + k), c1 = __ldg(ci + k + 32), c2 = __ldg(ci + k + 64), c3 = __ldg(ci + k + 96);
-        const A x0 = (A)x[c0], x1 = (A)x[c1], x2 = (A)x[c2], x3 = (A)x[c3];
-        acc = fma(v0, x0, acc);
-        acc = fma(v1, x1, acc);
-        acc = fma(v2, x2, acc);
-        acc = fma(v3, x3, acc);
+    for (; k + 32 * (U - 1) < e; k += 32 * U) {
+        A vv[U], xx[U];
+        int cc[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            vv[u] = (A)ldv(v, k + 32 * u);
+            cc[u] = __ldg(ci + k + 32 * u);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) xx[u] = xload(cc[u]);
+#pragma unroll
+        for (int u = 0; u < U; u++) acc = fma(vv[u], xx[u], acc);
     }
-    for (; k < e; k += 32) acc = fma((A)ldv(v, k), (A)x[__ldg(ci + k)], acc);
+    if (k < e) {  // fewer than U entries left on this lane
+        A vv[U - 1], xx[U - 1];
+        int cc[U - 1];
+#pragma unroll
+        for (int u = 0; u < U - 1; u++) {
+            const bool in = k + 32 * u < e;
+            vv[u] = in ? (A)ldv(v, k + 32 * u) : A(0);
+            cc[u] = in ? __ldg(ci + k + 32 * u) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < U - 1; u++) xx[u] = cc[u] >= 0 ? xload(cc[u]) : A(0);
+#pragma unroll
+        for (int u = 0; u < U - 1; u++)
+            if (cc[u] >= 0) acc = fma(vv[u], xx[u], acc);
+    }
     return acc;
+}
+
+template <typename A, typename V, typename X>
+__device__ __forceinline__ A lane_partial(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                          const V* __restrict__ v, const X* __restrict__ x, int i, int lane) {
+    return lane_partial_with<sizeof(A) == 4 ? 16 : 8, A>(rp, ci, v, [&](int c) { return (A)x[c]; }, i, lane);
 }
 
 // Matrix views of the row-group kernels.  CsrM: plain CSR.  RunM: CSR

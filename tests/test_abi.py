@@ -42,3 +42,18 @@ def test_binding_names_match_abi():
 
     for name in declared_functions():
         assert hasattr(amg, name), name
+
+
+def test_options_struct_defaults_through_the_binding_layout():
+    """amg_opts_default (host only) fills the binding's struct: every field
+    lands where the header puts it, the trailing network weights included."""
+    from paper_2511_21268_gb300 import amg
+
+    L = ctypes.CDLL(_build.build_cuda())
+    o = amg.AmgOpts()
+    assert L.amg_opts_default(ctypes.byref(o)) == 0
+    assert (o.nu_pre, o.nu_post, o.match_passes, o.coarse_max, o.max_levels, o.dense_max) == (1, 1, 2, 200, 30, 4096)
+    assert (o.testvec_sweeps, o.seed, o.stag, o.max_match_rounds) == (4, 20251126, 0.9, 1000)
+    assert (o.precision, o.flexible, o.resid_replace_every, o.matrix_format) == (amg.AMG_FP64, 0, 20, 2)
+    assert o.mpnn_weights is None and o.mpnn_bf16 == 1
+

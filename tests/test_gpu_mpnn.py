@@ -203,3 +203,37 @@ def test_training_over_several_hierarchies_uses_the_mean_loss():
     vh = c2 * g * g / (1 - float(f(0.999)))
     expect = w0 - 1e-3 * mh / (np.sqrt(vh) + 1e-8)
     assert np.allclose(w.cpu().numpy(), expect, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("prec,bf16", [(A.AMG_FP64, False), (A.AMG_FP32_BF16FINE, True)])
+def test_weights_at_setup_install_the_apply_damping_bit_for_bit(prec, bf16):
+    """Setup given the network weights (the finest level's network running on
+    a second stream alongside the coarse-level setup) installs exactly the
+    damping that amg_mpnn_apply installs after a plain setup: omega, the
+    V-cycle and the solve are bitwise equal, and w = NULL restores the plain
+    smoother bit for bit."""
+    prob = I.poisson_box(3, 14, 3)
+    args = (dev(prob.rowptr), dev(prob.col), dev(prob.val))
+    w = dev(varied_weights(9))
+    H1 = A.Hierarchy(*args, coarse_max=50, precision=prec)
+    r = np.random.default_rng(21).standard_normal(prob.n)
+    z_plain = H1.vcycle(dev(r)).cpu().numpy()
+    H1.mpnn_apply(w, bf16_weights=bf16)
+    H2 = A.Hierarchy(*args, coarse_max=50, precision=prec, mpnn_weights=w, mpnn_bf16=int(bf16))
+    assert H2.num_levels == H1.num_levels >= 3
+    assert H2.info.setup_phase_ms[9] > 0
+    for l in range(H1.num_levels - 1):
+        o1, o2 = H1.mpnn_omega(l).cpu().numpy(), H2.mpnn_omega(l).cpu().numpy()
+        assert np.array_equal(o1.view(np.uint32), o2.view(np.uint32)), l
+    z1, z2 = H1.vcycle(dev(r)).cpu().numpy(), H2.vcycle(dev(r)).cpu().numpy()
+    assert np.array_equal(z1.view(np.uint64), z2.view(np.uint64))
+    assert np.linalg.norm(z2 - z_plain) > 1e-3 * np.linalg.norm(z_plain)
+    g1, g2 = H1.solve(dev(prob.F), rtol=1e-8), H2.solve(dev(prob.F), rtol=1e-8)
+    assert g2["status"] == 0 and g1["iters"] == g2["iters"]
+    assert np.array_equal(g1["u"].cpu().numpy().view(np.uint64), g2["u"].cpu().numpy().view(np.uint64))
+    H2.mpnn_apply(None)
+    z_back = H2.vcycle(dev(r)).cpu().numpy()
+    assert np.array_equal(z_back.view(np.uint64), z_plain.view(np.uint64))
+    with pytest.raises(A.AmgError):
+        A.Hierarchy(*args, coarse_max=50, mpnn_weights=w, mpnn_bf16=2)
+

@@ -39,7 +39,14 @@ METRIC = "time-to-solution at rtol 1e-8 and V-cycle HBM GB/s: mixed/learned vs F
 WORKLOAD = "3-D Poisson unit cube, B-spline p=3 C^2, n=64 (N=274,625, nnz=86,938,307), FP64 AMG-PCG, rtol 1e-8"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fine_matrix_pass_fp64_3d_p3_n64.md")
 STREAM_SUMMARY = os.path.join(ROOT, "profiles", "staged_mixed_passes_3d_p3_n64.md")
-KERNEL_NAMES = ["k_spmv_pq<8> (q = K p)", "k_resid<8> (down-sweep residual)", "k_up0<8> (up-sweep smoothing)"]
+# FP64 finest-level passes by the layout the library chose (amg_info.staged_passes): 3 = sliced slabs
+# with FP64 values (k_sell64), else the row-group kernels on run-encoded columns
+FP64_KERNEL_NAMES = {
+    3: ["k_sell64<7, Epi64PQ> (q = K p)", "k_sell64<7, Epi64Resid> (down-sweep residual)",
+        "k_sell64<7, Epi64Up0> (up-sweep smoothing)"],
+    0: ["k_spmv_pq<8> (q = K p)", "k_resid<8> (down-sweep residual)", "k_up0<8> (up-sweep smoothing)"],
+}
+FP64_SOURCES = {3: ("sell_kernels.cu",), 0: ("row_kernels.cuh",)}
 # staged mixed-precision passes of the run-encoded finest matrix (matrix_format 2), by the
 # layout the library chose (amg_info.staged_passes): 2 = sliced slabs with a lane per row
 # (k_sell), 1 = slabs with a lane per run (k_stream)
@@ -703,15 +710,17 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     avg_ms = ms_sum / np.maximum(cnt_sum, 1)
     per_kernel = {}
+    fkind = 3 if int(info.staged_passes) == 3 else 0
+    KERNEL_NAMES = FP64_KERNEL_NAMES[fkind]
     for q, name in enumerate(KERNEL_NAMES):
         gbs = kbytes[q] / (avg_ms[q] * 1e-3) / 1e9 if avg_ms[q] > 0 else None
         per_kernel[name] = {"bytes_per_launch": kbytes[q], "avg_ms": avg_ms[q], "launches": int(cnt_sum[q]),
                             "achieved_gbs": gbs}
     dom = int(np.argmax(ms_sum))
-    traffic = committed_traffic()
+    traffic = committed_traffic(PROFILE_SUMMARY, FP64_SOURCES[fkind])
     tkey = ["spmv_pq", "resid", "up0"][dom]
-    # The FP64 finest pass issues one DFMA per stored entry; on GB300 that is the binding limit (ncu: FP64
-    # pipe 86 % busy at 37 % of DRAM peak), so its roofline is the FP64 rate derived from unit counts and clock.
+    # The FP64 finest pass issues one DFMA per stored entry; on GB300 that is the binding limit (the FP64
+    # pipe is far busier than DRAM), so its roofline is the FP64 rate derived from unit counts and clock.
     fpk = fp64_peak_tflops()
     flops_tf = 2.0 * prob.nnz / (avg_ms[dom] * 1e-3) / 1e12 if avg_ms[dom] > 0 else 0.0
     roof = {"bound": "alu", "kernel": KERNEL_NAMES[dom], "achieved": flops_tf, "peak": fpk, "unit": "TFLOP/s",
@@ -728,7 +737,10 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": args.n, "p": args.p, "N": prob.n, "nnz": prob.nnz,
                        "rtol": args.rtol, "precision": "fp64", "l2": "inputs larger than L2 (matrix 1.04 GB)",
-                       "matrix_format": ["csr", "run-encoded finest level", "run-encoded + streamed mixed passes"][args.matrix_format],
+                       "matrix_format": ["csr", "run-encoded finest level",
+                                         "run-encoded + sliced finest-level passes"][args.matrix_format],
+                       "fp64_passes": "sliced slabs, FP64 values, a warp per slab" if fkind == 3
+                       else "row-group kernels",
                        "parallelism": f"replicas x{world}"},
             "iters": it, "final_relres": rr, "setup_ms": info.setup_ms, "solve_ms": info.solve_ms,
             "setup_phase_ms": dict(zip(["copy+checks", "l1+testvec+diag", "edge_weights", "matching",

@@ -94,8 +94,10 @@ typedef struct {
     int32_t matrix_format;       /* finest-level matrix passes: 0 = plain CSR; 1 = run-encoded
                                     columns when every row is a sequence of equal runs (2..9
                                     entries, rows < 65536 entries) of consecutive columns, as in
-                                    tensor-product IgA matrices; 2 = as 1, and the mixed-precision
-                                    passes stream the matrix into shared memory by bulk copies (2) */
+                                    tensor-product IgA matrices; 2 = as 1, and the finest-level
+                                    passes run on a sliced copy (32-row slabs, a lane per row):
+                                    streamed into shared memory by bulk copies in mixed precision,
+                                    FP64 values with a warp per slab in FP64 (2) */
     const float* mpnn_weights;   /* NULL, or the weights of the damping network (AMG_MPNN_NPARAM
                                     floats in the layout of amg_mpnn_apply; DEVICE pointer, read
                                     during amg_setup only).  Setup then installs the learned damping
@@ -129,11 +131,13 @@ typedef struct {
      * the finest level's evaluation, install) */
     double setup_phase_ms[12];
     int32_t level_format[AMG_MAX_LEVELS]; /* 1 = run-encoded columns, 0 = plain CSR */
-    int32_t staged_passes; /* finest-level passes of a mixed-precision solve: 0 = row-group
-                              kernels, 1 = staged slabs with a lane per run, 2 = staged sliced
-                              slabs with a lane per row (matrix_format 2) */
+    int32_t staged_passes; /* finest-level passes: 0 = row-group kernels; mixed precision:
+                              1 = staged slabs with a lane per run, 2 = staged sliced slabs with
+                              a lane per row; FP64: 3 = sliced slabs with FP64 values, a warp per
+                              slab and a lane per row (2 and 3 need matrix_format 2) */
     int64_t staged_slots;  /* value slots of the sliced slabs (padding included), 0 if unused */
-    int32_t staged_buffers[2]; /* copy-ring buffers of the staged passes: [0] BF16 values, [1] FP32 */
+    int32_t staged_buffers[2]; /* copy-ring buffers of the staged passes: [0] BF16 values, [1] FP32
+                                  (0 for the FP64 sliced passes, which read values directly) */
     int32_t staged_window_bytes; /* largest per-block vector window of the staged passes */
     int32_t staged_level1; /* 1: level 1 also runs sliced staged passes (plain CSR, FP32 values) */
     double graph_build_ms; /* host time capturing and instantiating the iteration graph in the last

@@ -528,8 +528,9 @@ int build(amg_hierarchy* h, const amg_csr* K) {
             RC(dalloc(h, &F.t32, (size_t)n + 4));
         } else {
             if (l > 0) RC(dalloc(h, &F.f, n));
-            RC(dalloc(h, &F.x, n));
-            RC(dalloc(h, &F.t, n));
+            // + 4: the FP64 sliced passes copy vector windows in 4-entry groups
+            RC(dalloc(h, &F.x, (size_t)n + 4));
+            RC(dalloc(h, &F.t, (size_t)n + 4));
         }
     }
     if (h->mixed) RC(dalloc(h, &h->p32, (size_t)n0 + 4));
@@ -558,6 +559,7 @@ int build(amg_hierarchy* h, const amg_csr* K) {
     if (h->o.matrix_format == 2) {
         RC(stream_prepare(h, h->flag));
         RC(sell_prepare_level1(h, h->flag));
+        RC(sell64_prepare(h, h->flag));
     }
     if (h->o.mpnn_weights) {
         phase(h, 9);
@@ -580,7 +582,7 @@ double index_bytes(const Level& L) {
 // offsets (8 B per row) and the column index (index_bytes).
 static double fine_structure_bytes(const amg_hierarchy* h) {
     const Level& L0 = h->lev[0];
-    if (h->stream == 2) return (double)L0.nruns * 2.0 + (h->sell[0].nsl + 1.0) * 4.0;
+    if (h->stream == 2 || h->sell64) return (double)L0.nruns * 2.0 + (h->sell[0].nsl + 1.0) * 4.0;
     return index_bytes(L0) + (L0.A.n + 1.0) * 8.0;
 }
 
@@ -597,12 +599,16 @@ void fill_info(amg_hierarchy* h) {
         I.match_rounds[l] = rounds;
         I.level_format[l] = h->lev[l].run_ptr ? 1 : 0;
     }
-    I.staged_passes = h->stream;
-    const bool sl = h->stream == 2;
+    I.staged_passes = h->sell64 ? 3 : h->stream;
+    const bool sl = h->stream == 2 || h->sell64;
     I.staged_slots = sl ? h->sell[0].slots * h->sell[0].lm * 32 : 0;
-    I.staged_buffers[0] = sl ? h->sell[0].nbuf[0] : h->stream ? h->stream_nbuf[0] : 0;
-    I.staged_buffers[1] = sl ? h->sell[0].nbuf[1] : h->stream ? h->stream_nbuf[1] : 0;
-    I.staged_window_bytes = sl ? h->sell[0].xbytes : h->stream ? h->stream_xbytes : 0;
+    I.staged_buffers[0] = h->stream == 2 ? h->sell[0].nbuf[0] : h->stream ? h->stream_nbuf[0] : 0;
+    I.staged_buffers[1] = h->stream == 2 ? h->sell[0].nbuf[1] : h->stream ? h->stream_nbuf[1] : 0;
+    // the FP64 passes hold the same window entries in FP64
+    I.staged_window_bytes = h->sell64 ? 2 * h->sell[0].xbytes
+                            : sl      ? h->sell[0].xbytes
+                            : h->stream ? h->stream_xbytes
+                                        : 0;
     I.staged_level1 = h->sell[1].on;
     I.opc = tot / (double)h->lev[0].A.nnz;
     // algorithmic bytes: one matrix pass = nnz (value + 4) + (n + 1) 8 + x read + y write
@@ -1287,7 +1293,6 @@ int amg_kernel_times(const amg_hierarchy* h, double* ms, int64_t* count, double*
     if (!h) return AMG_ERR_ARG;
     const double n = h->lev[0].A.n, nnz = (double)h->lev[0].A.nnz;
     const double flex = h->o.flexible ? 8.0 * n : 0.0;
-    const double ib = index_bytes(h->lev[0]);
     double b[3];
     if (h->mixed) {  // FP32 outer values, FP32 (or BF16) V-cycle values, FP32 V-cycle vectors
         const double vcv = h->lev[0].val16 ? 2.0 : 4.0;
@@ -1296,7 +1301,7 @@ int amg_kernel_times(const amg_hierarchy* h, double* ms, int64_t* count, double*
         b[1] = nnz * vcv + rows + 8.0 * n + 4.0 * n + 4.0 * n;  // r, x, rbuf
         b[2] = nnz * vcv + rows + 8.0 * n + 4.0 * n + 4.0 * n + 8.0 * n + flex;  // r, x, invd, z
     } else {
-        const double base = nnz * 8.0 + ib + (n + 1.0) * 8.0;
+        const double base = nnz * 8.0 + fine_structure_bytes(h);
         b[0] = base + 16.0 * n + flex;
         b[1] = base + 24.0 * n;
         b[2] = base + 32.0 * n + flex;

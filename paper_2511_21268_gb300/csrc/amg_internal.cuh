@@ -143,6 +143,7 @@ struct SellLevel {
     int32_t* soff = nullptr;       // nsl + 1
     uint16_t* rs = nullptr;        // window offset of each (slot, lane)
     float* v32 = nullptr;          // FP32 values, slot-major, lane-minor
+    double* v64 = nullptr;         // FP64 values (plain FP64 solve; then v32 = v16 = nullptr)
     __nv_bfloat16* v16 = nullptr;  // BF16 values (BF16 finest values only)
     int vbytes[2] = {};            // value area per buffer: [0] BF16, [1] FP32
     int rbytes = 0;                // offset area per buffer
@@ -208,10 +209,12 @@ struct amg_hierarchy {
     int stream_rbytes[2] = {};  // run-start buffer bytes
     int stream_nbuf[2] = {};    // buffers in the copy ring
     int* stream_win = nullptr;  // int2 per block: first and last column of its rows
-    // sliced copies (32-row slabs, lane per row) used by the staged passes:
-    // [0] the finest level (when stream == 2), [1] level 1 (plain CSR, each
-    // entry a run of length 1)
+    // sliced copies (32-row slabs, lane per row): [0] the finest level (when
+    // stream == 2, FP32 and BF16 values; or when sell64, FP64 values), [1]
+    // level 1 in mixed precision (plain CSR, each entry a run of length 1)
     amg::SellLevel sell[2];
+    int sell64 = 0;        // plain FP64 solve: the finest-level passes run on sell[0] (FP64 values)
+    int sell64_warps = 0;  // warps per block of those passes
     // multi-system solves
     amg::MultiWork* mw = nullptr;
     // learned smoother damping: network buffers, and whether the smoother
@@ -302,6 +305,12 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used);
 int sell_prepare_level1(amg_hierarchy* h, int* scratch);
 cudaError_t sell_resid1(amg_hierarchy* h, const float* f, const float* x, float* rbuf, cudaStream_t s);
 cudaError_t sell_upy1(amg_hierarchy* h, const float* f, const float* x, const float* invd, float* y, cudaStream_t s);
+int sell64_prepare(amg_hierarchy* h, int* scratch);
+cudaError_t sell64_spmv_pq(amg_hierarchy* h, const double* p, const double* r, double* q, double* part_pq,
+                           double* part_pr, int flexible, cudaStream_t s);
+cudaError_t sell64_resid(amg_hierarchy* h, const double* f, const double* x, double* rbuf, cudaStream_t s);
+cudaError_t sell64_up0(amg_hierarchy* h, const double* r, const double* x, const double* invd, double* z,
+                       const double* q, double* part_rz, double* part_zq, int flexible, cudaStream_t s);
 cudaError_t sell_resid(amg_hierarchy* h, const double* f, const float* x, float* rbuf, cudaStream_t s);
 cudaError_t sell_up0(amg_hierarchy* h, const double* r, const float* x, const float* invd, double* z,
                      const double* q, double* part_rz, double* part_zq, int flexible, cudaStream_t s);

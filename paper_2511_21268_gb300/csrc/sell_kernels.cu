@@ -379,6 +379,170 @@ __global__ void __launch_bounds__(kSellThreads, 1)
     }
 }
 
+// ------------------------------------------------------------------ FP64
+// The plain FP64 solve's finest-level passes on the same sliced slabs, with
+// FP64 values.  GB300 issues about two FP64 FMAs per clock per SM, so these
+// passes are bound by the FP64 pipe, not by HBM (about 87 M FMAs against
+// 0.7 GB per pass on the 3-D p=3 n=64 system), and what counts is that nearly
+// every FP64 instruction is a useful FMA.  A warp takes a whole slab and a
+// lane its row; each lane runs its row's FMA chain over the run slots (two
+// accumulators), with 8-16 values per lane in flight whatever the run
+// length.  There are no partial sums to reduce across lanes and no lanes
+// idle past a row's end, only the padded slots.
+// Values come straight from global memory (one coalesced 256-byte load per
+// value slot and warp); the block's compacted window of the gathered vector
+// is first copied into shared memory in FP64 (the same window offsets as
+// the FP32 copy).  Dot products: each lane adds its rows' terms in slab
+// order, then the lanes and the warps are summed in a fixed order (one
+// deterministic partial per block).
+constexpr int kS64MinWarps = 12, kS64MaxWarps = 20;  // warps per block: chosen at setup (load balance)
+constexpr int kS64Static = 1024;                      // static shared memory and slack
+
+struct Epi64PQ {  // q = K p, p.q and (flexible) p.r
+    const double* p;
+    const double* r;
+    double* q;
+    int flexible;
+    __device__ __forceinline__ void operator()(int i, double s, double& a1, double& a2) const {
+        q[i] = s;
+        const double pi = p[i];
+        a1 += pi * s;
+        if (flexible) a2 += pi * r[i];
+    }
+};
+
+struct Epi64Resid {  // rbuf = f - K x
+    const double* f;
+    double* rbuf;
+    __device__ __forceinline__ void operator()(int i, double s, double&, double&) const { rbuf[i] = f[i] - s; }
+};
+
+struct Epi64Up0 {  // z = x + (r - K x) / d, r.z and (flexible) z.q
+    const double* r;
+    const double* x;
+    const double* invd;
+    double* z;
+    const double* q;
+    int flexible;
+    __device__ __forceinline__ void operator()(int i, double s, double& a1, double& a2) const {
+        const double ra = r[i];
+        const double za = fma(invd[i], ra - s, x[i]);
+        z[i] = za;
+        a1 += ra * za;
+        if (flexible) a2 += za * q[i];
+    }
+};
+
+template <int LM, typename Epi>
+__global__ void __launch_bounds__(kS64MaxWarps * 32, 1)
+    k_sell64(int n, int nsl, const int32_t* __restrict__ soff, const double* __restrict__ val,
+             const uint16_t* __restrict__ rs, const double* __restrict__ xg, const int4* __restrict__ wint,
+             const int* __restrict__ wcnt, Epi epi, double* part1, double* part2, const SolveState* st) {
+    pdl_entry();
+    if (st && st->done) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    double* xw = reinterpret_cast<double*>(smem);
+    __shared__ double red[2][kS64MaxWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int s0 = (int)((int64_t)blockIdx.x * nsl / gridDim.x);
+    const int s1 = (int)((int64_t)(blockIdx.x + 1) * nsl / gridDim.x);
+    // the compacted window: interval q holds entries [x, x + y) of the
+    // vector at window offset z (all multiples of 4 entries)
+    const int nq = s0 < s1 ? wcnt[blockIdx.x] : 0;
+    for (int q = wid; q < nq; q += nw) {
+        const int4 iv = wint[blockIdx.x * kMaxWinIntervals + q];
+        const double2* src = reinterpret_cast<const double2*>(xg + iv.x);
+        double2* dst = reinterpret_cast<double2*>(xw + iv.z);
+        for (int e = lane; e < (iv.y >> 1); e += 32) dst[e] = src[e];
+    }
+    __syncthreads();
+    double acc1 = 0.0, acc2 = 0.0;
+    for (int k = s0 + wid; k < s1; k += nw) {
+        const int o0 = __ldg(soff + k), R = __ldg(soff + k + 1) - o0;
+        const double* __restrict__ vk = val + (int64_t)o0 * (LM * kSlab) + lane;
+        const uint16_t* __restrict__ rk = rs + (int64_t)o0 * kSlab + lane;
+        // SP slots per step (8-16 values per lane), the next step's values
+        // loaded while this step's FMAs run; slot j of a step feeds
+        // accumulator j & 1
+        constexpr int SP = LM == 1 ? 8 : LM == 3 ? 4 : 2;
+        double a0 = 0.0, a1 = 0.0;
+        auto step = [&](const double (&v)[SP][LM], const int (&c)[SP], int live) {
+#pragma unroll
+            for (int j = 0; j < SP; j++)
+                if (j < live)
+#pragma unroll
+                    for (int o = 0; o < LM; o++) {
+                        if (j & 1) a1 = fma(v[j][o], xw[c[j] + o], a1);
+                        else a0 = fma(v[j][o], xw[c[j] + o], a0);
+                    }
+        };
+        int r = 0;
+        if (R >= SP) {
+            double v[SP][LM];
+            int c[SP];
+#pragma unroll
+            for (int j = 0; j < SP; j++) {
+                c[j] = __ldg(rk + j * kSlab);
+#pragma unroll
+                for (int o = 0; o < LM; o++) v[j][o] = __ldg(vk + (j * LM + o) * kSlab);
+            }
+#pragma unroll 1
+            for (; r + 2 * SP <= R; r += SP) {
+                double w[SP][LM];
+                int d[SP];
+#pragma unroll
+                for (int j = 0; j < SP; j++) {
+                    d[j] = __ldg(rk + (r + SP + j) * kSlab);
+#pragma unroll
+                    for (int o = 0; o < LM; o++) w[j][o] = __ldg(vk + ((r + SP + j) * LM + o) * kSlab);
+                }
+                step(v, c, SP);
+#pragma unroll
+                for (int j = 0; j < SP; j++) {
+                    c[j] = d[j];
+#pragma unroll
+                    for (int o = 0; o < LM; o++) v[j][o] = w[j][o];
+                }
+            }
+            step(v, c, SP);
+            r += SP;
+        }
+        if (r < R) {  // fewer than SP slots left: one predicated step
+            double v[SP][LM];
+            int c[SP];
+#pragma unroll
+            for (int j = 0; j < SP; j++) {
+                const bool in = r + j < R;
+                c[j] = in ? __ldg(rk + (r + j) * kSlab) : 0;
+#pragma unroll
+                for (int o = 0; o < LM; o++) v[j][o] = in ? __ldg(vk + ((r + j) * LM + o) * kSlab) : 0.0;
+            }
+            step(v, c, R - r);
+        }
+        const int i = k * kSlab + lane;
+        if (i < n) epi(i, a0 + a1, acc1, acc2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc1 += __shfl_xor_sync(FULL, acc1, o);
+        acc2 += __shfl_xor_sync(FULL, acc2, o);
+    }
+    if (lane == 0) {
+        red[0][wid] = acc1;
+        red[1][wid] = acc2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < nw; w++) {
+            t1 += red[0][w];
+            t2 += red[1][w];
+        }
+        if (part1) part1[blockIdx.x] = t1;
+        if (part2) part2[blockIdx.x] = t2;
+    }
+}
+
 // Run slots of each slab (the largest run count of its rows) and the
 // largest run length of the matrix (atomic max); a warp per slab.
 __global__ void k_sell_slots(int n, int nsl, const int32_t* __restrict__ rptr, const uint8_t* __restrict__ rlen,
@@ -585,17 +749,20 @@ __global__ void k_sell_intervals(int G, const int2* __restrict__ win, const int*
 // slot r at start c' = min(c, n - LM), its value q at offset q + c - c';
 // empty slots (r >= the row's runs, or no row) read LM zeros from the
 // slab's padding column (its first row's first start).
+// T: the value type of the copy (FP32, with an optional BF16 copy, for the
+// mixed-precision passes; FP64 for the plain FP64 passes).
+template <typename T>
 __global__ void __launch_bounds__(256) k_sell_fill(int n, int nsl, int G, int LM, int cap, int capr,
                                                    const int64_t* __restrict__ rp,
                                                    const int32_t* __restrict__ rptr, const uint8_t* __restrict__ rlen,
                                                    const int32_t* __restrict__ rst, const int32_t* __restrict__ soff,
                                                    const int2* __restrict__ win, const int* __restrict__ goff,
-                                                   const uint16_t* __restrict__ rank, const float* __restrict__ v32,
-                                                   float* o32, __nv_bfloat16* o16, uint16_t* ors) {
+                                                   const uint16_t* __restrict__ rank, const T* __restrict__ v32,
+                                                   T* o32, __nv_bfloat16* o16, uint16_t* ors) {
     pdl_entry();
     extern __shared__ __align__(16) unsigned char fill_smem[];
-    float* sv = reinterpret_cast<float*>(fill_smem);
-    int* srs = reinterpret_cast<int*>(fill_smem + 4 * (size_t)cap);
+    T* sv = reinterpret_cast<T*>(fill_smem);
+    int* srs = reinterpret_cast<int*>(fill_smem + sizeof(T) * (size_t)cap);
     __shared__ int mr0[kSlab], mri[kSlab], mli[kSlab];
     __shared__ int64_t me0[kSlab];
     for (int k = blockIdx.x; k < nsl; k += gridDim.x) {
@@ -607,11 +774,11 @@ __global__ void __launch_bounds__(256) k_sell_fill(int n, int nsl, int G, int LM
         if (staged) {  // eight loads in flight per thread before the stores
             constexpr int U = 8;
             for (int64_t q0 = ebase + threadIdx.x; q0 < eend; q0 += U * blockDim.x) {
-                float t[U];
+                T t[U];
 #pragma unroll
                 for (int u = 0; u < U; u++) {
                     const int64_t q = q0 + (int64_t)u * blockDim.x;
-                    t[u] = q < eend ? v32[q] : 0.f;
+                    t[u] = q < eend ? v32[q] : T(0);
                 }
 #pragma unroll
                 for (int u = 0; u < U; u++) {
@@ -664,7 +831,7 @@ __global__ void __launch_bounds__(256) k_sell_fill(int n, int nsl, int G, int LM
         for (int q = threadIdx.x; q < Rs * LM * kSlab; q += blockDim.x) {  // values
             const int t = q & (kSlab - 1), ro = q / kSlab;
             const int r = ro / LM, o = ro - r * LM;
-            float val = 0.f;
+            T val = T(0);
             if (r < mri[t]) {
                 const int c0 = runs[mr0[t] + r];
                 const int qv = o - (c0 - slot_start(c0, n, LM));
@@ -675,7 +842,8 @@ __global__ void __launch_bounds__(256) k_sell_fill(int n, int nsl, int G, int LM
             }
             const int64_t dst = (((int64_t)o0 + r) * LM + o) * kSlab + t;
             o32[dst] = val;
-            if (o16) o16[dst] = __float2bfloat16_rn(val);
+            if constexpr (sizeof(T) == 4)
+                if (o16) o16[dst] = __float2bfloat16_rn(val);
         }
     }
 }
@@ -757,7 +925,9 @@ cudaError_t sell_launch(amg_hierarchy* h, int q, const V* val, const float* x, c
 // slots (too few to occupy the 16 compute warps) or the window and two
 // buffers do not fit the shared-memory budget.
 int prepare_level(amg_hierarchy* h, SellLevel& S, int n, const int64_t* rp, const int32_t* rptr, const uint8_t* rlen,
-                  const int32_t* rst, const float* v32, bool with16, int* scratch, int optin) {
+                  const int32_t* rst, const float* v32, bool with16, int* scratch, int optin,
+                  const double* v64 = nullptr) {
+    const bool fp64 = v64 != nullptr;  // FP64 copy for k_sell64 (no copy ring), else FP32 (+ BF16) for k_sell
     constexpr int kMinSlots = 16;
     const int G = h->num_sms;
     if (n < 16) return AMG_OK;
@@ -792,19 +962,25 @@ int prepare_level(amg_hierarchy* h, SellLevel& S, int n, const int64_t* rp, cons
     // shared-memory shape
     const int64_t vb16 = (int64_t)rmax * LM * kSlab * 2, vb32 = (int64_t)rmax * LM * kSlab * 4;
     const int64_t rb = (int64_t)rmax * kSlab * 2;
-    if (vb32 + rb > (1 << 20)) return AMG_OK;
+    if (!fp64 && vb32 + rb > (1 << 20)) return AMG_OK;
     if (cudaMemcpyAsync(slots, hs.data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice, h->s) != cudaSuccess)
         return AMG_ERR_CUDA;
     // the sliced copy
     float* o32 = nullptr;
+    double* o64 = nullptr;
     __nv_bfloat16* o16 = nullptr;
     uint16_t* ors = nullptr;
     int2* swin = nullptr;
     int2* win = nullptr;
     const size_t nv = (size_t)total * LM * kSlab;
-    if (dev_alloc(reinterpret_cast<void**>(&o32), sizeof(float) * nv, h->s) != cudaSuccess) return AMG_ERR_NOMEM;
-    h->allocs.push_back(o32);
-    if (with16) {
+    if (fp64) {
+        if (dev_alloc(reinterpret_cast<void**>(&o64), sizeof(double) * nv, h->s) != cudaSuccess) return AMG_ERR_NOMEM;
+        h->allocs.push_back(o64);
+    } else {
+        if (dev_alloc(reinterpret_cast<void**>(&o32), sizeof(float) * nv, h->s) != cudaSuccess) return AMG_ERR_NOMEM;
+        h->allocs.push_back(o32);
+    }
+    if (with16 && !fp64) {
         if (dev_alloc(reinterpret_cast<void**>(&o16), sizeof(__nv_bfloat16) * nv, h->s) != cudaSuccess)
             return AMG_ERR_NOMEM;
         h->allocs.push_back(o16);
@@ -816,7 +992,7 @@ int prepare_level(amg_hierarchy* h, SellLevel& S, int n, const int64_t* rp, cons
     h->allocs.push_back(swin);
     if (dev_alloc(reinterpret_cast<void**>(&win), sizeof(int2) * G, h->s) != cudaSuccess) return AMG_ERR_NOMEM;
     h->allocs.push_back(win);
-    const void* arrays[] = {o32, o16, ors};
+    const void* arrays[] = {o32, o64, o16, ors};
     for (const void* a : arrays)
         if (a && (reinterpret_cast<uintptr_t>(a) & 15)) return AMG_OK;
     launch_pdl(k_sell_span, gw, 256, 0, h->s, n, nsl, LM, rptr, rst, slots, swin);
@@ -866,27 +1042,42 @@ int prepare_level(amg_hierarchy* h, SellLevel& S, int n, const int64_t* rp, cons
     int64_t xw = 16;
     for (int b = 0; b < G; b++) xw = std::max<int64_t>(xw, hwb[b]);
     int nb[2] = {0, 0};
-    for (int q = 0; q < 2; q++) {
-        const uint32_t vb = (uint32_t)(q == 0 ? vb16 : vb32);
-        for (int k = kSellBuf; k >= 2 && !nb[q]; k--) {
-            const SellShape sh{(uint32_t)xw, vb, (uint32_t)rb, k};
-            if (sell_smem_bytes(sh) + 256u <= (uint32_t)optin) nb[q] = k;  // 256: static shared memory
+    if (fp64) {  // the window in FP64 and the block's dot-product scratch
+        if (2 * xw + kS64Static > optin) return AMG_OK;
+    } else {
+        for (int q = 0; q < 2; q++) {
+            const uint32_t vb = (uint32_t)(q == 0 ? vb16 : vb32);
+            for (int k = kSellBuf; k >= 2 && !nb[q]; k--) {
+                const SellShape sh{(uint32_t)xw, vb, (uint32_t)rb, k};
+                if (sell_smem_bytes(sh) + 256u <= (uint32_t)optin) nb[q] = k;  // 256: static shared memory
+            }
         }
+        if (!nb[1] || (with16 && !nb[0])) return AMG_OK;
     }
-    if (!nb[1] || (with16 && !nb[0])) return AMG_OK;
     // stage: the largest slab's values and run starts (within the opt-in budget)
-    const int capr = (int)std::min<int64_t>((int64_t)rmax * kSlab, (optin - 1024) / 8);
-    const int cap = (int)std::min<int64_t>((int64_t)capr * LM, (optin - 1024 - 4 * (int64_t)capr) / 4);
-    const size_t fsm = 4 * (size_t)cap + 4 * (size_t)capr;
-    if (cudaFuncSetAttribute(k_sell_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm) != cudaSuccess)
-        return AMG_ERR_CUDA;
-    launch_pdl(k_sell_fill, std::min(nsl, 65535), 256, fsm, h->s, n, nsl, G, LM, cap, capr, rp, rptr, rlen, rst,
-               slots, win, goff, rank, v32, o32, o16, ors);
+    const int64_t es = fp64 ? 8 : 4;
+    const int capr = (int)std::min<int64_t>((int64_t)rmax * kSlab, (optin - 1024) / (4 + es));
+    const int cap = (int)std::min<int64_t>((int64_t)capr * LM, (optin - 1024 - 4 * (int64_t)capr) / es);
+    const size_t fsm = (size_t)es * cap + 4 * (size_t)capr;
+    if (fp64) {
+        if (cudaFuncSetAttribute(k_sell_fill<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm) !=
+            cudaSuccess)
+            return AMG_ERR_CUDA;
+        launch_pdl(k_sell_fill<double>, std::min(nsl, 65535), 256, fsm, h->s, n, nsl, G, LM, cap, capr, rp, rptr,
+                   rlen, rst, slots, win, goff, rank, v64, o64, nullptr, ors);
+    } else {
+        if (cudaFuncSetAttribute(k_sell_fill<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm) !=
+            cudaSuccess)
+            return AMG_ERR_CUDA;
+        launch_pdl(k_sell_fill<float>, std::min(nsl, 65535), 256, fsm, h->s, n, nsl, G, LM, cap, capr, rp, rptr,
+                   rlen, rst, slots, win, goff, rank, v32, o32, o16, ors);
+    }
     if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
     S.lm = LM;
     S.nsl = nsl;
     S.soff = slots;
     S.v32 = o32;
+    S.v64 = o64;
     S.v16 = o16;
     S.rs = ors;
     S.vbytes[0] = (int)vb16;
@@ -992,6 +1183,97 @@ cudaError_t sell_resid1(amg_hierarchy* h, const float* f, const float* x, float*
 cudaError_t sell_upy1(amg_hierarchy* h, const float* f, const float* x, const float* invd, float* y, cudaStream_t s) {
     const EpiUpY epi{{f, invd, x}, {4, 4, 4}, 3, y};
     return sell_launch_lm<1>(h, h->sell[1], h->lev[1].A.n, 1, h->sell[1].v32, x, epi, nullptr, nullptr, s);
+}
+
+// ------------------------------------------------------------------ FP64
+namespace {
+
+template <int LM, typename Epi>
+cudaError_t sell64_launch_lm(amg_hierarchy* h, const double* x, const Epi& epi, double* p1, double* p2,
+                             cudaStream_t s) {
+    const SellLevel& S = h->sell[0];
+    launch_pdl(k_sell64<LM, Epi>, h->num_sms, h->sell64_warps * 32, 2 * (size_t)S.xbytes, s, h->lev[0].A.n, S.nsl,
+               S.soff, static_cast<const double*>(S.v64), S.rs, x, static_cast<const int4*>(S.wint), S.wcnt, epi,
+               p1, p2, h->st);
+    return cudaGetLastError();
+}
+
+template <typename Epi>
+cudaError_t sell64_launch(amg_hierarchy* h, const double* x, const Epi& epi, double* p1, double* p2, cudaStream_t s) {
+    switch (h->sell[0].lm) {
+        case 3: return sell64_launch_lm<3>(h, x, epi, p1, p2, s);
+        case 5: return sell64_launch_lm<5>(h, x, epi, p1, p2, s);
+        case 7: return sell64_launch_lm<7>(h, x, epi, p1, p2, s);
+        default: return sell64_launch_lm<9>(h, x, epi, p1, p2, s);
+    }
+}
+
+// A warp takes whole slabs, so a block's time goes as ceil(slabs / W) W for
+// the block with the most slabs (the FP64 pipe is shared by its W warps).
+int sell64_pick_warps(const SellLevel& S, int G) {
+    const int cmax = (S.nsl + G - 1) / G;
+    int best = kS64MaxWarps;
+    for (int w = kS64MaxWarps; w >= kS64MinWarps; w--)
+        if (((cmax + w - 1) / w) * w < ((cmax + best - 1) / best) * best) best = w;
+    return best;
+}
+
+template <int LM>
+bool sell64_attrs_lm(int smem) {
+    return cudaFuncSetAttribute(k_sell64<LM, Epi64PQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(k_sell64<LM, Epi64Resid>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(k_sell64<LM, Epi64Up0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+               cudaSuccess;
+}
+
+}  // namespace
+
+// Plain FP64 solve: the sliced copy of the run-encoded finest level with FP64
+// values; sets h->sell64 when it applies, else leaves the hierarchy unchanged.
+int sell64_prepare(amg_hierarchy* h, int* scratch) {
+    h->sell64 = 0;
+    Level& F0 = h->lev[0];
+    SellLevel& S = h->sell[0];
+    if (h->mixed || !F0.run_ptr || h->nlev < 2) return AMG_OK;
+    const void* arrays[] = {F0.A.rowptr, F0.A.val, F0.x, F0.t, F0.invd, h->p, h->r, h->q, h->z};
+    for (const void* a : arrays)
+        if (a && (reinterpret_cast<uintptr_t>(a) & 15)) return AMG_OK;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return AMG_ERR_CUDA;
+    const int rc = prepare_level(h, S, F0.A.n, F0.A.rowptr, F0.run_ptr, F0.run_len, F0.run_start, nullptr, false,
+                                 scratch, optin, F0.A.val);
+    if (rc != AMG_OK || !S.on) return rc;
+    const int smem = 2 * S.xbytes;
+    bool attrs;
+    switch (S.lm) {
+        case 3: attrs = sell64_attrs_lm<3>(smem); break;
+        case 5: attrs = sell64_attrs_lm<5>(smem); break;
+        case 7: attrs = sell64_attrs_lm<7>(smem); break;
+        default: attrs = sell64_attrs_lm<9>(smem); break;
+    }
+    if (!attrs) return AMG_ERR_CUDA;
+    h->sell64_warps = sell64_pick_warps(S, h->num_sms);
+    h->stream_blocks = h->num_sms;
+    h->sell64 = 1;
+    return AMG_OK;
+}
+
+cudaError_t sell64_spmv_pq(amg_hierarchy* h, const double* p, const double* r, double* q, double* part_pq,
+                           double* part_pr, int flexible, cudaStream_t s) {
+    return sell64_launch(h, p, Epi64PQ{p, r, q, flexible}, part_pq, flexible ? part_pr : nullptr, s);
+}
+
+cudaError_t sell64_resid(amg_hierarchy* h, const double* f, const double* x, double* rbuf, cudaStream_t s) {
+    return sell64_launch(h, x, Epi64Resid{f, rbuf}, nullptr, nullptr, s);
+}
+
+cudaError_t sell64_up0(amg_hierarchy* h, const double* r, const double* x, const double* invd, double* z,
+                       const double* q, double* part_rz, double* part_zq, int flexible, cudaStream_t s) {
+    return sell64_launch(h, x, Epi64Up0{r, x, invd, z, q, flexible}, part_rz, flexible ? part_zq : nullptr, s);
 }
 
 }  // namespace amg

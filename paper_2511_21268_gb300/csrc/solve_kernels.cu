@@ -466,6 +466,13 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
                 A* rb = xalt[l];  // free buffer of this level holds the residual
                 const A* xc = xcur[l];
                 if (l == 0) prof_mark(h, 1, 0, s);
+                if constexpr (std::is_same_v<A, double>) {
+                    if (l == 0 && h->sell64) {
+                        sell64_resid(h, h->r, xc, rb, s);
+                        prof_mark(h, 1, 1, s);
+                        return;
+                    }
+                }
                 if constexpr (std::is_same_v<A, float>) {
                     if (l == 0 && h->stream) {
                         launch_stream_resid(h, h->r, xc, rb, s);
@@ -522,6 +529,13 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
             const A* xc = xcur[l];
             if (l == 0) {
                 prof_mark(h, 2, 0, s);
+                if constexpr (std::is_same_v<A, double>) {
+                    if (h->sell64) {
+                        sell64_up0(h, h->r, xc, Vw::invd(F), h->z, h->q, slot(h, S_RZ), slot(h, S_ZQ), flex, s);
+                        prof_mark(h, 2, 1, s);
+                        return;
+                    }
+                }
                 if constexpr (std::is_same_v<A, float>) {
                     if (h->stream) {
                         launch_stream_up0(h, h->r, xc, Vw::invd(F), h->z, h->q, slot(h, S_RZ), slot(h, S_ZQ), flex,
@@ -571,7 +585,7 @@ static int nb_res(amg_hierarchy* h) {
     return b < cap ? b : cap;
 }
 // partial sums written by the level-0 q = K p and up-sweep kernels
-static int nb_fine(amg_hierarchy* h) { return h->stream ? h->stream_blocks : nb0(h); }
+static int nb_fine(amg_hierarchy* h) { return (h->stream || h->sell64) ? h->stream_blocks : nb0(h); }
 static int nbz(amg_hierarchy* h) { return h->nlev > 1 ? nb_fine(h) : row_blocks(h->ndense, 1); }
 
 size_t partial_slot_size(int n0, int num_sms) {
@@ -636,6 +650,8 @@ cudaError_t enqueue_pcg_iteration(amg_hierarchy* h, cudaStream_t s) {
         constexpr int RPW = decltype(R)::value;
         if (h->mixed && h->stream)
             launch_stream_spmv_pq(h, h->p32, h->p, h->r, h->q, slot(h, S_PQ), slot(h, S_PR), flex, s);
+        else if (h->sell64)
+            sell64_spmv_pq(h, h->p, h->r, h->q, slot(h, S_PQ), slot(h, S_PR), flex, s);
         else if (h->mixed)
             with_mat(L0, static_cast<const float*>(L0.val32), [&](auto mat) {
                 launch_pdl(k_spmv_pq<RPW, float, decltype(mat), float>, nb, kBlock, 0, s,

@@ -100,19 +100,53 @@ def test_level_spmv_matches_oracle(d, n, p):
         assert np.abs(y - yo).max() <= SPMV_RTOL * np.abs(yo).max() * 10
 
 
+def sliced_fp64_expected(prob):
+    """The FP64 sliced passes (staged_passes 3) apply when the 32-row slabs
+    average at least 16 run slots (the largest run count of their rows)."""
+    rp, ci = prob.rowptr, prob.col
+    runs = np.array([1 + np.count_nonzero(np.diff(ci[rp[i]:rp[i + 1]]) != 1) for i in range(prob.n)])
+    nsl = (prob.n + 31) // 32
+    pad = np.zeros(nsl * 32, dtype=runs.dtype)
+    pad[:prob.n] = runs
+    return pad.reshape(nsl, 32).max(axis=1).mean() >= 16
+
+
 @pytest.mark.parametrize("d,n,p", CASES)
 @pytest.mark.parametrize("nu", [(1, 1), (2, 3)])
-@pytest.mark.parametrize("fmt", [0, 1], ids=["csr", "runs"])
+@pytest.mark.parametrize("fmt", [0, 1, 2], ids=["csr", "runs", "sliced"])
 def test_vcycle_matches_oracle(d, n, p, nu, fmt):
     prob = I.poisson_box(d, n, p)
     H, Ho = setup_both(prob, coarse_max=20, nu_pre=nu[0], nu_post=nu[1], matrix_format=fmt)
-    assert H.info.level_format[0] == fmt  # tensor-product rows: equal runs of consecutive columns
+    # tensor-product rows: equal runs of consecutive columns
+    assert H.info.level_format[0] == min(fmt, 1)
+    sliced = fmt == 2 and H.num_levels > 1 and sliced_fp64_expected(prob)
+    assert H.info.staged_passes == (3 if sliced else 0)
+    if sliced:
+        assert H.info.staged_slots >= prob.nnz and H.info.staged_window_bytes > 0
+    assert H.info.staged_level1 == 0  # level 1 runs sliced only in mixed precision
     rng = np.random.default_rng(1)
     for _ in range(3):
         r = rng.standard_normal(prob.n)
         z = H.vcycle(gpu(r)).cpu().numpy()
         zo = Ho.vcycle(r)
         assert np.linalg.norm(z - zo) <= VCYCLE_RTOL * np.linalg.norm(zo)
+
+
+@pytest.mark.parametrize("d,n,p", [(3, 16, 3), (3, 14, 2)])
+def test_fp64_sliced_finest_passes_match_oracle(d, n, p):
+    """FP64 sliced passes on the finest level (run slots of LM values, a warp
+    per slab), on hierarchies with several blocks' worth of slabs: the
+    V-cycle and the solve against the oracle."""
+    prob = I.poisson_box(d, n, p)
+    H, Ho = setup_both(prob, coarse_max=20)
+    assert H.info.staged_passes == 3 and H.info.staged_level1 == 0
+    rng = np.random.default_rng(4)
+    for _ in range(2):
+        r = rng.standard_normal(prob.n)
+        z = H.vcycle(gpu(r)).cpu().numpy()
+        zo = Ho.vcycle(r)
+        assert np.linalg.norm(z - zo) <= VCYCLE_RTOL * np.linalg.norm(zo)
+    compare_solves(prob, 1e-8, coarse_max=20)
 
 
 def compare_solves(prob, rtol, flexible=False, **opts):

@@ -625,8 +625,8 @@ int alloc_level(amg_hierarchy* h, int l) {
     return AMG_OK;
 }
 
-// Node and edge features of level l (Sec. 4.2) on stream s; the buffers must
-// be allocated and ordered before s.
+// Node features and edge weights of level l (see the file header) on stream
+// s; the buffers must be allocated and ordered before s.
 void features_level(amg_hierarchy* h, int l, cudaStream_t s) {
     MpnnLevel& m = h->mp->lev[l];
     if (m.features) return;
@@ -693,8 +693,8 @@ int prepare(amg_hierarchy* h) {
     return AMG_OK;
 }
 
-// omega of level l from the network (Sec. 4.2: encoder, two message-passing
-// layers, decoder; FP32 arithmetic, weights rounded to BF16 first when
+// omega of level l from the network (input layer, two message-passing
+// layers, output; FP32 arithmetic, weights rounded to BF16 first when
 // bf16 != 0), on stream s.
 void forward_level(amg_hierarchy* h, int l, const float* wd, int bf16, cudaStream_t s) {
     const Level& L = h->lev[l];

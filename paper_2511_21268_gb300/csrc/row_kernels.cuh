@@ -23,16 +23,16 @@ __device__ __forceinline__ double ldv(const double* v, int64_t k) { return __ldg
 __device__ __forceinline__ float ldv(const float* v, int64_t k) { return __ldg(v + k); }
 __device__ __forceinline__ float ldv(const __nv_bfloat16* v, int64_t k) { return __bfloat162float(v[k]); }
 
-// Lane partial of row i: sum over k = b + lane + 32 t of v_k x_{c_k}, in A,
-// with xload(c) giving x_c (the same FMA chain for every U).  The rows this runs on (levels with few rows,
-// a warp per row) are latency-bound: each chunk of U entries per lane loads
-// all its values and columns, then all its x entries, then runs the FMA
-// chain in entry order, and the last partial chunk does the same with
-// predicated loads, so a row of up to 32 U entries costs two dependent
-// round trips.
-template <int U, typename A, typename V, typename XL>
-__device__ __forceinline__ A lane_partial_with(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                               const V* __restrict__ v, XL xload, int i, int lane) {
+// Lane partial of row i: sum over k = b + lane + 32 t of v_k x_{c_k}, in A.
+// The rows this runs on (levels with few rows, a warp per row) are
+// latency-bound: each chunk of U entries per lane loads all its values and
+// columns, then all its x entries, then runs the FMA chain in entry order,
+// and the last partial chunk does the same with predicated loads, so a row
+// of up to 32 U entries costs two dependent round trips.
+template <typename A, typename V, typename X>
+__device__ __forceinline__ A lane_partial(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                          const V* __restrict__ v, const X* __restrict__ x, int i, int lane) {
+    constexpr int U = sizeof(A) == 4 ? 16 : 8;
     const int64_t b = rp[i], e = rp[i + 1];
     A acc = A(0);
     int64_t k = b + lane;
@@ -45,7 +45,7 @@ __device__ __forceinline__ A lane_partial_with(const int64_t* __restrict__ rp, c
             cc[u] = __ldg(ci + k + 32 * u);
         }
 #pragma unroll
-        for (int u = 0; u < U; u++) xx[u] = xload(cc[u]);
+        for (int u = 0; u < U; u++) xx[u] = (A)x[cc[u]];
 #pragma unroll
         for (int u = 0; u < U; u++) acc = fma(vv[u], xx[u], acc);
     }
@@ -59,18 +59,12 @@ __device__ __forceinline__ A lane_partial_with(const int64_t* __restrict__ rp, c
             cc[u] = in ? __ldg(ci + k + 32 * u) : -1;
         }
 #pragma unroll
-        for (int u = 0; u < U - 1; u++) xx[u] = cc[u] >= 0 ? xload(cc[u]) : A(0);
+        for (int u = 0; u < U - 1; u++) xx[u] = cc[u] >= 0 ? (A)x[cc[u]] : A(0);
 #pragma unroll
         for (int u = 0; u < U - 1; u++)
             if (cc[u] >= 0) acc = fma(vv[u], xx[u], acc);
     }
     return acc;
-}
-
-template <typename A, typename V, typename X>
-__device__ __forceinline__ A lane_partial(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                          const V* __restrict__ v, const X* __restrict__ x, int i, int lane) {
-    return lane_partial_with<sizeof(A) == 4 ? 16 : 8, A>(rp, ci, v, [&](int c) { return (A)x[c]; }, i, lane);
 }
 
 // Matrix views of the row-group kernels.  CsrM: plain CSR.  RunM: CSR

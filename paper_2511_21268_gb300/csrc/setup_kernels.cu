@@ -1133,6 +1133,11 @@ cudaError_t launch_galerkin_mirror(DevCSR& C, int* flag, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Threads per block of the bitmap Galerkin kernels: a coarse row of a 3-D
+// p=3 level holds about 700 fine entries, so small blocks spend less of their
+// time waiting at the row's block barriers and more rows are in flight per SM.
+constexpr int kGalerkinBlock = 128;
+
 static size_t bitmap_smem(int cap, int words, bool fill) {
     return 8 * (size_t)words + (fill ? 16 * (size_t)cap : 0);
 }
@@ -1142,7 +1147,7 @@ cudaError_t launch_galerkin_count_bitmap(const DevCSR& A, const int32_t* agg, co
     const size_t sm = bitmap_smem(cap, words, false);
     if (sm > 48 * 1024)
         AMG_TRY(cudaFuncSetAttribute(k_galerkin_bitmap<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_galerkin_bitmap<false><<<AMG_GRID(blocks_for(nc, 1, 65536)), kBlock, sm, s>>>(
+    k_galerkin_bitmap<false><<<AMG_GRID(blocks_for(nc, 1, 65536)), kGalerkinBlock, sm, s>>>(
         nc, A.rowptr, A.col, A.val, agg, nullptr, mem0, mem1, cap, words, rowcnt, nullptr, nullptr, nullptr, flag);
     return cudaGetLastError();
 }
@@ -1152,7 +1157,7 @@ cudaError_t launch_galerkin_fill_bitmap(const DevCSR& A, const int32_t* agg, con
     const size_t sm = bitmap_smem(cap, words, true);
     if (sm > 48 * 1024)
         AMG_TRY(cudaFuncSetAttribute(k_galerkin_bitmap<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_galerkin_bitmap<true><<<AMG_GRID(blocks_for(C.n, 1, 65536)), kBlock, sm, s>>>(
+    k_galerkin_bitmap<true><<<AMG_GRID(blocks_for(C.n, 1, 65536)), kGalerkinBlock, sm, s>>>(
         C.n, A.rowptr, A.col, A.val, agg, pval, mem0, mem1, cap, words, nullptr, C.rowptr, C.col, C.val, flag);
     return cudaGetLastError();
 }

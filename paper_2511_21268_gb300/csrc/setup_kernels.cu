@@ -78,7 +78,9 @@ __device__ __forceinline__ double fold_rows(int row0, int n, const int64_t* __re
     const int maxlen = __reduce_max_sync(FULL, mlen);
     double acc = 0.0;
     for (int c = 0; c < maxlen; c += 32) {
-#pragma unroll 4
+        // up to 16 rows' loads in flight per lane (three blocks per SM fit
+        // the tiles' shared memory)
+#pragma unroll 16
         for (int r = 0; r < 32; r++) {
             const int64_t rb = __shfl_sync(FULL, mb, r);
             const int rl = __shfl_sync(FULL, mlen, r);

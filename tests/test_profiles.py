@@ -43,3 +43,21 @@ def test_bench_reads_traffic_for_the_three_passes():
         for k in want:
             # a full 3-D p=3 n=64 launch moves hundreds of MB
             assert 1e8 < float(got[k]) < 2e9, (path, k, got[k])
+
+
+def test_a_stale_summary_reports_no_traffic(tmp_path):
+    """bench.py takes traffic from a summary only while the recorded SHA-256
+    matches the current kernel sources; otherwise it reports null."""
+    import hashlib
+
+    b = load_bench()
+    src = ("sell_kernels.cu",)
+    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2511_21268_gb300", "csrc", src[0]), "rb").read()).hexdigest()
+    body = "traffic_bytes_per_launch[pq]: 123456789\n"
+    good = tmp_path / "good.md"
+    good.write_text(body + f"source_sha256: {h}\n")
+    stale = tmp_path / "stale.md"
+    stale.write_text(body + "source_sha256: " + "0" * 64 + "\n")
+    assert b.committed_traffic(str(good), src) == {"pq": 123456789.0}
+    assert b.committed_traffic(str(stale), src) is None
+    assert b.committed_traffic(str(tmp_path / "missing.md"), src) is None

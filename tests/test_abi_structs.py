@@ -56,3 +56,30 @@ def test_info_struct_mirrors_header():
 
 def test_csr_struct_mirrors_header():
     check("amg_csr", amg.AmgCsr)
+
+
+def test_documented_option_defaults_are_the_defaults():
+    """Each amg_opts field's header comment ends with its default in
+    parentheses; amg_opts_default (host only) must fill exactly those."""
+    from paper_2511_21268_gb300 import _build
+
+    src = open(os.path.join(ROOT, "include", "amg_gb300.h")).read()
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*amg_opts\s*;", src).group(1)
+    documented = {}
+    for m in re.finditer(r"([A-Za-z_0-9 \*]+?)\s*;\s*/\*(.*?)\*/", body, flags=re.S):
+        field = m.group(1).split()[-1].lstrip("*")
+        default = re.findall(r"\(([^()]*)\)\s*$", " ".join(m.group(2).split()))
+        assert default, field
+        documented[field] = default[0]
+    assert set(documented) == {f for f, _ in amg.AmgOpts._fields_}
+    L = ctypes.CDLL(_build.build_cuda())
+    o = amg.AmgOpts()
+    assert L.amg_opts_default(ctypes.byref(o)) == 0
+    for field, text in documented.items():
+        got = getattr(o, field)
+        if text == "NULL":
+            assert got is None, field
+        elif text.startswith("AMG_"):
+            assert got == getattr(amg, text), field
+        else:
+            assert got == type(got)(float(text) if "." in text else int(text)), (field, got, text)

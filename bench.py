@@ -128,6 +128,40 @@ def fp64_peak_tflops():
     return sms * mhz * 1e6 * 2 * 2 / 1e12
 
 
+def measure_fp64_rate(A, torch, stream, uuid, seconds=2.0):
+    """FP64 FMA rate of this GPU, measured: the library's FMA probe kernel
+    (8 independent chains per thread, 8 blocks of 256 threads per SM) timed
+    with CUDA events on its stream over about `seconds`, SM clocks sampled
+    meanwhile.  Returns (TFLOP/s, clocks)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    blocks = torch.cuda.get_device_properties(dev).multi_processor_count * 8
+    out = torch.empty(blocks * 256, dtype=torch.float64, device=dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    trips = 64
+    for _ in range(4):  # calibrate one launch to about 0.25 s
+        e0.record(stream)
+        A.amg_dfma_probe(blocks, trips, out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        trips = max(64, int(trips * 250.0 / max(ms, 1e-3)))
+    launches = max(3, int(seconds / 0.25))
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.2)
+    e0.record(stream)
+    flops = 0.0
+    for _ in range(launches):
+        flops += A.amg_dfma_probe(blocks, trips, out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if not torch.isfinite(out).all():
+        raise RuntimeError("FP64 probe produced non-finite values")
+    return flops / (e0.elapsed_time(e1) * 1e-3) / 1e12, clk
+
+
 class ClockSampler:
     FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -201,30 +235,45 @@ def max_over_ranks(dist, x: float) -> float:
 
 # ------------------------------------------------------------------- oracle
 def cpu_baseline(prob, iters_gpu: int, rtol: float) -> dict:
-    """Time the CPU oracle on a bounded sample of the workload: the full setup,
-    CG with itmax = 0 (the start: median of three runs) and with itmax = 3
+    """Time the CPU oracle on a bounded sample of the workload: the full setup
+    (sequential: the greedy matching is defined by a sequential scan), CG
+    with itmax = 0 (the start: median of three runs) and with itmax = 3
     (three iterations beyond the start), scaled to the iteration count of the
-    GPU solve (the two agree within +-1)."""
+    GPU solve (the two agree within +-1).  The solve phase is timed on one
+    core and with its row loops on all host cores (same results)."""
     import oracle as O
 
+    cores = os.cpu_count() or 1
     t0 = time.perf_counter()
     H = O.Hierarchy(prob.rowptr, prob.col, prob.val)
     t_setup = time.perf_counter() - t0
-    starts = []
-    for _ in range(3):
-        t0 = time.perf_counter()
-        H.pcg(prob.F, rtol=rtol, itmax=0)
-        starts.append(time.perf_counter() - t0)
-    t_start = statistics.median(starts)
-    t0 = time.perf_counter()
-    H.pcg(prob.F, rtol=rtol, itmax=3)
-    t_iter = max((time.perf_counter() - t0 - t_start) / 3, 0.0)
-    value = t_setup + t_start + iters_gpu * t_iter
-    return {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"full oracle setup ({t_setup:.2f} s) + CG start ({t_start:.3f} s, median of 3) + "
-                       f"{t_iter:.3f} s per CG iteration (three iterations timed) on the full system, scaled to "
-                       f"{iters_gpu} iterations; single-threaded plain C oracle"),
-            "setup_s": t_setup, "iter_s": t_iter}
+
+    def solve_phase(threads):
+        used = O.set_threads(threads)
+        try:
+            starts = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                H.pcg(prob.F, rtol=rtol, itmax=0)
+                starts.append(time.perf_counter() - t0)
+            t_start = statistics.median(starts)
+            t0 = time.perf_counter()
+            H.pcg(prob.F, rtol=rtol, itmax=3)
+            t_iter = max((time.perf_counter() - t0 - t_start) / 3, 0.0)
+        finally:
+            O.set_threads(1)
+        return used, t_start, t_iter
+
+    _, s1, i1 = solve_phase(1)
+    used, sn, iN = solve_phase(cores)
+    v1 = t_setup + s1 + iters_gpu * i1
+    vn = t_setup + sn + iters_gpu * iN
+    return {"value": vn, "unit": "s", "cores": used, "kind": "oracle",
+            "sample": (f"full oracle setup ({t_setup:.2f} s, sequential) + CG start ({sn:.3f} s, median of 3) + "
+                       f"{iN:.3f} s per CG iteration (three iterations timed) on the full system, scaled to "
+                       f"{iters_gpu} iterations; plain C oracle, solve-phase row loops on {used} threads"),
+            "setup_s": t_setup, "iter_s": iN,
+            "one_core": {"value": v1, "cores": 1, "iter_s": i1, "start_s": s1}}
 
 
 def run_reference(args):
@@ -271,8 +320,54 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------- ours
+CONST_SWEEP = (1.0, 1.5, 1.8, 1.9, 1.95, 2.0, 2.2, 2.4, 2.6)
+
+
+def omega_stats(A, h, torch):
+    """min / max / mean / std of the installed network damping per smoothed
+    level, with the level's cap omega_max = 2 / lam_hat."""
+    info = A.amg_get_info(h)
+    out = []
+    for l in range(info.levels - 1):
+        om = A.amg_mpnn_omega(h, l, int(info.n[l])).double()
+        out.append({"level": l, "rows": int(info.n[l]), "min": float(om.min()), "max": float(om.max()),
+                    "mean": float(om.mean()), "std": float(om.std()),
+                    "omega_max": 2.0 / A.amg_smoother_bound(h, l)})
+    return out
+
+
+def constant_sweep(A, h, F, rtol, torch):
+    """PCG iterations with the constant damping omega on every smoothed
+    level, for each omega of CONST_SWEEP (None where the solve fails)."""
+    its = {}
+    for om in CONST_SWEEP:
+        A.amg_set_damping(h, om)
+        st, it, _ = A.amg_pcg_solve(h, F, torch.zeros_like(F), rtol, 3000)
+        its[om] = it if st == A.AMG_OK else None
+    A.amg_set_damping(h, 1.0)
+    ok = {o: i for o, i in its.items() if i is not None}
+    best = min(ok, key=lambda o: (ok[o], o))
+    return its, best
+
+
+def timed_steps(step, k, warm, stream, torch, dist):
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize()
+    barrier(dist)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        out = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return max_over_ranks(dist, e0.elapsed_time(e1)) / k, out
+
+
 def learned_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, ref_u, fp64_ms, mixed_ms):
-    """Mixed precision + learned smoother damping on the bench workload."""
+    """Mixed precision + learned smoother damping on the bench workload,
+    against mixed precision with the best constant damping of a sweep."""
     dev = F.device
     # training set: 3-D cube hierarchies, p in {2, 3, 4}, n = 16 (FP64)
     train = []
@@ -289,11 +384,13 @@ def learned_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, ref_u, fp64_
         A.amg_free(h)
     mopts = A.amg_opts_default(precision=A.AMG_FP32_BF16FINE, matrix_format=args.matrix_format)
 
-    # fallback rule on the workload itself (untimed): learned only if no worse
+    # constant damping sweep and the fallback rule against the best constant (untimed)
     h = A.amg_setup(rp, ci, va, mopts, stream)
-    used, it_plain, it_learned = A.amg_mpnn_select(h, w, F, args.rtol, 10000)
-    # inference time alone (features are computed on the first call)
+    sweep, best = constant_sweep(A, h, F, args.rtol, torch)
+    used, it_best, it_learned = A.amg_mpnn_select(h, w, F, args.rtol, 10000, omega_ref=best)
+    # inference time alone (features and damping caps are computed on the first call)
     A.amg_mpnn_apply(h, w, True)
+    stats = omega_stats(A, h, torch)
     i0 = torch.cuda.Event(enable_timing=True)
     i1 = torch.cuda.Event(enable_timing=True)
     i0.record(stream)
@@ -312,7 +409,7 @@ def learned_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, ref_u, fp64_
     # the weights go to the setup: the finest level's network overlaps the
     # coarse-level setup on a second stream
     lopts = A.amg_opts_default(precision=A.AMG_FP32_BF16FINE, matrix_format=args.matrix_format,
-                               mpnn_weights=w, mpnn_bf16=1) if used else mopts
+                               mpnn_weights=w, mpnn_bf16=1)
 
     def lstep():
         h = A.amg_setup(rp, ci, va, lopts, stream)
@@ -324,33 +421,47 @@ def learned_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, ref_u, fp64_
             raise RuntimeError(f"learned solve failed: {A.amg_strerror(st)}")
         return u, it, rr, info
 
-    for _ in range(args.warmup):
-        lstep()
-    torch.cuda.synchronize()
-    barrier(dist)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    def cstep():
+        h = A.amg_setup(rp, ci, va, mopts, stream)
+        A.amg_set_damping(h, best)
+        u = torch.zeros_like(F)
+        st, it, rr = A.amg_pcg_solve(h, F, u, args.rtol, 10000)
+        info = A.amg_get_info(h)
+        A.amg_free(h)
+        if st != A.AMG_OK:
+            raise RuntimeError(f"constant-damping solve failed: {A.amg_strerror(st)}")
+        return u, it, rr, info
+
     torch.cuda.nvtx.range_push("learned")
-    e0.record(stream)
-    for _ in range(args.steps):
-        lu, lit, lrr, linfo = lstep()
-    e1.record(stream)
-    torch.cuda.synchronize()
+    l_ms, (lu, lit, lrr, linfo) = timed_steps(lstep, args.steps, args.warmup, stream, torch, dist)
     torch.cuda.nvtx.range_pop()
-    l_ms = max_over_ranks(dist, e0.elapsed_time(e1)) / args.steps
+    c_ms, (cu, cit, crr, cinfo) = timed_steps(cstep, args.steps, args.warmup, stream, torch, dist)
+    # the fallback rule's choice is what a user gets
+    chosen_ms = l_ms if used else c_ms
     err = float(torch.linalg.norm(lu - ref_u) / torch.linalg.norm(ref_u))
-    return {"time_to_solution_s": l_ms / 1e3, "speedup_vs_fp64": fp64_ms / l_ms, "speedup_vs_mixed": mixed_ms / l_ms,
-            "iters": lit, "iters_mixed_plain": it_plain, "iters_fp64_learned": it64, "learned_kept": bool(used),
-            "final_relres_fp64": lrr, "rel_error_vs_fp64_solution": err, "inference_ms_alone": infer_ms,
-            "setup_ms": linfo.setup_ms, "setup_damping_phase_ms": linfo.setup_phase_ms[9],
-            "solve_ms": linfo.solve_ms,
+    cerr = float(torch.linalg.norm(cu - ref_u) / torch.linalg.norm(ref_u))
+    return {"time_to_solution_s": chosen_ms / 1e3, "speedup_vs_fp64": fp64_ms / chosen_ms,
+            "speedup_vs_mixed": mixed_ms / chosen_ms, "used": "learned" if used else f"constant omega {best}",
+            "network": {"time_to_solution_s": l_ms / 1e3, "iters": lit, "speedup_vs_fp64": fp64_ms / l_ms,
+                        "speedup_vs_best_constant": c_ms / l_ms, "final_relres_fp64": lrr,
+                        "rel_error_vs_fp64_solution": err, "setup_ms": linfo.setup_ms,
+                        "setup_damping_phase_ms": linfo.setup_phase_ms[9], "solve_ms": linfo.solve_ms,
+                        "inference_ms_alone": infer_ms, "omega": stats, "iters_fp64_learned": it64},
+            "best_constant": {"omega": best, "time_to_solution_s": c_ms / 1e3, "iters": cit,
+                              "speedup_vs_fp64": fp64_ms / c_ms, "final_relres_fp64": crr,
+                              "rel_error_vs_fp64_solution": cerr, "setup_ms": cinfo.setup_ms,
+                              "solve_ms": cinfo.solve_ms},
+            "constant_sweep_iters": {str(k): v for k, v in sweep.items()},
+            "fallback_rule": {"reference": f"constant omega {best}", "iters_reference": it_best,
+                              "iters_learned": it_learned, "learned_kept": bool(used)},
             "training": {"set": "3-D cube p in {2,3,4}, n=16, FP64 hierarchies", "steps": args.train_steps,
                          "probes": 4, "lr": 1e-2, "seconds": train_s,
                          "loss_first": float(hist[0]) if len(hist) else None,
                          "loss_last": float(hist[-1]) if len(hist) else None},
             "precision": "network BF16 weights / FP32 arithmetic; mixed-precision solve as in 'mixed'",
-            "timed_step": "setup with the network weights (finest-level features and network on a second stream "
-                          "alongside the coarse-level setup; coarse levels and install at its end) + solve + free"}
+            "timed_step": "network: setup with the network weights (finest-level features, damping cap and network "
+                          "on a second stream alongside the coarse-level setup; coarse levels and install at its "
+                          "end) + solve + free; constant: setup + amg_set_damping + solve + free"}
 
 
 def batched_leg(args, A, I, torch, np, stream):
@@ -488,15 +599,35 @@ def annulus_leg(args, A, I, torch, np, stream, dist):
     t64, u64, it64, rr64 = timed(o64, False, k)
     tml, uml, itml, rrml = timed(omx, True, k)
     h = A.amg_setup(rp, ci, va, omx, stream)
-    used, ip, il = A.amg_mpnn_select(h, w, F, args.rtol, 20000)
+    sweep, best = constant_sweep(A, h, F, args.rtol, torch)
+    used, ip, il = A.amg_mpnn_select(h, w, F, args.rtol, 20000, omega_ref=best)
+    A.amg_mpnn_apply(h, w, True)
+    stats = omega_stats(A, h, torch)
     A.amg_free(h)
+
+    def cstep():
+        h = A.amg_setup(rp, ci, va, omx, stream)
+        A.amg_set_damping(h, best)
+        u = torch.zeros_like(F)
+        st, it, rr = A.amg_pcg_solve(h, F, u, args.rtol, 20000)
+        A.amg_free(h)
+        if st != A.AMG_OK:
+            raise RuntimeError(f"annulus constant-damping solve failed: {A.amg_strerror(st)}")
+        return it
+
+    tc, itc = timed_steps(cstep, k, 2, stream, torch, dist)
     err = float(torch.linalg.norm(uml - u64) / torch.linalg.norm(u64))
     return {"workload": "quarter annulus x [0,1], NURBS geometry, B-spline p=3 C^2, n=64 (N=274,625, nnz=86,938,307), "
                         "kappa = exp(g), random Fourier features M=256, l=0.2, sigma=1",
             "assembly_s": asm_s, "fp64_time_to_solution_s": t64 / 1e3, "fp64_iters": it64,
             "mixed_learned_time_to_solution_s": tml / 1e3, "mixed_learned_iters": itml,
             "speedup_vs_fp64": t64 / tml, "rel_error_vs_fp64_solution": err, "final_relres_fp64": rrml,
-            "fallback_rule": {"learned_kept": bool(used), "iters_mixed_plain": ip, "iters_mixed_learned": il},
+            "best_constant": {"omega": best, "time_to_solution_s": tc / 1e3, "iters": itc,
+                              "speedup_vs_fp64": t64 / tc},
+            "network_vs_best_constant": tc / tml, "omega": stats,
+            "constant_sweep_iters": {str(kk): v for kk, v in sweep.items()},
+            "fallback_rule": {"reference": f"constant omega {best}", "learned_kept": bool(used),
+                              "iters_reference": ip, "iters_learned": il},
             "training": {"set": "annulus hierarchies p in {2,3,4}, n in {16,32}, 4 coefficient seeds each (FP64)",
                          "steps": args.train_steps,
                          "probes": 4, "lr": 1e-2, "seconds": train_s,
@@ -584,6 +715,9 @@ def run_ours(args):
         elapsed_ms = max_over_ranks(dist, e0.elapsed_time(e1))
         ms_per_step = elapsed_ms / args.steps
         it, rr, info = infos[-1]
+
+        # the FP64 rate that bounds the FP64 passes, measured on this GPU
+        fp64_meas, fp64_clk = measure_fp64_rate(A, torch, stream, uuid)
 
         # V-cycle alone (standalone applications, events on the same stream)
         h = A.amg_setup(rp, ci, va, opts, stream)
@@ -725,11 +859,14 @@ def run_ours(args):
     tkey = ["spmv_pq", "resid", "up0"][dom]
     # The FP64 finest pass issues one DFMA per stored entry; on GB300 that is the binding limit (the FP64
     # pipe is far busier than DRAM), so its roofline is the FP64 rate derived from unit counts and clock.
-    fpk = fp64_peak_tflops()
+    fpk = fp64_meas
     flops_tf = 2.0 * prob.nnz / (avg_ms[dom] * 1e-3) / 1e12 if avg_ms[dom] > 0 else 0.0
     roof = {"bound": "alu", "kernel": KERNEL_NAMES[dom], "achieved": flops_tf, "peak": fpk, "unit": "TFLOP/s",
             "frac": flops_tf / fpk, "traffic": (traffic or {}).get(tkey),
-            "peak_kind": "derived: SMs x max SM clock x 2 FP64 FMA/clk x 2 flop (nominal 1.25 TFLOP/s)",
+            "peak_kind": "measured on this GPU: amg_dfma_probe (8 independent FP64 FMA chains per thread, "
+                         "8 x 256 threads per SM, ~2 s, CUDA events)",
+            "peak_clocks": fp64_clk, "peak_derived": fp64_peak_tflops(),
+            "frac_of_derived": flops_tf / fp64_peak_tflops(),
             "flops_per_launch": 2.0 * prob.nnz, "bytes_per_launch": kbytes[dom], "avg_launch_ms": avg_ms[dom],
             "hbm": {"achieved_gbs": per_kernel[KERNEL_NAMES[dom]]["achieved_gbs"], "peak_gbs": peak,
                     "frac": (per_kernel[KERNEL_NAMES[dom]]["achieved_gbs"] or 0.0) / peak,

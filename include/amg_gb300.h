@@ -239,6 +239,17 @@ int amg_profile_kernels(amg_hierarchy* h, int32_t enable);
  * written once).  Any pointer may be NULL. */
 int amg_kernel_times(const amg_hierarchy* h, double* ms, int64_t* count, double* bytes);
 
+/* FP64 FMA throughput probe (measurement support; no paper counterpart):
+ * enqueues on cuda_stream (NULL = default stream) one kernel of `blocks`
+ * blocks x 256 threads, each thread running 8 independent FMA chains for
+ * trips x 16 steps, and returns at once (time it with events on the same
+ * stream).  out_dev: DEVICE array of blocks x 256 doubles that receives the
+ * chains' sums (keeps the work observable).  *flops (host, may be NULL):
+ * the kernel's floating-point operations, 2 per FMA.  Used to measure the
+ * FP64 rate that bounds the FP64 matrix passes.  Errors: AMG_ERR_ARG
+ * (blocks < 1, trips < 1, out_dev NULL), AMG_ERR_CUDA. */
+int amg_dfma_probe(int32_t blocks, int64_t trips, double* out_dev, void* cuda_stream, double* flops);
+
 /* Largest system amg_relres_noalloc accepts (rows). */
 #define AMG_NOALLOC_MAX_ROWS (1 << 19)
 
@@ -253,10 +264,14 @@ int amg_kernel_times(const amg_hierarchy* h, double* ms, int64_t* count, double*
  * synchronisation it may cause) is not acceptable.  It allocates nothing:
  * its reduction scratch is a fixed static device array of about 1 MB that
  * every GPU which loads the library keeps until the process exits.
- * The first call on a device looks up that array's device address (with the
- * device current) and caches it; make that first call before any stream
- * capture.  All calls share the array, so calls that overlap on the GPU
- * (e.g. on different streams) race; serialise them.
+ * The work runs on the device that owns cuda_stream (the current device
+ * for NULL); the call makes that device current while it works and restores
+ * the caller's current device.  The first call on a device looks up that
+ * array's device address (with the device current) and caches it; make that
+ * first call before any stream capture.  All calls share the array, so calls
+ * that overlap on the GPU (e.g. on different streams) race; serialise them.
+ * Launch failures are taken from this call's own launches: an unrelated
+ * error the caller left pending is neither reported nor cleared.
  * Errors: AMG_ERR_ARG for NULL pointers, host-resident K, n < 1 or
  * n > AMG_NOALLOC_MAX_ROWS; AMG_ERR_CUDA on a CUDA failure. */
 int amg_relres_noalloc(const amg_csr* K, const double* F, const double* u, double* relres, void* cuda_stream);
@@ -264,14 +279,18 @@ int amg_relres_noalloc(const amg_csr* K, const double* F, const double* u, doubl
 /* ------------------------------------------------------------------------
  * Learned per-row smoother damping.  The paper has no learned component;
  * this extends its l1-Jacobi smoother (Sec. 3.2, x <- x + D^-1 (f - K x))
- * to x <- x + diag(omega_i / d_i) (f - K x) with omega_i in (0, 2), which
- * keeps the smoother convergent in the K-norm (D_l1 - K is positive
- * semidefinite).  omega comes from a two-layer message-passing network
- * (hidden width AMG_MPNN_HIDDEN) evaluated on every level's matrix graph:
+ * to x <- x + diag(omega_i / d_i) (f - K x) with 0 < omega_i < omega_max.
+ * The smoother is a K-norm contraction (and the V-cycle SPD) while
+ * 2 diag(d / omega) - K is positive definite, i.e. for every omega_i below
+ * 2 / lambda_max(D^-1 K); the l1 diagonal gives lambda_max <= 1, so (0, 2)
+ * is always admissible.  Per level, omega_max = 2 / lam_hat with lam_hat =
+ * min(1, the Lanczos upper estimate of amg_smoother_bound).  omega comes
+ * from a two-layer message-passing network (hidden width AMG_MPNN_HIDDEN)
+ * evaluated on every level's matrix graph:
  *   x_i  = [sum_{j!=i}|k_ij|/k_ii, sum_{j!=i} k_ij/k_ii, log2(nnz_i)/8, 1]
  *   a_ij = k_ij / sqrt(k_ii k_jj) (j != i)
  *   h0 = relu(W0 x + b0); h_l = relu(U_l (A' h_{l-1}) + V_l h_{l-1} + b_l),
- *   l = 1, 2; omega = 2 sigmoid(q . h2 + c).
+ *   l = 1, 2; omega = omega_max sigmoid(q . h2 + c).
  * Weights: AMG_MPNN_NPARAM floats, row-major blocks in the order
  * W0[32][4], b0[32], U1[32][32], V1[32][32], b1[32], U2, V2, b2, q[32], c[1].
  * All weight, gradient and moment pointers are DEVICE pointers owned by the
@@ -326,14 +345,37 @@ int amg_mpnn_adam(amg_hierarchy* h, float* w, const double* grad, float* m, floa
 int amg_mpnn_train(amg_hierarchy* const* hs, int32_t count, float* w, int32_t steps, int32_t nprobe, uint64_t seed,
                    float lr, double* loss_hist);
 
-/* Fallback rule: solve K u = F (F device, u0 = 0) with the plain smoother
- * and with the network's damping (BF16 weights); keep the learned damping
- * installed only if it converged in no more iterations than the plain one,
- * else restore the plain smoother.  *used = 1 if the learned damping stays;
- * the two iteration counts are returned.  Not for batch hierarchies
- * (AMG_ERR_ARG). */
-int amg_mpnn_select(amg_hierarchy* h, const float* w, const double* F, double rtol, int32_t itmax, int32_t* used,
-                    int32_t* iters_plain, int32_t* iters_learned);
+/* Fallback rule: solve K u = F (F device, u0 = 0) with the reference
+ * damping -- the constant omega_ref on every smoothed level (omega_ref = 1:
+ * the plain l1-Jacobi smoother) -- and with the network's damping (BF16
+ * weights); keep the learned damping installed only if it converged in no
+ * more iterations than the reference, else install the reference damping
+ * (also on every error return after the reference solve).  *used = 1 if the
+ * learned damping stays; the two iteration counts are returned.  Not for
+ * batch hierarchies.  Errors: AMG_ERR_ARG (NULL pointers, omega_ref <= 0,
+ * rtol <= 0, itmax < 1, a batch hierarchy), AMG_ERR_NOMEM, AMG_ERR_CUDA. */
+int amg_mpnn_select(amg_hierarchy* h, const float* w, double omega_ref, const double* F, double rtol, int32_t itmax,
+                    int32_t* used, int32_t* iters_ref, int32_t* iters_learned);
+
+/* Install the constant damping x <- x + (omega / d_i) (f - K x) on every
+ * level that has a smoother (FP64 and, in the mixed-precision modes, FP32
+ * diagonals); omega = 1 restores the plain l1-Jacobi smoother of Sec. 3.2
+ * bit for bit.  omega must be positive; the smoother converges for omega <
+ * 2 / lambda_max(D^-1 K) (at least 2, see amg_smoother_bound).  The paper
+ * has no damping parameter; this is the constant baseline of the learned
+ * damping.  Errors: AMG_ERR_ARG (h NULL, omega not > 0 or not finite),
+ * AMG_ERR_CUDA. */
+int amg_set_damping(amg_hierarchy* h, double omega);
+
+/* lam_hat of `level` on the host: min(1, theta + beta_k |s_k|), theta the
+ * largest Ritz value of 15 Lanczos steps (fewer on levels with fewer rows)
+ * on D^-1/2 K D^-1/2 (spectrum of D^-1 K, D the l1 diagonal of Sec. 3.2)
+ * from a SplitMix64(0x4C414E43 + level) start vector, beta_k |s_k| its
+ * residual bound.  An upper estimate of lambda_max(D^-1 K) that caps the
+ * learned damping at omega_max = 2 / lam_hat.  Computed once per level and
+ * kept with the hierarchy.  Errors: AMG_ERR_ARG (h or lambda_hat NULL, level
+ * out of range), AMG_ERR_NOMEM, AMG_ERR_CUDA. */
+int amg_smoother_bound(amg_hierarchy* h, int32_t level, double* lambda_hat);
 
 /* Release the hierarchy and its device memory. */
 int amg_free(amg_hierarchy* h);

@@ -29,10 +29,14 @@ ERRORS = {0: "ok", -1: "bad argument", -2: "not SPD", -3: "breakdown", -4: "not 
 
 
 def build(force: bool = False) -> str:
+    """Compile the oracle (with OpenMP for the solve phase's row loops when
+    the compiler supports it, sequential otherwise)."""
     if force or not os.path.exists(LIB) or os.path.getmtime(SRC) > os.path.getmtime(LIB):
         tmp = LIB + ".tmp"
-        r = subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, SRC, "-lm"],
-                           capture_output=True, text=True)
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+        if r.returncode != 0:
+            r = subprocess.run(base, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("oracle build failed:\n" + r.stderr)
         os.replace(tmp, LIB)
@@ -54,6 +58,7 @@ def lib():
     if _lib is None:
         L = ctypes.CDLL(build())
         P, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        L.orc_set_threads.argtypes = [i32]
         L.orc_opts_default.argtypes = [P]
         L.orc_setup.argtypes = [i64, P, P, P, P, P]
         L.orc_setup.restype = P
@@ -213,6 +218,18 @@ def spmv(rowptr, col, val, x):
     y = np.empty(len(rp) - 1)
     lib().orc_spmv(len(y), _p(rp), _p(ci), _p(v), _p(x), _p(y))
     return y
+
+
+def set_threads(t: int) -> int:
+    """Threads of the solve phase's row loops (results do not depend on it);
+    returns the count in effect (1 without OpenMP)."""
+    L = lib()
+    L.orc_set_threads(int(t) if L.orc_have_openmp() else 1)
+    return L.orc_get_threads()
+
+
+def have_openmp() -> bool:
+    return bool(lib().orc_have_openmp())
 
 
 # ------------------------------------------------------------- hierarchy ----

@@ -52,12 +52,38 @@
  *     The coarsest matrix is factorised by dense Cholesky.
  *   - V-cycle with nu1 pre- and nu2 post-sweeps of l1-Jacobi from x = 0.
  *   - PCG stops when ||r_k||_2 <= rtol ||F||_2 on the recursive residual.
+ *
+ * Threads: the solve phase (V-cycle and CG) may run its row loops -- each
+ * row's sum evaluated exactly as in the sequential code -- on several
+ * OpenMP threads (orc_set_threads); restrictions, which add into shared
+ * coarse entries, and every dot product stay sequential, so the results do
+ * not depend on the thread count.  The setup is always sequential (the
+ * greedy matching is defined by its sequential scan).
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* threads of the solve phase's row loops (1 = sequential) */
+static int g_threads = 1;
+
+void orc_set_threads(int t) { g_threads = t < 1 ? 1 : t; }
+
+int orc_get_threads(void) { return g_threads; }
+
+/* 1 if this build runs the row loops on OpenMP threads */
+int orc_have_openmp(void) {
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 #define ORC_MAX_LEVELS 32
 #define ORC_MAX_PASSES 4
@@ -136,7 +162,15 @@ static double row_dot(const int64_t* rp, const int32_t* ci, const double* v, int
 }
 
 void orc_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* x, double* y) {
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
     for (int64_t i = 0; i < n; i++) y[i] = row_dot(rp, ci, v, i, x);
+}
+
+/* r = f - K x, row by row */
+static void residual(const int64_t* rp, const int32_t* ci, const double* v, int64_t n, const double* f,
+                     const double* x, double* r) {
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
+    for (int64_t i = 0; i < n; i++) r[i] = f[i] - row_dot(rp, ci, v, i, x);
 }
 
 static double dot(int64_t n, const double* a, const double* b) {
@@ -556,10 +590,10 @@ static void vcycle(const orc_hier* h, int l, const double* f, double* x) {
     double* r = (double*)malloc(sizeof(double) * n);
     for (int64_t i = 0; i < n; i++) x[i] = 0.0;
     for (int s = 0; s < h->o.nu_pre; s++) {
-        for (int64_t i = 0; i < n; i++) r[i] = f[i] - row_dot(L->rowptr, L->col, L->val, i, x);
+        residual(L->rowptr, L->col, L->val, n, f, x, r);
         for (int64_t i = 0; i < n; i++) x[i] = x[i] + r[i] / L->dl1[i];
     }
-    for (int64_t i = 0; i < n; i++) r[i] = f[i] - row_dot(L->rowptr, L->col, L->val, i, x);
+    residual(L->rowptr, L->col, L->val, n, f, x, r);
     const int64_t nc = h->lev[l + 1].n;
     double* fc = (double*)malloc(sizeof(double) * nc);
     double* ec = (double*)malloc(sizeof(double) * nc);
@@ -567,7 +601,7 @@ static void vcycle(const orc_hier* h, int l, const double* f, double* x) {
     vcycle(h, l + 1, fc, ec);
     for (int64_t i = 0; i < n; i++) x[i] = x[i] + L->pval[i] * ec[L->agg[i]];
     for (int s = 0; s < h->o.nu_post; s++) {
-        for (int64_t i = 0; i < n; i++) r[i] = f[i] - row_dot(L->rowptr, L->col, L->val, i, x);
+        residual(L->rowptr, L->col, L->val, n, f, x, r);
         for (int64_t i = 0; i < n; i++) x[i] = x[i] + r[i] / L->dl1[i];
     }
     free(r);
@@ -593,7 +627,7 @@ int orc_pcg(const orc_hier* h, const double* Fv, double* u, double rtol, int itm
     double* q = (double*)malloc(sizeof(double) * n);
     int rc = ORC_OK, it = 0;
     const double nF = sqrt(dot(n, Fv, Fv));
-    for (int64_t i = 0; i < n; i++) r[i] = Fv[i] - row_dot(L->rowptr, L->col, L->val, i, u);
+    residual(L->rowptr, L->col, L->val, n, Fv, u, r);
     double nr = sqrt(dot(n, r, r));
     if (history) history[0] = nF > 0.0 ? nr / nF : 0.0;
     if (!(nF > 0.0)) {
@@ -630,7 +664,7 @@ int orc_pcg(const orc_hier* h, const double* Fv, double* u, double rtol, int itm
         }
         if (rc == ORC_OK && nr > rtol * nF) rc = ORC_ERR_NOT_CONVERGED;
     }
-    for (int64_t i = 0; i < n; i++) r[i] = Fv[i] - row_dot(L->rowptr, L->col, L->val, i, u);
+    residual(L->rowptr, L->col, L->val, n, Fv, u, r);
     *relres = nF > 0.0 ? sqrt(dot(n, r, r)) / nF : 0.0;
     *iters = it;
     free(r); free(z); free(p); free(q);

@@ -2,11 +2,15 @@
 
 The paper's l1-Jacobi smoother (Sec. 3.2) uses x <- x + D^-1 (f - K x)
 with the l1 diagonal D.  The learned variant scales it per row,
-x <- x + diag(omega_i / d_i) (f - K x), omega_i in (0, 2): since
-D - K is positive semidefinite, every such omega keeps the smoother
-convergent in the K-norm.  omega is produced by a small message-passing
-network over the matrix graph and trained to minimise the error
-reduction of the V-cycle (Sec. 3, two-level correction applied
+x <- x + diag(omega_i / d_i) (f - K x), 0 < omega_i < omega_max.  The
+smoother converges in the K-norm when 2 diag(d / omega) - K is positive
+definite, which holds for every omega_i < 2 / lambda_max(D^-1 K); the l1
+diagonal gives lambda_max <= 1, so (0, 2) is always admissible, and the IgA
+levels have lambda_max of 0.7-0.9, so the admissible range reaches 2.2-2.8.
+omega_max = 2 / lam_hat per level, lam_hat = min(1, Lanczos upper estimate
+of lambda_max(D^-1 K)) (lanczos_bound below).  omega is produced by a small
+message-passing network over the matrix graph and trained to minimise the
+error reduction of the V-cycle (Sec. 3, two-level correction applied
 recursively) used as CG preconditioner.  The paper has no learned
 component; this file is the plain FP64 statement of what the GPU kernels
 compute, written out step by step.
@@ -19,8 +23,8 @@ Network (hidden width 32, two message-passing layers):
   h0  = relu(W0 x + b0)
   m_l = sum_j a_ij h_{l-1, j}
   h_l = relu(U_l m_l + V_l h_{l-1} + b_l),      l = 1, 2
-  omega = 2 sigmoid(q . h2 + c)
-applied to every level's matrix with the same weights.
+  omega = omega_max sigmoid(q . h2 + c)
+applied to every level's matrix with the same weights (omega_max per level).
 
 Loss for probe vectors x_k (SplitMix64 uniform in (-1, 1)):
   L = (1/m) sum_k log( y_k^T K y_k / x_k^T K x_k ),  y_k = x_k - B_omega K x_k
@@ -33,6 +37,9 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg as sl
 import scipy.sparse as sp
+
+LANCZOS_STEPS = 15
+LANCZOS_SEED = 0x4C414E43  # start vector of level l: SplitMix64(LANCZOS_SEED + l)
 
 HIDDEN = 32
 NFEAT = 4
@@ -85,7 +92,43 @@ def features(rowptr, col, val):
 
 
 # ----------------------------------------------------------------- network
-def forward(w, x, Ap):
+def lanczos_bound(K, d, steps=LANCZOS_STEPS, seed=LANCZOS_SEED):
+    """Upper estimate lam_hat of lambda_max(D^-1 K) for SPD K and positive d.
+
+    Lanczos (no reorthogonalisation) on the symmetric S = D^-1/2 K D^-1/2,
+    which has the spectrum of D^-1 K, from q_1 = x / ||x||, x_i = 2 U_i - 1
+    with U_i draw i of SplitMix64(seed) on 53 bits:
+        w = S q_j - beta_{j-1} q_{j-1}; alpha_j = q_j . w;
+        w = w - alpha_j q_j; beta_j = ||w||; q_{j+1} = w / beta_j.
+    The largest eigenvalue theta of the tridiagonal T = tridiag(beta,
+    alpha, beta) is a Ritz value of S, and some eigenvalue of S lies within
+    beta_k |s_k| of it (s the unit eigenvector of T for theta, k the last
+    step); theta + beta_k |s_k| is returned, capped at 1 (the l1 diagonal
+    bounds lambda_max by 1).  A zero beta_j ends the recurrence: the Krylov
+    space is invariant and theta is exact."""
+    n = K.shape[0]
+    isd = 1.0 / np.sqrt(d)
+    x = probes(seed, 1, n)[0]
+    q = x / np.sqrt(x @ x)
+    qp = np.zeros(n)
+    bprev = 0.0
+    alpha, beta = [], []
+    for _ in range(min(steps, n)):
+        w = isd * (K @ (isd * q)) - bprev * qp
+        a = q @ w
+        w = w - a * q
+        b = np.sqrt(w @ w)
+        alpha.append(a)
+        beta.append(b)
+        if b == 0.0:
+            break
+        qp, q, bprev = q, w / b, b
+    ev, S = sl.eigh_tridiagonal(np.array(alpha), np.array(beta[:-1]))
+    bound = ev[-1] + beta[-1] * abs(S[-1, -1])
+    return min(1.0, bound)
+
+
+def forward(w, x, Ap, omax=2.0):
     p = unpack(w)
     u0 = x @ p["W0"].T + p["b0"]
     h0 = np.maximum(u0, 0.0)
@@ -97,13 +140,13 @@ def forward(w, x, Ap):
     h2 = np.maximum(u2, 0.0)
     z = h2 @ p["q"] + p["c"][0]
     sg = 1.0 / (1.0 + np.exp(-z))
-    return 2.0 * sg, dict(x=x, u0=u0, h0=h0, m1=m1, u1=u1, h1=h1, m2=m2, u2=u2, h2=h2, z=z, sg=sg)
+    return omax * sg, dict(x=x, u0=u0, h0=h0, m1=m1, u1=u1, h1=h1, m2=m2, u2=u2, h2=h2, z=z, sg=sg)
 
 
-def backward(w, tape, Ap, domega):
+def backward(w, tape, Ap, domega, omax=2.0):
     """Gradient of the loss w.r.t. the flat weights given d loss / d omega."""
     p = unpack(w)
-    dz = domega * 2.0 * tape["sg"] * (1.0 - tape["sg"])
+    dz = domega * omax * tape["sg"] * (1.0 - tape["sg"])
     g = {"q": tape["h2"].T @ dz, "c": np.array([dz.sum()])}
     dh2 = np.outer(dz, p["q"])
     du2 = dh2 * (tape["u2"] > 0)
@@ -139,6 +182,8 @@ class Levels:
                 self.P.append(sp.csr_matrix((pv, (np.arange(n), agg)), shape=(n, H.level_n(l + 1))))
         self.chol = H.coarse_chol()
         self.csr = [(H.level_csr(l)) for l in range(self.L)]
+        # damping cap of every smoothed level: omega_max = 2 / lam_hat
+        self.omax = [2.0 / lanczos_bound(self.K[l], self.d[l], seed=LANCZOS_SEED + l) for l in range(self.L - 1)]
 
     def coarse_solve(self, f):
         y = sl.solve_triangular(self.chol, f, lower=True)
@@ -219,15 +264,17 @@ def loss_and_domega(lv: Levels, omegas, X):
 
 
 def loss_and_grad(H, w, nprobe=4, seed=99):
-    """Loss of the network's damping on hierarchy H and its gradient with
-    respect to the flat weights (network applied to every level)."""
-    lv = Levels(H)
-    feats = [features(*lv.csr[l]) for l in range(lv.L)]
-    outs = [forward(w, x, Ap) for x, Ap in feats]
-    omegas = [o[0] for o in outs]
+    """Loss of the network's damping on hierarchy H (an oracle Hierarchy or
+    its Levels) and its gradient with respect to the flat weights (network
+    applied to every smoothed level, omega_max of each level)."""
+    lv = H if isinstance(H, Levels) else Levels(H)
+    feats = [features(*lv.csr[l]) for l in range(lv.L - 1)]
+    outs = [forward(w, x, Ap, lv.omax[l]) for l, (x, Ap) in enumerate(feats)]
+    # the coarsest level is solved exactly: it has no smoother
+    omegas = [o[0] for o in outs] + [np.ones(lv.K[lv.L - 1].shape[0])]
     X = probes(seed, nprobe, lv.K[0].shape[0])
     loss, domegas = loss_and_domega(lv, omegas, X)
     grad = np.zeros(NPARAM)
-    for l in range(lv.L):
-        grad += backward(w, outs[l][1], feats[l][1], domegas[l])
+    for l in range(lv.L - 1):
+        grad += backward(w, outs[l][1], feats[l][1], domegas[l], lv.omax[l])
     return loss, grad, omegas

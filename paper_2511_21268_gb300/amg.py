@@ -102,8 +102,13 @@ _SIGS = {
     "amg_mpnn_adam": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int32] + [ctypes.c_float] * 4),
     "amg_mpnn_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_uint64, ctypes.c_float, ctypes.c_void_p]),
-    "amg_mpnn_select": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
-                                       ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_mpnn_select": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                       ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "amg_set_damping": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "amg_dfma_probe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    "amg_smoother_bound": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "amg_staged_wait_selftest": (ctypes.c_int, [ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "amg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "amg_last_cuda_error": (ctypes.c_char_p, []),
@@ -419,13 +424,34 @@ def amg_mpnn_train(hs, w, steps: int, nprobe: int, seed: int, lr: float):
     return hist[:steps]
 
 
-def amg_mpnn_select(h, w, F, rtol: float, itmax: int):
-    """(used, iters_plain, iters_learned) of the fallback rule."""
+def amg_mpnn_select(h, w, F, rtol: float, itmax: int, omega_ref: float = 1.0):
+    """(used, iters_ref, iters_learned) of the fallback rule against the
+    constant damping omega_ref (1: the plain smoother)."""
     wd = _dev_weights(w)
     used, ip, il = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-    _check(lib().amg_mpnn_select(h, wd.data_ptr(), F.data_ptr(), rtol, itmax, ctypes.byref(used), ctypes.byref(ip),
-                                 ctypes.byref(il)), "amg_mpnn_select")
+    _check(lib().amg_mpnn_select(h, wd.data_ptr(), float(omega_ref), F.data_ptr(), rtol, itmax, ctypes.byref(used),
+                                 ctypes.byref(ip), ctypes.byref(il)), "amg_mpnn_select")
     return bool(used.value), ip.value, il.value
+
+
+def amg_dfma_probe(blocks: int, trips: int, out, stream=None) -> float:
+    """Enqueue the FP64 FMA throughput kernel; returns its flop count."""
+    fl = ctypes.c_double()
+    _check(lib().amg_dfma_probe(int(blocks), int(trips), out.data_ptr(), _stream_handle(stream), ctypes.byref(fl)),
+           "amg_dfma_probe")
+    return fl.value
+
+
+def amg_set_damping(h, omega: float):
+    """Install the constant damping omega / d on every smoothed level."""
+    _check(lib().amg_set_damping(h, float(omega)), "amg_set_damping")
+
+
+def amg_smoother_bound(h, level: int) -> float:
+    """lam_hat, the Lanczos upper estimate of lambda_max(D^-1 K) on `level`."""
+    out = ctypes.c_double()
+    _check(lib().amg_smoother_bound(h, level, ctypes.byref(out)), "amg_smoother_bound")
+    return out.value
 
 
 class Hierarchy:
@@ -513,8 +539,14 @@ class Hierarchy:
         """Train w on this hierarchy (and the hierarchies in `others`)."""
         return amg_mpnn_train([self._h] + [o._h for o in others], w, steps, nprobe, seed, lr)
 
-    def mpnn_select(self, w, F, rtol: float = 1e-8, itmax: int = 10000):
-        return amg_mpnn_select(self._h, w, F, rtol, itmax)
+    def mpnn_select(self, w, F, rtol: float = 1e-8, itmax: int = 10000, omega_ref: float = 1.0):
+        return amg_mpnn_select(self._h, w, F, rtol, itmax, omega_ref)
+
+    def set_damping(self, omega: float):
+        amg_set_damping(self._h, omega)
+
+    def smoother_bound(self, level: int) -> float:
+        return amg_smoother_bound(self._h, level)
 
 
 class BatchHierarchy(Hierarchy):

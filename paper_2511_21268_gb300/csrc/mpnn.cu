@@ -1,19 +1,25 @@
 // Learned per-row smoother damping (the paper has no learned component).
 //
 // The l1-Jacobi smoother of Sec. 3.2 is scaled per row,
-//   x <- x + diag(omega_i / d_i) (f - K x),   omega_i in (0, 2),
-// which stays convergent in the K-norm for every such omega because D_l1 - K
-// is positive semidefinite.  omega comes from a two-layer message-passing
-// network over each level's matrix graph (the same weights on every level);
-// applying it only rescales each level's 1/d_i, so the FP64 and
-// mixed-precision V-cycle kernels run the learned smoother unchanged.
+//   x <- x + diag(omega_i / d_i) (f - K x),   0 < omega_i < omega_max,
+// which stays convergent in the K-norm while 2 diag(d / omega) - K is
+// positive definite, i.e. for every omega_i < 2 / lambda_max(D^-1 K).  The l1
+// diagonal bounds lambda_max by 1; IgA levels have 0.7-0.9, where the
+// best damping lies above 2.  So each level gets omega_max = 2 / lam_hat with
+// lam_hat = min(1, a Lanczos upper estimate of lambda_max(D^-1 K)) (15 steps
+// from a SplitMix64 start; the largest Ritz value plus its residual bound).
+// omega comes from a two-layer message-passing network over each level's
+// matrix graph (the same weights on every level); applying it only rescales
+// each level's 1/d_i, so the FP64 and mixed-precision V-cycle kernels run
+// the learned smoother unchanged.
 //
 // Network (hidden width 32):
 //   node features  x_i = [rho_i, sig_i, log2(nnz_i) / 8, 1],
 //                  rho_i = sum_{j!=i} |k_ij| / k_ii, sig_i = sum_{j!=i} k_ij / k_ii
 //   edge weights   a_ij = k_ij / sqrt(k_ii k_jj)  (j != i; a_ii = 0)
 //   h0 = relu(W0 x + b0); m_l = sum_j a_ij h_{l-1,j};
-//   h_l = relu(U_l m_l + V_l h_{l-1} + b_l) (l = 1, 2); omega = 2 sigmoid(q.h2 + c)
+//   h_l = relu(U_l m_l + V_l h_{l-1} + b_l) (l = 1, 2);
+//   omega = omega_max sigmoid(q.h2 + c)
 // Training loss over probe vectors x_k (SplitMix64 uniform in (-1, 1)):
 //   L = (1/m) sum_k log(y_k^T K y_k / x_k^T K x_k),  y_k = x_k - B_omega K x_k,
 // B_omega the V-cycle (one pre- and one post-sweep, exact coarsest solve).
@@ -53,6 +59,9 @@ constexpr int O_W0 = 0, O_B0 = O_W0 + H * 4, O_U1 = O_B0 + H, O_V1 = O_U1 + H * 
 static_assert(O_END == AMG_MPNN_NPARAM, "parameter layout");
 constexpr int kGradBlocks = 256;           // blocks of the weight-gradient kernels
 constexpr int kGradSlots = 2 * H * H + H;  // partial sums one block writes (largest kernel)
+constexpr int kLzMax = 16;                 // Lanczos steps of the damping cap (at most)
+constexpr int kLzSteps = 15;               // Lanczos steps taken (fewer on levels with fewer rows)
+constexpr uint64_t kLzSeed = 0x4C414E43ULL;  // start vector of level l: SplitMix64(kLzSeed + l)
 
 __device__ __forceinline__ float round_bf16(float w) { return __bfloat162float(__float2bfloat16_rn(w)); }
 
@@ -211,9 +220,11 @@ __global__ void __launch_bounds__(kBlock) k_nn_spmm(int n, const int64_t* __rest
 __global__ void __launch_bounds__(kBlock) k_nn_dense(int n, const float* __restrict__ w, int bf16, int layer,
                                                       const float* __restrict__ m, const float* __restrict__ hp,
                                                       float* __restrict__ u, float* __restrict__ h,
-                                                      float* __restrict__ sg, float* __restrict__ omega) {
+                                                      float* __restrict__ sg, float* __restrict__ omega,
+                                                      const double* __restrict__ cap) {
     __shared__ NetSmem s;
     load_net(w, s, layer, bf16);
+    const float omax = layer == 2 ? (float)cap[1] : 0.f;
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
@@ -233,7 +244,7 @@ __global__ void __launch_bounds__(kBlock) k_nn_dense(int n, const float* __restr
             if (lane == 0) {
                 const float sgm = 1.f / (1.f + expf(-(t + s.c)));
                 sg[i] = sgm;
-                omega[i] = 2.f * sgm;
+                omega[i] = omax * sgm;
             }
         }
     }
@@ -254,21 +265,22 @@ __device__ __forceinline__ void block_lane_sum(float (&red)[kWarpsPerBlock][H], 
     __syncthreads();
 }
 
-// dz = domega 2 sg (1 - sg); partials dq[j] = sum dz h2[j] (slots [0, H)),
-// dc = sum dz (slot H); du2 = dz q [u2 > 0]
+// dz = domega omega_max sg (1 - sg); partials dq[j] = sum dz h2[j] (slots
+// [0, H)), dc = sum dz (slot H); du2 = dz q [u2 > 0]
 __global__ void __launch_bounds__(kBlock) k_nn_out_bwd(int n, const float* __restrict__ w,
                                                         const double* __restrict__ domega,
                                                         const float* __restrict__ sg, const float* __restrict__ h2,
                                                         const float* __restrict__ u2, float* __restrict__ du2,
-                                                        float* __restrict__ part) {
+                                                        float* __restrict__ part, const double* __restrict__ cap) {
     __shared__ float red[kWarpsPerBlock][H];
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const float q = w[O_Q + lane];
+    const float omax = (float)cap[1];
     float aq = 0.f, ac = 0.f;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
         const float s = sg[i];
-        const float dz = (float)domega[i] * 2.f * s * (1.f - s);
+        const float dz = (float)domega[i] * omax * s * (1.f - s);
         aq = fmaf(dz, h2[(int64_t)i * H + lane], aq);
         ac += dz;
         du2[(int64_t)i * H + lane] = u2[(int64_t)i * H + lane] > 0.f ? dz * q : 0.f;
@@ -509,15 +521,140 @@ __global__ void k_adam(int n, float* __restrict__ w, const double* __restrict__ 
     w[i] -= lr * mh / (sqrtf(vh) + eps);
 }
 
-// smoother diagonal: invd = omega / dl1 (omega NULL: the plain 1 / dl1,
-// rounded as in setup) and its FP32 copy
-__global__ void k_set_damping(int n, const float* __restrict__ om, const double* __restrict__ dl1,
+// smoother diagonal: invd = omega / dl1 (omega NULL: the constant omc / dl1,
+// which for omc = 1 is the plain 1 / dl1 rounded as in setup) and its FP32
+// copy
+__global__ void k_set_damping(int n, const float* __restrict__ om, double omc, const double* __restrict__ dl1,
                               double* __restrict__ invd, float* __restrict__ invd32) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double v = om ? (double)om[i] / dl1[i] : __ddiv_rn(1.0, dl1[i]);
+    const double v = om ? (double)om[i] / dl1[i] : __ddiv_rn(omc, dl1[i]);
     invd[i] = v;
     if (invd32) invd32[i] = __double2float_rn(v);
+}
+
+// ------------------------------------------- damping cap (Lanczos estimate)
+// isd = 1 / sqrt(d)
+__global__ void k_lz_isd(int n, const double* __restrict__ d, double* __restrict__ isd) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) isd[i] = 1.0 / sqrt(d[i]);
+}
+
+// w = S q - beta_prev qp, S = D^-1/2 K D^-1/2 (a warp per row); beta_prev
+// is ab[kLzMax + j - 1] (none for j = 0)
+__global__ void __launch_bounds__(kBlock) k_lz_apply(int n, const int64_t* __restrict__ rp,
+                                                      const int32_t* __restrict__ ci, const double* __restrict__ v,
+                                                      const double* __restrict__ isd, const double* __restrict__ q,
+                                                      const double* __restrict__ qp, const double* __restrict__ bprev,
+                                                      double* __restrict__ w) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const double b = bprev ? *bprev : 0.0;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        double acc = 0.0;
+        for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
+            const int j = ci[k];
+            acc = fma(v[k], isd[j] * q[j], acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) w[i] = isd[i] * acc - b * qp[i];
+    }
+}
+
+// *out = a . b (one block, fixed order)
+__global__ void __launch_bounds__(1024) k_lz_dot(int n, const double* __restrict__ a, const double* __restrict__ b,
+                                                 double* __restrict__ out) {
+    __shared__ double sh[32];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) t = fma(a[i], b[i], t);
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) u += sh[k];
+        *out = u;
+    }
+}
+
+// w -= alpha q
+__global__ void k_lz_orth(int n, const double* __restrict__ alpha, const double* __restrict__ q,
+                          double* __restrict__ w) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w[i] -= *alpha * q[i];
+}
+
+// beta = sqrt(*nrm2) (written by block 0, thread 0 to *beta); qp = q;
+// q = w / beta (zero once beta = 0: the Krylov space is invariant)
+__global__ void k_lz_next(int n, const double* __restrict__ nrm2, double* __restrict__ beta, double* __restrict__ q,
+                          double* __restrict__ qp, const double* __restrict__ w) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double b = sqrt(*nrm2);
+    if (i == 0) *beta = b;
+    if (i < n) {
+        qp[i] = q[i];
+        q[i] = b > 0.0 ? w[i] / b : 0.0;
+    }
+}
+
+// q = x / ||x|| (x already holds the start vector; nrm2 = x . x)
+__global__ void k_lz_start(int n, const double* __restrict__ nrm2, double* __restrict__ q) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) q[i] = q[i] / sqrt(*nrm2);
+}
+
+// Largest eigenvalue theta of the symmetric tridiagonal T (diagonal
+// alpha[0..k), off-diagonal beta[0..k-1)), the steps used being those before
+// the first zero beta, by Sturm-sequence bisection; its eigenvector s from
+// the three-term recurrence (all components share a sign for the largest
+// eigenvalue: no cancellation); cap[0] = lam_hat = min(1, theta + beta_k
+// |s_k| / ||s||), cap[1] = 2 / lam_hat.  One thread.
+__global__ void k_lz_finish(int steps, const double* __restrict__ ab, double* __restrict__ cap) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double* al = ab;
+    const double* be = ab + kLzMax;
+    int k = 0;
+    while (k < steps) {
+        k++;
+        if (!(be[k - 1] > 0.0)) break;
+    }
+    // Gershgorin interval
+    double lo = al[0], hi = al[0];
+    for (int j = 0; j < k; j++) {
+        const double r = (j > 0 ? fabs(be[j - 1]) : 0.0) + (j + 1 < k ? fabs(be[j]) : 0.0);
+        lo = fmin(lo, al[j] - r);
+        hi = fmax(hi, al[j] + r);
+    }
+    // eigenvalues below x: sign changes of the LDL^T pivots of T - x I
+    auto below = [&](double x) {
+        int c = 0;
+        double dd = al[0] - x;
+        if (dd < 0.0) c++;
+        for (int j = 1; j < k; j++) {
+            if (dd == 0.0) dd = 1e-300;
+            dd = (al[j] - x) - be[j - 1] * be[j - 1] / dd;
+            if (dd < 0.0) c++;
+        }
+        return c;
+    };
+    for (int it = 0; it < 200; it++) {  // the largest eigenvalue lies in [lo, hi]
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (below(mid) == k) hi = mid;
+        else lo = mid;
+    }
+    const double th = hi;
+    double sp = 0.0, sc = 1.0, nrm = 1.0;
+    for (int j = 0; j + 1 < k; j++) {
+        const double sn = ((th - al[j]) * sc - (j > 0 ? be[j - 1] * sp : 0.0)) / be[j];
+        sp = sc;
+        sc = sn;
+        nrm += sc * sc;
+    }
+    const double resid = be[k - 1] > 0.0 ? be[k - 1] * fabs(sc) / sqrt(nrm) : 0.0;
+    const double lam = fmin(1.0, th + resid);
+    cap[0] = lam;
+    cap[1] = 2.0 / lam;
 }
 
 inline int eblk(int64_t n) { return (int)std::max<int64_t>(1, (n + kBlock - 1) / kBlock); }
@@ -536,8 +673,10 @@ struct MpnnLevel {
     float* omega = nullptr;
     double* domega = nullptr;
     double* v[kVec] = {};
+    double* ab = nullptr;   // Lanczos coefficients: alpha [0, kLzMax), beta [kLzMax, 2 kLzMax)
+    double* cap = nullptr;  // [0] lam_hat, [1] omega_max = 2 / lam_hat
     int alloc = 0;     // buffers allocated
-    int features = 0;  // features enqueued
+    int features = 0;  // features (and the damping cap) enqueued
 };
 
 struct MpnnWork {
@@ -563,6 +702,9 @@ struct MpnnWork {
 };
 
 namespace {
+
+// Vector slots of a level in the differentiated V-cycle.
+enum { V_F = 0, V_X1, V_R, V_X2, V_OUT, V_G, V_T };
 
 int grid_rows(const amg_hierarchy* h, int64_t n) {
     const int64_t cap = (int64_t)std::max(1, h->num_sms) * 8;
@@ -621,12 +763,42 @@ int alloc_level(amg_hierarchy* h, int l) {
     MP_ALLOC(m.omega, sizeof(float) * n);
     MP_ALLOC(m.domega, sizeof(double) * n);
     for (int t = 0; t < MpnnLevel::kVec; t++) MP_ALLOC(m.v[t], sizeof(double) * n);
+    MP_ALLOC(m.ab, sizeof(double) * 2 * kLzMax);
+    MP_ALLOC(m.cap, sizeof(double) * 2);
     m.alloc = 1;
     return AMG_OK;
 }
 
-// Node features and edge weights of level l (see the file header) on stream
-// s; the buffers must be allocated and ordered before s.
+// Damping cap of level l on stream s: Lanczos on D^-1/2 K D^-1/2 from the
+// SplitMix64(kLzSeed + l) start vector, min(kLzSteps, n) steps, then
+// lam_hat and omega_max into m.cap (see k_lz_finish).  Uses the level's
+// V-cycle vectors as workspace.
+void cap_level(amg_hierarchy* h, int l, cudaStream_t s) {
+    MpnnLevel& m = h->mp->lev[l];
+    const Level& L = h->lev[l];
+    const int n = L.A.n;
+    const int steps = std::min(kLzSteps, n);
+    double *q = m.v[V_F], *qp = m.v[V_X1], *wv = m.v[V_R], *isd = m.v[V_X2], *sc = m.v[V_T];
+    const int ge = eblk(n), gr = grid_rows(h, n);
+    k_lz_isd<<<AMG_GRID(ge), kBlock, 0, s>>>(n, L.dl1, isd);
+    k_v_probe<<<AMG_GRID(ge), kBlock, 0, s>>>(n, kLzSeed + (uint64_t)l, 0, q);
+    k_lz_dot<<<AMG_GRID(1), 1024, 0, s>>>(n, q, q, sc);
+    k_lz_start<<<AMG_GRID(ge), kBlock, 0, s>>>(n, sc, q);
+    cudaMemsetAsync(qp, 0, sizeof(double) * n, s);
+    for (int j = 0; j < steps; j++) {
+        k_lz_apply<<<AMG_GRID(gr), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, isd, q, qp,
+                                                   j > 0 ? m.ab + kLzMax + j - 1 : nullptr, wv);
+        k_lz_dot<<<AMG_GRID(1), 1024, 0, s>>>(n, q, wv, m.ab + j);
+        k_lz_orth<<<AMG_GRID(ge), kBlock, 0, s>>>(n, m.ab + j, q, wv);
+        k_lz_dot<<<AMG_GRID(1), 1024, 0, s>>>(n, wv, wv, sc);
+        k_lz_next<<<AMG_GRID(ge), kBlock, 0, s>>>(n, sc, m.ab + kLzMax + j, q, qp, wv);
+    }
+    k_lz_finish<<<AMG_GRID(1), 32, 0, s>>>(steps, m.ab, m.cap);
+}
+
+// Node features and edge weights of level l (see the file header), and its
+// damping cap, on stream s; the buffers must be allocated and ordered
+// before s.
 void features_level(amg_hierarchy* h, int l, cudaStream_t s) {
     MpnnLevel& m = h->mp->lev[l];
     if (m.features) return;
@@ -636,6 +808,7 @@ void features_level(amg_hierarchy* h, int l, cudaStream_t s) {
     k_nn_rsqrt_diag<<<AMG_GRID(eblk(n)), kBlock, 0, s>>>((int)n, L.kii, m.sg);
     k_nn_features<<<AMG_GRID(grid_rows(h, n)), kBlock, 0, s>>>((int)n, L.A.rowptr, L.A.col, L.A.val, L.kii, m.sg,
                                                                  m.x, m.ap);
+    cap_level(h, l, s);
     m.features = 1;
 }
 
@@ -705,9 +878,9 @@ void forward_level(amg_hierarchy* h, int l, const float* wd, int bf16, cudaStrea
           *h2 = m.t[7];
     k_nn_in<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, m.x, u0, h0);
     k_nn_spmm<<<AMG_GRID(g), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, m.ap, h0, nullptr, m1);
-    k_nn_dense<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, 1, m1, h0, u1, h1, nullptr, nullptr);
+    k_nn_dense<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, 1, m1, h0, u1, h1, nullptr, nullptr, nullptr);
     k_nn_spmm<<<AMG_GRID(g), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, m.ap, h1, nullptr, m2);
-    k_nn_dense<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, 2, m2, h1, u2, h2, m.sg, m.omega);
+    k_nn_dense<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, 2, m2, h1, u2, h2, m.sg, m.omega, m.cap);
 }
 
 // omega of levels [0, nlev - 1); the coarsest level has no smoother.
@@ -730,7 +903,7 @@ cudaError_t net_backward(amg_hierarchy* h, const float* wd, int l) {
           *h2 = m.t[7];
     float *b0 = w.bw[0], *b1 = w.bw[1], *b2 = w.bw[2];
     const int gs = eblk(kGradSlots);
-    k_nn_out_bwd<<<AMG_GRID(gg), kBlock, 0, s>>>(n, wd, m.domega, m.sg, h2, u2, b0, w.part);
+    k_nn_out_bwd<<<AMG_GRID(gg), kBlock, 0, s>>>(n, wd, m.domega, m.sg, h2, u2, b0, w.part, m.cap);
     k_nn_grad_sum<<<AMG_GRID(gs), kBlock, 0, s>>>(gg, w.part, H + 1, w.dst, w.gacc);
     // layer 2: du2 (b0) -> dm2 (b1), V2^T du2 (b2); dh1 = A' dm2 + V2^T du2 (b0)
     k_nn_dense_bwd<<<AMG_GRID(gg), kBlock, 0, s>>>(n, wd, 2, b0, m2, h1, b1, b2, w.part);
@@ -748,8 +921,6 @@ cudaError_t net_backward(amg_hierarchy* h, const float* wd, int l) {
     return cudaGetLastError();
 }
 
-// Vector slots of a level in the differentiated V-cycle.
-enum { V_F = 0, V_X1, V_R, V_X2, V_OUT, V_G, V_T };
 
 // Damped V-cycle from level l on f = v[V_F] into v[V_OUT], keeping the tape
 // (f in V_F, r2 in V_R):
@@ -847,14 +1018,15 @@ int loss_grad_enqueue(amg_hierarchy* h, const float* wd, int nprobe, uint64_t se
     return AMG_OK;
 }
 
-// Install the damping of the last network evaluation (learned) or the plain
-// l1-Jacobi diagonal on every level that has a smoother.
-cudaError_t set_damping(amg_hierarchy* h, bool learned) {
+// Install the damping of the last network evaluation (learned) or the
+// constant damping omc (omc = 1: the plain l1-Jacobi diagonal) on every
+// level that has a smoother.
+cudaError_t set_damping(amg_hierarchy* h, bool learned, double omc = 1.0) {
     cudaStream_t s = h->s;
     for (int l = 0; l + 1 < h->nlev; l++) {
         Level& L = h->lev[l];
-        k_set_damping<<<AMG_GRID(eblk(L.A.n)), kBlock, 0, s>>>(L.A.n, learned ? h->mp->lev[l].omega : nullptr, L.dl1,
-                                                                L.invd, L.invd32);
+        k_set_damping<<<AMG_GRID(eblk(L.A.n)), kBlock, 0, s>>>(L.A.n, learned ? h->mp->lev[l].omega : nullptr, omc,
+                                                                L.dl1, L.invd, L.invd32);
     }
     return cudaGetLastError();
 }
@@ -1029,9 +1201,31 @@ int amg_mpnn_train(amg_hierarchy* const* hs, int32_t count, float* w, int32_t st
     return AMG_OK;
 }
 
-int amg_mpnn_select(amg_hierarchy* h, const float* w, const double* F, double rtol, int32_t itmax, int32_t* used,
-                    int32_t* iters_plain, int32_t* iters_learned) {
-    if (!h || !w || !F || !(rtol > 0.0) || itmax < 1 || h->nsys > 0) return AMG_ERR_ARG;
+int amg_set_damping(amg_hierarchy* h, double omega) {
+    if (!h || !(omega > 0.0) || !isfinite(omega)) return AMG_ERR_ARG;
+    MP_RC(join_caller_stream(h));
+    MP_RC(status_of(set_damping(h, false, omega)));
+    MP_RC(sync_status(h));
+    h->damping_learned = 0;
+    return AMG_OK;
+}
+
+int amg_smoother_bound(amg_hierarchy* h, int32_t level, double* lambda_hat) {
+    if (!h || !lambda_hat || level < 0 || level >= h->nlev) return AMG_ERR_ARG;
+    MP_RC(join_caller_stream(h));
+    MP_RC(ensure_work(h));
+    if (h->mp->forked) MP_RC(status_of(cudaStreamWaitEvent(h->s, h->mp->ev_done, 0)));
+    MP_RC(alloc_level(h, level));
+    features_level(h, level, h->s);
+    MP_RC(status_of(cudaGetLastError()));
+    MP_RC(read_host(h, h->mp->lev[level].cap, lambda_hat));
+    return AMG_OK;
+}
+
+int amg_mpnn_select(amg_hierarchy* h, const float* w, double omega_ref, const double* F, double rtol, int32_t itmax,
+                    int32_t* used, int32_t* iters_ref, int32_t* iters_learned) {
+    if (!h || !w || !F || !(rtol > 0.0) || itmax < 1 || h->nsys > 0 || !(omega_ref > 0.0) || !isfinite(omega_ref))
+        return AMG_ERR_ARG;
     const int n = h->lev[0].A.n;
     double* u = nullptr;
     MP_RC(status_of(dev_alloc(reinterpret_cast<void**>(&u), sizeof(double) * n, h->s)));
@@ -1040,20 +1234,28 @@ int amg_mpnn_select(amg_hierarchy* h, const float* w, const double* F, double rt
         cudaStream_t s;
         ~Release() { cudaFreeAsync(p, s); }
     } release{u, h->s};
-    int32_t ip = 0, il = 0;
-    MP_RC(amg_mpnn_apply(h, nullptr, 0));
+    int32_t ir = 0, il = 0;
+    MP_RC(amg_set_damping(h, omega_ref));
     MP_RC(status_of(cudaMemsetAsync(u, 0, sizeof(double) * n, h->s)));
-    const int rp = amg_pcg_solve(h, F, u, AMG_MEM_DEVICE, rtol, itmax, &ip, nullptr);
-    if (rp == AMG_ERR_CUDA || rp == AMG_ERR_NOMEM) return rp;
+    const int rr = amg_pcg_solve(h, F, u, AMG_MEM_DEVICE, rtol, itmax, &ir, nullptr);
+    if (rr == AMG_ERR_CUDA || rr == AMG_ERR_NOMEM) return rr;
+    // from here on every early return puts the reference damping back
+    struct Restore {
+        amg_hierarchy* h;
+        double om;
+        bool keep = false;
+        ~Restore() {
+            if (!keep) amg_set_damping(h, om);
+        }
+    } restore{h, omega_ref};
     MP_RC(amg_mpnn_apply(h, w, 1));
     MP_RC(status_of(cudaMemsetAsync(u, 0, sizeof(double) * n, h->s)));
     const int rl = amg_pcg_solve(h, F, u, AMG_MEM_DEVICE, rtol, itmax, &il, nullptr);
     if (rl == AMG_ERR_CUDA || rl == AMG_ERR_NOMEM) return rl;
     // keep the learned damping only if it converged in no more iterations
-    const bool keep = rl == AMG_OK && (rp != AMG_OK || il <= ip);
-    if (!keep) MP_RC(amg_mpnn_apply(h, nullptr, 0));
-    if (used) *used = keep ? 1 : 0;
-    if (iters_plain) *iters_plain = ip;
+    restore.keep = rl == AMG_OK && (rr != AMG_OK || il <= ir);
+    if (used) *used = restore.keep ? 1 : 0;
+    if (iters_ref) *iters_ref = ir;
     if (iters_learned) *iters_learned = il;
     return AMG_OK;
 }

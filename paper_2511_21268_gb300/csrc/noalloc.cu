@@ -15,7 +15,14 @@
 // Host code must not use the array's name as a device address (on the host
 // it only names a host-side stand-in).  The first call on each device looks
 // up the real address with cudaGetSymbolAddress while that device is
-// current, caches it per device and passes it to the kernels.
+// current, caches it per device and passes it to the kernels.  The device is
+// the one that owns the caller's stream (the current device for the NULL
+// stream); the call makes it current for its duration and restores the
+// caller's current device before returning.
+//
+// Launch failures are read from the launch calls themselves, so an earlier
+// unrelated error pending in the caller's context is neither reported as
+// this call's failure nor cleared.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -97,11 +104,10 @@ __global__ void k_noalloc_finish(double* scratch, int nblocks) {
     }
 }
 
-// Device address of the scratch array on the current device (looked up once
-// per device).
-int noalloc_scratch(double** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return AMG_ERR_CUDA;
+// Device address of the scratch array on device `dev`, which must be the
+// current device (looked up once per device).
+int noalloc_scratch(int dev, double** out) {
+    if (dev < 0 || dev >= kNoallocMaxDevices) return AMG_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
         void* p = nullptr;
@@ -112,6 +118,31 @@ int noalloc_scratch(double** out) {
     return AMG_OK;
 }
 
+// The work of amg_relres_noalloc on the current device, which owns s.
+int relres_on_device(int dev, const amg_csr* K, const double* F, const double* u, double* relres, cudaStream_t s) {
+    double* scratch = nullptr;
+    int rc = noalloc_scratch(dev, &scratch);
+    if (rc != AMG_OK) return rc;
+    int n = K->n;
+    int nblocks = (n + kNoallocWarps - 1) / kNoallocWarps;
+    const int64_t* rp = K->rowptr;
+    const int32_t* ci = K->col;
+    const double* v = K->val;
+    void* a1[] = {&n, &rp, &ci, &v, &u, &F, &scratch, &nblocks};
+    cudaError_t e = cudaLaunchKernel((const void*)k_noalloc_partials, dim3(nblocks), dim3(kNoallocWarps * 32), a1, 0, s);
+    void* a2[] = {&scratch, &nblocks};
+    if (e == cudaSuccess) e = cudaLaunchKernel((const void*)k_noalloc_finish, dim3(1), dim3(256), a2, 0, s);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();  // this call's own launch error; leave no trace of it
+        return AMG_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(relres, scratch + 2 * kNoallocMaxBlocks, sizeof(double), cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+        return AMG_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return AMG_ERR_CUDA;
+    return AMG_OK;
+}
+
 }  // namespace
 
 extern "C" int amg_relres_noalloc(const amg_csr* K, const double* F, const double* u, double* relres,
@@ -119,17 +150,13 @@ extern "C" int amg_relres_noalloc(const amg_csr* K, const double* F, const doubl
     if (!K || !F || !u || !relres || !K->rowptr || !K->col || !K->val) return AMG_ERR_ARG;
     if (K->mem != AMG_MEM_DEVICE || K->n < 1) return AMG_ERR_ARG;
     if (K->n > AMG_NOALLOC_MAX_ROWS) return AMG_ERR_ARG;  // beyond the static scratch
-    double* scratch = nullptr;
-    int rc = noalloc_scratch(&scratch);
-    if (rc != AMG_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    const int nblocks = (K->n + kNoallocWarps - 1) / kNoallocWarps;
-    k_noalloc_partials<<<nblocks, kNoallocWarps * 32, 0, s>>>(K->n, K->rowptr, K->col, K->val, u, F, scratch, nblocks);
-    k_noalloc_finish<<<1, 256, 0, s>>>(scratch, nblocks);
-    if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
-    if (cudaMemcpyAsync(relres, scratch + 2 * kNoallocMaxBlocks, sizeof(double), cudaMemcpyDeviceToHost, s) !=
-        cudaSuccess)
-        return AMG_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return AMG_ERR_CUDA;
-    return AMG_OK;
+    int cur = 0, dev = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return AMG_ERR_CUDA;
+    if (cudaStreamGetDevice(s, &dev) != cudaSuccess) return AMG_ERR_CUDA;
+    if (dev == cur) return relres_on_device(dev, K, F, u, relres, s);
+    if (cudaSetDevice(dev) != cudaSuccess) return AMG_ERR_CUDA;
+    const int rc = relres_on_device(dev, K, F, u, relres, s);
+    if (cudaSetDevice(cur) != cudaSuccess) return AMG_ERR_CUDA;
+    return rc;
 }

@@ -1,18 +1,26 @@
 """Learned smoother damping on the GPU against the oracle (oracle/mpnn.py).
 
+* The damping cap: the Lanczos estimate lam_hat of lambda_max(D^-1 K) per
+  level against the oracle's (1e-10 relative).
 * omega of the network on every level: FP32 weights and BF16-rounded
   weights, against the oracle's FP64 forward with the same weights
-  (|diff| <= 2e-5; omega is in (0, 2) and the GPU computes in FP32).
+  (|diff| <= 2e-5; omega is in (0, omega_max), omega_max = 2 / lam_hat <
+  2.9, and the GPU computes in FP32).
 * The installed damping is what the V-cycle runs: GPU V-cycle vs the
   oracle's damped V-cycle with the GPU's omega (1e-12), and restoring the
   plain smoother is bitwise.
 * Loss and gradient: the loss with the GPU's omega equals the oracle's
   FP64 loss for that omega (1e-10); against the oracle's end-to-end
-  loss/gradient for the same weights, loss 1e-5 and gradient 2e-3 relative
-  (FP32 network).  Two runs are bitwise identical.
+  loss/gradient for the same weights, loss 1e-5 and gradient 1e-5 relative
+  (FP32 network and FP32 weights; every parameter block 1e-5 of its own
+  norm).  Two runs are bitwise identical.
 * Adam step against the textbook update; training lowers the loss and the
-  PCG iteration count; the fallback rule keeps the plain smoother when the
-  learned one is worse.
+  PCG iteration count; the fallback rule keeps the reference smoother when
+  the learned one is worse.
+* Constant damping (amg_set_damping): the V-cycle against the oracle's
+  damped V-cycle, omega = 1 restores the plain smoother bit for bit.
+* The trained network against the best constant damping of a sweep:
+  iterations, spread of omega, no saturation at the cap.
 """
 import numpy as np
 import pytest
@@ -70,7 +78,7 @@ def test_omega_matches_oracle(case, bf16):
     spread = 0.0
     for l in range(H.num_levels - 1):
         om = H.mpnn_omega(l).cpu().numpy().astype(np.float64)
-        ref, _ = M.forward(wref, *M.features(*lv.csr[l]))
+        ref, _ = M.forward(wref, *M.features(*lv.csr[l]), lv.omax[l])
         assert np.max(np.abs(om - ref)) <= 2e-5, (l, np.max(np.abs(om - ref)))
         spread = max(spread, ref.max() - ref.min())
     assert spread > 0.1
@@ -108,13 +116,37 @@ def test_loss_and_gradient_match_oracle(case):
     assert abs(loss - L_ref) <= 1e-5 * abs(L_ref)
     err = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
     print(f"N={prob.n}: loss {loss:.6f} (oracle {L_ref:.6f}), gradient relative error {err:.2e}")
-    assert err <= 2e-3
+    assert err <= 1e-5
     # every parameter block receives its gradient
     for name, blk in M.unpack(g_ref).items():
         gb = M.unpack(g)[name]
-        assert np.linalg.norm(gb - blk) <= 5e-3 * np.linalg.norm(blk) + 1e-4 * np.linalg.norm(g_ref), name
+        assert np.linalg.norm(gb - blk) <= 1e-5 * np.linalg.norm(blk) + 1e-7 * np.linalg.norm(g_ref), name
     loss2, g2 = H.mpnn_loss_grad(dev(w32), nprobe=3, seed=11)
     assert loss2 == loss and np.array_equal(g2.cpu().numpy(), g)
+
+
+def test_smoother_bound_matches_oracle(case):
+    prob, Ho, H, lv = case
+    for l in range(H.num_levels - 1):
+        lam = H.smoother_bound(l)
+        assert abs(2.0 / lam - lv.omax[l]) <= 1e-10 * lv.omax[l], (l, 2.0 / lam, lv.omax[l])
+        assert 0.6 < lam <= 1.0
+
+
+def test_constant_damping_matches_oracle_and_one_is_plain(case):
+    prob, Ho, H, lv = case
+    r = np.random.default_rng(4).standard_normal(prob.n)
+    z_plain = H.vcycle(dev(r)).cpu().numpy()
+    for om in (1.7, 2.2):
+        H.set_damping(om)
+        z = H.vcycle(dev(r)).cpu().numpy()
+        zo = M.vcycle_omega(lv, [np.full(lv.K[l].shape[0], om) for l in range(lv.L)], r)
+        assert np.linalg.norm(z - zo) <= 1e-12 * np.linalg.norm(zo)
+    H.set_damping(1.0)
+    z_back = H.vcycle(dev(r)).cpu().numpy()
+    assert np.array_equal(z_back.view(np.uint64), z_plain.view(np.uint64))
+    with pytest.raises(A.AmgError):
+        H.set_damping(0.0)
 
 
 def test_adam_step_matches_textbook():
@@ -168,6 +200,13 @@ def test_fallback_keeps_plain_smoother_when_learned_is_worse():
     assert not used and il > ip
     z = H.vcycle(dev(r)).cpu().numpy()
     assert np.array_equal(z.view(np.uint64), z_plain.view(np.uint64))
+    # against a constant reference damping: that damping stays installed
+    used, ic, il = H.mpnn_select(dev(M.pack(d).astype(np.float32)), dev(prob.F), rtol=1e-8, itmax=2000,
+                                 omega_ref=1.8)
+    assert not used and ic < ip
+    H.set_damping(1.8)
+    z18 = H.vcycle(dev(r)).cpu().numpy()
+    assert np.array_equal(H.vcycle(dev(r)).cpu().numpy().view(np.uint64), z18.view(np.uint64))
 
 
 @pytest.mark.parametrize("prec", [A.AMG_FP32, A.AMG_FP32_BF16FINE])
@@ -237,3 +276,52 @@ def test_weights_at_setup_install_the_apply_damping_bit_for_bit(prec, bf16):
     with pytest.raises(A.AmgError):
         A.Hierarchy(*args, coarse_max=50, mpnn_weights=w, mpnn_bf16=2)
 
+
+
+def test_trained_network_against_the_best_constant_damping():
+    """The question the learned part has to answer: does a per-row damping
+    beat the best single damping value?  Train on 3-D cubes p in {2, 3, 4},
+    n = 10 (FP64 hierarchies), then on a 3-D p=3 n=16 cube compare PCG
+    iterations with the network against a sweep of constants.  The trained
+    omega must vary over the rows (rows may sit at the level's cap 2 /
+    lam_hat, the edge of the range where the smoother is guaranteed to
+    converge, but not all of them); the fallback rule against the best
+    constant keeps whichever is better, so the installed smoother is never
+    worse than that constant."""
+    train = []
+    for pp in (2, 3, 4):
+        q = I.poisson_box(3, 10, pp)
+        train.append(A.Hierarchy(dev(q.rowptr), dev(q.col), dev(q.val)))
+    w = dev(I.mpnn_init_weights(1).astype(np.float32))
+    hist = train[0].mpnn_train(w, steps=60, nprobe=4, seed=1000, lr=1e-2, others=train[1:])
+    assert hist[-10:].mean() < hist[0] - 0.3
+    prob = I.poisson_box(3, 16, 3)
+    H = A.Hierarchy(dev(prob.rowptr), dev(prob.col), dev(prob.val))
+    F = dev(prob.F)
+    its = {}
+    for om in (1.0, 1.5, 1.8, 2.0, 2.2, 2.4):
+        H.set_damping(om)
+        g = H.solve(F, rtol=1e-8, itmax=2000)
+        if g["status"] == 0:
+            its[om] = g["iters"]
+    best = min(its, key=lambda o: (its[o], o))
+    H.mpnn_apply(w, bf16_weights=True)
+    g = H.solve(F, rtol=1e-8)
+    assert g["status"] == 0
+    stats = []
+    for l in range(H.num_levels - 1):
+        om = H.mpnn_omega(l).cpu().numpy()
+        omax = 2.0 / H.smoother_bound(l)
+        at_cap = float(np.mean(om >= 0.999 * omax))
+        stats.append((l, om.min(), om.max(), om.std(), omax, at_cap))
+        assert at_cap < 0.95
+    print("constant sweep", its, "best", best, "learned", g["iters"],
+          "omega per level (min, max, std, cap, fraction at the cap)",
+          [tuple(round(float(x), 3) for x in s_) for s_ in stats])
+    assert stats[0][3] > 1e-2  # omega varies over the rows of the finest level
+    assert g["iters"] < its[1.0]
+    used, ic, il = H.mpnn_select(w, F, rtol=1e-8, omega_ref=best)
+    assert ic == its[best] and il == g["iters"]
+    assert used == (il <= ic)
+    final = H.solve(F, rtol=1e-8)
+    assert final["iters"] == min(il, ic)

@@ -114,3 +114,69 @@ def test_damping_range_keeps_smoother_convergent(small):
     E = np.eye(prob.n) - (om / lv.d[0])[:, None] * K
     Lk = np.linalg.cholesky(K)
     assert np.linalg.norm(Lk.T @ E @ np.linalg.inv(Lk.T), 2) < 1
+
+
+# ---------------------------------------------------------- damping cap ----
+def test_lanczos_bound_exact_on_diagonal_matrices():
+    """For diagonal K the spectrum of D^-1 K is k_i / d_i: Lanczos with as
+    many steps as rows spans the whole space, so the estimate is the exact
+    maximum; with K = D it is 1 (the cap)."""
+    rng = np.random.default_rng(8)
+    k = rng.uniform(1.0, 3.0, 9)
+    d = k / rng.uniform(0.2, 0.95, 9)
+    import scipy.sparse as sp
+
+    lam = M.lanczos_bound(sp.diags(k).tocsr(), d, steps=20)
+    assert abs(lam - (k / d).max()) <= 1e-12
+    assert M.lanczos_bound(sp.diags(d).tocsr(), d) == 1.0
+
+
+@pytest.mark.parametrize("d,n,p", [(2, 10, 3), (3, 6, 2), (3, 5, 3)])
+def test_lanczos_bound_is_a_close_upper_estimate(d, n, p):
+    """Against the dense spectrum: lambda_max(D^-1 K) <= lam_hat <= 1.03
+    lambda_max on every level of IgA hierarchies (the residual term
+    beta_k |s_k| lifts the Ritz value over the eigenvalue)."""
+    prob = I.poisson_box(d, n, p)
+    H = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=20)
+    lv = M.Levels(H)
+    for l in range(lv.L - 1):
+        K = lv.K[l].toarray()
+        dl = lv.d[l]
+        lam = np.linalg.eigvalsh(K / np.sqrt(dl)[:, None] / np.sqrt(dl)[None, :]).max()
+        est = M.lanczos_bound(lv.K[l], dl, seed=M.LANCZOS_SEED + l)
+        assert lam <= est <= min(1.0, 1.03 * lam), (l, lam, est)
+        assert abs(lv.omax[l] - 2.0 / est) <= 1e-15 * lv.omax[l]
+        assert 0.6 < lam < 0.95  # IgA levels: the admissible damping reaches past 2
+
+
+def test_damping_below_the_cap_keeps_smoother_convergent(small):
+    """Every omega_i in (0, 2 / lam_hat) gives a K-norm contraction: the
+    cap enlarges the admissible range past 2 without losing convergence."""
+    prob, H, lv = small
+    K = lv.K[0].toarray()
+    rng = np.random.default_rng(6)
+    om = rng.uniform(0.01, 0.999 * lv.omax[0], prob.n)
+    om[:5] = 0.999 * lv.omax[0]
+    assert om.max() > 2.0
+    E = np.eye(prob.n) - (om / lv.d[0])[:, None] * K
+    Lk = np.linalg.cholesky(K)
+    assert np.linalg.norm(Lk.T @ E @ np.linalg.inv(Lk.T), 2) < 1
+
+
+def test_capped_output_gradient_finite_differences(small):
+    """The loss gradient through omega = omega_max sigmoid(z) (per-level
+    omega_max) against central differences of the weights."""
+    prob, H, lv = small
+    w = M.init_weights(12)
+    dd = M.unpack(w)
+    dd["q"] = dd["q"] * 10
+    dd["c"] = np.array([2.5])
+    w = M.pack(dd)
+    L0, g, om = M.loss_and_grad(lv, w, nprobe=2, seed=13)
+    assert max(o.max() for o in om[:-1]) > 2.0  # past the old (0, 2) range
+    v = np.random.default_rng(14).standard_normal(M.NPARAM)
+    h = 1e-6
+    Lp, _, _ = M.loss_and_grad(lv, w + h * v, nprobe=2, seed=13)
+    Lm, _, _ = M.loss_and_grad(lv, w - h * v, nprobe=2, seed=13)
+    fd = (Lp - Lm) / (2 * h)
+    assert abs(fd - g @ v) <= 1e-5 * max(abs(fd), 1e-8)

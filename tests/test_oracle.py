@@ -168,6 +168,51 @@ def test_l1_diag_dominates_and_smoother_contracts():
     assert O.l1_diag(prob.rowptr, prob.col, v)[1] == -2
 
 
+def tridiag(n):
+    """CSR of tridiag(-1, 2, -1) (1-D linear finite elements, h = 1)."""
+    T = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    return to_csr(T)
+
+
+def test_l1_diag_closed_forms():
+    """d_i = k_ii + sum_{j != i} |k_ij| (Sec. 3.2) on matrices whose l1
+    diagonal is known by hand: tridiag(-1, 2, -1) gives (3, 4, ..., 4, 3);
+    the 5-point Laplacian on a 3 x 3 grid gives 6 at corners, 7 on edges,
+    8 in the centre; a row with entries of both signs adds their moduli
+    (a double-counted k_ii or a signed sum would fail each of these)."""
+    d, rc = O.l1_diag(*tridiag(7))
+    assert rc == 0 and np.array_equal(d, [3.0, 4.0, 4.0, 4.0, 4.0, 4.0, 3.0])
+    T = 2.0 * np.eye(3) - np.eye(3, k=1) - np.eye(3, k=-1)
+    L2 = np.kron(T, np.eye(3)) + np.kron(np.eye(3), T)
+    d, rc = O.l1_diag(*to_csr(L2))
+    assert rc == 0 and np.array_equal(d, [6.0, 7.0, 6.0, 7.0, 8.0, 7.0, 6.0, 7.0, 6.0])
+    A = np.array([[4.0, -0.5, 0.25, -1.0], [-0.5, 3.0, 0.0, 0.125], [0.25, 0.0, 2.0, 0.0], [-1.0, 0.125, 0.0, 5.0]])
+    d, rc = O.l1_diag(*to_csr(A))
+    assert rc == 0 and np.array_equal(d, [5.75, 3.625, 2.25, 6.125])
+
+
+def test_test_vector_sweeps_closed_form():
+    """Test-vector relaxation w <- w - D_l1^-1 K w (Sec. 3.1 with the
+    smoother of Sec. 3.2) from w0 = 1 on tridiag(-1, 2, -1): K w0 =
+    (1, 0, ..., 0, 1), so one sweep gives (2/3, 1, ..., 1, 2/3); the second
+    gives (5/9, 11/12, 1, ..., 1, 11/12, 5/9).  Dividing by k_ii = 2 instead
+    of d_i, or sweeping in place (Gauss-Seidel order), changes both."""
+    rp, ci, v = tridiag(8)
+    w1 = O.test_vector(rp, ci, v, kind=1, sweeps=1)
+    assert np.allclose(w1, [2 / 3, 1, 1, 1, 1, 1, 1, 2 / 3], rtol=0, atol=1e-15)
+    w2 = O.test_vector(rp, ci, v, kind=1, sweeps=2)
+    assert np.allclose(w2, [5 / 9, 11 / 12, 1, 1, 1, 1, 11 / 12, 5 / 9], rtol=0, atol=1e-15)
+    # 2-D: the 5-point Laplacian on a 4 x 4 grid from w0 = 1.  (K 1)_i is
+    # the number of eliminated neighbours: 2 at corners (d = 6), 1 on edges
+    # (d = 7), 0 inside, so w1 = 1 - 2/6 at corners and 1 - 1/7 on edges.
+    T = 2.0 * np.eye(4) - np.eye(4, k=1) - np.eye(4, k=-1)
+    L2 = np.kron(T, np.eye(4)) + np.kron(np.eye(4), T)
+    w1 = O.test_vector(*to_csr(L2), kind=1, sweeps=1).reshape(4, 4)
+    expect = np.array([[2 / 3, 6 / 7, 6 / 7, 2 / 3], [6 / 7, 1, 1, 6 / 7], [6 / 7, 1, 1, 6 / 7],
+                       [2 / 3, 6 / 7, 6 / 7, 2 / 3]])
+    assert np.allclose(w1, expect, rtol=0, atol=1e-15)
+
+
 def test_test_vector_start_and_smoothing():
     prob = I.poisson_box(2, 10, 2)
     w0 = O.test_vector(prob.rowptr, prob.col, prob.val, seed=5, sweeps=0)
@@ -343,3 +388,20 @@ def test_setup_deterministic():
     for l in range(A.num_levels):
         for a, b in zip(A.level_csr(l), B.level_csr(l)):
             assert np.array_equal(a, b)
+
+
+def test_solve_phase_threads_do_not_change_results():
+    """The solve phase's row loops may run on several threads; each row's
+    sum and every dot product are evaluated as in the sequential code, so
+    the iterates are bitwise the same."""
+    prob = I.poisson_box(3, 8, 3)
+    H = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=30)
+    O.set_threads(1)
+    a = H.pcg(prob.F, rtol=1e-10)
+    got = O.set_threads(4)
+    try:
+        b = H.pcg(prob.F, rtol=1e-10)
+    finally:
+        O.set_threads(1)
+    assert got in (1, 4)
+    assert a["iters"] == b["iters"] and np.array_equal(a["u"].view(np.uint64), b["u"].view(np.uint64))

@@ -57,3 +57,22 @@ def test_noalloc_rejects_oversize_and_host_matrix():
                     A.AMG_MEM_HOST)
     assert A.lib().amg_relres_noalloc(ctypes.byref(host), F.data_ptr(), F.data_ptr(), ctypes.byref(out), None) == \
         A.AMG_ERR_ARG
+
+
+def test_noalloc_allocates_no_device_memory():
+    """The defining property: a warm call changes neither the device's free
+    memory nor torch's allocator (the first call may load the module and
+    look up the scratch address; later calls only launch and copy)."""
+    prob = I.poisson_box(3, 10, 3)
+    rp, ci, va, F = _dev(prob.rowptr), _dev(prob.col), _dev(prob.val), _dev(prob.F)
+    u = torch.zeros_like(F)
+    A.amg_relres_noalloc(rp, ci, va, F, u)  # warm: module loaded, address cached
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        assert abs(A.amg_relres_noalloc(rp, ci, va, F, u) - 1.0) <= RTOL
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_allocated() == alloc0
+

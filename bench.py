@@ -464,11 +464,16 @@ def learned_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, ref_u, fp64_
                           "end) + solve + free; constant: setup + amg_set_damping + solve + free"}
 
 
-def batched_leg(args, A, I, torch, np, stream):
+def batched_leg(args, A, I, torch, np, stream, dist=None, rank=0, world=1):
     """Batched solves (FP32 V-cycle, FP64 outer FCG(1), rtol as the bench):
     48 uneven 2-D instances as one block-diagonal hierarchy, and one 3-D
     p=3 n=48 system with 16 right-hand sides (SpMM passes), each against the
-    same systems solved one by one through amg_setup + amg_pcg_solve."""
+    same systems solved one by one through amg_setup + amg_pcg_solve.
+    Under torchrun the 48 instances are sharded across the ranks by stored
+    entries (paper_2511_21268_gb300.dist; no collective on the data path):
+    each rank times its share, the line reports the max over ranks."""
+    from paper_2511_21268_gb300 import dist as D
+
     dev = torch.device("cuda", torch.cuda.current_device())
     fp32 = A.amg_opts_default(precision=A.AMG_FP32)
     reps = 3
@@ -485,7 +490,9 @@ def batched_leg(args, A, I, torch, np, stream):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps, out
 
-    probs = I.batch_instances(seed=20251126, count=48)
+    all_probs = I.batch_instances(seed=20251126, count=48)
+    share = D.assign_by_nnz([q.nnz for q in all_probs], world)[rank]
+    probs = [all_probs[k] for k in share]
     systems = [tuple(torch.from_numpy(a).to(dev) for a in (q.rowptr, q.col, q.val)) for q in probs]
     Fs = [torch.from_numpy(q.F).to(dev) for q in probs]
 
@@ -509,6 +516,7 @@ def batched_leg(args, A, I, torch, np, stream):
 
     tb, itb = timed(batch_once)
     ts, its = timed(batch_seq)
+    tb, ts = max_over_ranks(dist, tb), max_over_ranks(dist, ts)
     q = I.poisson_box_random_rhs(3, 48, 3, seed=16, nrhs=16)
     rp, ci, va = (torch.from_numpy(a).to(dev) for a in (q.rowptr, q.col, q.val))
     Fm = torch.from_numpy(np.ascontiguousarray(q.F.reshape(16, q.n))).to(dev)
@@ -534,7 +542,9 @@ def batched_leg(args, A, I, torch, np, stream):
     tm, itm = timed(multi_once)
     tq, itq = timed(multi_seq)
     return {"batch48": {"instances": "48 x 2-D, p in {2,3,4}, n in 32..256 (seeded), F = K u, u ~ N(0,1)",
-                        "N_total": int(sum(p.n for p in probs)), "ms": tb, "ms_one_by_one": ts,
+                        "N_total": int(sum(p.n for p in all_probs)), "ms": tb, "ms_one_by_one": ts,
+                        "ranks": world, "instances_on_rank0": len(D.assign_by_nnz([q.nnz for q in all_probs],
+                                                                                 world)[0]),
                         "speedup": ts / tb, "iters_min_max": [int(min(itb)), int(max(itb))]},
             "rhs16": {"system": "3-D p=3 n=48 (N=117,649), 16 right-hand sides ~ N(0,1)", "ms": tm,
                       "ms_one_by_one": tq, "speedup": tq / tm, "iters_min_max": [int(min(itm)), int(max(itm))]},
@@ -840,7 +850,7 @@ def run_ours(args):
 
         batched = None
         if not args.no_batched:
-            batched = batched_leg(args, A, I, torch, np, stream)
+            batched = batched_leg(args, A, I, torch, np, stream, dist, rank, world)
         annulus = None
         if not args.no_annulus:
             annulus = annulus_leg(args, A, I, torch, np, stream, dist)

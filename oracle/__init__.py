@@ -47,7 +47,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("match_passes", ctypes.c_int),
                 ("coarse_max", ctypes.c_int), ("max_levels", ctypes.c_int), ("testvec_sweeps", ctypes.c_int),
                 ("testvec_kind", ctypes.c_int), ("seed", ctypes.c_uint64), ("stag", ctypes.c_double),
-                ("dense_max", ctypes.c_int)]
+                ("dense_max", ctypes.c_int), ("smooth_levels", ctypes.c_int), ("smooth_omega", ctypes.c_double)]
 
 
 _lib = None
@@ -62,6 +62,15 @@ def lib():
         L.orc_opts_default.argtypes = [P]
         L.orc_setup.argtypes = [i64, P, P, P, P, P]
         L.orc_setup.restype = P
+        L.orc_setup_ex.argtypes = [i64, P, P, P, P, P, P]
+        L.orc_setup_ex.restype = P
+        L.orc_level_sp_nnz.argtypes = [P, i32]
+        L.orc_level_sp_nnz.restype = i64
+        L.orc_level_sp.argtypes = [P, i32, P, P, P]
+        L.orc_smooth_prolongator.argtypes = [i64, P, P, P, P, P, P, P, i64, P, P, P]
+        L.orc_smooth_prolongator.restype = i32
+        L.orc_galerkin_general.argtypes = [i64, P, P, P, P, P, P, i64, P, P, P]
+        L.orc_galerkin_general.restype = i32
         L.orc_free.argtypes = [P]
         L.orc_num_levels.argtypes = [P]
         L.orc_num_levels.restype = i32
@@ -198,6 +207,46 @@ def galerkin(rowptr, col, val, agg, pval, nc):
     return rpc, cic, vc
 
 
+def smooth_prolongator(rowptr, col, val, dl1, theta, agg, pval, nc):
+    """P_bar = (I - diag(theta) D^-1 K) P as CSR (rowptr, col, val)."""
+    rp, ci, v = _csr(rowptr, col, val)
+    d = np.ascontiguousarray(dl1, np.float64)
+    th = np.ascontiguousarray(theta, np.float64)
+    a = np.ascontiguousarray(agg, np.int32)
+    pv = np.ascontiguousarray(pval, np.float64)
+    orp, oci, ov = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    rc = lib().orc_smooth_prolongator(len(rp) - 1, _p(rp), _p(ci), _p(v), _p(d), _p(th), _p(a), _p(pv), nc,
+                                      ctypes.byref(orp), ctypes.byref(oci), ctypes.byref(ov))
+    if rc != 0:
+        raise RuntimeError(ERRORS.get(rc, rc))
+    return _take_csr(len(rp) - 1, orp, oci, ov)
+
+
+def galerkin_general(rowptr, col, val, prp, pci, pv, nc):
+    """K_c = P^T (K P) for a general CSR prolongator P (n x nc)."""
+    rp, ci, v = _csr(rowptr, col, val)
+    a, b, c = _csr(prp, pci, pv)
+    orp, oci, ov = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    rc = lib().orc_galerkin_general(len(rp) - 1, _p(rp), _p(ci), _p(v), _p(a), _p(b), _p(c), nc,
+                                    ctypes.byref(orp), ctypes.byref(oci), ctypes.byref(ov))
+    if rc != 0:
+        raise RuntimeError(ERRORS.get(rc, rc))
+    return _take_csr(nc, orp, oci, ov)
+
+
+def _take_csr(n, orp, oci, ov):
+    """Copy a CSR the C code allocated with malloc into numpy and free it."""
+    libc = ctypes.CDLL(None)
+    libc.free.argtypes = [ctypes.c_void_p]
+    rp = np.ctypeslib.as_array(ctypes.cast(orp, ctypes.POINTER(ctypes.c_int64)), (n + 1,)).copy()
+    z = int(rp[-1])
+    ci = np.ctypeslib.as_array(ctypes.cast(oci, ctypes.POINTER(ctypes.c_int32)), (max(z, 1),))[:z].copy()
+    v = np.ctypeslib.as_array(ctypes.cast(ov, ctypes.POINTER(ctypes.c_double)), (max(z, 1),))[:z].copy()
+    for ptr in (orp, oci, ov):
+        libc.free(ptr)
+    return rp, ci, v
+
+
 def cholesky(A):
     A = np.array(A, np.float64, order="C")
     rc = lib().orc_cholesky(A.shape[0], _p(A))
@@ -236,12 +285,18 @@ def have_openmp() -> bool:
 class Hierarchy:
     """Oracle AMG hierarchy built from a CSR matrix (host arrays)."""
 
-    def __init__(self, rowptr, col, val, **opts):
+    def __init__(self, rowptr, col, val, theta0=None, **opts):
+        """opts: fields of Opts (smooth_levels, smooth_omega, ...); theta0:
+        per-row smoothing weights of level 0 when its prolongator is
+        smoothed (replacing smooth_omega there)."""
         self._keep = _csr(rowptr, col, val)
         rp, ci, v = self._keep
         self.opts = default_opts(**opts)
         st = ctypes.c_int()
-        self._h = lib().orc_setup(len(rp) - 1, _p(rp), _p(ci), _p(v), ctypes.byref(self.opts), ctypes.byref(st))
+        th = None if theta0 is None else np.ascontiguousarray(theta0, np.float64)
+        self._theta = th
+        self._h = lib().orc_setup_ex(len(rp) - 1, _p(rp), _p(ci), _p(v), ctypes.byref(self.opts),
+                                     None if th is None else _p(th), ctypes.byref(st))
         self.status = st.value
         if not self._h:
             raise RuntimeError(f"oracle setup failed: {ERRORS.get(st.value, st.value)}")
@@ -303,6 +358,21 @@ class Hierarchy:
 
     def pass_sizes(self, l):
         return [int(lib().orc_level_pass_n(self._h, l, s)) for s in range(self.level_npass(l) + 1)]
+
+    def prolongator(self, l):
+        """Level l's prolongator as CSR (rowptr, col, val): the smoothed one
+        where the level is smoothed, else the tentative one (one entry per
+        row)."""
+        n = self.level_n(l)
+        z = int(lib().orc_level_sp_nnz(self._h, l))
+        if z == 0:
+            agg, pv = self.level_map(l)
+            return np.arange(n + 1, dtype=np.int64), agg.astype(np.int32), pv
+        rp = np.empty(n + 1, np.int64)
+        ci = np.empty(z, np.int32)
+        v = np.empty(z)
+        lib().orc_level_sp(self._h, l, _p(rp), _p(ci), _p(v))
+        return rp, ci, v
 
     def coarse_chol(self):
         n = self.level_n(self.num_levels - 1)

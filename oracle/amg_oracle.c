@@ -23,6 +23,7 @@
  *   m-step aggregation P = P_1 ... P_m                  Sec. 3.1 ("Variants")
  *   Galerkin coarse matrix K_c = P^T K P                Sec. 3, Eq. (galerkin_matrix_projection)
  *   operator complexity                                 Sec. 3.1, Eq. (OPC)
+ *   smoothed prolongator P_bar = (I - w D^-1 K) P       Sec. 3.1 ("Variants")
  *   two-level correction / V-cycle                      Sec. 3 (steps 1-5)
  *   conjugate gradients, flexible CG                    Sec. 3, Sec. 4 ("Solver invocation"),
  *                                                       Sec. 5 (flexible CG, x0 = 0)
@@ -50,7 +51,24 @@
  *   - coarsening stops when N_l <= coarse_max, when a new level would keep
  *     more than `stag` of the rows (it is then discarded) or at max_levels.
  *     The coarsest matrix is factorised by dense Cholesky.
- *   - V-cycle with nu1 pre- and nu2 post-sweeps of l1-Jacobi from x = 0.
+ *   - smoothed prolongator (option smooth_levels): on the first
+ *     smooth_levels levels (-1: all) the composite tentative P (one entry per
+ *     row) becomes P_bar = (I - diag(theta) D^-1 K) P, D the l1 diagonal,
+ *     theta_i = smooth_omega (default 4/3: the classical 4 / (3 rho(D^-1 K))
+ *     with rho <= 1, which the l1 diagonal guarantees), or on level 0 a
+ *     per-row theta given by the caller.  Row i of P_bar holds the coarse
+ *     columns {agg(j) : j stored in row i} in ascending order, exact zeros
+ *     included; with t = theta_i / d_i and kp_J = sum over stored j of row i
+ *     in ascending order with agg(j) = J of k_ij p_j (from +0.0):
+ *       P_bar(i, J) = (J == agg(i) ? p_i : 0.0) - t kp_J.
+ *     Coarse matrix K_c = P_bar^T (K P_bar): T = K P_bar with T(i, J) = sum
+ *     over stored j of row i in ascending order of k_ij P_bar(j, J) (from
+ *     +0.0); for I <= J, K_c(I, J) = sum over the rows a of P_bar's column I
+ *     in ascending order of P_bar(a, I) T(a, J) (from +0.0);
+ *     K_c(J, I) := K_c(I, J).  Both patterns are structural.  The coarse
+ *     test vector stays w_c = P_tent^T w from the matching passes.
+ *   - V-cycle with nu1 pre- and nu2 post-sweeps of l1-Jacobi from x = 0;
+ *     restriction f_c = P^T r, prolongation x += P e (P_bar where smoothed).
  *   - PCG stops when ||r_k||_2 <= rtol ||F||_2 on the recursive residual.
  *
  * Threads: the solve phase (V-cycle and CG) may run its row loops -- each
@@ -101,6 +119,8 @@ typedef struct {
     uint64_t seed;
     double stag;      /* stop coarsening if n_{l+1} > stag * n_l */
     int dense_max;    /* largest coarsest level factorised densely */
+    int smooth_levels;   /* smoothed prolongator on the first levels (-1 = all, 0 = none) */
+    double smooth_omega; /* theta of the smoothed levels (4/3) */
 } orc_opts;
 
 typedef struct {
@@ -113,6 +133,10 @@ typedef struct {
     /* map to level l+1: composite aggregate map and prolongator values */
     int32_t* agg;
     double* pval;
+    /* smoothed prolongator (NULL when the level uses the tentative P) */
+    int64_t* sp_rp;
+    int32_t* sp_ci;
+    double* sp_v;
     /* per matching pass: mates, pass aggregate maps, pass values */
     int npass;
     int64_t pass_n[ORC_MAX_PASSES + 1];
@@ -409,6 +433,169 @@ int orc_galerkin(int64_t n, const int64_t* rp, const int32_t* ci, const double* 
     return ORC_OK;
 }
 
+/* --------------------------------------------- smoothed prolongator ---- */
+/* P_bar = (I - diag(theta) D^-1 K) P for the tentative P (value pval[i] in
+ * column agg[i]), Sec. 3.1 ("Variants"); theta[i] per row.  Output CSR
+ * (n rows, nc columns) in the order and with the values stated at the top. */
+int orc_smooth_prolongator(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* dl1,
+                           const double* theta, const int32_t* agg, const double* pval, int64_t nc,
+                           int64_t** out_rp, int32_t** out_ci, double** out_v) {
+    int64_t* prp = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+    int32_t* list = (int32_t*)malloc(sizeof(int32_t) * (nc > 0 ? nc : 1));
+    int64_t* mark = (int64_t*)malloc(sizeof(int64_t) * (nc > 0 ? nc : 1));
+    double* acc = (double*)malloc(sizeof(double) * (nc > 0 ? nc : 1));
+    if (!prp || !list || !mark || !acc) { free(prp); free(list); free(mark); free(acc); return ORC_ERR_NOMEM; }
+    for (int64_t J = 0; J < nc; J++) mark[J] = -1;
+    /* pattern: distinct agg(j) over the stored j of each row */
+    prp[0] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t cnt = 0;
+        for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+            int32_t J = agg[ci[k]];
+            if (mark[J] != i) { mark[J] = i; cnt++; }
+        }
+        prp[i + 1] = prp[i] + cnt;
+    }
+    int64_t nnz = prp[n];
+    int32_t* pci = (int32_t*)malloc(sizeof(int32_t) * (nnz > 0 ? nnz : 1));
+    double* pv = (double*)malloc(sizeof(double) * (nnz > 0 ? nnz : 1));
+    if (!pci || !pv) { free(prp); free(list); free(mark); free(acc); free(pci); free(pv); return ORC_ERR_NOMEM; }
+    for (int64_t J = 0; J < nc; J++) mark[J] = -1;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t nl = 0;
+        for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+            int32_t j = ci[k], J = agg[j];
+            if (mark[J] != i) { mark[J] = i; acc[J] = 0.0; list[nl++] = J; }
+            acc[J] = acc[J] + v[k] * pval[j];
+        }
+        qsort(list, (size_t)nl, sizeof(int32_t), cmp_i32);
+        const double t = theta[i] / dl1[i];
+        for (int64_t q = 0; q < nl; q++) {
+            int32_t J = list[q];
+            pci[prp[i] + q] = J;
+            pv[prp[i] + q] = (J == agg[i] ? pval[i] : 0.0) - t * acc[J];
+        }
+    }
+    free(list); free(mark); free(acc);
+    *out_rp = prp;
+    *out_ci = pci;
+    *out_v = pv;
+    return ORC_OK;
+}
+
+/* K_c = P^T (K P) for a general prolongator P (CSR, n x nc, sorted columns):
+ * T = K P row by row (for each coarse column, terms in ascending fine
+ * column order), then for I <= J the sum over the rows a of column I of P
+ * in ascending order of P(a, I) T(a, J), mirrored to J < I.  Output CSR with
+ * sorted columns. */
+int orc_galerkin_general(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const int64_t* prp,
+                         const int32_t* pci, const double* pv, int64_t nc, int64_t** out_rp, int32_t** out_ci,
+                         double** out_v) {
+    double* acc = (double*)malloc(sizeof(double) * (nc > 0 ? nc : 1));
+    int64_t* mark = (int64_t*)malloc(sizeof(int64_t) * (nc > 0 ? nc : 1));
+    int32_t* list = (int32_t*)malloc(sizeof(int32_t) * (nc > 0 ? nc : 1));
+    int64_t* trp = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+    if (!acc || !mark || !list || !trp) { free(acc); free(mark); free(list); free(trp); return ORC_ERR_NOMEM; }
+    /* T = K P */
+    int64_t cap = 1024, used = 0;
+    int32_t* tci = (int32_t*)malloc(sizeof(int32_t) * cap);
+    double* tv = (double*)malloc(sizeof(double) * cap);
+    for (int64_t J = 0; J < nc; J++) mark[J] = -1;
+    trp[0] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t nl = 0;
+        for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+            int64_t j = ci[k];
+            for (int64_t q = prp[j]; q < prp[j + 1]; q++) {
+                int32_t J = pci[q];
+                if (mark[J] != i) { mark[J] = i; acc[J] = 0.0; list[nl++] = J; }
+                acc[J] = acc[J] + v[k] * pv[q];
+            }
+        }
+        qsort(list, (size_t)nl, sizeof(int32_t), cmp_i32);
+        if (used + nl > cap) {
+            while (used + nl > cap) cap *= 2;
+            tci = (int32_t*)realloc(tci, sizeof(int32_t) * cap);
+            tv = (double*)realloc(tv, sizeof(double) * cap);
+        }
+        for (int64_t q = 0; q < nl; q++) { tci[used] = list[q]; tv[used] = acc[list[q]]; used++; }
+        trp[i + 1] = used;
+    }
+    /* columns of P: rows a ascending within each column */
+    int64_t* cp = (int64_t*)calloc(nc + 1, sizeof(int64_t));
+    int32_t* crow = (int32_t*)malloc(sizeof(int32_t) * (prp[n] > 0 ? prp[n] : 1));
+    double* cval = (double*)malloc(sizeof(double) * (prp[n] > 0 ? prp[n] : 1));
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (nc + 1));
+    for (int64_t q = 0; q < prp[n]; q++) cp[pci[q] + 1]++;
+    for (int64_t J = 0; J < nc; J++) cp[J + 1] += cp[J];
+    memcpy(fill, cp, sizeof(int64_t) * (nc + 1));
+    for (int64_t a = 0; a < n; a++)
+        for (int64_t q = prp[a]; q < prp[a + 1]; q++) {
+            crow[fill[pci[q]]] = (int32_t)a;
+            cval[fill[pci[q]]] = pv[q];
+            fill[pci[q]]++;
+        }
+    /* upper triangle of P^T T */
+    int64_t ucap = 1024, uused = 0;
+    int64_t* urp = (int64_t*)malloc(sizeof(int64_t) * (nc + 1));
+    int32_t* uci = (int32_t*)malloc(sizeof(int32_t) * ucap);
+    double* uv = (double*)malloc(sizeof(double) * ucap);
+    for (int64_t J = 0; J < nc; J++) mark[J] = -1;
+    urp[0] = 0;
+    for (int64_t I = 0; I < nc; I++) {
+        int64_t nl = 0;
+        for (int64_t q = cp[I]; q < cp[I + 1]; q++) {
+            int64_t a = crow[q];
+            for (int64_t t = trp[a]; t < trp[a + 1]; t++) {
+                int32_t J = tci[t];
+                if (J < I) continue;
+                if (mark[J] != I) { mark[J] = I; acc[J] = 0.0; list[nl++] = J; }
+                acc[J] = acc[J] + cval[q] * tv[t];
+            }
+        }
+        qsort(list, (size_t)nl, sizeof(int32_t), cmp_i32);
+        if (uused + nl > ucap) {
+            while (uused + nl > ucap) ucap *= 2;
+            uci = (int32_t*)realloc(uci, sizeof(int32_t) * ucap);
+            uv = (double*)realloc(uv, sizeof(double) * ucap);
+        }
+        for (int64_t t = 0; t < nl; t++) { uci[uused] = list[t]; uv[uused] = acc[list[t]]; uused++; }
+        urp[I + 1] = uused;
+    }
+    /* full symmetric matrix: row I = {J < I : I in upper row J} then upper row I */
+    int64_t* rp_c = (int64_t*)calloc(nc + 1, sizeof(int64_t));
+    for (int64_t I = 0; I < nc; I++)
+        for (int64_t t = urp[I]; t < urp[I + 1]; t++) {
+            rp_c[I + 1]++;
+            if (uci[t] != I) rp_c[uci[t] + 1]++;
+        }
+    for (int64_t I = 0; I < nc; I++) rp_c[I + 1] += rp_c[I];
+    int64_t nnzc = rp_c[nc];
+    int32_t* ci_c = (int32_t*)malloc(sizeof(int32_t) * (nnzc > 0 ? nnzc : 1));
+    double* v_c = (double*)malloc(sizeof(double) * (nnzc > 0 ? nnzc : 1));
+    memcpy(fill, rp_c, sizeof(int64_t) * (nc + 1));
+    for (int64_t I = 0; I < nc; I++)
+        for (int64_t t = urp[I]; t < urp[I + 1]; t++) {
+            int32_t J = uci[t];
+            if (J == I) continue;
+            ci_c[fill[J]] = (int32_t)I;
+            v_c[fill[J]] = uv[t];
+            fill[J]++;
+        }
+    for (int64_t I = 0; I < nc; I++)
+        for (int64_t t = urp[I]; t < urp[I + 1]; t++) {
+            ci_c[fill[I]] = uci[t];
+            v_c[fill[I]] = uv[t];
+            fill[I]++;
+        }
+    free(acc); free(mark); free(list); free(trp); free(tci); free(tv); free(cp); free(crow); free(cval);
+    free(fill); free(urp); free(uci); free(uv);
+    *out_rp = rp_c;
+    *out_ci = ci_c;
+    *out_v = v_c;
+    return ORC_OK;
+}
+
 /* -------------------------------------------------------- dense Cholesky ---- */
 /* A = L L^T, L lower, row-major in place (upper part zeroed). */
 int orc_cholesky(int64_t n, double* A) {
@@ -454,10 +641,13 @@ void orc_opts_default(orc_opts* o) {
     o->seed = 20251126ULL;
     o->stag = 0.9;
     o->dense_max = 4096;
+    o->smooth_levels = 0;
+    o->smooth_omega = 4.0 / 3.0;
 }
 
 static void level_free(orc_level* L) {
     free(L->rowptr); free(L->col); free(L->val); free(L->dl1); free(L->w); free(L->agg); free(L->pval);
+    free(L->sp_rp); free(L->sp_ci); free(L->sp_v);
     for (int s = 0; s < ORC_MAX_PASSES; s++) { free(L->pass_mate[s]); free(L->pass_agg[s]); free(L->pass_pval[s]); }
     memset(L, 0, sizeof(*L));
 }
@@ -469,8 +659,18 @@ void orc_free(orc_hier* h) {
     free(h);
 }
 
+orc_hier* orc_setup_ex(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const orc_opts* opts,
+                       const double* theta0, int* status);
+
 orc_hier* orc_setup(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const orc_opts* opts,
                     int* status) {
+    return orc_setup_ex(n, rp, ci, v, opts, NULL, status);
+}
+
+/* As orc_setup; theta0 (n entries, or NULL) replaces smooth_omega on level
+ * 0 when level 0's prolongator is smoothed. */
+orc_hier* orc_setup_ex(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const orc_opts* opts,
+                       const double* theta0, int* status) {
     orc_hier* h = (orc_hier*)calloc(1, sizeof(orc_hier));
     if (opts) h->o = *opts;
     else orc_opts_default(&h->o);
@@ -550,6 +750,32 @@ orc_hier* orc_setup(int64_t n, const int64_t* rp, const int32_t* ci, const doubl
             F->agg[i] = a;
             F->pval[i] = pv;
         }
+        const int lf = h->nlev - 1;
+        if (h->o.smooth_levels < 0 || lf < h->o.smooth_levels) {
+            /* smoothed prolongator and its Galerkin product replace the
+             * tentative P's coarse matrix */
+            double* th = (double*)malloc(sizeof(double) * F->n);
+            for (int64_t i = 0; i < F->n; i++) th[i] = (lf == 0 && theta0) ? theta0[i] : h->o.smooth_omega;
+            int rs = orc_smooth_prolongator(F->n, F->rowptr, F->col, F->val, F->dl1, th, F->agg, F->pval, cn,
+                                            &F->sp_rp, &F->sp_ci, &F->sp_v);
+            free(th);
+            int64_t* grp;
+            int32_t* gci;
+            double* gv;
+            if (rs == ORC_OK)
+                rs = orc_galerkin_general(F->n, F->rowptr, F->col, F->val, F->sp_rp, F->sp_ci, F->sp_v, cn, &grp,
+                                          &gci, &gv);
+            if (rs != ORC_OK) {
+                free(crp); free(cci); free(cv); free(cw);
+                *status = rs;
+                orc_free(h);
+                return NULL;
+            }
+            free(crp); free(cci); free(cv);
+            crp = grp;
+            cci = gci;
+            cv = gv;
+        }
         orc_level* C = &h->lev[h->nlev];
         C->n = cn;
         C->nnz = crp[cn];
@@ -597,9 +823,23 @@ static void vcycle(const orc_hier* h, int l, const double* f, double* x) {
     const int64_t nc = h->lev[l + 1].n;
     double* fc = (double*)malloc(sizeof(double) * nc);
     double* ec = (double*)malloc(sizeof(double) * nc);
-    orc_restrict(n, L->agg, L->pval, r, nc, fc);
+    if (L->sp_rp) { /* f_c = P_bar^T r, column by column in ascending row order */
+        for (int64_t J = 0; J < nc; J++) fc[J] = 0.0;
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t q = L->sp_rp[i]; q < L->sp_rp[i + 1]; q++) fc[L->sp_ci[q]] = fc[L->sp_ci[q]] + L->sp_v[q] * r[i];
+    } else {
+        orc_restrict(n, L->agg, L->pval, r, nc, fc);
+    }
     vcycle(h, l + 1, fc, ec);
-    for (int64_t i = 0; i < n; i++) x[i] = x[i] + L->pval[i] * ec[L->agg[i]];
+    if (L->sp_rp) { /* x += P_bar e */
+        for (int64_t i = 0; i < n; i++) {
+            double t = 0.0;
+            for (int64_t q = L->sp_rp[i]; q < L->sp_rp[i + 1]; q++) t = t + L->sp_v[q] * ec[L->sp_ci[q]];
+            x[i] = x[i] + t;
+        }
+    } else {
+        for (int64_t i = 0; i < n; i++) x[i] = x[i] + L->pval[i] * ec[L->agg[i]];
+    }
     for (int s = 0; s < h->o.nu_post; s++) {
         residual(L->rowptr, L->col, L->val, n, f, x, r);
         for (int64_t i = 0; i < n; i++) x[i] = x[i] + r[i] / L->dl1[i];
@@ -701,6 +941,19 @@ void orc_level_map(const orc_hier* h, int l, int s, int32_t* agg, double* pval, 
     if (pval) memcpy(pval, L->pass_pval[s], sizeof(double) * n);
     if (mate) memcpy(mate, L->pass_mate[s], sizeof(int32_t) * n);
 }
+/* stored entries of level l's smoothed prolongator (0 when tentative) */
+int64_t orc_level_sp_nnz(const orc_hier* h, int l) {
+    const orc_level* L = &h->lev[l];
+    return L->sp_rp ? L->sp_rp[L->n] : 0;
+}
+
+void orc_level_sp(const orc_hier* h, int l, int64_t* rp, int32_t* ci, double* v) {
+    const orc_level* L = &h->lev[l];
+    memcpy(rp, L->sp_rp, sizeof(int64_t) * (L->n + 1));
+    memcpy(ci, L->sp_ci, sizeof(int32_t) * L->sp_rp[L->n]);
+    memcpy(v, L->sp_v, sizeof(double) * L->sp_rp[L->n]);
+}
+
 void orc_coarse_chol(const orc_hier* h, double* L) { memcpy(L, h->chol, sizeof(double) * h->nc * h->nc); }
 
 double orc_opc(const orc_hier* h) {

@@ -405,3 +405,87 @@ def test_solve_phase_threads_do_not_change_results():
         O.set_threads(1)
     assert got in (1, 4)
     assert a["iters"] == b["iters"] and np.array_equal(a["u"].view(np.uint64), b["u"].view(np.uint64))
+
+
+# ------------------------------------------------- smoothed prolongator ----
+def _tentative(prob, **kw):
+    H = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=20, **kw)
+    d, _ = H.level_vectors(0)
+    agg, pv = H.level_map(0)
+    return H, d, agg, pv
+
+
+@pytest.mark.parametrize("d,n,p", [(2, 8, 2), (2, 6, 3), (3, 4, 2)])
+def test_smoothed_prolongator_and_galerkin_against_dense(d, n, p):
+    """P_bar = (I - diag(theta) D^-1 K) P (Sec. 3.1 "Variants") and K_c =
+    P_bar^T K P_bar against dense numpy products, per-row theta; the pattern
+    of P_bar is every aggregate a row's stored columns reach; K_c is
+    bitwise symmetric and positive definite."""
+    prob = I.poisson_box(d, n, p)
+    H, dl1, agg, pv = _tentative(prob)
+    nc = H.level_n(1)
+    K = prob.to_scipy().toarray()
+    P = np.zeros((prob.n, nc))
+    P[np.arange(prob.n), agg] = pv
+    theta = np.random.default_rng(d * 10 + p).uniform(0.3, 1.6, prob.n)
+    rp, ci, v = O.smooth_prolongator(prob.rowptr, prob.col, prob.val, dl1, theta, agg, pv, nc)
+    Pb = np.zeros((prob.n, nc))
+    for i in range(prob.n):
+        Pb[i, ci[rp[i]:rp[i + 1]]] = v[rp[i]:rp[i + 1]]
+        want = sorted({int(agg[j]) for j in prob.col[prob.rowptr[i]:prob.rowptr[i + 1]]})
+        assert list(ci[rp[i]:rp[i + 1]]) == want
+    ref = P - (theta / dl1)[:, None] * (K @ P)
+    assert np.abs(Pb - ref).max() <= 1e-14 * np.abs(ref).max()
+    crp, cci, cv = O.galerkin_general(prob.rowptr, prob.col, prob.val, rp, ci, v, nc)
+    Kc = np.zeros((nc, nc))
+    for I_ in range(nc):
+        Kc[I_, cci[crp[I_]:crp[I_ + 1]]] = cv[crp[I_]:crp[I_ + 1]]
+    Kref = ref.T @ K @ ref
+    assert np.abs(Kc - Kref).max() <= 1e-13 * np.abs(Kref).max()
+    assert np.array_equal(Kc, Kc.T)
+    np.linalg.cholesky(Kc)
+    # theta = 0 gives back the tentative prolongator (with explicit zeros)
+    rp0, ci0, v0 = O.smooth_prolongator(prob.rowptr, prob.col, prob.val, dl1, np.zeros(prob.n), agg, pv, nc)
+    P0 = np.zeros((prob.n, nc))
+    for i in range(prob.n):
+        P0[i, ci0[rp0[i]:rp0[i + 1]]] = v0[rp0[i]:rp0[i + 1]]
+    assert np.array_equal(P0, P)
+
+
+def test_smoothed_hierarchy_vcycle_symmetric_and_faster():
+    """With smoothed prolongators on every level the V-cycle stays symmetric
+    and positive (restriction = P_bar^T), the hierarchy's coarse matrices
+    are the general Galerkin products, and PCG needs fewer iterations than
+    with the tentative prolongators on a 2-D p=3 problem."""
+    prob = I.poisson_box(2, 24, 3)
+    Hs = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=30, smooth_levels=-1)
+    Ht = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=30)
+    rp, ci, v = Hs.prolongator(0)
+    crp, cci, cv = O.galerkin_general(prob.rowptr, prob.col, prob.val, rp, ci, v, Hs.level_n(1))
+    g = Hs.level_csr(1)
+    assert np.array_equal(g[0], crp) and np.array_equal(g[1], cci) and np.array_equal(g[2], cv)
+    rng = np.random.default_rng(3)
+    x, y = rng.standard_normal(prob.n), rng.standard_normal(prob.n)
+    bx, by = Hs.vcycle(x), Hs.vcycle(y)
+    assert abs(x @ by - y @ bx) <= 1e-12 * np.linalg.norm(x) * np.linalg.norm(bx)
+    assert x @ bx > 0
+    its_s = Hs.pcg(prob.F, rtol=1e-8)["iters"]
+    its_t = Ht.pcg(prob.F, rtol=1e-8)["iters"]
+    assert its_s < its_t
+    assert Hs.opc > Ht.opc  # the price: wider coarse operators
+
+
+def test_smoothed_level0_takes_per_row_theta():
+    """theta0 replaces smooth_omega on level 0 only; a constant theta0 equal
+    to smooth_omega reproduces the default hierarchy bit for bit."""
+    prob = I.poisson_box(2, 16, 2)
+    a = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=20, smooth_levels=1)
+    b = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=20, smooth_levels=1,
+                    theta0=np.full(prob.n, 4.0 / 3.0))
+    for l in range(a.num_levels):
+        for x, y in zip(a.level_csr(l), b.level_csr(l)):
+            assert np.array_equal(x, y)
+    c = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=20, smooth_levels=1,
+                    theta0=np.linspace(0.5, 1.5, prob.n))
+    assert not np.array_equal(c.level_csr(1)[2], a.level_csr(1)[2])
+    assert c.prolongator(1)[0][-1] == c.level_n(1)  # level 1 keeps the tentative prolongator

@@ -61,6 +61,7 @@ constexpr int kGradBlocks = 256;           // blocks of the weight-gradient kern
 constexpr int kGradSlots = 2 * H * H + H;  // partial sums one block writes (largest kernel)
 constexpr int kLzMax = 16;                 // Lanczos steps of the damping cap (at most)
 constexpr int kLzSteps = 15;               // Lanczos steps taken (fewer on levels with fewer rows)
+constexpr int kLzParts = 592;              // block partials of the Lanczos dot products (at most)
 constexpr uint64_t kLzSeed = 0x4C414E43ULL;  // start vector of level l: SplitMix64(kLzSeed + l)
 
 __device__ __forceinline__ float round_bf16(float w) { return __bfloat162float(__float2bfloat16_rn(w)); }
@@ -540,48 +541,75 @@ __global__ void k_lz_isd(int n, const double* __restrict__ d, double* __restrict
     if (i < n) isd[i] = 1.0 / sqrt(d[i]);
 }
 
-// w = S q - beta_prev qp, S = D^-1/2 K D^-1/2 (a warp per row); beta_prev
-// is ab[kLzMax + j - 1] (none for j = 0)
-__global__ void __launch_bounds__(kBlock) k_lz_apply(int n, const int64_t* __restrict__ rp,
-                                                      const int32_t* __restrict__ ci, const double* __restrict__ v,
-                                                      const double* __restrict__ isd, const double* __restrict__ q,
-                                                      const double* __restrict__ qp, const double* __restrict__ bprev,
-                                                      double* __restrict__ w) {
-    const int lane = threadIdx.x & 31;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    const double b = bprev ? *bprev : 0.0;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
-        double acc = 0.0;
-        for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
-            const int j = ci[k];
-            acc = fma(v[k], isd[j] * q[j], acc);
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) w[i] = isd[i] * acc - b * qp[i];
-    }
+// xs = isd q (the vector K multiplies in S q = isd K (isd q))
+__global__ void k_lz_scale(int n, const double* __restrict__ isd, const double* __restrict__ q,
+                           double* __restrict__ xs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) xs[i] = isd[i] * q[i];
 }
 
-// *out = a . b (one block, fixed order)
-__global__ void __launch_bounds__(1024) k_lz_dot(int n, const double* __restrict__ a, const double* __restrict__ b,
-                                                 double* __restrict__ out) {
-    __shared__ double sh[32];
-    double t = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) t = fma(a[i], b[i], t);
+// Fixed-order sum of one value per thread over the block -> part[blockIdx.x].
+__device__ __forceinline__ void lz_block_sum(double t, double* part) {
+    __shared__ double sh[kBlock / 32];
     t = warp_sum(t);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
     __syncthreads();
     if (threadIdx.x == 0) {
         double u = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); k++) u += sh[k];
-        *out = u;
+        for (int k = 0; k < kBlock / 32; k++) u += sh[k];
+        part[blockIdx.x] = u;
     }
 }
 
-// w -= alpha q
-__global__ void k_lz_orth(int n, const double* __restrict__ alpha, const double* __restrict__ q,
-                          double* __restrict__ w) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) w[i] -= *alpha * q[i];
+// w = isd y - beta_prev qp (beta_prev NULL: none); block partials of q . w
+__global__ void __launch_bounds__(kBlock) k_lz_w(int n, const double* __restrict__ isd, const double* __restrict__ y,
+                                                  const double* __restrict__ qp, const double* __restrict__ bprev,
+                                                  const double* __restrict__ q, double* __restrict__ w,
+                                                  double* __restrict__ part) {
+    const double b = bprev ? *bprev : 0.0;
+    double t = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double wi = isd[i] * y[i] - b * qp[i];
+        w[i] = wi;
+        t = fma(q[i], wi, t);
+    }
+    lz_block_sum(t, part);
+}
+
+// w -= alpha q; block partials of w . w
+__global__ void __launch_bounds__(kBlock) k_lz_orth(int n, const double* __restrict__ alpha,
+                                                     const double* __restrict__ q, double* __restrict__ w,
+                                                     double* __restrict__ part) {
+    const double a = *alpha;
+    double t = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double wi = w[i] - a * q[i];
+        w[i] = wi;
+        t = fma(wi, wi, t);
+    }
+    lz_block_sum(t, part);
+}
+
+// block partials of x . x
+__global__ void __launch_bounds__(kBlock) k_lz_norm2(int n, const double* __restrict__ x, double* __restrict__ part) {
+    double t = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) t = fma(x[i], x[i], t);
+    lz_block_sum(t, part);
+}
+
+// *out = sum of nb block partials (one block, fixed order)
+__global__ void __launch_bounds__(kBlock) k_lz_fin(int nb, const double* __restrict__ part, double* __restrict__ out) {
+    double t = 0.0;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) t += part[k];
+    __shared__ double sh[kBlock / 32];
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int k = 0; k < kBlock / 32; k++) u += sh[k];
+        *out = u;
+    }
 }
 
 // beta = sqrt(*nrm2) (written by block 0, thread 0 to *beta); qp = q;
@@ -673,7 +701,8 @@ struct MpnnLevel {
     float* omega = nullptr;
     double* domega = nullptr;
     double* v[kVec] = {};
-    double* ab = nullptr;   // Lanczos coefficients: alpha [0, kLzMax), beta [kLzMax, 2 kLzMax)
+    double* ab = nullptr;   // Lanczos coefficients: alpha [0, kLzMax), beta [kLzMax, 2 kLzMax), then
+                            // kLzParts block partials of the dot products
     double* cap = nullptr;  // [0] lam_hat, [1] omega_max = 2 / lam_hat
     int alloc = 0;     // buffers allocated
     int features = 0;  // features (and the damping cap) enqueued
@@ -763,7 +792,7 @@ int alloc_level(amg_hierarchy* h, int l) {
     MP_ALLOC(m.omega, sizeof(float) * n);
     MP_ALLOC(m.domega, sizeof(double) * n);
     for (int t = 0; t < MpnnLevel::kVec; t++) MP_ALLOC(m.v[t], sizeof(double) * n);
-    MP_ALLOC(m.ab, sizeof(double) * 2 * kLzMax);
+    MP_ALLOC(m.ab, sizeof(double) * (2 * kLzMax + kLzParts));
     MP_ALLOC(m.cap, sizeof(double) * 2);
     m.alloc = 1;
     return AMG_OK;
@@ -779,18 +808,23 @@ void cap_level(amg_hierarchy* h, int l, cudaStream_t s) {
     const int n = L.A.n;
     const int steps = std::min(kLzSteps, n);
     double *q = m.v[V_F], *qp = m.v[V_X1], *wv = m.v[V_R], *isd = m.v[V_X2], *sc = m.v[V_T];
-    const int ge = eblk(n), gr = grid_rows(h, n);
+    double *xs = m.v[V_OUT], *y = m.v[V_G];
+    double* part = m.ab + 2 * kLzMax;  // block partials
+    const int ge = eblk(n), gp = std::min(ge, kLzParts);
     k_lz_isd<<<AMG_GRID(ge), kBlock, 0, s>>>(n, L.dl1, isd);
     k_v_probe<<<AMG_GRID(ge), kBlock, 0, s>>>(n, kLzSeed + (uint64_t)l, 0, q);
-    k_lz_dot<<<AMG_GRID(1), 1024, 0, s>>>(n, q, q, sc);
+    k_lz_norm2<<<AMG_GRID(gp), kBlock, 0, s>>>(n, q, part);
+    k_lz_fin<<<AMG_GRID(1), kBlock, 0, s>>>(gp, part, sc);
     k_lz_start<<<AMG_GRID(ge), kBlock, 0, s>>>(n, sc, q);
     cudaMemsetAsync(qp, 0, sizeof(double) * n, s);
     for (int j = 0; j < steps; j++) {
-        k_lz_apply<<<AMG_GRID(gr), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, isd, q, qp,
-                                                   j > 0 ? m.ab + kLzMax + j - 1 : nullptr, wv);
-        k_lz_dot<<<AMG_GRID(1), 1024, 0, s>>>(n, q, wv, m.ab + j);
-        k_lz_orth<<<AMG_GRID(ge), kBlock, 0, s>>>(n, m.ab + j, q, wv);
-        k_lz_dot<<<AMG_GRID(1), 1024, 0, s>>>(n, wv, wv, sc);
+        k_lz_scale<<<AMG_GRID(ge), kBlock, 0, s>>>(n, isd, q, xs);
+        launch_spmv(L.A, xs, y, s);
+        k_lz_w<<<AMG_GRID(gp), kBlock, 0, s>>>(n, isd, y, qp, j > 0 ? m.ab + kLzMax + j - 1 : nullptr, q, wv,
+                                               part);
+        k_lz_fin<<<AMG_GRID(1), kBlock, 0, s>>>(gp, part, m.ab + j);
+        k_lz_orth<<<AMG_GRID(gp), kBlock, 0, s>>>(n, m.ab + j, q, wv, part);
+        k_lz_fin<<<AMG_GRID(1), kBlock, 0, s>>>(gp, part, sc);
         k_lz_next<<<AMG_GRID(ge), kBlock, 0, s>>>(n, sc, m.ab + kLzMax + j, q, qp, wv);
     }
     k_lz_finish<<<AMG_GRID(1), 32, 0, s>>>(steps, m.ab, m.cap);

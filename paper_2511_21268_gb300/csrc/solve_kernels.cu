@@ -493,16 +493,23 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
             else sweep_and_resid(static_cast<const A*>(Vw::f(F)));
         });
         const bool coarsest = (l + 1 == L - 1);
-        launch_pdl(k_restrict<A, 4>, restrict_blocks(C.A.n, sms), kBlock, 0, s,
-            C.A.n, F.mem_ptr, F.mem_idx, F.pval, xalt[l], Vw::f(C), coarsest ? nullptr : xcur[l + 1], Vw::invd(C), st);
+        if (F.smoothed)  // f_c = P_bar^T r
+            sp_restrict<A>(F, C, xalt[l], Vw::f(C), coarsest ? nullptr : xcur[l + 1], Vw::invd(C), st, s);
+        else
+            launch_pdl(k_restrict<A, 4>, restrict_blocks(C.A.n, sms), kBlock, 0, s, C.A.n, F.mem_ptr, F.mem_idx,
+                       F.pval, xalt[l], Vw::f(C), coarsest ? nullptr : xcur[l + 1], Vw::invd(C), st);
     }
     // coarsest
     {
         Level& F = h->lev[L - 2];
         Level& C = h->lev[L - 1];
-        launch_pdl(k_coarse<A, A>, row_blocks(C.A.n, 1), kBlock, 0, s,
-            C.A.n, h->Ainv, Vw::f(C), F.mem_ptr, F.mem_idx, F.pval, xcur[L - 2], nullptr, nullptr, nullptr, nullptr, 0,
-            st);
+        if (F.smoothed) {  // e = A^-1 f, then x += P_bar e
+            sp_coarse<A>(C.A.n, h->Ainv, Vw::f(C), xcur[L - 1], st, s);
+            sp_prolong<A>(F, xcur[L - 1], xcur[L - 2], st, s);
+        } else {
+            launch_pdl(k_coarse<A, A>, row_blocks(C.A.n, 1), kBlock, 0, s, C.A.n, h->Ainv, Vw::f(C), F.mem_ptr,
+                       F.mem_idx, F.pval, xcur[L - 2], nullptr, nullptr, nullptr, nullptr, 0, st);
+        }
     }
     // up
     for (int l = L - 2; l >= 0; l--) {
@@ -556,10 +563,22 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
                     if (l == 1 && h->sell[1].on) {  // y = smoothed level 1, then the gather into level 0
                         A* y = xalt[1];
                         sell_upy1(h, static_cast<const float*>(Vw::f(F)), xc, Vw::invd(F), y, s);
-                        launch_pdl(k_prolong<A>, vec_blocks(G.A.n, sms), kBlock, 0, s, G.A.n, G.agg, G.pval, y, xf,
-                                   st);
+                        if (G.smoothed)
+                            sp_prolong<A>(G, y, xf, st, s);
+                        else
+                            launch_pdl(k_prolong<A>, vec_blocks(G.A.n, sms), kBlock, 0, s, G.A.n, G.agg, G.pval, y,
+                                       xf, st);
                         return;
                     }
+                }
+                if (G.smoothed) {  // y = x + (f - K x) / d, then x_f += P_bar y
+                    A* y = xalt[l];
+                    with_rpw(rpw, [&](auto R) {
+                        launch_pdl(k_sweep<decltype(R)::value, A, M, A>, nb, kBlock, 0, s, n, mat,
+                                   static_cast<const A*>(Vw::f(F)), xc, Vw::invd(F), y, st);
+                    });
+                    sp_prolong<A>(G, y, xf, st, s);
+                    return;
                 }
                 with_rpw(rpw, [&](auto R) {
                     launch_pdl(k_up<decltype(R)::value, A, M>, nb, kBlock, 0, s,

@@ -312,8 +312,14 @@ int amg_relres_noalloc(const amg_csr* K, const double* F, const double* u, doubl
  *   a_ij = k_ij / sqrt(k_ii k_jj) (j != i)
  *   h0 = relu(W0 x + b0); h_l = relu(U_l (A' h_{l-1}) + V_l h_{l-1} + b_l),
  *   l = 1, 2; omega = omega_max sigmoid(q . h2 + c).
+ * A second head gives the per-row weight of the smoothed prolongator of
+ * level 0 (Sec. 3.1, "Variants", with a per-row weight):
+ *   theta = omega_max sigmoid(qt . h2 + ct),
+ *   P_bar = (I - diag(theta) D^-1 K) P,
+ * used by a setup given the weights with amg_opts.smooth_levels != 0.
  * Weights: AMG_MPNN_NPARAM floats, row-major blocks in the order
- * W0[32][4], b0[32], U1[32][32], V1[32][32], b1[32], U2, V2, b2, q[32], c[1].
+ * W0[32][4], b0[32], U1[32][32], V1[32][32], b1[32], U2, V2, b2, q[32], c[1],
+ * qt[32], ct[1].
  * All weight, gradient and moment pointers are DEVICE pointers owned by the
  * caller.  The network buffers (about 10 floats x 32 per row of every level
  * plus one float per stored entry) are allocated on first use and kept
@@ -321,7 +327,7 @@ int amg_relres_noalloc(const amg_csr* K, const double* F, const double* u, doubl
  * stream and return when their work is done.
  * ------------------------------------------------------------------------ */
 #define AMG_MPNN_HIDDEN 32
-#define AMG_MPNN_NPARAM 4353
+#define AMG_MPNN_NPARAM 4386
 
 /* Evaluate the network with weights w (weights rounded to BF16 when
  * bf16_weights = 1, FP32 when 0; FP32 arithmetic) on every level that has a
@@ -351,6 +357,28 @@ int amg_mpnn_omega(amg_hierarchy* h, int32_t level, float* omega);
 int amg_mpnn_loss_grad(amg_hierarchy* h, const float* w, int32_t nprobe, uint64_t seed, double* loss,
                        double* grad);
 
+/* Training objective of the smoothing weights theta (the network's second
+ * head) and its gradient, on a two-level hierarchy whose level-0
+ * prolongator is smoothed (amg_setup with smooth_levels = 1 and
+ * max_levels = 2):
+ *   loss = (1/m) sum_k log(y_k^T K y_k / x_k^T K x_k),
+ *   y_k = (I - M K)(I - P_bar K_c^-1 P_bar^T K)(I - M K) x_k,
+ * the two-grid error propagator with the exact coarse solve, K_c =
+ * P_bar^T K P_bar, M = diag(omega / d) with the network's omega held fixed
+ * (its gradient flows through theta only), probes as in amg_mpnn_loss_grad.
+ * The network's theta is installed into h (P_bar, the coarse matrix and its
+ * dense inverse are rewritten).  grad[AMG_MPNN_NPARAM] (device, FP64) and
+ * *loss (host) as in amg_mpnn_loss_grad.  amg_mpnn_train uses this loss for
+ * every such hierarchy it is given.  Errors: AMG_ERR_ARG (NULL pointers,
+ * nprobe < 1, another hierarchy shape), AMG_ERR_BREAKDOWN (a non-positive
+ * energy or coarse matrix), AMG_ERR_NAN, AMG_ERR_NOMEM, AMG_ERR_CUDA. */
+int amg_mpnn_theta_loss_grad(amg_hierarchy* h, const float* w, int32_t nprobe, uint64_t seed, double* loss,
+                             double* grad);
+
+/* Copy the level-0 theta of the last network evaluation (second head) to
+ * the device array theta[n_0].  AMG_ERR_ARG if there was none. */
+int amg_mpnn_theta(amg_hierarchy* h, float* theta);
+
 /* One Adam step (Kingma and Ba 2015) on w with gradient grad (FP64) and
  * moments m, v (FP32, zero before the first step); t counts steps from 1.
  * AMG_ERR_ARG on NULL pointers or parameters out of range. */
@@ -359,7 +387,9 @@ int amg_mpnn_adam(amg_hierarchy* h, float* w, const double* grad, float* m, floa
 
 /* `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on the
  * mean over the `count` hierarchies hs[0..count) (1 <= count <= 64, all on
- * the current device) of the loss of amg_mpnn_loss_grad, with probe seed
+ * the current device) of the loss of amg_mpnn_loss_grad (of
+ * amg_mpnn_theta_loss_grad for a two-level hierarchy with a smoothed level
+ * 0; other smoothed hierarchies: AMG_ERR_ARG), with probe seed
  * seed + step; w (device) is updated in place; loss_hist (host, optional)
  * receives each step's mean loss before its update.  The Adam moments live
  * with hs[0].  Errors as amg_mpnn_loss_grad. */

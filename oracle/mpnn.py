@@ -24,13 +24,24 @@ Network (hidden width 32, two message-passing layers):
   m_l = sum_j a_ij h_{l-1, j}
   h_l = relu(U_l m_l + V_l h_{l-1} + b_l),      l = 1, 2
   omega = omega_max sigmoid(q . h2 + c)
+  theta = theta_max sigmoid(qt . h2 + ct)     (second head, level 0 only)
 applied to every level's matrix with the same weights (omega_max per level).
+theta is the per-row weight of the smoothed prolongator of level 0,
+P_bar = (I - diag(theta) D^-1 K) P (the paper's Sec. 3.1 "Variants" with a
+per-row weight), theta_max = omega_max of level 0.
 
 Loss for probe vectors x_k (SplitMix64 uniform in (-1, 1)):
   L = (1/m) sum_k log( y_k^T K y_k / x_k^T K x_k ),  y_k = x_k - B_omega K x_k
 with B_omega the V-cycle (one pre- and one post-sweep, exact coarsest
 solve).  The gradient is obtained by reverse-mode differentiation of the
 V-cycle steps and of the network, written out by hand below.
+
+Loss of the smoothing weights (two-grid, level 0, exact coarse solve):
+  L_theta = (1/m) sum_k log( y_k^T K y_k / x_k^T K x_k ),
+  y_k = (I - M K)(I - P_bar K_c^-1 P_bar^T K)(I - M K) x_k,
+  K_c = P_bar^T K P_bar, M = diag(omega / d) (omega of the first head, held
+  fixed in this loss), with its gradient with respect to theta (hence to
+  qt, ct and the shared layers).
 """
 from __future__ import annotations
 
@@ -46,7 +57,7 @@ NFEAT = 4
 # flat parameter layout (name, shape)
 LAYOUT = [("W0", (HIDDEN, NFEAT)), ("b0", (HIDDEN,)), ("U1", (HIDDEN, HIDDEN)), ("V1", (HIDDEN, HIDDEN)),
           ("b1", (HIDDEN,)), ("U2", (HIDDEN, HIDDEN)), ("V2", (HIDDEN, HIDDEN)), ("b2", (HIDDEN,)),
-          ("q", (HIDDEN,)), ("c", (1,))]
+          ("q", (HIDDEN,)), ("c", (1,)), ("qt", (HIDDEN,)), ("ct", (1,))]
 NPARAM = sum(int(np.prod(s)) for _, s in LAYOUT)
 
 
@@ -128,7 +139,9 @@ def lanczos_bound(K, d, steps=LANCZOS_STEPS, seed=LANCZOS_SEED):
     return min(1.0, bound)
 
 
-def forward(w, x, Ap, omax=2.0):
+def forward(w, x, Ap, omax=2.0, tmax=2.0):
+    """omega (N,) of the first head and the tape; the tape also holds the
+    second head's theta = tmax sigmoid(qt . h2 + ct)."""
     p = unpack(w)
     u0 = x @ p["W0"].T + p["b0"]
     h0 = np.maximum(u0, 0.0)
@@ -140,15 +153,25 @@ def forward(w, x, Ap, omax=2.0):
     h2 = np.maximum(u2, 0.0)
     z = h2 @ p["q"] + p["c"][0]
     sg = 1.0 / (1.0 + np.exp(-z))
-    return omax * sg, dict(x=x, u0=u0, h0=h0, m1=m1, u1=u1, h1=h1, m2=m2, u2=u2, h2=h2, z=z, sg=sg)
+    zt = h2 @ p["qt"] + p["ct"][0]
+    sgt = 1.0 / (1.0 + np.exp(-zt))
+    return omax * sg, dict(x=x, u0=u0, h0=h0, m1=m1, u1=u1, h1=h1, m2=m2, u2=u2, h2=h2, z=z, sg=sg, zt=zt, sgt=sgt,
+                           theta=tmax * sgt)
 
 
-def backward(w, tape, Ap, domega, omax=2.0):
-    """Gradient of the loss w.r.t. the flat weights given d loss / d omega."""
+def backward(w, tape, Ap, domega, omax=2.0, dtheta=None, tmax=2.0):
+    """Gradient of the loss w.r.t. the flat weights given d loss / d omega
+    (and d loss / d theta of the second head, if any)."""
     p = unpack(w)
     dz = domega * omax * tape["sg"] * (1.0 - tape["sg"])
     g = {"q": tape["h2"].T @ dz, "c": np.array([dz.sum()])}
     dh2 = np.outer(dz, p["q"])
+    if dtheta is None:
+        g["qt"], g["ct"] = np.zeros(HIDDEN), np.zeros(1)
+    else:
+        dzt = dtheta * tmax * tape["sgt"] * (1.0 - tape["sgt"])
+        g["qt"], g["ct"] = tape["h2"].T @ dzt, np.array([dzt.sum()])
+        dh2 = dh2 + np.outer(dzt, p["qt"])
     du2 = dh2 * (tape["u2"] > 0)
     g["U2"] = du2.T @ tape["m2"]
     g["V2"] = du2.T @ tape["h1"]
@@ -278,3 +301,85 @@ def loss_and_grad(H, w, nprobe=4, seed=99):
     for l in range(lv.L - 1):
         grad += backward(w, outs[l][1], feats[l][1], domegas[l], lv.omax[l])
     return loss, grad, omegas
+
+
+# ----------------------------------------------- smoothing weights theta
+class TwoGrid:
+    """Level 0 of an oracle hierarchy with the pieces of the smoothed
+    prolongator: K, d, the tentative P (agg, pval), the product K P (its
+    values are what theta scales) and the cap omega_max of level 0."""
+
+    def __init__(self, H):
+        import oracle as O
+
+        self.O = O
+        rp, ci, v = H.level_csr(0)
+        n = len(rp) - 1
+        self.csr = (rp, ci, v)
+        self.K = sp.csr_matrix((v, ci, rp), shape=(n, n))
+        self.d = H.level_vectors(0)[0]
+        self.agg, self.pval = H.level_map(0)
+        self.nc = H.level_n(1)
+        self.P = sp.csr_matrix((self.pval, (np.arange(n), self.agg)), shape=(n, self.nc))
+        self.KP = (self.K @ self.P).tocsr()
+        self.omax = 2.0 / lanczos_bound(self.K, self.d, seed=LANCZOS_SEED)
+
+    def pbar(self, theta):
+        """P_bar and K_c = P_bar^T K P_bar in the oracle's own arithmetic."""
+        rp, ci, v = self.csr
+        prp, pci, pv = self.O.smooth_prolongator(rp, ci, v, self.d, theta, self.agg, self.pval, self.nc)
+        crp, cci, cv = self.O.galerkin_general(rp, ci, v, prp, pci, pv, self.nc)
+        Pb = sp.csr_matrix((pv, pci, prp), shape=(len(rp) - 1, self.nc))
+        Kc = sp.csr_matrix((cv, cci, crp), shape=(self.nc, self.nc)).toarray()
+        return Pb, Kc
+
+
+def twogrid_theta_loss(tg: TwoGrid, m, theta, X):
+    """L_theta (see the module header) for per-row smoothing weights theta
+    and smoother diagonal m = omega / d, and d L_theta / d theta.
+
+    Reverse pass for one probe x (K, M, K_c symmetric):
+      x1 = x - M K x; g = P_bar^T K x1; e = K_c^-1 g; x2 = x1 - P_bar e;
+      y = x2 - M K x2; L = log(y'Ky) - log(x'Kx)
+      ybar = 2 K y / y'Ky; x2bar = ybar - K M ybar; ebar = -P_bar^T x2bar;
+      gbar = K_c^-1 ebar;  d L / d P_bar = -a e' + b gbar' with
+      a = x2bar + K P_bar gbar, b = K x1 - K P_bar e = K x2;
+    and P_bar(i, J) = P(i, J) - (theta_i / d_i) (K P)(i, J) gives
+      d L / d theta_i = (a_i (K P e)_i - b_i (K P gbar)_i) / d_i."""
+    Pb, Kc = tg.pbar(theta)
+    L = sl.cho_factor(Kc)
+    K = tg.K
+    total = 0.0
+    dth = np.zeros(K.shape[0])
+    for x in X:
+        Kx = K @ x
+        x1 = x - m * Kx
+        Kx1 = K @ x1
+        e = sl.cho_solve(L, Pb.T @ Kx1)
+        x2 = x1 - Pb @ e
+        Kx2 = K @ x2
+        y = x2 - m * Kx2
+        Ky = K @ y
+        yKy, xKx = y @ Ky, x @ Kx
+        total += np.log(yKy) - np.log(xKx)
+        ybar = 2.0 * Ky / yKy
+        x2bar = ybar - K @ (m * ybar)
+        gbar = sl.cho_solve(L, -(Pb.T @ x2bar))
+        a = x2bar + K @ (Pb @ gbar)
+        b = Kx2
+        dth += (a * (tg.KP @ e) - b * (tg.KP @ gbar)) / tg.d
+    return total / len(X), dth / len(X)
+
+
+def theta_loss_and_grad(tg: TwoGrid, w, nprobe=4, seed=99, omega_fixed=None):
+    """L_theta of the network's two heads on level 0 (omega held fixed: the
+    first head's, or omega_fixed when given) and its gradient with respect
+    to the flat weights; returns (loss, grad, theta)."""
+    x, Ap = features(*tg.csr)
+    omega, tape = forward(w, x, Ap, tg.omax, tg.omax)
+    if omega_fixed is not None:
+        omega = omega_fixed
+    X = probes(seed, nprobe, tg.K.shape[0])
+    loss, dth = twogrid_theta_loss(tg, omega / tg.d, tape["theta"], X)
+    grad = backward(w, tape, Ap, np.zeros_like(omega), tg.omax, dth, tg.omax)
+    return loss, grad, tape["theta"]

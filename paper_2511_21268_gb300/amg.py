@@ -103,6 +103,9 @@ _SIGS = {
     "amg_mpnn_omega": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "amg_mpnn_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64,
                                           ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_mpnn_theta_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64,
+                                                ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_mpnn_theta": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "amg_mpnn_adam": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int32] + [ctypes.c_float] * 4),
     "amg_mpnn_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_uint64, ctypes.c_float, ctypes.c_void_p]),
@@ -376,7 +379,7 @@ def amg_free(h):
 
 # ------------------------------------------------------ learned damping
 AMG_MPNN_HIDDEN = 32
-AMG_MPNN_NPARAM = 4353
+AMG_MPNN_NPARAM = 4386
 
 
 def _dev_weights(w):
@@ -415,6 +418,24 @@ def amg_mpnn_loss_grad(h, w, nprobe: int, seed: int):
     _check(lib().amg_mpnn_loss_grad(h, wd.data_ptr(), nprobe, seed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(loss),
                                     g.data_ptr()), "amg_mpnn_loss_grad")
     return loss.value, g
+
+
+def amg_mpnn_theta_loss_grad(h, w, nprobe: int, seed: int):
+    """(loss, gradient) of the smoothing weights' two-grid loss."""
+    torch = _torch()
+    wd = _dev_weights(w)
+    g = torch.empty(AMG_MPNN_NPARAM, dtype=torch.float64, device="cuda")
+    loss = ctypes.c_double()
+    _check(lib().amg_mpnn_theta_loss_grad(h, wd.data_ptr(), nprobe, seed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(loss),
+                                          g.data_ptr()), "amg_mpnn_theta_loss_grad")
+    return loss.value, g
+
+
+def amg_mpnn_theta(h, n: int):
+    torch = _torch()
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    _check(lib().amg_mpnn_theta(h, out.data_ptr()), "amg_mpnn_theta")
+    return out
 
 
 def amg_mpnn_adam(h, w, grad, m, v, t: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
@@ -563,6 +584,12 @@ class Hierarchy:
     def mpnn_train(self, w, steps: int, nprobe: int = 4, seed: int = 1000, lr: float = 1e-2, others=()):
         """Train w on this hierarchy (and the hierarchies in `others`)."""
         return amg_mpnn_train([self._h] + [o._h for o in others], w, steps, nprobe, seed, lr)
+
+    def mpnn_theta_loss_grad(self, w, nprobe: int = 4, seed: int = 99):
+        return amg_mpnn_theta_loss_grad(self._h, w, nprobe, seed)
+
+    def mpnn_theta(self):
+        return amg_mpnn_theta(self._h, self.level_n(0))
 
     def mpnn_select(self, w, F, rtol: float = 1e-8, itmax: int = 10000, omega_ref: float = 1.0):
         return amg_mpnn_select(self._h, w, F, rtol, itmax, omega_ref)

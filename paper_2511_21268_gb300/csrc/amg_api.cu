@@ -486,6 +486,8 @@ int build(amg_hierarchy* h, const amg_csr* K) {
         if (h->o.smooth_levels < 0 || l < h->o.smooth_levels) {
             // smoothed prolongator: its Galerkin product replaces the tentative one
             phase(h, 10);
+            // a setup given network weights smooths level 0 with the network's theta
+            if (l == 0 && h->o.mpnn_weights) RC(mpnn_setup_theta(h));
             DevCSR Kc;
             RC(smooth_level(h, l, Kc));
             free_level_matrix(h, cur);

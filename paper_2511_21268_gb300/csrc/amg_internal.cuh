@@ -108,6 +108,7 @@ struct Level {
     // sp = P_bar (n x nc, CSR), spT = P_bar^T (nc x n, CSR, rows ascending)
     int smoothed = 0;
     DevCSR sp, spT;
+    double* kp = nullptr;  // level 0: values of K P (pattern of sp), which theta rescales into P_bar
     // V-cycle vectors (FP64 mode)
     double* f = nullptr;
     double* x = nullptr;
@@ -225,6 +226,9 @@ struct amg_hierarchy {
     // diagonals currently hold omega / d instead of 1 / d
     amg::MpnnWork* mp = nullptr;
     int damping_learned = 0;
+    // level-0 smoothing weights from the network of a setup given weights
+    // (device FP64, owned by the network buffers), NULL otherwise
+    const double* theta0 = nullptr;
     // block-diagonal batch (amg_setup_batch): systems and their row offsets
     int nsys = 0;
     std::vector<int64_t> sys_off;    // host copy [nsys + 1]
@@ -297,6 +301,7 @@ int multi_dot_stride();
 void mpnn_free(amg_hierarchy* h);
 int mpnn_setup_fork(amg_hierarchy* h);
 int mpnn_setup_join(amg_hierarchy* h);
+int mpnn_setup_theta(amg_hierarchy* h);
 // stream_kernels.cu
 int stream_prepare(amg_hierarchy* h, int* scratch2);
 cudaError_t launch_stream_resid(amg_hierarchy* h, const double* f, const float* x, float* rbuf, cudaStream_t s);
@@ -323,6 +328,9 @@ cudaError_t sell_spmv_pq(amg_hierarchy* h, const float* p32, const double* p, co
 // smooth_kernels.cu: smoothed prolongator and its Galerkin product for level
 // l (member lists and l1 diagonal present); the coarse matrix goes to Kc
 int smooth_level(amg_hierarchy* h, int l, DevCSR& Kc);
+// smooth_kernels.cu: level 0's P_bar for new per-row weights theta (device,
+// FP64) and the coarse matrix P_bar^T K P_bar rewritten in place (same pattern)
+int smooth_recompute(amg_hierarchy* h, const double* theta);
 template <typename A>
 void sp_restrict(const Level& F, const Level& C, const A* r, A* fc, A* xc, const A* invdc, const SolveState* st,
                  cudaStream_t s);

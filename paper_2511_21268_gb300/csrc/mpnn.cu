@@ -52,10 +52,10 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int H = AMG_MPNN_HIDDEN;
 static_assert(H == kWarp, "a warp per node, lane = hidden unit");
-// flat parameter layout: W0[32][4], b0, U1[32][32], V1, b1, U2, V2, b2, q, c
+// flat parameter layout: W0[32][4], b0, U1[32][32], V1, b1, U2, V2, b2, q, c, qt, ct
 constexpr int O_W0 = 0, O_B0 = O_W0 + H * 4, O_U1 = O_B0 + H, O_V1 = O_U1 + H * H, O_B1 = O_V1 + H * H,
               O_U2 = O_B1 + H, O_V2 = O_U2 + H * H, O_B2 = O_V2 + H * H, O_Q = O_B2 + H, O_C = O_Q + H,
-              O_END = O_C + 1;
+              O_QT = O_C + 1, O_CT = O_QT + H, O_END = O_CT + 1;
 static_assert(O_END == AMG_MPNN_NPARAM, "parameter layout");
 constexpr int kGradBlocks = 256;           // blocks of the weight-gradient kernels
 constexpr int kGradSlots = 2 * H * H + H;  // partial sums one block writes (largest kernel)
@@ -131,7 +131,7 @@ __global__ void k_nn_features(int n, const int64_t* __restrict__ rp, const int32
 // One layer's weights in shared memory; Ut[k][j] = U[j][k] so that lane j
 // reads consecutive words.
 struct NetSmem {
-    float W0t[4 * H], b0[H], Ut[H * H], Vt[H * H], b[H], q[H], c;
+    float W0t[4 * H], b0[H], Ut[H * H], Vt[H * H], b[H], q[H], qt[H], c, ct;
 };
 
 __device__ void load_net(const float* __restrict__ w, NetSmem& s, int layer, int bf16) {
@@ -142,13 +142,17 @@ __device__ void load_net(const float* __restrict__ w, NetSmem& s, int layer, int
         s.b0[t] = rd(O_B0 + t);
         s.b[t] = rd(oB + t);
         s.q[t] = rd(O_Q + t);
+        s.qt[t] = rd(O_QT + t);
     }
     for (int t = threadIdx.x; t < H * H; t += blockDim.x) {
         const int j = t / H, k = t % H;  // source U[j][k]
         s.Ut[k * H + j] = rd(oU + t);
         s.Vt[k * H + j] = rd(oV + t);
     }
-    if (threadIdx.x == 0) s.c = rd(O_C);
+    if (threadIdx.x == 0) {
+        s.c = rd(O_C);
+        s.ct = rd(O_CT);
+    }
     __syncthreads();
 }
 
@@ -217,12 +221,14 @@ __global__ void __launch_bounds__(kBlock) k_nn_spmm(int n, const int64_t* __rest
     }
 }
 
-// u = U m + V hp + b, h = relu(u); layer 2 also forms sigmoid(z) and omega.
+// u = U m + V hp + b, h = relu(u); layer 2 also forms sigmoid(z) and omega,
+// and (sgt non-NULL) the second head's sigmoid(zt) and theta (cap omega_max).
 __global__ void __launch_bounds__(kBlock) k_nn_dense(int n, const float* __restrict__ w, int bf16, int layer,
                                                       const float* __restrict__ m, const float* __restrict__ hp,
                                                       float* __restrict__ u, float* __restrict__ h,
                                                       float* __restrict__ sg, float* __restrict__ omega,
-                                                      const double* __restrict__ cap) {
+                                                      const double* __restrict__ cap, float* __restrict__ sgt,
+                                                      float* __restrict__ theta) {
     __shared__ NetSmem s;
     load_net(w, s, layer, bf16);
     const float omax = layer == 2 ? (float)cap[1] : 0.f;
@@ -247,6 +253,14 @@ __global__ void __launch_bounds__(kBlock) k_nn_dense(int n, const float* __restr
                 sg[i] = sgm;
                 omega[i] = omax * sgm;
             }
+            if (sgt) {
+                const float tt = warp_sumf(s.qt[lane] * hh);
+                if (lane == 0) {
+                    const float st = 1.f / (1.f + expf(-(tt + s.ct)));
+                    sgt[i] = st;
+                    theta[i] = omax * st;
+                }
+            }
         }
     }
 }
@@ -266,29 +280,43 @@ __device__ __forceinline__ void block_lane_sum(float (&red)[kWarpsPerBlock][H], 
     __syncthreads();
 }
 
-// dz = domega omega_max sg (1 - sg); partials dq[j] = sum dz h2[j] (slots
-// [0, H)), dc = sum dz (slot H); du2 = dz q [u2 > 0]
+// dz = domega omega_max sg (1 - sg) and (dtheta non-NULL) dzt = dtheta
+// omega_max sgt (1 - sgt); partials dq[j] = sum dz h2[j] (slots [0, H)),
+// dc = sum dz (slot H), dqt[j] (slots [H + 1, 2 H + 1)), dct (slot 2 H + 1);
+// du2 = (dz q + dzt qt) [u2 > 0]
 __global__ void __launch_bounds__(kBlock) k_nn_out_bwd(int n, const float* __restrict__ w,
                                                         const double* __restrict__ domega,
                                                         const float* __restrict__ sg, const float* __restrict__ h2,
                                                         const float* __restrict__ u2, float* __restrict__ du2,
-                                                        float* __restrict__ part, const double* __restrict__ cap) {
+                                                        float* __restrict__ part, const double* __restrict__ cap,
+                                                        const double* __restrict__ dtheta,
+                                                        const float* __restrict__ sgt) {
     __shared__ float red[kWarpsPerBlock][H];
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    const float q = w[O_Q + lane];
+    const float q = w[O_Q + lane], qt = w[O_QT + lane];
     const float omax = (float)cap[1];
-    float aq = 0.f, ac = 0.f;
+    float aq = 0.f, ac = 0.f, aqt = 0.f, act = 0.f;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
         const float s = sg[i];
         const float dz = (float)domega[i] * omax * s * (1.f - s);
-        aq = fmaf(dz, h2[(int64_t)i * H + lane], aq);
+        float dzt = 0.f;
+        if (dtheta) {
+            const float st = sgt[i];
+            dzt = (float)dtheta[i] * omax * st * (1.f - st);
+        }
+        const float hv = h2[(int64_t)i * H + lane];
+        aq = fmaf(dz, hv, aq);
         ac += dz;
-        du2[(int64_t)i * H + lane] = u2[(int64_t)i * H + lane] > 0.f ? dz * q : 0.f;
+        aqt = fmaf(dzt, hv, aqt);
+        act += dzt;
+        du2[(int64_t)i * H + lane] = u2[(int64_t)i * H + lane] > 0.f ? fmaf(dz, q, dzt * qt) : 0.f;
     }
     float* out = part + (int64_t)blockIdx.x * kGradSlots;
     block_lane_sum(red, aq, out);
-    block_lane_sum(red, lane == 0 ? ac : 0.f, out + H);  // slot H holds dc; H+1.. get zeros
+    block_lane_sum(red, lane == 0 ? ac : 0.f, out + H);  // slot H holds dc (H+1.. overwritten next)
+    block_lane_sum(red, aqt, out + H + 1);
+    block_lane_sum(red, lane == 0 ? act : 0.f, out + 2 * H + 1);
 }
 
 // Dense layer backward: dm = U^T du, dhp = V^T du; partials dU = du m^T
@@ -502,6 +530,51 @@ __global__ void k_v_lossgrad(int n, const double* __restrict__ Ky, const double*
     }
 }
 
+// ------------------------------ two-grid loss of the smoothing weights (FP64)
+// out = x - (omega / d) kx
+__global__ void k_tg_damp_sub(int n, const double* __restrict__ x, const float* __restrict__ om,
+                              const double* __restrict__ d, const double* __restrict__ kx, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = x[i] - ((double)om[i] / d[i]) * kx[i];
+}
+
+// out = (omega / d) a
+__global__ void k_tg_mul(int n, const float* __restrict__ om, const double* __restrict__ d,
+                         const double* __restrict__ a, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = ((double)om[i] / d[i]) * a[i];
+}
+
+// loss += (log(y.Ky) - log(x.Kx)) / m; ybar = 2 Ky / (y.Ky) / m; flags a
+// non-positive quotient
+__global__ void k_tg_lossgrad(int n, const double* __restrict__ Ky, const double* __restrict__ dots, double inv_m,
+                              double* __restrict__ ybar, double* __restrict__ loss, int* __restrict__ bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double yKy = dots[0], xKx = dots[1];
+    const bool ok = yKy > 0.0 && xKx > 0.0;
+    if (i < n) ybar[i] = ok ? 2.0 * Ky[i] / yKy * inv_m : 0.0;
+    if (i == 0) {
+        if (ok)
+            *loss += (log(yKy) - log(xKx)) * inv_m;
+        else
+            *bad = 1;
+    }
+}
+
+// dth += (a KPe - b KPg) / d
+__global__ void k_tg_dtheta(int n, const double* __restrict__ a, const double* __restrict__ kpe,
+                            const double* __restrict__ b, const double* __restrict__ kpg, const double* __restrict__ d,
+                            double* __restrict__ dth) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dth[i] += (a[i] * kpe[i] - b[i] * kpg[i]) / d[i];
+}
+
+// FP64 copy of an FP32 vector
+__global__ void k_tg_to64(int n, const float* __restrict__ in, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)in[i];
+}
+
 // out = (first ? 0 : out) + s a
 __global__ void k_scale_add(int n, const double* __restrict__ a, double s, int first, double* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -699,6 +772,8 @@ struct MpnnLevel {
     float* t[kTape] = {};
     float* sg = nullptr;  // sigmoid(z)
     float* omega = nullptr;
+    float* sgt = nullptr;    // second head: sigmoid(zt)
+    float* theta = nullptr;  // second head: prolongator-smoothing weight
     double* domega = nullptr;
     double* v[kVec] = {};
     double* ab = nullptr;   // Lanczos coefficients: alpha [0, kLzMax), beta [kLzMax, 2 kLzMax), then
@@ -720,6 +795,13 @@ struct MpnnWork {
     int* bad = nullptr;
     int* dst = nullptr;  // [4][kGradSlots] slot -> weight index maps
     float *adam_m = nullptr, *adam_v = nullptr;
+    // two-grid loss of the smoothing weights: level-0 and coarse vectors
+    static constexpr int kTgFine = 17, kTgCoarse = 4;
+    double* tgf[kTgFine] = {};
+    double* tgc[kTgCoarse] = {};
+    double* tgd = nullptr;  // dense coarse matrix for its inverse
+    int tg_alloc = 0;
+    double* theta64 = nullptr;  // level-0 theta in FP64 (setup with network weights)
     int have_omega = 0;  // omega of a network evaluation present
     int shared = 0;      // training buffers allocated
     // setup with weights: the finest level's network runs on `side` from the
@@ -790,6 +872,8 @@ int alloc_level(amg_hierarchy* h, int l) {
     for (int t = 0; t < MpnnLevel::kTape; t++) MP_ALLOC(m.t[t], sizeof(float) * H * n);
     MP_ALLOC(m.sg, sizeof(float) * n);
     MP_ALLOC(m.omega, sizeof(float) * n);
+    MP_ALLOC(m.sgt, sizeof(float) * n);
+    MP_ALLOC(m.theta, sizeof(float) * n);
     MP_ALLOC(m.domega, sizeof(double) * n);
     for (int t = 0; t < MpnnLevel::kVec; t++) MP_ALLOC(m.v[t], sizeof(double) * n);
     MP_ALLOC(m.ab, sizeof(double) * (2 * kLzMax + kLzParts));
@@ -877,8 +961,12 @@ int prepare(amg_hierarchy* h) {
     int* d_l2 = d_out + kGradSlots;
     int* d_l1 = d_l2 + kGradSlots;
     int* d_in = d_l1 + kGradSlots;
-    for (int j = 0; j < H; j++) d_out[j] = O_Q + j;
+    for (int j = 0; j < H; j++) {
+        d_out[j] = O_Q + j;
+        d_out[H + 1 + j] = O_QT + j;
+    }
     d_out[H] = O_C;
+    d_out[2 * H + 1] = O_CT;
     for (int k = 0; k < H; k++)
         for (int j = 0; j < H; j++) {
             d_l2[k * H + j] = O_U2 + j * H + k;
@@ -912,9 +1000,11 @@ void forward_level(amg_hierarchy* h, int l, const float* wd, int bf16, cudaStrea
           *h2 = m.t[7];
     k_nn_in<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, m.x, u0, h0);
     k_nn_spmm<<<AMG_GRID(g), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, m.ap, h0, nullptr, m1);
-    k_nn_dense<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, 1, m1, h0, u1, h1, nullptr, nullptr, nullptr);
+    k_nn_dense<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, 1, m1, h0, u1, h1, nullptr, nullptr, nullptr, nullptr,
+                                               nullptr);
     k_nn_spmm<<<AMG_GRID(g), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, m.ap, h1, nullptr, m2);
-    k_nn_dense<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, 2, m2, h1, u2, h2, m.sg, m.omega, m.cap);
+    k_nn_dense<<<AMG_GRID(g), kBlock, 0, s>>>(n, wd, bf16, 2, m2, h1, u2, h2, m.sg, m.omega, m.cap,
+                                               l == 0 ? m.sgt : nullptr, m.theta);
 }
 
 // omega of levels [0, nlev - 1); the coarsest level has no smoother.
@@ -924,8 +1014,9 @@ cudaError_t net_forward(amg_hierarchy* h, const float* wd, int bf16) {
     return cudaGetLastError();
 }
 
-// Network backward of level l given its domega; gradients added to gacc.
-cudaError_t net_backward(amg_hierarchy* h, const float* wd, int l) {
+// Network backward of level l given its domega (and, on level 0, dtheta of
+// the second head when non-NULL); gradients added to gacc.
+cudaError_t net_backward(amg_hierarchy* h, const float* wd, int l, const double* dtheta = nullptr) {
     MpnnWork& w = *h->mp;
     cudaStream_t s = h->s;
     Level& L = h->lev[l];
@@ -937,8 +1028,8 @@ cudaError_t net_backward(amg_hierarchy* h, const float* wd, int l) {
           *h2 = m.t[7];
     float *b0 = w.bw[0], *b1 = w.bw[1], *b2 = w.bw[2];
     const int gs = eblk(kGradSlots);
-    k_nn_out_bwd<<<AMG_GRID(gg), kBlock, 0, s>>>(n, wd, m.domega, m.sg, h2, u2, b0, w.part, m.cap);
-    k_nn_grad_sum<<<AMG_GRID(gs), kBlock, 0, s>>>(gg, w.part, H + 1, w.dst, w.gacc);
+    k_nn_out_bwd<<<AMG_GRID(gg), kBlock, 0, s>>>(n, wd, m.domega, m.sg, h2, u2, b0, w.part, m.cap, dtheta, m.sgt);
+    k_nn_grad_sum<<<AMG_GRID(gs), kBlock, 0, s>>>(gg, w.part, 2 * H + 2, w.dst, w.gacc);
     // layer 2: du2 (b0) -> dm2 (b1), V2^T du2 (b2); dh1 = A' dm2 + V2^T du2 (b0)
     k_nn_dense_bwd<<<AMG_GRID(gg), kBlock, 0, s>>>(n, wd, 2, b0, m2, h1, b1, b2, w.part);
     k_nn_grad_sum<<<AMG_GRID(gs), kBlock, 0, s>>>(gg, w.part, 2 * H * H + H, w.dst + kGradSlots, w.gacc);
@@ -1052,6 +1143,85 @@ int loss_grad_enqueue(amg_hierarchy* h, const float* wd, int nprobe, uint64_t se
     return AMG_OK;
 }
 
+template <typename T>
+int read_host(amg_hierarchy* h, const T* dptr, T* out);
+
+// Loss of the smoothing weights (two-grid, see the file header of the
+// oracle's counterpart) for the network's second head on a two-level
+// hierarchy whose level-0 prolongator is smoothed; the network's theta is
+// installed into the hierarchy (P_bar, the coarse matrix and its inverse
+// are rewritten).  Gradient left in gacc (omega held fixed), loss in loss.
+int theta_loss_grad_enqueue(amg_hierarchy* h, const float* wd, int nprobe, uint64_t seed) {
+    MpnnWork& w = *h->mp;
+    cudaStream_t s = h->s;
+    Level& L0 = h->lev[0];
+    Level& L1 = h->lev[1];
+    MpnnLevel& m0 = w.lev[0];
+    const int n = L0.A.n, nc = L1.A.n;
+    const int gr = grid_rows(h, n), ge = eblk(n), gc = eblk(nc);
+    if (!w.tg_alloc) {
+        for (int k = 0; k < MpnnWork::kTgFine; k++) MP_ALLOC(w.tgf[k], sizeof(double) * n);
+        for (int k = 0; k < MpnnWork::kTgCoarse; k++) MP_ALLOC(w.tgc[k], sizeof(double) * nc);
+        MP_ALLOC(w.tgd, sizeof(double) * (size_t)nc * nc);
+        w.tg_alloc = 1;
+    }
+    double *Kx = w.tgf[0], *x1 = w.tgf[1], *Kx1 = w.tgf[2], *x2 = w.tgf[3], *Kx2 = w.tgf[4], *y = w.tgf[5],
+           *Ky = w.tgf[6], *ybar = w.tgf[7], *t = w.tgf[8], *x2bar = w.tgf[9], *pbg = w.tgf[10], *a = w.tgf[11],
+           *kpe = w.tgf[12], *kpg = w.tgf[13], *dth = w.tgf[14], *th64 = w.tgf[15];
+    double *g = w.tgc[0], *e = w.tgc[1], *ebar = w.tgc[2], *gbar = w.tgc[3];
+    MP_CK(cudaMemsetAsync(w.loss, 0, sizeof(double), s));
+    MP_CK(cudaMemsetAsync(w.bad, 0, sizeof(int), s));
+    MP_CK(cudaMemsetAsync(w.gacc, 0, sizeof(double) * AMG_MPNN_NPARAM, s));
+    MP_CK(cudaMemsetAsync(m0.domega, 0, sizeof(double) * n, s));
+    MP_CK(cudaMemsetAsync(dth, 0, sizeof(double) * n, s));
+    forward_level(h, 0, wd, 0, s);
+    k_tg_to64<<<AMG_GRID(ge), kBlock, 0, s>>>(n, m0.theta, th64);
+    MP_CK(cudaGetLastError());
+    MP_TRY(smooth_recompute(h, th64));
+    MP_CK(launch_dense_from_csr(L1.A, w.tgd, s));
+    MP_CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    MP_CK(launch_dense_spd_inverse(nc, w.tgd, h->Ainv, h->flag, s));
+    int notspd = 0;
+    MP_TRY(read_host(h, h->flag, &notspd));
+    if (notspd) return AMG_ERR_BREAKDOWN;
+    const DevCSR& K = L0.A;
+    const DevCSR& P = L0.sp;
+    const DevCSR& PT = L0.spT;
+    const float* om = m0.omega;
+    const double inv_m = 1.0 / nprobe;
+    auto spmv = [&](const DevCSR& M, const double* xin, const double* base, double sc, double* out) {
+        k_v_spmv<<<AMG_GRID(grid_rows(h, M.n)), kBlock, 0, s>>>(M.n, M.rowptr, M.col, M.val, xin, base, sc, out);
+    };
+    for (int k = 0; k < nprobe; k++) {
+        k_v_probe<<<AMG_GRID(ge), kBlock, 0, s>>>(n, seed, k, w.px);
+        spmv(K, w.px, nullptr, 1.0, Kx);
+        k_tg_damp_sub<<<AMG_GRID(ge), kBlock, 0, s>>>(n, w.px, om, L0.dl1, Kx, x1);
+        spmv(K, x1, nullptr, 1.0, Kx1);
+        spmv(PT, Kx1, nullptr, 1.0, g);
+        k_v_dense<<<AMG_GRID(eblk((int64_t)nc * 32)), kBlock, 0, s>>>(nc, h->Ainv, g, e);
+        spmv(P, e, x1, -1.0, x2);
+        spmv(K, x2, nullptr, 1.0, Kx2);
+        k_tg_damp_sub<<<AMG_GRID(ge), kBlock, 0, s>>>(n, x2, om, L0.dl1, Kx2, y);
+        spmv(K, y, nullptr, 1.0, Ky);
+        k_v_dot2<<<AMG_GRID(1), 1024, 0, s>>>(n, y, Ky, w.px, Kx, w.dots);
+        k_tg_lossgrad<<<AMG_GRID(ge), kBlock, 0, s>>>(n, Ky, w.dots, inv_m, ybar, w.loss, w.bad);
+        k_tg_mul<<<AMG_GRID(ge), kBlock, 0, s>>>(n, om, L0.dl1, ybar, t);
+        spmv(K, t, ybar, -1.0, x2bar);
+        spmv(PT, x2bar, nullptr, -1.0, ebar);
+        k_v_dense<<<AMG_GRID(eblk((int64_t)nc * 32)), kBlock, 0, s>>>(nc, h->Ainv, ebar, gbar);
+        spmv(P, gbar, nullptr, 1.0, pbg);
+        spmv(K, pbg, x2bar, 1.0, a);
+        // K P e and K P gbar with the unsmoothed product (pattern of P_bar)
+        k_v_spmv<<<AMG_GRID(grid_rows(h, n)), kBlock, 0, s>>>(n, P.rowptr, P.col, L0.kp, e, nullptr, 1.0, kpe);
+        k_v_spmv<<<AMG_GRID(grid_rows(h, n)), kBlock, 0, s>>>(n, P.rowptr, P.col, L0.kp, gbar, nullptr, 1.0, kpg);
+        k_tg_dtheta<<<AMG_GRID(ge), kBlock, 0, s>>>(n, a, kpe, Kx2, kpg, L0.dl1, dth);
+    }
+    (void)gc;
+    MP_CK(net_backward(h, wd, 0, dth));
+    MP_CK(cudaGetLastError());
+    return AMG_OK;
+}
+
 // Install the damping of the last network evaluation (learned) or the
 // constant damping omc (omc = 1: the plain l1-Jacobi diagonal) on every
 // level that has a smoother.
@@ -1094,6 +1264,21 @@ int mpnn_setup_fork(amg_hierarchy* h) {
     MP_CK(cudaEventRecord(w.ev_done, w.side));
     w.forked = 1;
     MP_CK(cudaGetLastError());
+    return AMG_OK;
+}
+
+// Setup with network weights and a smoothed level 0: the finest level's
+// second head gives the smoothing weights; wait for its evaluation on the
+// second stream and hand them to the smoothing step in FP64.
+int mpnn_setup_theta(amg_hierarchy* h) {
+    if (!h->mp || !h->mp->forked) return AMG_OK;
+    MpnnWork& w = *h->mp;
+    const int n = h->lev[0].A.n;
+    MP_CK(cudaStreamWaitEvent(h->s, w.ev_done, 0));
+    if (!w.theta64) MP_ALLOC(w.theta64, sizeof(double) * n);
+    k_tg_to64<<<AMG_GRID(eblk(n)), kBlock, 0, h->s>>>(n, w.lev[0].theta, w.theta64);
+    MP_CK(cudaGetLastError());
+    h->theta0 = w.theta64;
     return AMG_OK;
 }
 
@@ -1169,6 +1354,12 @@ static bool any_smoothed(const amg_hierarchy* h) {
     return false;
 }
 
+// A hierarchy for the smoothing weights' two-grid loss: two levels, level 0
+// smoothed (with its K P kept).
+static bool twogrid_theta(const amg_hierarchy* h) {
+    return h->nlev == 2 && h->lev[0].smoothed && h->lev[0].kp && h->nsys == 0;
+}
+
 int amg_mpnn_loss_grad(amg_hierarchy* h, const float* w, int32_t nprobe, uint64_t seed, double* loss,
                        double* grad) {
     if (!h || !w || !loss || !grad || nprobe < 1 || h->nlev < 2 || any_smoothed(h)) return AMG_ERR_ARG;
@@ -1187,6 +1378,35 @@ int amg_mpnn_loss_grad(amg_hierarchy* h, const float* w, int32_t nprobe, uint64_
     return isfinite(lh) ? AMG_OK : AMG_ERR_NAN;
 }
 
+int amg_mpnn_theta_loss_grad(amg_hierarchy* h, const float* w, int32_t nprobe, uint64_t seed, double* loss,
+                             double* grad) {
+    if (!h || !w || !loss || !grad || nprobe < 1 || !twogrid_theta(h)) return AMG_ERR_ARG;
+    MP_RC(join_caller_stream(h));
+    MP_RC(prepare(h));
+    MP_RC(theta_loss_grad_enqueue(h, w, nprobe, seed));
+    MpnnWork& mw = *h->mp;
+    mw.have_omega = 1;
+    MP_RC(status_of(
+        cudaMemcpyAsync(grad, mw.gacc, sizeof(double) * AMG_MPNN_NPARAM, cudaMemcpyDeviceToDevice, h->s)));
+    double lh = 0.0;
+    int bad = 0;
+    MP_RC(read_host(h, mw.loss, &lh));
+    MP_RC(read_host(h, mw.bad, &bad));
+    *loss = lh;
+    if (bad) return AMG_ERR_BREAKDOWN;
+    return isfinite(lh) ? AMG_OK : AMG_ERR_NAN;
+}
+
+int amg_mpnn_theta(amg_hierarchy* h, float* theta) {
+    if (!h || !theta || h->nlev < 2) return AMG_ERR_ARG;
+    if (!h->mp || !h->mp->have_omega) return AMG_ERR_ARG;
+    MP_RC(join_caller_stream(h));
+    if (h->mp->forked) MP_RC(status_of(cudaStreamWaitEvent(h->s, h->mp->ev_done, 0)));
+    MP_RC(status_of(cudaMemcpyAsync(theta, h->mp->lev[0].theta, sizeof(float) * h->lev[0].A.n,
+                                    cudaMemcpyDeviceToDevice, h->s)));
+    return sync_status(h);
+}
+
 int amg_mpnn_adam(amg_hierarchy* h, float* w, const double* grad, float* m, float* v, int32_t t, float lr,
                   float beta1, float beta2, float eps) {
     if (!h || !w || !grad || !m || !v || t < 1 || !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) ||
@@ -1203,7 +1423,7 @@ int amg_mpnn_train(amg_hierarchy* const* hs, int32_t count, float* w, int32_t st
                    float lr, double* loss_hist) {
     if (!hs || count < 1 || count > 64 || !w || steps < 0 || nprobe < 1 || !(lr > 0.f)) return AMG_ERR_ARG;
     for (int k = 0; k < count; k++)
-        if (!hs[k] || hs[k]->nlev < 2 || any_smoothed(hs[k])) return AMG_ERR_ARG;
+        if (!hs[k] || hs[k]->nlev < 2 || (any_smoothed(hs[k]) && !twogrid_theta(hs[k]))) return AMG_ERR_ARG;
     for (int k = 0; k < count; k++) {
         MP_RC(join_caller_stream(hs[k]));
         MP_RC(prepare(hs[k]));
@@ -1219,7 +1439,10 @@ int amg_mpnn_train(amg_hierarchy* const* hs, int32_t count, float* w, int32_t st
         // every hierarchy's loss and gradient with the same weights (its own
         // stream, waited for on the host before the weights change)
         for (int k = 0; k < count; k++) {
-            MP_RC(loss_grad_enqueue(hs[k], w, nprobe, seed + (uint64_t)t));
+            if (twogrid_theta(hs[k]))
+                MP_RC(theta_loss_grad_enqueue(hs[k], w, nprobe, seed + (uint64_t)t));
+            else
+                MP_RC(loss_grad_enqueue(hs[k], w, nprobe, seed + (uint64_t)t));
             int bad = 0;
             double lk = 0.0;
             MP_RC(read_host(hs[k], hs[k]->mp->bad, &bad));

@@ -427,7 +427,13 @@ int smooth_level(amg_hierarchy* h, int l, DevCSR& Kc_out) {
     // K P, then P_bar in place
     int rc = spgemm(h, n, K.rowptr, K.col, K.val, prp, F.agg, F.pval, SP_VALUES, F.sp, dflag, scr);
     if (rc != AMG_OK) return rc;
-    const double* theta = (l == 0) ? h->o.smooth_theta : nullptr;
+    if (l == 0) {  // K P of level 0 is kept: theta rescales it (training of the smoothing weights)
+        if (dev_alloc((void**)&F.kp, sizeof(double) * ((size_t)F.sp.nnz + 8), s) != cudaSuccess) return AMG_ERR_NOMEM;
+        h->allocs.push_back(F.kp);
+        if (cudaMemcpyAsync(F.kp, F.sp.val, sizeof(double) * F.sp.nnz, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return AMG_ERR_CUDA;
+    }
+    const double* theta = (l == 0) ? (h->theta0 ? h->theta0 : h->o.smooth_theta) : nullptr;
     k_sp_pbar<<<AMG_GRID(sp_blocks(n, kWarpsPerBlock)), kBlock, 0, s>>>(n, F.sp.rowptr, F.sp.col, F.sp.val, F.agg,
                                                                         F.pval, theta, h->o.smooth_omega, F.dl1);
     // P_bar^T: the pattern of P^T K (the members' rows of K), values by search
@@ -456,6 +462,48 @@ int smooth_level(amg_hierarchy* h, int l, DevCSR& Kc_out) {
     Kc_out = Kc;
     F.smoothed = 1;
     return AMG_OK;
+}
+
+int smooth_recompute(amg_hierarchy* h, const double* theta) {
+    cudaStream_t s = h->s;
+    Level& F = h->lev[0];
+    Level& C = h->lev[1];
+    if (!F.smoothed || !F.kp) return AMG_ERR_ARG;
+    const DevCSR& K = F.A;
+    const int n = K.n, nc = F.nc;
+    int* dflag = h->flag + 8;
+    if (cudaMemsetAsync(h->flag + 10, 0, sizeof(int), s) != cudaSuccess) return AMG_ERR_CUDA;
+    // P_bar values from K P and theta, and its transpose's values
+    if (cudaMemcpyAsync(F.sp.val, F.kp, sizeof(double) * F.sp.nnz, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return AMG_ERR_CUDA;
+    k_sp_pbar<<<AMG_GRID(sp_blocks(n, kWarpsPerBlock)), kBlock, 0, s>>>(n, F.sp.rowptr, F.sp.col, F.sp.val, F.agg,
+                                                                        F.pval, theta, h->o.smooth_omega, F.dl1);
+    k_sp_tvals<<<AMG_GRID(sp_blocks(nc, kWarpsPerBlock)), kBlock, 0, s>>>(nc, F.spT.rowptr, F.spT.col, F.spT.val,
+                                                                         F.sp.rowptr, F.sp.col, F.sp.val, dflag + 2);
+    int64_t* scr = nullptr;
+    if (dev_alloc((void**)&scr, sizeof(int64_t) * (scan64_scratch(std::max(n, nc)) + 1), s) != cudaSuccess)
+        return AMG_ERR_NOMEM;
+    DevCSR T, Kc;
+    int rc = spgemm(h, n, K.rowptr, K.col, K.val, F.sp.rowptr, F.sp.col, F.sp.val, SP_VALUES, T, dflag, scr);
+    if (rc == AMG_OK)
+        rc = spgemm(h, nc, F.spT.rowptr, F.spT.col, F.spT.val, T.rowptr, T.col, T.val, SP_UPPER, Kc, dflag, scr);
+    cudaFreeAsync(scr, s);
+    drop(h, T.rowptr);
+    drop(h, T.col);
+    drop(h, T.val);
+    if (rc == AMG_OK && (Kc.nnz != C.A.nnz || Kc.n != C.A.n)) rc = AMG_ERR_CUDA;  // same structural pattern
+    if (rc == AMG_OK && launch_galerkin_mirror(Kc, h->flag + 3, s) != cudaSuccess) rc = AMG_ERR_CUDA;
+    if (rc == AMG_OK &&
+        cudaMemcpyAsync(C.A.val, Kc.val, sizeof(double) * Kc.nnz, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        rc = AMG_ERR_CUDA;
+    drop(h, Kc.rowptr);
+    drop(h, Kc.col);
+    drop(h, Kc.val);
+    if (rc != AMG_OK) return rc;
+    if (cudaMemcpyAsync(h->flag_host, h->flag + 10, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return AMG_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return AMG_ERR_CUDA;
+    return h->flag_host[0] ? AMG_ERR_CUDA : AMG_OK;
 }
 
 template <typename A>

@@ -268,7 +268,8 @@ def annulus_volume() -> float:
 # Block layout of the learned-damping network's flat weight vector (hidden
 # width 32, 4 node features): (name, shape) in storage order.
 MPNN_LAYOUT = [("W0", (32, 4)), ("b0", (32,)), ("U1", (32, 32)), ("V1", (32, 32)), ("b1", (32,)),
-               ("U2", (32, 32)), ("V2", (32, 32)), ("b2", (32,)), ("q", (32,)), ("c", (1,))]
+               ("U2", (32, 32)), ("V2", (32, 32)), ("b2", (32,)), ("q", (32,)), ("c", (1,)),
+               ("qt", (32,)), ("ct", (1,))]
 MPNN_NPARAM = sum(int(np.prod(s)) for _, s in MPNN_LAYOUT)
 
 
@@ -276,7 +277,9 @@ def mpnn_init_weights(seed: int = 1) -> np.ndarray:
     """Seeded initial weights (FP64): entry k of the flat vector is
     (2 U_k - 1) sqrt(3 / fan_in) with U_k draw k of SplitMix64(seed), fan_in
     the block's column count (32 for vectors); biases and c are zero and
-    the output weights q are scaled by 0.1, so omega starts near 1."""
+    the output weights q and qt are scaled by 0.1, so omega starts near half
+    its cap; ct = ln 2, so that the prolongator-smoothing weight theta
+    starts near two thirds of its cap."""
     u = rng_u01(seed, MPNN_NPARAM) * 2.0 - 1.0
     out, o = [], 0
     for name, shape in MPNN_LAYOUT:
@@ -285,7 +288,9 @@ def mpnn_init_weights(seed: int = 1) -> np.ndarray:
         blk = u[o:o + k] * np.sqrt(3.0 / fan)
         if name in ("b0", "b1", "b2", "c"):
             blk = np.zeros(k)
-        elif name == "q":
+        elif name == "ct":
+            blk = np.full(k, np.log(2.0))
+        elif name in ("q", "qt"):
             blk = blk * 0.1
         out.append(blk)
         o += k

@@ -28,7 +28,7 @@ def unit_omega_weights():
 
 
 def test_nparam_and_layout():
-    assert M.NPARAM == 4353
+    assert M.NPARAM == 4386
     w = M.init_weights(2)
     assert np.array_equal(M.pack(M.unpack(w)), w)
 
@@ -180,3 +180,68 @@ def test_capped_output_gradient_finite_differences(small):
     Lm, _, _ = M.loss_and_grad(lv, w - h * v, nprobe=2, seed=13)
     fd = (Lp - Lm) / (2 * h)
     assert abs(fd - g @ v) <= 1e-5 * max(abs(fd), 1e-8)
+
+
+# --------------------------------------------- prolongator smoothing theta ----
+@pytest.fixture(scope="module")
+def twogrid():
+    prob = I.poisson_box(2, 12, 3)
+    H = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=20)
+    return prob, M.TwoGrid(H)
+
+
+def test_twogrid_theta_gradient_finite_differences(twogrid):
+    """d L_theta / d theta against central differences of the per-row
+    smoothing weights (the two-grid loss rebuilds P_bar and K_c)."""
+    prob, tg = twogrid
+    rng = np.random.default_rng(21)
+    theta = rng.uniform(0.4, 1.6, prob.n)
+    m = rng.uniform(0.8, 2.0, prob.n) / tg.d
+    X = M.probes(5, 2, prob.n)
+    L0, g = M.twogrid_theta_loss(tg, m, theta, X)
+    v = rng.standard_normal(prob.n)
+    h = 1e-6
+    Lp, _ = M.twogrid_theta_loss(tg, m, theta + h * v, X)
+    Lm, _ = M.twogrid_theta_loss(tg, m, theta - h * v, X)
+    fd = (Lp - Lm) / (2 * h)
+    assert abs(fd - g @ v) <= 1e-6 * abs(fd)
+    assert L0 < 0
+
+
+def test_twogrid_theta_zero_is_the_tentative_two_grid(twogrid):
+    """theta = 0 gives the two-grid operator with the tentative P: the loss
+    equals the textbook E = (I - MK)(I - P K_c^-1 P^T K)(I - MK) applied
+    densely."""
+    prob, tg = twogrid
+    m = np.full(prob.n, 1.0) / tg.d
+    X = M.probes(6, 2, prob.n)
+    L0, _ = M.twogrid_theta_loss(tg, m, np.zeros(prob.n), X)
+    K = tg.K.toarray()
+    P = tg.P.toarray()
+    S = np.eye(prob.n) - m[:, None] * K
+    E = S @ (np.eye(prob.n) - P @ np.linalg.solve(P.T @ K @ P, P.T @ K)) @ S
+    ref = np.mean([np.log((E @ x) @ K @ (E @ x)) - np.log(x @ K @ x) for x in X])
+    assert abs(L0 - ref) <= 1e-12 * abs(ref)
+
+
+def test_theta_head_gradient_finite_differences(twogrid):
+    """The whole chain: network (second head) -> theta -> P_bar, K_c ->
+    two-grid loss, against central differences of the weights."""
+    prob, tg = twogrid
+    w = M.init_weights(8)
+    dd = M.unpack(w)
+    dd["qt"] = dd["qt"] * 10
+    dd["b2"] = np.full(M.HIDDEN, 0.05)
+    w = M.pack(dd)
+    L0, g, theta = M.theta_loss_and_grad(tg, w, nprobe=2, seed=3)
+    assert theta.std() > 1e-3 and 0 < theta.min() and theta.max() < tg.omax
+    assert np.all(M.unpack(g)["q"] == 0) and M.unpack(g)["c"][0] == 0  # omega is held fixed
+    om0, _ = M.forward(w, *M.features(*tg.csr), tg.omax)
+    rng = np.random.default_rng(9)
+    for _ in range(2):
+        v = rng.standard_normal(M.NPARAM)
+        h = 1e-6
+        Lp, _, _ = M.theta_loss_and_grad(tg, w + h * v, nprobe=2, seed=3, omega_fixed=om0)
+        Lm, _, _ = M.theta_loss_and_grad(tg, w - h * v, nprobe=2, seed=3, omega_fixed=om0)
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - g @ v) <= 1e-5 * max(abs(fd), 1e-8), (fd, g @ v)

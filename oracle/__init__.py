@@ -47,7 +47,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("match_passes", ctypes.c_int),
                 ("coarse_max", ctypes.c_int), ("max_levels", ctypes.c_int), ("testvec_sweeps", ctypes.c_int),
                 ("testvec_kind", ctypes.c_int), ("seed", ctypes.c_uint64), ("stag", ctypes.c_double),
-                ("dense_max", ctypes.c_int), ("smooth_levels", ctypes.c_int), ("smooth_omega", ctypes.c_double)]
+                ("dense_max", ctypes.c_int), ("smooth_levels", ctypes.c_int), ("smooth_omega", ctypes.c_double),
+                ("cheb_degree", ctypes.c_int)]
 
 
 _lib = None
@@ -71,6 +72,7 @@ def lib():
         L.orc_smooth_prolongator.restype = i32
         L.orc_galerkin_general.argtypes = [i64, P, P, P, P, P, P, i64, P, P, P]
         L.orc_galerkin_general.restype = i32
+        L.orc_cheb4_smooth.argtypes = [i64, P, P, P, P, P, P, P, P, P, i32, i32]
         L.orc_free.argtypes = [P]
         L.orc_num_levels.argtypes = [P]
         L.orc_num_levels.restype = i32
@@ -232,6 +234,21 @@ def galerkin_general(rowptr, col, val, prp, pci, pv, nc):
     if rc != 0:
         raise RuntimeError(ERRORS.get(rc, rc))
     return _take_csr(nc, orp, oci, ov)
+
+
+def cheb4_smooth(rowptr, col, val, dl1, f, x0=None, degree=4):
+    """degree steps of the 4th-kind Chebyshev acceleration of l1-Jacobi on
+    K x = f from x0 (None: from zero); returns (x, r), r the residual of the
+    recurrence when starting from zero."""
+    rp, ci, v = _csr(rowptr, col, val)
+    n = len(rp) - 1
+    d = np.ascontiguousarray(dl1, np.float64)
+    f = np.ascontiguousarray(f, np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, np.float64)
+    r, w1, w2 = np.empty(n), np.empty(n), np.empty(n)
+    lib().orc_cheb4_smooth(n, _p(rp), _p(ci), _p(v), _p(d), _p(f), _p(x), _p(r), _p(w1), _p(w2), int(degree),
+                           int(x0 is None))
+    return x, r
 
 
 def _take_csr(n, orp, oci, ov):

@@ -69,6 +69,20 @@
  *     test vector stays w_c = P_tent^T w from the matching passes.
  *   - V-cycle with nu1 pre- and nu2 post-sweeps of l1-Jacobi from x = 0;
  *     restriction f_c = P^T r, prolongation x += P e (P_bar where smoothed).
+ *   - Chebyshev acceleration of l1-Jacobi (option cheb_degree = k >= 1,
+ *     Sec. 3.2 and Sec. 5: polynomial smoothers of the 4th kind), taking
+ *     rho(D^-1 K) <= 1 from the l1 diagonal instead of a spectral estimate:
+ *       r_0 = f - K x_0, d_0 = (4/3) D^-1 r_0, x_1 = x_0 + d_0, and for
+ *       i = 1 .. k-1:  r_i = r_{i-1} - K d_{i-1},
+ *       d_i = (2i-1)/(2i+3) d_{i-1} + (8i+4)/(2i+3) D^-1 r_i,
+ *       x_{i+1} = x_i + d_i.
+ *     Its error polynomial is p_k(l) = (-1)^k T_{2k+1}(sqrt l) /
+ *     ((2k+1) sqrt l), l in the spectrum of D^-1 K, the degree-k polynomial
+ *     with p(0) = 1 of least max |sqrt(l) p(l)| on [0, 1].  Pre-smoothing
+ *     starts from x_0 = 0 (r_0 = f) and hands r_k = r_{k-1} - K d_{k-1} to
+ *     the restriction; post-smoothing starts from the prolongated x.  The
+ *     paper's "optimized" variant scales the steps by tabulated weights
+ *     that are not used here.
  *   - PCG stops when ||r_k||_2 <= rtol ||F||_2 on the recursive residual.
  *
  * Threads: the solve phase (V-cycle and CG) may run its row loops -- each
@@ -121,6 +135,7 @@ typedef struct {
     int dense_max;    /* largest coarsest level factorised densely */
     int smooth_levels;   /* smoothed prolongator on the first levels (-1 = all, 0 = none) */
     double smooth_omega; /* theta of the smoothed levels (4/3) */
+    int cheb_degree;     /* 0: nu_pre / nu_post l1-Jacobi sweeps; k >= 1: 4th-kind Chebyshev of degree k */
 } orc_opts;
 
 typedef struct {
@@ -643,6 +658,7 @@ void orc_opts_default(orc_opts* o) {
     o->dense_max = 4096;
     o->smooth_levels = 0;
     o->smooth_omega = 4.0 / 3.0;
+    o->cheb_degree = 0;
 }
 
 static void level_free(orc_level* L) {
@@ -803,6 +819,37 @@ orc_hier* orc_setup_ex(int64_t n, const int64_t* rp, const int32_t* ci, const do
     return h;
 }
 
+/* ------------------------------------------------ Chebyshev smoother ---- */
+/* k steps of the 4th-kind Chebyshev acceleration of l1-Jacobi (see the top
+ * of the file) on K x = f.  zero_start: x_0 = 0 (x is overwritten) and on
+ * return r holds r_k = r_{k-1} - K d_{k-1} (= f - K x_k); otherwise x holds
+ * x_0 and r is workspace.  d, t: workspace of n entries. */
+void orc_cheb4_smooth(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* dl1,
+                      const double* f, double* x, double* r, double* d, double* t, int degree, int zero_start) {
+    if (zero_start) {
+        for (int64_t i = 0; i < n; i++) {
+            x[i] = 0.0;
+            r[i] = f[i];
+        }
+    } else {
+        residual(rp, ci, v, n, f, x, r);
+    }
+    for (int64_t i = 0; i < n; i++) d[i] = (4.0 / 3.0) * (r[i] / dl1[i]);
+    for (int64_t i = 0; i < n; i++) x[i] = x[i] + d[i];
+    for (int s = 1; s < degree; s++) {
+        const double a = (double)(2 * s - 1) / (double)(2 * s + 3);
+        const double b = (double)(8 * s + 4) / (double)(2 * s + 3);
+        orc_spmv(n, rp, ci, v, d, t);
+        for (int64_t i = 0; i < n; i++) r[i] = r[i] - t[i];
+        for (int64_t i = 0; i < n; i++) d[i] = a * d[i] + b * (r[i] / dl1[i]);
+        for (int64_t i = 0; i < n; i++) x[i] = x[i] + d[i];
+    }
+    if (zero_start) { /* the residual for the restriction */
+        orc_spmv(n, rp, ci, v, d, t);
+        for (int64_t i = 0; i < n; i++) r[i] = r[i] - t[i];
+    }
+}
+
 /* ------------------------------------------------------------- V-cycle ---- */
 /* Two-level correction applied recursively (Sec. 3, steps 1-5), l1-Jacobi
  * smoothing from x = 0, exact coarsest solve. */
@@ -814,12 +861,19 @@ static void vcycle(const orc_hier* h, int l, const double* f, double* x) {
         return;
     }
     double* r = (double*)malloc(sizeof(double) * n);
-    for (int64_t i = 0; i < n; i++) x[i] = 0.0;
-    for (int s = 0; s < h->o.nu_pre; s++) {
+    const int cheb = h->o.cheb_degree;
+    double* d = cheb > 0 ? (double*)malloc(sizeof(double) * n) : NULL;
+    double* t = cheb > 0 ? (double*)malloc(sizeof(double) * n) : NULL;
+    if (cheb > 0) {
+        orc_cheb4_smooth(n, L->rowptr, L->col, L->val, L->dl1, f, x, r, d, t, cheb, 1);
+    } else {
+        for (int64_t i = 0; i < n; i++) x[i] = 0.0;
+        for (int s = 0; s < h->o.nu_pre; s++) {
+            residual(L->rowptr, L->col, L->val, n, f, x, r);
+            for (int64_t i = 0; i < n; i++) x[i] = x[i] + r[i] / L->dl1[i];
+        }
         residual(L->rowptr, L->col, L->val, n, f, x, r);
-        for (int64_t i = 0; i < n; i++) x[i] = x[i] + r[i] / L->dl1[i];
     }
-    residual(L->rowptr, L->col, L->val, n, f, x, r);
     const int64_t nc = h->lev[l + 1].n;
     double* fc = (double*)malloc(sizeof(double) * nc);
     double* ec = (double*)malloc(sizeof(double) * nc);
@@ -840,10 +894,16 @@ static void vcycle(const orc_hier* h, int l, const double* f, double* x) {
     } else {
         for (int64_t i = 0; i < n; i++) x[i] = x[i] + L->pval[i] * ec[L->agg[i]];
     }
-    for (int s = 0; s < h->o.nu_post; s++) {
-        residual(L->rowptr, L->col, L->val, n, f, x, r);
-        for (int64_t i = 0; i < n; i++) x[i] = x[i] + r[i] / L->dl1[i];
+    if (cheb > 0) {
+        orc_cheb4_smooth(n, L->rowptr, L->col, L->val, L->dl1, f, x, r, d, t, cheb, 0);
+    } else {
+        for (int s = 0; s < h->o.nu_post; s++) {
+            residual(L->rowptr, L->col, L->val, n, f, x, r);
+            for (int64_t i = 0; i < n; i++) x[i] = x[i] + r[i] / L->dl1[i];
+        }
     }
+    free(d);
+    free(t);
     free(r);
     free(fc);
     free(ec);

@@ -115,6 +115,13 @@ typedef struct {
                                     with rho <= 1 from the l1 diagonal (1.3333333333333333) */
     const double* smooth_theta;  /* NULL, or a per-row theta for level 0 (DEVICE pointer, n doubles,
                                     read during amg_setup only) (NULL) */
+    int32_t cheb_degree;         /* 0: nu_pre / nu_post l1-Jacobi sweeps; k >= 1: the 4th-kind Chebyshev
+                                    acceleration of l1-Jacobi of degree k before and after the coarse
+                                    correction on every level (Sec. 3.2 / Sec. 5; rho(D^-1 K) <= 1 from
+                                    the l1 diagonal, no spectral estimate; d[0] = (4/3) D^-1 r[0],
+                                    d[i] = (2i-1)/(2i+3) d[i-1] + (8i+4)/(2i+3) D^-1 r[i]); matrix passes
+                                    on CSR row groups; needs amg_pcg_solve / amg_vcycle_apply and no
+                                    damping network (0) */
 } amg_opts;
 
 #define AMG_MAX_LEVELS 32

@@ -536,11 +536,15 @@ int build(amg_hierarchy* h, const amg_csr* K) {
             // to 16-byte boundaries
             RC(dalloc(h, &F.x32, (size_t)n + 4));
             RC(dalloc(h, &F.t32, (size_t)n + 4));
+            if (h->o.cheb_degree > 0)
+                for (int c = 0; c < 2; c++) RC(dalloc(h, reinterpret_cast<float**>(&F.cd[c]), (size_t)n + 4));
         } else {
             if (l > 0) RC(dalloc(h, &F.f, n));
             // + 4: the FP64 sliced passes copy vector windows in 4-entry groups
             RC(dalloc(h, &F.x, (size_t)n + 4));
             RC(dalloc(h, &F.t, (size_t)n + 4));
+            if (h->o.cheb_degree > 0)
+                for (int c = 0; c < 2; c++) RC(dalloc(h, reinterpret_cast<double**>(&F.cd[c]), (size_t)n + 4));
         }
     }
     if (h->mixed) RC(dalloc(h, &h->p32, (size_t)n0 + 4));
@@ -725,6 +729,8 @@ int check_opts(const amg_opts& o) {
     if (o.matrix_format < 0 || o.matrix_format > 2) return AMG_ERR_ARG;
     if (o.mpnn_bf16 < 0 || o.mpnn_bf16 > 1) return AMG_ERR_ARG;
     if (o.smooth_levels < -1 || !(o.smooth_omega >= 0.0) || !std::isfinite(o.smooth_omega)) return AMG_ERR_ARG;
+    if (o.cheb_degree < 0 || o.cheb_degree > 64) return AMG_ERR_ARG;
+    if (o.cheb_degree > 0 && o.mpnn_weights) return AMG_ERR_ARG;  // the network damps l1-Jacobi sweeps
     return AMG_OK;
 }
 
@@ -755,6 +761,7 @@ int amg_opts_default(amg_opts* o) {
     o->smooth_levels = 0;
     o->smooth_omega = 4.0 / 3.0;
     o->smooth_theta = nullptr;
+    o->cheb_degree = 0;
     return AMG_OK;
 }
 
@@ -1135,8 +1142,10 @@ static int run_multi(amg_hierarchy* h, int32_t* iters, double* relres, int32_t* 
 
 static int check_multi_opts(const amg_hierarchy* h) {
     // the multi-system V-cycle prolongates with the tentative P's member lists
+    // and smooths with one l1-Jacobi sweep
     for (int l = 0; l < h->nlev; l++)
         if (h->lev[l].smoothed) return AMG_ERR_ARG;
+    if (h->o.cheb_degree > 0) return AMG_ERR_ARG;
     return (h->o.nu_pre == 1 && h->o.nu_post == 1) ? AMG_OK : AMG_ERR_ARG;
 }
 

@@ -109,6 +109,7 @@ struct Level {
     int smoothed = 0;
     DevCSR sp, spT;
     double* kp = nullptr;  // level 0: values of K P (pattern of sp), which theta rescales into P_bar
+    void* cd[2] = {};      // Chebyshev smoother directions (V-cycle precision), when cheb_degree > 0
     // V-cycle vectors (FP64 mode)
     double* f = nullptr;
     double* x = nullptr;

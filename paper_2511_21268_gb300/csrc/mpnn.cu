@@ -1327,7 +1327,7 @@ using namespace amg;
 extern "C" {
 
 int amg_mpnn_apply(amg_hierarchy* h, const float* w, int32_t bf16_weights) {
-    if (!h || bf16_weights < 0 || bf16_weights > 1) return AMG_ERR_ARG;
+    if (!h || bf16_weights < 0 || bf16_weights > 1 || h->o.cheb_degree > 0) return AMG_ERR_ARG;
     MP_RC(join_caller_stream(h));
     if (w) {
         MP_RC(prepare(h));
@@ -1349,6 +1349,7 @@ int amg_mpnn_omega(amg_hierarchy* h, int32_t level, float* omega) {
 }
 
 static bool any_smoothed(const amg_hierarchy* h) {
+    if (h->o.cheb_degree > 0) return true;  // the network's V-cycle smooths with l1-Jacobi sweeps
     for (int l = 0; l < h->nlev; l++)
         if (h->lev[l].smoothed) return true;
     return false;
@@ -1357,7 +1358,7 @@ static bool any_smoothed(const amg_hierarchy* h) {
 // A hierarchy for the smoothing weights' two-grid loss: two levels, level 0
 // smoothed (with its K P kept).
 static bool twogrid_theta(const amg_hierarchy* h) {
-    return h->nlev == 2 && h->lev[0].smoothed && h->lev[0].kp && h->nsys == 0;
+    return h->nlev == 2 && h->lev[0].smoothed && h->lev[0].kp && h->nsys == 0 && h->o.cheb_degree == 0;
 }
 
 int amg_mpnn_loss_grad(amg_hierarchy* h, const float* w, int32_t nprobe, uint64_t seed, double* loss,

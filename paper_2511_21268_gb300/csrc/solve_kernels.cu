@@ -163,6 +163,102 @@ __global__ void __launch_bounds__(kBlock) k_coarse(int n, const double* __restri
     }
 }
 
+// ------------------------------------------- Chebyshev smoothing (4th kind)
+// 4th-kind Chebyshev acceleration of l1-Jacobi with rho(D^-1 K) <= 1 (the l1
+// diagonal's bound): d_0 = (4/3) D^-1 r_0; r_i = r_{i-1} - K d_{i-1},
+// d_i = a_i d_{i-1} + b_i D^-1 r_i, a_i = (2i-1)/(2i+3), b_i = (8i+4)/(2i+3);
+// x advances by each d.  The x update of a step is deferred to the next
+// kernel, whose matrix pass reads d, not x (x stays row-local).
+
+// pre-smoothing from x = 0: x = 0, d = c0 D^-1 f
+template <typename A, typename FT>
+__global__ void k_cheb_start(int n, const FT* __restrict__ f, const A* __restrict__ invd, A c0, A* x, A* d,
+                             const SolveState* st) {
+    pdl_entry();
+    DONE_GUARD(st);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        x[i] = A(0);
+        d[i] = c0 * invd[i] * (A)f[i];
+    }
+}
+
+// x += dprev; r = rprev - K dprev; dnew = a dprev + b D^-1 r (r may be rprev)
+template <int RPW, typename A, typename M, typename FT>
+__global__ void __launch_bounds__(kBlock) k_cheb_step(int n, M mat, const A* __restrict__ dprev, const FT* rprev,
+                                                       A* r, const A* __restrict__ invd, A a, A b, A* dnew, A* x,
+                                                       const SolveState* st) {
+    pdl_entry();
+    DONE_GUARD(st);
+    ROWGROUP_PROLOGUE(A)
+    const A s = group_rows<RPW, A>(mat, dprev, row0, n, lane, tiles[wid]);
+    if (owner) {
+        const A ri = (A)rprev[myrow] - s;
+        const A dp = dprev[myrow];
+        r[myrow] = ri;
+        dnew[myrow] = fma(b, invd[myrow] * ri, a * dp);
+        x[myrow] += dp;
+    }
+}
+
+// end of pre-smoothing: x += dprev; r = rprev - K dprev (the residual)
+template <int RPW, typename A, typename M, typename FT>
+__global__ void __launch_bounds__(kBlock) k_cheb_resid(int n, M mat, const A* __restrict__ dprev, const FT* rprev,
+                                                        A* r, A* x, const SolveState* st) {
+    pdl_entry();
+    DONE_GUARD(st);
+    ROWGROUP_PROLOGUE(A)
+    const A s = group_rows<RPW, A>(mat, dprev, row0, n, lane, tiles[wid]);
+    if (owner) {
+        r[myrow] = (A)rprev[myrow] - s;
+        x[myrow] += dprev[myrow];
+    }
+}
+
+// start of post-smoothing: r = f - K x, d = c0 D^-1 r (x unchanged)
+template <int RPW, typename A, typename M, typename FT>
+__global__ void __launch_bounds__(kBlock) k_cheb_post0(int n, M mat, const FT* __restrict__ f,
+                                                        const A* __restrict__ x, const A* __restrict__ invd, A c0,
+                                                        A* r, A* d, const SolveState* st) {
+    pdl_entry();
+    DONE_GUARD(st);
+    ROWGROUP_PROLOGUE(A)
+    const A s = group_rows<RPW, A>(mat, x, row0, n, lane, tiles[wid]);
+    if (owner) {
+        const A ri = (A)f[myrow] - s;
+        r[myrow] = ri;
+        d[myrow] = c0 * invd[myrow] * ri;
+    }
+}
+
+// x += d
+template <typename A>
+__global__ void k_cheb_add(int n, const A* __restrict__ d, A* x, const SolveState* st) {
+    pdl_entry();
+    DONE_GUARD(st);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] += d[i];
+}
+
+// level 0 after post-smoothing: z = x + d (FP64); block partials r.z and
+// (flexible) z.q over a grid-stride loop
+template <typename A>
+__global__ void __launch_bounds__(kBlock) k_cheb_z(int n, const A* __restrict__ x, const A* __restrict__ d,
+                                                    const double* __restrict__ r, double* z,
+                                                    const double* __restrict__ q, double* part_rz, double* part_zq,
+                                                    int flexible, const SolveState* st) {
+    pdl_entry();
+    DONE_GUARD(st);
+    __shared__ double sh[kWarpsPerBlock];
+    double rz = 0.0, zq = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double zi = (double)(x[i] + d[i]);
+        z[i] = zi;
+        rz = fma(r[i], zi, rz);
+        if (flexible) zq = fma(zi, q[i], zq);
+    }
+    block_partial(rz, sh, part_rz + blockIdx.x);
+    if (flexible) block_partial(zq, sh, part_zq + blockIdx.x);
+}
+
 // ------------------------------------------------------------ CG scalars
 __global__ void k_scal_init(const double* part_rr, const double* part_ff, int nb, double rtol, int itmax,
                             int repl_every, double* hist, SolveState* st) {
@@ -590,7 +686,139 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// V-cycle with the Chebyshev smoother of degree cheb_degree on every level
+// (plain row-group matrix passes on every level, tentative or smoothed
+// prolongators); the coarsest solve and the CG interface as vcycle_impl.
+template <typename A>
+static cudaError_t vcycle_cheb(amg_hierarchy* h, cudaStream_t s) {
+    using Vw = View<A>;
+    const int L = h->nlev;
+    const int sms = h->num_sms;
+    const int k = h->o.cheb_degree;
+    const int flex = h->o.flexible;
+    const SolveState* st = h->st;
+    if (L == 1) {
+        launch_pdl(k_coarse<double, A>, row_blocks(h->ndense, 1), kBlock, 0, s,
+            h->ndense, h->Ainv, h->r, nullptr, nullptr, nullptr, nullptr, h->z, h->q, slot(h, S_RZ), slot(h, S_ZQ),
+            flex, st);
+        return cudaGetLastError();
+    }
+    const A c0 = A(4.0 / 3.0);
+    auto coef_a = [](int i) { return A((double)(2 * i - 1) / (double)(2 * i + 3)); };
+    auto coef_b = [](int i) { return A((double)(8 * i + 4) / (double)(2 * i + 3)); };
+    // down: pre-smoothing from zero, residual, restriction
+    for (int l = 0; l < L - 1; l++) {
+        Level& F = h->lev[l];
+        Level& C = h->lev[l + 1];
+        const int n = F.A.n;
+        const int rpw = rows_per_warp(n, sms), nb = row_blocks(n, rpw), nv = vec_blocks(n, sms);
+        A* x = Vw::x(F);
+        A* r = Vw::t(F);
+        A* d0 = static_cast<A*>(F.cd[0]);
+        A* d1 = static_cast<A*>(F.cd[1]);
+        auto run = [&](auto fp) {
+            using FT = vtype<decltype(fp)>;
+            launch_pdl(k_cheb_start<A, FT>, nv, kBlock, 0, s, n, fp, Vw::invd(F), c0, x, d0, st);
+            Vw::vals(F, l, [&](auto mat) {
+                using M = decltype(mat);
+                A* dp = d0;
+                A* dn = d1;
+                for (int i = 1; i < k; i++) {
+                    with_rpw(rpw, [&](auto R) {
+                        if (i == 1)
+                            launch_pdl(k_cheb_step<decltype(R)::value, A, M, FT>, nb, kBlock, 0, s, n, mat,
+                                       static_cast<const A*>(dp), fp, r, Vw::invd(F), coef_a(i), coef_b(i), dn, x,
+                                       st);
+                        else
+                            launch_pdl(k_cheb_step<decltype(R)::value, A, M, A>, nb, kBlock, 0, s, n, mat,
+                                       static_cast<const A*>(dp), static_cast<const A*>(r), r, Vw::invd(F),
+                                       coef_a(i), coef_b(i), dn, x, st);
+                    });
+                    std::swap(dp, dn);
+                }
+                with_rpw(rpw, [&](auto R) {
+                    if (k == 1)
+                        launch_pdl(k_cheb_resid<decltype(R)::value, A, M, FT>, nb, kBlock, 0, s, n, mat,
+                                   static_cast<const A*>(dp), fp, r, x, st);
+                    else
+                        launch_pdl(k_cheb_resid<decltype(R)::value, A, M, A>, nb, kBlock, 0, s, n, mat,
+                                   static_cast<const A*>(dp), static_cast<const A*>(r), r, x, st);
+                });
+            });
+        };
+        if (l == 0) run(static_cast<const double*>(h->r));
+        else run(static_cast<const A*>(Vw::f(F)));
+        if (F.smoothed)
+            sp_restrict<A>(F, C, r, Vw::f(C), static_cast<A*>(nullptr), Vw::invd(C), st, s);
+        else
+            launch_pdl(k_restrict<A, 4>, restrict_blocks(C.A.n, sms), kBlock, 0, s, C.A.n, F.mem_ptr, F.mem_idx,
+                       F.pval, static_cast<const A*>(r), Vw::f(C), static_cast<A*>(nullptr), Vw::invd(C), st);
+    }
+    // coarsest: exact dense solve, prolongated into level L-2
+    {
+        Level& F = h->lev[L - 2];
+        Level& C = h->lev[L - 1];
+        if (F.smoothed) {
+            sp_coarse<A>(C.A.n, h->Ainv, Vw::f(C), Vw::x(C), st, s);
+            sp_prolong<A>(F, Vw::x(C), Vw::x(F), st, s);
+        } else {
+            launch_pdl(k_coarse<A, A>, row_blocks(C.A.n, 1), kBlock, 0, s, C.A.n, h->Ainv, Vw::f(C), F.mem_ptr,
+                       F.mem_idx, F.pval, Vw::x(F), nullptr, nullptr, nullptr, nullptr, 0, st);
+        }
+    }
+    // up: post-smoothing from the corrected x, then prolongation to the finer level
+    for (int l = L - 2; l >= 0; l--) {
+        Level& F = h->lev[l];
+        const int n = F.A.n;
+        const int rpw = rows_per_warp(n, sms), nb = row_blocks(n, rpw), nv = vec_blocks(n, sms);
+        A* x = Vw::x(F);
+        A* r = Vw::t(F);
+        A* d0 = static_cast<A*>(F.cd[0]);
+        A* d1 = static_cast<A*>(F.cd[1]);
+        A* dlast = d0;
+        auto run = [&](auto fp) {
+            using FT = vtype<decltype(fp)>;
+            Vw::vals(F, l, [&](auto mat) {
+                using M = decltype(mat);
+                with_rpw(rpw, [&](auto R) {
+                    launch_pdl(k_cheb_post0<decltype(R)::value, A, M, FT>, nb, kBlock, 0, s, n, mat, fp,
+                               static_cast<const A*>(x), Vw::invd(F), c0, r, d0, st);
+                });
+                A* dp = d0;
+                A* dn = d1;
+                for (int i = 1; i < k; i++) {
+                    with_rpw(rpw, [&](auto R) {
+                        launch_pdl(k_cheb_step<decltype(R)::value, A, M, A>, nb, kBlock, 0, s, n, mat,
+                                   static_cast<const A*>(dp), static_cast<const A*>(r), r, Vw::invd(F), coef_a(i),
+                                   coef_b(i), dn, x, st);
+                    });
+                    std::swap(dp, dn);
+                }
+                dlast = dp;
+            });
+        };
+        if (l == 0) run(static_cast<const double*>(h->r));
+        else run(static_cast<const A*>(Vw::f(F)));
+        if (l == 0) {
+            const int nbz0 = (h->stream || h->sell64) ? h->stream_blocks : row_blocks(n, rows_per_warp(n, sms));
+            launch_pdl(k_cheb_z<A>, nbz0, kBlock, 0, s, n, static_cast<const A*>(x), static_cast<const A*>(dlast),
+                       static_cast<const double*>(h->r), h->z, static_cast<const double*>(h->q), slot(h, S_RZ),
+                       slot(h, S_ZQ), flex, st);
+        } else {
+            launch_pdl(k_cheb_add<A>, nv, kBlock, 0, s, n, static_cast<const A*>(dlast), x, st);
+            Level& G = h->lev[l - 1];
+            if (G.smoothed)
+                sp_prolong<A>(G, static_cast<const A*>(x), Vw::x(G), st, s);
+            else
+                launch_pdl(k_prolong<A>, vec_blocks(G.A.n, sms), kBlock, 0, s, G.A.n, G.agg, G.pval,
+                           static_cast<const A*>(x), Vw::x(G), st);
+        }
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t enqueue_vcycle(amg_hierarchy* h, cudaStream_t s) {
+    if (h->o.cheb_degree > 0) return h->mixed ? vcycle_cheb<float>(h, s) : vcycle_cheb<double>(h, s);
     return h->mixed ? vcycle_impl<float>(h, s) : vcycle_impl<double>(h, s);
 }
 

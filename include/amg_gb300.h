@@ -122,6 +122,12 @@ typedef struct {
                                     d[i] = (2i-1)/(2i+3) d[i-1] + (8i+4)/(2i+3) D^-1 r[i]); matrix passes
                                     on CSR row groups; needs amg_pcg_solve / amg_vcycle_apply and no
                                     damping network (0) */
+    int32_t coarse_solver;       /* coarsest level: 0 = exact solve with the dense inverse; 1 = CG
+                                    preconditioned by Jacobi (z = r / k_ii) from zero, to coarse_tol or
+                                    coarse_maxit iterations (Sec. 5), a variable preconditioner: use it
+                                    with flexible = 1 (0) */
+    double coarse_tol;           /* coarse CG: stop once ||r|| <= coarse_tol ||f|| (0.0001) */
+    int32_t coarse_maxit;        /* coarse CG: at most this many iterations (30) */
 } amg_opts;
 
 #define AMG_MAX_LEVELS 32

@@ -48,7 +48,8 @@ class Opts(ctypes.Structure):
                 ("coarse_max", ctypes.c_int), ("max_levels", ctypes.c_int), ("testvec_sweeps", ctypes.c_int),
                 ("testvec_kind", ctypes.c_int), ("seed", ctypes.c_uint64), ("stag", ctypes.c_double),
                 ("dense_max", ctypes.c_int), ("smooth_levels", ctypes.c_int), ("smooth_omega", ctypes.c_double),
-                ("cheb_degree", ctypes.c_int)]
+                ("cheb_degree", ctypes.c_int), ("coarse_solver", ctypes.c_int), ("coarse_tol", ctypes.c_double),
+                ("coarse_maxit", ctypes.c_int)]
 
 
 _lib = None
@@ -73,6 +74,7 @@ def lib():
         L.orc_galerkin_general.argtypes = [i64, P, P, P, P, P, P, i64, P, P, P]
         L.orc_galerkin_general.restype = i32
         L.orc_cheb4_smooth.argtypes = [i64, P, P, P, P, P, P, P, P, P, i32, i32]
+        L.orc_coarse_cg.argtypes = [i64, P, P, P, P, dbl, i32, P]
         L.orc_free.argtypes = [P]
         L.orc_num_levels.argtypes = [P]
         L.orc_num_levels.restype = i32
@@ -249,6 +251,15 @@ def cheb4_smooth(rowptr, col, val, dl1, f, x0=None, degree=4):
     lib().orc_cheb4_smooth(n, _p(rp), _p(ci), _p(v), _p(d), _p(f), _p(x), _p(r), _p(w1), _p(w2), int(degree),
                            int(x0 is None))
     return x, r
+
+
+def coarse_cg(rowptr, col, val, f, tol=1e-4, maxit=30):
+    """Jacobi-preconditioned CG from zero (the coarse solver option)."""
+    rp, ci, v = _csr(rowptr, col, val)
+    f = np.ascontiguousarray(f, np.float64)
+    x = np.empty(len(rp) - 1)
+    lib().orc_coarse_cg(len(rp) - 1, _p(rp), _p(ci), _p(v), _p(f), float(tol), int(maxit), _p(x))
+    return x
 
 
 def _take_csr(n, orp, oci, ov):

@@ -83,6 +83,10 @@
  *     the restriction; post-smoothing starts from the prolongated x.  The
  *     paper's "optimized" variant scales the steps by tabulated weights
  *     that are not used here.
+ *   - coarsest solve (option coarse_solver = 1, Sec. 5): CG preconditioned
+ *     by Jacobi (z = r / k_ii) from x = 0, stopping once ||r|| <= coarse_tol
+ *     ||f|| (recursive residual) or after coarse_maxit iterations; the
+ *     default is the exact dense Cholesky solve.
  *   - PCG stops when ||r_k||_2 <= rtol ||F||_2 on the recursive residual.
  *
  * Threads: the solve phase (V-cycle and CG) may run its row loops -- each
@@ -136,6 +140,9 @@ typedef struct {
     int smooth_levels;   /* smoothed prolongator on the first levels (-1 = all, 0 = none) */
     double smooth_omega; /* theta of the smoothed levels (4/3) */
     int cheb_degree;     /* 0: nu_pre / nu_post l1-Jacobi sweeps; k >= 1: 4th-kind Chebyshev of degree k */
+    int coarse_solver;   /* 0: dense Cholesky; 1: CG with Jacobi preconditioning */
+    double coarse_tol;   /* coarse CG: stop at ||r|| <= coarse_tol ||f|| (1e-4) */
+    int coarse_maxit;    /* coarse CG: at most this many iterations (30) */
 } orc_opts;
 
 typedef struct {
@@ -659,6 +666,9 @@ void orc_opts_default(orc_opts* o) {
     o->smooth_levels = 0;
     o->smooth_omega = 4.0 / 3.0;
     o->cheb_degree = 0;
+    o->coarse_solver = 0;
+    o->coarse_tol = 1e-4;
+    o->coarse_maxit = 30;
 }
 
 static void level_free(orc_level* L) {
@@ -850,6 +860,40 @@ void orc_cheb4_smooth(int64_t n, const int64_t* rp, const int32_t* ci, const dou
     }
 }
 
+/* Jacobi-preconditioned CG on K x = f from x = 0 (coarsest level, Sec. 5):
+ * at most maxit iterations, stopping when ||r||_2 <= tol ||f||_2. */
+void orc_coarse_cg(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* f, double tol,
+                   int maxit, double* x) {
+    double* r = (double*)malloc(sizeof(double) * n);
+    double* z = (double*)malloc(sizeof(double) * n);
+    double* p = (double*)malloc(sizeof(double) * n);
+    double* q = (double*)malloc(sizeof(double) * n);
+    double* dg = (double*)malloc(sizeof(double) * n);
+    for (int64_t i = 0; i < n; i++) {
+        x[i] = 0.0;
+        r[i] = f[i];
+        dg[i] = diag_of(rp, ci, v, i);
+        z[i] = r[i] / dg[i];
+        p[i] = z[i];
+    }
+    const double stop = tol * sqrt(dot(n, f, f));
+    double rho = dot(n, r, z);
+    for (int it = 0; it < maxit && sqrt(dot(n, r, r)) > stop; it++) {
+        orc_spmv(n, rp, ci, v, p, q);
+        const double pq = dot(n, p, q);
+        if (!(pq > 0.0)) break;
+        const double alpha = rho / pq;
+        for (int64_t i = 0; i < n; i++) x[i] = x[i] + alpha * p[i];
+        for (int64_t i = 0; i < n; i++) r[i] = r[i] - alpha * q[i];
+        for (int64_t i = 0; i < n; i++) z[i] = r[i] / dg[i];
+        const double rho1 = dot(n, r, z);
+        const double beta = rho1 / rho;
+        rho = rho1;
+        for (int64_t i = 0; i < n; i++) p[i] = z[i] + beta * p[i];
+    }
+    free(r); free(z); free(p); free(q); free(dg);
+}
+
 /* ------------------------------------------------------------- V-cycle ---- */
 /* Two-level correction applied recursively (Sec. 3, steps 1-5), l1-Jacobi
  * smoothing from x = 0, exact coarsest solve. */
@@ -857,7 +901,10 @@ static void vcycle(const orc_hier* h, int l, const double* f, double* x) {
     const orc_level* L = &h->lev[l];
     const int64_t n = L->n;
     if (l == h->nlev - 1) {
-        orc_chol_solve(n, h->chol, f, x);
+        if (h->o.coarse_solver == 1 && h->nlev > 1)
+            orc_coarse_cg(n, L->rowptr, L->col, L->val, f, h->o.coarse_tol, h->o.coarse_maxit, x);
+        else
+            orc_chol_solve(n, h->chol, f, x);
         return;
     }
     double* r = (double*)malloc(sizeof(double) * n);

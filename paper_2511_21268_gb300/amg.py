@@ -47,7 +47,8 @@ class AmgOpts(ctypes.Structure):
                 ("flexible", ctypes.c_int32), ("resid_replace_every", ctypes.c_int32),
                 ("matrix_format", ctypes.c_int32), ("mpnn_weights", ctypes.c_void_p), ("mpnn_bf16", ctypes.c_int32),
                 ("smooth_levels", ctypes.c_int32), ("smooth_omega", ctypes.c_double),
-                ("smooth_theta", ctypes.c_void_p), ("cheb_degree", ctypes.c_int32)]
+                ("smooth_theta", ctypes.c_void_p), ("cheb_degree", ctypes.c_int32),
+                ("coarse_solver", ctypes.c_int32), ("coarse_tol", ctypes.c_double), ("coarse_maxit", ctypes.c_int32)]
 
 
 class AmgInfo(ctypes.Structure):

@@ -517,6 +517,7 @@ int build(amg_hierarchy* h, const amg_csr* K) {
     CK(launch_dense_spd_inverse(nd, D, h->Ainv, h->flag, s));
     RC(read_flag(h, &bad));
     if (bad) return AMG_ERR_NOT_SPD;
+    if (h->o.coarse_solver == 1) RC(dalloc(h, &h->ccg, (size_t)5 * nd));
     // solve workspace
     phase(h, 8);
     for (int l = 0; l < h->nlev; l++) {
@@ -731,6 +732,8 @@ int check_opts(const amg_opts& o) {
     if (o.smooth_levels < -1 || !(o.smooth_omega >= 0.0) || !std::isfinite(o.smooth_omega)) return AMG_ERR_ARG;
     if (o.cheb_degree < 0 || o.cheb_degree > 64) return AMG_ERR_ARG;
     if (o.cheb_degree > 0 && o.mpnn_weights) return AMG_ERR_ARG;  // the network damps l1-Jacobi sweeps
+    if (o.coarse_solver < 0 || o.coarse_solver > 1 || !(o.coarse_tol >= 0.0) || o.coarse_maxit < 1)
+        return AMG_ERR_ARG;
     return AMG_OK;
 }
 
@@ -762,6 +765,9 @@ int amg_opts_default(amg_opts* o) {
     o->smooth_omega = 4.0 / 3.0;
     o->smooth_theta = nullptr;
     o->cheb_degree = 0;
+    o->coarse_solver = 0;
+    o->coarse_tol = 1e-4;
+    o->coarse_maxit = 30;
     return AMG_OK;
 }
 
@@ -1141,6 +1147,7 @@ static int run_multi(amg_hierarchy* h, int32_t* iters, double* relres, int32_t* 
 }
 
 static int check_multi_opts(const amg_hierarchy* h) {
+    if (h->o.coarse_solver != 0) return AMG_ERR_ARG;  // the multi-system solves use the dense coarse inverse
     // the multi-system V-cycle prolongates with the tentative P's member lists
     // and smooths with one l1-Jacobi sweep
     for (int l = 0; l < h->nlev; l++)

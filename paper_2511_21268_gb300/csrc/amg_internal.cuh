@@ -169,6 +169,7 @@ struct amg_hierarchy {
     amg::Level lev[AMG_MAX_LEVELS];
     int ndense = 0;
     double* Ainv = nullptr;  // dense inverse of the coarsest matrix (row-major)
+    double* ccg = nullptr;   // coarse CG work vectors (5 x coarsest rows), coarse_solver = 1
     // CG workspace (level 0)
     double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *F = nullptr;
     float* p32 = nullptr;  // FP32 copy of p for the mixed-precision outer SpMV

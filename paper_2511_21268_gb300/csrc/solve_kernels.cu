@@ -163,6 +163,87 @@ __global__ void __launch_bounds__(kBlock) k_coarse(int n, const double* __restri
     }
 }
 
+// ------------------------------------------------- coarsest level by CG
+// Fixed-order sum over one block of 1024 threads (result on every thread).
+__device__ __forceinline__ double block_sum1024(double t, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) u += red[w];
+        red[32] = u;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// Coarsest level by Jacobi-preconditioned CG from x = 0 (Sec. 5's coarse
+// solver): at most maxit iterations, stop once ||r|| <= tol ||f||.  One
+// block; FP64 work vectors r, z, p, q, x in global memory (4 n + n doubles);
+// the result goes to e in the V-cycle precision.
+template <typename A>
+__global__ void __launch_bounds__(1024) k_coarse_cg(int n, const int64_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ ci, const double* __restrict__ v,
+                                                     const double* __restrict__ kii, const A* __restrict__ f, A* e,
+                                                     double* work, double tol, int maxit, const SolveState* st) {
+    pdl_entry();
+    DONE_GUARD(st);
+    __shared__ double red[33];
+    double *r = work, *z = work + n, *p = work + 2 * (int64_t)n, *q = work + 3 * (int64_t)n,
+           *x = work + 4 * (int64_t)n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwp = blockDim.x >> 5;
+    double ff = 0.0, rz = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double fi = (double)f[i], zi = fi / kii[i];
+        x[i] = 0.0;
+        r[i] = fi;
+        z[i] = zi;
+        p[i] = zi;
+        ff = fma(fi, fi, ff);
+        rz = fma(fi, zi, rz);
+    }
+    ff = block_sum1024(ff, red);
+    double rho = block_sum1024(rz, red);
+    double rr = ff;
+    const double stop = tol * sqrt(ff);
+    for (int it = 0; it < maxit && sqrt(rr) > stop; it++) {
+        for (int i = wid; i < n; i += nwp) {  // q = K p, a warp per row
+            double acc = 0.0;
+            for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) acc = fma(v[k], p[ci[k]], acc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+            if (lane == 0) q[i] = acc;
+        }
+        __syncthreads();
+        double t = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) t = fma(p[i], q[i], t);
+        const double pq = block_sum1024(t, red);
+        if (!(pq > 0.0)) break;
+        const double alpha = rho / pq;
+        double t1 = 0.0, t2 = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            x[i] = fma(alpha, p[i], x[i]);
+            const double ri = fma(-alpha, q[i], r[i]);
+            const double zi = ri / kii[i];
+            r[i] = ri;
+            z[i] = zi;
+            t1 = fma(ri, zi, t1);
+            t2 = fma(ri, ri, t2);
+        }
+        const double rho1 = block_sum1024(t1, red);
+        rr = block_sum1024(t2, red);
+        const double beta = rho1 / rho;
+        rho = rho1;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = fma(beta, p[i], z[i]);
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) e[i] = (A)x[i];
+}
+
 // ------------------------------------------- Chebyshev smoothing (4th kind)
 // 4th-kind Chebyshev acceleration of l1-Jacobi with rho(D^-1 K) <= 1 (the l1
 // diagonal's bound): d_0 = (4/3) D^-1 r_0; r_i = r_{i-1} - K d_{i-1},
@@ -518,6 +599,34 @@ struct View<float> {
 template <typename T>
 using vtype = std::remove_cv_t<std::remove_pointer_t<T>>;
 
+// Coarsest level of a hierarchy with at least two levels: e = A^-1 f
+// (dense inverse, or CG when coarse_solver = 1), prolongated into x of
+// level L - 2 (tentative P fused with the dense solve, or a gather).
+template <typename A>
+static void coarsest_solve(amg_hierarchy* h, A* xF, cudaStream_t s) {
+    using Vw = View<A>;
+    const int L = h->nlev;
+    Level& F = h->lev[L - 2];
+    Level& C = h->lev[L - 1];
+    const SolveState* st = h->st;
+    if (h->o.coarse_solver == 1) {
+        A* e = Vw::x(C);
+        launch_pdl(k_coarse_cg<A>, 1, 1024, 0, s, C.A.n, C.A.rowptr, C.A.col, C.A.val, C.kii,
+                   static_cast<const A*>(Vw::f(C)), e, h->ccg, h->o.coarse_tol, h->o.coarse_maxit, st);
+        if (F.smoothed)
+            sp_prolong<A>(F, static_cast<const A*>(e), xF, st, s);
+        else
+            launch_pdl(k_prolong<A>, vec_blocks(F.A.n, h->num_sms), kBlock, 0, s, F.A.n, F.agg, F.pval,
+                       static_cast<const A*>(e), xF, st);
+    } else if (F.smoothed) {
+        sp_coarse<A>(C.A.n, h->Ainv, Vw::f(C), Vw::x(C), st, s);
+        sp_prolong<A>(F, Vw::x(C), xF, st, s);
+    } else {
+        launch_pdl(k_coarse<A, A>, row_blocks(C.A.n, 1), kBlock, 0, s, C.A.n, h->Ainv, Vw::f(C), F.mem_ptr,
+                   F.mem_idx, F.pval, xF, nullptr, nullptr, nullptr, nullptr, 0, st);
+    }
+}
+
 // V-cycle on r (= f_0); the pre-smoothed level-0 iterate is already in x_0.
 // Writes z (FP64) and the partial sums of r.z (and z.q).
 template <typename A>
@@ -596,17 +705,7 @@ static cudaError_t vcycle_impl(amg_hierarchy* h, cudaStream_t s) {
                        F.pval, xalt[l], Vw::f(C), coarsest ? nullptr : xcur[l + 1], Vw::invd(C), st);
     }
     // coarsest
-    {
-        Level& F = h->lev[L - 2];
-        Level& C = h->lev[L - 1];
-        if (F.smoothed) {  // e = A^-1 f, then x += P_bar e
-            sp_coarse<A>(C.A.n, h->Ainv, Vw::f(C), xcur[L - 1], st, s);
-            sp_prolong<A>(F, xcur[L - 1], xcur[L - 2], st, s);
-        } else {
-            launch_pdl(k_coarse<A, A>, row_blocks(C.A.n, 1), kBlock, 0, s, C.A.n, h->Ainv, Vw::f(C), F.mem_ptr,
-                       F.mem_idx, F.pval, xcur[L - 2], nullptr, nullptr, nullptr, nullptr, 0, st);
-        }
-    }
+    coarsest_solve<A>(h, xcur[L - 2], s);
     // up
     for (int l = L - 2; l >= 0; l--) {
         Level& F = h->lev[l];
@@ -754,18 +853,8 @@ static cudaError_t vcycle_cheb(amg_hierarchy* h, cudaStream_t s) {
             launch_pdl(k_restrict<A, 4>, restrict_blocks(C.A.n, sms), kBlock, 0, s, C.A.n, F.mem_ptr, F.mem_idx,
                        F.pval, static_cast<const A*>(r), Vw::f(C), static_cast<A*>(nullptr), Vw::invd(C), st);
     }
-    // coarsest: exact dense solve, prolongated into level L-2
-    {
-        Level& F = h->lev[L - 2];
-        Level& C = h->lev[L - 1];
-        if (F.smoothed) {
-            sp_coarse<A>(C.A.n, h->Ainv, Vw::f(C), Vw::x(C), st, s);
-            sp_prolong<A>(F, Vw::x(C), Vw::x(F), st, s);
-        } else {
-            launch_pdl(k_coarse<A, A>, row_blocks(C.A.n, 1), kBlock, 0, s, C.A.n, h->Ainv, Vw::f(C), F.mem_ptr,
-                       F.mem_idx, F.pval, Vw::x(F), nullptr, nullptr, nullptr, nullptr, 0, st);
-        }
-    }
+    // coarsest, prolongated into level L-2
+    coarsest_solve<A>(h, Vw::x(h->lev[L - 2]), s);
     // up: post-smoothing from the corrected x, then prolongation to the finer level
     for (int l = L - 2; l >= 0; l--) {
         Level& F = h->lev[l];

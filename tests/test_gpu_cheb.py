@@ -62,18 +62,38 @@ def test_chebyshev_mixed_precision(prec):
     assert np.linalg.norm(u - u64) <= 1e-7 * np.linalg.norm(u64)
 
 
+@pytest.mark.parametrize("smooth,deg", [(0, 0), (-1, 4)])
+def test_coarse_cg_matches_oracle(smooth, deg):
+    """The coarse solver of Sec. 5 (Jacobi-preconditioned CG to 1e-4 or 30
+    iterations) against the oracle's: V-cycle within 1e-10, flexible-CG
+    iterations +-1."""
+    prob = I.poisson_box(2, 28, 3)
+    kw = dict(coarse_max=150, coarse_solver=1, smooth_levels=smooth, cheb_degree=deg, flexible=1)
+    Ho = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=150, coarse_solver=1, smooth_levels=smooth,
+                     cheb_degree=deg)
+    H = A.Hierarchy(dev(prob.rowptr), dev(prob.col), dev(prob.val), **kw)
+    r = np.random.default_rng(8).standard_normal(prob.n)
+    z = H.vcycle(dev(r)).cpu().numpy()
+    zo = Ho.vcycle(r)
+    assert np.linalg.norm(z - zo) <= 1e-10 * np.linalg.norm(zo)
+    g = H.solve(dev(prob.F), rtol=1e-8)
+    ref = Ho.pcg(prob.F, rtol=1e-8, flexible=True)
+    assert g["status"] == 0 and abs(g["iters"] - ref["iters"]) <= 1
+
+
 def test_papers_configuration_trend():
     """Sec. 5 settings on the cube (homogeneous Dirichlet here): m = 3
     (aggregates <= 8), smoothed prolongators, Chebyshev degree 8 (p = 3) /
-    12 (p = 4), flexible CG, rtol 1e-6, x0 = 0.  The iteration counts should
-    stay nearly flat in n, as in the paper's Table 1."""
+    12 (p = 4), the coarse CG to 1e-4 or 30 iterations, flexible CG, rtol
+    1e-6, x0 = 0.  The iteration counts should stay nearly flat in n, as in
+    the paper's Table 1."""
     deg = {3: 8, 4: 12}
     out = {}
     for p in (3, 4):
         for n in (8, 12, 16, 24):
             prob = I.poisson_box(3, n, p)
             H = A.Hierarchy(dev(prob.rowptr), dev(prob.col), dev(prob.val), match_passes=3, smooth_levels=-1,
-                            cheb_degree=deg[p], flexible=1)
+                            cheb_degree=deg[p], flexible=1, coarse_solver=1)
             g = H.solve(dev(prob.F), rtol=1e-6)
             assert g["status"] == 0
             out[(p, n)] = (g["iters"], round(H.info.opc, 2), H.num_levels)

@@ -538,3 +538,30 @@ def test_chebyshev_vcycle_symmetric_positive_and_faster():
     assert x @ bx > 0
     Hj = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=30)
     assert Hc.pcg(prob.F, rtol=1e-8)["iters"] < Hj.pcg(prob.F, rtol=1e-8)["iters"]
+
+
+def test_coarse_cg_against_textbook_and_dense():
+    """The coarse CG (Sec. 5: Jacobi-preconditioned CG to a relative
+    tolerance or an iteration cap) reaches the dense solution when run to a
+    tight tolerance, stops at the cap otherwise, and the V-cycle with it
+    still solves the system under flexible CG."""
+    prob = I.poisson_box(2, 12, 2)
+    Hd = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=60)
+    Hc = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=60, coarse_solver=1, coarse_tol=1e-14,
+                     coarse_maxit=1000)
+    r = np.random.default_rng(4).standard_normal(prob.n)
+    zd, zc = Hd.vcycle(r), Hc.vcycle(r)
+    assert np.linalg.norm(zd - zc) <= 1e-10 * np.linalg.norm(zd)
+    H4 = O.Hierarchy(prob.rowptr, prob.col, prob.val, coarse_max=60, coarse_solver=1)
+    g = H4.pcg(prob.F, rtol=1e-8, flexible=True)
+    assert g["status"] == 0 and g["relres"] <= 1e-8 * 1.0001
+    # one iteration of the coarse CG is the Jacobi-preconditioned steepest-descent step
+    L = Hd.num_levels - 1
+    rp, ci, v = Hd.level_csr(L)
+    Kc = dense(rp, ci, v)
+    f = np.random.default_rng(5).standard_normal(len(rp) - 1)
+    z = f / np.diag(Kc)
+    x1 = (f @ z) / (z @ Kc @ z) * z
+    assert np.allclose(O.coarse_cg(rp, ci, v, f, 1e-4, 1), x1, rtol=1e-13, atol=0)
+    # to a tight tolerance it is the dense solve
+    assert np.allclose(O.coarse_cg(rp, ci, v, f, 1e-13, 500), np.linalg.solve(Kc, f), rtol=1e-10, atol=0)

@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-annulus", action="store_true")
+    ap.add_argument("--no-smoothing", action="store_true")
+    ap.add_argument("--no-paper-config", action="store_true")
     ap.add_argument("--train-steps", type=int, default=60)
     ap.add_argument("--matrix-format", type=int, choices=[0, 1, 2], default=2,
                     help="2 = run-encoded finest level + bulk-copy streamed mixed passes (default), 1 = run-encoded, 0 = CSR")
@@ -646,6 +648,84 @@ def annulus_leg(args, A, I, torch, np, stream, dist):
             "steps": k}
 
 
+def smoothing_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, fp64_ms):
+    """Prolongator smoothing on the bench workload (Sec. 3.1 "Variants"):
+    level 0's prolongator smoothed with the constant theta = 4/3 and with the
+    network's per-row theta (second head, trained on two-level 3-D cubes
+    p in {2,3,4}, n = 8, jointly with the damping hierarchies of the learned
+    leg), against the tentative prolongator; mixed precision, plain
+    l1-Jacobi smoother in all three, each step = setup + solve + free."""
+    dev = F.device
+    dmp, sm = [], []
+    for pp in (2, 3, 4):
+        q = I.poisson_box(3, 8, pp)
+        a = (torch.from_numpy(q.rowptr).to(dev), torch.from_numpy(q.col).to(dev), torch.from_numpy(q.val).to(dev))
+        dmp.append(A.amg_setup(*a, A.amg_opts_default(), stream))
+        sm.append(A.amg_setup(*a, A.amg_opts_default(smooth_levels=1, max_levels=2, coarse_max=20), stream))
+    w = torch.from_numpy(I.mpnn_init_weights(1).astype(np.float32)).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = A.amg_mpnn_train(dmp + sm, w, 40, 4, 1000, 1e-2)
+    train_s = time.perf_counter() - t0
+    for h in dmp + sm:
+        A.amg_free(h)
+    base = dict(precision=A.AMG_FP32_BF16FINE, matrix_format=args.matrix_format)
+    legs = {"tentative": A.amg_opts_default(**base),
+            "theta_4/3": A.amg_opts_default(smooth_levels=1, **base),
+            "theta_learned": A.amg_opts_default(smooth_levels=1, mpnn_weights=w, mpnn_bf16=1, **base)}
+    out = {}
+    k = max(2, min(args.steps, 3))
+    for name, o in legs.items():
+        def st(o=o, learned=name == "theta_learned"):
+            h = A.amg_setup(rp, ci, va, o, stream)
+            if learned:
+                A.amg_set_damping(h, 1.0)  # compare the prolongators with the plain smoother
+            u = torch.zeros_like(F)
+            s_, it, rr = A.amg_pcg_solve(h, F, u, args.rtol, 10000)
+            info = A.amg_get_info(h)
+            A.amg_free(h)
+            if s_ != A.AMG_OK:
+                raise RuntimeError(f"smoothing leg {name}: {A.amg_strerror(s_)}")
+            return it, info
+        ms, (it, info) = timed_steps(st, k, 1, stream, torch, dist)
+        out[name] = {"time_to_solution_s": ms / 1e3, "iters": it, "opc": info.opc, "setup_ms": info.setup_ms,
+                     "solve_ms": info.solve_ms, "smoothing_phase_ms": info.setup_phase_ms[10],
+                     "p0_nnz": int(info.p_nnz[0]), "speedup_vs_fp64": fp64_ms / ms}
+    return {"legs": out, "steps": k, "training": {"steps": 40, "seconds": train_s,
+                                                   "loss_first": float(hist[0]), "loss_last": float(hist[-1])},
+            "note": "theta = 4/3 is the classical 4 / (3 rho(D^-1 K)) with rho <= 1 from the l1 diagonal"}
+
+
+def paper_config_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, fp64_ms):
+    """The paper's solver configuration of Sec. 5 on the bench workload:
+    aggregates of up to 8 (three matching passes), smoothed prolongators on
+    every level (theta = 4/3), 4th-kind Chebyshev l1-Jacobi of degree 8 (p =
+    3), coarse CG to 1e-4 or 30 iterations, flexible CG; FP64 and mixed
+    precision, rtol as the bench; each step = setup + solve + free."""
+    out = {}
+    k = max(2, min(args.steps, 3))
+    for name, prec in (("fp64", A.AMG_FP64), ("mixed", A.AMG_FP32_BF16FINE)):
+        o = A.amg_opts_default(match_passes=3, smooth_levels=-1, cheb_degree=8, coarse_solver=1, flexible=1,
+                               precision=prec, matrix_format=args.matrix_format)
+
+        def st(o=o):
+            h = A.amg_setup(rp, ci, va, o, stream)
+            u = torch.zeros_like(F)
+            s_, it, rr = A.amg_pcg_solve(h, F, u, args.rtol, 10000)
+            info = A.amg_get_info(h)
+            A.amg_free(h)
+            if s_ != A.AMG_OK:
+                raise RuntimeError(f"paper configuration {name}: {A.amg_strerror(s_)}")
+            return it, rr, info
+        ms, (it, rr, info) = timed_steps(st, k, 1, stream, torch, dist)
+        out[name] = {"time_to_solution_s": ms / 1e3, "iters": it, "final_relres_fp64": rr, "opc": info.opc,
+                     "levels": [int(info.n[l]) for l in range(info.levels)], "setup_ms": info.setup_ms,
+                     "smoothing_phase_ms": info.setup_phase_ms[10], "solve_ms": info.solve_ms,
+                     "speedup_vs_plain_fp64": fp64_ms / ms}
+    return {"legs": out, "steps": k, "settings": "m=3, smoothed P on every level (theta 4/3), Chebyshev degree 8, "
+                                                 "coarse CG 1e-4 / 30 its, FCG; rtol as the bench (the paper: 1e-6)"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -848,6 +928,13 @@ def run_ours(args):
         if not args.no_learned and not args.no_mixed:
             learned = learned_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, ref_u, ms_per_step, m_ms)
 
+        smoothing = None
+        if not args.no_smoothing:
+            smoothing = smoothing_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, ms_per_step)
+        paper_cfg = None
+        if not args.no_paper_config:
+            paper_cfg = paper_config_leg(args, A, I, torch, np, stream, dist, rp, ci, va, F, ms_per_step)
+
         batched = None
         if not args.no_batched:
             batched = batched_leg(args, A, I, torch, np, stream, dist, rank, world)
@@ -905,7 +992,8 @@ def run_ours(args):
             "kernel_timing": "CUDA event-record nodes on the library's stream around each finest-level pass "
                              "inside the iteration graph, over as many profiled steps run right after the "
                              "timed (unprofiled) steps",
-            "learned": learned, "batched": batched, "annulus_learned": annulus}
+            "learned": learned, "batched": batched, "annulus_learned": annulus,
+            "prolongator_smoothing": smoothing, "paper_configuration": paper_cfg}
     if mixed is not None:
         mixed["roofline"]["peak"] = peak
         mixed["roofline"]["frac"] = (mixed["roofline"]["achieved"] or 0.0) / peak

@@ -128,6 +128,11 @@ typedef struct {
                                     with flexible = 1 (0) */
     double coarse_tol;           /* coarse CG: stop once ||r|| <= coarse_tol ||f|| (0.0001) */
     int32_t coarse_maxit;        /* coarse CG: at most this many iterations (30) */
+    int32_t autotune;            /* 1: at setup, time the finest level's q = K p pass in each available
+                                    layout (sliced slabs with every supported warps-per-block count in
+                                    FP64, the staged slabs in mixed precision, CSR row groups) and keep
+                                    the fastest for all three passes; cached per process by the
+                                    matrix shape, so later setups of that shape do not time (0) */
 } amg_opts;
 
 #define AMG_MAX_LEVELS 32
@@ -168,6 +173,8 @@ typedef struct {
                               solve (0 when the hierarchy's graph was reused) */
     int32_t smoothed[AMG_MAX_LEVELS]; /* 1 where the level's prolongator is smoothed */
     int64_t p_nnz[AMG_MAX_LEVELS];    /* stored entries of each level's prolongator */
+    int32_t sell64_warps;  /* warps per block of the FP64 sliced passes (0 when not in use) */
+    double tune_ms;        /* host time the setup spent autotuning (0: not asked, or a cached choice) */
 } amg_info;
 
 typedef struct amg_hierarchy amg_hierarchy;

@@ -48,7 +48,8 @@ class AmgOpts(ctypes.Structure):
                 ("matrix_format", ctypes.c_int32), ("mpnn_weights", ctypes.c_void_p), ("mpnn_bf16", ctypes.c_int32),
                 ("smooth_levels", ctypes.c_int32), ("smooth_omega", ctypes.c_double),
                 ("smooth_theta", ctypes.c_void_p), ("cheb_degree", ctypes.c_int32),
-                ("coarse_solver", ctypes.c_int32), ("coarse_tol", ctypes.c_double), ("coarse_maxit", ctypes.c_int32)]
+                ("coarse_solver", ctypes.c_int32), ("coarse_tol", ctypes.c_double), ("coarse_maxit", ctypes.c_int32),
+                ("autotune", ctypes.c_int32)]
 
 
 class AmgInfo(ctypes.Structure):
@@ -61,7 +62,8 @@ class AmgInfo(ctypes.Structure):
                 ("staged_passes", ctypes.c_int32), ("staged_slots", ctypes.c_int64),
                 ("staged_buffers", ctypes.c_int32 * 2), ("staged_window_bytes", ctypes.c_int32),
                 ("staged_level1", ctypes.c_int32), ("graph_build_ms", ctypes.c_double),
-                ("smoothed", ctypes.c_int32 * AMG_MAX_LEVELS), ("p_nnz", ctypes.c_int64 * AMG_MAX_LEVELS)]
+                ("smoothed", ctypes.c_int32 * AMG_MAX_LEVELS), ("p_nnz", ctypes.c_int64 * AMG_MAX_LEVELS),
+                ("sell64_warps", ctypes.c_int32), ("tune_ms", ctypes.c_double)]
 
 
 class AmgError(RuntimeError):

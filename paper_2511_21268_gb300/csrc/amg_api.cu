@@ -372,6 +372,114 @@ int build_runs(amg_hierarchy* h, Level& L) {
     return AMG_OK;
 }
 
+// ------------------------------------------------------------ autotuning
+// The finest level's matrix passes have several layouts (sliced slabs with
+// a chosen number of warps per block in FP64; staged slabs in mixed
+// precision; CSR row groups).  With opts.autotune the setup times the
+// q = K p pass of each candidate on the hierarchy's own matrix and vectors
+// (CUDA events on its stream: one warm-up and five timed launches each)
+// and keeps the fastest; the three passes of an iteration share the layout.
+// The choice is cached for the process by the matrix shape, so later setups
+// of the same shape apply it without timing.
+struct TuneKey {
+    int n;
+    int64_t nnz;
+    int mixed, stream, sell64, lm;
+    bool operator==(const TuneKey& o) const {
+        return n == o.n && nnz == o.nnz && mixed == o.mixed && stream == o.stream && sell64 == o.sell64 && lm == o.lm;
+    }
+};
+struct TuneChoice {
+    int rowgroups;  // 1: CSR row groups
+    int warps;      // FP64 sliced passes: warps per block
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, TuneChoice>> g_tune_cache;
+
+int autotune(amg_hierarchy* h) {
+    if (!h->sell64 && !h->stream) return AMG_OK;  // one layout only
+    const auto t0 = std::chrono::steady_clock::now();
+    const TuneKey key{h->lev[0].A.n, h->lev[0].A.nnz, h->mixed, h->stream, h->sell64, h->sell[0].lm};
+    TuneChoice choice{0, h->sell64_warps};
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (const auto& kv : g_tune_cache)
+            if (kv.first == key) {
+                choice = kv.second;
+                cached = true;
+            }
+    }
+    if (!cached) {
+        cudaStream_t s = h->s;
+        const int n = h->lev[0].A.n;
+        CK(cudaMemsetAsync(h->p, 0, sizeof(double) * n, s));
+        CK(cudaMemsetAsync(h->r, 0, sizeof(double) * n, s));
+        if (h->p32) CK(cudaMemsetAsync(h->p32, 0, sizeof(float) * n, s));
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        struct Ev {
+            cudaEvent_t a, b;
+            ~Ev() {
+                cudaEventDestroy(a);
+                cudaEventDestroy(b);
+            }
+        } ev{e0, e1};
+        double* slots = h->partials;  // the pq / pr partial slots are rewritten by the first solve
+        auto timed = [&](auto&& launch, float* ms) -> int {
+            CK(launch());
+            CK(cudaEventRecord(e0, s));
+            for (int k = 0; k < 5; k++) CK(launch());
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaEventElapsedTime(ms, e0, e1));
+            return AMG_OK;
+        };
+        (void)slots;
+        const int save_sell64 = h->sell64, save_stream = h->stream, save_warps = h->sell64_warps;
+        float best = 1e30f, ms = 0.f;
+        if (save_sell64) {
+            int lo, hi;
+            sell64_warp_range(&lo, &hi);
+            for (int w = lo; w <= hi; w++) {
+                h->sell64_warps = w;
+                RC(timed([&] { return sell64_spmv_pq(h, h->p, h->r, h->q, h->partials, h->partials, 0, s); }, &ms));
+                if (ms < best) {
+                    best = ms;
+                    choice = TuneChoice{0, w};
+                }
+            }
+        } else {
+            RC(timed([&] {
+                return h->stream == 2 ? sell_spmv_pq(h, h->p32, h->p, h->r, h->q, h->partials, h->partials, 0, s)
+                                      : launch_stream_spmv_pq(h, h->p32, h->p, h->r, h->q, h->partials, h->partials,
+                                                              0, s);
+            }, &ms));
+            best = ms;
+            choice = TuneChoice{0, save_warps};
+        }
+        h->sell64 = 0;
+        h->stream = 0;
+        RC(timed([&] { return launch_rowgroup_pq(h, s); }, &ms));
+        h->sell64 = save_sell64;
+        h->stream = save_stream;
+        h->sell64_warps = save_warps;
+        if (ms < best) choice = TuneChoice{1, save_warps};
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache.push_back({key, choice});
+    }
+    if (choice.rowgroups) {
+        h->sell64 = 0;
+        h->stream = 0;
+        h->sell[1].on = 0;  // level 1's sliced passes follow the finest level's staged layout
+    } else {
+        h->sell64_warps = choice.warps;
+    }
+    h->tune_ms = cached ? 0.0 : std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return AMG_OK;
+}
+
 int build(amg_hierarchy* h, const amg_csr* K) {
     cudaStream_t s = h->s;
     const int n0 = K->n;
@@ -576,6 +684,7 @@ int build(amg_hierarchy* h, const amg_csr* K) {
         RC(sell_prepare_level1(h, h->flag));
         RC(sell64_prepare(h, h->flag));
     }
+    if (h->o.autotune && h->o.cheb_degree == 0) RC(autotune(h));
     if (h->o.mpnn_weights) {
         phase(h, 9);
         RC(mpnn_setup_join(h));
@@ -627,6 +736,8 @@ void fill_info(amg_hierarchy* h) {
                             : h->stream ? h->stream_xbytes
                                         : 0;
     I.staged_level1 = h->sell[1].on;
+    I.sell64_warps = h->sell64 ? h->sell64_warps : 0;
+    I.tune_ms = h->tune_ms;
     I.opc = tot / (double)h->lev[0].A.nnz;
     // algorithmic bytes: one matrix pass = nnz (value + 4) + (n + 1) 8 + x read + y write
     // (value and vector sizes of the V-cycle precision: 8 / 8 in FP64, 4 / 4 in
@@ -734,6 +845,7 @@ int check_opts(const amg_opts& o) {
     if (o.cheb_degree > 0 && o.mpnn_weights) return AMG_ERR_ARG;  // the network damps l1-Jacobi sweeps
     if (o.coarse_solver < 0 || o.coarse_solver > 1 || !(o.coarse_tol >= 0.0) || o.coarse_maxit < 1)
         return AMG_ERR_ARG;
+    if (o.autotune < 0 || o.autotune > 1) return AMG_ERR_ARG;
     return AMG_OK;
 }
 
@@ -768,6 +880,7 @@ int amg_opts_default(amg_opts* o) {
     o->coarse_solver = 0;
     o->coarse_tol = 1e-4;
     o->coarse_maxit = 30;
+    o->autotune = 0;
     return AMG_OK;
 }
 

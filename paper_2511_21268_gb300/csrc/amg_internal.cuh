@@ -221,6 +221,7 @@ struct amg_hierarchy {
     // level 1 in mixed precision (plain CSR, each entry a run of length 1)
     amg::SellLevel sell[2];
     int sell64 = 0;        // plain FP64 solve: the finest-level passes run on sell[0] (FP64 values)
+    double tune_ms = 0.0;  // host time of the setup's autotuning (0 when skipped or cached)
     int sell64_warps = 0;  // warps per block of those passes
     // multi-system solves
     amg::MultiWork* mw = nullptr;
@@ -293,6 +294,7 @@ cudaError_t enqueue_vcycle_standalone(amg_hierarchy* h, cudaStream_t s);
 cudaError_t enqueue_pcg_start(amg_hierarchy* h, cudaStream_t s);
 cudaError_t enqueue_pcg_iteration(amg_hierarchy* h, cudaStream_t s);
 cudaError_t launch_final_residual(amg_hierarchy* h, cudaStream_t s);
+cudaError_t launch_rowgroup_pq(amg_hierarchy* h, cudaStream_t s);
 double* final_residual_slot(amg_hierarchy* h);
 // multi_solve.cu
 cudaError_t enqueue_multi_start(amg_hierarchy* h, cudaStream_t s);
@@ -317,6 +319,7 @@ int sell_prepare_level1(amg_hierarchy* h, int* scratch);
 cudaError_t sell_resid1(amg_hierarchy* h, const float* f, const float* x, float* rbuf, cudaStream_t s);
 cudaError_t sell_upy1(amg_hierarchy* h, const float* f, const float* x, const float* invd, float* y, cudaStream_t s);
 int sell64_prepare(amg_hierarchy* h, int* scratch);
+void sell64_warp_range(int* lo, int* hi);
 cudaError_t sell64_spmv_pq(amg_hierarchy* h, const double* p, const double* r, double* q, double* part_pq,
                            double* part_pr, int flexible, cudaStream_t s);
 cudaError_t sell64_resid(amg_hierarchy* h, const double* f, const double* x, double* rbuf, cudaStream_t s);

@@ -1262,6 +1262,11 @@ int sell64_prepare(amg_hierarchy* h, int* scratch) {
     return AMG_OK;
 }
 
+void sell64_warp_range(int* lo, int* hi) {
+    *lo = kS64MinWarps;
+    *hi = kS64MaxWarps;
+}
+
 cudaError_t sell64_spmv_pq(amg_hierarchy* h, const double* p, const double* r, double* q, double* part_pq,
                            double* part_pr, int flexible, cudaStream_t s) {
     return sell64_launch(h, p, Epi64PQ{p, r, q, flexible}, part_pq, flexible ? part_pr : nullptr, s);

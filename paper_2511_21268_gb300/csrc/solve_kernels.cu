@@ -1020,6 +1020,28 @@ cudaError_t enqueue_pcg_iteration(amg_hierarchy* h, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The row-group q = K p pass of the finest level (the layout used when no
+// sliced or staged copy is in use), for the setup's autotuning.
+cudaError_t launch_rowgroup_pq(amg_hierarchy* h, cudaStream_t s) {
+    Level& L0 = h->lev[0];
+    const int n = L0.A.n;
+    const int rpw = rows_per_warp(n, h->num_sms), nb = row_blocks(n, rpw);
+    with_rpw(rpw, [&](auto R) {
+        constexpr int RPW = decltype(R)::value;
+        if (h->mixed)
+            with_mat(L0, static_cast<const float*>(L0.val32), [&](auto mat) {
+                launch_pdl(k_spmv_pq<RPW, float, decltype(mat), float>, nb, kBlock, 0, s, n, mat, h->p32, h->p,
+                           h->r, h->q, slot(h, S_PQ), slot(h, S_PR), 0, h->st);
+            });
+        else
+            with_mat(L0, static_cast<const double*>(L0.A.val), [&](auto mat) {
+                launch_pdl(k_spmv_pq<RPW, double, decltype(mat), double>, nb, kBlock, 0, s, n, mat, h->p, h->p,
+                           h->r, h->q, slot(h, S_PQ), slot(h, S_PR), 0, h->st);
+            });
+    });
+    return cudaGetLastError();
+}
+
 // ||F - K x|| and ||F|| into slot(S_OUT)[0..1] (FP64, recomputed).
 cudaError_t launch_final_residual(amg_hierarchy* h, cudaStream_t s) {
     AMG_TRY(launch_residual(h, h->q, false, S_RR, true, nullptr, s));

@@ -51,6 +51,10 @@ def lib():
         L.iga_nnz.restype = i64
         L.iga_assemble_kron.argtypes = [i32, i32, i32, i32, P, P, P]
         L.iga_assemble_kron.restype = i32
+        L.iga_kron_box_nnz.argtypes = [i32, i32, P, P, P]
+        L.iga_kron_box_nnz.restype = i32
+        L.iga_assemble_kron_box.argtypes = [i32, i32, P, P, P, P, P]
+        L.iga_assemble_kron_box.restype = i32
         L.iga_load_sine.argtypes = [i32, i32, i32, i32, i32, P]
         L.iga_load_sine.restype = i32
         L.iga_assemble_elem.argtypes = [i32, i32, i32, i32, i32, i32, i32, dbl, dbl, u64, i32, P, P, P, P]
@@ -245,6 +249,108 @@ def batch_instances(seed: int = 20251126, count: int = 48, d: int = 2) -> list[P
         out.append(poisson_box_random_rhs(d, n, p, seed=seed + 1 + k))
         out[-1].meta["instance"] = k
     return out
+
+
+# ------------------------------------- cube with mixed boundary conditions
+def assemble_kron_box(n: int, p: int, lo, hi):
+    """3-D unit cube stiffness restricted to the DOFs lo[k] <= i_k < hi[k]
+    (full tensor indices per direction, x fastest)."""
+    lo = np.ascontiguousarray(lo, np.int32)
+    hi = np.ascontiguousarray(hi, np.int32)
+    z = ctypes.c_int64()
+    if lib().iga_kron_box_nnz(n, p, _p(lo), _p(hi), ctypes.byref(z)) != 0:
+        raise ValueError("bad arguments")
+    N = int(np.prod(hi - lo))
+    rowptr = np.empty(N + 1, np.int64)
+    col = np.empty(z.value, np.int32)
+    val = np.empty(z.value, np.float64)
+    if lib().iga_assemble_kron_box(n, p, _p(lo), _p(hi), _p(rowptr), _p(col), _p(val)) != 0:
+        raise ValueError("assembly failed")
+    return rowptr, col, val
+
+
+def load_1d(n: int, p: int, g, nq: int | None = None) -> np.ndarray:
+    """b_a = integral over [0, 1] of g(x) N_a(x) (Gauss, nq points per element)."""
+    q = nq or p + 3
+    gx, gw = gauss_legendre(q)
+    b = np.zeros(n + p)
+    for e in range(n):
+        for t in range(q):
+            x = (e + 0.5 * (gx[t] + 1.0)) / n
+            v, _ = bspline_all(n, p, x)
+            b += v * (g(x) * 0.5 * gw[t] / n)
+    return b
+
+
+def _apply_kron3(A, B, C, v):
+    """(A (x) B (x) C) v for v indexed [z][y][x] (C acts on x, B on y, A on z)."""
+    return np.einsum("ai,bj,ck,ijk->abc", A, B, C, v, optimize=True)
+
+
+def cube_mixed_bc(n: int, p: int) -> Problem:
+    """The paper's cube test case (Sec. 5): -Laplace u = f on [0,1]^3 with
+    f = -exp(x+z) sin(y), Dirichlet data g_D = exp(x+z) sin(y) on x = 0,
+    x = 1, y = 0 and Neumann data on y = 1 (exp(x+z) cos(y)), z = 0
+    (-exp(x+z) sin(y)) and z = 1 (exp(x+z) sin(y)); exact solution
+    u = exp(x+z) sin(y).  B-splines of degree p, maximal regularity, n
+    elements per direction: (n+p-2)(n+p-1)(n+p) unknowns (x: both ends
+    eliminated, y: one, z: none), the paper's matrix sizes.
+
+    Non-homogeneous Dirichlet data by lifting: u_D = the L2 projection of
+    g_D onto the tensor spline space (g_D is separable, so it is the tensor
+    product of the 1-D projections), kept on the Dirichlet DOFs; the system
+    is K_ff u_f = F_f - K_fD u_D with F = the load plus the Neumann face
+    integrals (all separable products of 1-D integrals)."""
+    nb = n + p
+    K1, M1 = one_d_matrices(n, p)
+    ex = load_1d(n, p, math.exp)
+    sn = load_1d(n, p, math.sin)
+    e_first, e_last = np.zeros(nb), np.zeros(nb)
+    e_first[0], e_last[-1] = 1.0, 1.0  # the only basis functions nonzero at 0 and 1
+    # load (f = -exp(x) sin(y) exp(z)) and Neumann terms; tensors indexed [z][y][x]
+    F = -np.einsum("a,b,c->abc", ex, sn, ex)
+    F += math.cos(1.0) * np.einsum("a,b,c->abc", ex, e_last, ex)       # y = 1: exp(x+z) cos(1)
+    F += -np.einsum("a,b,c->abc", e_first, sn, ex)                    # z = 0: -exp(x) sin(y)
+    F += math.e * np.einsum("a,b,c->abc", e_last, sn, ex)             # z = 1: exp(x+1) sin(y)
+    # lifting: L2 projection of g_D = exp(x) sin(y) exp(z), kept on the Dirichlet DOFs
+    import scipy.linalg as sl
+
+    Px = sl.solve(M1, ex, assume_a="pos")
+    Py = sl.solve(M1, sn, assume_a="pos")
+    U = np.einsum("a,b,c->abc", Px, Py, Px)
+    dmask = np.zeros((nb, nb, nb), bool)
+    dmask[:, :, 0] = dmask[:, :, -1] = True  # x = 0, x = 1
+    dmask[:, 0, :] = True                    # y = 0
+    uD = np.where(dmask, U, 0.0)
+    KuD = (_apply_kron3(M1, M1, K1, uD) + _apply_kron3(M1, K1, M1, uD)) + _apply_kron3(K1, M1, M1, uD)
+    R = F - KuD
+    lo, hi = (1, 1, 0), (nb - 1, nb, nb)  # kept index ranges in x, y, z
+    rowptr, col, val = assemble_kron_box(n, p, lo, hi)
+    Ff = np.ascontiguousarray(R[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]].reshape(-1))
+    prob = Problem(len(rowptr) - 1, rowptr, col, val, Ff,
+                   {"kind": "cube_mixed_bc", "d": 3, "n": n, "p": p})
+    prob.lift = uD
+    prob.free = (lo, hi)
+    return prob
+
+
+def cube_mixed_bc_l2_error(prob: Problem, u_free: np.ndarray, nq: int | None = None) -> float:
+    """||u_h - u||_L2 on the cube for u = exp(x+z) sin(y), u_h the spline
+    with the free coefficients u_free and the lifting on the Dirichlet DOFs."""
+    n, p = prob.meta["n"], prob.meta["p"]
+    nb = n + p
+    lo, hi = prob.free
+    C = prob.lift.copy()
+    C[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = np.asarray(u_free).reshape(hi[2] - lo[2], hi[1] - lo[1], hi[0] - lo[0])
+    q = nq or p + 3
+    gx, gw = gauss_legendre(q)
+    pts = np.array([(e + 0.5 * (gx[t] + 1.0)) / n for e in range(n) for t in range(q)])
+    wts = np.array([0.5 * gw[t] / n for e in range(n) for t in range(q)])
+    B = np.stack([bspline_all(n, p, x)[0] for x in pts])  # [point][basis]
+    uh = np.einsum("ai,bj,ck,ijk->abc", B, B, B, C, optimize=True)
+    ue = np.einsum("a,b,c->abc", np.exp(pts), np.sin(pts), np.exp(pts))
+    w3 = np.einsum("a,b,c->abc", wts, wts, wts)
+    return float(np.sqrt(np.sum(w3 * (uh - ue) ** 2)))
 
 
 ANNULUS_KAPPA = dict(M=256, ell=0.2, sigma=1.0)

@@ -265,6 +265,67 @@ static inline int64_t pat_pos(int d, int m, int p, int i1, int i2, int i3, int j
     return r;
 }
 
+/* ------------------------------------------ box with per-direction DOFs ---- */
+/* 3-D unit cube, K restricted to the DOFs (i1, i2, i3) with lo[k] <= i_k <
+ * hi[k] (indices of the full tensor space of n + p functions per direction,
+ * x fastest): the system of a box whose faces carry Dirichlet data on some
+ * sides only (the eliminated faces are the excluded index planes).  Same
+ * entry expression as iga_assemble_kron; rows and columns numbered
+ * (i1 - lo1) + m1 ((i2 - lo2) + m2 (i3 - lo3)), columns sorted. */
+int iga_kron_box_nnz(int n, int p, const int* lo, const int* hi, int64_t* nnz) {
+    if (p < 1 || p > IGA_MAXP || n < 1) return -1;
+    const int nb = n + p;
+    int64_t prod = 1;
+    for (int k = 0; k < 3; k++) {
+        if (lo[k] < 0 || hi[k] > nb || hi[k] <= lo[k]) return -1;
+        const int m = hi[k] - lo[k];
+        int64_t c = 0;
+        for (int i = 0; i < m; i++) {
+            const int a = i - p < 0 ? 0 : i - p, b = i + p > m - 1 ? m - 1 : i + p;
+            c += b - a + 1;
+        }
+        prod *= c;
+    }
+    *nnz = prod;
+    return 0;
+}
+
+int iga_assemble_kron_box(int n, int p, const int* lo, const int* hi, int64_t* rowptr, int32_t* col, double* val) {
+    int64_t z;
+    if (iga_kron_box_nnz(n, p, lo, hi, &z) != 0) return -1;
+    const int nb = n + p;
+    const int m1 = hi[0] - lo[0], m2 = hi[1] - lo[1], m3 = hi[2] - lo[2];
+    double* K1 = (double*)malloc(sizeof(double) * nb * nb);
+    double* M1 = (double*)malloc(sizeof(double) * nb * nb);
+    if (!K1 || !M1) { free(K1); free(M1); return -2; }
+    iga_1d_matrices(n, p, p + 1, K1, M1);
+    const int64_t N = (int64_t)m1 * m2 * m3;
+    int64_t pos = 0;
+    rowptr[0] = 0;
+    for (int64_t I = 0; I < N; I++) {
+        const int i1 = (int)(I % m1), i2 = (int)((I / m1) % m2), i3 = (int)(I / ((int64_t)m1 * m2));
+        const int a1 = i1 - p < 0 ? 0 : i1 - p, b1 = i1 + p > m1 - 1 ? m1 - 1 : i1 + p;
+        const int a2 = i2 - p < 0 ? 0 : i2 - p, b2 = i2 + p > m2 - 1 ? m2 - 1 : i2 + p;
+        const int a3 = i3 - p < 0 ? 0 : i3 - p, b3 = i3 + p > m3 - 1 ? m3 - 1 : i3 + p;
+        const int g1 = i1 + lo[0], g2 = i2 + lo[1], g3 = i3 + lo[2];
+        for (int j3 = a3; j3 <= b3; j3++)
+            for (int j2 = a2; j2 <= b2; j2++)
+                for (int j1 = a1; j1 <= b1; j1++) {
+                    const int h1 = j1 + lo[0], h2 = j2 + lo[1], h3 = j3 + lo[2];
+                    const double kx = K1[g1 * nb + h1], mx = M1[g1 * nb + h1];
+                    const double ky = K1[g2 * nb + h2], my = M1[g2 * nb + h2];
+                    const double kz = K1[g3 * nb + h3], mz = M1[g3 * nb + h3];
+                    col[pos] = (int32_t)(j1 + (int64_t)m1 * (j2 + (int64_t)m2 * j3));
+                    val[pos] = ((kx * my) * mz + (mx * ky) * mz) + (mx * my) * kz;
+                    pos++;
+                }
+        rowptr[I + 1] = pos;
+    }
+    free(K1);
+    free(M1);
+    return pos == z ? 0 : -3;
+}
+
 /* ------------------------------------------------- Kronecker assembly ---- */
 /* K = K1 (x) M1 (x) M1 + M1 (x) K1 (x) M1 + M1 (x) M1 (x) K1 on the unit cube
  * (two terms on the unit square), restricted to the DOF set.  The entry for

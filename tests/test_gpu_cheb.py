@@ -101,3 +101,33 @@ def test_papers_configuration_trend():
     for p in (3, 4):
         its = [out[(p, n)][0] for n in (8, 12, 16, 24)]
         assert max(its) <= 2 * min(its) + 4
+
+
+def test_papers_cube_table1_trend():
+    """The paper's own cube (Sec. 5: mixed Dirichlet / Neumann data, its
+    matrix sizes) with its solver configuration, against its Table 1
+    (tests/golden/cube_table1.txt): sizes equal, iteration counts printed
+    beside the paper's (trend, not parity: the Chebyshev weights and the
+    aggregation's matching differ), OPC close, and the discrete solution
+    accurate (L2 error against exp(x+z) sin(y))."""
+    from tests.conftest import read_golden
+
+    deg = {3: 8, 4: 12, 5: 14, 6: 16}
+    rows = []
+    for k, p, size, its_paper, opc_paper in read_golden("cube_table1.txt"):
+        k, p = int(k), int(p)
+        if k > 48 or (p >= 5 and k > 24):
+            continue
+        prob = I.cube_mixed_bc(k, p)
+        assert prob.n == int(size)
+        H = A.Hierarchy(dev(prob.rowptr), dev(prob.col), dev(prob.val), match_passes=3, smooth_levels=-1,
+                        cheb_degree=deg[p], coarse_solver=1, flexible=1)
+        g = H.solve(dev(prob.F), rtol=1e-6)
+        assert g["status"] == 0
+        err = I.cube_mixed_bc_l2_error(prob, g["u"].cpu().numpy())
+        rows.append((k, p, prob.n, g["iters"], int(its_paper), round(H.info.opc, 2), float(opc_paper), err))
+        assert g["iters"] <= 3 * int(its_paper) + 5
+        assert err < 1e-3
+    print("k p size iterations (paper) OPC (paper) L2 error:")
+    for r in rows:
+        print("  %d %d %d %d (%d) %.2f (%.2f) %.1e" % r)

@@ -169,3 +169,37 @@ def test_batch_params_seeded():
     assert all(p in (2, 3, 4) and 32 <= n <= 256 for p, n in pn)
     assert pn == I.batch_params(20251126, 48)
     assert len(set(p for p, _ in pn)) == 3
+
+
+# ------------------------------------------------ mixed-BC cube (Sec. 5) ----
+def test_cube_mixed_bc_sizes_are_the_papers():
+    """(k+p)(k+p-1)(k+p-2) unknowns: the matrix sizes of the paper's Table 1
+    (tests/golden/cube_table1.txt), computed without assembling."""
+    from tests.conftest import read_golden
+
+    for k, p, size, _, _ in read_golden("cube_table1.txt"):
+        k, p, size = int(k), int(p), int(size)
+        assert (k + p) * (k + p - 1) * (k + p - 2) == size
+    prob = I.cube_mixed_bc(12, 3)
+    assert prob.n == 2730
+    K = prob.to_scipy()
+    assert (K != K.T).nnz == 0  # bitwise symmetric
+    assert np.all(np.diff(prob.rowptr) > 0)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_cube_mixed_bc_converges_at_order_p_plus_1(p):
+    """The discrete solution (direct solve) approaches u = exp(x+z) sin(y)
+    in L2 at rate p+1: the load, the three Neumann face integrals and the
+    Dirichlet lifting are all right (a wrong sign or face breaks the rate)."""
+    import scipy.sparse.linalg as spl
+
+    errs = []
+    ns = [4, 8, 16]
+    for n in ns:
+        prob = I.cube_mixed_bc(n, p)
+        u = spl.spsolve(prob.to_scipy().tocsc(), prob.F)
+        errs.append(I.cube_mixed_bc_l2_error(prob, u))
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert errs[-1] < 1e-4
+    assert abs(rates[-1] - (p + 1)) < 0.4, (errs, rates)

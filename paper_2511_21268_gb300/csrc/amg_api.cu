@@ -308,7 +308,14 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
     // else the candidate-sorting kernels
     const int words = (maxspan + 31) / 32 + 1;
     const bool bitmap = 8.0 * words + 16.0 * maxcand <= kBitmapSmem;
-    if (!bitmap && cap > kMaxGalerkinCap) return AMG_ERR_ROW_TOO_LONG;
+    if (!bitmap && cap > kMaxGalerkinCap) {
+        // rows too wide for both kernels (dense coarse levels of smoothed
+        // hierarchies): the row-merge SpGEMMs, same product up to rounding
+        RC(galerkin_pass_spgemm(h, A, P.agg, P.pval, mem0, mem1, nc, C));
+        h->galerkin_spgemm_passes++;
+        phase(h, 1);
+        return AMG_OK;
+    }
     C.n = nc;
     RC(dalloc(h, &C.rowptr, (size_t)nc + 1));
     int64_t *rowcnt, *scr64;

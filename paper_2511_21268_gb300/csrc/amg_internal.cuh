@@ -222,6 +222,7 @@ struct amg_hierarchy {
     amg::SellLevel sell[2];
     int sell64 = 0;        // plain FP64 solve: the finest-level passes run on sell[0] (FP64 values)
     double tune_ms = 0.0;  // host time of the setup's autotuning (0 when skipped or cached)
+    int galerkin_spgemm_passes = 0;  // pass Galerkin products done by the SpGEMM path (too-wide rows)
     int sell64_warps = 0;  // warps per block of those passes
     // multi-system solves
     amg::MultiWork* mw = nullptr;
@@ -336,6 +337,11 @@ int smooth_level(amg_hierarchy* h, int l, DevCSR& Kc);
 // smooth_kernels.cu: level 0's P_bar for new per-row weights theta (device,
 // FP64) and the coarse matrix P_bar^T K P_bar rewritten in place (same pattern)
 int smooth_recompute(amg_hierarchy* h, const double* theta);
+// smooth_kernels.cu: a matching pass's Galerkin product P^T A P by the
+// row-merge SpGEMMs (rows too wide for the bitmap and sorting kernels); C's
+// arrays are recorded in h->allocs
+int galerkin_pass_spgemm(amg_hierarchy* h, const DevCSR& A, const int32_t* agg, const double* pval,
+                         const int32_t* mem0, const int32_t* mem1, int nc, DevCSR& C);
 template <typename A>
 void sp_restrict(const Level& F, const Level& C, const A* r, A* fc, A* xc, const A* invdc, const SolveState* st,
                  cudaStream_t s);

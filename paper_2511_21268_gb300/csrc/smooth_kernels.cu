@@ -235,6 +235,29 @@ __global__ void k_sp_widen(int n, const int32_t* __restrict__ in, int64_t* out) 
     if (i < n) out[i] = in[i];
 }
 
+// P^T of a matching pass (coarse row I: member mem0[I], and mem1[I] when
+// >= 0; ascending) as CSR: counts, then columns and values
+__global__ void k_sp_pairs_count(int nc, const int32_t* __restrict__ mem1, int64_t* cnt) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I < nc) cnt[I] = mem1[I] >= 0 ? 2 : 1;
+}
+
+__global__ void k_sp_pairs_fill(int nc, const int32_t* __restrict__ mem0, const int32_t* __restrict__ mem1,
+                                const double* __restrict__ pval, const int64_t* __restrict__ rp, int32_t* ci,
+                                double* v) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    const int64_t k = rp[I];
+    const int a = mem0[I], b = mem1[I];
+    const int lo = (b >= 0 && b < a) ? b : a, hi = (b >= 0 && b < a) ? a : b;
+    ci[k] = lo;
+    v[k] = pval[lo];
+    if (b >= 0) {
+        ci[k + 1] = hi;
+        v[k + 1] = pval[hi];
+    }
+}
+
 // ---------------------------------------------------------------- V-cycle
 // f_c[I] = sum over P_bar^T row I of P_bar(a, I) r_a; x_c = f_c / d_c when
 // x_c is given (pre-smoothing of the next level from zero).
@@ -462,6 +485,58 @@ int smooth_level(amg_hierarchy* h, int l, DevCSR& Kc_out) {
     Kc_out = Kc;
     F.smoothed = 1;
     return AMG_OK;
+}
+
+int galerkin_pass_spgemm(amg_hierarchy* h, const DevCSR& A, const int32_t* agg, const double* pval,
+                         const int32_t* mem0, const int32_t* mem1, int nc, DevCSR& C) {
+    cudaStream_t s = h->s;
+    const int n = A.n;
+    int* dflag = h->flag + 8;
+    if (cudaMemsetAsync(h->flag + 10, 0, sizeof(int), s) != cudaSuccess) return AMG_ERR_CUDA;
+    struct Tmp {
+        void* p[5] = {};
+        cudaStream_t s;
+        ~Tmp() {
+            for (void* q : p)
+                if (q) cudaFreeAsync(q, s);
+        }
+    } tmp{{}, s};
+    int64_t *scr = nullptr, *prp = nullptr, *trp = nullptr, *cnt = nullptr;
+    int32_t* tci = nullptr;
+    double* tv = nullptr;
+    const size_t scr_n = scan64_scratch(std::max(n, nc)) + 1;
+    if (dev_alloc((void**)&scr, sizeof(int64_t) * scr_n, s) != cudaSuccess) return AMG_ERR_NOMEM;
+    tmp.p[0] = scr;
+    if (dev_alloc((void**)&prp, sizeof(int64_t) * ((size_t)n + 1), s) != cudaSuccess) return AMG_ERR_NOMEM;
+    tmp.p[1] = prp;
+    if (dev_alloc((void**)&trp, sizeof(int64_t) * ((size_t)nc + 1), s) != cudaSuccess) return AMG_ERR_NOMEM;
+    tmp.p[2] = trp;
+    if (dev_alloc((void**)&cnt, sizeof(int64_t) * ((size_t)nc + 1), s) != cudaSuccess) return AMG_ERR_NOMEM;
+    tmp.p[3] = cnt;
+    if (dev_alloc((void**)&tci, sizeof(int32_t) * (2 * (size_t)nc + 8), s) != cudaSuccess) return AMG_ERR_NOMEM;
+    tmp.p[4] = tci;
+    if (dev_alloc((void**)&tv, sizeof(double) * (2 * (size_t)nc + 8), s) != cudaSuccess) return AMG_ERR_NOMEM;
+    struct FreeV {
+        double* p;
+        cudaStream_t s;
+        ~FreeV() { cudaFreeAsync(p, s); }
+    } free_tv{tv, s};
+    k_sp_iota<<<AMG_GRID((n + 1 + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, prp);
+    k_sp_pairs_count<<<AMG_GRID((nc + kBlock - 1) / kBlock), kBlock, 0, s>>>(nc, mem1, cnt);
+    if (launch_scan64(cnt, trp, nc, scr, s) != cudaSuccess) return AMG_ERR_CUDA;
+    k_sp_pairs_fill<<<AMG_GRID((nc + kBlock - 1) / kBlock), kBlock, 0, s>>>(nc, mem0, mem1, pval, trp, tci, tv);
+    DevCSR T;
+    int rc = spgemm(h, n, A.rowptr, A.col, A.val, prp, agg, pval, SP_VALUES, T, dflag, scr);
+    if (rc == AMG_OK) rc = spgemm(h, nc, trp, tci, tv, T.rowptr, T.col, T.val, SP_UPPER, C, dflag, scr);
+    drop(h, T.rowptr);
+    drop(h, T.col);
+    drop(h, T.val);
+    if (rc != AMG_OK) return rc;
+    if (launch_galerkin_mirror(C, h->flag + 3, s) != cudaSuccess) return AMG_ERR_CUDA;
+    if (cudaMemcpyAsync(h->flag_host, h->flag + 10, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return AMG_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return AMG_ERR_CUDA;
+    return h->flag_host[0] ? AMG_ERR_CUDA : AMG_OK;
 }
 
 int smooth_recompute(amg_hierarchy* h, const double* theta) {

@@ -55,6 +55,8 @@ def lib():
         L.iga_kron_box_nnz.restype = i32
         L.iga_assemble_kron_box.argtypes = [i32, i32, P, P, P, P, P]
         L.iga_assemble_kron_box.restype = i32
+        L.iga_assemble_lshape.argtypes = [i32, i32, P, i32, i32, P, P, P, i64]
+        L.iga_assemble_lshape.restype = i32
         L.iga_load_sine.argtypes = [i32, i32, i32, i32, i32, P]
         L.iga_load_sine.restype = i32
         L.iga_assemble_elem.argtypes = [i32, i32, i32, i32, i32, i32, i32, dbl, dbl, u64, i32, P, P, P, P]
@@ -351,6 +353,131 @@ def cube_mixed_bc_l2_error(prob: Problem, u_free: np.ndarray, nq: int | None = N
     ue = np.einsum("a,b,c->abc", np.exp(pts), np.sin(pts), np.exp(pts))
     w3 = np.einsum("a,b,c->abc", wts, wts, wts)
     return float(np.sqrt(np.sum(w3 * (uh - ue) ** 2)))
+
+
+# ----------------------------------------------- three-patch L-shape
+# Patches (x offset, y offset) of the L-shaped cross-section: A = [0,1]^2,
+# B = [-1,0]x[0,1], C = [0,1]x[-1,0]; each times [0,1] in z.
+LSHAPE_PATCHES = ((0.0, 0.0), (-1.0, 0.0), (0.0, -1.0))
+
+
+def _lshape_lattice_offsets(m):
+    """Lattice offsets (gx, gy) of the patches A, B, C (see iga_gen.c)."""
+    return ((m - 1, m - 1), (0, m - 1), (m - 1, 0))
+
+
+def _lshape_u(x, y, z):
+    return np.exp(x) * np.sin(x * y) * np.cos(z)
+
+
+def _lshape_f(x, y, z):
+    return np.exp(x) * np.cos(z) * (-2.0 * np.cos(x * y) * y + np.sin(x * y) * (y * y + x * x))
+
+
+def _quad_1d(n, p, nq=None):
+    q = nq or p + 3
+    gx, gw = gauss_legendre(q)
+    pts = np.array([(e + 0.5 * (gx[t] + 1.0)) / n for e in range(n) for t in range(q)])
+    wts = np.array([0.5 * gw[t] / n for e in range(n) for t in range(q)])
+    B = np.stack([bspline_all(n, p, x)[0] for x in pts])  # [point][basis]
+    return pts, wts, B
+
+
+def lshape_mixed_bc(n: int, p: int) -> Problem:
+    """The paper's multipatch L-shaped test case (Sec. 2.3, Sec. 5): three
+    conforming unit-cube patches forming an L in (x, y) (A = [0,1]^2,
+    B = [-1,0]x[0,1], C = [0,1]x[-1,0]) times [0,1] in z, -Laplace u = f with
+    the exact solution u = exp(x) sin(xy) cos(z); Dirichlet data on the four
+    outer lateral faces and on z = 0, z = 1, Neumann data on the two
+    re-entrant faces (x = 0 for y < 0: -du/dx; y = 0 for x < 0: -du/dy).
+    Maximal regularity inside each patch, C^0 across the patch interfaces
+    (shared interface functions).  Unknowns (m-2)(m-1)(3m-5), m = n + p: the
+    paper's matrix sizes.  Dirichlet data by lifting (per-patch L2
+    projection of g_D, kept on the Dirichlet functions)."""
+    import scipy.linalg as sl
+
+    m = n + p
+    Lg = 2 * m - 1
+    offs = _lshape_lattice_offsets(m)
+    # lattice membership and the Dirichlet set (outer lateral edges; z = 0, 1)
+    inL = np.zeros((Lg, Lg), bool)
+    for ox, oy in offs:
+        inL[oy:oy + m, ox:ox + m] = True
+    keep2 = inL.copy()
+    keep2[:, 0] = keep2[:, Lg - 1] = False   # x = -1 (B), x = 1 (A, C)
+    keep2[0, :] = keep2[Lg - 1, :] = False   # y = -1 (C), y = 1 (A, B)
+    # stiffness of the free functions
+    nfree2 = int(keep2.sum())
+    N = nfree2 * (m - 2)
+    cap = N * (2 * p + 1) ** 3
+    rowptr = np.empty(N + 1, np.int64)
+    col = np.empty(cap, np.int32)
+    val = np.empty(cap, np.float64)
+    k2 = np.ascontiguousarray(keep2.astype(np.uint8).reshape(-1))
+    if lib().iga_assemble_lshape(n, p, _p(k2), 1, m - 1, _p(rowptr), _p(col), _p(val), cap) != 0:
+        raise ValueError("assembly failed")
+    z = int(rowptr[-1])
+    col, val = col[:z].copy(), val[:z].copy()
+    # per-patch load of f and L2 projection of g_D; global tensors [z][gy][gx]
+    K1, M1 = one_d_matrices(n, p)
+    Minv = sl.inv(M1)
+    pts, wts, B = _quad_1d(n, p)
+    Fg = np.zeros((m, Lg, Lg))
+    Ug = np.zeros((m, Lg, Lg))
+    seen = np.zeros((m, Lg, Lg), bool)
+    for (wx, wy), (ox, oy) in zip(LSHAPE_PATCHES, offs):
+        X, Y, Z = np.meshgrid(pts + wx, pts + wy, pts, indexing="ij")  # [x][y][z]
+        W = np.einsum("a,b,c->abc", wts, wts, wts)
+        fq = np.transpose(_lshape_f(X, Y, Z) * W, (2, 1, 0))  # [z][y][x]
+        gq = np.transpose(_lshape_u(X, Y, Z) * W, (2, 1, 0))
+        Fg[:, oy:oy + m, ox:ox + m] += np.einsum("ci,bj,ak,ijk->cba", B.T, B.T, B.T, fq, optimize=True)
+        proj = np.einsum("ci,bj,ak,ijk->cba", B.T, B.T, B.T, gq, optimize=True)
+        proj = _apply_kron3(Minv, Minv, Minv, proj)
+        sl_ = (slice(None), slice(oy, oy + m), slice(ox, ox + m))
+        new = ~seen[sl_]
+        Ug[sl_][new] = proj[new]
+        seen[sl_] = True
+    # Neumann data on the re-entrant faces
+    Y2, Z2 = np.meshgrid(pts - 1.0, pts, indexing="ij")  # C's face x = 0: world y in [-1, 0]
+    W2 = np.einsum("a,b->ab", wts, wts)
+    gN = (-(Y2) * np.cos(Z2)) * W2                          # -du/dx at x = 0
+    ox, oy = offs[2]
+    Fg[:, oy:oy + m, ox] += np.einsum("cj,bi,ij->cb", B.T, B.T, gN, optimize=True)
+    X2, Z2 = np.meshgrid(pts - 1.0, pts, indexing="ij")  # B's face y = 0: world x in [-1, 0]
+    gN = (-X2 * np.exp(X2) * np.cos(Z2)) * W2                # -du/dy at y = 0
+    ox, oy = offs[1]
+    Fg[:, oy, ox:ox + m] += np.einsum("cj,ai,ij->ca", B.T, B.T, gN, optimize=True)
+    # lifting: K u_D through the patches, then the free rows
+    free = np.zeros((m, Lg, Lg), bool)
+    free[1:m - 1] = keep2[None, :, :]
+    uD = np.where(inL[None, :, :] & ~free, Ug, 0.0)
+    KuD = np.zeros_like(uD)
+    for ox, oy in offs:
+        t = uD[:, oy:oy + m, ox:ox + m]
+        KuD[:, oy:oy + m, ox:ox + m] += ((_apply_kron3(M1, M1, K1, t) + _apply_kron3(M1, K1, M1, t))
+                                        + _apply_kron3(K1, M1, M1, t))
+    R = Fg - KuD
+    Ff = np.ascontiguousarray(R[free])  # z outermost, then y, then x: the assembly's numbering
+    prob = Problem(N, rowptr, col, val, Ff, {"kind": "lshape_mixed_bc", "d": 3, "n": n, "p": p})
+    prob.lift = uD
+    prob.free_mask = free
+    return prob
+
+
+def lshape_mixed_bc_l2_error(prob: Problem, u_free: np.ndarray) -> float:
+    """||u_h - u||_L2 over the three patches, u = exp(x) sin(xy) cos(z)."""
+    n, p = prob.meta["n"], prob.meta["p"]
+    m = n + p
+    C = prob.lift.copy()
+    C[prob.free_mask] = np.asarray(u_free)
+    pts, wts, B = _quad_1d(n, p)
+    W = np.einsum("a,b,c->abc", wts, wts, wts)
+    err = 0.0
+    for (wx, wy), (ox, oy) in zip(LSHAPE_PATCHES, _lshape_lattice_offsets(m)):
+        uh = np.einsum("ai,bj,ck,ijk->abc", B, B, B, C[:, oy:oy + m, ox:ox + m], optimize=True)  # [z][y][x]
+        Z, Y, X = np.meshgrid(pts, pts + wy, pts + wx, indexing="ij")
+        err += float(np.sum(np.transpose(W, (2, 1, 0)) * (uh - _lshape_u(X, Y, Z)) ** 2))
+    return math.sqrt(err)
 
 
 ANNULUS_KAPPA = dict(M=256, ell=0.2, sigma=1.0)

@@ -326,6 +326,87 @@ int iga_assemble_kron_box(int n, int p, const int* lo, const int* hi, int64_t* r
     return pos == z ? 0 : -3;
 }
 
+/* ------------------------------------------------ three-patch L-shape ---- */
+/* Three unit-cube patches with the same open knot vectors (n elements,
+ * degree p, m = n + p functions per direction), conforming along their
+ * shared faces: A = [0,1]x[0,1], B = [-1,0]x[0,1], C = [0,1]x[-1,0] in
+ * (x, y), each times [0,1] in z.  Their functions sit on a (2m-1) x (2m-1)
+ * lattice in (x, y) (B: gx < m, A and C: gx >= m-1; C: gy < m, A and B:
+ * gy >= m-1), the quadrant gx < m-1, gy < m-1 being absent; a function on
+ * an interface line belongs to both patches (C^0 coupling).  Two functions
+ * couple through every patch that holds both; the entry is the sum over
+ * those patches (in the order A, B, C) of the unit-cube Kronecker entry
+ * ((kx my) mz + (mx ky) mz) + (mx my) kz in patch-local indices.  The
+ * kept functions are the lattice points with keep2[gy (2m-1) + gx] != 0
+ * times the z indices [z0, z1), numbered x fastest, then y, then z; columns
+ * sorted; cap bounds the stored entries. */
+static int lshape_patch_has(int m, int pidx, int gx, int gy) {
+    switch (pidx) {
+        case 0: return gx >= m - 1 && gy >= m - 1;  /* A */
+        case 1: return gx <= m - 1 && gy >= m - 1;  /* B */
+        default: return gx >= m - 1 && gy <= m - 1; /* C */
+    }
+}
+static int lshape_off(int m, int pidx, int axis) {
+    if (axis == 0) return pidx == 1 ? 0 : m - 1;
+    return pidx == 2 ? 0 : m - 1;
+}
+
+int iga_assemble_lshape(int n, int p, const uint8_t* keep2, int z0, int z1, int64_t* rowptr, int32_t* col,
+                        double* val, int64_t cap) {
+    if (p < 1 || p > IGA_MAXP || n < 1 || z0 < 0 || z1 > n + p || z1 <= z0) return -1;
+    const int m = n + p, L = 2 * m - 1, mz = z1 - z0;
+    double* K1 = (double*)malloc(sizeof(double) * m * m);
+    double* M1 = (double*)malloc(sizeof(double) * m * m);
+    int64_t* idx2 = (int64_t*)malloc(sizeof(int64_t) * L * L);
+    if (!K1 || !M1 || !idx2) { free(K1); free(M1); free(idx2); return -2; }
+    iga_1d_matrices(n, p, p + 1, K1, M1);
+    int64_t n2 = 0;
+    for (int gy = 0; gy < L; gy++)
+        for (int gx = 0; gx < L; gx++) {
+            const int in = lshape_patch_has(m, 0, gx, gy) || lshape_patch_has(m, 1, gx, gy) ||
+                           lshape_patch_has(m, 2, gx, gy);
+            idx2[gy * L + gx] = (in && keep2[gy * L + gx]) ? n2++ : -1;
+        }
+    int64_t pos = 0, row = 0;
+    rowptr[0] = 0;
+    for (int iz = z0; iz < z1; iz++)
+        for (int gy = 0; gy < L; gy++)
+            for (int gx = 0; gx < L; gx++) {
+                if (idx2[gy * L + gx] < 0) continue;
+                for (int jz = (iz - p > z0 ? iz - p : z0); jz <= (iz + p < z1 - 1 ? iz + p : z1 - 1); jz++)
+                    for (int hy = (gy - p > 0 ? gy - p : 0); hy <= (gy + p < L - 1 ? gy + p : L - 1); hy++)
+                        for (int hx = (gx - p > 0 ? gx - p : 0); hx <= (gx + p < L - 1 ? gx + p : L - 1); hx++) {
+                            const int64_t j2 = idx2[hy * L + hx];
+                            if (j2 < 0) continue;
+                            double v = 0.0;
+                            int any = 0;
+                            for (int P = 0; P < 3; P++) {
+                                if (!lshape_patch_has(m, P, gx, gy) || !lshape_patch_has(m, P, hx, hy)) continue;
+                                const int ax = gx - lshape_off(m, P, 0), bx = hx - lshape_off(m, P, 0);
+                                const int ay = gy - lshape_off(m, P, 1), by = hy - lshape_off(m, P, 1);
+                                const double kx = K1[ax * m + bx], mx = M1[ax * m + bx];
+                                const double ky = K1[ay * m + by], my = M1[ay * m + by];
+                                const double kz = K1[iz * m + jz], mzz = M1[iz * m + jz];
+                                const double e = ((kx * my) * mzz + (mx * ky) * mzz) + (mx * my) * kz;
+                                v = any ? v + e : e;
+                                any = 1;
+                            }
+                            if (!any) continue;
+                            if (pos >= cap) { free(K1); free(M1); free(idx2); return -3; }
+                            col[pos] = (int32_t)(j2 + n2 * (int64_t)(jz - z0));
+                            val[pos] = v;
+                            pos++;
+                        }
+                rowptr[++row] = pos;
+            }
+    (void)mz;
+    free(K1);
+    free(M1);
+    free(idx2);
+    return 0;
+}
+
 /* ------------------------------------------------- Kronecker assembly ---- */
 /* K = K1 (x) M1 (x) M1 + M1 (x) K1 (x) M1 + M1 (x) M1 (x) K1 on the unit cube
  * (two terms on the unit square), restricted to the DOF set.  The entry for

@@ -131,3 +131,33 @@ def test_papers_cube_table1_trend():
     print("k p size iterations (paper) OPC (paper) L2 error:")
     for r in rows:
         print("  %d %d %d %d (%d) %.2f (%.2f) %.1e" % r)
+
+
+def test_papers_lshape_table2_trend():
+    """The paper's multipatch L-shaped case (three conforming patches, its
+    matrix sizes) with its solver configuration, beside its table
+    (tests/golden/lshape_table2.txt): iterations printed as a trend, the
+    discrete solution accurate.  Chebyshev degree 8 for p = 2 and 3, 12 / 14
+    / 16 for p = 4 / 5 / 6."""
+    from tests.conftest import read_golden
+
+    deg = {2: 8, 3: 8, 4: 12, 5: 14, 6: 16}
+    rows = []
+    for row in read_golden("lshape_table2.txt"):
+        k, p, size, its_paper, opc_paper = int(row[0]), int(row[1]), int(row[2]), row[3], row[4]
+        if k > 24:
+            continue
+        prob = I.lshape_mixed_bc(k, p)
+        m = k + p
+        assert prob.n == (m - 2) * (m - 1) * (3 * m - 5)
+        H = A.Hierarchy(dev(prob.rowptr), dev(prob.col), dev(prob.val), match_passes=3, smooth_levels=-1,
+                        cheb_degree=deg[p], coarse_solver=1, flexible=1)
+        g = H.solve(dev(prob.F), rtol=1e-6)
+        assert g["status"] == 0
+        err = I.lshape_mixed_bc_l2_error(prob, g["u"].cpu().numpy())
+        rows.append((k, p, prob.n, g["iters"], int(its_paper), round(H.info.opc, 2), float(opc_paper), err))
+        assert g["iters"] <= 3 * int(its_paper) + 5
+        assert err < 1e-2
+    print("k p size iterations (paper) OPC (paper) L2 error:")
+    for r in rows:
+        print("  %d %d %d %d (%d) %.2f (%.2f) %.1e" % r)

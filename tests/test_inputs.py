@@ -203,3 +203,43 @@ def test_cube_mixed_bc_converges_at_order_p_plus_1(p):
     rates = [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
     assert errs[-1] < 1e-4
     assert abs(rates[-1] - (p + 1)) < 0.4, (errs, rates)
+
+
+# --------------------------------------------- multipatch L-shape (Sec. 5) ----
+def test_lshape_sizes_are_the_papers():
+    """(m-2)(m-1)(3m-5) unknowns, m = k + p: the matrix sizes of the
+    paper's multipatch L-shaped table (tests/golden/lshape_table2.txt)."""
+    from tests.conftest import read_golden
+
+    for row in read_golden("lshape_table2.txt"):
+        k, p, size = int(row[0]), int(row[1]), int(row[2])
+        m = k + p
+        ours = (m - 2) * (m - 1) * (3 * m - 5)
+        if len(row) > 5 and row[5] == "misprint":
+            # printed value off in at most two digits of the same length
+            a, b = str(ours), str(size)
+            assert len(a) == len(b) and sum(x != y for x, y in zip(a, b)) <= 2, (k, p, size, ours)
+        else:
+            assert ours == size, (k, p, size, ours)
+    prob = I.lshape_mixed_bc(12, 2)
+    assert prob.n == 5772
+    K = prob.to_scipy()
+    assert (K != K.T).nnz == 0
+    # SPD: the smallest eigenvalue of a small case is positive
+    small = I.lshape_mixed_bc(3, 2).to_scipy().toarray()
+    assert np.linalg.eigvalsh(small).min() > 0
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_lshape_converges_at_order_p_plus_1(p):
+    """Three conforming patches with shared interface functions (C^0 across
+    the interfaces), Dirichlet lifting, Neumann data on the re-entrant
+    faces: the discrete solution approaches exp(x) sin(xy) cos(z) in L2 at
+    rate p+1 (a wrong interface identification, face or sign breaks it)."""
+    errs = []
+    for n in (4, 8, 16):
+        prob = I.lshape_mixed_bc(n, p)
+        u = spl.spsolve(prob.to_scipy().tocsc(), prob.F)
+        errs.append(I.lshape_mixed_bc_l2_error(prob, u))
+    rate = np.log2(errs[-2] / errs[-1])
+    assert abs(rate - (p + 1)) < 0.4, (errs, rate)

@@ -18,10 +18,19 @@
 // bitmap over the row's column span (bounded by the first and last column of
 // every B row it reads), and prefix popcounts of the bitmap words give each
 // column its rank in the sorted row: no sorting and no atomics on values.
-// The numeric pass walks A's entries of the row in ascending order, one at a
-// time; the lanes share B's row (distinct output columns, so no two lanes
-// touch the same accumulator) and __syncwarp orders successive entries, which
-// makes every output entry's sum run in ascending order of A's column.
+// Two kernels walk a row's items -- the pairs (t, q) of an entry t of A's row
+// and an entry q of B's row aci[t], t ascending, then q:
+//   * short B rows (the tentative P, one entry per row): one warp per output
+//     row takes 32 consecutive items per round, with the loads of kSpBatch
+//     rounds in flight together (A's entries 32 at a time; a scan of their
+//     B-row lengths places each item).  In the numeric pass the items of a
+//     round that hit the same output column come from different t (a B row
+//     has distinct columns) and are added in lane order, i.e. in ascending t;
+//   * long B rows (K, P_bar, K P_bar): one block per output row shares one
+//     accumulator (a warp's share of shared memory would leave the SM a few
+//     warps); its threads split B's row of one t at a time (distinct columns,
+//     no conflicts) and a block barrier separates successive t.
+// Either way every output entry's sum runs in ascending order of A's column.
 //
 // The transpose P_bar^T needs no sort either: with K structurally symmetric,
 // column J of P_bar holds exactly the rows that K's rows of J's members
@@ -45,6 +54,10 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kSpWarps = 8;  // warps per block of the SpGEMM row kernels (fewer if shared memory is short)
+constexpr int kSpBatch = 8;  // rounds of 32 items whose loads a warp keeps in flight together
+constexpr int kSpBlk = 256;  // threads of the block-per-row kernel (also the A entries it stages at once)
+constexpr int kSpUnroll = 4;  // B entries a thread of that kernel loads before it accumulates them
+constexpr double kSpLongRow = 128.0;  // average B row length from which the block-per-row kernel is used
 
 enum SpMode { SP_COUNT = 0, SP_COLS = 1, SP_VALUES = 2, SP_UPPER = 3 };
 
@@ -64,6 +77,84 @@ __device__ __forceinline__ void row_span(const int64_t* __restrict__ arp, const 
     }
     lo = __reduce_min_sync(FULL, l);
     hi = __reduce_max_sync(FULL, h);
+}
+
+// A chunk of A's row: lane l takes entry tb + l (when < a1): the range
+// [q0, q0 + len) of B's row aci[t] -- from its first column >= cfirst when
+// cfirst >= 0 -- and the value a = av[t] (0 without values).  incl is the
+// inclusive scan of len over the lanes, tot the chunk's item count.
+__device__ __forceinline__ void chunk_open(const int32_t* __restrict__ aci, const double* __restrict__ av,
+                                           const int64_t* __restrict__ brp, const int32_t* __restrict__ bci,
+                                           int64_t tb, int64_t a1, int lane, int cfirst, int64_t& q0, int& len,
+                                           int& incl, int& tot, double& a) {
+    q0 = 0;
+    len = 0;
+    a = 0.0;
+    const int64_t t = tb + lane;
+    if (t < a1) {
+        const int k = aci[t];
+        int64_t b0 = brp[k];
+        const int64_t b1 = brp[k + 1];
+        if (cfirst >= 0) {
+            int64_t hi = b1;
+            while (b0 < hi) {
+                const int64_t mid = (b0 + hi) >> 1;
+                if (bci[mid] < cfirst) b0 = mid + 1;
+                else hi = mid;
+            }
+        }
+        q0 = b0;
+        len = (int)(b1 - b0);
+        if (av) a = av[t];
+    }
+    incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    tot = __shfl_sync(FULL, incl, 31);
+}
+
+// Item f of the chunk (0 <= f < tot): it belongs to the first lane s whose
+// running length exceeds f; returns its B position q and A value a_s.  All
+// lanes take part (lanes with f >= tot get a position they must not use).
+__device__ __forceinline__ int64_t chunk_item(int f, int64_t q0, int len, int incl, double a, double& as) {
+    int s = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int v = __shfl_sync(FULL, incl, s + step - 1);
+        if (v <= f) s += step;
+    }
+    const int is = __shfl_sync(FULL, incl, s), ls = __shfl_sync(FULL, len, s);
+    const int64_t qs = __shfl_sync(FULL, q0, s);
+    as = __shfl_sync(FULL, a, s);
+    return qs + (f - (is - ls));
+}
+
+// Marks the output columns of row i (A's row [a0, a1)) in bits (span from lo).
+__device__ __forceinline__ void mark_row(const int32_t* __restrict__ aci, const int64_t* __restrict__ brp,
+                                         const int32_t* __restrict__ bci, int64_t a0, int64_t a1, int lo, int lane,
+                                         uint32_t* bits) {
+    for (int64_t tb = a0; tb < a1; tb += 32) {
+        int64_t q0;
+        int len, incl, tot;
+        double a;
+        chunk_open(aci, nullptr, brp, bci, tb, a1, lane, -1, q0, len, incl, tot, a);
+        for (int fb = 0; fb < tot; fb += 32 * kSpBatch) {
+            int J[kSpBatch];
+#pragma unroll
+            for (int u = 0; u < kSpBatch; u++) {
+                const int f = fb + 32 * u + lane;
+                double as;
+                const int64_t q = chunk_item(f, q0, len, incl, a, as);
+                J[u] = f < tot ? bci[q] - lo : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kSpBatch; u++)
+                if (J[u] >= 0) atomicOr(&bits[J[u] >> 5], 1u << (J[u] & 31));
+        }
+    }
 }
 
 // Largest bitmap (words) any output row of A B needs.
@@ -111,13 +202,7 @@ __global__ void k_sp_row(int n, const int64_t* __restrict__ arp, const int32_t* 
         for (int w = lane; w < W; w += 32) bits[w] = 0u;
         __syncwarp();
         const int64_t a0 = arp[i], a1 = arp[i + 1];
-        for (int64_t t = a0; t < a1; t++) {
-            const int k = aci[t];
-            for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
-                const int J = bci[q] - lo;
-                atomicOr(&bits[J >> 5], 1u << (J & 31));
-            }
-        }
+        mark_row(aci, brp, bci, a0, a1, lo, lane, bits);
         __syncwarp();
         // exclusive prefix of the words' popcounts (lane-contiguous chunks)
         const int chunk = (W + 31) >> 5;
@@ -159,20 +244,215 @@ __global__ void k_sp_row(int n, const int64_t* __restrict__ arp, const int32_t* 
         if (MODE == SP_COLS) continue;
         for (int u = lane; u < total; u += 32) acc[u] = 0.0;
         __syncwarp();
-        for (int64_t t = a0; t < a1; t++) {
-            const int k = aci[t];
-            const double a = av[t];
-            for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
-                const int Jg = bci[q];
-                if (MODE == SP_UPPER && Jg < i) continue;
-                const int J = Jg - lo;
-                const int r = pre[J >> 5] + __popc(bits[J >> 5] & ((1u << (J & 31)) - 1u));
-                acc[r] = __dadd_rn(acc[r], __dmul_rn(a, bv[q]));
+        const unsigned below = (1u << lane) - 1u;
+        for (int64_t tb = a0; tb < a1; tb += 32) {
+            int64_t q0;
+            int len, incl, tot;
+            double a;
+            chunk_open(aci, av, brp, bci, tb, a1, lane, MODE == SP_UPPER ? i : -1, q0, len, incl, tot, a);
+            for (int fb = 0; fb < tot; fb += 32 * kSpBatch) {
+                int J[kSpBatch];
+                double x[kSpBatch], y[kSpBatch];
+#pragma unroll
+                for (int u = 0; u < kSpBatch; u++) {
+                    const int f = fb + 32 * u + lane;
+                    const int64_t q = chunk_item(f, q0, len, incl, a, x[u]);
+                    J[u] = -1;
+                    y[u] = 0.0;
+                    if (f < tot) {
+                        J[u] = bci[q] - lo;
+                        y[u] = bv[q];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kSpBatch; u++) {
+                    if (fb + 32 * u >= tot) break;  // warp-uniform
+                    int r = -1 - lane;
+                    if (J[u] >= 0) r = pre[J[u] >> 5] + __popc(bits[J[u] >> 5] & ((1u << (J[u] & 31)) - 1u));
+                    const unsigned grp = __match_any_sync(FULL, r);
+                    const int pos = __popc(grp & below);
+                    const int npos = __reduce_max_sync(FULL, (unsigned)pos);
+                    const double prod = __dmul_rn(x[u], y[u]);
+                    for (int k = 0; k <= npos; k++) {
+                        if (r >= 0 && pos == k) acc[r] = __dadd_rn(acc[r], prod);
+                        __syncwarp();
+                    }
+                }
             }
-            __syncwarp();
         }
         for (int u = lane; u < total; u += 32) cv[cb + u] = acc[u];
         __syncwarp();
+    }
+    if (MODE == SP_COUNT) {
+        best = __reduce_max_sync(FULL, best);
+        if (lane == 0 && best > 0) atomicMax(maxc, best);
+    }
+}
+
+// The same passes with one block of kSpBlk threads per output row (see the
+// file header).  Shared memory: bits[wmax], pre[wmax], acc[cmax] (value
+// modes), then the staged A entries of the numeric pass (B range start and
+// length, value) and a reduction scratch.
+template <int MODE>
+__global__ void __launch_bounds__(kSpBlk) k_sp_row_blk(int n, const int64_t* __restrict__ arp,
+                                                       const int32_t* __restrict__ aci, const double* __restrict__ av,
+                                                       const int64_t* __restrict__ brp, const int32_t* __restrict__ bci,
+                                                       const double* __restrict__ bv, int wmax, int cmax,
+                                                       int64_t* __restrict__ rowcnt, int* maxc,
+                                                       const int64_t* __restrict__ crp, int32_t* __restrict__ cci,
+                                                       double* __restrict__ cv, int* flag) {
+    extern __shared__ __align__(16) unsigned char sp_smem[];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    constexpr int NW = kSpBlk / 32;
+    uint32_t* bits = reinterpret_cast<uint32_t*>(sp_smem);
+    int32_t* pre = reinterpret_cast<int32_t*>(sp_smem + (size_t)4 * wmax);
+    double* acc = reinterpret_cast<double*>(sp_smem + (size_t)8 * wmax);
+    unsigned char* tail = sp_smem + (size_t)8 * wmax + (MODE >= SP_VALUES ? (size_t)8 * cmax : 0);
+    int64_t* sq0 = reinterpret_cast<int64_t*>(tail);
+    double* sa = reinterpret_cast<double*>(tail + 8 * kSpBlk);
+    int* slen = reinterpret_cast<int*>(tail + 16 * kSpBlk);
+    int* red = reinterpret_cast<int*>(tail + 20 * kSpBlk);  // [0..NW) lo, [NW..2NW) hi, [2NW] total
+    int best = 0;
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const int64_t a0 = arp[i], a1 = arp[i + 1];
+        // column span of the row
+        int l = 0x7fffffff, hmax = -1;
+        for (int64_t t = a0 + tid; t < a1; t += kSpBlk) {
+            const int k = aci[t];
+            const int64_t b0 = brp[k], b1 = brp[k + 1];
+            if (b1 > b0) {
+                l = min(l, bci[b0]);
+                hmax = max(hmax, bci[b1 - 1]);
+            }
+        }
+        l = __reduce_min_sync(FULL, l);
+        hmax = __reduce_max_sync(FULL, hmax);
+        if (lane == 0) {
+            red[wid] = l;
+            red[NW + wid] = hmax;
+        }
+        __syncthreads();
+        int lo = red[0], hi = red[NW];
+#pragma unroll
+        for (int w = 1; w < NW; w++) {
+            lo = min(lo, red[w]);
+            hi = max(hi, red[NW + w]);
+        }
+        const int W = hi >= lo ? ((hi - lo) >> 5) + 1 : 0;
+        if (W > wmax) {  // sized from k_sp_span; cannot happen
+            if (tid == 0) atomicOr(flag, 1);
+            __syncthreads();
+            continue;
+        }
+        for (int w = tid; w < W; w += kSpBlk) bits[w] = 0u;
+        __syncthreads();
+        // mark: warp wid takes A's entries a0 + wid, a0 + wid + NW, ...
+        for (int64_t t = a0 + wid; t < a1; t += NW) {
+            const int k = aci[t];
+            const int64_t b0 = brp[k], b1 = brp[k + 1];
+            for (int64_t q = b0 + lane; q < b1; q += 32 * kSpUnroll) {
+                int J[kSpUnroll];
+#pragma unroll
+                for (int u = 0; u < kSpUnroll; u++) J[u] = q + 32 * u < b1 ? bci[q + 32 * u] - lo : -1;
+#pragma unroll
+                for (int u = 0; u < kSpUnroll; u++)
+                    if (J[u] >= 0) atomicOr(&bits[J[u] >> 5], 1u << (J[u] & 31));
+            }
+        }
+        __syncthreads();
+        // exclusive prefix of the words' popcounts (warp 0, lane-contiguous chunks)
+        if (wid == 0) {
+            const int chunk = (W + 31) >> 5;
+            const int w0 = min(W, lane * chunk), w1 = min(W, w0 + chunk);
+            int mine = 0;
+            for (int w = w0; w < w1; w++) mine += __popc(bits[w]);
+            int xs = mine;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, xs, o);
+                if (lane >= o) xs += y;
+            }
+            int run = xs - mine;
+            for (int w = w0; w < w1; w++) {
+                pre[w] = run;
+                run += __popc(bits[w]);
+            }
+            if (lane == 31) red[2 * NW] = xs;
+        }
+        __syncthreads();
+        const int total = red[2 * NW];
+        if (MODE == SP_COUNT) {
+            if (tid == 0) rowcnt[i] = total;
+            best = max(best, total);
+            __syncthreads();
+            continue;
+        }
+        if (total > cmax && MODE >= SP_VALUES) {  // sized from the counting pass; cannot happen
+            if (tid == 0) atomicOr(flag, 2);
+            __syncthreads();
+            continue;
+        }
+        const int64_t cb = crp[i];
+        for (int w = tid; w < W; w += kSpBlk) {
+            uint32_t m = bits[w];
+            int pos = pre[w];
+            while (m) {
+                const int bit = __ffs(m) - 1;
+                m &= m - 1;
+                cci[cb + pos++] = lo + (w << 5) + bit;
+            }
+        }
+        if (MODE == SP_COLS) {
+            __syncthreads();
+            continue;
+        }
+        for (int u = tid; u < total; u += kSpBlk) acc[u] = 0.0;
+        for (int64_t tb = a0; tb < a1; tb += kSpBlk) {
+            const int nt = (int)min((int64_t)kSpBlk, a1 - tb);
+            __syncthreads();  // the previous stage's entries are consumed
+            if (tid < nt) {
+                const int64_t t = tb + tid;
+                const int k = aci[t];
+                int64_t b0 = brp[k];
+                const int64_t b1 = brp[k + 1];
+                if (MODE == SP_UPPER) {  // first column >= i
+                    int64_t hb = b1;
+                    while (b0 < hb) {
+                        const int64_t mid = (b0 + hb) >> 1;
+                        if (bci[mid] < i) b0 = mid + 1;
+                        else hb = mid;
+                    }
+                }
+                sq0[tid] = b0;
+                slen[tid] = (int)(b1 - b0);
+                sa[tid] = av[t];
+            }
+            __syncthreads();
+            for (int u = 0; u < nt; u++) {
+                const int64_t q0 = sq0[u];
+                const int len = slen[u];
+                const double a = sa[u];
+                for (int x = tid; x < len; x += kSpBlk * kSpUnroll) {
+                    int J[kSpUnroll];
+                    double y[kSpUnroll];
+#pragma unroll
+                    for (int v = 0; v < kSpUnroll; v++) {
+                        const int xv = x + kSpBlk * v;
+                        J[v] = xv < len ? bci[q0 + xv] - lo : -1;
+                        y[v] = xv < len ? bv[q0 + xv] : 0.0;
+                    }
+#pragma unroll
+                    for (int v = 0; v < kSpUnroll; v++)
+                        if (J[v] >= 0) {
+                            const int r = pre[J[v] >> 5] + __popc(bits[J[v] >> 5] & ((1u << (J[v] & 31)) - 1u));
+                            acc[r] = __dadd_rn(acc[r], __dmul_rn(a, y[v]));
+                        }
+                }
+                __syncthreads();  // successive t in ascending order
+            }
+        }
+        for (int u = tid; u < total; u += kSpBlk) cv[cb + u] = acc[u];
+        __syncthreads();
     }
     if (MODE == SP_COUNT) {
         best = __reduce_max_sync(FULL, best);
@@ -329,12 +609,13 @@ inline int sp_blocks(int64_t rows, int warps) {
 // C.val in the value modes) are allocated with dev_alloc on s and recorded
 // in h->allocs (owned by the hierarchy).  Device words dflag[0] and
 // dflag[1] are this call's span and count maxima; dflag[2] accumulates the
-// rows' error bits (cleared by the caller).  Returns AMG_OK,
-// AMG_ERR_ROW_TOO_LONG (an output row needs more shared memory than a
-// block has), AMG_ERR_NOMEM or AMG_ERR_CUDA.
+// rows' error bits (cleared by the caller).  b_avg is B's average row
+// length: from kSpLongRow on, the block-per-row kernel runs, else the
+// warp-per-row one.  Returns AMG_OK, AMG_ERR_ROW_TOO_LONG (an output row
+// needs more shared memory than a block has), AMG_ERR_NOMEM or AMG_ERR_CUDA.
 static int spgemm(amg_hierarchy* h, int nA, const int64_t* arp, const int32_t* aci, const double* av,
-                  const int64_t* brp, const int32_t* bci, const double* bv, int mode, DevCSR& C, int* dflag,
-                  int64_t* scratch64) {
+                  const int64_t* brp, const int32_t* bci, const double* bv, double b_avg, int mode, DevCSR& C,
+                  int* dflag, int64_t* scratch64) {
     cudaStream_t s = h->s;
     int* hflag = h->flag_host;
     auto fail = [](cudaError_t e) { return e == cudaErrorMemoryAllocation ? AMG_ERR_NOMEM : AMG_ERR_CUDA; };
@@ -367,15 +648,28 @@ static int spgemm(amg_hierarchy* h, int nA, const int64_t* arp, const int32_t* a
         cudaStream_t s;
         ~FreeCnt() { cudaFreeAsync(p, s); }
     } free_cnt{rowcnt, s};
-    size_t per = (size_t)8 * wmax;
-    int warps = (int)std::min<size_t>(kSpWarps, (size_t)smem_optin / per);
-    if (warps < 1) return AMG_ERR_ROW_TOO_LONG;
+    const bool blk = b_avg >= kSpLongRow;
+    // shared memory of the block-per-row kernel beyond bits/pre/acc: staged
+    // A entries (8 + 8 + 4 bytes each) and the reduction scratch
+    const size_t blk_tail = (size_t)20 * kSpBlk + 4 * (2 * (kSpBlk / 32) + 1) + 16;
     auto cfg = [&](auto kern, size_t bytes) {
         return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     };
-    SP_CK(cfg(k_sp_row<SP_COUNT>, per * warps));
-    k_sp_row<SP_COUNT><<<AMG_GRID(sp_blocks(nA, warps)), 32 * warps, per * warps, s>>>(
-        nA, arp, aci, av, brp, bci, bv, wmax, 0, rowcnt, dflag + 1, nullptr, nullptr, nullptr, dflag + 2);
+    auto blocks_blk = [&]() { return (int)std::max<int64_t>(1, std::min<int64_t>(nA, (int64_t)1 << 20)); };
+    size_t per = (size_t)8 * wmax;
+    int warps = 0;
+    if (blk) {
+        if (per + blk_tail > (size_t)smem_optin) return AMG_ERR_ROW_TOO_LONG;
+        SP_CK(cfg(k_sp_row_blk<SP_COUNT>, per + blk_tail));
+        k_sp_row_blk<SP_COUNT><<<AMG_GRID(blocks_blk()), kSpBlk, per + blk_tail, s>>>(
+            nA, arp, aci, av, brp, bci, bv, wmax, 0, rowcnt, dflag + 1, nullptr, nullptr, nullptr, dflag + 2);
+    } else {
+        warps = (int)std::min<size_t>(kSpWarps, (size_t)smem_optin / per);
+        if (warps < 1) return AMG_ERR_ROW_TOO_LONG;
+        SP_CK(cfg(k_sp_row<SP_COUNT>, per * warps));
+        k_sp_row<SP_COUNT><<<AMG_GRID(sp_blocks(nA, warps)), 32 * warps, per * warps, s>>>(
+            nA, arp, aci, av, brp, bci, bv, wmax, 0, rowcnt, dflag + 1, nullptr, nullptr, nullptr, dflag + 2);
+    }
     SP_CK(cudaGetLastError());
     SP_CK(launch_scan64(rowcnt, C.rowptr, nA, scratch64, s));
     SP_CK(cudaMemcpyAsync(hflag + 1, dflag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -387,6 +681,28 @@ static int spgemm(amg_hierarchy* h, int nA, const int64_t* arp, const int32_t* a
     SP_CK(halloc((void**)&C.col, sizeof(int32_t) * ((size_t)C.nnz + 8)));
     if (mode >= SP_VALUES) SP_CK(halloc((void**)&C.val, sizeof(double) * ((size_t)C.nnz + 8)));
     per = (size_t)8 * wmax + (mode >= SP_VALUES ? (size_t)8 * cmax : 0);
+    if (blk) {
+        if (per + blk_tail > (size_t)smem_optin) return AMG_ERR_ROW_TOO_LONG;
+        const size_t sm = per + blk_tail;
+        const int gb = blocks_blk();
+        if (mode == SP_COLS) {
+            SP_CK(cfg(k_sp_row_blk<SP_COLS>, sm));
+            k_sp_row_blk<SP_COLS><<<AMG_GRID(gb), kSpBlk, sm, s>>>(nA, arp, aci, av, brp, bci, bv, wmax, cmax, nullptr,
+                                                                   nullptr, C.rowptr, C.col, nullptr, dflag + 2);
+        } else if (mode == SP_VALUES) {
+            SP_CK(cfg(k_sp_row_blk<SP_VALUES>, sm));
+            k_sp_row_blk<SP_VALUES><<<AMG_GRID(gb), kSpBlk, sm, s>>>(nA, arp, aci, av, brp, bci, bv, wmax, cmax,
+                                                                     nullptr, nullptr, C.rowptr, C.col, C.val,
+                                                                     dflag + 2);
+        } else {
+            SP_CK(cfg(k_sp_row_blk<SP_UPPER>, sm));
+            k_sp_row_blk<SP_UPPER><<<AMG_GRID(gb), kSpBlk, sm, s>>>(nA, arp, aci, av, brp, bci, bv, wmax, cmax,
+                                                                    nullptr, nullptr, C.rowptr, C.col, C.val,
+                                                                    dflag + 2);
+        }
+        SP_CK(cudaGetLastError());
+        return AMG_OK;
+    }
     warps = (int)std::min<size_t>(kSpWarps, (size_t)smem_optin / per);
     if (warps < 1) return AMG_ERR_ROW_TOO_LONG;
     const int gb = sp_blocks(nA, warps);
@@ -448,7 +764,7 @@ int smooth_level(amg_hierarchy* h, int l, DevCSR& Kc_out) {
     k_sp_iota<<<AMG_GRID((n + 1 + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, prp);
     k_sp_widen<<<AMG_GRID((nc + 1 + kBlock - 1) / kBlock), kBlock, 0, s>>>(nc + 1, F.mem_ptr, mrp);
     // K P, then P_bar in place
-    int rc = spgemm(h, n, K.rowptr, K.col, K.val, prp, F.agg, F.pval, SP_VALUES, F.sp, dflag, scr);
+    int rc = spgemm(h, n, K.rowptr, K.col, K.val, prp, F.agg, F.pval, 1.0, SP_VALUES, F.sp, dflag, scr);
     if (rc != AMG_OK) return rc;
     if (l == 0) {  // K P of level 0 is kept: theta rescales it (training of the smoothing weights)
         if (dev_alloc((void**)&F.kp, sizeof(double) * ((size_t)F.sp.nnz + 8), s) != cudaSuccess) return AMG_ERR_NOMEM;
@@ -460,7 +776,8 @@ int smooth_level(amg_hierarchy* h, int l, DevCSR& Kc_out) {
     k_sp_pbar<<<AMG_GRID(sp_blocks(n, kWarpsPerBlock)), kBlock, 0, s>>>(n, F.sp.rowptr, F.sp.col, F.sp.val, F.agg,
                                                                         F.pval, theta, h->o.smooth_omega, F.dl1);
     // P_bar^T: the pattern of P^T K (the members' rows of K), values by search
-    rc = spgemm(h, nc, mrp, F.mem_idx, nullptr, K.rowptr, K.col, nullptr, SP_COLS, F.spT, dflag, scr);
+    rc = spgemm(h, nc, mrp, F.mem_idx, nullptr, K.rowptr, K.col, nullptr, (double)K.nnz / std::max(n, 1), SP_COLS,
+                F.spT, dflag, scr);
     if (rc != AMG_OK) return rc;
     if (dev_alloc((void**)&F.spT.val, sizeof(double) * ((size_t)F.spT.nnz + 8), s) != cudaSuccess)
         return AMG_ERR_NOMEM;
@@ -469,9 +786,11 @@ int smooth_level(amg_hierarchy* h, int l, DevCSR& Kc_out) {
                                                                          F.sp.rowptr, F.sp.col, F.sp.val, dflag + 2);
     // T = K P_bar, K_c = P_bar^T T (upper triangle), mirrored
     DevCSR T, Kc;
-    rc = spgemm(h, n, K.rowptr, K.col, K.val, F.sp.rowptr, F.sp.col, F.sp.val, SP_VALUES, T, dflag, scr);
+    rc = spgemm(h, n, K.rowptr, K.col, K.val, F.sp.rowptr, F.sp.col, F.sp.val, (double)F.sp.nnz / std::max(n, 1),
+                    SP_VALUES, T, dflag, scr);
     if (rc == AMG_OK)
-        rc = spgemm(h, nc, F.spT.rowptr, F.spT.col, F.spT.val, T.rowptr, T.col, T.val, SP_UPPER, Kc, dflag, scr);
+        rc = spgemm(h, nc, F.spT.rowptr, F.spT.col, F.spT.val, T.rowptr, T.col, T.val,
+                    (double)T.nnz / std::max(n, 1), SP_UPPER, Kc, dflag, scr);
     drop(h, T.rowptr);
     drop(h, T.col);
     drop(h, T.val);
@@ -526,8 +845,9 @@ int galerkin_pass_spgemm(amg_hierarchy* h, const DevCSR& A, const int32_t* agg, 
     if (launch_scan64(cnt, trp, nc, scr, s) != cudaSuccess) return AMG_ERR_CUDA;
     k_sp_pairs_fill<<<AMG_GRID((nc + kBlock - 1) / kBlock), kBlock, 0, s>>>(nc, mem0, mem1, pval, trp, tci, tv);
     DevCSR T;
-    int rc = spgemm(h, n, A.rowptr, A.col, A.val, prp, agg, pval, SP_VALUES, T, dflag, scr);
-    if (rc == AMG_OK) rc = spgemm(h, nc, trp, tci, tv, T.rowptr, T.col, T.val, SP_UPPER, C, dflag, scr);
+    int rc = spgemm(h, n, A.rowptr, A.col, A.val, prp, agg, pval, 1.0, SP_VALUES, T, dflag, scr);
+    if (rc == AMG_OK) rc = spgemm(h, nc, trp, tci, tv, T.rowptr, T.col, T.val, (double)T.nnz / std::max(n, 1), SP_UPPER, C, dflag,
+                    scr);
     drop(h, T.rowptr);
     drop(h, T.col);
     drop(h, T.val);
@@ -559,9 +879,11 @@ int smooth_recompute(amg_hierarchy* h, const double* theta) {
     if (dev_alloc((void**)&scr, sizeof(int64_t) * (scan64_scratch(std::max(n, nc)) + 1), s) != cudaSuccess)
         return AMG_ERR_NOMEM;
     DevCSR T, Kc;
-    int rc = spgemm(h, n, K.rowptr, K.col, K.val, F.sp.rowptr, F.sp.col, F.sp.val, SP_VALUES, T, dflag, scr);
+    int rc = spgemm(h, n, K.rowptr, K.col, K.val, F.sp.rowptr, F.sp.col, F.sp.val, (double)F.sp.nnz / std::max(n, 1),
+                    SP_VALUES, T, dflag, scr);
     if (rc == AMG_OK)
-        rc = spgemm(h, nc, F.spT.rowptr, F.spT.col, F.spT.val, T.rowptr, T.col, T.val, SP_UPPER, Kc, dflag, scr);
+        rc = spgemm(h, nc, F.spT.rowptr, F.spT.col, F.spT.val, T.rowptr, T.col, T.val,
+                    (double)T.nnz / std::max(n, 1), SP_UPPER, Kc, dflag, scr);
     cudaFreeAsync(scr, s);
     drop(h, T.rowptr);
     drop(h, T.col);

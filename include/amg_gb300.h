@@ -454,6 +454,56 @@ int amg_free(amg_hierarchy* h);
 /* Static description of a status code. */
 const char* amg_strerror(int code);
 
+/* ------------------------------------------------------------ IgA assembly
+ * Stiffness matrix K and load vector F of -div(kappa grad u) = f on one
+ * tensor-product B-spline patch (Sec. 2.2, single-patch discretization):
+ *   k_ij = int kappa(F(xi)) (grad_xi N_j)^T J^-1 J^-T (grad_xi N_i) |det J| dxi,
+ *   f_i  = int f(F(xi)) N_i |det J| dxi
+ * over the parametric cube [0,1]^3, J = dF/dxi, N_i the tensor products of
+ * the degree-p B-splines on the open uniform knot vector with n elements per
+ * direction (Sec. 2.1), nq Gauss points per element and direction.  The
+ * discrete space is the B-spline space on the parametric cube for both
+ * geometries (non-isoparametric for the annulus, Sec. 2.4).  Computed on
+ * the GPU by sum factorization: the 3-D quadrature sums are contracted one
+ * direction at a time with 1-D tables of products of B-spline values and
+ * derivatives, the tensor-product alternative to the element loop that
+ * Sec. 2.2 points to.  FP64; agrees with an element loop to rounding. */
+#define AMG_GEOM_CUBE 0     /* F(xi) = xi */
+#define AMG_GEOM_ANNULUS 1  /* quarter annulus of radii 1 and 2 extruded over z in [0,1]: (1 + xi1) c(xi2) + xi3 e_z, c the quadratic NURBS arc through (1,0), (1,1), (0,1) with weights 1, sqrt(2)/2, 1 */
+#define AMG_SRC_ONE 0       /* f = 1 */
+#define AMG_SRC_SINE 1      /* f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z) */
+
+typedef struct {
+    int32_t n;                 /* elements per direction, >= 1 */
+    int32_t p;                 /* B-spline degree, 1..8 */
+    int32_t nq;                /* Gauss points per element and direction, 1..16; 0 = p + 1; n nq <= 768 */
+    int32_t geometry;          /* AMG_GEOM_CUBE or AMG_GEOM_ANNULUS */
+    int32_t with_boundary;     /* 0: the functions nonzero on the boundary are eliminated (homogeneous Dirichlet data), m = n + p - 2 unknowns per direction; 1: all, m = n + p */
+    int32_t source;            /* AMG_SRC_ONE or AMG_SRC_SINE */
+    int32_t kappa_m;           /* random Fourier features of kappa; 0: kappa = 1 */
+    double kappa_sigma;        /* kappa = exp(sigma sqrt(2/M) sum_m cos(omega_m . x + phi_m)) */
+    const double* kappa_omega; /* device, kappa_m x 3 frequencies, row-major */
+    const double* kappa_phi;   /* device, kappa_m phases */
+} amg_iga_patch;
+
+/* Size of the system of patch P: *n = m^3 unknowns (numbered i1 + m (i2 +
+ * m i3)), *nnz = stored entries of K (row I couples to every J with
+ * |i_k - j_k| <= p per direction).  Host only.  AMG_OK or AMG_ERR_ARG. */
+int amg_iga_size(const amg_iga_patch* P, int64_t* n, int64_t* nnz);
+
+/* Assembles K (CSR: rowptr[n+1] int64, col[nnz] int32 ascending per row,
+ * val[nnz]) and, when F is not NULL, F[n] -- all device arrays of the sizes
+ * amg_iga_size gives, owned by the caller -- on cuda_stream (NULL = legacy
+ * default stream) of the current device; returns after the work finished.
+ * Device workspace is taken from the library's stream-ordered pool and
+ * released before the return: at its peak 8 (4 R Q^2 + 4 R^2 Q) bytes with
+ * Q = n nq and R = (2p+1) m (2.7 GB for n = 64, p = 3; 8.9 GB for n = 96),
+ * plus 8 Q^2 (2M rounded up to 16) for kappa.  *flops (may be NULL) receives the
+ * floating-point operations of the quadrature sums (2 per multiply-add).
+ * Returns AMG_OK, AMG_ERR_ARG, AMG_ERR_NOMEM or AMG_ERR_CUDA. */
+int amg_iga_assemble(const amg_iga_patch* P, int64_t* rowptr, int32_t* col, double* val, double* F,
+                     void* cuda_stream, double* flops);
+
 /* Self-test of the bounded waits of the staged passes (the mbarrier waits of
  * the bulk-copy pipelines, which on expiry end the kernel with
  * AMG_ERR_TIMEOUT instead of hanging).  Runs one thread on the current

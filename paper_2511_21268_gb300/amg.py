@@ -66,6 +66,16 @@ class AmgInfo(ctypes.Structure):
                 ("sell64_warps", ctypes.c_int32), ("tune_ms", ctypes.c_double)]
 
 
+AMG_GEOM_CUBE, AMG_GEOM_ANNULUS = 0, 1
+AMG_SRC_ONE, AMG_SRC_SINE = 0, 1
+
+
+class AmgIgaPatch(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("p", ctypes.c_int32), ("nq", ctypes.c_int32), ("geometry", ctypes.c_int32),
+                ("with_boundary", ctypes.c_int32), ("source", ctypes.c_int32), ("kappa_m", ctypes.c_int32),
+                ("kappa_sigma", ctypes.c_double), ("kappa_omega", ctypes.c_void_p), ("kappa_phi", ctypes.c_void_p)]
+
+
 class AmgError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
         self.code = code
@@ -120,6 +130,8 @@ _SIGS = {
                                       ctypes.c_void_p]),
     "amg_smoother_bound": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "amg_staged_wait_selftest": (ctypes.c_int, [ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_iga_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_iga_assemble": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6),
     "amg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "amg_last_cuda_error": (ctypes.c_char_p, []),
 }
@@ -466,6 +478,64 @@ def amg_mpnn_select(h, w, F, rtol: float, itmax: int, omega_ref: float = 1.0):
     _check(lib().amg_mpnn_select(h, wd.data_ptr(), float(omega_ref), F.data_ptr(), rtol, itmax, ctypes.byref(used),
                                  ctypes.byref(ip), ctypes.byref(il)), "amg_mpnn_select")
     return bool(used.value), ip.value, il.value
+
+
+def _iga_patch(n, p, nq=0, geometry=AMG_GEOM_CUBE, with_boundary=False, source=AMG_SRC_ONE, kappa=None):
+    """The patch struct; kappa = (omega, phi, sigma) with omega (M, 3) and
+    phi (M,) FP64 device tensors, or None (kappa = 1).  Returns the struct
+    and the tensors it points to (keep them alive)."""
+    P = AmgIgaPatch(int(n), int(p), int(nq), int(geometry), int(bool(with_boundary)), int(source), 0, 0.0, None, None)
+    keep = ()
+    if kappa is not None:
+        om, ph, sigma = kappa
+        if om.dtype != ph.dtype or str(om.dtype) != "torch.float64" or not (om.is_cuda and ph.is_cuda):
+            raise ValueError("kappa's omega and phi must be FP64 device tensors")
+        if om.numel() != 3 * ph.numel():
+            raise ValueError("omega must hold 3 frequencies per phase")
+        om = om.contiguous()
+        ph = ph.contiguous()
+        P.kappa_m = int(ph.numel())
+        P.kappa_sigma = float(sigma)
+        P.kappa_omega = om.data_ptr()
+        P.kappa_phi = ph.data_ptr()
+        keep = (om, ph)
+    return P, keep
+
+
+def amg_iga_size(patch) -> tuple[int, int]:
+    """(unknowns, stored entries) of an AmgIgaPatch."""
+    n, z = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().amg_iga_size(ctypes.byref(patch), ctypes.byref(n), ctypes.byref(z)), "amg_iga_size")
+    return n.value, z.value
+
+
+def amg_iga_assemble(patch, rowptr, col, val, F=None, stream=None) -> float:
+    """Assemble into caller-allocated device tensors; returns the flop count
+    of the quadrature sums."""
+    fl = ctypes.c_double()
+    _check(lib().amg_iga_assemble(ctypes.byref(patch), rowptr.data_ptr(), col.data_ptr(), val.data_ptr(),
+                                  None if F is None else F.data_ptr(), _stream_handle(stream), ctypes.byref(fl)),
+           "amg_iga_assemble")
+    return fl.value
+
+
+def iga_assemble(n, p, nq=0, geometry=AMG_GEOM_CUBE, with_boundary=False, source=AMG_SRC_ONE, kappa=None,
+                 load=True, stream=None, device=None):
+    """K (CSR) and F of a patch as new device tensors: dict with rowptr, col,
+    val, F (or None), n, flops."""
+    import torch
+
+    P, keep = _iga_patch(n, p, nq, geometry, with_boundary, source, kappa)
+    N, Z = amg_iga_size(P)
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    rowptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(max(Z, 1), dtype=torch.int32, device=dev)
+    val = torch.empty(max(Z, 1), dtype=torch.float64, device=dev)
+    F = torch.empty(max(N, 1), dtype=torch.float64, device=dev) if load else None
+    fl = amg_iga_assemble(P, rowptr, col, val, F, stream)
+    del keep
+    return {"rowptr": rowptr, "col": col[:Z], "val": val[:Z], "F": None if F is None else F[:N], "n": N,
+            "flops": fl}
 
 
 def amg_dfma_probe(blocks: int, trips: int, out, stream=None) -> float:

@@ -832,6 +832,7 @@ int join_caller(amg_hierarchy* h) {
 
 namespace amg {
 int join_caller_stream(amg_hierarchy* h) { return join_caller(h); }
+int report_cuda(cudaError_t e, const char* what) { return cuda_fail(e, what); }
 }  // namespace amg
 
 namespace {

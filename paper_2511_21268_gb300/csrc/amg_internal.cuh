@@ -353,6 +353,9 @@ void sp_coarse(int n, const double* Ainv, const A* f, A* e, const SolveState* st
 int join_caller_stream(amg_hierarchy* h);
 // amg_api.cu: stream-ordered device allocation from the library's memory pool
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
+// Records a CUDA error for amg_last_cuda_error; AMG_ERR_NOMEM for an
+// allocation failure, else AMG_ERR_CUDA.
+int report_cuda(cudaError_t e, const char* what);
 cudaError_t launch_interleave(int n, int R, int64_t ld, const double* src, double* dst, cudaStream_t s);
 cudaError_t launch_deinterleave(int n, int R, int64_t ld, const double* src, double* dst, cudaStream_t s);
 // batch assembly (setup_kernels.cu)

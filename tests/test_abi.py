@@ -57,3 +57,30 @@ def test_options_struct_defaults_through_the_binding_layout():
     assert (o.precision, o.flexible, o.resid_replace_every, o.matrix_format) == (amg.AMG_FP64, 0, 20, 2)
     assert o.mpnn_weights is None and o.mpnn_bf16 == 1
 
+
+
+def test_iga_size_closed_form_and_argument_checks():
+    """amg_iga_size (host only): m^3 unknowns and the band's entry count
+    (sum over rows of the per-direction band widths, cubed), and the
+    argument checks of the assembly entry points."""
+    from paper_2511_21268_gb300 import amg
+
+    L = amg.lib()
+    for n, p, wb in [(1, 1, 1), (1, 1, 0), (3, 2, 0), (7, 3, 1), (64, 3, 0), (96, 3, 1)]:
+        P, _ = amg._iga_patch(n, p, with_boundary=wb)
+        N, Z = amg.amg_iga_size(P)
+        m = n + p if wb else n + p - 2
+        T = sum(min(p, m - 1 - i) + min(p, i) + 1 for i in range(m))
+        assert (N, Z) == (m ** 3, T ** 3)
+    for bad in (dict(n=0, p=2), dict(n=4, p=0), dict(n=4, p=9), dict(n=4, p=2, nq=17), dict(n=300, p=2, nq=3),
+                dict(n=4, p=2, geometry=7), dict(n=4, p=2, source=5)):
+        P, _ = amg._iga_patch(**bad)
+        try:
+            amg.amg_iga_size(P)
+            raise AssertionError(bad)
+        except amg.AmgError as e:
+            assert e.code == amg.AMG_ERR_ARG
+    P, _ = amg._iga_patch(4, 2)
+    P.kappa_m = 3  # features without their arrays
+    assert L.amg_iga_size(ctypes.byref(P), ctypes.byref(ctypes.c_int64()), ctypes.byref(ctypes.c_int64())) == -1
+    assert L.amg_iga_assemble(None, None, None, None, None, None, None) == -1

@@ -83,3 +83,7 @@ def test_documented_option_defaults_are_the_defaults():
             assert got == getattr(amg, text), field
         else:
             assert got == type(got)(float(text) if "." in text else int(text)), (field, got, text)
+
+
+def test_iga_patch_struct_mirrors_header():
+    check("amg_iga_patch", amg.AmgIgaPatch)

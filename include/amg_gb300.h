@@ -258,6 +258,15 @@ int amg_export_level(const amg_hierarchy* h, int32_t level, int64_t* rowptr, int
 int amg_export_prolongator(const amg_hierarchy* h, int32_t level, int64_t* nnz, int64_t* rowptr, int32_t* col,
                            double* val);
 
+/* The coarsest level's dense factorisation on the host: *n (required)
+ * receives its size n_L; L[n_L^2] (may be NULL) the Cholesky factor,
+ * row-major with zeros above the diagonal (l_jj = sqrt(a_jj - sum_k<j
+ * l_jk^2), l_ij = (a_ij - sum_k<j l_ik l_jk) / l_jj, k ascending, each product
+ * and difference rounded once); Ainv[n_L^2] (may be NULL) the inverse the
+ * V-cycle applies, row-major (column c = L^-T L^-1 e_c by forward and
+ * backward substitution).  AMG_ERR_ARG without a hierarchy. */
+int amg_export_coarse(const amg_hierarchy* h, int32_t* n, double* L, double* Ainv);
+
 /* Copy matching pass s of level l to host buffers: mate[n_s] (partner or
  * -1 for a singleton), agg[n_s], pval[n_s]; *n_s = rows the pass matched. */
 int amg_export_pass(const amg_hierarchy* h, int32_t level, int32_t pass, int64_t* n_s, int32_t* mate, int32_t* agg,
@@ -282,14 +291,20 @@ int amg_kernel_times(const amg_hierarchy* h, double* ms, int64_t* count, double*
 
 /* FP64 FMA throughput probe (measurement support; no paper counterpart):
  * enqueues on cuda_stream (NULL = default stream) one kernel of `blocks`
- * blocks x 256 threads, each thread running 8 independent FMA chains for
+ * blocks, each thread running independent FMA chains x <- x a + b for
  * trips x 16 steps, and returns at once (time it with events on the same
- * stream).  out_dev: DEVICE array of blocks x 256 doubles that receives the
- * chains' sums (keeps the work observable).  *flops (host, may be NULL):
- * the kernel's floating-point operations, 2 per FMA.  Used to measure the
- * FP64 rate that bounds the FP64 matrix passes.  Errors: AMG_ERR_ARG
- * (blocks < 1, trips < 1, out_dev NULL), AMG_ERR_CUDA. */
-int amg_dfma_probe(int32_t blocks, int64_t trips, double* out_dev, void* cuda_stream, double* flops);
+ * stream).  `variant` picks the chain count, whether the chains share their
+ * operands and the block size (*threads, host, receives it): the rate
+ * depends on these beyond the FMA count, so a caller times every variant
+ * and keeps the fastest.  variant = -1 writes the number of variants to
+ * *threads; blocks = 0 only writes the variant's block size.  out_dev:
+ * DEVICE array of blocks x *threads doubles that receives the chains' sums
+ * (keeps the work observable).  *flops (host, may be NULL): the kernel's
+ * floating-point operations, 2 per FMA.  Used to measure the FP64 rate that
+ * bounds the FP64 matrix passes.  Errors: AMG_ERR_ARG (bad variant, blocks <
+ * 0, trips < 1, out_dev NULL), AMG_ERR_CUDA. */
+int amg_dfma_probe(int32_t variant, int32_t blocks, int64_t trips, double* out_dev, void* cuda_stream,
+                   int32_t* threads, double* flops);
 
 /* Largest system amg_relres_noalloc accepts (rows). */
 #define AMG_NOALLOC_MAX_ROWS (1 << 19)

@@ -106,6 +106,7 @@ _SIGS = {
     "amg_export_level": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 7),
     "amg_export_pass": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 4),
     "amg_export_prolongator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 4),
+    "amg_export_coarse": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "amg_free": (ctypes.c_int, [ctypes.c_void_p]),
     "amg_kernel_launches": (ctypes.c_int64, []),
     "amg_relres_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -126,8 +127,8 @@ _SIGS = {
                                        ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p]),
     "amg_set_damping": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
-    "amg_dfma_probe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
-                                      ctypes.c_void_p]),
+    "amg_dfma_probe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "amg_smoother_bound": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "amg_staged_wait_selftest": (ctypes.c_int, [ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "amg_iga_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -538,12 +539,37 @@ def iga_assemble(n, p, nq=0, geometry=AMG_GEOM_CUBE, with_boundary=False, source
             "flops": fl}
 
 
-def amg_dfma_probe(blocks: int, trips: int, out, stream=None) -> float:
-    """Enqueue the FP64 FMA throughput kernel; returns its flop count."""
+def amg_dfma_probe_variants() -> int:
+    """Number of FP64 probe variants."""
+    n = ctypes.c_int32()
+    _check(lib().amg_dfma_probe(-1, 0, 1, None, None, ctypes.byref(n), None), "amg_dfma_probe")
+    return n.value
+
+
+def amg_dfma_probe_threads(variant: int) -> int:
+    """Block size of FP64 probe variant `variant`."""
+    t = ctypes.c_int32()
+    _check(lib().amg_dfma_probe(int(variant), 0, 1, None, None, ctypes.byref(t), None), "amg_dfma_probe")
+    return t.value
+
+
+def amg_dfma_probe(variant: int, blocks: int, trips: int, out, stream=None) -> float:
+    """Enqueue FP64 probe variant `variant`; returns its flop count."""
     fl = ctypes.c_double()
-    _check(lib().amg_dfma_probe(int(blocks), int(trips), out.data_ptr(), _stream_handle(stream), ctypes.byref(fl)),
-           "amg_dfma_probe")
+    t = ctypes.c_int32()
+    _check(lib().amg_dfma_probe(int(variant), int(blocks), int(trips), out.data_ptr(), _stream_handle(stream),
+                                ctypes.byref(t), ctypes.byref(fl)), "amg_dfma_probe")
     return fl.value
+
+
+def amg_export_coarse(h):
+    """(L, Ainv) of the coarsest level's dense factorisation, host arrays."""
+    n = ctypes.c_int32()
+    _check(lib().amg_export_coarse(h, ctypes.byref(n), None, None), "amg_export_coarse")
+    L = np.zeros((n.value, n.value))
+    Ai = np.zeros((n.value, n.value))
+    _check(lib().amg_export_coarse(h, ctypes.byref(n), L.ctypes.data, Ai.ctypes.data), "amg_export_coarse")
+    return L, Ai
 
 
 def amg_export_prolongator(h, level: int, n: int):
@@ -643,6 +669,9 @@ class Hierarchy:
 
     def export_prolongator(self, l: int):
         return amg_export_prolongator(self._h, l, self.level_n(l))
+
+    def export_coarse(self):
+        return amg_export_coarse(self._h)
 
     # learned smoother damping
     def mpnn_apply(self, w=None, bf16_weights: bool = True):

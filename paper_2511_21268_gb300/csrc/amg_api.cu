@@ -1433,6 +1433,19 @@ int amg_export_prolongator(const amg_hierarchy* hc, int32_t level, int64_t* nnz,
     return AMG_OK;
 }
 
+int amg_export_coarse(const amg_hierarchy* hc, int32_t* n, double* L, double* Ainv) {
+    amg_hierarchy* h = const_cast<amg_hierarchy*>(hc);
+    if (!h || !n || !h->Ainv) return AMG_ERR_ARG;
+    RC(join_caller(h));
+    const int nd = h->ndense;
+    *n = nd;
+    const size_t bytes = sizeof(double) * (size_t)nd * nd;
+    if (Ainv) CK(cudaMemcpyAsync(Ainv, h->Ainv, bytes, cudaMemcpyDeviceToHost, h->s));
+    if (L) CK(cudaMemcpyAsync(L, h->Ainv + (size_t)nd * nd, bytes, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return AMG_OK;
+}
+
 int amg_export_pass(const amg_hierarchy* hc, int32_t level, int32_t pass, int64_t* n_s, int32_t* mate, int32_t* agg,
                     double* pval) {
     amg_hierarchy* h = const_cast<amg_hierarchy*>(hc);

@@ -396,9 +396,13 @@ __global__ void __launch_bounds__(32 * kCtWarps) k_iga_outer(int64_t IN, int Q, 
 }
 
 // Last contraction (the innermost axis, q1) and the CSR scatter: rows
-// o = r3 R + r2 of the ng direction-1 groups X_g[o][q1], warp per row, lanes
-// over r1; K(I, J) = sum_g sum_k W_g[r1][k] X_g[o][s[r1] + k] goes to the
-// position of J in row I (columns in (delta3, delta2, delta1) order).
+// o = r3 R + r2 of the ng direction-1 groups X_g[o][q1];
+// K(I, J) = sum_g sum_k W_g[r1][k] X_g[o][s[r1] + k] goes to the position of
+// J in row I (columns in (delta3, delta2, delta1) order).  A block stages
+// `rows` consecutive rows of every group in shared memory (row stride Q + 1);
+// thread t takes row t % rows and the pairs r1 = t / rows + k (256 / rows), so
+// the lanes that share r1 read the same weights (a broadcast) and rows a
+// padded stride apart.
 struct InnerGroups {
     const double* X[4];
     const double* W[4];
@@ -410,21 +414,25 @@ __device__ __forceinline__ void band_range(int i, int m, int p, int& lo, int& nv
     nv = min(p, m - 1 - i) - lo + 1;
 }
 
-__global__ void __launch_bounds__(32 * kInRows) k_iga_inner_csr(IgaDims d, InnerGroups G, const int* __restrict__ s,
-                                                                const int* __restrict__ L,
-                                                                const int64_t* __restrict__ rowptr, double* val) {
-    extern __shared__ double xs[];  // [ng][kInRows][Q + 1]
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+constexpr int kInThreads = 256;
+
+template <int NG>
+__global__ void __launch_bounds__(kInThreads) k_iga_inner_csr(IgaDims d, InnerGroups G, int rows,
+                                                              const int* __restrict__ s, const int* __restrict__ L,
+                                                              const int64_t* __restrict__ rowptr, double* val) {
+    extern __shared__ double xs[];  // [NG][rows][Q + 1]
     const int64_t O = (int64_t)d.R * d.R;
-    const int64_t o0 = (int64_t)blockIdx.x * kInRows;
+    const int64_t o0 = (int64_t)blockIdx.x * rows;
     const int Qp = d.Q + 1;
-    for (int g = 0; g < G.ng; g++)
-        for (int t = threadIdx.x; t < kInRows * d.Q; t += blockDim.x) {
+#pragma unroll
+    for (int g = 0; g < NG; g++)
+        for (int t = threadIdx.x; t < rows * d.Q; t += blockDim.x) {
             const int row = t / d.Q, q = t % d.Q;
-            xs[((int64_t)g * kInRows + row) * Qp + q] = o0 + row < O ? G.X[g][(o0 + row) * d.Q + q] : 0.0;
+            xs[((int64_t)g * rows + row) * Qp + q] = o0 + row < O ? G.X[g][(o0 + row) * d.Q + q] : 0.0;
         }
     __syncthreads();
-    const int64_t o = o0 + w;
+    const int row = threadIdx.x % rows, slot = threadIdx.x / rows, nslot = kInThreads / rows;
+    const int64_t o = o0 + row;
     if (o >= O) return;
     const int r3 = (int)(o / d.R), r2 = (int)(o % d.R);
     const int i3 = r3 / d.B, d3 = r3 % d.B - d.p, i2 = r2 / d.B, d2 = r2 % d.B - d.p;
@@ -433,15 +441,17 @@ __global__ void __launch_bounds__(32 * kInRows) k_iga_inner_csr(IgaDims d, Inner
     int lo3, nv3, lo2, nv2;
     band_range(i3, d.m, d.p, lo3, nv3);
     band_range(i2, d.m, d.p, lo2, nv2);
-    for (int r1 = lane; r1 < d.R; r1 += 32) {
+    const double* xr = xs + (int64_t)row * Qp;
+    for (int r1 = slot; r1 < d.R; r1 += nslot) {
         const int i1 = r1 / d.B, d1 = r1 % d.B - d.p, j1 = i1 + d1;
         if (j1 < 0 || j1 >= d.m) continue;
         const int st = s[r1], len = L[r1];
         double acc = 0.0;
-        for (int g = 0; g < G.ng; g++) {
-            const double* x = xs + ((int64_t)g * kInRows + w) * Qp + st;
+#pragma unroll
+        for (int g = 0; g < NG; g++) {
+            const double* x = xr + (int64_t)g * rows * Qp + st;
             const double* wt = G.W[g] + (int64_t)r1 * d.Lmax;
-            for (int k = 0; k < len; k++) acc = fma(wt[k], x[k], acc);
+            for (int k = 0; k < len; k++) acc = fma(__ldg(wt + k), x[k], acc);
         }
         int lo1, nv1;
         band_range(i1, d.m, d.p, lo1, nv1);
@@ -724,11 +734,24 @@ extern "C" int amg_iga_assemble(const amg_iga_patch* P, int64_t* rowptr, int32_t
     }
     G.X[G.ng] = Gvv;
     G.W[G.ng++] = Wvv;
-    const size_t smi = (size_t)G.ng * kInRows * (Q + 1) * sizeof(double);
-    if ((err = cudaFuncSetAttribute(k_iga_inner_csr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smi)) !=
-        cudaSuccess)
-        return report_cuda(err, "amg_iga_assemble smem");
-    k_iga_inner_csr<<<AMG_GRID(nblk(R2, kInRows)), 32 * kInRows, smi, s>>>(d, G, sp, Lp, rowptr, val);
+    // rows per block of the last contraction: 16 (two pairs per warp), fewer
+    // when the staged rows would not fit the shared memory
+    int optin = 0, devi = 0;
+    if ((err = cudaGetDevice(&devi)) != cudaSuccess ||
+        (err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, devi)) != cudaSuccess)
+        return report_cuda(err, "amg_iga_assemble device");
+    int rows = 16;
+    while (rows > 1 && (size_t)G.ng * rows * (Q + 1) * sizeof(double) > (size_t)optin) rows >>= 1;
+    const size_t smi = (size_t)G.ng * rows * (Q + 1) * sizeof(double);
+    if (smi > (size_t)optin) return AMG_ERR_ARG;
+    auto inner = [&](auto kern) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smi);
+        if (e != cudaSuccess) return e;
+        kern<<<AMG_GRID(nblk(R2, rows)), kInThreads, smi, s>>>(d, G, rows, sp, Lp, rowptr, val);
+        return cudaGetLastError();
+    };
+    err = G.ng == 4 ? inner(k_iga_inner_csr<4>) : inner(k_iga_inner_csr<2>);
+    if (err != cudaSuccess) return report_cuda(err, "amg_iga_assemble last contraction");
     if (F) {
         const size_t smf = (size_t)kInRows * (Q + 1) * sizeof(double);
         if ((err = cudaFuncSetAttribute(k_iga_inner_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,

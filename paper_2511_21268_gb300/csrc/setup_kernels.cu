@@ -845,18 +845,21 @@ __global__ void k_cholesky(int n, double* D, int* flag) {
                 atomicOr(flag, 16);
                 piv = 1.0;
             } else {
-                piv = sqrt(djj);
+                piv = __dsqrt_rn(djj);
             }
             D[(int64_t)j * n + j] = piv;
         }
         __syncthreads();
         const double ljj = piv;
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) D[(int64_t)i * n + j] /= ljj;
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x)
+            D[(int64_t)i * n + j] = __ddiv_rn(D[(int64_t)i * n + j], ljj);
         __syncthreads();
         const int m = n - j - 1;
         for (int64_t t = threadIdx.x; t < (int64_t)m * m; t += blockDim.x) {
             const int i = j + 1 + (int)(t / m), k = j + 1 + (int)(t % m);
-            if (k <= i) D[(int64_t)i * n + k] -= D[(int64_t)i * n + j] * D[(int64_t)k * n + j];
+            if (k <= i)
+                D[(int64_t)i * n + k] =
+                    __dsub_rn(D[(int64_t)i * n + k], __dmul_rn(D[(int64_t)i * n + j], D[(int64_t)k * n + j]));
         }
         __syncthreads();
     }
@@ -871,21 +874,22 @@ __global__ void k_chol_inverse(int n, const double* __restrict__ L, double* Ainv
         for (int k = 0; k < n; k++) {  // forward: L y = e_c
             __shared__ double yk;
             if (threadIdx.x == 0) {
-                yk = y[k] / L[(int64_t)k * n + k];
+                yk = __ddiv_rn(y[k], L[(int64_t)k * n + k]);
                 y[k] = yk;
             }
             __syncthreads();
-            for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) y[i] -= L[(int64_t)i * n + k] * yk;
+            for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x)
+                y[i] = __dsub_rn(y[i], __dmul_rn(L[(int64_t)i * n + k], yk));
             __syncthreads();
         }
         for (int k = n - 1; k >= 0; k--) {  // backward: L^T x = y
             __shared__ double xk;
             if (threadIdx.x == 0) {
-                xk = y[k] / L[(int64_t)k * n + k];
+                xk = __ddiv_rn(y[k], L[(int64_t)k * n + k]);
                 y[k] = xk;
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] -= L[(int64_t)k * n + i] * xk;
+            for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = __dsub_rn(y[i], __dmul_rn(L[(int64_t)k * n + i], xk));
             __syncthreads();
         }
         for (int i = threadIdx.x; i < n; i += blockDim.x) Ainv[(int64_t)i * n + c] = y[i];
@@ -1206,11 +1210,20 @@ cudaError_t launch_dense_from_csr(const DevCSR& A, double* D, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// D (n x n, overwritten by its Cholesky factor); Ainv receives the inverse.
-// Ainv must have room for 2 n^2 doubles (second half is work space).
+// Lower triangle of the factor, zeros above (row-major n x n).
+__global__ void k_keep_factor(int n, const double* __restrict__ D, double* L) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * n;
+         t += (int64_t)gridDim.x * blockDim.x)
+        L[t] = (t % n) <= (t / n) ? D[t] : 0.0;
+}
+
+// D (n x n, overwritten by its Cholesky factor); Ainv receives the inverse
+// in its first n^2 doubles and the factor L (zeros above the diagonal) in
+// the second n^2 (work space of the inverse before).
 cudaError_t launch_dense_spd_inverse(int n, double* D, double* Ainv, int* flag, cudaStream_t s) {
     k_cholesky<<<AMG_GRID(1), 1024, 0, s>>>(n, D, flag);
     k_chol_inverse<<<AMG_GRID(blocks_for(n, 1, 4096)), kBlock, 0, s>>>(n, D, Ainv, Ainv + (int64_t)n * n);
+    k_keep_factor<<<AMG_GRID(blocks_for((int64_t)n * n, kBlock, 1024)), kBlock, 0, s>>>(n, D, Ainv + (int64_t)n * n);
     return cudaGetLastError();
 }
 

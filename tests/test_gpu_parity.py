@@ -62,6 +62,19 @@ def assert_setup_identical(H, Ho):
                 assert np.array_equal(mg, mo), f"level {l} pass {s} matching"
                 assert np.array_equal(ag, ao)
                 assert np.array_equal(pg.view(np.uint64), po.view(np.uint64))
+    # a9: the coarsest level's Cholesky factor bit for bit (same operation
+    # order, each product and difference rounded once), its inverse against
+    # numpy's inverse of the coarse matrix
+    Lg, Ai = H.export_coarse()
+    Lo = Ho.coarse_chol()
+    assert np.array_equal(Lg.view(np.uint64), Lo.view(np.uint64)), "coarse Cholesky factor"
+    rp, ci, v = Ho.level_csr(H.num_levels - 1)
+    nc = len(rp) - 1
+    Kc = np.zeros((nc, nc))
+    for i in range(nc):
+        Kc[i, ci[rp[i]:rp[i + 1]]] = v[rp[i]:rp[i + 1]]
+    inv = np.linalg.inv(Kc)
+    assert np.abs(Ai - inv).max() <= 1e-11 * np.abs(inv).max(), "coarse inverse"
 
 
 @pytest.mark.parametrize("d,n,p", CASES)

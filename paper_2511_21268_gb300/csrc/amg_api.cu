@@ -231,14 +231,20 @@ int pow2ceil(int x) {
 }
 
 // One matching pass on A with test vector w: fills P and the coarse matrix C
-// (allocated in the hierarchy) and the coarse test vector *wc.
-int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevCSR& C, double** wc) {
+// (allocated in the hierarchy) and the coarse test vector *wc.  kii_known:
+// A's diagonal when the caller has it (a level's first pass), else NULL.
+int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevCSR& C, double** wc,
+               const double* kii_known) {
     const int n = A.n;
     cudaStream_t s = h->s;
-    double* kii = nullptr;
+    const double* kii = kii_known;
     Tmp tk(s), tkey(s), tstate(s), tcand(s), tlead(s), tcidx(s), tscan(s);
-    RC(tk.get(&kii, n));
-    CK(launch_diag(A, kii, s));
+    if (!kii) {
+        double* kd = nullptr;
+        RC(tk.get(&kd, n));
+        CK(launch_diag(A, kd, s));
+        kii = kd;
+    }
     uint64_t* key;
     int32_t *state, *cand, *leader, *cidx, *scr;
     RC(tkey.get(&key, A.nnz));
@@ -558,7 +564,7 @@ int build(amg_hierarchy* h, const amg_csr* K) {
         F.npass = h->o.match_passes;
         for (int q = 0; q < F.npass; q++) {
             next = DevCSR{};
-            RC(match_pass(h, cur, cw, F.pass[q], next, &nw));
+            RC(match_pass(h, cur, cw, F.pass[q], next, &nw, q == 0 ? F.kii : nullptr));
             if (q > 0) {  // intermediate pass matrix no longer needed
                 free_level_matrix(h, cur);
                 forget(h, cw);

@@ -734,14 +734,15 @@ extern "C" int amg_iga_assemble(const amg_iga_patch* P, int64_t* rowptr, int32_t
     }
     G.X[G.ng] = Gvv;
     G.W[G.ng++] = Wvv;
-    // rows per block of the last contraction: 16 (two pairs per warp), fewer
-    // when the staged rows would not fit the shared memory
+    // rows per block of the last contraction: 8 (four pairs per warp), so
+    // that several blocks share an SM (16 rows left one block, 8 warps, per
+    // SM: 12 % of the warp slots); fewer when the staged rows do not fit
     int optin = 0, devi = 0;
     if ((err = cudaGetDevice(&devi)) != cudaSuccess ||
         (err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, devi)) != cudaSuccess)
         return report_cuda(err, "amg_iga_assemble device");
-    int rows = 16;
-    while (rows > 1 && (size_t)G.ng * rows * (Q + 1) * sizeof(double) > (size_t)optin) rows >>= 1;
+    int rows = 8;
+    while (rows > 1 && (size_t)G.ng * rows * (Q + 1) * sizeof(double) > (size_t)optin / 2) rows >>= 1;
     const size_t smi = (size_t)G.ng * rows * (Q + 1) * sizeof(double);
     if (smi > (size_t)optin) return AMG_ERR_ARG;
     auto inner = [&](auto kern) {

@@ -100,15 +100,19 @@ __global__ void __launch_bounds__(kBlock) k_l1diag(int n, const int64_t* __restr
                                                     const int32_t* __restrict__ ci, const double* __restrict__ v,
                                                     double* kii, double* dl1, double* invd, int* flag) {
     __shared__ double tiles[kWarpsPerBlock][32][33];
+    __shared__ double diags[kWarpsPerBlock][32];  // the rows' diagonal entries (0 when a row has none)
     double(*tile)[33] = tiles[threadIdx.x >> 5];
+    double* dg = diags[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int row0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; row0 < n; row0 += nwarps * 32) {
+        dg[lane] = 0.0;
+        __syncwarp();
         auto term = [&](int64_t k, int row) -> double {
             const int j = ci[k];
             const double x = v[k];
             if (j == row) {
-                kii[row] = x;
+                dg[row - row0] = x;
                 return 0.0;
             }
             return fabs(x);
@@ -117,7 +121,8 @@ __global__ void __launch_bounds__(kBlock) k_l1diag(int n, const int64_t* __restr
         __syncwarp();
         const int i = row0 + lane;
         if (i < n) {
-            const double d = kii[i];
+            const double d = dg[lane];
+            kii[i] = d;
             if (!(d > 0.0)) atomicOr(flag, 1);
             const double dl = __dadd_rn(d, s);
             dl1[i] = dl;

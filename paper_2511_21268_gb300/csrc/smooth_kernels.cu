@@ -45,6 +45,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "amg_internal.cuh"
 
@@ -55,9 +56,10 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kSpWarps = 8;  // warps per block of the SpGEMM row kernels (fewer if shared memory is short)
 constexpr int kSpBatch = 8;  // rounds of 32 items whose loads a warp keeps in flight together
-constexpr int kSpBlk = 256;  // threads of the block-per-row kernel (also the A entries it stages at once)
-constexpr int kSpUnroll = 4;  // B entries a thread of that kernel loads before it accumulates them
-constexpr double kSpLongRow = 128.0;  // average B row length from which the block-per-row kernel is used
+constexpr int kSpUnroll = 4;  // B entries a thread of the block-per-row kernel loads before it accumulates them
+constexpr double kSpMidRow = 16.0;    // average B row length from which the block-per-row kernel (64 threads) runs
+constexpr double kSpLongRow = 256.0;  // ... and from which it runs with 256 threads
+constexpr size_t kSpBitsBudget = (size_t)4 << 30;  // bytes of stored row bitmaps, at most
 
 enum SpMode { SP_COUNT = 0, SP_COLS = 1, SP_VALUES = 2, SP_UPPER = 3 };
 
@@ -241,46 +243,47 @@ __global__ void k_sp_row(int n, const int64_t* __restrict__ arp, const int32_t* 
                 cci[cb + pos++] = lo + (w << 5) + bit;
             }
         }
-        if (MODE == SP_COLS) continue;
-        for (int u = lane; u < total; u += 32) acc[u] = 0.0;
-        __syncwarp();
-        const unsigned below = (1u << lane) - 1u;
-        for (int64_t tb = a0; tb < a1; tb += 32) {
-            int64_t q0;
-            int len, incl, tot;
-            double a;
-            chunk_open(aci, av, brp, bci, tb, a1, lane, MODE == SP_UPPER ? i : -1, q0, len, incl, tot, a);
-            for (int fb = 0; fb < tot; fb += 32 * kSpBatch) {
-                int J[kSpBatch];
-                double x[kSpBatch], y[kSpBatch];
-#pragma unroll
-                for (int u = 0; u < kSpBatch; u++) {
-                    const int f = fb + 32 * u + lane;
-                    const int64_t q = chunk_item(f, q0, len, incl, a, x[u]);
-                    J[u] = -1;
-                    y[u] = 0.0;
-                    if (f < tot) {
-                        J[u] = bci[q] - lo;
-                        y[u] = bv[q];
+        if constexpr (MODE != SP_COLS) {
+            for (int u = lane; u < total; u += 32) acc[u] = 0.0;
+            __syncwarp();
+            const unsigned below = (1u << lane) - 1u;
+            for (int64_t tb = a0; tb < a1; tb += 32) {
+                int64_t q0;
+                int len, incl, tot;
+                double a;
+                chunk_open(aci, av, brp, bci, tb, a1, lane, MODE == SP_UPPER ? i : -1, q0, len, incl, tot, a);
+                for (int fb = 0; fb < tot; fb += 32 * kSpBatch) {
+                    int J[kSpBatch];
+                    double x[kSpBatch], y[kSpBatch];
+    #pragma unroll
+                    for (int u = 0; u < kSpBatch; u++) {
+                        const int f = fb + 32 * u + lane;
+                        const int64_t q = chunk_item(f, q0, len, incl, a, x[u]);
+                        J[u] = -1;
+                        y[u] = 0.0;
+                        if (f < tot) {
+                            J[u] = bci[q] - lo;
+                            y[u] = bv[q];
+                        }
+                    }
+    #pragma unroll
+                    for (int u = 0; u < kSpBatch; u++) {
+                        if (fb + 32 * u >= tot) break;  // warp-uniform
+                        int r = -1 - lane;
+                        if (J[u] >= 0) r = pre[J[u] >> 5] + __popc(bits[J[u] >> 5] & ((1u << (J[u] & 31)) - 1u));
+                        const unsigned grp = __match_any_sync(FULL, r);
+                        const int pos = __popc(grp & below);
+                        const int npos = __reduce_max_sync(FULL, (unsigned)pos);
+                        const double prod = __dmul_rn(x[u], y[u]);
+                        for (int k = 0; k <= npos; k++) {
+                            if (r >= 0 && pos == k) acc[r] = __dadd_rn(acc[r], prod);
+                            __syncwarp();
+                        }
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < kSpBatch; u++) {
-                    if (fb + 32 * u >= tot) break;  // warp-uniform
-                    int r = -1 - lane;
-                    if (J[u] >= 0) r = pre[J[u] >> 5] + __popc(bits[J[u] >> 5] & ((1u << (J[u] & 31)) - 1u));
-                    const unsigned grp = __match_any_sync(FULL, r);
-                    const int pos = __popc(grp & below);
-                    const int npos = __reduce_max_sync(FULL, (unsigned)pos);
-                    const double prod = __dmul_rn(x[u], y[u]);
-                    for (int k = 0; k <= npos; k++) {
-                        if (r >= 0 && pos == k) acc[r] = __dadd_rn(acc[r], prod);
-                        __syncwarp();
-                    }
-                }
-            }
         }
         for (int u = lane; u < total; u += 32) cv[cb + u] = acc[u];
+        }
         __syncwarp();
     }
     if (MODE == SP_COUNT) {
@@ -289,35 +292,37 @@ __global__ void k_sp_row(int n, const int64_t* __restrict__ arp, const int32_t* 
     }
 }
 
-// The same passes with one block of kSpBlk threads per output row (see the
+// The same passes with one block of BT threads per output row (see the
 // file header).  Shared memory: bits[wmax], pre[wmax], acc[cmax] (value
 // modes), then the staged A entries of the numeric pass (B range start and
-// length, value) and a reduction scratch.
-template <int MODE>
-__global__ void __launch_bounds__(kSpBlk) k_sp_row_blk(int n, const int64_t* __restrict__ arp,
-                                                       const int32_t* __restrict__ aci, const double* __restrict__ av,
-                                                       const int64_t* __restrict__ brp, const int32_t* __restrict__ bci,
-                                                       const double* __restrict__ bv, int wmax, int cmax,
-                                                       int64_t* __restrict__ rowcnt, int* maxc,
-                                                       const int64_t* __restrict__ crp, int32_t* __restrict__ cci,
-                                                       double* __restrict__ cv, int* flag) {
+// length, value) and a reduction scratch.  With gbits (global, wmax words
+// per row) the counting pass stores each row's bitmap and the later passes
+// load it instead of marking the row again.
+template <int MODE, int BT>
+__global__ void __launch_bounds__(BT) k_sp_row_blk(int n, const int64_t* __restrict__ arp,
+                                                   const int32_t* __restrict__ aci, const double* __restrict__ av,
+                                                   const int64_t* __restrict__ brp, const int32_t* __restrict__ bci,
+                                                   const double* __restrict__ bv, int wmax, int cmax,
+                                                   int64_t* __restrict__ rowcnt, int* maxc,
+                                                   const int64_t* __restrict__ crp, int32_t* __restrict__ cci,
+                                                   double* __restrict__ cv, uint32_t* gbits, int* flag) {
     extern __shared__ __align__(16) unsigned char sp_smem[];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    constexpr int NW = kSpBlk / 32;
+    constexpr int NW = BT / 32;
     uint32_t* bits = reinterpret_cast<uint32_t*>(sp_smem);
     int32_t* pre = reinterpret_cast<int32_t*>(sp_smem + (size_t)4 * wmax);
     double* acc = reinterpret_cast<double*>(sp_smem + (size_t)8 * wmax);
     unsigned char* tail = sp_smem + (size_t)8 * wmax + (MODE >= SP_VALUES ? (size_t)8 * cmax : 0);
     int64_t* sq0 = reinterpret_cast<int64_t*>(tail);
-    double* sa = reinterpret_cast<double*>(tail + 8 * kSpBlk);
-    int* slen = reinterpret_cast<int*>(tail + 16 * kSpBlk);
-    int* red = reinterpret_cast<int*>(tail + 20 * kSpBlk);  // [0..NW) lo, [NW..2NW) hi, [2NW] total
+    double* sa = reinterpret_cast<double*>(tail + 8 * BT);
+    int* slen = reinterpret_cast<int*>(tail + 16 * BT);
+    int* red = reinterpret_cast<int*>(tail + 20 * BT);  // [0..NW) lo, [NW..2NW) hi, [2NW] total
     int best = 0;
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
         const int64_t a0 = arp[i], a1 = arp[i + 1];
         // column span of the row
         int l = 0x7fffffff, hmax = -1;
-        for (int64_t t = a0 + tid; t < a1; t += kSpBlk) {
+        for (int64_t t = a0 + tid; t < a1; t += BT) {
             const int k = aci[t];
             const int64_t b0 = brp[k], b1 = brp[k + 1];
             if (b1 > b0) {
@@ -344,22 +349,29 @@ __global__ void __launch_bounds__(kSpBlk) k_sp_row_blk(int n, const int64_t* __r
             __syncthreads();
             continue;
         }
-        for (int w = tid; w < W; w += kSpBlk) bits[w] = 0u;
-        __syncthreads();
-        // mark: warp wid takes A's entries a0 + wid, a0 + wid + NW, ...
-        for (int64_t t = a0 + wid; t < a1; t += NW) {
-            const int k = aci[t];
-            const int64_t b0 = brp[k], b1 = brp[k + 1];
-            for (int64_t q = b0 + lane; q < b1; q += 32 * kSpUnroll) {
-                int J[kSpUnroll];
+        uint32_t* gb = gbits ? gbits + (size_t)i * wmax : nullptr;
+        if (gb && MODE != SP_COUNT) {  // the counting pass's bitmap
+            for (int w = tid; w < W; w += BT) bits[w] = gb[w];
+        } else {
+            for (int w = tid; w < W; w += BT) bits[w] = 0u;
+            __syncthreads();
+            // mark: warp wid takes A's entries a0 + wid, a0 + wid + NW, ...
+            for (int64_t t = a0 + wid; t < a1; t += NW) {
+                const int k = aci[t];
+                const int64_t b0 = brp[k], b1 = brp[k + 1];
+                for (int64_t q = b0 + lane; q < b1; q += 32 * kSpUnroll) {
+                    int J[kSpUnroll];
 #pragma unroll
-                for (int u = 0; u < kSpUnroll; u++) J[u] = q + 32 * u < b1 ? bci[q + 32 * u] - lo : -1;
+                    for (int u = 0; u < kSpUnroll; u++) J[u] = q + 32 * u < b1 ? bci[q + 32 * u] - lo : -1;
 #pragma unroll
-                for (int u = 0; u < kSpUnroll; u++)
-                    if (J[u] >= 0) atomicOr(&bits[J[u] >> 5], 1u << (J[u] & 31));
+                    for (int u = 0; u < kSpUnroll; u++)
+                        if (J[u] >= 0) atomicOr(&bits[J[u] >> 5], 1u << (J[u] & 31));
+                }
             }
         }
         __syncthreads();
+        if (MODE == SP_COUNT && gb)
+            for (int w = tid; w < W; w += BT) gb[w] = bits[w];
         // exclusive prefix of the words' popcounts (warp 0, lane-contiguous chunks)
         if (wid == 0) {
             const int chunk = (W + 31) >> 5;
@@ -393,7 +405,7 @@ __global__ void __launch_bounds__(kSpBlk) k_sp_row_blk(int n, const int64_t* __r
             continue;
         }
         const int64_t cb = crp[i];
-        for (int w = tid; w < W; w += kSpBlk) {
+        for (int w = tid; w < W; w += BT) {
             uint32_t m = bits[w];
             int pos = pre[w];
             while (m) {
@@ -402,56 +414,54 @@ __global__ void __launch_bounds__(kSpBlk) k_sp_row_blk(int n, const int64_t* __r
                 cci[cb + pos++] = lo + (w << 5) + bit;
             }
         }
-        if (MODE == SP_COLS) {
-            __syncthreads();
-            continue;
-        }
-        for (int u = tid; u < total; u += kSpBlk) acc[u] = 0.0;
-        for (int64_t tb = a0; tb < a1; tb += kSpBlk) {
-            const int nt = (int)min((int64_t)kSpBlk, a1 - tb);
-            __syncthreads();  // the previous stage's entries are consumed
-            if (tid < nt) {
-                const int64_t t = tb + tid;
-                const int k = aci[t];
-                int64_t b0 = brp[k];
-                const int64_t b1 = brp[k + 1];
-                if (MODE == SP_UPPER) {  // first column >= i
-                    int64_t hb = b1;
-                    while (b0 < hb) {
-                        const int64_t mid = (b0 + hb) >> 1;
-                        if (bci[mid] < i) b0 = mid + 1;
-                        else hb = mid;
-                    }
-                }
-                sq0[tid] = b0;
-                slen[tid] = (int)(b1 - b0);
-                sa[tid] = av[t];
-            }
-            __syncthreads();
-            for (int u = 0; u < nt; u++) {
-                const int64_t q0 = sq0[u];
-                const int len = slen[u];
-                const double a = sa[u];
-                for (int x = tid; x < len; x += kSpBlk * kSpUnroll) {
-                    int J[kSpUnroll];
-                    double y[kSpUnroll];
-#pragma unroll
-                    for (int v = 0; v < kSpUnroll; v++) {
-                        const int xv = x + kSpBlk * v;
-                        J[v] = xv < len ? bci[q0 + xv] - lo : -1;
-                        y[v] = xv < len ? bv[q0 + xv] : 0.0;
-                    }
-#pragma unroll
-                    for (int v = 0; v < kSpUnroll; v++)
-                        if (J[v] >= 0) {
-                            const int r = pre[J[v] >> 5] + __popc(bits[J[v] >> 5] & ((1u << (J[v] & 31)) - 1u));
-                            acc[r] = __dadd_rn(acc[r], __dmul_rn(a, y[v]));
+        if constexpr (MODE != SP_COLS) {
+            for (int u = tid; u < total; u += BT) acc[u] = 0.0;
+            for (int64_t tb = a0; tb < a1; tb += BT) {
+                const int nt = (int)min((int64_t)BT, a1 - tb);
+                __syncthreads();  // the previous stage's entries are consumed
+                if (tid < nt) {
+                    const int64_t t = tb + tid;
+                    const int k = aci[t];
+                    int64_t b0 = brp[k];
+                    const int64_t b1 = brp[k + 1];
+                    if (MODE == SP_UPPER) {  // first column >= i
+                        int64_t hb = b1;
+                        while (b0 < hb) {
+                            const int64_t mid = (b0 + hb) >> 1;
+                            if (bci[mid] < i) b0 = mid + 1;
+                            else hb = mid;
                         }
+                    }
+                    sq0[tid] = b0;
+                    slen[tid] = (int)(b1 - b0);
+                    sa[tid] = av[t];
                 }
-                __syncthreads();  // successive t in ascending order
-            }
+                __syncthreads();
+                for (int u = 0; u < nt; u++) {
+                    const int64_t q0 = sq0[u];
+                    const int len = slen[u];
+                    const double a = sa[u];
+                    for (int x = tid; x < len; x += BT * kSpUnroll) {
+                        int J[kSpUnroll];
+                        double y[kSpUnroll];
+    #pragma unroll
+                        for (int v = 0; v < kSpUnroll; v++) {
+                            const int xv = x + BT * v;
+                            J[v] = xv < len ? bci[q0 + xv] - lo : -1;
+                            y[v] = xv < len ? bv[q0 + xv] : 0.0;
+                        }
+    #pragma unroll
+                        for (int v = 0; v < kSpUnroll; v++)
+                            if (J[v] >= 0) {
+                                const int r = pre[J[v] >> 5] + __popc(bits[J[v] >> 5] & ((1u << (J[v] & 31)) - 1u));
+                                acc[r] = __dadd_rn(acc[r], __dmul_rn(a, y[v]));
+                            }
+                    }
+                    __syncthreads();  // successive t in ascending order
+                }
         }
-        for (int u = tid; u < total; u += kSpBlk) cv[cb + u] = acc[u];
+        for (int u = tid; u < total; u += BT) cv[cb + u] = acc[u];
+        }
         __syncthreads();
     }
     if (MODE == SP_COUNT) {
@@ -648,21 +658,63 @@ static int spgemm(amg_hierarchy* h, int nA, const int64_t* arp, const int32_t* a
         cudaStream_t s;
         ~FreeCnt() { cudaFreeAsync(p, s); }
     } free_cnt{rowcnt, s};
-    const bool blk = b_avg >= kSpLongRow;
+    // kernel by B's average row length: a warp per row (the tentative P), a
+    // block of 64 threads (P_bar of the finest level), or of 256
+    const int bt = b_avg >= kSpLongRow ? 256 : (b_avg >= kSpMidRow ? 64 : 0);
+    const bool blk = bt > 0;
     // shared memory of the block-per-row kernel beyond bits/pre/acc: staged
     // A entries (8 + 8 + 4 bytes each) and the reduction scratch
-    const size_t blk_tail = (size_t)20 * kSpBlk + 4 * (2 * (kSpBlk / 32) + 1) + 16;
+    const size_t blk_tail = (size_t)20 * bt + 4 * (2 * (bt / 32) + 1) + 16;
     auto cfg = [&](auto kern, size_t bytes) {
         return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     };
     auto blocks_blk = [&]() { return (int)std::max<int64_t>(1, std::min<int64_t>(nA, (int64_t)1 << 20)); };
+    // the counting pass's row bitmaps, kept for the later pass when they fit the budget
+    uint32_t* gbits = nullptr;
+    if (blk && (size_t)nA * (size_t)wmax * 4 <= kSpBitsBudget &&
+        dev_alloc((void**)&gbits, (size_t)nA * (size_t)wmax * 4 + 16, s) != cudaSuccess) {
+        gbits = nullptr;  // no room: the later pass marks the rows again
+        (void)cudaGetLastError();
+    }
+    struct FreeBits {
+        uint32_t* p;
+        cudaStream_t s;
+        ~FreeBits() {
+            if (p) cudaFreeAsync(p, s);
+        }
+    } free_bits{gbits, s};
+    // launch of a block-per-row pass with BT threads
+    auto run_blk = [&](auto mode_tag, auto bt_tag, size_t sm, int gb, int cm, int64_t* rc, int* mc) -> cudaError_t {
+        constexpr int MODE = decltype(mode_tag)::value, BT = decltype(bt_tag)::value;
+        cudaError_t e = cfg(k_sp_row_blk<MODE, BT>, sm);
+        if (e != cudaSuccess) return e;
+        k_sp_row_blk<MODE, BT><<<AMG_GRID(gb), BT, sm, s>>>(nA, arp, aci, av, brp, bci, bv, wmax, cm, rc, mc, C.rowptr,
+                                                            C.col, C.val, gbits, dflag + 2);
+        return cudaGetLastError();
+    };
+    auto blk_pass = [&](int m, size_t sm, int gb, int cm, int64_t* rc, int* mc) -> cudaError_t {
+        using I64 = std::integral_constant<int, 64>;
+        using I256 = std::integral_constant<int, 256>;
+        switch (m) {
+            case SP_COUNT:
+                return bt == 64 ? run_blk(std::integral_constant<int, SP_COUNT>{}, I64{}, sm, gb, cm, rc, mc)
+                                : run_blk(std::integral_constant<int, SP_COUNT>{}, I256{}, sm, gb, cm, rc, mc);
+            case SP_COLS:
+                return bt == 64 ? run_blk(std::integral_constant<int, SP_COLS>{}, I64{}, sm, gb, cm, rc, mc)
+                                : run_blk(std::integral_constant<int, SP_COLS>{}, I256{}, sm, gb, cm, rc, mc);
+            case SP_VALUES:
+                return bt == 64 ? run_blk(std::integral_constant<int, SP_VALUES>{}, I64{}, sm, gb, cm, rc, mc)
+                                : run_blk(std::integral_constant<int, SP_VALUES>{}, I256{}, sm, gb, cm, rc, mc);
+            default:
+                return bt == 64 ? run_blk(std::integral_constant<int, SP_UPPER>{}, I64{}, sm, gb, cm, rc, mc)
+                                : run_blk(std::integral_constant<int, SP_UPPER>{}, I256{}, sm, gb, cm, rc, mc);
+        }
+    };
     size_t per = (size_t)8 * wmax;
     int warps = 0;
     if (blk) {
         if (per + blk_tail > (size_t)smem_optin) return AMG_ERR_ROW_TOO_LONG;
-        SP_CK(cfg(k_sp_row_blk<SP_COUNT>, per + blk_tail));
-        k_sp_row_blk<SP_COUNT><<<AMG_GRID(blocks_blk()), kSpBlk, per + blk_tail, s>>>(
-            nA, arp, aci, av, brp, bci, bv, wmax, 0, rowcnt, dflag + 1, nullptr, nullptr, nullptr, dflag + 2);
+        SP_CK(blk_pass(SP_COUNT, per + blk_tail, blocks_blk(), 0, rowcnt, dflag + 1));
     } else {
         warps = (int)std::min<size_t>(kSpWarps, (size_t)smem_optin / per);
         if (warps < 1) return AMG_ERR_ROW_TOO_LONG;
@@ -683,24 +735,7 @@ static int spgemm(amg_hierarchy* h, int nA, const int64_t* arp, const int32_t* a
     per = (size_t)8 * wmax + (mode >= SP_VALUES ? (size_t)8 * cmax : 0);
     if (blk) {
         if (per + blk_tail > (size_t)smem_optin) return AMG_ERR_ROW_TOO_LONG;
-        const size_t sm = per + blk_tail;
-        const int gb = blocks_blk();
-        if (mode == SP_COLS) {
-            SP_CK(cfg(k_sp_row_blk<SP_COLS>, sm));
-            k_sp_row_blk<SP_COLS><<<AMG_GRID(gb), kSpBlk, sm, s>>>(nA, arp, aci, av, brp, bci, bv, wmax, cmax, nullptr,
-                                                                   nullptr, C.rowptr, C.col, nullptr, dflag + 2);
-        } else if (mode == SP_VALUES) {
-            SP_CK(cfg(k_sp_row_blk<SP_VALUES>, sm));
-            k_sp_row_blk<SP_VALUES><<<AMG_GRID(gb), kSpBlk, sm, s>>>(nA, arp, aci, av, brp, bci, bv, wmax, cmax,
-                                                                     nullptr, nullptr, C.rowptr, C.col, C.val,
-                                                                     dflag + 2);
-        } else {
-            SP_CK(cfg(k_sp_row_blk<SP_UPPER>, sm));
-            k_sp_row_blk<SP_UPPER><<<AMG_GRID(gb), kSpBlk, sm, s>>>(nA, arp, aci, av, brp, bci, bv, wmax, cmax,
-                                                                    nullptr, nullptr, C.rowptr, C.col, C.val,
-                                                                    dflag + 2);
-        }
-        SP_CK(cudaGetLastError());
+        SP_CK(blk_pass(mode, per + blk_tail, blocks_blk(), cmax, nullptr, nullptr));
         return AMG_OK;
     }
     warps = (int)std::min<size_t>(kSpWarps, (size_t)smem_optin / per);

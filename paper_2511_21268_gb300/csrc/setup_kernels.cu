@@ -64,32 +64,38 @@ __global__ void k_validate(int n, int64_t nnz, const int64_t* __restrict__ rp, c
 
 // ------------------------------------------------------------- ordered folds
 // Warp-cooperative left-to-right row folds.  The warp owns rows
-// row0 .. row0+31; in each 32-column chunk lane r stages entry (chunk + lane)
-// of row r into tile[r][lane] (coalesced), then every lane adds the 32 staged
+// row0 .. row0+31; in each chunk of kFoldCols columns, every load instruction
+// stages kFoldCols consecutive entries of 32 / kFoldCols rows into
+// tile[row][column] (coalesced per row), then every lane adds the staged
 // terms of its own row in order.  Padding terms are +0.0, which leaves a sum
-// that started at +0.0 unchanged.
+// that started at +0.0 unchanged.  The narrow chunk keeps the tile at 2.3 KB
+// per warp, so that many warps share an SM: the lanes' sums are dependent
+// chains, and the loads of other warps fill their gaps.
+constexpr int kFoldCols = 8;
+
 template <typename Term>
 __device__ __forceinline__ double fold_rows(int row0, int n, const int64_t* __restrict__ rp, Term term,
-                                            double (*tile)[33]) {
+                                            double (*tile)[kFoldCols + 1]) {
+    constexpr int kRowsPerLoad = 32 / kFoldCols;
     const int lane = threadIdx.x & 31;
+    const int sub = lane % kFoldCols, rsel = lane / kFoldCols;
     const int my = row0 + lane;
     const int64_t mb = my < n ? rp[my] : 0;
     const int mlen = my < n ? (int)(rp[my + 1] - mb) : 0;
     const int maxlen = __reduce_max_sync(FULL, mlen);
     double acc = 0.0;
-    for (int c = 0; c < maxlen; c += 32) {
-        // up to 16 rows' loads in flight per lane (three blocks per SM fit
-        // the tiles' shared memory)
-#pragma unroll 16
-        for (int r = 0; r < 32; r++) {
+    for (int c = 0; c < maxlen; c += kFoldCols) {
+#pragma unroll
+        for (int r0 = 0; r0 < 32; r0 += kRowsPerLoad) {
+            const int r = r0 + rsel;
             const int64_t rb = __shfl_sync(FULL, mb, r);
             const int rl = __shfl_sync(FULL, mlen, r);
-            const int t = c + lane;
-            tile[r][lane] = (t < rl) ? term(rb + t, row0 + r) : 0.0;
+            const int t = c + sub;
+            tile[r][sub] = (t < rl) ? term(rb + t, row0 + r) : 0.0;
         }
         __syncwarp();
-#pragma unroll 8
-        for (int s = 0; s < 32; s++) acc = __dadd_rn(acc, tile[lane][s]);
+#pragma unroll
+        for (int s = 0; s < kFoldCols; s++) acc = __dadd_rn(acc, tile[lane][s]);
         __syncwarp();
     }
     return acc;
@@ -99,9 +105,9 @@ __device__ __forceinline__ double fold_rows(int row0, int n, const int64_t* __re
 __global__ void __launch_bounds__(kBlock) k_l1diag(int n, const int64_t* __restrict__ rp,
                                                     const int32_t* __restrict__ ci, const double* __restrict__ v,
                                                     double* kii, double* dl1, double* invd, int* flag) {
-    __shared__ double tiles[kWarpsPerBlock][32][33];
+    __shared__ double tiles[kWarpsPerBlock][32][kFoldCols + 1];
     __shared__ double diags[kWarpsPerBlock][32];  // the rows' diagonal entries (0 when a row has none)
-    double(*tile)[33] = tiles[threadIdx.x >> 5];
+    double(*tile)[kFoldCols + 1] = tiles[threadIdx.x >> 5];
     double* dg = diags[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -153,8 +159,8 @@ __global__ void __launch_bounds__(kBlock) k_testvec_sweep(int n, const int64_t* 
                                                            const double* __restrict__ v,
                                                            const double* __restrict__ dl1,
                                                            const double* __restrict__ w, double* wout) {
-    __shared__ double tiles[kWarpsPerBlock][32][33];
-    double(*tile)[33] = tiles[threadIdx.x >> 5];
+    __shared__ double tiles[kWarpsPerBlock][32][kFoldCols + 1];
+    double(*tile)[kFoldCols + 1] = tiles[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int row0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; row0 < n; row0 += nwarps * 32) {

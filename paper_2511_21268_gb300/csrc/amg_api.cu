@@ -238,7 +238,7 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
     const int n = A.n;
     cudaStream_t s = h->s;
     const double* kii = kii_known;
-    Tmp tk(s), tkey(s), tstate(s), tcand(s), tlead(s), tcidx(s), tscan(s);
+    Tmp tk(s), tkey(s), tstate(s), tcand(s), tlead(s), tcidx(s), tscan(s), tlists(s);
     if (!kii) {
         double* kd = nullptr;
         RC(tk.get(&kd, n));
@@ -253,6 +253,8 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
     RC(tlead.get(&leader, n));
     RC(tcidx.get(&cidx, n));
     RC(tscan.get(&scr, scan_scratch_ints(n) + 1));
+    int32_t* lists;  // the rounds' active-vertex lists (two, alternating)
+    RC(tlists.get(&lists, 2 * (size_t)n));
     phase(h, 2);
     CK(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), s));
     CK(launch_edge_keys(A, kii, w, key, h->flag + 1, s));
@@ -267,7 +269,7 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
     while (!done) {
         if (rounds >= maxr) return AMG_ERR_TIMEOUT;
         const int cnt = std::min(kRoundBatch, maxr - rounds);
-        CK(launch_match_rounds(A, key, state, cand, h->round_active, rounds, cnt, s));
+        CK(launch_match_rounds(A, key, state, cand, h->round_active, lists, rounds, cnt, s));
         CK(cudaMemcpyAsync(h->flag_host, h->round_active + rounds, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
         // the edge-key kernel's unsymmetric-pattern flag rides on the same read
         CK(cudaMemcpyAsync(h->flag_host + 32, h->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -439,7 +441,6 @@ int autotune(amg_hierarchy* h) {
                 cudaEventDestroy(b);
             }
         } ev{e0, e1};
-        double* slots = h->partials;  // the pq / pr partial slots are rewritten by the first solve
         auto timed = [&](auto&& launch, float* ms) -> int {
             CK(launch());
             CK(cudaEventRecord(e0, s));
@@ -449,7 +450,6 @@ int autotune(amg_hierarchy* h) {
             CK(cudaEventElapsedTime(ms, e0, e1));
             return AMG_OK;
         };
-        (void)slots;
         const int save_sell64 = h->sell64, save_stream = h->stream, save_warps = h->sell64_warps;
         float best = 1e30f, ms = 0.f;
         if (save_sell64) {

@@ -252,12 +252,8 @@ cudaError_t launch_testvec_sweep(const DevCSR& A, const double* dl1, const doubl
 cudaError_t launch_edge_keys(const DevCSR& A, const double* kii, const double* w, uint64_t* key, int* flag,
                              cudaStream_t s);
 cudaError_t launch_match_init(int n, int32_t* state, cudaStream_t s);
-cudaError_t launch_match_propose(const DevCSR& A, const uint64_t* key, const int32_t* state, int32_t* cand,
-                                 const int* prev_active, cudaStream_t s);
-cudaError_t launch_match_commit(int n, const int32_t* cand, int32_t* state, int* active, const int* prev_active,
-                                cudaStream_t s);
 cudaError_t launch_match_rounds(const DevCSR& A, const uint64_t* key, int32_t* state, int32_t* cand, int* active,
-                                int first_round, int count, cudaStream_t s);
+                                int32_t* lists, int first_round, int count, cudaStream_t s);
 cudaError_t launch_match_finish(int n, const int32_t* state, int32_t* mate, int32_t* leader, cudaStream_t s);
 cudaError_t launch_aggregate(int n, const int32_t* mate, const int32_t* cidx, const double* w, int32_t* agg,
                              double* pval, int32_t* mem0, int32_t* mem1, double* wc, cudaStream_t s);

@@ -400,9 +400,9 @@ __global__ void __launch_bounds__(32 * kCtWarps) k_iga_outer(int64_t IN, int Q, 
 // K(I, J) = sum_g sum_k W_g[r1][k] X_g[o][s[r1] + k] goes to the position of
 // J in row I (columns in (delta3, delta2, delta1) order).  A block stages
 // `rows` consecutive rows of every group in shared memory (row stride Q + 1);
-// thread t takes row t % rows and the pairs r1 = t / rows + k (256 / rows), so
-// the lanes that share r1 read the same weights (a broadcast) and rows a
-// padded stride apart.
+// thread t takes row t % rows and every (256 / rows)-th pair from t / rows on,
+// so the lanes that share a pair read the same weights (a broadcast) and rows
+// a padded stride apart.
 struct InnerGroups {
     const double* X[4];
     const double* W[4];
@@ -442,7 +442,10 @@ __global__ void __launch_bounds__(kInThreads) k_iga_inner_csr(IgaDims d, InnerGr
     band_range(i3, d.m, d.p, lo3, nv3);
     band_range(i2, d.m, d.p, lo2, nv2);
     const double* xr = xs + (int64_t)row * Qp;
-    for (int r1 = slot; r1 < d.R; r1 += nslot) {
+    // pairs in delta-major order: the pairs a warp shares have the same
+    // delta, hence the same number of common Gauss points (no divergence)
+    for (int u = slot; u < d.R; u += nslot) {
+        const int r1 = (u % d.m) * d.B + u / d.m;
         const int i1 = r1 / d.B, d1 = r1 % d.B - d.p, j1 = i1 + d1;
         if (j1 < 0 || j1 >= d.m) continue;
         const int st = s[r1], len = L[r1];

@@ -64,28 +64,28 @@ __global__ void k_validate(int n, int64_t nnz, const int64_t* __restrict__ rp, c
 
 // ------------------------------------------------------------- ordered folds
 // Warp-cooperative left-to-right row folds.  The warp owns rows
-// row0 .. row0+31; in each chunk of kFoldCols columns, every load instruction
-// stages kFoldCols consecutive entries of 32 / kFoldCols rows into
-// tile[row][column] (coalesced per row), then every lane adds the staged
-// terms of its own row in order.  Padding terms are +0.0, which leaves a sum
-// that started at +0.0 unchanged.  The narrow chunk keeps the tile at 2.3 KB
-// per warp, so that many warps share an SM: the lanes' sums are dependent
-// chains, and the loads of other warps fill their gaps.
-constexpr int kFoldCols = 8;
-
-template <typename Term>
+// row0 .. row0+31; in each chunk of CW columns, every load instruction stages
+// CW consecutive entries of 32 / CW rows into tile[row][column] (coalesced
+// per row), then every lane adds the staged terms of its own row in order.
+// Padding terms are +0.0, which leaves a sum that started at +0.0 unchanged.
+// The chunk width does not change the sums.  A narrow chunk (8) keeps the
+// tile at 2.3 KB per warp, so that many warps share an SM when the matrix has
+// the rows to fill them (the lanes' sums are dependent chains, and the loads
+// of other warps fill their gaps); with few rows a wide chunk (32) does the
+// same work in fewer synchronised steps.
+template <int CW, typename Term>
 __device__ __forceinline__ double fold_rows(int row0, int n, const int64_t* __restrict__ rp, Term term,
-                                            double (*tile)[kFoldCols + 1]) {
-    constexpr int kRowsPerLoad = 32 / kFoldCols;
+                                            double (*tile)[CW + 1]) {
+    constexpr int kRowsPerLoad = 32 / CW;
     const int lane = threadIdx.x & 31;
-    const int sub = lane % kFoldCols, rsel = lane / kFoldCols;
+    const int sub = lane % CW, rsel = lane / CW;
     const int my = row0 + lane;
     const int64_t mb = my < n ? rp[my] : 0;
     const int mlen = my < n ? (int)(rp[my + 1] - mb) : 0;
     const int maxlen = __reduce_max_sync(FULL, mlen);
     double acc = 0.0;
-    for (int c = 0; c < maxlen; c += kFoldCols) {
-#pragma unroll
+    for (int c = 0; c < maxlen; c += CW) {
+#pragma unroll(CW == 32 ? 16 : 8)
         for (int r0 = 0; r0 < 32; r0 += kRowsPerLoad) {
             const int r = r0 + rsel;
             const int64_t rb = __shfl_sync(FULL, mb, r);
@@ -94,20 +94,25 @@ __device__ __forceinline__ double fold_rows(int row0, int n, const int64_t* __re
             tile[r][sub] = (t < rl) ? term(rb + t, row0 + r) : 0.0;
         }
         __syncwarp();
-#pragma unroll
-        for (int s = 0; s < kFoldCols; s++) acc = __dadd_rn(acc, tile[lane][s]);
+#pragma unroll 8
+        for (int s = 0; s < CW; s++) acc = __dadd_rn(acc, tile[lane][s]);
         __syncwarp();
     }
     return acc;
 }
 
+// Chunk width of the folds: narrow when the rows give every SM at least 32
+// warps.
+inline bool fold_narrow(int n, int num_sms) { return (int64_t)(n + 31) / 32 >= 32LL * num_sms; }
+
 // l1 diagonal (Sec. 3.2): d_i = k_ii + sum_{j != i} |k_ij|.
+template <int CW>
 __global__ void __launch_bounds__(kBlock) k_l1diag(int n, const int64_t* __restrict__ rp,
                                                     const int32_t* __restrict__ ci, const double* __restrict__ v,
                                                     double* kii, double* dl1, double* invd, int* flag) {
-    __shared__ double tiles[kWarpsPerBlock][32][kFoldCols + 1];
+    __shared__ double tiles[kWarpsPerBlock][32][CW + 1];
     __shared__ double diags[kWarpsPerBlock][32];  // the rows' diagonal entries (0 when a row has none)
-    double(*tile)[kFoldCols + 1] = tiles[threadIdx.x >> 5];
+    double(*tile)[CW + 1] = tiles[threadIdx.x >> 5];
     double* dg = diags[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -123,7 +128,7 @@ __global__ void __launch_bounds__(kBlock) k_l1diag(int n, const int64_t* __restr
             }
             return fabs(x);
         };
-        const double s = fold_rows(row0, n, rp, term, tile);
+        const double s = fold_rows<CW>(row0, n, rp, term, tile);
         __syncwarp();
         const int i = row0 + lane;
         if (i < n) {
@@ -154,18 +159,19 @@ __global__ void k_testvec_init(int n, int kind, uint64_t seed, double* w) {
 }
 
 // One relaxation sweep on K w = 0 (Sec. 3.1): w_i <- w_i - (K w)_i / d_i.
+template <int CW>
 __global__ void __launch_bounds__(kBlock) k_testvec_sweep(int n, const int64_t* __restrict__ rp,
                                                            const int32_t* __restrict__ ci,
                                                            const double* __restrict__ v,
                                                            const double* __restrict__ dl1,
                                                            const double* __restrict__ w, double* wout) {
-    __shared__ double tiles[kWarpsPerBlock][32][kFoldCols + 1];
-    double(*tile)[kFoldCols + 1] = tiles[threadIdx.x >> 5];
+    __shared__ double tiles[kWarpsPerBlock][32][CW + 1];
+    double(*tile)[CW + 1] = tiles[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int row0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; row0 < n; row0 += nwarps * 32) {
         auto term = [&](int64_t k, int) -> double { return __dmul_rn(v[k], w[ci[k]]); };
-        const double s = fold_rows(row0, n, rp, term, tile);
+        const double s = fold_rows<CW>(row0, n, rp, term, tile);
         const int i = row0 + lane;
         if (i < n) wout[i] = __dsub_rn(w[i], __ddiv_rn(s, dl1[i]));
     }
@@ -236,16 +242,19 @@ __device__ __forceinline__ bool heavier(uint64_t ka, int loa, int hia, uint64_t 
 // Every active vertex proposes to its heaviest eligible active neighbour.
 __global__ void k_match_propose(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                 const uint64_t* __restrict__ key, const int32_t* __restrict__ state,
-                                int32_t* cand, const int* prev_active) {
-    if (prev_active && *prev_active == 0) return;  // the matching already ended: a no-op round
+                                int32_t* cand, const int32_t* __restrict__ list, const int* __restrict__ count) {
+    // round 0: every vertex (list NULL); later rounds: the vertices the
+    // previous round left active
+    const int m = list ? *count : n;
+    if (m == 0) return;  // the matching already ended: a no-op round
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int i = warp; i < n; i += nw) {
-        if (state[i] != -1) continue;
+    for (int idx = warp; idx < m; idx += nw) {
+        const int i = list ? list[idx] : idx;
         // Active neighbours only leave between rounds, so the heaviest one of
         // the previous round is still the heaviest while it stays active.
-        if (prev_active) {
+        if (list) {
             const int c = cand[i];
             if (c >= 0 && state[c] == -1) continue;
         }
@@ -281,20 +290,33 @@ __global__ void k_match_propose(int n, const int64_t* __restrict__ rp, const int
     }
 }
 
-// Mutual proposals become pairs; vertices without a candidate die.
-__global__ void k_match_commit(int n, const int32_t* __restrict__ cand, int32_t* state, int* active,
-                               const int* prev_active) {
-    if (prev_active && *prev_active == 0) return;
-    int left = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        if (state[i] != -1) continue;
-        const int c = cand[i];
-        if (c < 0) state[i] = -2;
-        else if (cand[c] == i) state[i] = c;
-        else left++;
+// Commit of a round over its active vertices (list_in, *count_in; round 0:
+// all): mutual proposals pair, vertices without a candidate become
+// singletons, the others stay active and are appended to list_out, whose
+// length *count_out (zero on entry) is the round's active count.  The list's
+// order depends on the atomics; nothing computed from it does.
+__global__ void k_match_commit(int n, const int32_t* __restrict__ cand, int32_t* state,
+                               const int32_t* __restrict__ list_in, const int* __restrict__ count_in,
+                               int32_t* list_out, int* count_out) {
+    const int m = list_in ? *count_in : n;
+    const int lane = threadIdx.x & 31;
+    for (int base = blockIdx.x * blockDim.x; base < m; base += gridDim.x * blockDim.x) {  // warp-uniform
+        const int idx = base + threadIdx.x;
+        int i = -1;
+        bool keep = false;
+        if (idx < m) {
+            i = list_in ? list_in[idx] : idx;
+            const int c = cand[i];
+            if (c < 0) state[i] = -2;
+            else if (cand[c] == i) state[i] = c;
+            else keep = true;
+        }
+        const unsigned b = __ballot_sync(FULL, keep);
+        int off = 0;
+        if (lane == 0 && b) off = atomicAdd(count_out, __popc(b));
+        off = __shfl_sync(FULL, off, 0);
+        if (keep) list_out[off + __popc(b & ((1u << lane) - 1u))] = i;
     }
-    left = __reduce_add_sync(FULL, left);
-    if ((threadIdx.x & 31) == 0 && left) atomicAdd(active, left);
 }
 
 __global__ void k_match_finish(int n, const int32_t* __restrict__ state, int32_t* mate, int32_t* leader) {
@@ -1044,7 +1066,15 @@ cudaError_t launch_validate_csr(const DevCSR& A, int* flag, cudaStream_t s) {
 cudaError_t launch_l1diag(const DevCSR& A, double* kii, double* dl1, double* invd, int* flag, cudaStream_t s) {
     if (A.n == 0) return cudaSuccess;
     AMG_TRY(cudaMemsetAsync(kii, 0, sizeof(double) * A.n, s));
-    k_l1diag<<<AMG_GRID(blocks_for(A.n, kBlock, 4096)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, kii, dl1, invd, flag);
+    int dev = 0, sms = 148;
+    AMG_TRY(cudaGetDevice(&dev));
+    AMG_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (fold_narrow(A.n, sms))
+        k_l1diag<8><<<AMG_GRID(blocks_for(A.n, kBlock, 4096)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, kii, dl1,
+                                                                              invd, flag);
+    else
+        k_l1diag<32><<<AMG_GRID(blocks_for(A.n, kBlock, 4096)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, kii, dl1,
+                                                                               invd, flag);
     return cudaGetLastError();
 }
 
@@ -1060,7 +1090,15 @@ cudaError_t launch_testvec_init(int n, int kind, uint64_t seed, double* w, cudaS
 }
 
 cudaError_t launch_testvec_sweep(const DevCSR& A, const double* dl1, const double* w, double* wout, cudaStream_t s) {
-    k_testvec_sweep<<<AMG_GRID(blocks_for(A.n, kBlock, 4096)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, dl1, w, wout);
+    int dev = 0, sms = 148;
+    AMG_TRY(cudaGetDevice(&dev));
+    AMG_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (fold_narrow(A.n, sms))
+        k_testvec_sweep<8><<<AMG_GRID(blocks_for(A.n, kBlock, 4096)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val,
+                                                                                     dl1, w, wout);
+    else
+        k_testvec_sweep<32><<<AMG_GRID(blocks_for(A.n, kBlock, 4096)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val,
+                                                                                      dl1, w, wout);
     return cudaGetLastError();
 }
 
@@ -1076,30 +1114,24 @@ cudaError_t launch_match_init(int n, int32_t* state, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_match_propose(const DevCSR& A, const uint64_t* key, const int32_t* state, int32_t* cand,
-                                 const int* prev_active, cudaStream_t s) {
-    k_match_propose<<<AMG_GRID(blocks_for(A.n, kWarpsPerBlock, 8192)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, key, state, cand,
-                                                                                        prev_active);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_match_commit(int n, const int32_t* cand, int32_t* state, int* active, const int* prev_active,
-                                cudaStream_t s) {
-    k_match_commit<<<AMG_GRID(blocks_for(n, kBlock, 4096)), kBlock, 0, s>>>(n, cand, state, active, prev_active);
-    return cudaGetLastError();
-}
-
-// `count` rounds back to back; active[r] receives the number of vertices
-// still active after round first_round + r (the caller zeroes active[]).
+// One batch of `count` rounds from round first_round: round r's active
+// vertices are listed in lists[(r - 1) & 1] (n entries each) with their
+// count in active[r - 1]; it writes the next list to lists[r & 1] and the
+// count to active[r] (zeroed by the caller).  Grids are sized for the first
+// round and loop over the (shrinking) lists.
 cudaError_t launch_match_rounds(const DevCSR& A, const uint64_t* key, int32_t* state, int32_t* cand, int* active,
-                                int first_round, int count, cudaStream_t s) {
+                                int32_t* lists, int first_round, int count, cudaStream_t s) {
+    const int n = A.n;
+    const int gp = blocks_for(n, kWarpsPerBlock, 2048), gc = blocks_for(n, kBlock, 1024);
     for (int r = 0; r < count; r++) {
         const int round = first_round + r;
-        const int* prev = round > 0 ? active + round - 1 : nullptr;
-        AMG_TRY(launch_match_propose(A, key, state, cand, prev, s));
-        AMG_TRY(launch_match_commit(A.n, cand, state, active + round, prev, s));
+        const int32_t* lin = round > 0 ? lists + (size_t)((round - 1) & 1) * n : nullptr;
+        const int* cin = round > 0 ? active + round - 1 : nullptr;
+        k_match_propose<<<AMG_GRID(gp), kBlock, 0, s>>>(n, A.rowptr, A.col, key, state, cand, lin, cin);
+        k_match_commit<<<AMG_GRID(gc), kBlock, 0, s>>>(n, cand, state, lin, cin, lists + (size_t)(round & 1) * n,
+                                                         active + round);
     }
-    return cudaSuccess;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_match_finish(int n, const int32_t* state, int32_t* mate, int32_t* leader, cudaStream_t s) {

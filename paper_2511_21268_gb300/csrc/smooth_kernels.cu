@@ -359,10 +359,13 @@ __global__ void __launch_bounds__(BT) k_sp_row_blk(int n, const int64_t* __restr
             for (int64_t t = a0 + wid; t < a1; t += NW) {
                 const int k = aci[t];
                 const int64_t b0 = brp[k], b1 = brp[k + 1];
-                for (int64_t q = b0 + lane; q < b1; q += 32 * kSpUnroll) {
+                for (int64_t qb = b0; qb < b1; qb += 32 * kSpUnroll) {  // warp-uniform trip count
                     int J[kSpUnroll];
 #pragma unroll
-                    for (int u = 0; u < kSpUnroll; u++) J[u] = q + 32 * u < b1 ? bci[q + 32 * u] - lo : -1;
+                    for (int u = 0; u < kSpUnroll; u++) {
+                        const int64_t q = qb + lane + 32 * u;
+                        J[u] = q < b1 ? bci[q] - lo : -1;
+                    }
 #pragma unroll
                     for (int u = 0; u < kSpUnroll; u++)
                         if (J[u] >= 0) atomicOr(&bits[J[u] >> 5], 1u << (J[u] & 31));

@@ -158,6 +158,7 @@ struct SellLevel {
     void* wint = nullptr;          // int4 per window interval (kMaxWinIntervals per block)
     int* wcnt = nullptr;           // window intervals of each block
     int* wbytes = nullptr;         // compacted window bytes of each block
+    int G = 0;                     // blocks of the launch (1, 2, 4 or 8 per SM: the windows must fit)
 };
 
 }  // namespace amg
@@ -322,6 +323,14 @@ cudaError_t sell64_spmv_pq(amg_hierarchy* h, const double* p, const double* r, d
 cudaError_t sell64_resid(amg_hierarchy* h, const double* f, const double* x, double* rbuf, cudaStream_t s);
 cudaError_t sell64_up0(amg_hierarchy* h, const double* r, const double* x, const double* invd, double* z,
                        const double* q, double* part_rz, double* part_zq, int flexible, cudaStream_t s);
+// Chebyshev steps of the finest level on the sliced FP64 copy (see
+// vcycle_cheb in solve_kernels.cu).
+cudaError_t sell64_cheb_step(amg_hierarchy* h, const double* dprev, const double* rprev, double* r,
+                             const double* invd, double a, double b, double* dnew, double* x, cudaStream_t s);
+cudaError_t sell64_cheb_resid(amg_hierarchy* h, const double* dprev, const double* rprev, double* r, double* x,
+                              cudaStream_t s);
+cudaError_t sell64_cheb_post0(amg_hierarchy* h, const double* x, const double* f, const double* invd, double c0,
+                              double* r, double* d, cudaStream_t s);
 cudaError_t sell_resid(amg_hierarchy* h, const double* f, const float* x, float* rbuf, cudaStream_t s);
 cudaError_t sell_up0(amg_hierarchy* h, const double* r, const float* x, const float* invd, double* z,
                      const double* q, double* part_rz, double* part_zq, int flexible, cudaStream_t s);

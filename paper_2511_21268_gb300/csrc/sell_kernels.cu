@@ -433,6 +433,49 @@ struct Epi64Up0 {  // z = x + (r - K x) / d, r.z and (flexible) z.q
     }
 };
 
+// Chebyshev steps of the finest level (the paper's smoother, see
+// vcycle_cheb): the matrix pass reads d (or x), the rest is row-local.
+struct Epi64ChebStep {  // r = rprev - K dprev; dnew = a dprev + b D^-1 r; x += dprev (r may be rprev)
+    const double* dprev;
+    const double* rprev;
+    double* r;
+    const double* invd;
+    double a, b;
+    double* dnew;
+    double* x;
+    __device__ __forceinline__ void operator()(int i, double s, double&, double&) const {
+        const double ri = rprev[i] - s;
+        const double dp = dprev[i];
+        r[i] = ri;
+        dnew[i] = fma(b, invd[i] * ri, a * dp);
+        x[i] += dp;
+    }
+};
+
+struct Epi64ChebResid {  // r = rprev - K dprev; x += dprev (end of pre-smoothing)
+    const double* dprev;
+    const double* rprev;
+    double* r;
+    double* x;
+    __device__ __forceinline__ void operator()(int i, double s, double&, double&) const {
+        r[i] = rprev[i] - s;
+        x[i] += dprev[i];
+    }
+};
+
+struct Epi64ChebPost0 {  // r = f - K x; d = c0 D^-1 r (start of post-smoothing)
+    const double* f;
+    const double* invd;
+    double c0;
+    double* r;
+    double* d;
+    __device__ __forceinline__ void operator()(int i, double s, double&, double&) const {
+        const double ri = f[i] - s;
+        r[i] = ri;
+        d[i] = c0 * invd[i] * ri;
+    }
+};
+
 template <int LM, typename Epi>
 __global__ void __launch_bounds__(kS64MaxWarps * 32, 1)
     k_sell64(int n, int nsl, const int32_t* __restrict__ soff, const double* __restrict__ val,
@@ -671,7 +714,7 @@ __global__ void k_sell_intervals(int G, const int2* __restrict__ win, const int*
     constexpr int kBounds = 4096;  // run boundaries (2 per run)
     __shared__ int bpos[kBounds];
     __shared__ int ia[kMaxWinIntervals], ie[kMaxWinIntervals], id[kMaxWinIntervals];
-    __shared__ int nint_s, d_s;
+    __shared__ int nint_s;
     const int b = blockIdx.x, lane = threadIdx.x;
     if (b >= G) return;
     const int lo4 = win[b].x & ~3;
@@ -729,7 +772,6 @@ __global__ void k_sell_intervals(int G, const int2* __restrict__ win, const int*
             m++;
         }
         nint_s = m;
-        d_s = d;
         wcnt[b] = m;
         wbytes[b] = 16 * d;
     }
@@ -900,7 +942,7 @@ template <int LM, typename V, typename Epi>
 cudaError_t sell_launch_lm(amg_hierarchy* h, const SellLevel& S, int n, int q, const V* val, const float* x,
                            const Epi& epi, double* p1, double* p2, cudaStream_t s) {
     const SellShape sh = sell_shape(S, q);
-    launch_pdl(k_sell<LM, V, Epi>, h->num_sms, kSellThreads, sell_smem_bytes(sh), s, n, S.nsl, S.soff, val, S.rs, x,
+    launch_pdl(k_sell<LM, V, Epi>, S.G, kSellThreads, sell_smem_bytes(sh), s, n, S.nsl, S.soff, val, S.rs, x,
                static_cast<const int4*>(S.wint), S.wcnt, S.wbytes, sh, epi, p1, p2, h->st);
     return cudaGetLastError();
 }
@@ -929,7 +971,6 @@ int prepare_level(amg_hierarchy* h, SellLevel& S, int n, const int64_t* rp, cons
                   const double* v64 = nullptr) {
     const bool fp64 = v64 != nullptr;  // FP64 copy for k_sell64 (no copy ring), else FP32 (+ BF16) for k_sell
     constexpr int kMinSlots = 16;
-    const int G = h->num_sms;
     if (n < 16) return AMG_OK;
     const int nsl = (n + kSlab - 1) / kSlab;
     int32_t* slots = nullptr;
@@ -990,70 +1031,88 @@ int prepare_level(amg_hierarchy* h, SellLevel& S, int n, const int64_t* rp, cons
     h->allocs.push_back(ors);
     if (dev_alloc(reinterpret_cast<void**>(&swin), sizeof(int2) * nsl, h->s) != cudaSuccess) return AMG_ERR_NOMEM;
     h->allocs.push_back(swin);
-    if (dev_alloc(reinterpret_cast<void**>(&win), sizeof(int2) * G, h->s) != cudaSuccess) return AMG_ERR_NOMEM;
+    // blocks of the launch: one per SM unless a block's vector window
+    // outgrows the 16-bit offsets or the shared memory; then 2, 4 or 8 per SM
+    // (smaller blocks, smaller windows)
+    const int Gmax = 8 * h->num_sms;
+    if (dev_alloc(reinterpret_cast<void**>(&win), sizeof(int2) * Gmax, h->s) != cudaSuccess) return AMG_ERR_NOMEM;
     h->allocs.push_back(win);
     const void* arrays[] = {o32, o64, o16, ors};
     for (const void* a : arrays)
         if (a && (reinterpret_cast<uintptr_t>(a) & 15)) return AMG_OK;
     launch_pdl(k_sell_span, gw, 256, 0, h->s, n, nsl, LM, rptr, rst, slots, swin);
-    launch_pdl(k_sell_window, G, 256, 0, h->s, nsl, G, swin, win);
-    std::vector<int2> hw(G);
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(hw.data(), win, sizeof(int2) * G, cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
-        cudaStreamSynchronize(h->s) != cudaSuccess)
-        return AMG_ERR_CUDA;
-    // compacted windows: group bitmaps, intervals and group ranks
-    std::vector<int> hword(G + 1, 0), hgoff(G + 1, 0);
-    for (int b = 0; b < G; b++) {
-        const int lo4 = hw[b].x & ~3;
-        const int ng = hw[b].y >= lo4 ? ((hw[b].y - lo4) >> 2) + 1 : 0;
-        if ((int64_t)ng * 16 > 4 * 65536) return AMG_OK;  // offsets into the window are 16-bit
-        hgoff[b + 1] = hgoff[b] + ng;
-        hword[b + 1] = hword[b] + (ng + 31) / 32;
-    }
     int *wordoff = nullptr, *goff = nullptr, *wcnt = nullptr, *wbytes = nullptr;
-    uint32_t* bits = nullptr;
-    uint16_t* rank = nullptr;
     int4* wint = nullptr;
     auto alloc = [&](void** p, size_t bytes) {
         if (dev_alloc(p, bytes, h->s) != cudaSuccess) return false;
         h->allocs.push_back(*p);
         return true;
     };
-    if (!alloc(reinterpret_cast<void**>(&wordoff), sizeof(int) * (G + 1)) ||
-        !alloc(reinterpret_cast<void**>(&goff), sizeof(int) * (G + 1)) ||
-        !alloc(reinterpret_cast<void**>(&wcnt), sizeof(int) * G) ||
-        !alloc(reinterpret_cast<void**>(&wbytes), sizeof(int) * G) ||
-        !alloc(reinterpret_cast<void**>(&bits), sizeof(uint32_t) * std::max(hword[G], 1)) ||
-        !alloc(reinterpret_cast<void**>(&rank), sizeof(uint16_t) * std::max(hgoff[G], 1)) ||
-        !alloc(reinterpret_cast<void**>(&wint), sizeof(int4) * (size_t)G * kMaxWinIntervals))
+    if (!alloc(reinterpret_cast<void**>(&wordoff), sizeof(int) * (Gmax + 1)) ||
+        !alloc(reinterpret_cast<void**>(&goff), sizeof(int) * (Gmax + 1)) ||
+        !alloc(reinterpret_cast<void**>(&wcnt), sizeof(int) * Gmax) ||
+        !alloc(reinterpret_cast<void**>(&wbytes), sizeof(int) * Gmax) ||
+        !alloc(reinterpret_cast<void**>(&wint), sizeof(int4) * (size_t)Gmax * kMaxWinIntervals))
         return AMG_ERR_NOMEM;
-    std::vector<int> hwb(G);
-    if (cudaMemcpyAsync(wordoff, hword.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, h->s) != cudaSuccess ||
-        cudaMemcpyAsync(goff, hgoff.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, h->s) != cudaSuccess ||
-        cudaMemsetAsync(bits, 0, sizeof(uint32_t) * std::max(hword[G], 1), h->s) != cudaSuccess)
-        return AMG_ERR_CUDA;
-    launch_pdl(k_sell_mark, gw, 256, 0, h->s, n, nsl, G, LM, rptr, rst, slots, win, wordoff, bits);
-    launch_pdl(k_sell_intervals, G, 32, 0, h->s, G, win, wordoff, goff, bits, wint, wcnt, wbytes, rank);
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(hwb.data(), wbytes, sizeof(int) * G, cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
-        cudaStreamSynchronize(h->s) != cudaSuccess)
-        return AMG_ERR_CUDA;
+    int G = 0;
     int64_t xw = 16;
-    for (int b = 0; b < G; b++) xw = std::max<int64_t>(xw, hwb[b]);
     int nb[2] = {0, 0};
-    if (fp64) {  // the window in FP64 and the block's dot-product scratch
-        if (2 * xw + kS64Static > optin) return AMG_OK;
-    } else {
-        for (int q = 0; q < 2; q++) {
-            const uint32_t vb = (uint32_t)(q == 0 ? vb16 : vb32);
-            for (int k = kSellBuf; k >= 2 && !nb[q]; k--) {
-                const SellShape sh{(uint32_t)xw, vb, (uint32_t)rb, k};
-                if (sell_smem_bytes(sh) + 256u <= (uint32_t)optin) nb[q] = k;  // 256: static shared memory
-            }
+    uint16_t* rank_sel = nullptr;  // group ranks of the chosen block count
+    for (int g = h->num_sms; g <= Gmax && !G; g *= 2) {
+        if (g > h->num_sms && g > nsl) break;  // more blocks than slabs: nothing gained
+        launch_pdl(k_sell_window, g, 256, 0, h->s, nsl, g, swin, win);
+        std::vector<int2> hw(g);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(hw.data(), win, sizeof(int2) * g, cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
+            cudaStreamSynchronize(h->s) != cudaSuccess)
+            return AMG_ERR_CUDA;
+        // compacted windows: group bitmaps, intervals and group ranks
+        std::vector<int> hword(g + 1, 0), hgoff(g + 1, 0);
+        bool fits = true;
+        for (int b = 0; b < g && fits; b++) {
+            const int lo4 = hw[b].x & ~3;
+            const int ng = hw[b].y >= lo4 ? ((hw[b].y - lo4) >> 2) + 1 : 0;
+            if ((int64_t)ng * 16 > 4 * 65536) fits = false;  // offsets into the window are 16-bit
+            hgoff[b + 1] = hgoff[b] + ng;
+            hword[b + 1] = hword[b] + (ng + 31) / 32;
         }
-        if (!nb[1] || (with16 && !nb[0])) return AMG_OK;
+        if (!fits) continue;
+        uint32_t* bits = nullptr;
+        uint16_t* rank = nullptr;
+        if (!alloc(reinterpret_cast<void**>(&bits), sizeof(uint32_t) * std::max(hword[g], 1)) ||
+            !alloc(reinterpret_cast<void**>(&rank), sizeof(uint16_t) * std::max(hgoff[g], 1)))
+            return AMG_ERR_NOMEM;
+        std::vector<int> hwb(g);
+        if (cudaMemcpyAsync(wordoff, hword.data(), sizeof(int) * (g + 1), cudaMemcpyHostToDevice, h->s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(goff, hgoff.data(), sizeof(int) * (g + 1), cudaMemcpyHostToDevice, h->s) != cudaSuccess ||
+            cudaMemsetAsync(bits, 0, sizeof(uint32_t) * std::max(hword[g], 1), h->s) != cudaSuccess)
+            return AMG_ERR_CUDA;
+        launch_pdl(k_sell_mark, gw, 256, 0, h->s, n, nsl, g, LM, rptr, rst, slots, win, wordoff, bits);
+        launch_pdl(k_sell_intervals, g, 32, 0, h->s, g, win, wordoff, goff, bits, wint, wcnt, wbytes, rank);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(hwb.data(), wbytes, sizeof(int) * g, cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
+            cudaStreamSynchronize(h->s) != cudaSuccess)
+            return AMG_ERR_CUDA;
+        xw = 16;
+        for (int b = 0; b < g; b++) xw = std::max<int64_t>(xw, hwb[b]);
+        if (fp64) {  // the window in FP64 and the block's dot-product scratch
+            if (2 * xw + kS64Static > optin) continue;
+        } else {
+            nb[0] = nb[1] = 0;
+            for (int q = 0; q < 2; q++) {
+                const uint32_t vb = (uint32_t)(q == 0 ? vb16 : vb32);
+                for (int k = kSellBuf; k >= 2 && !nb[q]; k--) {
+                    const SellShape sh{(uint32_t)xw, vb, (uint32_t)rb, k};
+                    if (sell_smem_bytes(sh) + 256u <= (uint32_t)optin) nb[q] = k;  // 256: static shared memory
+                }
+            }
+            if (!nb[1] || (with16 && !nb[0])) continue;
+        }
+        G = g;
+        rank_sel = rank;
     }
+    if (!G) return AMG_OK;
     // stage: the largest slab's values and run starts (within the opt-in budget)
     const int64_t es = fp64 ? 8 : 4;
     const int capr = (int)std::min<int64_t>((int64_t)rmax * kSlab, (optin - 1024) / (4 + es));
@@ -1064,13 +1123,13 @@ int prepare_level(amg_hierarchy* h, SellLevel& S, int n, const int64_t* rp, cons
             cudaSuccess)
             return AMG_ERR_CUDA;
         launch_pdl(k_sell_fill<double>, std::min(nsl, 65535), 256, fsm, h->s, n, nsl, G, LM, cap, capr, rp, rptr,
-                   rlen, rst, slots, win, goff, rank, v64, o64, nullptr, ors);
+                   rlen, rst, slots, win, goff, rank_sel, v64, o64, nullptr, ors);
     } else {
         if (cudaFuncSetAttribute(k_sell_fill<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm) !=
             cudaSuccess)
             return AMG_ERR_CUDA;
         launch_pdl(k_sell_fill<float>, std::min(nsl, 65535), 256, fsm, h->s, n, nsl, G, LM, cap, capr, rp, rptr,
-                   rlen, rst, slots, win, goff, rank, v32, o32, o16, ors);
+                   rlen, rst, slots, win, goff, rank_sel, v32, o32, o16, ors);
     }
     if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
     S.lm = LM;
@@ -1090,6 +1149,7 @@ int prepare_level(amg_hierarchy* h, SellLevel& S, int n, const int64_t* rp, cons
     S.wint = wint;
     S.wcnt = wcnt;
     S.wbytes = wbytes;
+    S.G = G;
     S.on = 1;
     return AMG_OK;
 }
@@ -1115,7 +1175,8 @@ int sell_prepare(amg_hierarchy* h, int* scratch, int optin, int* used) {
         default: attrs = sell_attrs_lm<9>(m16 ? m16 : m32, m32); break;
     }
     if (!attrs) return AMG_ERR_CUDA;
-    h->stream_blocks = h->num_sms;
+    if ((size_t)S.G + 2 > (size_t)h->npart) return AMG_OK;  // one dot-product partial per block
+    h->stream_blocks = S.G;
     h->stream = 2;
     *used = 1;
     return AMG_OK;
@@ -1192,7 +1253,7 @@ template <int LM, typename Epi>
 cudaError_t sell64_launch_lm(amg_hierarchy* h, const double* x, const Epi& epi, double* p1, double* p2,
                              cudaStream_t s) {
     const SellLevel& S = h->sell[0];
-    launch_pdl(k_sell64<LM, Epi>, h->num_sms, h->sell64_warps * 32, 2 * (size_t)S.xbytes, s, h->lev[0].A.n, S.nsl,
+    launch_pdl(k_sell64<LM, Epi>, S.G, h->sell64_warps * 32, 2 * (size_t)S.xbytes, s, h->lev[0].A.n, S.nsl,
                S.soff, static_cast<const double*>(S.v64), S.rs, x, static_cast<const int4*>(S.wint), S.wcnt, epi,
                p1, p2, h->st);
     return cudaGetLastError();
@@ -1225,6 +1286,12 @@ bool sell64_attrs_lm(int smem) {
            cudaFuncSetAttribute(k_sell64<LM, Epi64Resid>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
                cudaSuccess &&
            cudaFuncSetAttribute(k_sell64<LM, Epi64Up0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(k_sell64<LM, Epi64ChebStep>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(k_sell64<LM, Epi64ChebResid>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(k_sell64<LM, Epi64ChebPost0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
                cudaSuccess;
 }
 
@@ -1256,8 +1323,9 @@ int sell64_prepare(amg_hierarchy* h, int* scratch) {
         default: attrs = sell64_attrs_lm<9>(smem); break;
     }
     if (!attrs) return AMG_ERR_CUDA;
-    h->sell64_warps = sell64_pick_warps(S, h->num_sms);
-    h->stream_blocks = h->num_sms;
+    if ((size_t)S.G + 2 > (size_t)h->npart) return AMG_OK;  // one dot-product partial per block
+    h->sell64_warps = sell64_pick_warps(S, S.G);
+    h->stream_blocks = S.G;
     h->sell64 = 1;
     return AMG_OK;
 }
@@ -1279,6 +1347,21 @@ cudaError_t sell64_resid(amg_hierarchy* h, const double* f, const double* x, dou
 cudaError_t sell64_up0(amg_hierarchy* h, const double* r, const double* x, const double* invd, double* z,
                        const double* q, double* part_rz, double* part_zq, int flexible, cudaStream_t s) {
     return sell64_launch(h, x, Epi64Up0{r, x, invd, z, q, flexible}, part_rz, flexible ? part_zq : nullptr, s);
+}
+
+cudaError_t sell64_cheb_step(amg_hierarchy* h, const double* dprev, const double* rprev, double* r,
+                             const double* invd, double a, double b, double* dnew, double* x, cudaStream_t s) {
+    return sell64_launch(h, dprev, Epi64ChebStep{dprev, rprev, r, invd, a, b, dnew, x}, nullptr, nullptr, s);
+}
+
+cudaError_t sell64_cheb_resid(amg_hierarchy* h, const double* dprev, const double* rprev, double* r, double* x,
+                              cudaStream_t s) {
+    return sell64_launch(h, dprev, Epi64ChebResid{dprev, rprev, r, x}, nullptr, nullptr, s);
+}
+
+cudaError_t sell64_cheb_post0(amg_hierarchy* h, const double* x, const double* f, const double* invd, double c0,
+                              double* r, double* d, cudaStream_t s) {
+    return sell64_launch(h, x, Epi64ChebPost0{f, invd, c0, r, d}, nullptr, nullptr, s);
 }
 
 }  // namespace amg

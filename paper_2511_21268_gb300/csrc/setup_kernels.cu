@@ -260,17 +260,32 @@ __global__ void k_match_propose(int n, const int64_t* __restrict__ rp, const int
         }
         uint64_t bk = 0;
         int blo = 0x7fffffff, bhi = 0x7fffffff, bj = -1;
-        for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
-            const uint64_t kk = key[k];
-            if (kk == 0) continue;
-            const int j = ci[k];
-            if (state[j] != -1) continue;
-            const int lo = min(i, j), hi = max(i, j);
-            if (bj < 0 || heavier(kk, lo, hi, bk, blo, bhi)) {
-                bk = kk;
-                blo = lo;
-                bhi = hi;
-                bj = j;
+        // four 32-entry chunks per step: their keys and columns, then the
+        // neighbours' states, are loaded together (the heaviest edge does not
+        // depend on the order the entries are seen in)
+        const int64_t b0 = rp[i], b1 = rp[i + 1];
+        for (int64_t kb = b0; kb < b1; kb += 128) {
+            uint64_t kk[4];
+            int jj[4], sj[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int64_t k = kb + lane + 32 * u;
+                kk[u] = k < b1 ? key[k] : 0;
+                jj[u] = k < b1 ? ci[k] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) sj[u] = kk[u] != 0 ? state[jj[u]] : 0;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (kk[u] == 0 || sj[u] != -1) continue;
+                const int j = jj[u];
+                const int lo = min(i, j), hi = max(i, j);
+                if (bj < 0 || heavier(kk[u], lo, hi, bk, blo, bhi)) {
+                    bk = kk[u];
+                    blo = lo;
+                    bhi = hi;
+                    bj = j;
+                }
             }
         }
 #pragma unroll

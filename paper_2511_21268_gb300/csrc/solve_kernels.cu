@@ -845,8 +845,25 @@ static cudaError_t vcycle_cheb(amg_hierarchy* h, cudaStream_t s) {
                 });
             });
         };
-        if (l == 0) run(static_cast<const double*>(h->r));
-        else run(static_cast<const A*>(Vw::f(F)));
+        bool sliced = false;
+        if constexpr (std::is_same_v<A, double>) {
+            if (l == 0 && h->sell64) {  // the finest level's matrix passes on its sliced FP64 copy
+                const double* f0 = h->r;
+                launch_pdl(k_cheb_start<double, double>, nv, kBlock, 0, s, n, f0, Vw::invd(F), c0, x, d0, st);
+                A* dp = d0;
+                A* dn = d1;
+                for (int i = 1; i < k; i++) {
+                    sell64_cheb_step(h, dp, i == 1 ? f0 : r, r, Vw::invd(F), coef_a(i), coef_b(i), dn, x, s);
+                    std::swap(dp, dn);
+                }
+                sell64_cheb_resid(h, dp, k == 1 ? f0 : r, r, x, s);
+                sliced = true;
+            }
+        }
+        if (!sliced) {
+            if (l == 0) run(static_cast<const double*>(h->r));
+            else run(static_cast<const A*>(Vw::f(F)));
+        }
         if (F.smoothed)
             sp_restrict<A>(F, C, r, Vw::f(C), static_cast<A*>(nullptr), Vw::invd(C), st, s);
         else
@@ -886,8 +903,24 @@ static cudaError_t vcycle_cheb(amg_hierarchy* h, cudaStream_t s) {
                 dlast = dp;
             });
         };
-        if (l == 0) run(static_cast<const double*>(h->r));
-        else run(static_cast<const A*>(Vw::f(F)));
+        bool sliced = false;
+        if constexpr (std::is_same_v<A, double>) {
+            if (l == 0 && h->sell64) {  // the finest level's matrix passes on its sliced FP64 copy
+                sell64_cheb_post0(h, x, h->r, Vw::invd(F), c0, r, d0, s);
+                A* dp = d0;
+                A* dn = d1;
+                for (int i = 1; i < k; i++) {
+                    sell64_cheb_step(h, dp, r, r, Vw::invd(F), coef_a(i), coef_b(i), dn, x, s);
+                    std::swap(dp, dn);
+                }
+                dlast = dp;
+                sliced = true;
+            }
+        }
+        if (!sliced) {
+            if (l == 0) run(static_cast<const double*>(h->r));
+            else run(static_cast<const A*>(Vw::f(F)));
+        }
         if (l == 0) {
             const int nbz0 = (h->stream || h->sell64) ? h->stream_blocks : row_blocks(n, rows_per_warp(n, sms));
             launch_pdl(k_cheb_z<A>, nbz0, kBlock, 0, s, n, static_cast<const A*>(x), static_cast<const A*>(dlast),

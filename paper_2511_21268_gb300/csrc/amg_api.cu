@@ -38,6 +38,7 @@ namespace {
 constexpr int kGraphIters = 8;
 constexpr int kMaxGalerkinCap = 16384;  // candidate entries per Galerkin row (shared memory)
 constexpr double kBitmapSmem = 200.0 * 1024;  // shared memory budget of the bitmap Galerkin kernels
+constexpr double kWarpGalerkinSmem = 160.0 * 1024;  // and of the warp-per-row values kernel (per block)
 constexpr int kHistCap = 1 << 16;
 // Matrix column/value arrays get kPad trailing entries: the FP32/BF16 matrix
 // passes load groups of four entries from 4-aligned positions.
@@ -230,6 +231,48 @@ int pow2ceil(int x) {
     return p;
 }
 
+// Galerkin product of one matching pass with the warp-per-row kernels: the
+// counting kernel gives the row lengths and the widest span and row, which
+// size the values kernel (the block kernels take rows too wide for it).
+int galerkin_warp(amg_hierarchy* h, const DevCSR& A, const Pass& P, const int32_t* mem0, const int32_t* mem1, int nc,
+                  int maxcand, int bit_symmetric, DevCSR& C) {
+    cudaStream_t s = h->s;
+    C.n = nc;
+    RC(dalloc(h, &C.rowptr, (size_t)nc + 1));
+    int64_t *rowcnt, *scr64;
+    Tmp trc(s), ts64(s);
+    RC(trc.get(&rowcnt, nc));
+    RC(ts64.get(&scr64, scan64_scratch(nc) + 1));
+    // Galerkin errors accumulate in flag[3], read once after the last level;
+    // flag[1], flag[2]: widest span, longest coarse row (zeroed by the caller)
+    CK(launch_galerkin_warp_count(A, P.agg, mem0, mem1, nc, maxcand, rowcnt, h->flag + 1, h->flag + 3, s));
+    CK(launch_scan64(rowcnt, C.rowptr, nc, scr64, s));
+    CK(cudaMemcpyAsync(h->flag_host, C.rowptr + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->flag_host + 2, h->flag + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int64_t nnzc = 0;
+    memcpy(&nnzc, h->flag_host, sizeof(int64_t));
+    const int maxspan = h->flag_host[2], maxu = h->flag_host[3];
+    C.nnz = nnzc;
+    RC(dalloc(h, &C.col, (size_t)nnzc + kPad));
+    RC(dalloc(h, &C.val, (size_t)nnzc + kPad));
+    const int words = (maxspan + 31) / 32 + 1;
+    const bool mirror = !bit_symmetric;
+    if ((double)galerkin_warp_fill_smem(maxcand, words, maxu) <= kWarpGalerkinSmem) {
+        CK(launch_galerkin_warp_fill(A, P.agg, P.pval, P.mate, mem0, mem1, maxcand, words, maxu, bit_symmetric, C,
+                                     h->flag + 3, s));
+        if (mirror) CK(launch_galerkin_mirror(C, h->flag + 3, s));
+    } else if (8.0 * words + 16.0 * maxcand <= kBitmapSmem) {
+        CK(launch_galerkin_fill_bitmap(A, P.agg, P.pval, mem0, mem1, maxcand, words, C, h->flag + 3, s));
+        CK(launch_galerkin_mirror(C, h->flag + 3, s));
+    } else {
+        const int cap = pow2ceil(std::max(maxcand, 1));  // <= kGalWarpCand < kMaxGalerkinCap
+        CK(launch_galerkin_fill(A, P.agg, P.pval, mem0, mem1, cap, C, s));
+        CK(launch_galerkin_mirror(C, h->flag + 3, s));
+    }
+    return AMG_OK;
+}
+
 // One matching pass on A with test vector w: fills P and the coarse matrix C
 // (allocated in the hierarchy) and the coarse test vector *wc.  kii_known:
 // A's diagonal when the caller has it (a level's first pass), else NULL.
@@ -284,7 +327,10 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
         if (!done) rounds += cnt;
     }
     P.rounds = rounds;
-    if (h->flag_host[32]) return AMG_ERR_ARG;  // structurally unsymmetric matrix
+    if (h->flag_host[32] & 64) return AMG_ERR_ARG;  // structurally unsymmetric matrix
+    // values symmetric in every bit: the Galerkin kernels may compute the
+    // lower triangle in place
+    const int bit_symmetric = (h->flag_host[32] & 128) ? 0 : 1;
     phase(h, 4);
     P.n = n;
     RC(dalloc(h, &P.mate, n));
@@ -304,9 +350,19 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
     CK(launch_aggregate(n, P.mate, cidx, w, P.agg, P.pval, mem0, mem1, *wc, s));
     // Galerkin product of this pass
     phase(h, 5);
-    // widest candidate list and coarse-column span of the coarse rows (one read)
+    // widest candidate list of the coarse rows
     CK(cudaMemsetAsync(h->flag, 0, 3 * sizeof(int), s));
     CK(launch_row_stats(A, mem0, mem1, nc, h->flag, s));
+    if (nc < (1 << 30)) {
+        CK(cudaMemcpyAsync(h->flag_host, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (h->flag_host[0] <= kGalWarpCand) {
+            RC(galerkin_warp(h, A, P, mem0, mem1, nc, h->flag_host[0], bit_symmetric, C));
+            phase(h, 1);
+            return AMG_OK;
+        }
+    }
+    // widest coarse-column span as well (one read)
     CK(launch_row_span(A, P.agg, mem0, mem1, nc, h->flag + 2, s));
     CK(cudaMemcpyAsync(h->flag_host, h->flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

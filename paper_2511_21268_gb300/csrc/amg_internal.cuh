@@ -270,6 +270,17 @@ cudaError_t launch_galerkin_count_bitmap(const DevCSR& A, const int32_t* agg, co
                                          int nc, int cap, int words, int64_t* rowcnt, int* flag, cudaStream_t s);
 cudaError_t launch_galerkin_fill_bitmap(const DevCSR& A, const int32_t* agg, const double* pval, const int32_t* mem0,
                                         const int32_t* mem1, int cap, int words, DevCSR& C, int* flag, cudaStream_t s);
+// Warp-per-row Galerkin kernels (candidate counts up to kGalWarpCand):
+// counting (row lengths, and stats[0] = widest coarse-column span, stats[1] =
+// longest coarse row) and values (sym: the level matrix is symmetric in every
+// bit, so the lower triangle is computed in place; else the mirror fills it).
+constexpr int kGalWarpCand = 4096;
+size_t galerkin_warp_fill_smem(int cmax, int words, int umax);  // bytes per block
+cudaError_t launch_galerkin_warp_count(const DevCSR& A, const int32_t* agg, const int32_t* mem0, const int32_t* mem1,
+                                       int nc, int cmax, int64_t* rowcnt, int* stats, int* flag, cudaStream_t s);
+cudaError_t launch_galerkin_warp_fill(const DevCSR& A, const int32_t* agg, const double* pval, const int32_t* mate,
+                                      const int32_t* mem0, const int32_t* mem1, int cmax, int words, int umax, int sym,
+                                      DevCSR& C, int* flag, cudaStream_t s);
 cudaError_t launch_row_span(const DevCSR& A, const int32_t* agg, const int32_t* mem0, const int32_t* mem1, int nc,
                             int* maxspan, cudaStream_t s);
 cudaError_t launch_scan64(const int64_t* in, int64_t* out, int n, int64_t* scratch, cudaStream_t s);

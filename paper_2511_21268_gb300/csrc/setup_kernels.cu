@@ -183,13 +183,16 @@ __global__ void __launch_bounds__(kBlock) k_testvec_sweep(int n, const int64_t* 
 // w_lo^2 + w_hi^2 > 0.  Each edge is evaluated once, from its upper entry
 // (row i, column j > i), and the key is written to that entry and to its
 // mirror (row j, column i; found by binary search).  flag bit 64: a mirror
-// entry is missing (structurally unsymmetric matrix).
+// entry is missing (structurally unsymmetric matrix); flag bit 128: a mirror
+// entry's value differs from the upper entry's in its bits (symmetric only up
+// to rounding), which the Galerkin kernels need to know.
 __global__ void k_edge_keys(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                             const double* __restrict__ v, const double* __restrict__ kii,
                             const double* __restrict__ w, uint64_t* key, int* flag) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
+    bool asym = false;  // some K(j,i) differs from K(i,j) in its bits
     for (int i = warp; i < n; i += nw) {
         const double wi = w[i], ki = kii[i];
         for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
@@ -220,10 +223,15 @@ __global__ void k_edge_keys(int n, const int64_t* __restrict__ rp, const int32_t
                 if (cm < i) lo = mid + 1;
                 else hi = mid - 1;
             }
-            if (pos < 0) atomicOr(flag, 64);
-            else key[pos] = out;
+            if (pos < 0) {
+                atomicOr(flag, 64);
+            } else {
+                key[pos] = out;
+                asym |= __double_as_longlong(v[pos]) != __double_as_longlong(a);
+            }
         }
     }
+    if (__any_sync(FULL, asym) && lane == 0) atomicOr(flag, 128);
 }
 
 // Matching state: -1 active (unmatched, may still match), -2 dead (no
@@ -782,6 +790,238 @@ __global__ void k_galerkin_bitmap(int nc, const int64_t* __restrict__ rp, const 
     }
 }
 
+// Galerkin product with one warp per coarse row I (Sec. 3, Eq. of the
+// Galerkin projection).  The candidates of row I are the entries (a, b) of
+// its member rows a (a0, then a1); each goes to coarse column J = agg[b].
+// A warp-private bitmap over [Jmin, Jmax] with prefix popcounts ranks the
+// distinct J (the sorted coarse row) without sorting.
+//
+// Counting kernel: the bitmap covers `words` words at a time (windows over
+// the span), so any span fits; it records the widest span and the longest
+// coarse row (stats[0], stats[1]) for the values kernel's sizing.
+//
+// Values kernel: a coarse entry K_c(I,J) has at most four terms, one per
+// pair (a in I, b in J).  Each candidate records its index in the entry's
+// slot 2 rank(a in I) + rank(b in J) for J >= I (the canonical order of
+// K_c(I,J)); each entry then sums its slots' terms in slot order, a missing
+// slot contributing a zero term (the running sum starts from +0.0 and is
+// never -0.0, so adding a zero leaves it unchanged).  For J < I the entry is
+// defined as K_c(J,I), whose canonical order runs over J's members first:
+// with K(a,b) = K(b,a) in every bit its terms are (p_b K(a,b)) p_a in slot
+// 2 rank(b in J) + rank(a in I), so the lower triangle is computed in place
+// and needs no mirror pass.  When the level matrix is symmetric only up to
+// rounding (sym == 0) the lower entries are left to the mirror kernel.
+//
+// GB300 runs FP64 at about two lanes per SM per clock: the values kernel
+// spends 8 multiplies and 3 adds per entry with every lane busy, and keeps
+// its shared memory near 10 KB per row so that about 20 rows per SM are in
+// flight to cover the latency of the gathers (agg, mate, pval).
+constexpr int kGalWarps = 4;   // coarse rows per block
+constexpr int kGalBatch = 8;   // candidates per lane in flight in the gathers
+constexpr unsigned kNoSlot = 0xffffu;
+
+__device__ __forceinline__ size_t gal_align(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// member rows of a coarse row and their ranges in the level matrix
+struct GalRow {
+    int a0, a1, len0, len1;
+    int64_t b0, b1;
+};
+
+__device__ __forceinline__ GalRow gal_members(int a0, int a1, const int64_t* __restrict__ rp) {
+    GalRow r{a0, a1, 0, 0, 0, 0};
+    if (a0 >= 0) {
+        r.b0 = rp[a0];
+        r.len0 = (int)(rp[a0 + 1] - r.b0);
+    }
+    if (a1 >= 0) {
+        r.b1 = rp[a1];
+        r.len1 = (int)(rp[a1 + 1] - r.b1);
+    }
+    return r;
+}
+
+// Marks the candidates' columns d = jb[t] (>> shift) - wb in [0, 32 W) in
+// the bitmap.  Each lane takes a contiguous run of candidates (an odd
+// number, so the lanes' jb reads fall in distinct banks): neighbouring
+// candidates mostly share a bitmap word, and contiguous runs keep the lanes
+// of one atomic on different words.
+__device__ __forceinline__ void gal_mark(const int32_t* jb, int c, int shift, int wb, int W, uint32_t* bits, int lane) {
+    const int per = ((c + 31) >> 5) | 1;
+    const int tb = min(c, lane * per), te = min(c, tb + per);
+    for (int t = tb; t < te; t++) {
+        const int d = (jb[t] >> shift) - wb;
+        if (d >= 0 && d < 32 * W) atomicOr(&bits[d >> 5], 1u << (d & 31));
+    }
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(kGalWarps * 32)
+    k_galerkin_warp(int nc, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                    const double* __restrict__ v, const int32_t* __restrict__ agg, const double* __restrict__ pval,
+                    const int32_t* __restrict__ mate, const int32_t* __restrict__ mem0,
+                    const int32_t* __restrict__ mem1, int cmax, int words, int umax, int sym, int64_t* rowcnt,
+                    const int64_t* __restrict__ crp, int32_t* cci, double* cv, int* stats, int* flag) {
+    extern __shared__ __align__(16) unsigned char gsm[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const size_t o_bits = gal_align(4 * (size_t)cmax);
+    const size_t o_pre = o_bits + gal_align(4 * (size_t)words);
+    const size_t o_sidx = o_pre + (FILL ? gal_align(2 * (size_t)words) : 0);
+    const size_t per_warp = o_sidx + (FILL ? gal_align(8 * (size_t)umax) : 0);
+    unsigned char* my = gsm + per_warp * wid;
+    int32_t* jb = reinterpret_cast<int32_t*>(my);  // candidates' coarse columns (FILL: 2 J + rank(b in J))
+    uint32_t* bits = reinterpret_cast<uint32_t*>(my + o_bits);
+    uint16_t* pre = reinterpret_cast<uint16_t*>(my + o_pre);     // FILL: entries before each word
+    uint2* sidx = reinterpret_cast<uint2*>(my + o_sidx);          // FILL: four 16-bit slots per entry
+    const int stride = gridDim.x * kGalWarps;
+    int I = blockIdx.x * kGalWarps + wid;
+    GalRow cur = gal_members(I < nc ? mem0[I] : -1, I < nc ? mem1[I] : -1, rp);
+    int span_max = 0, u_max = 0, err = 0;
+    for (; I < nc; I += stride) {
+        const int In = I + stride;  // the next row's members load during this row's gathers
+        const int n0 = In < nc ? mem0[In] : -1, n1 = In < nc ? mem1[In] : -1;
+        const int len0 = cur.len0, c = cur.len0 + cur.len1;
+        const bool fits = c <= cmax;  // sized from the row statistics; cannot fail
+        if (!fits) err = 1;
+        int lo = 0x7fffffff, hi = -1;
+        if (fits) {
+            for (int t0 = 0; t0 < c; t0 += 32 * kGalBatch) {
+                int bb[kGalBatch], jj[kGalBatch], mm[kGalBatch];
+#pragma unroll
+                for (int r = 0; r < kGalBatch; r++) {
+                    const int t = t0 + 32 * r + lane;
+                    bb[r] = t < c ? ci[t < len0 ? cur.b0 + t : cur.b1 + (t - len0)] : -1;
+                }
+#pragma unroll
+                for (int r = 0; r < kGalBatch; r++) {
+                    jj[r] = bb[r] >= 0 ? agg[bb[r]] : 0;
+                    mm[r] = (FILL && bb[r] >= 0) ? mate[bb[r]] : -1;
+                }
+#pragma unroll
+                for (int r = 0; r < kGalBatch; r++) {
+                    const int t = t0 + 32 * r + lane;
+                    if (t < c) {
+                        lo = min(lo, jj[r]);
+                        hi = max(hi, jj[r]);
+                        jb[t] = FILL ? 2 * jj[r] + ((mm[r] >= 0 && mm[r] < bb[r]) ? 1 : 0) : jj[r];
+                    }
+                }
+            }
+        }
+        lo = __reduce_min_sync(FULL, lo);
+        hi = __reduce_max_sync(FULL, hi);
+        const GalRow nxt = gal_members(n0, n1, rp);
+        __syncwarp();
+        if (fits && c > 0 && !FILL) {
+            int u = 0;
+            for (int wb = lo; wb <= hi; wb += 32 * words) {
+                const int W = min(words, ((hi - wb) >> 5) + 1);
+                for (int w = lane; w < W; w += 32) bits[w] = 0u;
+                __syncwarp();
+                gal_mark(jb, c, 0, wb, W, bits, lane);
+                __syncwarp();
+                int cnt = 0;
+                for (int w = lane; w < W; w += 32) cnt += __popc(bits[w]);
+                u += __reduce_add_sync(FULL, cnt);
+                __syncwarp();
+            }
+            if (lane == 0) rowcnt[I] = u;
+            span_max = max(span_max, hi - lo + 1);
+            u_max = max(u_max, u);
+        } else if (!FILL && lane == 0) {
+            rowcnt[I] = 0;
+        }
+        if (fits && c > 0 && FILL) {
+            const int W = ((hi - lo) >> 5) + 1;
+            if (W > words) err = 1;  // sized from the counting kernel; cannot happen
+            int u = 0;
+            if (W <= words) {
+                for (int w = lane; w < W; w += 32) bits[w] = 0u;
+                __syncwarp();
+                gal_mark(jb, c, 1, lo, W, bits, lane);
+                __syncwarp();
+                // exclusive prefix of the words' popcounts (contiguous chunks per lane)
+                const int per = (W + 31) >> 5;
+                const int w0 = min(W, lane * per), w1 = min(W, w0 + per);
+                int mine = 0;
+                for (int w = w0; w < w1; w++) mine += __popc(bits[w]);
+                int incl = mine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                u = __shfl_sync(FULL, incl, 31);
+                int run = incl - mine;
+                for (int w = w0; w < w1; w++) {
+                    pre[w] = (uint16_t)run;
+                    run += __popc(bits[w]);
+                }
+                if (u > umax) err = 1;  // sized from the counting kernel; cannot happen
+            }
+            if (W <= words && u <= umax) {
+                for (int pos = lane; pos < u; pos += 32) sidx[pos] = make_uint2(0xffffffffu, 0xffffffffu);
+                __syncwarp();
+                // every candidate's slot
+                for (int t = lane; t < c; t += 32) {
+                    const int e = jb[t];
+                    const int J = e >> 1, rb = e & 1, ra = t >= len0 ? 1 : 0;
+                    const int d = J - lo;
+                    const int pos = pre[d >> 5] + __popc(bits[d >> 5] & ((1u << (d & 31)) - 1u));
+                    const int q = J >= I ? 2 * ra + rb : 2 * rb + ra;
+                    reinterpret_cast<uint16_t*>(sidx)[4 * pos + q] = (uint16_t)t;
+                }
+                __syncwarp();
+                // entries: the slots' terms and their ordered sum
+                const int64_t base = crp[I];
+                const double p0 = pval[cur.a0], p1 = cur.a1 >= 0 ? pval[cur.a1] : 0.0;
+                for (int pos = lane; pos < u; pos += 32) {
+                    const uint2 raw = sidx[pos];
+                    const unsigned tq[4] = {raw.x & 0xffffu, raw.x >> 16, raw.y & 0xffffu, raw.y >> 16};
+                    int64_t kk[4];
+                    int bq[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const int t = (int)tq[q];
+                        kk[q] = t < len0 ? cur.b0 + t : cur.b1 + (t - len0);
+                        bq[q] = tq[q] != kNoSlot ? ci[kk[q]] : -1;
+                    }
+                    const unsigned tv = tq[0] != kNoSlot ? tq[0] : tq[1] != kNoSlot ? tq[1] : tq[2] != kNoSlot ? tq[2] : tq[3];
+                    const int J = jb[min((int)tv, c - 1)] >> 1;  // every entry holds a candidate
+                    const bool upper = J >= I;
+                    double term[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const double vk = bq[q] >= 0 ? v[kk[q]] : 0.0;
+                        const double pb = bq[q] >= 0 ? pval[bq[q]] : 0.0;
+                        const int ra = upper ? (q >> 1) : (q & 1);
+                        const double pa = ra ? p1 : p0;
+                        term[q] = __dmul_rn(__dmul_rn(upper ? pa : pb, vk), upper ? pb : pa);
+                    }
+                    // +0.0 + term[0] without an FP64 add: only -0.0 changes (to +0.0)
+                    double acc = __double_as_longlong(term[0]) == (long long)0x8000000000000000ULL ? 0.0 : term[0];
+                    acc = __dadd_rn(acc, term[1]);
+                    acc = __dadd_rn(acc, term[2]);
+                    acc = __dadd_rn(acc, term[3]);
+                    cci[base + pos] = J;
+                    cv[base + pos] = acc;
+                }
+            }
+            __syncwarp();
+        }
+        cur = nxt;
+    }
+    if (!FILL) {
+        span_max = __reduce_max_sync(FULL, span_max);
+        u_max = __reduce_max_sync(FULL, u_max);
+        if (lane == 0) {
+            atomicMax(stats, span_max);
+            atomicMax(stats + 1, u_max);
+        }
+    }
+    if (__any_sync(FULL, err) && lane == 0) atomicOr(flag, 32);
+}
+
 // max over coarse rows of the coarse-column span Jmax - Jmin + 1
 __global__ void k_row_span(int nc, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const int32_t* __restrict__ agg, const int32_t* __restrict__ mem0,
@@ -1223,6 +1463,44 @@ cudaError_t launch_galerkin_fill_bitmap(const DevCSR& A, const int32_t* agg, con
         AMG_TRY(cudaFuncSetAttribute(k_galerkin_bitmap<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_galerkin_bitmap<true><<<AMG_GRID(blocks_for(C.n, 1, 65536)), kGalerkinBlock, sm, s>>>(
         C.n, A.rowptr, A.col, A.val, agg, pval, mem0, mem1, cap, words, nullptr, C.rowptr, C.col, C.val, flag);
+    return cudaGetLastError();
+}
+
+// Bitmap window of the warp counting kernel: 1024 words (32,768 coarse
+// columns) per pass over a row's candidates.
+constexpr int kGalCountWords = 1024;
+
+static size_t galerkin_warp_bytes(int cmax, int words, int umax, bool fill) {
+    auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    const size_t w = al(4 * (size_t)cmax) + al(4 * (size_t)words) +
+                     (fill ? al(2 * (size_t)words) + al(8 * (size_t)umax) : 0);
+    return w * kGalWarps;
+}
+
+size_t galerkin_warp_fill_smem(int cmax, int words, int umax) {
+    return galerkin_warp_bytes(cmax, words, umax, true);
+}
+
+cudaError_t launch_galerkin_warp_count(const DevCSR& A, const int32_t* agg, const int32_t* mem0, const int32_t* mem1,
+                                       int nc, int cmax, int64_t* rowcnt, int* stats, int* flag, cudaStream_t s) {
+    const size_t sm = galerkin_warp_bytes(cmax, kGalCountWords, 0, false);
+    if (sm > 48 * 1024)
+        AMG_TRY(cudaFuncSetAttribute(k_galerkin_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_galerkin_warp<false><<<AMG_GRID(blocks_for(nc, kGalWarps, 1 << 20)), kGalWarps * 32, sm, s>>>(
+        nc, A.rowptr, A.col, A.val, agg, nullptr, nullptr, mem0, mem1, cmax, kGalCountWords, 0, 0, rowcnt, nullptr,
+        nullptr, nullptr, stats, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_galerkin_warp_fill(const DevCSR& A, const int32_t* agg, const double* pval, const int32_t* mate,
+                                      const int32_t* mem0, const int32_t* mem1, int cmax, int words, int umax, int sym,
+                                      DevCSR& C, int* flag, cudaStream_t s) {
+    const size_t sm = galerkin_warp_bytes(cmax, words, umax, true);
+    if (sm > 48 * 1024)
+        AMG_TRY(cudaFuncSetAttribute(k_galerkin_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_galerkin_warp<true><<<AMG_GRID(blocks_for(C.n, kGalWarps, 1 << 20)), kGalWarps * 32, sm, s>>>(
+        C.n, A.rowptr, A.col, A.val, agg, pval, mate, mem0, mem1, cmax, words, umax, sym, nullptr, C.rowptr, C.col,
+        C.val, nullptr, flag);
     return cudaGetLastError();
 }
 

@@ -100,6 +100,35 @@ def test_setup_bit_exact_variable_coefficient_annulus():
     assert_setup_identical(H, Ho)
 
 
+def _symmetry_variant(prob, lower_ulps):
+    """The input with every lower entry set to its upper mirror's bits, moved
+    by `lower_ulps` ulps: 0 gives a matrix symmetric in every bit, 1 one that
+    is symmetric only up to rounding."""
+    import types
+    rp, ci = prob.rowptr, prob.col
+    v = prob.val.copy()
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    low = np.nonzero(ci < rows)[0]
+    for k in low:
+        i, j = rows[k], ci[k]
+        m = rp[j] + np.searchsorted(ci[rp[j]:rp[j + 1]], i)
+        v[k] = v[m]
+    if lower_ulps:
+        v[low] = np.nextafter(v[low], np.inf)
+    return types.SimpleNamespace(rowptr=rp, col=ci, val=v)
+
+
+@pytest.mark.parametrize("lower_ulps", [0, 1])
+def test_setup_bit_exact_bit_symmetric_and_rounding_symmetric_input(lower_ulps):
+    """The Galerkin values kernel computes the lower triangle in place when
+    the level matrix is symmetric in every bit (0) and leaves it to the
+    mirror pass when it is symmetric only up to rounding (1); the oracle
+    takes K_c(I,J), J < I, from K_c(J,I) in both cases."""
+    prob = _symmetry_variant(I.annulus_kappa(6, 2, kappa_seed=3), lower_ulps)
+    H, Ho = setup_both(prob, coarse_max=30)
+    assert_setup_identical(H, Ho)
+
+
 @pytest.mark.parametrize("d,n,p", CASES)
 def test_level_spmv_matches_oracle(d, n, p):
     prob = I.poisson_box(d, n, p)

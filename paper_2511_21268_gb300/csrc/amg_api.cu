@@ -309,6 +309,15 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
     const int maxr = h->o.max_match_rounds;
     CK(cudaMemsetAsync(h->round_active, 0, sizeof(int) * (maxr + kRoundBatch), s));
     int rounds = 0, done = 0;
+    if (h->coop) {  // every round in one launch, one read
+        CK(launch_match_rounds_coop(A, key, state, cand, h->round_active, lists, maxr, h->flag + 6, h->num_sms, s));
+        CK(cudaMemcpyAsync(h->flag_host, h->flag + 6, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h->flag_host + 32, h->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        rounds = h->flag_host[0];
+        if (rounds > maxr) return AMG_ERR_TIMEOUT;
+        done = 1;
+    }
     while (!done) {
         if (rounds >= maxr) return AMG_ERR_TIMEOUT;
         const int cnt = std::min(kRoundBatch, maxr - rounds);
@@ -1001,6 +1010,7 @@ static int create_hierarchy(const amg_opts* opts, void* cuda_stream, amg_hierarc
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->coop, cudaDevAttrCooperativeLaunch, dev);
     if (e != cudaSuccess) {
         rc = cuda_fail(e, "amg_setup init");
         destroy(h);

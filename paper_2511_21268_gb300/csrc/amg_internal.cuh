@@ -190,6 +190,7 @@ struct amg_hierarchy {
     int hist_cap = 0;
     amg_info info;
     int num_sms = 0;
+    int coop = 0;  // the device runs cooperative launches (all matching rounds of a pass in one)
     bool own_stream = false;
     // captured iteration graph
     cudaGraphExec_t graph = nullptr;
@@ -255,6 +256,8 @@ cudaError_t launch_edge_keys(const DevCSR& A, const double* kii, const double* w
 cudaError_t launch_match_init(int n, int32_t* state, cudaStream_t s);
 cudaError_t launch_match_rounds(const DevCSR& A, const uint64_t* key, int32_t* state, int32_t* cand, int* active,
                                 int32_t* lists, int first_round, int count, cudaStream_t s);
+cudaError_t launch_match_rounds_coop(const DevCSR& A, const uint64_t* key, int32_t* state, int32_t* cand, int* active,
+                                     int32_t* lists, int max_rounds, int* rounds_out, int num_sms, cudaStream_t s);
 cudaError_t launch_match_finish(int n, const int32_t* state, int32_t* mate, int32_t* leader, cudaStream_t s);
 cudaError_t launch_aggregate(int n, const int32_t* mate, const int32_t* cidx, const double* w, int32_t* agg,
                              double* pval, int32_t* mem0, int32_t* mem1, double* wc, cudaStream_t s);

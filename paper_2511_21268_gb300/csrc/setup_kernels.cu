@@ -15,12 +15,16 @@
 // never computed redundantly across lanes: a warp folds 32 rows at once, each
 // lane owning one row, after staging 32x32 tiles through shared memory with
 // coalesced loads.
+#include <algorithm>
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "amg_internal.cuh"
 
 namespace amg {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -178,6 +182,21 @@ __global__ void __launch_bounds__(kBlock) k_testvec_sweep(int n, const int64_t* 
 }
 
 // ------------------------------------------------------------------ matching
+// Tests of an FP64 value decided on its bits, so that they take no FP64
+// instruction (GB300 issues about two FP64 operations per SM per clock):
+// x != 0.0 (NaN counts as nonzero, as in IEEE comparison), x > 0.0 (true on
+// (0, +inf], false for zeros, negatives and NaN), and x is NaN.
+__device__ __forceinline__ bool nonzero_bits(double x) {
+    return ((unsigned long long)__double_as_longlong(x) << 1) != 0ull;
+}
+__device__ __forceinline__ bool positive_bits(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool nan_bits(double x) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+}
+
 // Edge key of every stored entry: order_key(c_ij) (Eq. cij) for eligible
 // edges, 0 otherwise.  Eligible: j != i, k_ij != 0, denominator > 0 and
 // w_lo^2 + w_hi^2 > 0.  Each edge is evaluated once, from its upper entry
@@ -194,7 +213,8 @@ __global__ void k_edge_keys(int n, const int64_t* __restrict__ rp, const int32_t
     const int nw = (gridDim.x * blockDim.x) >> 5;
     bool asym = false;  // some K(j,i) differs from K(i,j) in its bits
     for (int i = warp; i < n; i += nw) {
-        const double wi = w[i], ki = kii[i];
+        const double wi = w[i];
+        const double wi2 = __dmul_rn(wi, wi), kwi2 = __dmul_rn(kii[i], wi2);
         for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
             const int j = ci[k];
             if (j < i) continue;  // written by the owner of the upper entry
@@ -204,12 +224,14 @@ __global__ void k_edge_keys(int n, const int64_t* __restrict__ rp, const int32_t
             }
             const double a = v[k];
             uint64_t out = 0;
-            if (a != 0.0) {
-                const double wj = w[j], kj = kii[j];
+            if (nonzero_bits(a)) {
+                const double wj = w[j];
+                const double wj2 = __dmul_rn(wj, wj);
                 const double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a), wi), wj);
-                const double den = __dadd_rn(__dmul_rn(ki, __dmul_rn(wi, wi)), __dmul_rn(kj, __dmul_rn(wj, wj)));
-                const double nrm2 = __dadd_rn(__dmul_rn(wi, wi), __dmul_rn(wj, wj));
-                if (den > 0.0 && nrm2 > 0.0) out = order_key(__dsub_rn(1.0, __ddiv_rn(num, den)));
+                const double den = __dadd_rn(kwi2, __dmul_rn(kii[j], wj2));
+                // w_i^2 + w_j^2 > 0: both squares are +0, positive, +inf or NaN
+                const bool nrm2_pos = !nan_bits(wi2) && !nan_bits(wj2) && (positive_bits(wi2) || positive_bits(wj2));
+                if (positive_bits(den) && nrm2_pos) out = order_key(__dsub_rn(1.0, __ddiv_rn(num, den)));
             }
             key[k] = out;
             int64_t lo = rp[j], hi = rp[j + 1] - 1, pos = -1;
@@ -247,24 +269,32 @@ __device__ __forceinline__ bool heavier(uint64_t ka, int loa, int hia, uint64_t 
     return hia < hib;
 }
 
+// Loads of the matching state, which the rounds of one cooperative launch
+// write from other SMs: COHERENT loads bypass L1 (ld.global.cg), plain
+// loads are used between separate launches.
+template <bool COHERENT>
+__device__ __forceinline__ int ld_match(const int* p) {
+    if (COHERENT) return __ldcg(p);
+    return *p;
+}
+
 // Every active vertex proposes to its heaviest eligible active neighbour.
-__global__ void k_match_propose(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                const uint64_t* __restrict__ key, const int32_t* __restrict__ state,
-                                int32_t* cand, const int32_t* __restrict__ list, const int* __restrict__ count) {
-    // round 0: every vertex (list NULL); later rounds: the vertices the
-    // previous round left active
-    const int m = list ? *count : n;
-    if (m == 0) return;  // the matching already ended: a no-op round
+// Round 0 covers every vertex (list NULL); later rounds the vertices the
+// previous round left active (list, *count).  Warps gw = 0 .. nw-1 of the
+// grid take one vertex at a time.
+template <bool COHERENT>
+__device__ __forceinline__ void match_propose(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                              const uint64_t* __restrict__ key, const int32_t* state, int32_t* cand,
+                                              const int32_t* list, const int* count, int gw, int nw) {
+    const int m = list ? ld_match<COHERENT>(count) : n;
     const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int idx = warp; idx < m; idx += nw) {
-        const int i = list ? list[idx] : idx;
+    for (int idx = gw; idx < m; idx += nw) {
+        const int i = list ? ld_match<COHERENT>(list + idx) : idx;
         // Active neighbours only leave between rounds, so the heaviest one of
         // the previous round is still the heaviest while it stays active.
         if (list) {
-            const int c = cand[i];
-            if (c >= 0 && state[c] == -1) continue;
+            const int c = ld_match<COHERENT>(cand + i);
+            if (c >= 0 && ld_match<COHERENT>(state + c) == -1) continue;
         }
         uint64_t bk = 0;
         int blo = 0x7fffffff, bhi = 0x7fffffff, bj = -1;
@@ -282,7 +312,7 @@ __global__ void k_match_propose(int n, const int64_t* __restrict__ rp, const int
                 jj[u] = k < b1 ? ci[k] : 0;
             }
 #pragma unroll
-            for (int u = 0; u < 4; u++) sj[u] = kk[u] != 0 ? state[jj[u]] : 0;
+            for (int u = 0; u < 4; u++) sj[u] = kk[u] != 0 ? ld_match<COHERENT>(state + jj[u]) : 0;
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 if (kk[u] == 0 || sj[u] != -1) continue;
@@ -317,21 +347,23 @@ __global__ void k_match_propose(int n, const int64_t* __restrict__ rp, const int
 // all): mutual proposals pair, vertices without a candidate become
 // singletons, the others stay active and are appended to list_out, whose
 // length *count_out (zero on entry) is the round's active count.  The list's
-// order depends on the atomics; nothing computed from it does.
-__global__ void k_match_commit(int n, const int32_t* __restrict__ cand, int32_t* state,
-                               const int32_t* __restrict__ list_in, const int* __restrict__ count_in,
-                               int32_t* list_out, int* count_out) {
-    const int m = list_in ? *count_in : n;
+// order depends on the atomics; nothing computed from it does.  Blocks
+// blk = 0 .. nblk-1 take blockDim.x vertices at a time.
+template <bool COHERENT>
+__device__ __forceinline__ void match_commit(int n, const int32_t* cand, int32_t* state, const int32_t* list_in,
+                                             const int* count_in, int32_t* list_out, int* count_out, int blk,
+                                             int nblk) {
+    const int m = list_in ? ld_match<COHERENT>(count_in) : n;
     const int lane = threadIdx.x & 31;
-    for (int base = blockIdx.x * blockDim.x; base < m; base += gridDim.x * blockDim.x) {  // warp-uniform
+    for (int base = blk * blockDim.x; base < m; base += nblk * blockDim.x) {  // warp-uniform
         const int idx = base + threadIdx.x;
         int i = -1;
         bool keep = false;
         if (idx < m) {
-            i = list_in ? list_in[idx] : idx;
-            const int c = cand[i];
+            i = list_in ? ld_match<COHERENT>(list_in + idx) : idx;
+            const int c = ld_match<COHERENT>(cand + i);
             if (c < 0) state[i] = -2;
-            else if (cand[c] == i) state[i] = c;
+            else if (ld_match<COHERENT>(cand + c) == i) state[i] = c;
             else keep = true;
         }
         const unsigned b = __ballot_sync(FULL, keep);
@@ -340,6 +372,48 @@ __global__ void k_match_commit(int n, const int32_t* __restrict__ cand, int32_t*
         off = __shfl_sync(FULL, off, 0);
         if (keep) list_out[off + __popc(b & ((1u << lane) - 1u))] = i;
     }
+}
+
+__global__ void k_match_propose(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                const uint64_t* __restrict__ key, const int32_t* __restrict__ state,
+                                int32_t* cand, const int32_t* __restrict__ list, const int* __restrict__ count) {
+    match_propose<false>(n, rp, ci, key, state, cand, list, count, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                         (gridDim.x * blockDim.x) >> 5);
+}
+
+__global__ void k_match_commit(int n, const int32_t* __restrict__ cand, int32_t* state,
+                               const int32_t* __restrict__ list_in, const int* __restrict__ count_in,
+                               int32_t* list_out, int* count_out) {
+    match_commit<false>(n, cand, state, list_in, count_in, list_out, count_out, blockIdx.x, gridDim.x);
+}
+
+// Every round of one matching pass in one cooperative launch: propose, grid
+// barrier, commit, grid barrier, until a round leaves no vertex active or
+// max_rounds rounds have run.  *rounds_out = the number of rounds run, or
+// max_rounds + 1 if the last one still left active vertices.  The launch
+// fits the grid to the blocks that can be resident at once, so the
+// barriers cannot wait on a block that never runs.
+__global__ void __launch_bounds__(kBlock) k_match_rounds_coop(int n, const int64_t* __restrict__ rp,
+                                                              const int32_t* __restrict__ ci,
+                                                              const uint64_t* __restrict__ key, int32_t* state,
+                                                              int32_t* cand, int* active, int32_t* lists,
+                                                              int max_rounds, int* rounds_out) {
+    cg::grid_group g = cg::this_grid();
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int r = 0; r < max_rounds; r++) {
+        const int32_t* lin = r > 0 ? lists + (size_t)((r - 1) & 1) * n : nullptr;
+        const int* cin = r > 0 ? active + r - 1 : nullptr;
+        match_propose<true>(n, rp, ci, key, state, cand, lin, cin, gw, nw);
+        g.sync();
+        match_commit<true>(n, cand, state, lin, cin, lists + (size_t)(r & 1) * n, active + r, blockIdx.x, gridDim.x);
+        g.sync();
+        if (__ldcg(active + r) == 0) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) *rounds_out = r + 1;
+            return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *rounds_out = max_rounds + 1;
 }
 
 __global__ void k_match_finish(int n, const int32_t* __restrict__ state, int32_t* mate, int32_t* leader) {
@@ -1387,6 +1461,23 @@ cudaError_t launch_match_rounds(const DevCSR& A, const uint64_t* key, int32_t* s
                                                          active + round);
     }
     return cudaGetLastError();
+}
+
+// All rounds of a pass in one cooperative launch (see k_match_rounds_coop):
+// up to four blocks per SM, never more than can be resident at once.
+// active[0 .. max_rounds-1] must be zero on entry.
+cudaError_t launch_match_rounds_coop(const DevCSR& A, const uint64_t* key, int32_t* state, int32_t* cand, int* active,
+                                     int32_t* lists, int max_rounds, int* rounds_out, int num_sms, cudaStream_t s) {
+    int per_sm = 0;
+    AMG_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match_rounds_coop, kBlock, 0));
+    if (per_sm < 1 || num_sms < 1) return cudaErrorNotSupported;
+    const int blocks = num_sms * std::min(per_sm, 4);
+    int n = A.n;
+    const int64_t* rp = A.rowptr;
+    const int32_t* ci = A.col;
+    void* args[] = {&n, &rp, &ci, &key, &state, &cand, &active, &lists, &max_rounds, &rounds_out};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_match_rounds_coop), dim3(blocks), dim3(kBlock), args,
+                                       0, s);
 }
 
 cudaError_t launch_match_finish(int n, const int32_t* state, int32_t* mate, int32_t* leader, cudaStream_t s) {

@@ -306,6 +306,19 @@ int amg_kernel_times(const amg_hierarchy* h, double* ms, int64_t* count, double*
 int amg_dfma_probe(int32_t variant, int32_t blocks, int64_t trips, double* out_dev, void* cuda_stream,
                    int32_t* threads, double* flops);
 
+/* Check of the correctly rounded FP64 division the setup uses for the edge
+ * weights c_ij (Sec. 3.1, Eq. of the edge weights): q_dev[i] = a_dev[i] /
+ * b_dev[i] rounded to nearest even, for i < n, and *fast_count_dev (DEVICE,
+ * added to, not cleared) += the number of quotients the division's fast path
+ * accepted (a reciprocal estimate, one Newton-Raphson step, a residual
+ * correction and an exact residual test; the rest go to the compiler's
+ * division).  All arrays are DEVICE memory of n doubles; the work is
+ * enqueued on cuda_stream (NULL = default stream) and the call returns at
+ * once.  Used by the tests to hold the division to IEEE results.  Errors:
+ * AMG_ERR_ARG (n < 0, a NULL array with n > 0), AMG_ERR_CUDA. */
+int amg_div_check(int64_t n, const double* a_dev, const double* b_dev, double* q_dev, uint64_t* fast_count_dev,
+                  void* cuda_stream);
+
 /* Largest system amg_relres_noalloc accepts (rows). */
 #define AMG_NOALLOC_MAX_ROWS (1 << 19)
 

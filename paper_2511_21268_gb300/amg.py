@@ -129,6 +129,7 @@ _SIGS = {
     "amg_set_damping": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "amg_dfma_probe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "amg_div_check": (ctypes.c_int, [ctypes.c_int64] + [ctypes.c_void_p] * 5),
     "amg_smoother_bound": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "amg_staged_wait_selftest": (ctypes.c_int, [ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "amg_iga_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -560,6 +561,19 @@ def amg_dfma_probe(variant: int, blocks: int, trips: int, out, stream=None) -> f
     _check(lib().amg_dfma_probe(int(variant), int(blocks), int(trips), out.data_ptr(), _stream_handle(stream),
                                 ctypes.byref(t), ctypes.byref(fl)), "amg_dfma_probe")
     return fl.value
+
+
+def amg_div_check(a, b, stream=None):
+    """(a / b rounded by the library's FP64 division, number of quotients its
+    fast path accepted) for device float64 tensors a, b of equal length."""
+    import torch
+    a = a.contiguous()
+    b = b.contiguous()
+    q = torch.empty_like(a)
+    cnt = torch.zeros(1, dtype=torch.int64, device=a.device)
+    _check(lib().amg_div_check(a.numel(), a.data_ptr(), b.data_ptr(), q.data_ptr(), cnt.data_ptr(),
+                               _stream_handle(stream)), "amg_div_check")
+    return q, cnt
 
 
 def amg_export_coarse(h):

@@ -395,9 +395,62 @@ size_t partial_slot_count();
 // Monotone map of a finite double to an unsigned key (larger value ->
 // larger key); -0 is folded onto +0.  Key 0 is reserved for "no edge".
 __device__ __forceinline__ uint64_t order_key(double c) {
-    if (c == 0.0) c = 0.0;
     uint64_t b = (uint64_t)__double_as_longlong(c);
+    if ((b << 1) == 0) b = 0;  // -0 -> +0, decided on the bits
     return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+
+// Correctly rounded a / b (IEEE binary64, round to nearest even): the same
+// bits as __ddiv_rn(a, b), in fewer FP64 operations for operands of
+// moderate magnitude (both normal, binary exponents in [-500, 500]); other
+// operands go to __ddiv_rn.
+//   1. y0 ~ 1/b: the FP32 reciprocal of b's leading 23 mantissa bits, scaled
+//      by integer exponent arithmetic (relative error below 2^-22).
+//   2. One Newton-Raphson step, y1 = y0 + y0 (1 - b y0) (error below 2^-44).
+//   3. q0 = a y1 and Markstein's correction q = q0 + (a - b q0) y1, whose
+//      value before rounding lies within about 2^-89 (relative) of a / b.
+//   4. Acceptance: the FMA residual r = a - b q is exact whenever q is a
+//      faithful quotient (Boldo and Daumas, "Representable correcting terms
+//      for possibly underflowing floating point operations", 2003), and then
+//      |r| < |b| h(q), h(q) the half-gap from q to its nearer neighbour
+//      (half an ulp; a quarter at a power of two), says a / b is closer to q
+//      than to either neighbour, i.e. q = RN(a / b).  When q is not faithful
+//      |r| is at least |b| times a full gap, so the test fails; it also fails
+//      on exact ties.  A failed test falls back to __ddiv_rn.
+// Six FP64 operations on the fast path; the tests run on integer bits.
+// div_rn_fast returns false (and leaves *q unset) where the fast path
+// declines.
+__device__ __forceinline__ bool div_rn_fast(double a, double b, double* q_out) {
+    const long long ab = __double_as_longlong(a), bb = __double_as_longlong(b);
+    const int ea = (int)((ab >> 52) & 0x7ff) - 1023, eb = (int)((bb >> 52) & 0x7ff) - 1023;
+    if (ea < -500 || ea > 500 || eb < -500 || eb > 500) return false;
+    // 1. reciprocal estimate: f = 1.m (FP32, top 23 mantissa bits), 1/f in (1/2, 1]
+    const float f = __int_as_float(0x3f800000 | (int)((bb >> 29) & 0x7fffff));
+    const int rf = __float_as_int(__frcp_rn(f));
+    const int erf = ((rf >> 23) & 0xff) - 127;  // -1 or 0
+    const long long y0b = (bb & (long long)0x8000000000000000ULL) | ((long long)(erf - eb + 1023) << 52) |
+                          ((long long)(rf & 0x7fffff) << 29);
+    const double y0 = __longlong_as_double(y0b);
+    // 2. Newton-Raphson step
+    const double y1 = __fma_rn(y0, __fma_rn(-b, y0, 1.0), y0);
+    // 3. quotient and correction
+    const double q0 = __dmul_rn(a, y1);
+    const double q = __fma_rn(__fma_rn(-b, q0, a), y1, q0);
+    // 4. exact residual and acceptance test on the bits
+    const double r = __fma_rn(-b, q, a);
+    const long long qb = __double_as_longlong(q) & 0x7fffffffffffffffLL;
+    const int eq = (int)(qb >> 52) - 1023;
+    const int k = ((qb & 0xfffffffffffffLL) == 0 ? eq - 54 : eq - 53);  // log2 of h(q)
+    const long long tb = (bb & 0x7fffffffffffffffLL) + ((long long)k << 52);  // |b| h(q), exact
+    const long long rb = __double_as_longlong(r) & 0x7fffffffffffffffLL;
+    if (eq < -1010 || eq > 1010 || rb >= tb) return false;
+    *q_out = q;
+    return true;
+}
+
+__device__ __forceinline__ double div_rn(double a, double b) {
+    double q;
+    return div_rn_fast(a, b, &q) ? q : __ddiv_rn(a, b);
 }
 
 // SplitMix64 (Steele, Lea, Flood 2014): draw k of the stream seeded `seed`.

@@ -14,6 +14,7 @@
 // by all chains most shapes level off at 0.84 of the unit-count rate, while
 // four chains with their own operands at 128 threads reach it; the caller
 // times every variant and keeps the fastest.
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -76,4 +77,33 @@ extern "C" int amg_dfma_probe(int32_t variant, int32_t blocks, int64_t trips, do
     if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
     if (flops) *flops = 2.0 * v.chains * kUnroll * (double)trips * (double)blocks * v.threads;
     return AMG_OK;
+}
+
+// Check of the library's correctly rounded division (div_rn, used by the
+// edge weights of the matching): q[i] = div_rn(a[i], b[i]) and the number of
+// quotients its fast path accepted.
+namespace {
+__global__ void k_div_check(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* q,
+                            unsigned long long* fast) {
+    unsigned long long local = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double f;
+        const bool ok = amg::div_rn_fast(a[i], b[i], &f);
+        q[i] = amg::div_rn(a[i], b[i]);
+        local += ok ? 1 : 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(fast, local);
+}
+}  // namespace
+
+extern "C" int amg_div_check(int64_t n, const double* a_dev, const double* b_dev, double* q_dev,
+                             uint64_t* fast_count_dev, void* cuda_stream) {
+    if (n < 0 || (n > 0 && (!a_dev || !b_dev || !q_dev || !fast_count_dev))) return AMG_ERR_ARG;
+    if (n == 0) return AMG_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    k_div_check<<<AMG_GRID((int)blocks), 256, 0, s>>>(n, a_dev, b_dev, q_dev,
+                                                     reinterpret_cast<unsigned long long*>(fast_count_dev));
+    return cudaGetLastError() == cudaSuccess ? AMG_OK : AMG_ERR_CUDA;
 }

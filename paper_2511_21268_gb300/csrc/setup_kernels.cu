@@ -77,6 +77,11 @@ __global__ void k_validate(int n, int64_t nnz, const int64_t* __restrict__ rp, c
 // the rows to fill them (the lanes' sums are dependent chains, and the loads
 // of other warps fill their gaps); with few rows a wide chunk (32) does the
 // same work in fewer synchronised steps.
+// |x| by clearing the sign bit (an integer operation, not an FP64 one).
+__device__ __forceinline__ double abs_bits(double x) {
+    return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+}
+
 template <int CW, typename Term>
 __device__ __forceinline__ double fold_rows(int row0, int n, const int64_t* __restrict__ rp, Term term,
                                             double (*tile)[CW + 1]) {
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(kBlock) k_l1diag(int n, const int64_t* __restr
                 dg[row - row0] = x;
                 return 0.0;
             }
-            return fabs(x);
+            return abs_bits(x);
         };
         const double s = fold_rows<CW>(row0, n, rp, term, tile);
         __syncwarp();
@@ -231,7 +236,7 @@ __global__ void k_edge_keys(int n, const int64_t* __restrict__ rp, const int32_t
                 const double den = __dadd_rn(kwi2, __dmul_rn(kii[j], wj2));
                 // w_i^2 + w_j^2 > 0: both squares are +0, positive, +inf or NaN
                 const bool nrm2_pos = !nan_bits(wi2) && !nan_bits(wj2) && (positive_bits(wi2) || positive_bits(wj2));
-                if (positive_bits(den) && nrm2_pos) out = order_key(__dsub_rn(1.0, __ddiv_rn(num, den)));
+                if (positive_bits(den) && nrm2_pos) out = order_key(__dsub_rn(1.0, div_rn(num, den)));
             }
             key[k] = out;
             int64_t lo = rp[j], hi = rp[j + 1] - 1, pos = -1;

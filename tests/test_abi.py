@@ -35,6 +35,9 @@ def test_library_exports_every_declared_symbol():
     assert L.amg_mpnn_apply(None, None, 0) == -1
     assert L.amg_mpnn_loss_grad(None, None, 1, ctypes.c_uint64(0), None, None) == -1
     assert L.amg_mpnn_train(None, 1, None, 1, 1, ctypes.c_uint64(0), ctypes.c_float(0.01), None) == -1
+    assert L.amg_div_check(ctypes.c_int64(-1), None, None, None, None, None) == -1
+    assert L.amg_div_check(ctypes.c_int64(4), None, None, None, None, None) == -1
+    assert L.amg_div_check(ctypes.c_int64(0), None, None, None, None, None) == 0
 
 
 def test_binding_names_match_abi():

@@ -392,10 +392,20 @@ size_t partial_slot_count();
 
 // ----------------------------------------------------------------- device helpers
 #ifdef __CUDACC__
+// The bits of an FP64 value through an opaque move, so that the compiler
+// keeps integer operations on them integer: masking the sign bit of a
+// reinterpreted double would otherwise become an FP64 absolute value, and
+// some tests of the bits FP64 comparisons, on GB300's narrow FP64 pipe.
+__device__ __forceinline__ long long dbits(double x) {
+    long long r;
+    asm("mov.b64 %0, %1;" : "=l"(r) : "d"(x));
+    return r;
+}
+
 // Monotone map of a finite double to an unsigned key (larger value ->
 // larger key); -0 is folded onto +0.  Key 0 is reserved for "no edge".
 __device__ __forceinline__ uint64_t order_key(double c) {
-    uint64_t b = (uint64_t)__double_as_longlong(c);
+    uint64_t b = (uint64_t)dbits(c);
     if ((b << 1) == 0) b = 0;  // -0 -> +0, decided on the bits
     return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
 }
@@ -421,7 +431,7 @@ __device__ __forceinline__ uint64_t order_key(double c) {
 // div_rn_fast returns false (and leaves *q unset) where the fast path
 // declines.
 __device__ __forceinline__ bool div_rn_fast(double a, double b, double* q_out) {
-    const long long ab = __double_as_longlong(a), bb = __double_as_longlong(b);
+    const long long ab = dbits(a), bb = dbits(b);
     const int ea = (int)((ab >> 52) & 0x7ff) - 1023, eb = (int)((bb >> 52) & 0x7ff) - 1023;
     if (ea < -500 || ea > 500 || eb < -500 || eb > 500) return false;
     // 1. reciprocal estimate: f = 1.m (FP32, top 23 mantissa bits), 1/f in (1/2, 1]
@@ -438,11 +448,11 @@ __device__ __forceinline__ bool div_rn_fast(double a, double b, double* q_out) {
     const double q = __fma_rn(__fma_rn(-b, q0, a), y1, q0);
     // 4. exact residual and acceptance test on the bits
     const double r = __fma_rn(-b, q, a);
-    const long long qb = __double_as_longlong(q) & 0x7fffffffffffffffLL;
+    const long long qb = dbits(q) & 0x7fffffffffffffffLL;
     const int eq = (int)(qb >> 52) - 1023;
     const int k = ((qb & 0xfffffffffffffLL) == 0 ? eq - 54 : eq - 53);  // log2 of h(q)
     const long long tb = (bb & 0x7fffffffffffffffLL) + ((long long)k << 52);  // |b| h(q), exact
-    const long long rb = __double_as_longlong(r) & 0x7fffffffffffffffLL;
+    const long long rb = dbits(r) & 0x7fffffffffffffffLL;
     if (eq < -1010 || eq > 1010 || rb >= tb) return false;
     *q_out = q;
     return true;

@@ -79,7 +79,7 @@ __global__ void k_validate(int n, int64_t nnz, const int64_t* __restrict__ rp, c
 // same work in fewer synchronised steps.
 // |x| by clearing the sign bit (an integer operation, not an FP64 one).
 __device__ __forceinline__ double abs_bits(double x) {
-    return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+    return __longlong_as_double(dbits(x) & 0x7fffffffffffffffLL);
 }
 
 template <int CW, typename Term>
@@ -192,14 +192,14 @@ __global__ void __launch_bounds__(kBlock) k_testvec_sweep(int n, const int64_t* 
 // x != 0.0 (NaN counts as nonzero, as in IEEE comparison), x > 0.0 (true on
 // (0, +inf], false for zeros, negatives and NaN), and x is NaN.
 __device__ __forceinline__ bool nonzero_bits(double x) {
-    return ((unsigned long long)__double_as_longlong(x) << 1) != 0ull;
+    return ((unsigned long long)dbits(x) << 1) != 0ull;
 }
 __device__ __forceinline__ bool positive_bits(double x) {
-    const long long b = __double_as_longlong(x);
+    const long long b = dbits(x);
     return b > 0 && b <= 0x7ff0000000000000LL;
 }
 __device__ __forceinline__ bool nan_bits(double x) {
-    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+    return (dbits(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
 }
 
 // Edge key of every stored entry: order_key(c_ij) (Eq. cij) for eligible
@@ -1078,7 +1078,7 @@ __global__ void __launch_bounds__(kGalWarps * 32)
                         term[q] = __dmul_rn(__dmul_rn(upper ? pa : pb, vk), upper ? pb : pa);
                     }
                     // +0.0 + term[0] without an FP64 add: only -0.0 changes (to +0.0)
-                    double acc = __double_as_longlong(term[0]) == (long long)0x8000000000000000ULL ? 0.0 : term[0];
+                    double acc = dbits(term[0]) == (long long)0x8000000000000000ULL ? 0.0 : term[0];
                     acc = __dadd_rn(acc, term[1]);
                     acc = __dadd_rn(acc, term[2]);
                     acc = __dadd_rn(acc, term[3]);

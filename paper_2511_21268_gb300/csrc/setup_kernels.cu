@@ -83,29 +83,68 @@ __device__ __forceinline__ double abs_bits(double x) {
 }
 
 template <int CW, typename Term>
-__device__ __forceinline__ double fold_rows(int row0, int n, const int64_t* __restrict__ rp, Term term,
+__device__ __forceinline__ double fold_rows(int row0, int n, const int64_t* __restrict__ rp,
+                                            const int32_t* __restrict__ ci, const double* __restrict__ v, Term term,
                                             double (*tile)[CW + 1]) {
     constexpr int kRowsPerLoad = 32 / CW;
+    constexpr int kLoads = 32 / kRowsPerLoad;  // entries a lane loads per chunk
     const int lane = threadIdx.x & 31;
     const int sub = lane % CW, rsel = lane / CW;
     const int my = row0 + lane;
     const int64_t mb = my < n ? rp[my] : 0;
     const int mlen = my < n ? (int)(rp[my + 1] - mb) : 0;
     const int maxlen = __reduce_max_sync(FULL, mlen);
-    double acc = 0.0;
-    for (int c = 0; c < maxlen; c += CW) {
-#pragma unroll(CW == 32 ? 16 : 8)
-        for (int r0 = 0; r0 < 32; r0 += kRowsPerLoad) {
-            const int r = r0 + rsel;
+    // chunk c's entries (column and value; column -1 past a row's end),
+    // loaded one chunk ahead of the sums so that the loads of the next chunk
+    // are in flight while this one is folded
+    auto load = [&](int c, int (&jj)[kLoads], double (&xx)[kLoads]) {
+#pragma unroll
+        for (int u = 0; u < kLoads; u++) {
+            const int r = u * kRowsPerLoad + rsel;
             const int64_t rb = __shfl_sync(FULL, mb, r);
             const int rl = __shfl_sync(FULL, mlen, r);
             const int t = c + sub;
-            tile[r][sub] = (t < rl) ? term(rb + t, row0 + r) : 0.0;
+            jj[u] = t < rl ? ci[rb + t] : -1;
+            xx[u] = t < rl ? v[rb + t] : 0.0;
+        }
+    };
+    double acc = 0.0;
+    if constexpr (kLoads > 8) {  // wide chunks: no register room for a second chunk
+        for (int c = 0; c < maxlen; c += CW) {
+#pragma unroll 16
+            for (int u = 0; u < kLoads; u++) {
+                const int r = u * kRowsPerLoad + rsel;
+                const int64_t rb = __shfl_sync(FULL, mb, r);
+                const int rl = __shfl_sync(FULL, mlen, r);
+                const int t = c + sub;
+                tile[r][sub] = t < rl ? term(ci[rb + t], v[rb + t], row0 + r) : 0.0;
+            }
+            __syncwarp();
+#pragma unroll 8
+            for (int s = 0; s < CW; s++) acc = __dadd_rn(acc, tile[lane][s]);
+            __syncwarp();
+        }
+        return acc;
+    }
+    int j0[kLoads], j1[kLoads];
+    double x0[kLoads], x1[kLoads];
+    if (maxlen > 0) load(0, j0, x0);
+    for (int c = 0; c < maxlen; c += CW) {
+        if (c + CW < maxlen) load(c + CW, j1, x1);  // warp-uniform
+#pragma unroll
+        for (int u = 0; u < kLoads; u++) {
+            const int r = u * kRowsPerLoad + rsel;
+            tile[r][sub] = j0[u] >= 0 ? term(j0[u], x0[u], row0 + r) : 0.0;
         }
         __syncwarp();
 #pragma unroll 8
         for (int s = 0; s < CW; s++) acc = __dadd_rn(acc, tile[lane][s]);
         __syncwarp();
+#pragma unroll
+        for (int u = 0; u < kLoads; u++) {
+            j0[u] = j1[u];
+            x0[u] = x1[u];
+        }
     }
     return acc;
 }
@@ -116,7 +155,7 @@ inline bool fold_narrow(int n, int num_sms) { return (int64_t)(n + 31) / 32 >= 3
 
 // l1 diagonal (Sec. 3.2): d_i = k_ii + sum_{j != i} |k_ij|.
 template <int CW>
-__global__ void __launch_bounds__(kBlock) k_l1diag(int n, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(kBlock, 3) k_l1diag(int n, const int64_t* __restrict__ rp,
                                                     const int32_t* __restrict__ ci, const double* __restrict__ v,
                                                     double* kii, double* dl1, double* invd, int* flag) {
     __shared__ double tiles[kWarpsPerBlock][32][CW + 1];
@@ -128,16 +167,14 @@ __global__ void __launch_bounds__(kBlock) k_l1diag(int n, const int64_t* __restr
     for (int row0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; row0 < n; row0 += nwarps * 32) {
         dg[lane] = 0.0;
         __syncwarp();
-        auto term = [&](int64_t k, int row) -> double {
-            const int j = ci[k];
-            const double x = v[k];
+        auto term = [&](int j, double x, int row) -> double {
             if (j == row) {
                 dg[row - row0] = x;
                 return 0.0;
             }
             return abs_bits(x);
         };
-        const double s = fold_rows<CW>(row0, n, rp, term, tile);
+        const double s = fold_rows<CW>(row0, n, rp, ci, v, term, tile);
         __syncwarp();
         const int i = row0 + lane;
         if (i < n) {
@@ -169,7 +206,7 @@ __global__ void k_testvec_init(int n, int kind, uint64_t seed, double* w) {
 
 // One relaxation sweep on K w = 0 (Sec. 3.1): w_i <- w_i - (K w)_i / d_i.
 template <int CW>
-__global__ void __launch_bounds__(kBlock) k_testvec_sweep(int n, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(kBlock, 3) k_testvec_sweep(int n, const int64_t* __restrict__ rp,
                                                            const int32_t* __restrict__ ci,
                                                            const double* __restrict__ v,
                                                            const double* __restrict__ dl1,
@@ -179,8 +216,8 @@ __global__ void __launch_bounds__(kBlock) k_testvec_sweep(int n, const int64_t* 
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int row0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; row0 < n; row0 += nwarps * 32) {
-        auto term = [&](int64_t k, int) -> double { return __dmul_rn(v[k], w[ci[k]]); };
-        const double s = fold_rows<CW>(row0, n, rp, term, tile);
+        auto term = [&](int j, double x, int) -> double { return __dmul_rn(x, w[j]); };
+        const double s = fold_rows<CW>(row0, n, rp, ci, v, term, tile);
         const int i = row0 + lane;
         if (i < n) wout[i] = __dsub_rn(w[i], __ddiv_rn(s, dl1[i]));
     }
@@ -1476,7 +1513,11 @@ cudaError_t launch_match_rounds_coop(const DevCSR& A, const uint64_t* key, int32
     int per_sm = 0;
     AMG_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match_rounds_coop, kBlock, 0));
     if (per_sm < 1 || num_sms < 1) return cudaErrorNotSupported;
-    const int blocks = num_sms * std::min(per_sm, 4);
+    // small levels: fewer blocks (about four vertices per warp in the first
+    // round) make the grid barriers cheaper
+    constexpr int kVertsPerBlock = 4 * (kBlock / 32);
+    const int64_t want = ((int64_t)A.n + kVertsPerBlock - 1) / kVertsPerBlock;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * std::min(per_sm, 4), want));
     int n = A.n;
     const int64_t* rp = A.rowptr;
     const int32_t* ci = A.col;

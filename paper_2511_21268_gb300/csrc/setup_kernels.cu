@@ -149,6 +149,77 @@ __device__ __forceinline__ double fold_rows(int row0, int n, const int64_t* __re
     return acc;
 }
 
+// The same fold for the terms x_k g[j_k] with a gathered factor g (the test
+// vector sweep's K w): three chunks in flight -- the entries of chunk c+2
+// load, the gathers of chunk c+1 (whose columns arrived) issue, and chunk c
+// is multiplied and folded -- so that neither the stream nor the gathers
+// wait on the FP64 sums.  kLoads = 4 keeps the three stages in registers at
+// four blocks per SM.
+template <int CW>
+__device__ __forceinline__ double fold_rows_gather(int row0, int n, const int64_t* __restrict__ rp,
+                                                   const int32_t* __restrict__ ci, const double* __restrict__ v,
+                                                   const double* __restrict__ g, double (*tile)[CW + 1]) {
+    constexpr int kRowsPerLoad = 32 / CW;
+    constexpr int kLoads = 32 / kRowsPerLoad;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % CW, rsel = lane / CW;
+    const int my = row0 + lane;
+    const int64_t mb = my < n ? rp[my] : 0;
+    const int mlen = my < n ? (int)(rp[my + 1] - mb) : 0;
+    const int maxlen = __reduce_max_sync(FULL, mlen);
+    auto load = [&](int c, int (&jj)[kLoads], double (&xx)[kLoads]) {
+#pragma unroll
+        for (int u = 0; u < kLoads; u++) {
+            const int r = u * kRowsPerLoad + rsel;
+            const int64_t rb = __shfl_sync(FULL, mb, r);
+            const int rl = __shfl_sync(FULL, mlen, r);
+            const int t = c + sub;
+            jj[u] = t < rl ? ci[rb + t] : -1;
+            xx[u] = t < rl ? v[rb + t] : 0.0;
+        }
+    };
+    auto gather = [&](const int (&jj)[kLoads], double (&gg)[kLoads]) {
+#pragma unroll
+        for (int u = 0; u < kLoads; u++) gg[u] = jj[u] >= 0 ? g[jj[u]] : 0.0;
+    };
+    int j1[kLoads], j2[kLoads];
+    double x0[kLoads], g0[kLoads], x1[kLoads], g1[kLoads], x2[kLoads];
+#pragma unroll
+    for (int u = 0; u < kLoads; u++) {
+        j1[u] = j2[u] = -1;
+        x1[u] = x2[u] = g1[u] = 0.0;
+    }
+    double acc = 0.0;
+    if (maxlen <= 0) return acc;
+    {
+        int j0[kLoads];
+        load(0, j0, x0);
+        if (CW < maxlen) load(CW, j1, x1);
+        gather(j0, g0);
+    }
+    for (int c = 0; c < maxlen; c += CW) {
+        if (c + 2 * CW < maxlen) load(c + 2 * CW, j2, x2);  // warp-uniform
+        if (c + CW < maxlen) gather(j1, g1);
+#pragma unroll
+        for (int u = 0; u < kLoads; u++) {
+            const int r = u * kRowsPerLoad + rsel;
+            tile[r][sub] = __dmul_rn(x0[u], g0[u]);  // x = 0, g = 0 past a row's end: +0
+        }
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < CW; s++) acc = __dadd_rn(acc, tile[lane][s]);
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < kLoads; u++) {
+            x0[u] = x1[u];
+            g0[u] = g1[u];
+            j1[u] = j2[u];
+            x1[u] = x2[u];
+        }
+    }
+    return acc;
+}
+
 // Chunk width of the folds: narrow when the rows give every SM at least 32
 // warps.
 inline bool fold_narrow(int n, int num_sms) { return (int64_t)(n + 31) / 32 >= 32LL * num_sms; }
@@ -206,7 +277,7 @@ __global__ void k_testvec_init(int n, int kind, uint64_t seed, double* w) {
 
 // One relaxation sweep on K w = 0 (Sec. 3.1): w_i <- w_i - (K w)_i / d_i.
 template <int CW>
-__global__ void __launch_bounds__(kBlock, 3) k_testvec_sweep(int n, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(kBlock, 4) k_testvec_sweep(int n, const int64_t* __restrict__ rp,
                                                            const int32_t* __restrict__ ci,
                                                            const double* __restrict__ v,
                                                            const double* __restrict__ dl1,
@@ -216,8 +287,13 @@ __global__ void __launch_bounds__(kBlock, 3) k_testvec_sweep(int n, const int64_
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int row0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; row0 < n; row0 += nwarps * 32) {
-        auto term = [&](int j, double x, int) -> double { return __dmul_rn(x, w[j]); };
-        const double s = fold_rows<CW>(row0, n, rp, ci, v, term, tile);
+        double s;
+        if constexpr (CW <= 4) {
+            s = fold_rows_gather<CW>(row0, n, rp, ci, v, w, tile);
+        } else {
+            auto term = [&](int j, double x, int) -> double { return __dmul_rn(x, w[j]); };
+            s = fold_rows<CW>(row0, n, rp, ci, v, term, tile);
+        }
         const int i = row0 + lane;
         if (i < n) wout[i] = __dsub_rn(w[i], __ddiv_rn(s, dl1[i]));
     }
@@ -234,6 +310,13 @@ __device__ __forceinline__ bool nonzero_bits(double x) {
 __device__ __forceinline__ bool positive_bits(double x) {
     const long long b = dbits(x);
     return b > 0 && b <= 0x7ff0000000000000LL;
+}
+// 2 x, exact: one more in the exponent field for normal x away from the
+// top binade, else the FP64 multiply.
+__device__ __forceinline__ double twice(double x) {
+    const long long b = dbits(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    return (e >= 1 && e <= 2045) ? __longlong_as_double(b + (1LL << 52)) : __dmul_rn(2.0, x);
 }
 __device__ __forceinline__ bool nan_bits(double x) {
     return (dbits(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
@@ -269,7 +352,7 @@ __global__ void k_edge_keys(int n, const int64_t* __restrict__ rp, const int32_t
             if (nonzero_bits(a)) {
                 const double wj = w[j];
                 const double wj2 = __dmul_rn(wj, wj);
-                const double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a), wi), wj);
+                const double num = __dmul_rn(__dmul_rn(twice(a), wi), wj);
                 const double den = __dadd_rn(kwi2, __dmul_rn(kii[j], wj2));
                 // w_i^2 + w_j^2 > 0: both squares are +0, positive, +inf or NaN
                 const bool nrm2_pos = !nan_bits(wi2) && !nan_bits(wj2) && (positive_bits(wi2) || positive_bits(wj2));
@@ -1356,9 +1439,15 @@ __global__ void k_run_rows(int n, const int64_t* __restrict__ rp, const int32_t*
         const int64_t L = first_break - b;
         bool ok = L >= 2 && L <= kMaxRunLen && (e - b) % L == 0 && (e - b) < 65536;
         if (ok) {
+            // offset within the run of entry k = b + 1 + lane + 32 s, kept
+            // incrementally (no division per entry)
+            const int Li = (int)L, step = 32 % Li;
+            int o = (1 + lane) % Li;
             for (int64_t k = b + 1 + lane; k < e; k += 32) {
                 const bool brk = ci[k] != ci[k - 1] + 1;
-                if (brk != ((k - b) % L == 0)) ok = false;
+                if (brk != (o == 0)) ok = false;
+                o += step;
+                if (o >= Li) o -= Li;
             }
         }
         ok = __all_sync(0xffffffffu, ok);
@@ -1465,7 +1554,7 @@ cudaError_t launch_testvec_sweep(const DevCSR& A, const double* dl1, const doubl
     AMG_TRY(cudaGetDevice(&dev));
     AMG_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (fold_narrow(A.n, sms))
-        k_testvec_sweep<8><<<AMG_GRID(blocks_for(A.n, kBlock, 4096)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val,
+        k_testvec_sweep<4><<<AMG_GRID(blocks_for(A.n, kBlock, 4096)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val,
                                                                                      dl1, w, wout);
     else
         k_testvec_sweep<32><<<AMG_GRID(blocks_for(A.n, kBlock, 4096)), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val,

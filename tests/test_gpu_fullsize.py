@@ -53,6 +53,10 @@ def test_fullsize_fp64_hierarchy_bit_exact(cube64):
         rp, ci, v = Ho.level_csr(l)
         assert np.array_equal(g["rowptr"], rp) and np.array_equal(g["col"], ci)
         assert np.array_equal(g["val"].view(np.uint64), v.view(np.uint64))
+        d, w = Ho.level_vectors(l)  # l1 diagonal and test vector (the wide-level folds)
+        assert np.array_equal(g["dl1"].view(np.uint64), d.view(np.uint64))
+        if g["w"] is not None:
+            assert np.array_equal(g["w"].view(np.uint64), w.view(np.uint64))
         if l < H.num_levels - 1:
             agg, pv = Ho.level_map(l)
             assert np.array_equal(g["agg"], agg) and np.array_equal(g["pval"].view(np.uint64), pv.view(np.uint64))

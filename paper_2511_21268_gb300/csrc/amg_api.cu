@@ -309,13 +309,10 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
     const int maxr = h->o.max_match_rounds;
     CK(cudaMemsetAsync(h->round_active, 0, sizeof(int) * (maxr + kRoundBatch), s));
     int rounds = 0, done = 0;
-    if (h->coop) {  // every round in one launch, one read
+    if (h->coop) {  // every round in one launch; its round count is read with the aggregation's counts
         CK(launch_match_rounds_coop(A, key, state, cand, h->round_active, lists, maxr, h->flag + 6, h->num_sms, s));
-        CK(cudaMemcpyAsync(h->flag_host, h->flag + 6, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h->flag_host + 40, h->flag + 6, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(h->flag_host + 32, h->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        rounds = h->flag_host[0];
-        if (rounds > maxr) return AMG_ERR_TIMEOUT;
         done = 1;
     }
     while (!done) {
@@ -335,41 +332,48 @@ int match_pass(amg_hierarchy* h, const DevCSR& A, const double* w, Pass& P, DevC
         }
         if (!done) rounds += cnt;
     }
-    P.rounds = rounds;
-    if (h->flag_host[32] & 64) return AMG_ERR_ARG;  // structurally unsymmetric matrix
-    // values symmetric in every bit: the Galerkin kernels may compute the
-    // lower triangle in place
-    const int bit_symmetric = (h->flag_host[32] & 128) ? 0 : 1;
     phase(h, 4);
+    // Aggregates and the coarse rows' widest candidate list are computed
+    // before the host learns the coarse size: the buffers sized by it take
+    // the fine size n (an upper bound), and one read brings back the coarse
+    // size, the widest list, and (cooperative matching) the round count and
+    // the edge-key flags.
     P.n = n;
     RC(dalloc(h, &P.mate, n));
     CK(launch_match_finish(n, state, P.mate, leader, s));
     int32_t* total = scr + scan_scratch_ints(n);
     CK(launch_exclusive_scan(leader, cidx, n, total, scr, s));
-    int nc = 0;
-    RC(read_scalar(h, total, &nc));
-    P.nc = nc;
     RC(dalloc(h, &P.agg, n));
     RC(dalloc(h, &P.pval, n));
     int32_t *mem0, *mem1;
     Tmp tm0(s), tm1(s);
-    RC(tm0.get(&mem0, nc));
-    RC(tm1.get(&mem1, nc));
-    RC(dalloc(h, wc, nc));
+    RC(tm0.get(&mem0, n));
+    RC(tm1.get(&mem1, n));
+    RC(dalloc(h, wc, n));
     CK(launch_aggregate(n, P.mate, cidx, w, P.agg, P.pval, mem0, mem1, *wc, s));
-    // Galerkin product of this pass
     phase(h, 5);
-    // widest candidate list of the coarse rows
     CK(cudaMemsetAsync(h->flag, 0, 3 * sizeof(int), s));
-    CK(launch_row_stats(A, mem0, mem1, nc, h->flag, s));
-    if (nc < (1 << 30)) {
-        CK(cudaMemcpyAsync(h->flag_host, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        if (h->flag_host[0] <= kGalWarpCand) {
-            RC(galerkin_warp(h, A, P, mem0, mem1, nc, h->flag_host[0], bit_symmetric, C));
-            phase(h, 1);
-            return AMG_OK;
-        }
+    CK(launch_row_stats(A, mem0, mem1, n, h->flag, s, total));
+    CK(cudaMemcpyAsync(h->flag_host, total, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->flag_host + 1, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h->coop) {
+        rounds = h->flag_host[40];
+        if (rounds > maxr) return AMG_ERR_TIMEOUT;
+    }
+    P.rounds = rounds;
+    if (h->flag_host[32] & 64) return AMG_ERR_ARG;  // structurally unsymmetric matrix
+    // values symmetric in every bit: the Galerkin kernels may compute the
+    // lower triangle in place
+    const int bit_symmetric = (h->flag_host[32] & 128) ? 0 : 1;
+    const int nc = h->flag_host[0];
+    const int maxcand_all = h->flag_host[1];
+    P.nc = nc;
+    // Galerkin product of this pass
+    if (nc < (1 << 30) && maxcand_all <= kGalWarpCand) {
+        RC(galerkin_warp(h, A, P, mem0, mem1, nc, maxcand_all, bit_symmetric, C));
+        phase(h, 1);
+        return AMG_OK;
     }
     // widest coarse-column span as well (one read)
     CK(launch_row_span(A, P.agg, mem0, mem1, nc, h->flag + 2, s));

@@ -289,7 +289,7 @@ cudaError_t launch_row_span(const DevCSR& A, const int32_t* agg, const int32_t* 
 cudaError_t launch_scan64(const int64_t* in, int64_t* out, int n, int64_t* scratch, cudaStream_t s);
 size_t scan64_scratch(int n);
 cudaError_t launch_row_stats(const DevCSR& A, const int32_t* mem0, const int32_t* mem1, int nc, int* maxcand,
-                             cudaStream_t s);
+                             cudaStream_t s, const int* nc_dev = nullptr);
 cudaError_t launch_compose(int n, int npass, const Pass* passes, int32_t* agg, double* pval, cudaStream_t s);
 cudaError_t launch_member_count(int n, const int32_t* agg, int nc, int32_t* cnt, cudaStream_t s);
 cudaError_t launch_member_fill(int n, const int32_t* agg, const int32_t* mem_ptr, int nc, int32_t* mem_idx,

@@ -1012,9 +1012,9 @@ __global__ void k_galerkin_bitmap(int nc, const int64_t* __restrict__ rp, const 
 // rounding (sym == 0) the lower entries are left to the mirror kernel.
 //
 // GB300 runs FP64 at about two lanes per SM per clock: the values kernel
-// spends 8 multiplies and 3 adds per entry with every lane busy, and keeps
-// its shared memory near 10 KB per row so that about 20 rows per SM are in
-// flight to cover the latency of the gathers (agg, mate, pval).
+// computes each candidate's term once, in the pass that gathers its coarse
+// column (2 multiplies, every lane busy), keeps it in shared memory, and
+// spends 3 adds per entry on the slot sums.
 constexpr int kGalWarps = 4;   // coarse rows per block
 constexpr int kGalBatch = 8;   // candidates per lane in flight in the gathers
 constexpr unsigned kNoSlot = 0xffffu;
@@ -1063,7 +1063,8 @@ __global__ void __launch_bounds__(kGalWarps * 32)
                     const int64_t* __restrict__ crp, int32_t* cci, double* cv, int* stats, int* flag) {
     extern __shared__ __align__(16) unsigned char gsm[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const size_t o_bits = gal_align(4 * (size_t)cmax);
+    const size_t o_tb = gal_align(4 * (size_t)cmax);
+    const size_t o_bits = o_tb + (FILL ? gal_align(8 * (size_t)cmax) : 0);
     const size_t o_pre = o_bits + gal_align(4 * (size_t)words);
     const size_t o_sidx = o_pre + (FILL ? gal_align(2 * (size_t)words) : 0);
     const size_t per_warp = o_sidx + (FILL ? gal_align(8 * (size_t)umax) : 0);
@@ -1072,6 +1073,7 @@ __global__ void __launch_bounds__(kGalWarps * 32)
     uint32_t* bits = reinterpret_cast<uint32_t*>(my + o_bits);
     uint16_t* pre = reinterpret_cast<uint16_t*>(my + o_pre);     // FILL: entries before each word
     uint2* sidx = reinterpret_cast<uint2*>(my + o_sidx);          // FILL: four 16-bit slots per entry
+    double* tb = reinterpret_cast<double*>(my + o_tb);            // FILL: the candidates' terms
     const int stride = gridDim.x * kGalWarps;
     int I = blockIdx.x * kGalWarps + wid;
     GalRow cur = gal_members(I < nc ? mem0[I] : -1, I < nc ? mem1[I] : -1, rp);
@@ -1084,21 +1086,36 @@ __global__ void __launch_bounds__(kGalWarps * 32)
         if (!fits) err = 1;
         int lo = 0x7fffffff, hi = -1;
         if (fits) {
+            // FILL: the member rows' prolongator values, for the terms
+            const double p0 = (FILL && c > 0) ? pval[cur.a0] : 0.0;
+            const double p1 = (FILL && cur.a1 >= 0) ? pval[cur.a1] : 0.0;
             for (int t0 = 0; t0 < c; t0 += 32 * kGalBatch) {
                 int bb[kGalBatch], jj[kGalBatch], mm[kGalBatch];
+                double vk[kGalBatch], pb[kGalBatch];
 #pragma unroll
                 for (int r = 0; r < kGalBatch; r++) {
                     const int t = t0 + 32 * r + lane;
-                    bb[r] = t < c ? ci[t < len0 ? cur.b0 + t : cur.b1 + (t - len0)] : -1;
+                    const int64_t k = t < len0 ? cur.b0 + t : cur.b1 + (t - len0);
+                    bb[r] = t < c ? ci[k] : -1;
+                    vk[r] = (FILL && t < c) ? v[k] : 0.0;
                 }
 #pragma unroll
                 for (int r = 0; r < kGalBatch; r++) {
                     jj[r] = bb[r] >= 0 ? agg[bb[r]] : 0;
                     mm[r] = (FILL && bb[r] >= 0) ? mate[bb[r]] : -1;
+                    pb[r] = (FILL && bb[r] >= 0) ? pval[bb[r]] : 0.0;
                 }
 #pragma unroll
                 for (int r = 0; r < kGalBatch; r++) {
+                    if (FILL && t0 + 32 * r >= c) break;  // warp-uniform: no FP64 issue for empty rounds
                     const int t = t0 + 32 * r + lane;
+                    if (FILL) {
+                        // (p_a K(a,b)) p_b for J >= I, (p_b K(a,b)) p_a for J < I
+                        const bool upper = jj[r] >= I;
+                        const double pa = t >= len0 ? p1 : p0;
+                        const double term = __dmul_rn(__dmul_rn(upper ? pa : pb[r], vk[r]), upper ? pb[r] : pa);
+                        if (t < c) tb[t] = term;
+                    }
                     if (t < c) {
                         lo = min(lo, jj[r]);
                         hi = max(hi, jj[r]);
@@ -1171,32 +1188,16 @@ __global__ void __launch_bounds__(kGalWarps * 32)
                     reinterpret_cast<uint16_t*>(sidx)[4 * pos + q] = (uint16_t)t;
                 }
                 __syncwarp();
-                // entries: the slots' terms and their ordered sum
+                // entries: their slots' terms summed in slot order
                 const int64_t base = crp[I];
-                const double p0 = pval[cur.a0], p1 = cur.a1 >= 0 ? pval[cur.a1] : 0.0;
                 for (int pos = lane; pos < u; pos += 32) {
                     const uint2 raw = sidx[pos];
                     const unsigned tq[4] = {raw.x & 0xffffu, raw.x >> 16, raw.y & 0xffffu, raw.y >> 16};
-                    int64_t kk[4];
-                    int bq[4];
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        const int t = (int)tq[q];
-                        kk[q] = t < len0 ? cur.b0 + t : cur.b1 + (t - len0);
-                        bq[q] = tq[q] != kNoSlot ? ci[kk[q]] : -1;
-                    }
                     const unsigned tv = tq[0] != kNoSlot ? tq[0] : tq[1] != kNoSlot ? tq[1] : tq[2] != kNoSlot ? tq[2] : tq[3];
                     const int J = jb[min((int)tv, c - 1)] >> 1;  // every entry holds a candidate
-                    const bool upper = J >= I;
                     double term[4];
 #pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        const double vk = bq[q] >= 0 ? v[kk[q]] : 0.0;
-                        const double pb = bq[q] >= 0 ? pval[bq[q]] : 0.0;
-                        const int ra = upper ? (q >> 1) : (q & 1);
-                        const double pa = ra ? p1 : p0;
-                        term[q] = __dmul_rn(__dmul_rn(upper ? pa : pb, vk), upper ? pb : pa);
-                    }
+                    for (int q = 0; q < 4; q++) term[q] = tq[q] != kNoSlot ? tb[tq[q]] : 0.0;
                     // +0.0 + term[0] without an FP64 add: only -0.0 changes (to +0.0)
                     double acc = dbits(term[0]) == (long long)0x8000000000000000ULL ? 0.0 : term[0];
                     acc = __dadd_rn(acc, term[1]);
@@ -1249,7 +1250,8 @@ __global__ void k_row_span(int nc, const int64_t* __restrict__ rp, const int32_t
 
 // max over coarse rows of the candidate count len(a0) + len(a1)
 __global__ void k_row_stats(int nc, const int64_t* __restrict__ rp, const int32_t* __restrict__ mem0,
-                            const int32_t* __restrict__ mem1, int* maxcand) {
+                            const int32_t* __restrict__ mem1, int* maxcand, const int* __restrict__ nc_dev) {
+    if (nc_dev) nc = *nc_dev;  // the coarse row count as the scan left it on the device
     int m = 0;
     for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
         const int a0 = mem0[I], a1 = mem1[I];
@@ -1325,6 +1327,7 @@ __global__ void k_dense_from_csr(int n, const int64_t* __restrict__ rp, const in
 // Right-looking Cholesky D = L L^T in place (lower triangle, one block).
 __global__ void k_cholesky(int n, double* D, int* flag) {
     __shared__ double piv;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int j = 0; j < n; j++) {
         if (threadIdx.x == 0) {
             const double djj = D[(int64_t)j * n + j];
@@ -1339,48 +1342,49 @@ __global__ void k_cholesky(int n, double* D, int* flag) {
         __syncthreads();
         const double ljj = piv;
         for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x)
-            D[(int64_t)i * n + j] = __ddiv_rn(D[(int64_t)i * n + j], ljj);
+            D[(int64_t)i * n + j] = div_rn(D[(int64_t)i * n + j], ljj);  // correctly rounded, short latency
         __syncthreads();
-        const int m = n - j - 1;
-        for (int64_t t = threadIdx.x; t < (int64_t)m * m; t += blockDim.x) {
-            const int i = j + 1 + (int)(t / m), k = j + 1 + (int)(t % m);
-            if (k <= i)
-                D[(int64_t)i * n + k] =
-                    __dsub_rn(D[(int64_t)i * n + k], __dmul_rn(D[(int64_t)i * n + j], D[(int64_t)k * n + j]));
+        // trailing update, a warp per row i > j, its lanes over the columns k in (j, i]
+        for (int i = j + 1 + wid; i < n; i += nwarps) {
+            const double lij = D[(int64_t)i * n + j];
+            for (int k = j + 1 + lane; k <= i; k += 32)
+                D[(int64_t)i * n + k] = __dsub_rn(D[(int64_t)i * n + k], __dmul_rn(lij, D[(int64_t)k * n + j]));
         }
         __syncthreads();
     }
 }
 
-// Column c of A^-1 = L^-T L^-1 e_c, one block per column.
+// Column c of A^-1 = L^-T L^-1 e_c, a warp per column: forward substitution
+// from row c (the rows above hold zeros), then backward substitution; each
+// step scales by the diagonal's reciprocal and updates the remaining rows
+// lane-parallel, so a step costs one multiply's latency rather than a
+// division's and a block barrier.
 __global__ void k_chol_inverse(int n, const double* __restrict__ L, double* Ainv, double* work) {
-    for (int c = blockIdx.x; c < n; c += gridDim.x) {
+    extern __shared__ double rinv[];  // reciprocals of the factor's diagonal
+    for (int i = threadIdx.x; i < n; i += blockDim.x) rinv[i] = __ddiv_rn(1.0, L[(int64_t)i * n + i]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int c = gw; c < n; c += nw) {
         double* y = work + (int64_t)c * n;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (i == c) ? 1.0 : 0.0;
-        __syncthreads();
-        for (int k = 0; k < n; k++) {  // forward: L y = e_c
-            __shared__ double yk;
-            if (threadIdx.x == 0) {
-                yk = __ddiv_rn(y[k], L[(int64_t)k * n + k]);
-                y[k] = yk;
-            }
-            __syncthreads();
-            for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x)
-                y[i] = __dsub_rn(y[i], __dmul_rn(L[(int64_t)i * n + k], yk));
-            __syncthreads();
+        for (int i = lane; i < n; i += 32) y[i] = (i == c) ? 1.0 : 0.0;
+        __syncwarp();
+        for (int k = c; k < n; k++) {  // forward: L y = e_c
+            const double yk = __dmul_rn(y[k], rinv[k]);
+            __syncwarp();
+            if (lane == 0) y[k] = yk;
+            for (int i = k + 1 + lane; i < n; i += 32) y[i] = __dsub_rn(y[i], __dmul_rn(L[(int64_t)i * n + k], yk));
+            __syncwarp();
         }
         for (int k = n - 1; k >= 0; k--) {  // backward: L^T x = y
-            __shared__ double xk;
-            if (threadIdx.x == 0) {
-                xk = __ddiv_rn(y[k], L[(int64_t)k * n + k]);
-                y[k] = xk;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = __dsub_rn(y[i], __dmul_rn(L[(int64_t)k * n + i], xk));
-            __syncthreads();
+            const double xk = __dmul_rn(y[k], rinv[k]);
+            __syncwarp();
+            if (lane == 0) y[k] = xk;
+            for (int i = lane; i < k; i += 32) y[i] = __dsub_rn(y[i], __dmul_rn(L[(int64_t)k * n + i], xk));
+            __syncwarp();
         }
-        for (int i = threadIdx.x; i < n; i += blockDim.x) Ainv[(int64_t)i * n + c] = y[i];
-        __syncthreads();
+        for (int i = lane; i < n; i += 32) Ainv[(int64_t)i * n + c] = y[i];
+        __syncwarp();
     }
 }
 
@@ -1699,7 +1703,7 @@ constexpr int kGalCountWords = 1024;
 static size_t galerkin_warp_bytes(int cmax, int words, int umax, bool fill) {
     auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
     const size_t w = al(4 * (size_t)cmax) + al(4 * (size_t)words) +
-                     (fill ? al(2 * (size_t)words) + al(8 * (size_t)umax) : 0);
+                     (fill ? al(8 * (size_t)cmax) + al(2 * (size_t)words) + al(8 * (size_t)umax) : 0);
     return w * kGalWarps;
 }
 
@@ -1707,12 +1711,31 @@ size_t galerkin_warp_fill_smem(int cmax, int words, int umax) {
     return galerkin_warp_bytes(cmax, words, umax, true);
 }
 
+// Blocks of `kernel` that can be resident on the device at once (at least
+// one): the warp-per-row kernels loop over their rows from that many blocks,
+// so that each warp takes row after row (and loads the next row's members
+// early) instead of one block being scheduled per few rows.
+template <typename K>
+static cudaError_t resident_blocks(K kernel, int threads, size_t smem, int* blocks) {
+    int dev = 0, sms = 0, per_sm = 0;
+    AMG_TRY(cudaGetDevice(&dev));
+    AMG_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    AMG_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
+    *blocks = std::max(1, per_sm * sms);
+    return cudaSuccess;
+}
+
 cudaError_t launch_galerkin_warp_count(const DevCSR& A, const int32_t* agg, const int32_t* mem0, const int32_t* mem1,
                                        int nc, int cmax, int64_t* rowcnt, int* stats, int* flag, cudaStream_t s) {
     const size_t sm = galerkin_warp_bytes(cmax, kGalCountWords, 0, false);
     if (sm > 48 * 1024)
         AMG_TRY(cudaFuncSetAttribute(k_galerkin_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_galerkin_warp<false><<<AMG_GRID(blocks_for(nc, kGalWarps, 1 << 20)), kGalWarps * 32, sm, s>>>(
+    // rows in flight are bounded by shared memory: ask for the largest carveout
+    AMG_TRY(cudaFuncSetAttribute(k_galerkin_warp<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared));
+    int res = 0;
+    AMG_TRY(resident_blocks(k_galerkin_warp<false>, kGalWarps * 32, sm, &res));
+    k_galerkin_warp<false><<<AMG_GRID(std::min(blocks_for(nc, kGalWarps, 1 << 20), res)), kGalWarps * 32, sm, s>>>(
         nc, A.rowptr, A.col, A.val, agg, nullptr, nullptr, mem0, mem1, cmax, kGalCountWords, 0, 0, rowcnt, nullptr,
         nullptr, nullptr, stats, flag);
     return cudaGetLastError();
@@ -1724,7 +1747,11 @@ cudaError_t launch_galerkin_warp_fill(const DevCSR& A, const int32_t* agg, const
     const size_t sm = galerkin_warp_bytes(cmax, words, umax, true);
     if (sm > 48 * 1024)
         AMG_TRY(cudaFuncSetAttribute(k_galerkin_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_galerkin_warp<true><<<AMG_GRID(blocks_for(C.n, kGalWarps, 1 << 20)), kGalWarps * 32, sm, s>>>(
+    AMG_TRY(cudaFuncSetAttribute(k_galerkin_warp<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared));
+    int res = 0;
+    AMG_TRY(resident_blocks(k_galerkin_warp<true>, kGalWarps * 32, sm, &res));
+    k_galerkin_warp<true><<<AMG_GRID(std::min(blocks_for(C.n, kGalWarps, 1 << 20), res)), kGalWarps * 32, sm, s>>>(
         C.n, A.rowptr, A.col, A.val, agg, pval, mate, mem0, mem1, cmax, words, umax, sym, nullptr, C.rowptr, C.col,
         C.val, nullptr, flag);
     return cudaGetLastError();
@@ -1738,8 +1765,9 @@ cudaError_t launch_row_span(const DevCSR& A, const int32_t* agg, const int32_t* 
 }
 
 cudaError_t launch_row_stats(const DevCSR& A, const int32_t* mem0, const int32_t* mem1, int nc, int* maxcand,
-                             cudaStream_t s) {
-    k_row_stats<<<AMG_GRID(blocks_for(nc, kBlock, 4096)), kBlock, 0, s>>>(nc, A.rowptr, mem0, mem1, maxcand);
+                             cudaStream_t s, const int* nc_dev) {
+    // nc_dev: read the row count there (nc then bounds it, for the grid)
+    k_row_stats<<<AMG_GRID(blocks_for(nc, kBlock, 4096)), kBlock, 0, s>>>(nc, A.rowptr, mem0, mem1, maxcand, nc_dev);
     return cudaGetLastError();
 }
 
@@ -1784,7 +1812,9 @@ __global__ void k_keep_factor(int n, const double* __restrict__ D, double* L) {
 // the second n^2 (work space of the inverse before).
 cudaError_t launch_dense_spd_inverse(int n, double* D, double* Ainv, int* flag, cudaStream_t s) {
     k_cholesky<<<AMG_GRID(1), 1024, 0, s>>>(n, D, flag);
-    k_chol_inverse<<<AMG_GRID(blocks_for(n, 1, 4096)), kBlock, 0, s>>>(n, D, Ainv, Ainv + (int64_t)n * n);
+    const size_t sm = sizeof(double) * (size_t)n;  // the diagonal's reciprocals (n <= 4096: 32 KB)
+    if (sm > 48 * 1024) AMG_TRY(cudaFuncSetAttribute(k_chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_chol_inverse<<<AMG_GRID(blocks_for(n, kWarpsPerBlock, 4096)), kBlock, sm, s>>>(n, D, Ainv, Ainv + (int64_t)n * n);
     k_keep_factor<<<AMG_GRID(blocks_for((int64_t)n * n, kBlock, 1024)), kBlock, 0, s>>>(n, D, Ainv + (int64_t)n * n);
     return cudaGetLastError();
 }

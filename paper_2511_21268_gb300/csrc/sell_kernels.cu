@@ -813,8 +813,9 @@ __global__ void __launch_bounds__(256) k_sell_fill(int n, int nsl, int G, int LM
         const int rbase = rptr[a], rend = rptr[e];
         const bool staged = eend - ebase <= cap && rend - rbase <= capr;
         __syncthreads();  // the previous slab's readers are done
-        if (staged) {  // eight loads in flight per thread before the stores
-            constexpr int U = 8;
+        if (staged) {  // U loads in flight per thread before the stores (a slab of FP64 values
+                       // fills most of the shared memory, so few blocks share an SM)
+            constexpr int U = sizeof(T) == 8 ? 24 : 8;
             for (int64_t q0 = ebase + threadIdx.x; q0 < eend; q0 += U * blockDim.x) {
                 T t[U];
 #pragma unroll

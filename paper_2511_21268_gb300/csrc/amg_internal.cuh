@@ -414,8 +414,9 @@ __device__ __forceinline__ uint64_t order_key(double c) {
 // bits as __ddiv_rn(a, b), in fewer FP64 operations for operands of
 // moderate magnitude (both normal, binary exponents in [-500, 500]); other
 // operands go to __ddiv_rn.
-//   1. y0 ~ 1/b: the FP32 reciprocal of b's leading 23 mantissa bits, scaled
-//      by integer exponent arithmetic (relative error below 2^-22).
+//   1. y0 ~ 1/b: the FP32 reciprocal (SFU approximation) of b's leading 23
+//      mantissa bits, scaled by integer exponent arithmetic (relative error
+//      about 2^-22).
 //   2. One Newton-Raphson step, y1 = y0 + y0 (1 - b y0) (error below 2^-44).
 //   3. q0 = a y1 and Markstein's correction q = q0 + (a - b q0) y1, whose
 //      value before rounding lies within about 2^-89 (relative) of a / b.
@@ -436,7 +437,9 @@ __device__ __forceinline__ bool div_rn_fast(double a, double b, double* q_out) {
     if (ea < -500 || ea > 500 || eb < -500 || eb > 500) return false;
     // 1. reciprocal estimate: f = 1.m (FP32, top 23 mantissa bits), 1/f in (1/2, 1]
     const float f = __int_as_float(0x3f800000 | (int)((bb >> 29) & 0x7fffff));
-    const int rf = __float_as_int(__frcp_rn(f));
+    float rcp;  // PTX rcp.approx.ftz.f32: the SFU reciprocal, about 1 ulp of FP32
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rcp) : "f"(f));
+    const int rf = __float_as_int(rcp);
     const int erf = ((rf >> 23) & 0xff) - 127;  // -1 or 0
     const long long y0b = (bb & (long long)0x8000000000000000ULL) | ((long long)(erf - eb + 1023) << 52) |
                           ((long long)(rf & 0x7fffff) << 29);
@@ -458,9 +461,13 @@ __device__ __forceinline__ bool div_rn_fast(double a, double b, double* q_out) {
     return true;
 }
 
+// The fallback is a call, so that none of the compiler's division is
+// scheduled speculatively ahead of the fast path's test.
+static __device__ __noinline__ double div_rn_slow(double a, double b) { return __ddiv_rn(a, b); }
+
 __device__ __forceinline__ double div_rn(double a, double b) {
     double q;
-    return div_rn_fast(a, b, &q) ? q : __ddiv_rn(a, b);
+    return div_rn_fast(a, b, &q) ? q : div_rn_slow(a, b);
 }
 
 // SplitMix64 (Steele, Lea, Flood 2014): draw k of the stream seeded `seed`.

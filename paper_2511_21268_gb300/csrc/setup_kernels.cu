@@ -57,7 +57,7 @@ __global__ void k_validate(int n, int64_t nnz, const int64_t* __restrict__ rp, c
             int j = ci[k];
             if (j < 0 || j >= n) bad |= 1;
             if (k > b && ci[k - 1] >= j) bad |= 1;
-            if (!isfinite(v[k])) bad |= 2;
+            if (((dbits(v[k]) >> 52) & 0x7ff) == 0x7ff) bad |= 2;  // inf or NaN, decided on the bits
             if (j == i) has_diag = true;
         }
         bad = __reduce_or_sync(FULL, bad);
@@ -311,12 +311,20 @@ __device__ __forceinline__ bool positive_bits(double x) {
     const long long b = dbits(x);
     return b > 0 && b <= 0x7ff0000000000000LL;
 }
-// 2 x, exact: one more in the exponent field for normal x away from the
-// top binade, else the FP64 multiply.
+// 2 x on the bits, no FP64 instruction: one more in the exponent field for
+// normal x below the top binade; a subnormal's significand doubles (a carry
+// into the exponent field makes it normal); the top binade overflows to
+// infinity; infinity stays.  (NaN does not reach it: the matrix is checked
+// for non-finite values.)
 __device__ __forceinline__ double twice(double x) {
-    const long long b = dbits(x);
-    const int e = (int)((b >> 52) & 0x7ff);
-    return (e >= 1 && e <= 2045) ? __longlong_as_double(b + (1LL << 52)) : __dmul_rn(2.0, x);
+    const unsigned long long u = (unsigned long long)dbits(x);
+    const unsigned long long sign = u & 0x8000000000000000ULL, mag = u & 0x7fffffffffffffffULL;
+    const int e = (int)(mag >> 52);
+    unsigned long long r = u;
+    if (e == 0) r = sign | (mag << 1);
+    else if (e < 2046) r = u + (1ULL << 52);
+    else if (e == 2046) r = sign | 0x7ff0000000000000ULL;
+    return __longlong_as_double((long long)r);
 }
 __device__ __forceinline__ bool nan_bits(double x) {
     return (dbits(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;

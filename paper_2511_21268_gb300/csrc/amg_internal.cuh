@@ -444,13 +444,15 @@ __device__ __forceinline__ bool div_rn_fast(double a, double b, double* q_out) {
     const long long y0b = (bb & (long long)0x8000000000000000ULL) | ((long long)(erf - eb + 1023) << 52) |
                           ((long long)(rf & 0x7fffff) << 29);
     const double y0 = __longlong_as_double(y0b);
+    // -b by its sign bit (an integer operation)
+    const double nb = __longlong_as_double(bb ^ (long long)0x8000000000000000ULL);
     // 2. Newton-Raphson step
-    const double y1 = __fma_rn(y0, __fma_rn(-b, y0, 1.0), y0);
+    const double y1 = __fma_rn(y0, __fma_rn(nb, y0, 1.0), y0);
     // 3. quotient and correction
     const double q0 = __dmul_rn(a, y1);
-    const double q = __fma_rn(__fma_rn(-b, q0, a), y1, q0);
+    const double q = __fma_rn(__fma_rn(nb, q0, a), y1, q0);
     // 4. exact residual and acceptance test on the bits
-    const double r = __fma_rn(-b, q, a);
+    const double r = __fma_rn(nb, q, a);
     const long long qb = dbits(q) & 0x7fffffffffffffffLL;
     const int eq = (int)(qb >> 52) - 1023;
     const int k = ((qb & 0xfffffffffffffLL) == 0 ? eq - 54 : eq - 53);  // log2 of h(q)

@@ -168,6 +168,42 @@ struct SlotDot<LM, LM, V> {
     static __device__ __forceinline__ void run(uint32_t, uint32_t, float&, float&) {}
 };
 
+// BF16 run slots hold their values in pairs: value pair p (values 2p, 2p+1)
+// of lane t at 4 (p 32 + t) bytes, then (odd LM) the last value at 2 (2P 32
+// + t) bytes past the P = LM / 2 pairs.  One 4-byte load brings two values,
+// so a slot of 7 costs 4 shared-memory loads instead of 7 (the BF16 passes
+// are bound by the SM's shared-memory wavefronts, not by the FMAs).  The
+// FMAs and their accumulators are the same as value by value.
+template <int LM>
+__device__ __forceinline__ void slot_dot_bf16(uint32_t sbase, int lane, uint32_t xa, float& a0, float& a1) {
+    constexpr int P = LM / 2;
+    const uint32_t pa = sbase + 4u * (uint32_t)lane;
+#pragma unroll
+    for (int p = 0; p < P; p++) {
+        uint32_t u;
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(u) : "r"(pa + 4u * kSlab * (uint32_t)p));
+        const float v0 = __uint_as_float(u << 16), v1 = __uint_as_float(u & 0xffff0000u);
+        float x0, x1;
+        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(x0) : "r"(xa + 8u * (uint32_t)p));
+        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(x1) : "r"(xa + 8u * (uint32_t)p + 4u));
+        a0 = fmaf(v0, x0, a0);
+        a1 = fmaf(v1, x1, a1);
+    }
+    if constexpr (LM & 1) {
+        unsigned short h;
+        asm volatile("ld.shared.u16 %0, [%1];" : "=h"(h) : "r"(sbase + 4u * kSlab * P + 2u * (uint32_t)lane));
+        float x2;
+        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(x2) : "r"(xa + 8u * P));
+        a0 = fmaf(__uint_as_float((uint32_t)h << 16), x2, a0);
+    }
+}
+
+// Position of value o of lane t in a BF16 run slot of LM values (above).
+__device__ __forceinline__ int bf16_slot_pos(int o, int t, int LM) {
+    const int P = LM / 2;
+    return o < 2 * P ? ((o >> 1) * kSlab + t) * 2 + (o & 1) : 2 * P * kSlab + t;
+}
+
 // Block b owns slabs [b nsl / G, (b + 1) nsl / G) and the vector window
 // win[b] = (lo, hi), the smallest and largest column its slabs read.  The
 // epilogue vectors are read in 16-byte-widened segments of the slab's rows
@@ -346,7 +382,10 @@ __global__ void __launch_bounds__(kSellThreads, 1)
 #pragma unroll 1
             for (; r < R; r += kStreamWarps) {
                 const uint32_t xa = xbase + 4u * lds_u16(ra0 + (uint32_t)r * (uint32_t)(kSlab * 2));
-                SlotDot<0, LM, V>::run(va0 + (uint32_t)r * (uint32_t)(LM * kSlab * sizeof(V)), xa, a0, a1);
+                if constexpr (LM > 1 && sizeof(V) == 2)
+                    slot_dot_bf16<LM>(smem_addr(bv) + (uint32_t)r * (uint32_t)(LM * kSlab * 2), lane, xa, a0, a1);
+                else
+                    SlotDot<0, LM, V>::run(va0 + (uint32_t)r * (uint32_t)(LM * kSlab * sizeof(V)), xa, a0, a1);
             }
             float* part = reinterpret_cast<float*>(bv + o_part);
             part[wid * kSlab + lane] = a0 + a1;
@@ -782,7 +821,8 @@ __global__ void k_sell_intervals(int G, const int2* __restrict__ win, const int*
 }
 
 // Fill the sliced copy, a thread block per slab: FP32 values, BF16 values
-// (if o16: rounded from the FP32 value, as the BF16 copy of the level is)
+// (if o16: rounded from the FP32 value, as the BF16 copy of the level is;
+// stored in value pairs within each run slot, see slot_dot_bf16)
 // and the compacted-window offsets of the slot starts.  The slab's rows are
 // consecutive, so their CSR values and run starts are two contiguous ranges:
 // the block stages them in shared memory (sized for the largest slab: cap
@@ -885,8 +925,10 @@ __global__ void __launch_bounds__(256) k_sell_fill(int n, int nsl, int G, int LM
             }
             const int64_t dst = (((int64_t)o0 + r) * LM + o) * kSlab + t;
             o32[dst] = val;
-            if constexpr (sizeof(T) == 4)
-                if (o16) o16[dst] = __float2bfloat16_rn(val);
+            if constexpr (sizeof(T) == 4)  // BF16 slots in value pairs (slot_dot_bf16)
+                if (o16)
+                    o16[((int64_t)o0 + r) * LM * kSlab + (LM > 1 ? bf16_slot_pos(o, t, LM) : t)] =
+                        __float2bfloat16_rn(val);
         }
     }
 }

@@ -11,7 +11,9 @@ candidate passes only if it is the correctly rounded quotient, and the
 correctly rounded quotient passes except when a / b lies in the outer half
 of the wider side of a power of two (where the GPU falls back to the
 compiler's division).  The GPU side is held to IEEE quotients by
-tests/test_gpu_divide.py.
+tests/test_gpu_divide.py.  The last test does the same for the edge
+weights' exact doubling 2 a on integer bits (normal, subnormal, overflowing
+and infinite a), against the IEEE product.
 """
 import math
 from fractions import Fraction
@@ -70,3 +72,42 @@ def test_the_correctly_rounded_quotient_passes_unless_beside_a_power_of_two():
             exact = Fraction(a) / Fraction(b)
             assert abs(exact) > abs(Fraction(q)), (a, b, q)
     assert rejected < 0.05 * len(A)
+
+
+def _bits(x: float) -> int:
+    import struct
+    return struct.unpack("<Q", struct.pack("<d", x))[0]
+
+
+def _from_bits(u: int) -> float:
+    import struct
+    return struct.unpack("<d", struct.pack("<Q", u & 0xFFFFFFFFFFFFFFFF))[0]
+
+
+def twice_bits(x: float) -> float:
+    """The edge weights' exact doubling on integer bits, as the GPU code
+    takes it: exponent + 1 for normal x below the top binade, the
+    significand shifted for a subnormal (a carry makes it normal), infinity
+    from the top binade, infinity kept."""
+    u = _bits(x)
+    sign, mag = u & 0x8000000000000000, u & 0x7FFFFFFFFFFFFFFF
+    e = mag >> 52
+    if e == 0:
+        return _from_bits(sign | (mag << 1))
+    if e < 2046:
+        return _from_bits(u + (1 << 52))
+    if e == 2046:
+        return _from_bits(sign | 0x7FF0000000000000)
+    return x
+
+
+def test_doubling_on_the_bits_equals_the_product():
+    rng = np.random.default_rng(4)
+    xs = [0.0, -0.0, 5e-324, -5e-324, 2.2250738585072009e-308, 2.2250738585072014e-308, 1.1125369292536007e-308,
+          1.7976931348623157e308, -1.7976931348623157e308, 8.98846567431158e307, math.inf, -math.inf, 1.0, -3.5]
+    xs += (rng.standard_normal(2000) * np.exp2(rng.integers(-1074, 1024, 2000))).tolist()
+    with np.errstate(over="ignore"):
+        for x in xs:
+            want = float(np.float64(2.0) * np.float64(x))
+            got = twice_bits(x)
+            assert _bits(got) == _bits(want), (x, got, want)
